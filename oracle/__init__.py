@@ -1,0 +1,194 @@
+"""FP64 CPU oracle for the point-cloud Fresnel hologram (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the library itself
+never does, and it shares no code with the CUDA path.
+
+The arithmetic lives in ``cgh_oracle.c`` (plain C, double precision, libm
+cos/sin, OpenMP over rows).  This module compiles it with gcc on first use and
+wraps it with ctypes.  Every function cites the passage it follows:
+
+* ``field``/``field_at``: Eq. 2 and Eq. 5 of Section 2.1, without the per-point
+  piston and reference phase,
+  I(m, n) = sum_j A_j cos(pi p^2/(lambda z_j) ((m - x_j)^2 + (n - y_j)^2)).
+* ``wave``: the complex object wave of Eq. 2 (same restriction), for Eq. 3.
+* ``factors``: the separable factor matrices P, Q with I = P Q^T.
+* ``quantize8``: the min/max 8-bit quantiser (the listings of Section 4.1
+  quantise a phase with 255/(2 pi); this is the amplitude counterpart).
+* ``recurrence_phases``: Eqs. 6-8 (Section 2.2) iterated in exact rationals.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from fractions import Fraction
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cgh_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_F32P = ctypes.POINTER(ctypes.c_float)
+_F64P = ctypes.POINTER(ctypes.c_double)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile cgh_oracle.c into liboracle.so (gcc, OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-std=c11", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_field_window.argtypes = [ctypes.c_double, ctypes.c_double, _F32P, _F32P,
+                                                ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, _F64P]
+            lib.oracle_field_points.argtypes = [ctypes.c_double, ctypes.c_double, _F32P, _F32P,
+                                                ctypes.c_int64, _I32P, _I32P, ctypes.c_int64, _F64P]
+            lib.oracle_wave_window.argtypes = [ctypes.c_double, ctypes.c_double, _F32P, _F32P,
+                                               ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, _F64P, _F64P]
+            lib.oracle_factors.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           _F32P, _F32P, ctypes.c_int64, _F64P, _F64P]
+            lib.oracle_quantize8.argtypes = [_F32P, ctypes.c_int64, _U8P, _F32P]
+            _lib = lib
+    return _lib
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def field(pitch_m: float, lambda_m: float, xyz, amp, width: int, height: int,
+          window: Optional[Sequence[int]] = None) -> np.ndarray:
+    """I(m, n) of Eq. 5 (restricted form) in FP64, [rows][cols].
+
+    window = (row0, col0, rows, cols); default the whole width x height hologram.
+    """
+    xyz = _f32(xyz).reshape(-1, 3)
+    amp = _f32(amp).reshape(-1)
+    if window is None:
+        window = (0, 0, height, width)
+    r0, c0, rows, cols = (int(v) for v in window)
+    out = np.empty((rows, cols), dtype=np.float64)
+    rc = _load().oracle_field_window(float(pitch_m), float(lambda_m), _ptr(xyz, _F32P), _ptr(amp, _F32P),
+                                     amp.shape[0], r0, rows, c0, cols, _ptr(out, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_field_window rejected its arguments")
+    return out
+
+
+def field_at(pitch_m: float, lambda_m: float, xyz, amp, cols, rows) -> np.ndarray:
+    """I at scattered pixels (cols[i], rows[i]) in FP64."""
+    xyz = _f32(xyz).reshape(-1, 3)
+    amp = _f32(amp).reshape(-1)
+    pm = np.ascontiguousarray(cols, dtype=np.int32)
+    pn = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.empty(pm.shape[0], dtype=np.float64)
+    rc = _load().oracle_field_points(float(pitch_m), float(lambda_m), _ptr(xyz, _F32P), _ptr(amp, _F32P),
+                                     amp.shape[0], _ptr(pm, _I32P), _ptr(pn, _I32P), pm.shape[0],
+                                     _ptr(out, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_field_points rejected its arguments")
+    return out
+
+
+def wave(pitch_m: float, lambda_m: float, xyz, amp, width: int, height: int,
+         window: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Complex object wave O(m, n) of Eq. 2 (restricted form), complex128 [rows][cols]."""
+    xyz = _f32(xyz).reshape(-1, 3)
+    amp = _f32(amp).reshape(-1)
+    if window is None:
+        window = (0, 0, height, width)
+    r0, c0, rows, cols = (int(v) for v in window)
+    re = np.empty((rows, cols), dtype=np.float64)
+    im = np.empty((rows, cols), dtype=np.float64)
+    rc = _load().oracle_wave_window(float(pitch_m), float(lambda_m), _ptr(xyz, _F32P), _ptr(amp, _F32P),
+                                    amp.shape[0], r0, rows, c0, cols, _ptr(re, _F64P), _ptr(im, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_wave_window rejected its arguments")
+    return re + 1j * im
+
+
+def factors(pitch_m: float, lambda_m: float, xyz, amp, width: int, height: int):
+    """Separable factors (P [height][2N], Q [width][2N]) in FP64 with I = P Q^T."""
+    xyz = _f32(xyz).reshape(-1, 3)
+    amp = _f32(amp).reshape(-1)
+    n = amp.shape[0]
+    P = np.empty((height, 2 * n), dtype=np.float64)
+    Q = np.empty((width, 2 * n), dtype=np.float64)
+    rc = _load().oracle_factors(int(width), int(height), float(pitch_m), float(lambda_m),
+                                _ptr(xyz, _F32P), _ptr(amp, _F32P), n, _ptr(P, _F64P), _ptr(Q, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_factors rejected its arguments")
+    return P, Q
+
+
+def quantize8(field32) -> tuple:
+    """Min/max 8-bit quantisation of a float32 field: (uint8 array, (lo, hi, s))."""
+    f = _f32(field32)
+    flat = f.reshape(-1)
+    out = np.empty(flat.shape[0], dtype=np.uint8)
+    lohi = np.zeros(3, dtype=np.float32)
+    rc = _load().oracle_quantize8(_ptr(flat, _F32P), flat.shape[0], _ptr(out, _U8P), _ptr(lohi, _F32P))
+    if rc != 0:
+        raise ValueError("oracle_quantize8 rejected its arguments")
+    return out.reshape(f.shape), (float(lohi[0]), float(lohi[1]), float(lohi[2]))
+
+
+def nrms(test, ref) -> float:
+    """Normalised RMS error ||test - ref||_2 / ||ref||_2 in FP64."""
+    t = np.asarray(test, dtype=np.float64)
+    r = np.asarray(ref, dtype=np.float64)
+    den = float(np.sqrt(np.sum(r * r)))
+    num = float(np.sqrt(np.sum((t - r) ** 2)))
+    return num / den if den > 0 else num
+
+
+def recurrence_phases(c: Fraction, dx0: int, dy: int, steps: int):
+    """Phases Gamma_1..Gamma_steps along a hologram row by Eqs. 6-8 (Section 2.2), exactly.
+
+    Gamma_1 = P_j (dx0^2 + dy^2), delta_1 = P_j (2 dx0 + 1), Delta = 2 P_j with
+    P_j = c the turn coefficient in px^-2; Gamma_{k+1} = Gamma_k + delta_k and
+    delta_{k+1} = delta_k + Delta.  Gamma_k is the phase at dx = dx0 + k - 1.
+    """
+    g = c * (dx0 * dx0 + dy * dy)
+    d = c * (2 * dx0 + 1)
+    step = 2 * c
+    out = []
+    for _ in range(steps):
+        out.append(g)
+        g = g + d
+        d = d + step
+    return out

@@ -1,0 +1,239 @@
+/*
+ * FP64 CPU oracle for the point-cloud Fresnel hologram.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's compute path may link,
+ * load or call this file; only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header, table or constant
+ * generator with the CUDA path, and it uses different arithmetic on purpose:
+ * double-precision phases reduced in turns and libm cos/sin, where the GPU
+ * uses 64-bit fixed-point turns and single precision.
+ *
+ * What it computes (the plain definition):
+ *
+ *   Eq. 2 (Fresnel approximation of the spherical wave of Eq. 1) and Eq. 5
+ *   (amplitude CGH after dropping |O|^2, |R|^2 and the constant 2 A_r), with
+ *   the per-point piston 2 pi z_j / lambda and the reference phase phi_r left
+ *   out, and with hologram pixels (m, n) and point positions (x_j, y_j) in
+ *   pixel units of pitch p:
+ *
+ *     I(m, n) = sum_j A_j cos(pi p^2 / (lambda z_j) * ((m - x_j)^2 + (n - y_j)^2))
+ *
+ *   which is written here as cos(2 pi t) with t = c_j r^2 turns and
+ *   c_j = p^2 / (2 lambda z_j) turns per px^2 (Section 2.2 writes the same
+ *   constant as P_j = 1/(2 lambda z_j) in metres).  t is reduced by
+ *   subtracting the nearest integer before the cosine.
+ *
+ *   The complex object wave O(m, n) = sum_j A_j exp(i 2 pi t) of Eq. 2 (same
+ *   restriction) is given too, for the kinoform of Eq. 3.
+ *
+ *   The separable factors: with alpha = 2 pi c_j (m - x_j)^2 and
+ *   beta = 2 pi c_j (n - y_j)^2 the phase is alpha + beta, so
+ *   cos(alpha + beta) = cos(alpha) cos(beta) - sin(alpha) sin(beta).  The
+ *   factor matrices P[n][2j] = cos beta, P[n][2j+1] = sin beta,
+ *   Q[m][2j] = A_j cos alpha, Q[m][2j+1] = -A_j sin alpha give I = P Q^T.
+ *
+ *   The 8-bit quantiser of an amplitude hologram (min/max rule); the paper
+ *   only prints the phase rule of its listings (Section 4.1:
+ *   holo = (uchar)(255/(2 pi) psi)), the min/max form is this library's reading
+ *   for amplitude holograms.  It is specified in single precision with every
+ *   product and difference rounded separately, so that it can be reproduced
+ *   bit for bit; build this file with -ffp-contract=off.
+ *
+ * Pixels are stored row-major, out[n * width + m] (Section 4.1, adr = j + WIDTH i).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <float.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define TWO_PI 6.283185307179586476925286766559
+
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* c_j = p^2 / (2 lambda z_j), turns per square pixel, from the float inputs promoted to double. */
+static double *turn_coefficients(double pitch, double lambda, const float *xyz, int64_t n)
+{
+    double *c = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!c) return NULL;
+    for (int64_t j = 0; j < n; ++j) {
+        double z = (double)xyz[3 * j + 2];
+        c[j] = (pitch * pitch) / (2.0 * lambda * z);
+    }
+    return c;
+}
+
+/* 2 pi times the distance of t from its nearest integer, in [-pi, pi]. */
+static double reduced_angle(double t)
+{
+    return TWO_PI * (t - rint(t));
+}
+
+/* One pixel of Eq. 5 (restricted form): sum_j A_j cos(2 pi c_j r^2). */
+static double pixel_amplitude(double m, double n_row, const float *xyz, const float *amp,
+                              const double *c, int64_t npts)
+{
+    double acc = 0.0;
+    for (int64_t j = 0; j < npts; ++j) {
+        double dx = m - (double)xyz[3 * j + 0];
+        double dy = n_row - (double)xyz[3 * j + 1];
+        double r2 = dx * dx + dy * dy;
+        acc += (double)amp[j] * cos(reduced_angle(c[j] * r2));
+    }
+    return acc;
+}
+
+/*
+ * I over the window rows [row0, row0+rows) x cols [col0, col0+cols) of the
+ * hologram; out is [rows][cols] row-major.  Returns 0, or -1 on bad arguments.
+ */
+int oracle_field_window(double pitch, double lambda, const float *xyz, const float *amp, int64_t npts,
+                        int row0, int rows, int col0, int cols, double *out)
+{
+    if (rows < 0 || cols < 0 || npts < 0 || !out) return -1;
+    double *c = turn_coefficients(pitch, lambda, xyz, npts);
+    if (!c) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < rows; ++r) {
+        for (int q = 0; q < cols; ++q) {
+            out[(int64_t)r * cols + q] =
+                pixel_amplitude((double)(col0 + q), (double)(row0 + r), xyz, amp, c, npts);
+        }
+    }
+    free(c);
+    return 0;
+}
+
+/* I at npix scattered pixels (pm[i], pn[i]) = (column, row). */
+int oracle_field_points(double pitch, double lambda, const float *xyz, const float *amp, int64_t npts,
+                        const int32_t *pm, const int32_t *pn, int64_t npix, double *out)
+{
+    if (npix < 0 || npts < 0 || !out) return -1;
+    double *c = turn_coefficients(pitch, lambda, xyz, npts);
+    if (!c) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < npix; ++i)
+        out[i] = pixel_amplitude((double)pm[i], (double)pn[i], xyz, amp, c, npts);
+    free(c);
+    return 0;
+}
+
+/* Complex object wave of Eq. 2 (restricted form) over a window: re + i im. */
+int oracle_wave_window(double pitch, double lambda, const float *xyz, const float *amp, int64_t npts,
+                       int row0, int rows, int col0, int cols, double *re, double *im)
+{
+    if (rows < 0 || cols < 0 || npts < 0 || !re || !im) return -1;
+    double *c = turn_coefficients(pitch, lambda, xyz, npts);
+    if (!c) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < rows; ++r) {
+        for (int q = 0; q < cols; ++q) {
+            double sr = 0.0, si = 0.0;
+            for (int64_t j = 0; j < npts; ++j) {
+                double dx = (double)(col0 + q) - (double)xyz[3 * j + 0];
+                double dy = (double)(row0 + r) - (double)xyz[3 * j + 1];
+                double a = reduced_angle(c[j] * (dx * dx + dy * dy));
+                sr += (double)amp[j] * cos(a);
+                si += (double)amp[j] * sin(a);
+            }
+            re[(int64_t)r * cols + q] = sr;
+            im[(int64_t)r * cols + q] = si;
+        }
+    }
+    free(c);
+    return 0;
+}
+
+/*
+ * Separable factors: P is [height][2 npts], Q is [width][2 npts] (row-major),
+ * with the interleaving described in the header comment.
+ */
+int oracle_factors(int width, int height, double pitch, double lambda, const float *xyz,
+                   const float *amp, int64_t npts, double *P, double *Q)
+{
+    if (width < 0 || height < 0 || npts < 0 || !P || !Q) return -1;
+    double *c = turn_coefficients(pitch, lambda, xyz, npts);
+    if (!c) return -1;
+    #pragma omp parallel for
+    for (int n = 0; n < height; ++n) {
+        for (int64_t j = 0; j < npts; ++j) {
+            double dy = (double)n - (double)xyz[3 * j + 1];
+            double b = reduced_angle(c[j] * dy * dy);
+            P[(int64_t)n * 2 * npts + 2 * j] = cos(b);
+            P[(int64_t)n * 2 * npts + 2 * j + 1] = sin(b);
+        }
+    }
+    #pragma omp parallel for
+    for (int m = 0; m < width; ++m) {
+        for (int64_t j = 0; j < npts; ++j) {
+            double dx = (double)m - (double)xyz[3 * j + 0];
+            double a = reduced_angle(c[j] * dx * dx);
+            Q[(int64_t)m * 2 * npts + 2 * j] = (double)amp[j] * cos(a);
+            Q[(int64_t)m * 2 * npts + 2 * j + 1] = -(double)amp[j] * sin(a);
+        }
+    }
+    free(c);
+    return 0;
+}
+
+/*
+ * Min/max 8-bit quantiser of an amplitude hologram.
+ *   lo = min F, hi = max F (exact, order independent; NaN entries ignored);
+ *   if hi == lo (or no finite range) every output is 0;
+ *   s  = the smallest float >= 255 / ((double)hi - (double)lo), capped at FLT_MAX;
+ *   q  = floor((v - lo) * s) in float with each operation rounded to nearest,
+ *        then 255 if q >= 255, q if q >= 0, else 0 (NaN -> 0).
+ * The upward rounding of s makes hi map to 255; lo maps to 0.
+ * lohi (optional) receives {lo, hi, s}.
+ */
+int oracle_quantize8(const float *field, int64_t n, uint8_t *out, float *lohi)
+{
+    if (n < 0 || (n > 0 && (!field || !out))) return -1;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        float v = field[i];
+        if (v < lo) lo = v;
+        if (v > hi) hi = v;
+    }
+    float s = 0.0f;
+    int degenerate = !(hi > lo);
+    if (!degenerate) {
+        double range = (double)hi - (double)lo;
+        double sd = 255.0 / range;
+        if (sd > (double)FLT_MAX) {
+            s = FLT_MAX;
+        } else {
+            s = (float)sd;
+            if ((double)s < sd) s = nextafterf(s, INFINITY);
+            if (isinf(s)) s = FLT_MAX;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (degenerate) { out[i] = 0; continue; }
+        volatile float d = field[i] - lo;   /* rounded on its own */
+        volatile float x = d * s;           /* rounded on its own */
+        float f = floorf(x);
+        out[i] = (f >= 255.0f) ? (uint8_t)255 : ((f >= 0.0f) ? (uint8_t)f : (uint8_t)0);
+    }
+    if (lohi) { lohi[0] = lo; lohi[1] = hi; lohi[2] = s; }
+    return 0;
+}

@@ -1,0 +1,295 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: exact
+rational brute force, closed-form special values, the zone-plate zeros of a
+single point (Eq. 2/5), linearity of the sum, mirror and translation
+symmetry, the separable factorisation, the recurrence of Eqs. 6-8, and hand
+cases of the quantiser.  A plausible slip in the oracle (a dropped term, a
+wrong sign, pi for 2 pi, lambda in the numerator as printed in the paper's
+listings, transposed m/n) fails at least one of them.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_2734_gb300 import workloads
+
+P8 = 8e-6
+L532 = 532e-9
+
+
+def _cloud(pts, amps=None):
+    xyz = np.asarray(pts, dtype=np.float32).reshape(-1, 3)
+    a = np.ones(xyz.shape[0], np.float32) if amps is None else np.asarray(amps, np.float32)
+    return xyz, a
+
+
+def _exact_pixel(pitch, lam, xyz, amp, m, n):
+    """Brute force: exact rational phase in turns, reduced exactly, then math.cos; fsum."""
+    p = Fraction(pitch)
+    L = Fraction(lam)
+    terms = []
+    for (x, y, z), a in zip(xyz.astype(np.float64), amp.astype(np.float64)):
+        c = p * p / (2 * L * Fraction(float(z)))
+        dx = Fraction(m) - Fraction(float(x))
+        dy = Fraction(n) - Fraction(float(y))
+        t = c * (dx * dx + dy * dy)
+        f = t - round(t)
+        terms.append(float(a) * math.cos(2 * math.pi * float(f)))
+    return math.fsum(terms)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_brute_force_tiny(seed):
+    """Eq. 5 (restricted form) on W, H <= 5 and N <= 3, exact rational arithmetic."""
+    rng = np.random.default_rng(seed)
+    W, H = 5, 4
+    n = 3
+    xyz = np.stack([rng.integers(-3, 8, n), rng.integers(-3, 7, n), rng.uniform(0.2, 1.0, n)], 1)
+    if seed == 3:
+        xyz[:, 0] += 0.5      # non-integer positions: the definition still holds
+    xyz = xyz.astype(np.float32)
+    amp = rng.uniform(0.1, 1.0, n).astype(np.float32)
+    pitch = [8e-6, 6.4e-6, 3.74e-6][seed - 1]
+    lam = [532e-9, 633e-9, 488e-9][seed - 1]
+    got = oracle.field(pitch, lam, xyz, amp, W, H)
+    for nn in range(H):
+        for mm in range(W):
+            assert abs(got[nn, mm] - _exact_pixel(pitch, lam, xyz, amp, mm, nn)) < 1e-12
+
+
+def test_quarter_turn_closed_form():
+    """c = p^2/(2 lambda z) = 1/8 turn/px^2: cos(pi r^2 / 4) takes 8 textbook values."""
+    table = {0: 1.0, 1: math.sqrt(0.5), 2: 0.0, 3: -math.sqrt(0.5), 4: -1.0,
+             5: -math.sqrt(0.5), 6: 0.0, 7: math.sqrt(0.5)}
+    x0, y0 = 1, 2
+    xyz, amp = _cloud([[x0, y0, 4.0]])
+    W, H = 7, 5                  # not square, point off-centre: catches m/n transposition
+    got = oracle.field(1.0, 1.0, xyz, amp, W, H)
+    for n in range(H):
+        for m in range(W):
+            r2 = (m - x0) ** 2 + (n - y0) ** 2
+            assert abs(got[n, m] - table[r2 % 8]) < 1e-13, (m, n)
+
+
+def test_half_turn_closed_form():
+    """c = 1/2 turn/px^2: every pixel is (-1)^(r^2), scaled by A."""
+    xyz, amp = _cloud([[3, 0, 1.0]], [0.75])
+    got = oracle.field(0.5, 0.25, xyz, amp, 6, 3)
+    for n in range(3):
+        for m in range(6):
+            r2 = (m - 3) ** 2 + n * n
+            assert abs(got[n, m] - 0.75 * (-1) ** r2) < 1e-14
+
+
+def test_zone_plate_zero_crossings():
+    """A single point gives a Fresnel zone plate: I = cos(pi p^2 r^2/(lambda z)).
+
+    Along the point's row the sign changes exactly between the pixels that
+    bracket r_k = sqrt((2k+1) lambda z / 2) / p (pitch units), for every r_k
+    below the sampling (Nyquist) radius lambda z / (2 p^2).
+    """
+    z = 0.5
+    x0, y0 = 1000, 3
+    xyz, amp = _cloud([[x0, y0, z]])
+    W = 2048
+    row = oracle.field(P8, L532, xyz, amp, W, 8, window=(y0, 0, 1, W))[0]
+    nyq = L532 * z / (2 * P8 * P8)
+    radii = []
+    k = 0
+    while True:
+        r = math.sqrt((2 * k + 1) * L532 * z / 2) / P8
+        if r >= min(nyq, W - 1 - x0) - 2:
+            break
+        radii.append(r)
+        k += 1
+    assert len(radii) > 100
+    right = row[x0:]
+    signs = np.sign(right)
+    changes = np.nonzero(signs[1:] != signs[:-1])[0]       # change between d and d+1
+    rmax = int(math.floor(radii[-1])) + 1
+    changes = changes[changes < rmax]
+    assert len(changes) == len(radii)
+    for d, r in zip(changes, radii):
+        assert d < r < d + 1
+    # the same zeros on the left, and the closed form value at the centre
+    assert row[x0] == pytest.approx(1.0, abs=1e-15)
+    assert np.allclose(row[x0 - 500:x0], row[x0 + 500:x0:-1], atol=1e-12)
+
+
+def test_lambda_placement_matters():
+    """The listings' phase pi*lambda*r^2/z would not give these zeros (Section 4.1)."""
+    z = 0.8
+    xyz, amp = _cloud([[0, 0, z]])
+    row = oracle.field(P8, L532, xyz, amp, 400, 1)[0]
+    r0 = math.sqrt(L532 * z / 2) / P8          # first zero, ~36.5 px
+    d = int(math.floor(r0))
+    assert row[d] > 0 > row[d + 1]
+
+
+def test_linearity_points_and_amplitudes():
+    c = workloads.random_cloud(77, 40, 30, 200)
+    a, b = c.amp.copy(), c.amp.copy()
+    a[100:] = 0
+    b[:100] = 0
+    full = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 40, 30)
+    pa = oracle.field(c.pitch_m, c.lambda_m, c.xyz[:100], c.amp[:100], 40, 30)
+    pb = oracle.field(c.pitch_m, c.lambda_m, c.xyz[100:], c.amp[100:], 40, 30)
+    assert np.allclose(full, pa + pb, rtol=0, atol=1e-11 * np.abs(full).max())
+    za = oracle.field(c.pitch_m, c.lambda_m, c.xyz, a, 40, 30)
+    assert np.allclose(za, pa, atol=1e-12)
+    scaled = oracle.field(c.pitch_m, c.lambda_m, c.xyz, (c.amp * 0.5).astype(np.float32), 40, 30)
+    assert np.allclose(scaled, 0.5 * full, atol=1e-12 * np.abs(full).max())
+    empty = oracle.field(c.pitch_m, c.lambda_m, c.xyz[:0], c.amp[:0], 40, 30)
+    assert np.all(empty == 0.0)
+
+
+def test_mirror_symmetry():
+    W, H = 33, 21
+    c = workloads.random_cloud(5, W, H, 60)
+    mx = c.xyz.copy()
+    mx[:, 0] = (W - 1) - mx[:, 0]
+    xyz = np.concatenate([c.xyz, mx])
+    amp = np.concatenate([c.amp, c.amp])
+    I = oracle.field(c.pitch_m, c.lambda_m, xyz, amp, W, H)
+    assert np.allclose(I, I[:, ::-1], atol=1e-11)
+    my = c.xyz.copy()
+    my[:, 1] = (H - 1) - my[:, 1]
+    I2 = oracle.field(c.pitch_m, c.lambda_m, np.concatenate([c.xyz, my]), amp, W, H)
+    assert np.allclose(I2, I2[::-1, :], atol=1e-11)
+    # an asymmetric cloud is not symmetric (the test can fail)
+    I3 = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, W, H)
+    assert not np.allclose(I3, I3[:, ::-1], atol=1e-3)
+
+
+def test_integer_translation():
+    W, H = 48, 40
+    c = workloads.random_cloud(9, 32, 24, 80)
+    dx, dy = 7, 5
+    sh = c.xyz.copy()
+    sh[:, 0] += dx
+    sh[:, 1] += dy
+    a = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, W, H)
+    b = oracle.field(c.pitch_m, c.lambda_m, sh, c.amp, W, H)
+    assert np.allclose(b[dy:, dx:], a[:H - dy, :W - dx], atol=1e-11)
+
+
+def test_separable_factors_reproduce_field():
+    """P Q^T with P[n][2j] = cos b, P[n][2j+1] = sin b, Q = A(cos a, -sin a) equals I."""
+    c = workloads.random_cloud(21, 37, 29, 150)
+    P, Q = oracle.factors(c.pitch_m, c.lambda_m, c.xyz, c.amp, 37, 29)
+    I = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 37, 29)
+    assert P.shape == (29, 300) and Q.shape == (37, 300)
+    assert np.allclose(P @ Q.T, I, atol=1e-10)
+    # each factor entry against the exact single-axis phase
+    p, L = Fraction(c.pitch_m), Fraction(c.lambda_m)
+    for j in (0, 77, 149):
+        x, y, z = (float(v) for v in c.xyz[j])
+        cc = p * p / (2 * L * Fraction(z))
+        for n in (0, 13, 28):
+            t = cc * (Fraction(n) - Fraction(y)) ** 2
+            b = 2 * math.pi * float(t - round(t))
+            assert abs(P[n, 2 * j] - math.cos(b)) < 1e-13
+            assert abs(P[n, 2 * j + 1] - math.sin(b)) < 1e-13
+        for m in (0, 20, 36):
+            t = cc * (Fraction(m) - Fraction(x)) ** 2
+            a = 2 * math.pi * float(t - round(t))
+            assert abs(Q[m, 2 * j] - float(c.amp[j]) * math.cos(a)) < 1e-13
+            assert abs(Q[m, 2 * j + 1] + float(c.amp[j]) * math.sin(a)) < 1e-13
+
+
+def test_wave_real_part_and_modulus():
+    c = workloads.random_cloud(4, 20, 16, 50)
+    O = oracle.wave(c.pitch_m, c.lambda_m, c.xyz, c.amp, 20, 16)
+    I = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 20, 16)
+    assert np.allclose(O.real, I, atol=1e-12)
+    one = oracle.wave(c.pitch_m, c.lambda_m, c.xyz[:1], c.amp[:1], 20, 16)
+    assert np.allclose(np.abs(one), float(c.amp[0]), atol=1e-13)
+
+
+def test_recurrence_reproduces_quadratic_phase():
+    """Eqs. 6-8: Gamma_{k+1} = Gamma_k + delta_k, delta_{k+1} = delta_k + Delta, exactly."""
+    c = Fraction(P8) ** 2 / (2 * Fraction(L532) * Fraction(float(np.float32(0.37))))
+    for dx0, dy in ((-20, 3), (0, 0), (5, -17)):
+        g = oracle.recurrence_phases(c, dx0, dy, 40)
+        for k, gk in enumerate(g):
+            assert gk == c * ((dx0 + k) ** 2 + dy * dy)
+    # and the oracle's cosine of that phase at those pixels
+    z = float(np.float32(0.37))
+    xyz, amp = _cloud([[30, 10, z]])
+    row = oracle.field(P8, L532, xyz, amp, 80, 20, window=(13, 0, 1, 80))[0]
+    g = oracle.recurrence_phases(c, 10 - 30, 13 - 10, 40)
+    for k in range(40):
+        f = g[k] - round(g[k])
+        assert abs(row[10 + k] - math.cos(2 * math.pi * float(f))) < 1e-12
+
+
+def test_field_at_matches_window():
+    c = workloads.random_cloud(8, 50, 40, 64)
+    I = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 50, 40)
+    rng = np.random.default_rng(0)
+    cols = rng.integers(0, 50, 30)
+    rows = rng.integers(0, 40, 30)
+    v = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    assert np.array_equal(v, I[rows, cols])
+    win = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 50, 40, window=(7, 11, 9, 13))
+    assert np.array_equal(win, I[7:16, 11:24])
+
+
+def test_accumulation_at_display_point_count():
+    """FP64 sum over 10^4 points agrees with exact-phase fsum to 1e-11 relative."""
+    c = workloads.display_direct()
+    cols = np.array([0, 959, 1919, 1234])
+    rows = np.array([0, 539, 1079, 77])
+    v = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    scale = math.sqrt(np.sum(c.amp.astype(np.float64) ** 2))
+    for i in range(2):
+        ref = _exact_pixel(c.pitch_m, c.lambda_m, c.xyz, c.amp, int(cols[i]), int(rows[i]))
+        assert abs(v[i] - ref) < 1e-11 * scale
+
+
+# ---- quantiser ------------------------------------------------------------
+
+def test_quantize_endpoints_and_constant():
+    f = np.array([-3.5, 0.0, 2.25, 7.125, -3.5], np.float32)
+    q, (lo, hi, s) = oracle.quantize8(f)
+    assert lo == -3.5 and hi == 7.125
+    assert q[0] == 0 and q[4] == 0 and q[3] == 255
+    assert s >= 255.0 / (7.125 + 3.5)
+    c, _ = oracle.quantize8(np.full(17, 4.0, np.float32))
+    assert np.all(c == 0)
+    e, _ = oracle.quantize8(np.zeros(0, np.float32))
+    assert e.shape == (0,)
+
+
+def test_quantize_exact_bins():
+    """lo = 0, hi = 255/256: s = 256 exactly, so v = k/256 maps to k and just below to k-1."""
+    k = np.arange(256, dtype=np.float64)
+    v = (k / 256.0).astype(np.float32)
+    q, (lo, hi, s) = oracle.quantize8(v)
+    assert s == 256.0
+    assert np.array_equal(q, np.arange(256, dtype=np.uint8))
+    below = np.nextafter(v[1:], np.float32(-1)).astype(np.float32)
+    qb, _ = oracle.quantize8(np.concatenate([v[:1], below, v[-1:]]))
+    assert np.array_equal(qb[1:-1], np.arange(255, dtype=np.uint8))
+
+
+def test_quantize_properties_random():
+    rng = np.random.default_rng(3)
+    f = (rng.standard_normal(10000) * 37.0).astype(np.float32)
+    q, (lo, hi, s) = oracle.quantize8(f)
+    order = np.argsort(f, kind="stable")
+    assert np.all(np.diff(q[order].astype(int)) >= 0)          # monotone
+    assert q[np.argmin(f)] == 0 and q[np.argmax(f)] == 255
+    ideal = np.floor(255.0 * (f.astype(np.float64) - lo) / (float(hi) - float(lo)))
+    assert np.max(np.abs(q.astype(np.float64) - np.minimum(ideal, 255))) <= 1
+    perm = rng.permutation(f.shape[0])
+    q2, lh2 = oracle.quantize8(f[perm])
+    assert np.array_equal(q2, q[perm]) and lh2 == (lo, hi, s)
+    fn = f.copy()
+    fn[5] = np.nan
+    qn, _ = oracle.quantize8(fn)
+    assert qn[5] == 0
