@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of the point-cloud Fresnel hologram on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): a 1920x1080 hologram of 10,000 seeded synthetic points
+(z ~ U[0.3, 1.0] m, A ~ U[0.5, 1.0], lambda = 532 nm, p = 8 um), the
+display-size case of the paper's direct-calculation experiments.  One step is
+one pass of the hot path over that cloud: point preparation, the direct
+kernel (SFU cosine), the chunk reduction when the launch splits the points,
+and the 8-bit quantiser.  Inputs and outputs are far below L2, so a 256 MiB
+buffer is written between timed steps to flush L2; the flush is not timed.
+
+Metric: G point-pixel evaluations per second (W*H*N per hologram), with
+holograms/s beside it.  Rank 0 prints one JSON line.  Under torchrun every
+rank computes its own replica (no collective on the data path; weak scaling),
+and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G point-pixel evals/s and holograms/s, direct FP32 vs tensor GEMM, at stated NRMS error"
+UNIT = "Gevals/s"
+MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
+
+# DRAM bytes per launch of the dominant kernel from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
+# taken on; a changed source reports null until it is profiled again.
+NCU_TRAFFIC = {}
+
+
+def _sha1(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while it runs."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(cloud, target_s: float = 12.0, gpu_field=None):
+    """The FP64 oracle, as it stands, on a window of rows of the same workload (host cores)."""
+    import numpy as np
+    import oracle
+    cores = oracle.threads()
+    W, H = cloud.width, cloud.height
+    t0 = time.perf_counter()
+    probe_rows = max(1, min(H, cores))
+    oracle.field(cloud.pitch_m, cloud.lambda_m, cloud.xyz, cloud.amp, W, H, window=(0, 0, probe_rows, W))
+    per_row = (time.perf_counter() - t0) / probe_rows
+    rows = int(max(cores, min(H, target_s / max(per_row, 1e-9))))
+    rows = max(cores, rows // cores * cores) if rows >= cores else rows
+    rows = min(rows, H)
+    r0 = (H - rows) // 2
+    t0 = time.perf_counter()
+    ref = oracle.field(cloud.pitch_m, cloud.lambda_m, cloud.xyz, cloud.amp, W, H, window=(r0, 0, rows, W))
+    dt = time.perf_counter() - t0
+    evals = rows * W * cloud.n_points
+    out = {"value": evals / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"rows {r0}..{r0 + rows - 1} (all {W} columns, all {cloud.n_points} points) of the "
+                     f"{W}x{H} hologram; {evals:.3e} FP64 evals in {dt:.1f} s",
+           "seconds": dt}
+    nrms = None
+    if gpu_field is not None:
+        nrms = oracle.nrms(gpu_field[r0:r0 + rows], ref)
+    return out, nrms
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1309_2734_gb300 import workloads
+    import oracle
+    cloud = workloads.WORKLOADS[args.workload]()
+    cores = oracle.threads()
+    W, H = cloud.width, cloud.height
+    # size one step to about 6 s of host work so the whole run stays within minutes
+    t0 = time.perf_counter()
+    oracle.field(cloud.pitch_m, cloud.lambda_m, cloud.xyz, cloud.amp, W, H, window=(0, 0, cores, W))
+    per_row = (time.perf_counter() - t0) / cores
+    rows = max(1, min(H, int(6.0 / max(per_row, 1e-9))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        r0 = (i * rows) % max(1, H - rows + 1)
+        t0 = time.perf_counter()
+        oracle.field(cloud.pitch_m, cloud.lambda_m, cloud.xyz, cloud.amp, W, H, window=(r0, 0, rows, W))
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    evals = rows * W * cloud.n_points
+    value = evals * len(times) / sum(times) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": cloud.name, "width": W, "height": H, "n_points": cloud.n_points,
+                       "step": f"{rows} rows x {W} columns of the hologram (bounded sample)"},
+            "holograms_per_s": value * 1e9 / cloud.evals,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} of {H} rows per step, all {cloud.n_points} points"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    from paper_1309_2734_gb300 import Hologram, workloads
+    from paper_1309_2734_gb300.build import build
+    if rank == 0:
+        build()
+    if dist is not None:
+        dist.barrier()
+
+    cloud = workloads.WORKLOADS[args.workload]()
+    W, H, N = cloud.width, cloud.height, cloud.n_points
+    stream = torch.cuda.current_stream()
+    xyz = torch.from_numpy(cloud.xyz).cuda()
+    amp = torch.from_numpy(cloud.amp).cuda()
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    q = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    h = Hologram(W, H, cloud.pitch_m, cloud.lambda_m, form=args.form, stream=stream)
+
+    def step():
+        h.point_cloud(xyz, amp, out)
+        h.quantize8(out, q)
+
+    for _ in range(args.warmup):
+        step()
+    h.sync()
+    h.profile(True)
+    h.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local).start()
+    for a, b in ev:
+        flush.fill_(1)
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = clk.stop()
+    h.sync()
+    prof = h.profile_read(reset=True)
+    h.profile(False)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    launches = sum(v[0] for v in prof.values())
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hx = torch.from_numpy(cloud.xyz).pin_memory()
+    ha = torch.from_numpy(cloud.amp).pin_memory()
+    ho = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        h.point_cloud_host(hx, ha, ho)
+    e2e_s = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        h.point_cloud_host(hx, ha, ho)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_s)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    # other forms on the same cloud, for the comparison the metric names
+    forms = {}
+    for extra in args.compare:
+        if extra == args.form:
+            continue
+        h.set_form(extra)
+        for _ in range(2):
+            h.point_cloud(xyz, amp, out)
+        h.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(3, args.steps // 4)
+        e0.record(stream)
+        for _ in range(reps):
+            h.point_cloud(xyz, amp, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        forms[extra] = {"gevals_per_s": cloud.evals / ms / 1e6, "ms_per_hologram": ms}
+    h.set_form(args.form)
+    h.point_cloud(xyz, amp, out)
+    h.sync()
+    field = out.cpu().numpy()
+
+    if rank != 0:
+        h.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    evals_all = cloud.evals * args.steps * world
+    value = evals_all / (total_ms * 1e-3) / 1e9
+    dom = "direct_sfu" if args.form == "direct_sfu" else "direct_accurate"
+    dom_launches, dom_ms = prof.get(dom, (0, 0.0))
+    props = torch.cuda.get_device_properties(local)
+    peaks = _peaks()
+    sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak = MUFU_PER_SM_PER_CLK * props.multi_processor_count * sm_max * 1e6 / 1e9
+    achieved = cloud.evals / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e9 if dom_ms > 0 else None
+    kernel_src = os.path.join(ROOT, "paper_1309_2734_gb300", "csrc", "direct.cu")
+    traffic = NCU_TRAFFIC.get(dom, {})
+    traffic = traffic.get("bytes_per_launch") if traffic.get("sha1") == _sha1(kernel_src) else None
+
+    cpu, nrms = (None, None)
+    if not args.no_cpu_baseline:
+        cpu, nrms = cpu_baseline(cloud, gpu_field=field)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cloud.name, "width": W, "height": H, "n_points": N, "form": args.form,
+                   "step": "prep + direct kernel (+ chunk reduction) + quantize8",
+                   "l2": "flushed between timed steps (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "holograms_per_s": args.steps * world / (total_ms * 1e-3),
+        "nrms_vs_oracle": nrms,
+        "nrms_sample": "the cpu_baseline rows" if nrms is not None else None,
+        "gpu_launches": launches,
+        "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "Gcos/s (MUFU)", "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic,
+                     "peak_basis": f"{MUFU_PER_SM_PER_CLK} MUFU cos/clk/SM x {props.multi_processor_count} SMs x "
+                                   f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)"},
+        "clocks": clocks,
+        "e2e": {"value": cloud.evals * args.steps * world / e2e_total / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": int(cloud.xyz.nbytes + cloud.amp.nbytes),
+                "d2h_bytes_per_step": int(W * H * 4),
+                "path": "cgh_point_cloud_host (pinned host buffers, copies and sync inside)"},
+        "forms": forms,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="direct-1920x1080-n10000")
+    ap.add_argument("--form", default="direct_sfu")
+    ap.add_argument("--compare", nargs="*", default=["direct_accurate"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * cgh.h - C ABI of the GB300 point-cloud Fresnel hologram library (libcgh.so).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a), the amplitude
+ * computer-generated hologram of a point cloud
+ *
+ *     I(m, n) = sum_j A_j cos( pi p^2 / (lambda z_j) * ((m - x_j)^2 + (n - y_j)^2) )
+ *
+ * which is Eq. 5 of the paper (Section 2.1: the interference term of Eq. 4
+ * with the Fresnel approximation of Eq. 2), without the per-point piston
+ * 2 pi z_j / lambda, the reference phase phi_r and the constant 2 A_r.
+ * m is the hologram column, n the row (both in [0, width) x [0, height));
+ * x_j, y_j are the point's position in pixel units (integers, origin at pixel
+ * (0, 0)); z_j is its distance in metres; p is the pixel pitch and lambda the
+ * wavelength, in metres.  Holograms are row-major float32, out[n * width + m]
+ * (Section 4.1: adr = j + WIDTH * i).
+ *
+ * Two forms compute the same sum:
+ *   - direct: per pixel and per point, the phase is built incrementally in
+ *     exact 32/64-bit fixed-point turns (the recurrence of Eqs. 6-8,
+ *     Section 2.2) and fed to a single-precision cosine;
+ *   - separable GEMM: exp(i phi) factors exactly into a column term and a row
+ *     term, so I = P Q^T with P [height][2N] and Q [width][2N]; the product
+ *     runs on the tcgen05 tensor cores in FP16, BF16 or split hi+lo FP16 with
+ *     FP32 accumulation.
+ *
+ * Conventions for every entry point:
+ *   - Return value: CGH_OK (0) or a cgh_status code; no exception or signal
+ *     ever leaves the library.  Arguments that the host can check (null
+ *     pointers, sizes, non-finite scalars) are rejected at once and nothing is
+ *     launched.  Errors found by the GPU in the data (z <= 0, NaN, non-integer
+ *     or out-of-range coordinates) are latched in the context's status word
+ *     and returned by cgh_sync(); the output is then unspecified.
+ *   - Pointers named d_* are device pointers (cudaMalloc / torch CUDA
+ *     tensors) on the context's device; h_* are host pointers.  The caller
+ *     owns every buffer it passes; the library never frees them.  The
+ *     context owns its own workspace and frees it in cgh_destroy().
+ *   - Work is enqueued on the context's stream (cgh_set_stream) and is
+ *     asynchronous unless stated otherwise; cgh_sync() waits for it.
+ *   - A context is not thread safe: use one per host thread.
+ *   - There is no CPU fallback: a build without a usable CUDA device returns
+ *     CGH_ECUDA from cgh_create().
+ */
+#ifndef CGH_H
+#define CGH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CGH_ABI_VERSION 1
+
+/* Status codes. */
+enum {
+    CGH_OK = 0,
+    CGH_EINVAL = 1,    /* bad argument, checked on the host */
+    CGH_ENOMEM = 2,    /* device allocation failed */
+    CGH_ECUDA = 3,     /* CUDA runtime/driver error, or no usable device */
+    CGH_ETIMEOUT = 4,  /* a bounded wait (device or host) ran out */
+    CGH_EINPUT = 5,    /* bad point data, found on the device */
+    CGH_ENOTSUP = 6    /* form or option not available for this problem */
+};
+
+/* How the hologram is computed. */
+enum {
+    CGH_FORM_AUTO = 0,          /* autotuner's choice for the accuracy class */
+    CGH_DIRECT_SFU = 1,         /* direct sum, hardware (MUFU) cosine */
+    CGH_DIRECT_ACCURATE = 2,    /* direct sum, polynomial cosine on the FMA pipe */
+    CGH_GEMM_F16 = 3,           /* I = P Q^T, FP16 factors, FP32 accumulate */
+    CGH_GEMM_BF16 = 4,          /* I = P Q^T, BF16 factors, FP32 accumulate */
+    CGH_GEMM_SPLIT16 = 5        /* I = Ph Qh^T + Ph Ql^T + Pl Qh^T, hi+lo FP16 */
+};
+
+/* 8-bit quantisation rules (cgh_quantize8). */
+enum {
+    CGH_Q_AMPLITUDE_MINMAX = 0  /* floor((v - min) * s), s = 255 / (max - min) rounded up */
+};
+
+/* Options (cgh_set_option). */
+enum {
+    CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side and host-side wait; default 5000 */
+    CGH_OPT_POINT_SPLIT = 2,    /* direct form: point chunks reduced afterwards; 0 = automatic */
+    CGH_OPT_GEMM_SPLITK = 3,    /* GEMM forms: K splits reduced afterwards; 0 = automatic */
+    CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width (16..256, multiple of 16); 0 = automatic */
+    CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */
+    CGH_OPT_PROFILE = 6         /* 1: bracket every kernel launch with CUDA events (cgh_profile_read) */
+};
+
+typedef struct cgh_ctx cgh_ctx;
+
+/*
+ * Creates a context for width x height holograms of pixel pitch pitch_m and
+ * wavelength lambda_m (Section 4.1 fixes the CGH size, pitch P and wavelength
+ * WL of each run).  1 <= width, height <= 16384; pitch_m and lambda_m finite
+ * and > 0.  Binds the current CUDA device and the legacy default stream.
+ * *out receives the context; on failure *out is NULL.
+ */
+int cgh_create(int width, int height, double pitch_m, double lambda_m, cgh_ctx **out);
+
+/* Waits for the context's work (bounded), frees its workspace and the context. NULL is allowed. */
+int cgh_destroy(cgh_ctx *ctx);
+
+/* Binds a CUDA stream (a cudaStream_t passed as void*; NULL = legacy default stream). */
+int cgh_set_stream(cgh_ctx *ctx, void *cuda_stream);
+
+/* Selects the form (CGH_FORM_* above). */
+int cgh_set_form(cgh_ctx *ctx, int form);
+
+/* Sets an option (CGH_OPT_* above). */
+int cgh_set_option(cgh_ctx *ctx, int key, int64_t value);
+
+/*
+ * The hologram of one point cloud (Eq. 5, restricted form; Section 2.1).
+ *   d_xyz : float32 [n_points][3], x and y in pixel units, z in metres.
+ *           x and y must be integers with |x|, |y| <= 16384; z finite and > 0.
+ *   d_amp : float32 [n_points], amplitudes A_j (finite).
+ *   d_out : float32 [height][width], row-major; fully overwritten.
+ * n_points == 0 writes zeros.  n_points <= 2^31 - 1.
+ */
+int cgh_point_cloud(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points,
+                    float *d_out);
+
+/*
+ * Same as cgh_point_cloud, with host buffers: copies h_xyz and h_amp to the
+ * device, computes, copies the hologram back to h_out and waits (bounded).
+ * Page-locked host memory makes the copies faster but is not required.
+ */
+int cgh_point_cloud_host(cgh_ctx *ctx, const float *h_xyz, const float *h_amp, int64_t n_points,
+                         float *h_out);
+
+/*
+ * The separable factors of one point cloud (the GEMM form's operands).
+ * With alpha = 2 pi c_j (m - x_j)^2, beta = 2 pi c_j (n - y_j)^2,
+ * c_j = p^2 / (2 lambda z_j), so that the phase of Eq. 5 is alpha + beta:
+ *   P[n][2j] = cos beta,        P[n][2j+1] = sin beta          (d_p: [height][ld])
+ *   Q[m][2j] = A_j cos alpha,   Q[m][2j+1] = -A_j sin alpha    (d_q: [width][ld])
+ * dtype_form is CGH_GEMM_F16 or CGH_GEMM_BF16 (16-bit elements), or
+ * CGH_GEMM_SPLIT16, for which d_p and d_q each hold two planes, hi then lo,
+ * of [rows][ld] FP16 elements (lo = fp16(v - hi)).  ld >= 2 n_points counts
+ * elements and must be a multiple of 64; columns [2 n_points, ld) are zeroed.
+ */
+int cgh_factors(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points,
+                int dtype_form, void *d_p, void *d_q, int64_t ld);
+
+/* One instance of a batch: a whole hologram problem. */
+typedef struct {
+    int width, height;
+    double pitch_m, lambda_m;
+    const float *d_xyz;     /* float32 [n_points][3] */
+    const float *d_amp;     /* float32 [n_points] */
+    int64_t n_points;
+    float *d_out;           /* float32 [height][width] */
+} cgh_instance;
+
+/*
+ * Many holograms (for example the frames of a holographic video) in one
+ * persistent launch.  inst is a host array of n_inst instances (the context's
+ * own width/height/pitch/lambda are not used).  The form of each instance is
+ * the autotuner's choice under the context's tolerance (CGH_FORM_AUTO) or the
+ * context's form.  The first call with a given set of shapes builds the work
+ * list and captures the launch in a CUDA graph; later calls with the same
+ * shapes and buffers replay it.
+ */
+int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
+
+/*
+ * 8-bit quantisation of a float32 field of n values (mode CGH_Q_AMPLITUDE_MINMAX):
+ *   lo = min, hi = max over the field (NaN ignored); if !(hi > lo) all 0;
+ *   s  = the smallest float >= 255 / ((double)hi - (double)lo) (at most FLT_MAX);
+ *   q  = floor(fl(fl(v - lo) * s)), each operation rounded to nearest, no FMA;
+ *        255 if q >= 255, 0 if q < 0 or NaN.
+ * The paper quantises its phase-only CGHs with 255/(2 pi) (Section 4.1); this
+ * is the amplitude counterpart.  d_field and d_out may not overlap.
+ */
+int cgh_quantize8(cgh_ctx *ctx, const float *d_field, int64_t n, int mode, uint8_t *d_out);
+
+/* Device time of one kernel of the library, summed over its launches (CGH_OPT_PROFILE). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} cgh_kernel_time;
+
+/*
+ * Reads the per-kernel device times recorded since the last reset while
+ * CGH_OPT_PROFILE was on.  The events are recorded on the context's stream
+ * around each launch; this call waits (bounded) for them.  Up to max_entries
+ * entries go to out; *n_entries receives the number of distinct kernels.
+ * reset != 0 clears the record afterwards.
+ */
+int cgh_profile_read(cgh_ctx *ctx, cgh_kernel_time *out, int max_entries, int *n_entries, int reset);
+
+/* Waits for the context's work (bounded by CGH_OPT_TIMEOUT_MS); returns and clears the latched status. */
+int cgh_sync(cgh_ctx *ctx);
+
+/* Static text for a status code. */
+const char *cgh_status_string(int status);
+
+/* CGH_ABI_VERSION of the loaded library. */
+int cgh_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGH_H */

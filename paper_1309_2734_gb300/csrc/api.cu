@@ -1,0 +1,486 @@
+// The C ABI (include/cgh.h): argument checks, the context and its workspace,
+// and the order of kernel launches for each entry point.  No arithmetic of
+// the method runs here; every step of the hologram runs in the kernels.
+#include <cfloat>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/cgh.h"
+#include "device_util.cuh"
+#include "kernels.h"
+#include "tuner.h"
+
+using namespace cgh;
+
+struct cgh_ctx {
+    int width = 0, height = 0;
+    double pitch = 0.0, lambda = 0.0;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    int form = CGH_FORM_AUTO;
+    int64_t timeout_ms = 5000;
+    int point_split = 0;
+    int gemm_splitk = 0;
+    int gemm_bn = 0;
+    int64_t tol_e9 = 10000;   // 1e-5
+    int *d_status = nullptr;  // [0] status bits, [1..2] quantiser scratch, [3] spare
+    void *ws = nullptr;       // grow-only workspace
+    size_t ws_bytes = 0;
+    void *io = nullptr;       // device staging of cgh_point_cloud_host
+    size_t io_bytes = 0;
+    // CGH_OPT_PROFILE: events around each launch, folded into per-kernel totals on read
+    bool profile = false;
+    struct Pending {
+        const char *name;
+        int launches;
+        cudaEvent_t start, stop;
+    };
+    struct Total {
+        std::string name;
+        int64_t launches;
+        double ms;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<Total> totals;
+};
+
+namespace {
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+        dev_ = dev;
+    }
+    ~DeviceGuard()
+    {
+        if (prev_ != dev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0, dev_ = 0;
+};
+
+bool finite_positive(double v)
+{
+    return std::isfinite(v) && v > 0.0;
+}
+
+bool valid_size(int w, int h)
+{
+    return w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide;
+}
+
+size_t align_up(size_t v, size_t a)
+{
+    return (v + a - 1) / a * a;
+}
+
+int ensure(void **buf, size_t *cap, size_t need)
+{
+    if (need <= *cap) return CGH_OK;
+    if (*buf) {
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    size_t want = align_up(need + need / 4, 1 << 20);
+    if (cudaMalloc(buf, want) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return CGH_ENOMEM;
+    }
+    *cap = want;
+    return CGH_OK;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return CGH_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? CGH_ENOMEM : CGH_ECUDA;
+}
+
+cudaEvent_t take_event(cgh_ctx *ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets the launches made in its scope with events on the context's stream.
+class ProfileScope {
+  public:
+    ProfileScope(cgh_ctx *ctx, const char *name, int launches) : ctx_(ctx), name_(name), launches_(launches)
+    {
+        if (ctx_->profile && (start_ = take_event(ctx_))) cudaEventRecord(start_, ctx_->stream);
+    }
+    ~ProfileScope()
+    {
+        if (!start_) return;
+        cudaEvent_t stop = take_event(ctx_);
+        if (!stop) return;
+        cudaEventRecord(stop, ctx_->stream);
+        ctx_->pending.push_back({name_, launches_, start_, stop});
+    }
+
+  private:
+    cgh_ctx *ctx_;
+    const char *name_;
+    int launches_;
+    cudaEvent_t start_ = nullptr;
+};
+
+int64_t padded_points(int64_t n)
+{
+    return (n + kPointTile - 1) / kPointTile * kPointTile;
+}
+
+// Direct form: prep, then the direct kernel over point chunks, then the
+// fixed-order chunk reduction when there is more than one chunk.
+int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, double lambda, const float *d_xyz,
+               const float *d_amp, int64_t n, float *d_out)
+{
+    const int64_t n_pad = padded_points(n);
+    const int64_t n_ptiles = n_pad / kPointTile;
+    const DirectShape sh = direct_shape(sfu);
+    const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
+    int split = ctx->point_split > 0 ? ctx->point_split : choose_point_split(tiles, n_ptiles, ctx->num_sms);
+    if (split > n_ptiles) split = (int)(n_ptiles > 0 ? n_ptiles : 1);
+    const int64_t plane = (int64_t)width * height;
+    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
+    const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
+    const size_t part_bytes = split > 1 ? (size_t)split * plane * sizeof(float) : 0;
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + part_bytes);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->ws);
+    int4 *geo = reinterpret_cast<int4 *>(base);
+    uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
+    float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
+    cudaError_t e;
+    {
+        ProfileScope ps(ctx, "prep_points", 1);
+        e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status,
+                               ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
+    {
+        ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);
+        e = launch_direct(sfu, geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out, plane,
+                          ctx->d_status, tmo, ctx->stream);
+    }
+    if (e != cudaSuccess || split == 1) return cuda_status(e);
+    ProfileScope ps(ctx, "reduce_slices", 1);
+    return cuda_status(launch_reduce_slices(parts, split, plane, plane, d_out, ctx->stream));
+}
+
+int resolve_form(const cgh_ctx *ctx, int width, int height, int64_t n)
+{
+    if (ctx->form != CGH_FORM_AUTO) return ctx->form;
+    return choose_form(width, height, n, (double)ctx->tol_e9 * 1e-9, ctx->num_sms);
+}
+
+int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double lambda, const float *d_xyz,
+                     const float *d_amp, int64_t n, float *d_out)
+{
+    if (n == 0) return cuda_status(cudaMemsetAsync(d_out, 0, (size_t)width * height * sizeof(float), ctx->stream));
+    const int form = resolve_form(ctx, width, height, n);
+    switch (form) {
+    case CGH_DIRECT_SFU:
+        return run_direct(ctx, true, width, height, pitch, lambda, d_xyz, d_amp, n, d_out);
+    case CGH_DIRECT_ACCURATE:
+        return run_direct(ctx, false, width, height, pitch, lambda, d_xyz, d_amp, n, d_out);
+    default:
+        return CGH_ENOTSUP;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int cgh_abi_version(void)
+{
+    return CGH_ABI_VERSION;
+}
+
+const char *cgh_status_string(int status)
+{
+    switch (status) {
+    case CGH_OK: return "ok";
+    case CGH_EINVAL: return "invalid argument";
+    case CGH_ENOMEM: return "device memory allocation failed";
+    case CGH_ECUDA: return "CUDA error or no usable CUDA device";
+    case CGH_ETIMEOUT: return "bounded wait ran out";
+    case CGH_EINPUT: return "invalid point data (z <= 0, NaN, or non-integer / out-of-range x, y)";
+    case CGH_ENOTSUP: return "form or option not supported for this problem";
+    default: return "unknown status";
+    }
+}
+
+int cgh_create(int width, int height, double pitch_m, double lambda_m, cgh_ctx **out)
+{
+    if (!out) return CGH_EINVAL;
+    *out = nullptr;
+    if (!valid_size(width, height) || !finite_positive(pitch_m) || !finite_positive(lambda_m)) return CGH_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CGH_ECUDA;
+    }
+    int major = 0, minor = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CGH_ECUDA;
+    }
+    if (major != 10 || minor != 3) return CGH_ECUDA;   // the kernels are built for sm_103a only
+    cgh_ctx *ctx = new (std::nothrow) cgh_ctx();
+    if (!ctx) return CGH_ENOMEM;
+    ctx->width = width;
+    ctx->height = height;
+    ctx->pitch = pitch_m;
+    ctx->lambda = lambda_m;
+    ctx->device = dev;
+    ctx->num_sms = sms;
+    if (cudaMalloc(&ctx->d_status, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, 4 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        delete ctx;
+        return CGH_ENOMEM;
+    }
+    *out = ctx;
+    return CGH_OK;
+}
+
+int cgh_destroy(cgh_ctx *ctx)
+{
+    if (!ctx) return CGH_OK;
+    DeviceGuard g(ctx->device);
+    int rc = cgh_sync(ctx);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->io) cudaFree(ctx->io);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    for (auto &p : ctx->pending) {
+        cudaEventDestroy(p.start);
+        cudaEventDestroy(p.stop);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    delete ctx;
+    return rc == CGH_ETIMEOUT ? rc : CGH_OK;
+}
+
+int cgh_set_stream(cgh_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return CGH_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return CGH_OK;
+}
+
+int cgh_set_form(cgh_ctx *ctx, int form)
+{
+    if (!ctx || form < CGH_FORM_AUTO || form > CGH_GEMM_SPLIT16) return CGH_EINVAL;
+    ctx->form = form;
+    return CGH_OK;
+}
+
+int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
+{
+    if (!ctx) return CGH_EINVAL;
+    switch (key) {
+    case CGH_OPT_TIMEOUT_MS:
+        if (value < 1 || value > 3600000) return CGH_EINVAL;
+        ctx->timeout_ms = value;
+        return CGH_OK;
+    case CGH_OPT_POINT_SPLIT:
+        if (value < 0 || value > 4096) return CGH_EINVAL;
+        ctx->point_split = (int)value;
+        return CGH_OK;
+    case CGH_OPT_GEMM_SPLITK:
+        if (value < 0 || value > 64) return CGH_EINVAL;
+        ctx->gemm_splitk = (int)value;
+        return CGH_OK;
+    case CGH_OPT_GEMM_BN:
+        if (value != 0 && (value < 16 || value > 256 || value % 16 != 0)) return CGH_EINVAL;
+        ctx->gemm_bn = (int)value;
+        return CGH_OK;
+    case CGH_OPT_TOLERANCE_E9:
+        if (value < 1) return CGH_EINVAL;
+        ctx->tol_e9 = value;
+        return CGH_OK;
+    case CGH_OPT_PROFILE:
+        if (value != 0 && value != 1) return CGH_EINVAL;
+        ctx->profile = value == 1;
+        return CGH_OK;
+    default:
+        return CGH_EINVAL;
+    }
+}
+
+int cgh_point_cloud(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, float *d_out)
+{
+    if (!ctx || !d_out || n_points < 0 || n_points > 0x7fffffffll) return CGH_EINVAL;
+    if (n_points > 0 && (!d_xyz || !d_amp)) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    return compute_hologram(ctx, ctx->width, ctx->height, ctx->pitch, ctx->lambda, d_xyz, d_amp, n_points, d_out);
+}
+
+int cgh_point_cloud_host(cgh_ctx *ctx, const float *h_xyz, const float *h_amp, int64_t n_points, float *h_out)
+{
+    if (!ctx || !h_out || n_points < 0 || n_points > 0x7fffffffll) return CGH_EINVAL;
+    if (n_points > 0 && (!h_xyz || !h_amp)) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    const size_t xyz_b = align_up((size_t)n_points * 3 * sizeof(float), 256);
+    const size_t amp_b = align_up((size_t)n_points * sizeof(float), 256);
+    const size_t out_b = (size_t)ctx->width * ctx->height * sizeof(float);
+    int rc = ensure(&ctx->io, &ctx->io_bytes, xyz_b + amp_b + out_b);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->io);
+    float *d_xyz = reinterpret_cast<float *>(base);
+    float *d_amp = reinterpret_cast<float *>(base + xyz_b);
+    float *d_out = reinterpret_cast<float *>(base + xyz_b + amp_b);
+    if (n_points > 0) {
+        if (cudaMemcpyAsync(d_xyz, h_xyz, (size_t)n_points * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                            ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_amp, h_amp, (size_t)n_points * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) !=
+                cudaSuccess)
+            return cuda_status(cudaGetLastError());
+    }
+    rc = compute_hologram(ctx, ctx->width, ctx->height, ctx->pitch, ctx->lambda, d_xyz, d_amp, n_points, d_out);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(h_out, d_out, out_b, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+    return cgh_sync(ctx);
+}
+
+int cgh_factors(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, int dtype_form, void *d_p,
+                void *d_q, int64_t ld)
+{
+    if (!ctx || !d_p || !d_q || n_points < 0 || n_points > 0x3fffffffll) return CGH_EINVAL;
+    if (n_points > 0 && (!d_xyz || !d_amp)) return CGH_EINVAL;
+    if (dtype_form != CGH_GEMM_F16 && dtype_form != CGH_GEMM_BF16 && dtype_form != CGH_GEMM_SPLIT16)
+        return CGH_EINVAL;
+    if (ld < 2 * n_points || ld % 64 != 0 || ld <= 0) return CGH_EINVAL;
+    return CGH_ENOTSUP;
+}
+
+int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst)
+{
+    if (!ctx || n_inst < 0 || (n_inst > 0 && !inst)) return CGH_EINVAL;
+    for (int i = 0; i < n_inst; ++i) {
+        const cgh_instance &b = inst[i];
+        if (!valid_size(b.width, b.height) || !finite_positive(b.pitch_m) || !finite_positive(b.lambda_m) ||
+            !b.d_out || b.n_points < 0 || b.n_points > 0x7fffffffll || (b.n_points > 0 && (!b.d_xyz || !b.d_amp)))
+            return CGH_EINVAL;
+    }
+    DeviceGuard g(ctx->device);
+    for (int i = 0; i < n_inst; ++i) {
+        const cgh_instance &b = inst[i];
+        int rc = compute_hologram(ctx, b.width, b.height, b.pitch_m, b.lambda_m, b.d_xyz, b.d_amp, b.n_points,
+                                  b.d_out);
+        if (rc) return rc;
+    }
+    return CGH_OK;
+}
+
+int cgh_quantize8(cgh_ctx *ctx, const float *d_field, int64_t n, int mode, uint8_t *d_out)
+{
+    if (!ctx || n < 0 || (n > 0 && (!d_field || !d_out)) || mode != CGH_Q_AMPLITUDE_MINMAX) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    ProfileScope ps(ctx, "quantize8", 3);
+    return cuda_status(
+        launch_quantize8(d_field, n, d_out, reinterpret_cast<uint32_t *>(ctx->d_status + 1), ctx->stream));
+}
+
+int cgh_profile_read(cgh_ctx *ctx, cgh_kernel_time *out, int max_entries, int *n_entries, int reset)
+{
+    if (!ctx || max_entries < 0 || (max_entries > 0 && !out)) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!ctx->pending.empty()) {
+        const auto t0 = std::chrono::steady_clock::now();
+        cudaEvent_t last = ctx->pending.back().stop;
+        for (;;) {
+            cudaError_t q = cudaEventQuery(last);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) return cuda_status(q);
+            const auto ms =
+                std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+            if (ms.count() > ctx->timeout_ms) return CGH_ETIMEOUT;
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        for (auto &p : ctx->pending) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, p.start, p.stop) != cudaSuccess) {
+                cudaGetLastError();
+                ms = 0.0f;
+            }
+            bool found = false;
+            for (auto &t : ctx->totals)
+                if (t.name == p.name) {
+                    t.launches += p.launches;
+                    t.ms += ms;
+                    found = true;
+                    break;
+                }
+            if (!found) ctx->totals.push_back({p.name, (int64_t)p.launches, (double)ms});
+            ctx->event_pool.push_back(p.start);
+            ctx->event_pool.push_back(p.stop);
+        }
+        ctx->pending.clear();
+    }
+    const int n = (int)ctx->totals.size();
+    for (int i = 0; i < n && i < max_entries; ++i) {
+        std::memset(out[i].name, 0, sizeof(out[i].name));
+        std::strncpy(out[i].name, ctx->totals[i].name.c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = ctx->totals[i].launches;
+        out[i].total_ms = ctx->totals[i].ms;
+    }
+    if (n_entries) *n_entries = n;
+    if (reset) ctx->totals.clear();
+    return CGH_OK;
+}
+
+int cgh_sync(cgh_ctx *ctx)
+{
+    if (!ctx) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(ctx->stream);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_status(q);
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+        if (ms.count() > ctx->timeout_ms) return CGH_ETIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int bits = 0;
+    if (cudaMemcpy(&bits, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+    if (bits != 0 && cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) return cuda_status(cudaGetLastError());
+    if (bits & kStatusTimeout) return CGH_ETIMEOUT;
+    if (bits & kStatusInput) return CGH_EINPUT;
+    return CGH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// a2: the direct kernel.  Every thread owns a TL x TR block of hologram pixels
+// (TL consecutive columns of TR consecutive rows) and sums every point of the
+// cloud into it, I(m, n) = sum_j A_j cos(2 pi c_j r^2) (Eq. 5, restricted form).
+//
+// Point tiles of kPointTile prepared points are staged in shared memory by
+// 1-D bulk copies (TMA engine, no multicast), double buffered behind two
+// mbarriers, and read back as warp-wide broadcasts.
+//
+// Phase.  For one point, the thread forms its corner phase G = C r^2 mod 2^64
+// (top 32 bits, exact to one unit of 2^-32 turn), the first differences along
+// x and y, and then walks its block with the recurrence of Eqs. 6-8
+// (Section 2.2): Gamma_{k+1} = Gamma_k + delta_k, delta_{k+1} = delta_k + Delta,
+// Delta = 2 c_j, in 32-bit fixed-point turns, where wrap-around is the
+// reduction modulo one turn.  Moving down one row adds the row difference
+// (shared by all TL columns) the same way.  The drift of the walk is below
+// 1 + TL + TL^2/2 + TR + TR^2/2 units of 2^-32 turn (about 5e-8 rad for 8 x 4).
+//
+// Cosine.
+//  - SFU form: the top 23 bits of the turn become the mantissa of a float f in
+//    [1, 2) (one funnel shift), 2 pi f - 3 pi lies in [-pi, pi) and equals
+//    2 pi t - pi, so the hardware cosine (__cosf, MUFU) returns -cos(2 pi t);
+//    the point's amplitude is negated to compensate.  The bias added to the
+//    corner phase rounds the 23-bit truncation to nearest and cancels the
+//    constant offset of the float constants 2 pi and 3 pi.
+//  - accurate form: the turn, read as a signed 32-bit integer, converts to
+//    t in [-1/2, 1/2) and cos(2 pi t) is a degree-12 even polynomial
+//    (cospoly.h), all on the FMA pipe.
+//
+// Accumulation is two-level: each point tile is summed into fresh partials
+// that are then added into the running totals, which keeps single-precision
+// rounding error at N = 10^6 well below 1e-5 relative.
+#include "cospoly.h"
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace cgh {
+
+namespace {
+
+constexpr float kTwoPiF = 6.28318548202514648f;     // 2 pi rounded to float
+constexpr float kThreePiF = 9.42477798461914062f;   // 3 pi rounded to float
+// 2^8 rounds the 23-bit truncation to nearest; 163 units of 2^-32 turn cancel
+// the 2.384e-7 rad by which fl(2 pi) * 1.5 - fl(3 pi) misses zero.
+constexpr uint32_t kSfuBias = 256u - 163u;
+
+template <bool SFU>
+__device__ __forceinline__ float cos_term(uint32_t g)
+{
+    if constexpr (SFU) {
+        const float f = __uint_as_float(__funnelshift_r(g, 0x7fu, 9));   // 1 + top23(g) 2^-23
+        return __cosf(fmaf(f, kTwoPiF, -kThreePiF));                    // = -cos(2 pi t)
+    } else {
+        const float t = (float)(int)g * 2.3283064365386963e-10f;        // signed turn, [-1/2, 1/2)
+        const float u = t * t;
+        float c = CGH_COSPOLY_6;
+        c = fmaf(c, u, CGH_COSPOLY_5);
+        c = fmaf(c, u, CGH_COSPOLY_4);
+        c = fmaf(c, u, CGH_COSPOLY_3);
+        c = fmaf(c, u, CGH_COSPOLY_2);
+        c = fmaf(c, u, CGH_COSPOLY_1);
+        c = fmaf(c, u, CGH_COSPOLY_0);
+        return c;                                                        // = cos(2 pi t)
+    }
+}
+
+template <int TL, int TR, int BX, int BY, bool SFU>
+__global__ void __launch_bounds__(BX *BY, 2)
+    direct_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_ptiles, int width,
+                  int height, int tiles_x, int split, float *__restrict__ out, long long slice_stride,
+                  bool vec, int *status, unsigned long long timeout_ns)
+{
+    constexpr int T = kPointTile;
+    constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
+    __shared__ alignas(128) int4 s_geo[2][T];
+    __shared__ alignas(128) uint2 s_aux[2][T];
+    __shared__ alignas(8) uint64_t s_bar[2];
+
+    const int tid = threadIdx.x;
+    const int lx = tid % BX, ly = tid / BX;
+    const int tile = blockIdx.x;
+    const int m0 = (tile % tiles_x) * (BX * TL) + lx * TL;
+    const int n0 = (tile / tiles_x) * (BY * TR) + ly * TR;
+    const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
+    const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
+    const int nt = t_end - t_begin;
+
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](int k) {
+        const int st = k & 1;
+        const long long first = (long long)(t_begin + k) * T;
+        mbar_arrive_expect_tx(&s_bar[st], kTileBytes);
+        bulk_copy_g2s(&s_geo[st][0], geo + first, T * sizeof(int4), &s_bar[st]);
+        bulk_copy_g2s(&s_aux[st][0], aux + first, T * sizeof(uint2), &s_bar[st]);
+    };
+    if (tid == 0) {
+        if (nt > 0) issue(0);
+        if (nt > 1) issue(1);
+    }
+
+    float tot[TR][TL];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int i = 0; i < TL; ++i) tot[r][i] = 0.0f;
+
+    for (int k = 0; k < nt; ++k) {
+        const int st = k & 1;
+        const bool arrived = mbar_wait(&s_bar[st], (uint32_t)((k >> 1) & 1), timeout_ns);
+        if (__syncthreads_or(!arrived)) {
+            if (tid == 0) atomicOr(status, kStatusTimeout);
+            break;
+        }
+        float part[TR][TL];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int i = 0; i < TL; ++i) part[r][i] = 0.0f;
+
+        const int4 *sg = s_geo[st];
+        const uint2 *sa = s_aux[st];
+#pragma unroll 1
+        for (int p = 0; p < T; ++p) {
+            const int4 q = sg[p];
+            const uint2 w = sa[p];
+            const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
+            const uint32_t dx = (uint32_t)(m0 - q.x);
+            const uint32_t dy = (uint32_t)(n0 - q.y);
+            const uint32_t r2 = dx * dx + dy * dy;          // < 2^31, exact
+            const uint32_t r2x = r2 + 2u * dx + 1u;         // (dx+1)^2 + dy^2
+            const uint32_t r2y = r2 + 2u * dy + 1u;         // dx^2 + (dy+1)^2
+            const uint32_t g0 = chi * r2 + __umulhi(clo, r2);
+            uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
+            uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
+            const uint32_t D = w.x;
+            const float a = SFU ? -__uint_as_float(w.y) : __uint_as_float(w.y);
+            uint32_t g[TL];
+            g[0] = g0 + (SFU ? kSfuBias : 0u);
+#pragma unroll
+            for (int i = 1; i < TL; ++i) {
+                g[i] = g[i - 1] + d;
+                d += D;
+            }
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+#pragma unroll
+                for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<SFU>(g[i]), part[r][i]);
+                if (r + 1 < TR) {
+#pragma unroll
+                    for (int i = 0; i < TL; ++i) g[i] += e;
+                    e += D;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int i = 0; i < TL; ++i) tot[r][i] += part[r][i];
+
+        __syncthreads();   // every thread is done with stage st
+        if (tid == 0 && k + 2 < nt) issue(k + 2);
+    }
+
+    float *dst = out + (long long)blockIdx.y * slice_stride;
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int n = n0 + r;
+        if (n >= height || m0 >= width) continue;
+        float *row = dst + (long long)n * width + m0;
+        if (vec && m0 + TL <= width) {
+#pragma unroll
+            for (int i = 0; i < TL; i += 4)
+                *reinterpret_cast<float4 *>(row + i) = make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < TL; ++i)
+                if (m0 + i < width) row[i] = tot[r][i];
+        }
+    }
+}
+
+constexpr int kTL = 8, kTR = 4, kBX = 32, kBY = 8;
+
+}  // namespace
+
+DirectShape direct_shape(bool)
+{
+    return DirectShape{kBX * kTL, kBY * kTR, kBX * kBY};
+}
+
+cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
+                          int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
+                          cudaStream_t s)
+{
+    const DirectShape sh = direct_shape(sfu);
+    const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
+    const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
+    const int n_ptiles = n_pad / kPointTile;
+    if (split < 1) split = 1;
+    dim3 grid(tiles_x * tiles_y, split);
+    // 16-byte stores only when every row start of every slice is 16-byte aligned
+    const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    if (sfu)
+        direct_kernel<kTL, kTR, kBX, kBY, true><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns);
+    else
+        direct_kernel<kTL, kTR, kBX, kBY, false><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace cgh

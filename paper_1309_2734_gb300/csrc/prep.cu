@@ -1,0 +1,57 @@
+// a1: point preparation.  One thread per (padded) point computes the point's
+// fixed-point phase constants and checks its data.
+//
+// The phase of Eq. 5 in turns is c_j r^2 with c_j = p^2 / (2 lambda z_j)
+// (Section 2.2 names the same constant P_j = 1/(2 lambda z_j) in metres).
+// Because r^2 is an integer, only frac(c_j) matters modulo one turn; it is
+// stored as the 64-bit fixed-point C_j = round(frac(c_j) 2^64).  Every phase
+// the kernels form is then C_j * (integer) mod 2^64, exact up to C_j's own
+// rounding (<= 2^-65 turn per px^2, i.e. < 2^-33 turn for r^2 < 2^32).
+// FP64 is used only here, O(N) work.
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace cgh {
+
+__global__ void prep_points_kernel(const float *__restrict__ xyz, const float *__restrict__ amp, int n,
+                                   int n_pad, double pitch, double lambda, int4 *__restrict__ geo,
+                                   uint2 *__restrict__ aux, int *status)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_pad) return;
+    if (j >= n) {  // padding: zero amplitude, zero phase
+        geo[j] = make_int4(0, 0, 0, 0);
+        aux[j] = make_uint2(0u, 0u);
+        return;
+    }
+    const float fx = xyz[3 * j + 0], fy = xyz[3 * j + 1], fz = xyz[3 * j + 2];
+    const float a = amp[j];
+    const bool ok = isfinite(fx) && isfinite(fy) && isfinite(fz) && isfinite(a) && fz > 0.0f &&
+                    fx == rintf(fx) && fy == rintf(fy) && fabsf(fx) <= (float)kMaxCoord &&
+                    fabsf(fy) <= (float)kMaxCoord;
+    if (!ok) {
+        atomicOr(status, kStatusInput);
+        geo[j] = make_int4(0, 0, 0, 0);
+        aux[j] = make_uint2(0u, 0u);
+        return;
+    }
+    const double c = (pitch * pitch) / (2.0 * lambda * (double)fz);   // turns per px^2
+    const double fr = c - floor(c);                                  // [0, 1), exact
+    const double scaled = ldexp(fr, 64);                              // exact power-of-two scaling
+    unsigned long long C = (scaled >= 18446744073709551616.0) ? 0ull : __double2ull_rn(scaled);
+    geo[j] = make_int4((int)fx, (int)fy, (int)(unsigned)(C >> 32), (int)(unsigned)(C & 0xffffffffull));
+    const unsigned delta = (unsigned)((C << 1) >> 32);   // second difference 2 c_j, top 32 bits
+    aux[j] = make_uint2(delta, __float_as_uint(a));
+}
+
+cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
+                               double lambda, int4 *geo, uint2 *aux, int *status, cudaStream_t s)
+{
+    if (n_pad <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (n_pad + threads - 1) / threads;
+    prep_points_kernel<<<blocks, threads, 0, s>>>(d_xyz, d_amp, n, n_pad, pitch, lambda, geo, aux, status);
+    return cudaGetLastError();
+}
+
+}  // namespace cgh

@@ -1,0 +1,15 @@
+// Launch-shape and form selection (host side).
+#pragma once
+
+#include <cstdint>
+
+namespace cgh {
+
+// Point chunks for the direct kernel so that (pixel tiles x chunks) fills
+// whole waves of resident CTAs; 1 when one wave is already nearly full.
+int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms);
+
+// Form for CGH_FORM_AUTO: the fastest form whose stated NRMS bound is within tol.
+int choose_form(int width, int height, int64_t n_points, double tol, int num_sms);
+
+}  // namespace cgh

@@ -1,0 +1,224 @@
+"""Parity of the direct form (prep + direct kernel + chunk reduction) and of
+the quantiser against the FP64 oracle, through the C ABI on the GPU.
+
+Tolerances (NRMS = ||I_gpu - I_ref|| / ||I_ref||): 1e-5 for the FP32 direct
+forms.  Per pixel the error may not exceed 1e-5 * sqrt(sum_j A_j^2), the RMS
+size of a pixel of a random-phase sum times ~1.4e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_2734_gb300 import CghError, Hologram, workloads
+from paper_1309_2734_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NRMS_DIRECT = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_2734_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+
+
+def _dev(c):
+    return torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda()
+
+
+def _run(c, form, split=None, xyz=None, amp=None):
+    if xyz is None:
+        xyz, amp = _dev(c)
+    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form=form) as h:
+        if split:
+            h.set_option(_lib.CGH_OPT_POINT_SPLIT, split)
+        f = h.point_cloud(xyz, amp)
+        h.sync()
+        return f.cpu().numpy()
+
+
+def _check(got, ref, amp, tol=NRMS_DIRECT):
+    err = oracle.nrms(got, ref)
+    assert err <= tol, f"NRMS {err:.3e} > {tol:.1e}"
+    per_pixel = 1e-5 * math.sqrt(float(np.sum(amp.astype(np.float64) ** 2)))
+    worst = float(np.max(np.abs(got.astype(np.float64) - ref))) if ref.size else 0.0
+    assert worst <= per_pixel, f"max abs error {worst:.3e} > {per_pixel:.3e}"
+    return err
+
+
+@pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate"])
+def test_small_direct_full_field(form):
+    c = workloads.small_direct()
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    _check(_run(c, form), ref, c.amp)
+
+
+@pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate"])
+@pytest.mark.parametrize("w,h,n", [(1, 1, 1), (257, 33, 300), (300, 37, 513), (31, 300, 256),
+                                   (1000, 3, 77), (258, 35, 1)])
+def test_ragged_shapes(form, w, h, n):
+    c = workloads.random_cloud(1000 + w + n, w, h, n)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
+    _check(_run(c, form), ref, c.amp)
+
+
+def test_points_outside_the_hologram_and_negative_coordinates():
+    rng = np.random.default_rng(11)
+    n = 400
+    xyz = np.stack([rng.integers(-16384, 16385, n), rng.integers(-16384, 16385, n),
+                    rng.uniform(0.05, 2.0, n)], 1).astype(np.float32)
+    xyz[:4, :2] = [[-16384, -16384], [16384, 16384], [-16384, 16384], [0, 0]]
+    amp = rng.uniform(-1.0, 1.0, n).astype(np.float32)
+    c = workloads.Cloud(96, 80, 8e-6, 532e-9, xyz, amp, "far")
+    ref = oracle.field(c.pitch_m, c.lambda_m, xyz, amp, 96, 80)
+    for form in ("direct_sfu", "direct_accurate"):
+        _check(_run(c, form), ref, amp)
+
+
+def test_empty_cloud_writes_zeros():
+    c = workloads.random_cloud(1, 70, 50, 0)
+    with Hologram(70, 50, c.pitch_m, c.lambda_m, form="direct_sfu") as h:
+        out = torch.full((50, 70), 7.0, device="cuda")
+        h.point_cloud(torch.zeros((0, 3), device="cuda"), torch.zeros(0, device="cuda"), out=out)
+        h.sync()
+        assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("split", [2, 3, 7])
+def test_point_split_matches_oracle(split):
+    c = workloads.random_cloud(44, 300, 70, 2000)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    got = _run(c, "direct_sfu", split=split)
+    _check(got, ref, c.amp)
+    one = _run(c, "direct_sfu", split=1)
+    assert oracle.nrms(got, one) < 2e-7
+
+
+def test_deterministic():
+    c = workloads.random_cloud(45, 333, 91, 3000)
+    a = _run(c, "direct_sfu")
+    b = _run(c, "direct_sfu")
+    assert np.array_equal(a, b)
+
+
+def test_display_size_sampled():
+    """1920x1080, 10^4 points, in the launch configuration the benchmark times."""
+    c = workloads.display_direct()
+    rng = np.random.default_rng(5)
+    cols = np.concatenate([rng.integers(0, 1920, 400), [0, 1919, 0, 1919, 1792, 1919]])
+    rows = np.concatenate([rng.integers(0, 1080, 400), [0, 0, 1079, 1079, 1056, 1056]])
+    ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    for form in ("direct_sfu", "direct_accurate"):
+        got = _run(c, form)
+        _check(got[rows, cols], ref, c.amp)
+
+
+def test_layered_million_points_sampled():
+    """4096x4096, 10^6 points on 16 depth planes: sampled pixels vs the oracle."""
+    c = workloads.large_layered()
+    rng = np.random.default_rng(6)
+    cols = rng.integers(0, 4096, 48)
+    rows = rng.integers(0, 4096, 48)
+    ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    got = _run(c, "direct_sfu")
+    _check(got[rows, cols], ref, c.amp)
+
+
+@pytest.mark.parametrize("bad", ["z0", "zneg", "nan", "frac", "range", "ampnan"])
+def test_bad_points_are_reported(bad):
+    c = workloads.random_cloud(3, 64, 64, 100)
+    xyz, amp = c.xyz.copy(), c.amp.copy()
+    if bad == "z0":
+        xyz[10, 2] = 0.0
+    elif bad == "zneg":
+        xyz[10, 2] = -0.5
+    elif bad == "nan":
+        xyz[10, 0] = np.nan
+    elif bad == "frac":
+        xyz[10, 1] = 3.5
+    elif bad == "range":
+        xyz[10, 0] = 16385
+    else:
+        amp[10] = np.inf
+    with Hologram(64, 64, c.pitch_m, c.lambda_m, form="direct_sfu") as h:
+        h.point_cloud(torch.from_numpy(xyz).cuda(), torch.from_numpy(amp).cuda())
+        with pytest.raises(CghError) as ei:
+            h.sync()
+        assert ei.value.code == _lib.CGH_EINPUT
+        # the status is cleared and the context stays usable
+        xg, ag = _dev(c)
+        f = h.point_cloud(xg, ag)
+        h.sync()
+        ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 64, 64)
+        _check(f.cpu().numpy(), ref, c.amp)
+
+
+def test_host_buffer_entry_point():
+    c = workloads.random_cloud(12, 128, 96, 600)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 128, 96)
+    out = torch.empty((96, 128), dtype=torch.float32).pin_memory()
+    with Hologram(128, 96, c.pitch_m, c.lambda_m, form="direct_sfu") as h:
+        h.point_cloud_host(torch.from_numpy(c.xyz), torch.from_numpy(c.amp), out)
+    _check(out.numpy(), ref, c.amp)
+
+
+# ---- quantiser -------------------------------------------------------------
+
+def _q_gpu(field_np, offset=0):
+    buf = torch.zeros(field_np.size + offset, dtype=torch.float32, device="cuda")
+    buf[offset:] = torch.from_numpy(field_np.reshape(-1)).cuda()
+    out = torch.zeros(field_np.size + offset, dtype=torch.uint8, device="cuda")
+    with Hologram(8, 8, 8e-6, 532e-9) as h:
+        rc = _lib.cgh_quantize8(h.ctx, buf[offset:].data_ptr(), field_np.size, 0, out[offset:].data_ptr())
+        assert rc == 0
+        h.sync()
+    return out[offset:].cpu().numpy()
+
+
+@pytest.mark.parametrize("n,offset", [(65536, 0), (1000, 0), (1000, 1), (17, 3), (1, 0)])
+def test_quantize_bit_exact_on_same_field(n, offset):
+    rng = np.random.default_rng(n + offset)
+    f = (rng.standard_normal(n) * 50).astype(np.float32)
+    want, _ = oracle.quantize8(f)
+    assert np.array_equal(_q_gpu(f, offset), want)
+
+
+def test_quantize_special_fields():
+    f = np.full(100, 3.25, np.float32)
+    assert np.all(_q_gpu(f) == 0)
+    k = np.arange(256, dtype=np.float64)
+    v = (k / 256.0).astype(np.float32)
+    assert np.array_equal(_q_gpu(v), np.arange(256, dtype=np.uint8))
+    g = np.linspace(-1, 1, 999).astype(np.float32)
+    g[[3, 500]] = np.nan
+    want, _ = oracle.quantize8(g)
+    assert np.array_equal(_q_gpu(g), want)
+
+
+def test_quantize_hologram_vs_oracle_quantisation():
+    """uint8 of the GPU field equals the oracle's quantisation of the FP64 field away from ties."""
+    c = workloads.small_direct()
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    got = _run(c, "direct_sfu")
+    with Hologram(8, 8, 8e-6, 532e-9) as h:
+        q = h.quantize8(torch.from_numpy(got).cuda())
+        h.sync()
+    q = q.cpu().numpy()
+    assert np.array_equal(q, oracle.quantize8(got)[0])
+    ref32 = ref.astype(np.float32)
+    qr, (lo, hi, s) = oracle.quantize8(ref32)
+    scaled = (ref.astype(np.float64) - lo) * s
+    delta = (np.max(np.abs(got.astype(np.float64) - ref)) + abs(float(got.min()) - lo)) * s + 2.0 ** -20 + \
+        np.abs(ref32.astype(np.float64) - ref).max() * s
+    ties = np.abs(scaled - np.round(scaled)) <= delta
+    mism = q != qr
+    assert not np.any(mism & ~ties)
+    assert ties.mean() < 0.01
