@@ -85,7 +85,8 @@ enum {
     CGH_OPT_GEMM_SPLITK = 3,    /* GEMM forms: K splits reduced afterwards; 0 = automatic */
     CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width (16..256, multiple of 16); 0 = automatic */
     CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */
-    CGH_OPT_PROFILE = 6         /* 1: bracket every kernel launch with CUDA events (cgh_profile_read) */
+    CGH_OPT_PROFILE = 6,        /* 1: bracket every kernel launch with CUDA events (cgh_profile_read) */
+    CGH_OPT_GEMM_CHUNK = 7      /* GEMM forms: k-blocks of 64 per tensor-memory accumulation chain; 0 = default */
 };
 
 typedef struct cgh_ctx cgh_ctx;

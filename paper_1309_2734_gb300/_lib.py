@@ -24,6 +24,7 @@ CGH_Q_AMPLITUDE_MINMAX = 0
 # options
 CGH_OPT_TIMEOUT_MS, CGH_OPT_POINT_SPLIT, CGH_OPT_GEMM_SPLITK, CGH_OPT_GEMM_BN, CGH_OPT_TOLERANCE_E9 = 1, 2, 3, 4, 5
 CGH_OPT_PROFILE = 6
+CGH_OPT_GEMM_CHUNK = 7
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",

@@ -29,6 +29,7 @@ struct cgh_ctx {
     int point_split = 0;
     int gemm_splitk = 0;
     int gemm_bn = 0;
+    int gemm_chunk = 0;
     int64_t tol_e9 = 10000;   // 1e-5
     int *d_status = nullptr;  // [0] status bits, [1..2] quantiser scratch, [3] spare
     void *ws = nullptr;       // grow-only workspace
@@ -179,7 +180,7 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     {
         ProfileScope ps(ctx, "prep_points", 1);
         e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status,
-                               ctx->stream);
+                               nullptr, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_status(e);
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
@@ -191,6 +192,73 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     if (e != cudaSuccess || split == 1) return cuda_status(e);
     ProfileScope ps(ctx, "reduce_slices", 1);
     return cuda_status(launch_reduce_slices(parts, split, plane, plane, d_out, ctx->stream));
+}
+
+// k-blocks per TMEM accumulation chain of the split-FP16 form (3 passes each)
+constexpr int kSplit16ChunkKb = 8;
+
+int factor_mode(int form)
+{
+    return form == CGH_GEMM_BF16 ? kFactorBF16 : (form == CGH_GEMM_SPLIT16 ? kFactorSplit16 : kFactorF16);
+}
+
+// GEMM form: prep, factors P and Q (scaled by 1/max|A|), the tcgen05 GEMM over
+// K splits, and the fixed-order split reduction when there is more than one.
+int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double lambda, const float *d_xyz,
+             const float *d_amp, int64_t n, float *d_out)
+{
+    const int mode = factor_mode(form);
+    const int planes = mode == kFactorSplit16 ? 2 : 1;
+    const int64_t n_pad = padded_points(n);
+    const int64_t ld = (2 * n + 63) / 64 * 64;
+    const int64_t nkb = ld / 64;
+    GemmPlan plan;
+    plan.mode = mode;
+    plan.bn = ctx->gemm_bn > 0 ? ctx->gemm_bn : choose_gemm_bn(width);
+    if (plan.bn != 128 && plan.bn != 192 && plan.bn != 240 && plan.bn != 256) return CGH_ENOTSUP;
+    plan.ctas = gemm_max_ctas(ctx->num_sms);
+    plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
+    const int64_t tiles = (int64_t)((height + 127) / 128) * ((width + plan.bn - 1) / plan.bn);
+    plan.splits = ctx->gemm_splitk > 0 ? ctx->gemm_splitk : choose_gemm_splits(tiles, nkb, plan.ctas);
+    if (plan.splits > nkb) plan.splits = (int)nkb;
+    const int64_t plane = (int64_t)width * height;
+    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
+    const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
+    const size_t amax_bytes = 256;
+    const size_t p_bytes = align_up((size_t)planes * height * ld * 2, 256);
+    const size_t q_bytes = align_up((size_t)planes * width * ld * 2, 256);
+    const size_t part_bytes = plan.splits > 1 ? (size_t)plan.splits * plane * sizeof(float) : 0;
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes + part_bytes);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->ws);
+    int4 *geo = reinterpret_cast<int4 *>(base);
+    uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
+    float *amax = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
+    void *P = base + geo_bytes + aux_bytes + amax_bytes;
+    void *Q = base + geo_bytes + aux_bytes + amax_bytes + p_bytes;
+    float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes);
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    {
+        ProfileScope ps(ctx, "prep_points", 1);
+        e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status, amax,
+                               ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    {
+        ProfileScope ps(ctx, "factors", 1);
+        e = launch_factors(mode, geo, aux, (int)n, height, width, P, Q, ld, amax, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
+    {
+        ProfileScope ps(ctx, "gemm_tcgen05", 1);
+        e = launch_gemm(plan, P, Q, height, width, ld, plan.splits > 1 ? parts : d_out, plane, amax, ctx->d_status,
+                        tmo, ctx->stream);
+    }
+    if (e != cudaSuccess || plan.splits == 1) return cuda_status(e);
+    ProfileScope ps(ctx, "reduce_slices", 1);
+    return cuda_status(launch_reduce_slices(parts, plan.splits, plane, plane, d_out, ctx->stream));
 }
 
 int resolve_form(const cgh_ctx *ctx, int width, int height, int64_t n)
@@ -209,6 +277,10 @@ int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double l
         return run_direct(ctx, true, width, height, pitch, lambda, d_xyz, d_amp, n, d_out);
     case CGH_DIRECT_ACCURATE:
         return run_direct(ctx, false, width, height, pitch, lambda, d_xyz, d_amp, n, d_out);
+    case CGH_GEMM_F16:
+    case CGH_GEMM_BF16:
+    case CGH_GEMM_SPLIT16:
+        return run_gemm(ctx, form, width, height, pitch, lambda, d_xyz, d_amp, n, d_out);
     default:
         return CGH_ENOTSUP;
     }
@@ -329,6 +401,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         if (value < 1) return CGH_EINVAL;
         ctx->tol_e9 = value;
         return CGH_OK;
+    case CGH_OPT_GEMM_CHUNK:
+        if (value < 0 || value > (1 << 24)) return CGH_EINVAL;
+        ctx->gemm_chunk = (int)value;
+        return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->profile = value == 1;
@@ -382,7 +458,26 @@ int cgh_factors(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_
     if (dtype_form != CGH_GEMM_F16 && dtype_form != CGH_GEMM_BF16 && dtype_form != CGH_GEMM_SPLIT16)
         return CGH_EINVAL;
     if (ld < 2 * n_points || ld % 64 != 0 || ld <= 0) return CGH_EINVAL;
-    return CGH_ENOTSUP;
+    if ((uintptr_t)d_p % 16 != 0 || (uintptr_t)d_q % 16 != 0) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    const int64_t n_pad = padded_points(n_points);
+    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
+    const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + 256);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->ws);
+    int4 *geo = reinterpret_cast<int4 *>(base);
+    uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
+    cudaError_t e;
+    {
+        ProfileScope ps(ctx, "prep_points", 1);
+        e = launch_prep_points(d_xyz, d_amp, (int)n_points, (int)n_pad, ctx->pitch, ctx->lambda, geo, aux,
+                               ctx->d_status, nullptr, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    ProfileScope ps(ctx, "factors", 1);
+    return cuda_status(launch_factors(factor_mode(dtype_form), geo, aux, (int)n_points, ctx->height, ctx->width,
+                                      d_p, d_q, ld, nullptr, ctx->stream));
 }
 
 int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst)

@@ -16,12 +16,19 @@
 // 1 + TL + TL^2/2 + TR + TR^2/2 units of 2^-32 turn (about 5e-8 rad for 8 x 4).
 //
 // Cosine.
-//  - SFU form: the top 23 bits of the turn become the mantissa of a float f in
-//    [1, 2) (one funnel shift), 2 pi f - 3 pi lies in [-pi, pi) and equals
-//    2 pi t - pi, so the hardware cosine (__cosf, MUFU) returns -cos(2 pi t);
-//    the point's amplitude is negated to compensate.  The bias added to the
-//    corner phase rounds the 23-bit truncation to nearest and cancels the
-//    constant offset of the float constants 2 pi and 3 pi.
+//  - SFU form: the turn is advanced by a quarter (t' = t + 1/4, folded into
+//    the corner phase), its top 23 bits become the mantissa of a float f in
+//    [1, 2) (one funnel shift), and u = 2 pi f - 3 pi = 2 pi t - pi/2 lies in
+//    [-pi, pi).  The hardware sine (__sinf, MUFU) of u is -cos(2 pi t); the
+//    point's amplitude is negated to compensate.  Every other point instead
+//    takes the sine of -u (= +cos(2 pi t)) with its amplitude as it is: the
+//    hardware sine carries a small mean error (about 1.3e-8 of the
+//    amplitude per term, independent of the pixel), which grows linearly
+//    with N and reached NRMS 1.6e-5 at N = 10^6; evaluated at u and -u on
+//    alternate points, that mean error enters with opposite signs and
+//    cancels, at no extra cost.  The bias also rounds the 23-bit
+//    truncation to nearest and cancels the constant offset of the float
+//    constants 2 pi and 3 pi.
 //  - accurate form: the turn, read as a signed 32-bit integer, converts to
 //    t in [-1/2, 1/2) and cos(2 pi t) is a degree-12 even polynomial
 //    (cospoly.h), all on the FMA pipe.
@@ -39,16 +46,18 @@ namespace {
 
 constexpr float kTwoPiF = 6.28318548202514648f;     // 2 pi rounded to float
 constexpr float kThreePiF = 9.42477798461914062f;   // 3 pi rounded to float
-// 2^8 rounds the 23-bit truncation to nearest; 163 units of 2^-32 turn cancel
-// the 2.384e-7 rad by which fl(2 pi) * 1.5 - fl(3 pi) misses zero.
-constexpr uint32_t kSfuBias = 256u - 163u;
+// 2^30: a quarter turn; 2^8 rounds the 23-bit truncation to nearest; 163
+// units of 2^-32 turn cancel the 2.384e-7 rad by which fl(2 pi) * 1.5 - fl(3 pi)
+// misses zero.
+constexpr uint32_t kSfuBias = (1u << 30) + 256u - 163u;
 
+// SFU: k1 = +-2 pi, k0 = -+3 pi selects u or -u (see above).
 template <bool SFU>
-__device__ __forceinline__ float cos_term(uint32_t g)
+__device__ __forceinline__ float cos_term(uint32_t g, float k1, float k0)
 {
     if constexpr (SFU) {
         const float f = __uint_as_float(__funnelshift_r(g, 0x7fu, 9));   // 1 + top23(g) 2^-23
-        return __cosf(fmaf(f, kTwoPiF, -kThreePiF));                    // = -cos(2 pi t)
+        return __sinf(fmaf(f, k1, k0));                                 // = -+cos(2 pi t)
     } else {
         const float t = (float)(int)g * 2.3283064365386963e-10f;        // signed turn, [-1/2, 1/2)
         const float u = t * t;
@@ -137,7 +146,11 @@ __global__ void __launch_bounds__(BX *BY, 2)
             uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
             uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
             const uint32_t D = w.x;
-            const float a = SFU ? -__uint_as_float(w.y) : __uint_as_float(w.y);
+            // SFU: even points evaluate sin(u) = -cos, odd points sin(-u) = +cos
+            const bool odd = (p & 1) != 0;
+            const float a = (SFU && !odd) ? -__uint_as_float(w.y) : __uint_as_float(w.y);
+            const float k1 = odd ? -kTwoPiF : kTwoPiF;
+            const float k0 = odd ? kThreePiF : -kThreePiF;
             uint32_t g[TL];
             g[0] = g0 + (SFU ? kSfuBias : 0u);
 #pragma unroll
@@ -148,7 +161,7 @@ __global__ void __launch_bounds__(BX *BY, 2)
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
 #pragma unroll
-                for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<SFU>(g[i]), part[r][i]);
+                for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<SFU>(g[i], k1, k0), part[r][i]);
                 if (r + 1 < TR) {
 #pragma unroll
                     for (int i = 0; i < TL; ++i) g[i] += e;

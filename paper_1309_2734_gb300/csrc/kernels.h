@@ -10,9 +10,11 @@ namespace cgh {
 // are padded to a multiple of it.
 constexpr int kPointTile = 256;
 
-// a1: per-point constants and validation (prep.cu).
+// a1: per-point constants and validation (prep.cu).  amp_max (optional, zeroed
+// by the caller) receives max_j |A_j|.
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
-                               double lambda, int4 *geo, uint2 *aux, int *status, cudaStream_t s);
+                               double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
+                               cudaStream_t s);
 
 // a2: direct kernel (direct.cu).
 struct DirectShape {
@@ -23,6 +25,26 @@ DirectShape direct_shape(bool sfu);
 cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
                           int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
                           cudaStream_t s);
+
+// a3: separable factors P [height][ld], Q [width][ld] (factors.cu).  For
+// kFactorSplit16 the lo planes follow the hi planes (offset rows * ld).
+// amp_max (optional) scales Q by 1 / max|A|.
+enum { kFactorF16 = 0, kFactorBF16 = 1, kFactorSplit16 = 2 };
+cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_points, int height, int width,
+                           void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s);
+
+// a4: tcgen05 GEMM, out[n][m] (+)= sum_k P[n][k] Q[m][k] over K splits (gemm.cu).
+struct GemmPlan {
+    int mode;          // kFactorF16 / kFactorBF16 / kFactorSplit16
+    int bn;            // tile width in columns of the hologram (Q rows)
+    int splits;        // K splits; > 1 writes partial planes
+    int ctas;          // persistent CTAs
+    int chunk_kb;      // k-blocks (of 64) per TMEM accumulation chain; 0 = whole split
+};
+int gemm_max_ctas(int num_sms);
+cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int height, int width, int64_t ld,
+                        float *out, int64_t slice_stride, const float *amp_max, int *status, uint64_t timeout_ns,
+                        cudaStream_t s);
 
 // a5: fixed-order sum of `slices` planes of n floats (reduce.cu).
 cudaError_t launch_reduce_slices(const float *parts, int slices, int64_t n, int64_t slice_stride, float *out,

@@ -15,7 +15,7 @@ namespace cgh {
 
 __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *__restrict__ amp, int n,
                                    int n_pad, double pitch, double lambda, int4 *__restrict__ geo,
-                                   uint2 *__restrict__ aux, int *status)
+                                   uint2 *__restrict__ aux, int *status, float *amp_max)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
@@ -42,15 +42,18 @@ __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *_
     geo[j] = make_int4((int)fx, (int)fy, (int)(unsigned)(C >> 32), (int)(unsigned)(C & 0xffffffffull));
     const unsigned delta = (unsigned)((C << 1) >> 32);   // second difference 2 c_j, top 32 bits
     aux[j] = make_uint2(delta, __float_as_uint(a));
+    if (amp_max != nullptr) atomicMax(reinterpret_cast<unsigned *>(amp_max), __float_as_uint(fabsf(a)));
 }
 
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
-                               double lambda, int4 *geo, uint2 *aux, int *status, cudaStream_t s)
+                               double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
+                               cudaStream_t s)
 {
     if (n_pad <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (n_pad + threads - 1) / threads;
-    prep_points_kernel<<<blocks, threads, 0, s>>>(d_xyz, d_amp, n, n_pad, pitch, lambda, geo, aux, status);
+    prep_points_kernel<<<blocks, threads, 0, s>>>(d_xyz, d_amp, n, n_pad, pitch, lambda, geo, aux, status,
+                                                         amp_max);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,40 @@ int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms)
     return best;
 }
 
+int choose_gemm_bn(int width)
+{
+    static const int cands[] = {256, 240, 192, 128};
+    int best = 256;
+    double best_waste = 1e30;
+    for (int bn : cands) {
+        const int tiles = (width + bn - 1) / bn;
+        const double waste = (double)(tiles * bn - width) / (double)width + 1e-3 * (256 - bn) / 256.0;
+        if (waste < best_waste) {
+            best_waste = waste;
+            best = bn;
+        }
+    }
+    return best;
+}
+
+int choose_gemm_splits(int64_t tiles, int64_t k_blocks, int ctas)
+{
+    if (tiles <= 0 || ctas <= 0) return 1;
+    int best = 1;
+    double best_time = 1e30;
+    for (int64_t s = 1; s <= 32 && s * 4 <= (k_blocks > 4 ? k_blocks : 4); ++s) {
+        const int64_t units = tiles * s;
+        const int64_t rounds = (units + ctas - 1) / ctas;
+        // time in units of one whole-K tile; each extra split costs a partial plane
+        const double t = (double)rounds / (double)s + 0.01 * (double)(s - 1);
+        if (t < best_time - 1e-9) {
+            best_time = t;
+            best = (int)s;
+        }
+    }
+    return best;
+}
+
 int choose_form(int width, int height, int64_t n_points, double tol, int num_sms)
 {
     (void)width;

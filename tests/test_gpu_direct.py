@@ -34,10 +34,10 @@ def _dev(c):
     return torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda()
 
 
-def _run(c, form, split=None, xyz=None, amp=None):
+def _run(c, form, split=None, xyz=None, amp=None, timeout_ms=None):
     if xyz is None:
         xyz, amp = _dev(c)
-    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form=form) as h:
+    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form=form, timeout_ms=timeout_ms) as h:
         if split:
             h.set_option(_lib.CGH_OPT_POINT_SPLIT, split)
         f = h.point_cloud(xyz, amp)
@@ -121,15 +121,27 @@ def test_display_size_sampled():
         _check(got[rows, cols], ref, c.amp)
 
 
-def test_layered_million_points_sampled():
-    """4096x4096, 10^6 points on 16 depth planes: sampled pixels vs the oracle."""
+@pytest.fixture(scope="module")
+def layered():
     c = workloads.large_layered()
     rng = np.random.default_rng(6)
     cols = rng.integers(0, 4096, 48)
     rows = rng.integers(0, 4096, 48)
-    ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
-    got = _run(c, "direct_sfu")
-    _check(got[rows, cols], ref, c.amp)
+    return c, cols, rows, oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+
+
+@pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate"])
+def test_layered_million_points_sampled(layered, form):
+    """4096x4096, 10^6 points on 16 depth planes: sampled pixels vs the oracle.
+
+    At this N a per-term bias of 1e-8 would already show as NRMS ~1e-5, so
+    the mean error is checked as well as the NRMS.
+    """
+    c, cols, rows, ref = layered
+    got = _run(c, form, timeout_ms=120000)[rows, cols].astype(np.float64)
+    bias = float(np.mean(got - ref))
+    assert abs(bias) < 3e-6 * math.sqrt(float(np.sum(c.amp.astype(np.float64) ** 2))), bias
+    _check(got, ref, c.amp)
 
 
 @pytest.mark.parametrize("bad", ["z0", "zneg", "nan", "frac", "range", "ampnan"])

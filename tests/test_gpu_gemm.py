@@ -1,0 +1,159 @@
+"""Parity of the separable tensor-core form: factor generation (cgh_factors)
+against the oracle's FP64 factors, the tcgen05 GEMM against a plain PyTorch
+FP32 matmul of the very same 16-bit operands, and the whole GEMM form
+against the FP64 oracle field.
+
+NRMS tolerances of the GEMM forms against the oracle: 2e-3 (FP16), 1e-2
+(BF16), 1e-5 (split hi+lo FP16).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_2734_gb300 import Hologram, workloads
+from paper_1309_2734_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NRMS = {"gemm_f16": 2e-3, "gemm_bf16": 1e-2, "gemm_split16": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_2734_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+
+
+def _dev(c):
+    return torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda()
+
+
+def _run(c, form, bn=None, splitk=None, chunk=None):
+    xyz, amp = _dev(c)
+    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form=form, timeout_ms=3000) as h:
+        if bn:
+            h.set_option(_lib.CGH_OPT_GEMM_BN, bn)
+        if splitk:
+            h.set_option(_lib.CGH_OPT_GEMM_SPLITK, splitk)
+        if chunk:
+            h.set_option(_lib.CGH_OPT_GEMM_CHUNK, chunk)
+        f = h.point_cloud(xyz, amp)
+        h.sync()
+        return f.cpu().numpy()
+
+
+# ---- a3: factors -----------------------------------------------------------
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_bf16", "gemm_split16"])
+def test_factors_match_fp64_oracle(form):
+    c = workloads.random_cloud(31, 70, 45, 150)
+    Pr, Qr = oracle.factors(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    xyz, amp = _dev(c)
+    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m) as h:
+        P, Q = h.factors(xyz, amp, form)
+        h.sync()
+    k = 2 * c.n_points
+    if form == "gemm_split16":
+        Pg = (P[0].float() + P[1].float()).cpu().numpy().astype(np.float64)
+        Qg = (Q[0].float() + Q[1].float()).cpu().numpy().astype(np.float64)
+        pad_p, pad_q = P[:, :, k:], Q[:, :, k:]
+        rel, floor = 2.0 ** -21, 4e-7
+    else:
+        Pg = P.float().cpu().numpy().astype(np.float64)
+        Qg = Q.float().cpu().numpy().astype(np.float64)
+        pad_p, pad_q = P[:, k:], Q[:, k:]
+        rel, floor = (2.0 ** -8, 2e-7) if form == "gemm_bf16" else (2.0 ** -11, 2e-7)
+    for got, ref in ((Pg[:, :k], Pr), (Qg[:, :k], Qr)):
+        err = np.abs(got - ref)
+        assert np.all(err <= rel * np.abs(ref) + floor), float(np.max(err - rel * np.abs(ref)))
+    assert torch.count_nonzero(pad_p).item() == 0 and torch.count_nonzero(pad_q).item() == 0
+
+
+# ---- a4: the GEMM kernel against an FP32 matmul of the same operands -------
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_bf16", "gemm_split16"])
+@pytest.mark.parametrize("shape", [(300, 200, 700), (1920, 131, 2048), (96, 260, 37)])
+def test_gemm_matches_fp32_matmul_of_same_operands(form, shape):
+    w, h, n = shape
+    c = workloads.random_cloud(7 + w + n, w, h, n)
+    c.amp[0] = 1.0            # max |A| = 1: the form's internal amplitude scale is exactly 1
+    xyz, amp = _dev(c)
+    with Hologram(w, h, c.pitch_m, c.lambda_m, form=form, timeout_ms=3000) as hh:
+        P, Q = hh.factors(xyz, amp, form)
+        f = hh.point_cloud(xyz, amp)
+        hh.sync()
+    P, Q = P.cpu().double(), Q.cpu().double()
+    if form == "gemm_split16":
+        ref = P[0] @ Q[0].t() + P[0] @ Q[1].t() + P[1] @ Q[0].t()
+    else:
+        ref = P @ Q.t()
+    ref = ref.numpy()
+    got = f.cpu().numpy().astype(np.float64)
+    err = oracle.nrms(got, ref)
+    assert err < 2e-6, err
+
+
+# ---- the whole form against the oracle ---------------------------------------
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_bf16", "gemm_split16"])
+@pytest.mark.parametrize("w,h,n", [(256, 256, 1024), (257, 129, 333), (130, 300, 64), (1, 1, 1), (1000, 3, 5)])
+def test_gemm_form_vs_oracle(form, w, h, n):
+    c = workloads.random_cloud(100 + w + h + n, w, h, n)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
+    got = _run(c, form)
+    assert oracle.nrms(got, ref) <= NRMS[form]
+
+
+@pytest.mark.parametrize("bn", [128, 192, 240, 256])
+@pytest.mark.parametrize("splitk", [1, 2, 3, 5])
+def test_tiles_and_splits(bn, splitk):
+    c = workloads.random_cloud(55, 500, 270, 1500)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 500, 270)
+    got = _run(c, "gemm_split16", bn=bn, splitk=splitk)
+    assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]
+
+
+def test_split_results_agree_across_splits():
+    """Same accumulation chunks, K split over 1 or 4 partial planes: only FP32 summation order differs."""
+    c = workloads.random_cloud(56, 384, 256, 4096)
+    a = _run(c, "gemm_f16", splitk=1, chunk=8)
+    b = _run(c, "gemm_f16", splitk=4, chunk=8)
+    assert oracle.nrms(b, a) < 1e-6
+    assert np.array_equal(a, _run(c, "gemm_f16", splitk=1, chunk=8))     # deterministic
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 8, 16])
+def test_accumulation_chunks(chunk):
+    """Chunked TMEM accumulation (any chunk length, ragged last chunk) against the oracle."""
+    c = workloads.random_cloud(58, 300, 140, 3000)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 300, 140)
+    got = _run(c, "gemm_split16", splitk=2, chunk=chunk)
+    assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]
+
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_bf16", "gemm_split16"])
+def test_display_size_50k_points_sampled(form):
+    """1920x1080, 5x10^4 points, in the launch configuration the benchmark times."""
+    c = workloads.display_gemm()
+    rng = np.random.default_rng(8)
+    cols = np.concatenate([rng.integers(0, 1920, 300), [0, 1919, 0, 1919]])
+    rows = np.concatenate([rng.integers(0, 1080, 300), [0, 0, 1079, 1079]])
+    ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    got = _run(c, form)[rows, cols]
+    assert oracle.nrms(got, ref) <= NRMS[form]
+
+
+def test_large_amplitudes_are_scaled():
+    """Amplitudes far outside the FP16 range still give the right field (scale by 1/max|A|)."""
+    c = workloads.random_cloud(57, 200, 100, 500)
+    c.amp *= np.float32(1e6)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 200, 100)
+    got = _run(c, "gemm_split16")
+    assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]
