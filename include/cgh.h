@@ -193,6 +193,31 @@ typedef struct {
  */
 int cgh_profile_read(cgh_ctx *ctx, cgh_kernel_time *out, int max_entries, int *n_entries, int reset);
 
+/*
+ * For callers that cannot allocate device memory (no cudaMalloc allowed, as
+ * in a real-time loop, a host that only hands out pre-registered buffers, or
+ * a plug-in living inside another program's memory budget): the direct SFU
+ * hologram of one point cloud with no context and no allocation.  The paper
+ * has no counterpart; it is this library's own entry point.
+ *
+ * Arguments as cgh_create() and cgh_point_cloud(); cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  The point constants go to a
+ * fixed scratch array of CGH_NOALLOC_MAX_POINTS entries (3 MiB) in the
+ * library's own device memory, which every GPU that loads libcgh.so holds
+ * until the process exits; n_points > CGH_NOALLOC_MAX_POINTS returns
+ * CGH_EINVAL before anything is launched (use cgh_point_cloud instead).
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  It waits for its own work and returns CGH_OK, CGH_EINPUT
+ * (bad point data) or CGH_ETIMEOUT.  The first call on a device looks up the
+ * scratch address for that device (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the scratch and it keeps the
+ * last call's contents; calls that overlap on the GPU (several host threads
+ * or streams at once) race on it and must be serialised by the caller.
+ */
+#define CGH_NOALLOC_MAX_POINTS 131072
+int cgh_point_cloud_noalloc(int width, int height, double pitch_m, double lambda_m, const float *d_xyz,
+                            const float *d_amp, int64_t n_points, float *d_out, void *cuda_stream);
+
 /* Waits for the context's work (bounded by CGH_OPT_TIMEOUT_MS); returns and clears the latched status. */
 int cgh_sync(cgh_ctx *ctx);
 

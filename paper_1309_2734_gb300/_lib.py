@@ -28,7 +28,8 @@ CGH_OPT_GEMM_CHUNK = 7
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
-           "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync")
+           "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc")
+CGH_NOALLOC_MAX_POINTS = 131072
 
 
 class cgh_instance(ctypes.Structure):
@@ -78,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_quantize8": ([vp, vp, i64, ci, vp], ci),
             "cgh_profile_read": ([vp, ctypes.POINTER(cgh_kernel_time), ci, ctypes.POINTER(ci), ci], ci),
             "cgh_sync": ([vp], ci),
+            "cgh_point_cloud_noalloc": ([ci, ci, cd, cd, vp, vp, i64, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -157,3 +159,10 @@ def cgh_profile_read(ctx: int, reset: bool = True) -> dict:
 
 def cgh_sync(ctx: int) -> int:
     return load().cgh_sync(ctx)
+
+
+def cgh_point_cloud_noalloc(width: int, height: int, pitch_m: float, lambda_m: float, d_xyz: int, d_amp: int,
+                            n_points: int, d_out: int, stream_handle: int = 0) -> int:
+    """The context-free, allocation-free direct hologram (see include/cgh.h)."""
+    return load().cgh_point_cloud_noalloc(int(width), int(height), float(pitch_m), float(lambda_m), d_xyz, d_amp,
+                                          int(n_points), d_out, stream_handle)
