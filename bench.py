@@ -39,7 +39,10 @@ MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
 # DRAM bytes per launch of the dominant kernel from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # taken on; a changed source reports null until it is profiled again.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/direct_sfu-1920x1080-n10000.md: 0.265 MB read + 21.99 MB written per launch
+    "direct_sfu": {"sha1": "8c2e19d767a30cb9e62e7a3699111372619139e0", "bytes_per_launch": 22255616},
+}
 
 
 def _sha1(path):
@@ -146,7 +149,29 @@ def cpu_baseline(cloud, target_s: float = 12.0, gpu_field=None):
     nrms = None
     if gpu_field is not None:
         nrms = oracle.nrms(gpu_field[r0:r0 + rows], ref)
-    return out, nrms
+    return out, nrms, (r0, rows, ref)
+
+
+def nrms_of_forms(samples, cloud, rows_ref):
+    """NRMS of each compared form: on the oracle rows of the timed cloud, or on 256 sampled
+    pixels (FP64 oracle) of the other clouds."""
+    import numpy as np
+    import oracle
+    r0, rows, ref = rows_ref
+    out = {}
+    cache = {}
+    for key, (wc, field) in samples.items():
+        if wc is cloud:
+            out[key] = oracle.nrms(field[r0:r0 + rows], ref)
+            continue
+        if wc.name not in cache:
+            rng = np.random.default_rng(20260)
+            cols = rng.integers(0, wc.width, 256)
+            rws = rng.integers(0, wc.height, 256)
+            cache[wc.name] = (cols, rws, oracle.field_at(wc.pitch_m, wc.lambda_m, wc.xyz, wc.amp, cols, rws))
+        cols, rws, pix = cache[wc.name]
+        out[key] = oracle.nrms(field[rws, cols], pix)
+    return out
 
 
 def run_reference(args):
@@ -158,11 +183,12 @@ def run_reference(args):
     cloud = workloads.WORKLOADS[args.workload]()
     cores = oracle.threads()
     W, H = cloud.width, cloud.height
-    # size one step to about 6 s of host work so the whole run stays within minutes
+    # size one step so that the whole --steps/--warmup run takes about two minutes of host work
     t0 = time.perf_counter()
     oracle.field(cloud.pitch_m, cloud.lambda_m, cloud.xyz, cloud.amp, W, H, window=(0, 0, cores, W))
     per_row = (time.perf_counter() - t0) / cores
-    rows = max(1, min(H, int(6.0 / max(per_row, 1e-9))))
+    step_s = min(6.0, max(0.3, 120.0 / (args.steps + args.warmup)))
+    rows = max(1, min(H, int(step_s / max(per_row, 1e-9))))
     times = []
     for i in range(args.warmup + args.steps):
         r0 = (i * rows) % max(1, H - rows + 1)
@@ -262,24 +288,53 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
 
-    # other forms on the same cloud, for the comparison the metric names
+    # other forms, for the comparison the metric names: every form on this cloud, and the
+    # GEMM forms also on the 1920x1080, 50,000-point cloud they are meant for
     forms = {}
+    samples = {}
+    gemm_cloud = workloads.display_gemm() if any(f.startswith("gemm") for f in args.compare) else None
+    gemm_dev = None
     for extra in args.compare:
-        if extra == args.form:
-            continue
-        h.set_form(extra)
-        for _ in range(2):
-            h.point_cloud(xyz, amp, out)
-        h.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(3, args.steps // 4)
-        e0.record(stream)
-        for _ in range(reps):
-            h.point_cloud(xyz, amp, out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        forms[extra] = {"gevals_per_s": cloud.evals / ms / 1e6, "ms_per_hologram": ms}
+        for wc in ([cloud] + ([gemm_cloud] if extra.startswith("gemm") else [])):
+            if wc is cloud:
+                cx, ca, hh = xyz, amp, h
+            else:
+                if gemm_dev is None:
+                    gemm_dev = (torch.from_numpy(wc.xyz).cuda(), torch.from_numpy(wc.amp).cuda(),
+                                Hologram(wc.width, wc.height, wc.pitch_m, wc.lambda_m, stream=stream))
+                cx, ca, hh = gemm_dev
+            hh.set_form(extra)
+            o = torch.empty((wc.height, wc.width), dtype=torch.float32, device="cuda")
+            for _ in range(2):
+                hh.point_cloud(cx, ca, o)
+            hh.sync()
+            hh.profile(True)
+            hh.profile_read(reset=True)
+            reps = max(3, args.steps // 4)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                hh.point_cloud(cx, ca, o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            hh.sync()
+            kp = hh.profile_read(reset=True)
+            hh.profile(False)
+            ms = e0.elapsed_time(e1) / reps
+            rec = {"gevals_per_s": wc.evals / ms / 1e6, "ms_per_hologram": ms,
+                   "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kp.items()}}
+            if extra.startswith("gemm") and "gemm_tcgen05" in kp:
+                passes = 3 if extra == "gemm_split16" else 1
+                gl, gms = kp["gemm_tcgen05"]
+                tflops = 4.0 * wc.evals * passes / (gms / max(gl, 1) * 1e-3) / 1e12
+                peak_tc = _peaks().get("bf16_tflops") or 1939.7
+                rec["roofline"] = {"kernel": "gemm_tcgen05", "bound": "tensor", "achieved": tflops,
+                                   "peak": peak_tc, "unit": "TFLOP/s", "frac": tflops / peak_tc,
+                                   "flops_per_eval": 4 * passes,
+                                   "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
+            key = f"{extra}@{wc.name}"
+            forms[key] = rec
+            samples[key] = (wc, o.cpu().numpy())
     h.set_form(args.form)
     h.point_cloud(xyz, amp, out)
     h.sync()
@@ -306,7 +361,10 @@ def run_ours(args):
 
     cpu, nrms = (None, None)
     if not args.no_cpu_baseline:
-        cpu, nrms = cpu_baseline(cloud, gpu_field=field)
+        cpu, nrms, rows_ref = cpu_baseline(cloud, gpu_field=field)
+        form_nrms = nrms_of_forms(samples, cloud, rows_ref)
+        for k, v in form_nrms.items():
+            forms[k]["nrms_vs_oracle"] = v
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -349,7 +407,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="direct-1920x1080-n10000")
     ap.add_argument("--form", default="direct_sfu")
-    ap.add_argument("--compare", nargs="*", default=["direct_accurate"])
+    ap.add_argument("--compare", nargs="*",
+                    default=["direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -80,13 +80,15 @@ enum {
 
 /* Options (cgh_set_option). */
 enum {
-    CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side and host-side wait; default 5000 */
+    CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side wait; host-side waits allow 2x + 1 s; default 5000 */
     CGH_OPT_POINT_SPLIT = 2,    /* direct form: point chunks reduced afterwards; 0 = automatic */
     CGH_OPT_GEMM_SPLITK = 3,    /* GEMM forms: K splits reduced afterwards; 0 = automatic */
     CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width (16..256, multiple of 16); 0 = automatic */
     CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */
     CGH_OPT_PROFILE = 6,        /* 1: bracket every kernel launch with CUDA events (cgh_profile_read) */
-    CGH_OPT_GEMM_CHUNK = 7      /* GEMM forms: k-blocks of 64 per tensor-memory accumulation chain; 0 = default */
+    CGH_OPT_GEMM_CHUNK = 7,     /* GEMM forms: k-blocks of 64 per tensor-memory accumulation chain; 0 = default */
+    CGH_OPT_TEST_DROP_TILE = 8  /* test hook, direct forms: never load point tile k (>= 0) of the first chunk, so the
+                                   kernel's bounded wait runs out and cgh_sync returns CGH_ETIMEOUT; -1 = off */
 };
 
 typedef struct cgh_ctx cgh_ctx;
@@ -165,6 +167,19 @@ typedef struct {
  * shapes and buffers replay it.
  */
 int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
+
+/*
+ * Calibrates the autotuner on this device: times every form on three small
+ * synthetic clouds and fits, per form, t = c0 + c1 W H N + c2 (W + H) N, from
+ * which CGH_FORM_AUTO picks the fastest form whose stated NRMS bound meets
+ * CGH_OPT_TOLERANCE_E9; GEMM tile widths are timed per hologram shape on first
+ * use.  Runs on the context's stream and waits; must not be called during
+ * stream capture.  The first CGH_FORM_AUTO call calibrates by itself if this
+ * was not called.  force != 0 re-measures even if a calibration exists.  With
+ * the environment variable CGH_TUNE_CACHE=<file>, measurements are read from
+ * and saved to that JSON file (keyed by device name and ABI version).
+ */
+int cgh_autotune(cgh_ctx *ctx, int force);
 
 /*
  * 8-bit quantisation of a float32 field of n values (mode CGH_Q_AMPLITUDE_MINMAX):

@@ -25,10 +25,12 @@ CGH_Q_AMPLITUDE_MINMAX = 0
 CGH_OPT_TIMEOUT_MS, CGH_OPT_POINT_SPLIT, CGH_OPT_GEMM_SPLITK, CGH_OPT_GEMM_BN, CGH_OPT_TOLERANCE_E9 = 1, 2, 3, 4, 5
 CGH_OPT_PROFILE = 6
 CGH_OPT_GEMM_CHUNK = 7
+CGH_OPT_TEST_DROP_TILE = 8
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
-           "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc")
+           "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
+           "cgh_autotune")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -80,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_profile_read": ([vp, ctypes.POINTER(cgh_kernel_time), ci, ctypes.POINTER(ci), ci], ci),
             "cgh_sync": ([vp], ci),
             "cgh_point_cloud_noalloc": ([ci, ci, cd, cd, vp, vp, i64, vp, vp], ci),
+            "cgh_autotune": ([vp, ci], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -155,6 +158,10 @@ def cgh_profile_read(ctx: int, reset: bool = True) -> dict:
     n = ctypes.c_int(0)
     check(load().cgh_profile_read(ctx, buf, 64, ctypes.byref(n), 1 if reset else 0), "cgh_profile_read")
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def cgh_autotune(ctx: int, force: bool = False) -> int:
+    return load().cgh_autotune(ctx, 1 if force else 0)
 
 
 def cgh_sync(ctx: int) -> int:

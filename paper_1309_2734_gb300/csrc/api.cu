@@ -11,149 +11,12 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/cgh.h"
-#include "device_util.cuh"
-#include "kernels.h"
+#include "context.h"
 #include "tuner.h"
 
 using namespace cgh;
 
-struct cgh_ctx {
-    int width = 0, height = 0;
-    double pitch = 0.0, lambda = 0.0;
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t stream = nullptr;
-    int form = CGH_FORM_AUTO;
-    int64_t timeout_ms = 5000;
-    int point_split = 0;
-    int gemm_splitk = 0;
-    int gemm_bn = 0;
-    int gemm_chunk = 0;
-    int64_t tol_e9 = 10000;   // 1e-5
-    int *d_status = nullptr;  // [0] status bits, [1..2] quantiser scratch, [3] spare
-    void *ws = nullptr;       // grow-only workspace
-    size_t ws_bytes = 0;
-    void *io = nullptr;       // device staging of cgh_point_cloud_host
-    size_t io_bytes = 0;
-    // CGH_OPT_PROFILE: events around each launch, folded into per-kernel totals on read
-    bool profile = false;
-    struct Pending {
-        const char *name;
-        int launches;
-        cudaEvent_t start, stop;
-    };
-    struct Total {
-        std::string name;
-        int64_t launches;
-        double ms;
-    };
-    std::vector<Pending> pending;
-    std::vector<cudaEvent_t> event_pool;
-    std::vector<Total> totals;
-};
-
-namespace {
-
-class DeviceGuard {
-  public:
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev_);
-        if (prev_ != dev) cudaSetDevice(dev);
-        dev_ = dev;
-    }
-    ~DeviceGuard()
-    {
-        if (prev_ != dev_) cudaSetDevice(prev_);
-    }
-
-  private:
-    int prev_ = 0, dev_ = 0;
-};
-
-bool finite_positive(double v)
-{
-    return std::isfinite(v) && v > 0.0;
-}
-
-bool valid_size(int w, int h)
-{
-    return w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide;
-}
-
-size_t align_up(size_t v, size_t a)
-{
-    return (v + a - 1) / a * a;
-}
-
-int ensure(void **buf, size_t *cap, size_t need)
-{
-    if (need <= *cap) return CGH_OK;
-    if (*buf) {
-        cudaFree(*buf);
-        *buf = nullptr;
-        *cap = 0;
-    }
-    size_t want = align_up(need + need / 4, 1 << 20);
-    if (cudaMalloc(buf, want) != cudaSuccess) {
-        cudaGetLastError();
-        *buf = nullptr;
-        return CGH_ENOMEM;
-    }
-    *cap = want;
-    return CGH_OK;
-}
-
-int cuda_status(cudaError_t e)
-{
-    if (e == cudaSuccess) return CGH_OK;
-    cudaGetLastError();
-    return e == cudaErrorMemoryAllocation ? CGH_ENOMEM : CGH_ECUDA;
-}
-
-cudaEvent_t take_event(cgh_ctx *ctx)
-{
-    if (!ctx->event_pool.empty()) {
-        cudaEvent_t e = ctx->event_pool.back();
-        ctx->event_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return e;
-}
-
-// Brackets the launches made in its scope with events on the context's stream.
-class ProfileScope {
-  public:
-    ProfileScope(cgh_ctx *ctx, const char *name, int launches) : ctx_(ctx), name_(name), launches_(launches)
-    {
-        if (ctx_->profile && (start_ = take_event(ctx_))) cudaEventRecord(start_, ctx_->stream);
-    }
-    ~ProfileScope()
-    {
-        if (!start_) return;
-        cudaEvent_t stop = take_event(ctx_);
-        if (!stop) return;
-        cudaEventRecord(stop, ctx_->stream);
-        ctx_->pending.push_back({name_, launches_, start_, stop});
-    }
-
-  private:
-    cgh_ctx *ctx_;
-    const char *name_;
-    int launches_;
-    cudaEvent_t start_ = nullptr;
-};
-
-int64_t padded_points(int64_t n)
-{
-    return (n + kPointTile - 1) / kPointTile * kPointTile;
-}
+namespace cgh {
 
 // Direct form: prep, then the direct kernel over point chunks, then the
 // fixed-order chunk reduction when there is more than one chunk.
@@ -187,7 +50,7 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     {
         ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);
         e = launch_direct(sfu, geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out, plane,
-                          ctx->d_status, tmo, ctx->stream);
+                          ctx->d_status, tmo, ctx->stream, ctx->drop_tile);
     }
     if (e != cudaSuccess || split == 1) return cuda_status(e);
     ProfileScope ps(ctx, "reduce_slices", 1);
@@ -214,7 +77,9 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     const int64_t nkb = ld / 64;
     GemmPlan plan;
     plan.mode = mode;
-    plan.bn = ctx->gemm_bn > 0 ? ctx->gemm_bn : choose_gemm_bn(width);
+    plan.bn = ctx->gemm_bn > 0 ? ctx->gemm_bn
+                               : (ctx->form == CGH_FORM_AUTO ? tune_choose_bn(ctx, width, height, form)
+                                                             : choose_gemm_bn(width));
     if (plan.bn != 128 && plan.bn != 192 && plan.bn != 240 && plan.bn != 256) return CGH_ENOTSUP;
     plan.ctas = gemm_max_ctas(ctx->num_sms);
     plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
@@ -261,10 +126,10 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     return cuda_status(launch_reduce_slices(parts, plan.splits, plane, plane, d_out, ctx->stream));
 }
 
-int resolve_form(const cgh_ctx *ctx, int width, int height, int64_t n)
+int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n)
 {
     if (ctx->form != CGH_FORM_AUTO) return ctx->form;
-    return choose_form(width, height, n, (double)ctx->tol_e9 * 1e-9, ctx->num_sms);
+    return tune_choose_form(ctx, width, height, n, (double)ctx->tol_e9 * 1e-9);
 }
 
 int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double lambda, const float *d_xyz,
@@ -286,7 +151,7 @@ int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double l
     }
 }
 
-}  // namespace
+}  // namespace cgh
 
 extern "C" {
 
@@ -359,6 +224,8 @@ int cgh_destroy(cgh_ctx *ctx)
         cudaEventDestroy(p.stop);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    destroy_batch_plan(ctx->batch);
+    destroy_tune_state(ctx->tune);
     delete ctx;
     return rc == CGH_ETIMEOUT ? rc : CGH_OK;
 }
@@ -404,6 +271,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_GEMM_CHUNK:
         if (value < 0 || value > (1 << 24)) return CGH_EINVAL;
         ctx->gemm_chunk = (int)value;
+        return CGH_OK;
+    case CGH_OPT_TEST_DROP_TILE:
+        if (value < -1 || value > 0x7fffffff) return CGH_EINVAL;
+        ctx->drop_tile = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;
@@ -486,17 +357,19 @@ int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst)
     for (int i = 0; i < n_inst; ++i) {
         const cgh_instance &b = inst[i];
         if (!valid_size(b.width, b.height) || !finite_positive(b.pitch_m) || !finite_positive(b.lambda_m) ||
-            !b.d_out || b.n_points < 0 || b.n_points > 0x7fffffffll || (b.n_points > 0 && (!b.d_xyz || !b.d_amp)))
+            !b.d_out || b.n_points < 0 || b.n_points > 0x3fffffffll || (b.n_points > 0 && (!b.d_xyz || !b.d_amp)))
             return CGH_EINVAL;
     }
+    if (n_inst == 0) return CGH_OK;
     DeviceGuard g(ctx->device);
-    for (int i = 0; i < n_inst; ++i) {
-        const cgh_instance &b = inst[i];
-        int rc = compute_hologram(ctx, b.width, b.height, b.pitch_m, b.lambda_m, b.d_xyz, b.d_amp, b.n_points,
-                                  b.d_out);
-        if (rc) return rc;
-    }
-    return CGH_OK;
+    return run_batch(ctx, inst, n_inst);
+}
+
+int cgh_autotune(cgh_ctx *ctx, int force)
+{
+    if (!ctx) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    return tune_calibrate(ctx, force != 0);
 }
 
 int cgh_quantize8(cgh_ctx *ctx, const float *d_field, int64_t n, int mode, uint8_t *d_out)
@@ -566,7 +439,8 @@ int cgh_sync(cgh_ctx *ctx)
         if (q == cudaSuccess) break;
         if (q != cudaErrorNotReady) return cuda_status(q);
         const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
-        if (ms.count() > ctx->timeout_ms) return CGH_ETIMEOUT;
+        // the device-side waits give up after timeout_ms; leave them room to report
+        if (ms.count() > 2 * ctx->timeout_ms + 1000) return CGH_ETIMEOUT;
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     int bits = 0;

@@ -1,0 +1,335 @@
+// a7: many holograms in one persistent launch, captured in a CUDA graph.
+//
+// The first cgh_batch call with a given set of instances builds a plan:
+//   - a form per instance (the context's form, or the autotuner's choice
+//     under the tolerance) and, for GEMM instances, a tile width;
+//   - one device arena holding every instance's prepared points, factors
+//     and the job tables of the batched kernels;
+//   - the unit lists: GEMM units {job, tile} over the whole K range of their
+//     hologram (accumulation chunks keep TMEM chains short) and direct units
+//     {job, pixel tile} over all points, handed out greedily (largest cost
+//     first within each job order) to the CTA with the least work so far;
+//   - a CUDA graph of the whole batch: per instance the point preparation
+//     (and factor generation), then ONE persistent GEMM launch for all GEMM
+//     instances and ONE persistent direct launch per direct form.
+// Later calls with the same instances (shapes, parameters and buffers) only
+// replay the graph on the context's stream.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "context.h"
+#include "tuner.h"
+
+namespace cgh {
+
+struct BatchPlan {
+    std::vector<uint64_t> key;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> forms;
+};
+
+void destroy_batch_plan(BatchPlan *p)
+{
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->arena) cudaFree(p->arena);
+    if (p->capture) cudaStreamDestroy(p->capture);
+    delete p;
+}
+
+namespace {
+
+uint64_t bits_of(double v)
+{
+    uint64_t b;
+    std::memcpy(&b, &v, sizeof b);
+    return b;
+}
+
+std::vector<uint64_t> plan_key(const cgh_ctx *ctx, const cgh_instance *inst, int n)
+{
+    std::vector<uint64_t> k;
+    k.reserve(4 + (size_t)n * 8);
+    k.push_back((uint64_t)n);
+    k.push_back((uint64_t)ctx->form);
+    k.push_back((uint64_t)ctx->tol_e9);
+    k.push_back(((uint64_t)ctx->gemm_bn << 32) | (uint64_t)(uint32_t)ctx->gemm_chunk);
+    for (int i = 0; i < n; ++i) {
+        const cgh_instance &b = inst[i];
+        k.push_back(((uint64_t)(uint32_t)b.width << 32) | (uint32_t)b.height);
+        k.push_back(bits_of(b.pitch_m));
+        k.push_back(bits_of(b.lambda_m));
+        k.push_back((uint64_t)(uintptr_t)b.d_xyz);
+        k.push_back((uint64_t)(uintptr_t)b.d_amp);
+        k.push_back((uint64_t)b.n_points);
+        k.push_back((uint64_t)(uintptr_t)b.d_out);
+    }
+    return k;
+}
+
+// Greedy assignment: units in the given order, each to the least-loaded CTA.
+void assign(const std::vector<int2> &units, const std::vector<double> &cost, int ctas, std::vector<int> &off,
+            std::vector<int2> &ordered)
+{
+    std::vector<std::vector<int2>> per(ctas);
+    std::vector<double> load(ctas, 0.0);
+    for (size_t i = 0; i < units.size(); ++i) {
+        int best = 0;
+        for (int c = 1; c < ctas; ++c)
+            if (load[c] < load[best]) best = c;
+        per[best].push_back(units[i]);
+        load[best] += cost[i];
+    }
+    off.assign(ctas + 1, 0);
+    ordered.clear();
+    for (int c = 0; c < ctas; ++c) {
+        off[c] = (int)ordered.size();
+        ordered.insert(ordered.end(), per[c].begin(), per[c].end());
+    }
+    off[ctas] = (int)ordered.size();
+}
+
+struct Layout {
+    size_t bytes = 0;
+    size_t take(size_t n, size_t align = 256)
+    {
+        bytes = (bytes + align - 1) / align * align;
+        const size_t at = bytes;
+        bytes += n;
+        return at;
+    }
+};
+
+constexpr int kSplit16ChunkKbBatch = 8;
+
+int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
+{
+    const double tol = (double)ctx->tol_e9 * 1e-9;
+    plan->forms.assign(n, CGH_DIRECT_SFU);
+    std::vector<int> bn(n, 256);
+    for (int i = 0; i < n; ++i) {
+        if (inst[i].n_points == 0) continue;
+        const int f = ctx->form != CGH_FORM_AUTO
+                          ? ctx->form
+                          : tune_choose_form(ctx, inst[i].width, inst[i].height, inst[i].n_points, tol);
+        plan->forms[i] = f;
+        if (f >= CGH_GEMM_F16)
+            bn[i] = ctx->gemm_bn > 0 ? ctx->gemm_bn
+                                     : (ctx->form == CGH_FORM_AUTO ? tune_choose_bn(ctx, inst[i].width, inst[i].height, f)
+                                                                   : choose_gemm_bn(inst[i].width));
+    }
+    // arena layout
+    Layout L;
+    struct Off {
+        size_t geo, aux, amax, p, q;
+        int64_t n_pad, ld;
+    };
+    std::vector<Off> off(n);
+    int n_gemm = 0, n_dsfu = 0, n_dacc = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t np = inst[i].n_points;
+        if (np == 0) continue;
+        Off &o = off[i];
+        o.n_pad = padded_points(np);
+        o.geo = L.take((size_t)o.n_pad * sizeof(int4));
+        o.aux = L.take((size_t)o.n_pad * sizeof(uint2));
+        o.amax = L.take(sizeof(float));
+        const int f = plan->forms[i];
+        if (f >= CGH_GEMM_F16) {
+            const int planes = f == CGH_GEMM_SPLIT16 ? 2 : 1;
+            o.ld = (2 * np + 63) / 64 * 64;
+            o.p = L.take((size_t)planes * inst[i].height * o.ld * 2);
+            o.q = L.take((size_t)planes * inst[i].width * o.ld * 2);
+            ++n_gemm;
+        } else if (f == CGH_DIRECT_SFU) {
+            ++n_dsfu;
+        } else {
+            ++n_dacc;
+        }
+    }
+    // job tables and unit lists
+    std::vector<GemmJob> gjobs;
+    std::vector<DirectJob> djobs[2];
+    std::vector<int2> gunits, dunits[2];
+    std::vector<double> gcost, dcost[2];
+    const DirectShape dsh = direct_shape(true);
+    for (int i = 0; i < n; ++i) {
+        if (inst[i].n_points == 0) continue;
+        const int f = plan->forms[i];
+        if (f >= CGH_GEMM_F16) {
+            const int j = (int)gjobs.size();
+            gjobs.emplace_back();
+            // device pointers are filled after the arena exists; remember the instance
+            const int tiles = ((inst[i].height + 127) / 128) * ((inst[i].width + bn[i] - 1) / bn[i]);
+            const double c = (double)((2 * inst[i].n_points + 63) / 64) * (f == CGH_GEMM_SPLIT16 ? 3.0 : 1.0) * bn[i];
+            for (int t = 0; t < tiles; ++t) {
+                gunits.push_back(make_int2(j, t));
+                gcost.push_back(c);
+            }
+        } else {
+            const int which = f == CGH_DIRECT_SFU ? 0 : 1;
+            const int j = (int)djobs[which].size();
+            djobs[which].emplace_back();
+            const int tiles_x = (inst[i].width + dsh.tile_w - 1) / dsh.tile_w;
+            const int tiles = tiles_x * ((inst[i].height + dsh.tile_h - 1) / dsh.tile_h);
+            for (int t = 0; t < tiles; ++t) {
+                dunits[which].push_back(make_int2(j, t));
+                dcost[which].push_back((double)off[i].n_pad);
+            }
+        }
+    }
+    const int gctas = gunits.empty() ? 0 : std::min<int>(gemm_max_ctas(ctx->num_sms), (int)gunits.size());
+    const int dctas_max = ctx->num_sms * direct_ctas_per_sm();
+    int dctas[2];
+    std::vector<int> goff, doff[2];
+    std::vector<int2> gord, dord[2];
+    if (gctas) assign(gunits, gcost, gctas, goff, gord);
+    for (int w = 0; w < 2; ++w) {
+        dctas[w] = dunits[w].empty() ? 0 : std::min<int>(dctas_max, (int)dunits[w].size());
+        if (dctas[w]) assign(dunits[w], dcost[w], dctas[w], doff[w], dord[w]);
+    }
+    const size_t t_gjobs = L.take(gjobs.size() * sizeof(GemmJob), 128);
+    const size_t t_goff = L.take(goff.size() * sizeof(int));
+    const size_t t_gunits = L.take(gord.size() * sizeof(int2));
+    size_t t_djobs[2], t_doff[2], t_dunits[2];
+    for (int w = 0; w < 2; ++w) {
+        t_djobs[w] = L.take(djobs[w].size() * sizeof(DirectJob));
+        t_doff[w] = L.take(doff[w].size() * sizeof(int));
+        t_dunits[w] = L.take(dord[w].size() * sizeof(int2));
+    }
+    // (re)allocate the arena
+    if (L.bytes > plan->arena_bytes) {
+        if (plan->arena) {
+            cudaFree(plan->arena);
+            plan->arena = nullptr;
+            plan->arena_bytes = 0;
+        }
+        if (cudaMalloc(&plan->arena, L.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return CGH_ENOMEM;
+        }
+        plan->arena_bytes = L.bytes;
+    }
+    char *A = static_cast<char *>(plan->arena);
+    // fill the job tables with device pointers
+    {
+        int gj = 0, dj[2] = {0, 0};
+        for (int i = 0; i < n; ++i) {
+            if (inst[i].n_points == 0) continue;
+            const int f = plan->forms[i];
+            const Off &o = off[i];
+            if (f >= CGH_GEMM_F16) {
+                if (!fill_gemm_job(&gjobs[gj], factor_mode(f), bn[i], A + o.p, A + o.q, inst[i].height,
+                                   inst[i].width, o.ld,
+                                   f == CGH_GEMM_SPLIT16 ? (ctx->gemm_chunk > 0 ? ctx->gemm_chunk : kSplit16ChunkKbBatch)
+                                                         : ctx->gemm_chunk,
+                                   inst[i].d_out, reinterpret_cast<float *>(A + o.amax)))
+                    return CGH_ECUDA;
+                ++gj;
+            } else {
+                const int w = f == CGH_DIRECT_SFU ? 0 : 1;
+                DirectJob &J = djobs[w][dj[w]++];
+                J.geo = reinterpret_cast<const int4 *>(A + o.geo);
+                J.aux = reinterpret_cast<const uint2 *>(A + o.aux);
+                J.out = inst[i].d_out;
+                J.n_ptiles = (int)(o.n_pad / kPointTile);
+                J.width = inst[i].width;
+                J.height = inst[i].height;
+                J.tiles_x = (inst[i].width + dsh.tile_w - 1) / dsh.tile_w;
+                J.vec = (inst[i].width % 4 == 0) && ((uintptr_t)inst[i].d_out % 16 == 0);
+                J.pad = 0;
+            }
+        }
+    }
+    auto up = [&](size_t at, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpy(A + at, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!up(t_gjobs, gjobs.data(), gjobs.size() * sizeof(GemmJob)) || !up(t_goff, goff.data(), goff.size() * sizeof(int)) ||
+        !up(t_gunits, gord.data(), gord.size() * sizeof(int2)))
+        return cuda_status(cudaGetLastError());
+    for (int w = 0; w < 2; ++w)
+        if (!up(t_djobs[w], djobs[w].data(), djobs[w].size() * sizeof(DirectJob)) ||
+            !up(t_doff[w], doff[w].data(), doff[w].size() * sizeof(int)) ||
+            !up(t_dunits[w], dord[w].data(), dord[w].size() * sizeof(int2)))
+            return cuda_status(cudaGetLastError());
+
+    // capture the whole batch
+    if (!plan->capture && cudaStreamCreateWithFlags(&plan->capture, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+    if (plan->exec) {
+        cudaGraphExecDestroy(plan->exec);
+        plan->exec = nullptr;
+    }
+    const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
+    cudaStream_t s = plan->capture;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const cgh_instance &b = inst[i];
+        if (b.n_points == 0) {
+            e = cudaMemsetAsync(b.d_out, 0, (size_t)b.width * b.height * sizeof(float), s);
+            continue;
+        }
+        const int f = plan->forms[i];
+        const Off &o = off[i];
+        float *amax = reinterpret_cast<float *>(A + o.amax);
+        const bool gemm = f >= CGH_GEMM_F16;
+        if (gemm) e = cudaMemsetAsync(amax, 0, sizeof(float), s);
+        if (e == cudaSuccess)
+            e = launch_prep_points(b.d_xyz, b.d_amp, (int)b.n_points, (int)o.n_pad, b.pitch_m, b.lambda_m,
+                                   reinterpret_cast<int4 *>(A + o.geo), reinterpret_cast<uint2 *>(A + o.aux),
+                                   ctx->d_status, gemm ? amax : nullptr, s);
+        if (e == cudaSuccess && gemm)
+            e = launch_factors(factor_mode(f), reinterpret_cast<const int4 *>(A + o.geo),
+                               reinterpret_cast<const uint2 *>(A + o.aux), (int)b.n_points, b.height, b.width,
+                               A + o.p, A + o.q, o.ld, amax, s);
+    }
+    if (e == cudaSuccess && gctas)
+        e = launch_gemm_batch(reinterpret_cast<const GemmJob *>(A + t_gjobs), reinterpret_cast<const int *>(A + t_goff),
+                              reinterpret_cast<const int2 *>(A + t_gunits), gctas, ctx->d_status, tmo, s);
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+        if (dctas[w])
+            e = launch_direct_batch(w == 0, reinterpret_cast<const DirectJob *>(A + t_djobs[w]),
+                                    reinterpret_cast<const int *>(A + t_doff[w]),
+                                    reinterpret_cast<const int2 *>(A + t_dunits[w]), dctas[w], ctx->d_status, tmo, s);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return CGH_ECUDA;
+    }
+    ec = cudaGraphInstantiate(&plan->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) {
+        plan->exec = nullptr;
+        return cuda_status(ec);
+    }
+    plan->key = plan_key(ctx, inst, n);
+    return CGH_OK;
+}
+
+}  // namespace
+
+int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n)
+{
+    if (!ctx->batch) ctx->batch = new BatchPlan();
+    BatchPlan *plan = ctx->batch;
+    const std::vector<uint64_t> key = plan_key(ctx, inst, n);
+    if (!(plan->exec && plan->key == key)) {
+        // the previous graph may still be running on the context's stream
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_status(cudaGetLastError());
+        plan->key.clear();
+        const int rc = build_plan(ctx, inst, n, plan);
+        if (rc) return rc;
+    }
+    ProfileScope ps(ctx, "batch_graph", 1);
+    return cuda_status(cudaGraphLaunch(plan->exec, ctx->stream));
+}
+
+}  // namespace cgh

@@ -1,0 +1,177 @@
+// Internal: the context behind the C ABI's opaque cgh_ctx, its workspace
+// helpers, and the pipeline entry points shared by api.cu, batch.cu and tuner.cpp.
+#pragma once
+
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cgh.h"
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace cgh {
+struct BatchPlan;
+struct TuneState;
+void destroy_batch_plan(BatchPlan *plan);
+void destroy_tune_state(TuneState *t);
+}  // namespace cgh
+
+struct cgh_ctx {
+    int width = 0, height = 0;
+    double pitch = 0.0, lambda = 0.0;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    int form = CGH_FORM_AUTO;
+    int64_t timeout_ms = 5000;
+    int point_split = 0;
+    int gemm_splitk = 0;
+    int gemm_bn = 0;
+    int gemm_chunk = 0;
+    int drop_tile = -1;       // CGH_OPT_TEST_DROP_TILE
+    int64_t tol_e9 = 10000;   // 1e-5
+    int *d_status = nullptr;  // [0] status bits, [1..2] quantiser scratch, [3] spare
+    void *ws = nullptr;       // grow-only workspace
+    size_t ws_bytes = 0;
+    void *io = nullptr;       // device staging of cgh_point_cloud_host
+    size_t io_bytes = 0;
+    // CGH_OPT_PROFILE: events around each launch, folded into per-kernel totals on read
+    bool profile = false;
+    struct Pending {
+        const char *name;
+        int launches;
+        cudaEvent_t start, stop;
+    };
+    struct Total {
+        std::string name;
+        int64_t launches;
+        double ms;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<Total> totals;
+    cgh::BatchPlan *batch = nullptr;   // cgh_batch: cached plan and CUDA graph
+    cgh::TuneState *tune = nullptr;    // autotuner measurements
+};
+
+namespace cgh {
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+        dev_ = dev;
+    }
+    ~DeviceGuard()
+    {
+        if (prev_ != dev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0, dev_ = 0;
+};
+
+inline bool finite_positive(double v)
+{
+    return std::isfinite(v) && v > 0.0;
+}
+
+inline bool valid_size(int w, int h)
+{
+    return w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide;
+}
+
+inline size_t align_up(size_t v, size_t a)
+{
+    return (v + a - 1) / a * a;
+}
+
+inline int ensure(void **buf, size_t *cap, size_t need)
+{
+    if (need <= *cap) return CGH_OK;
+    if (*buf) {
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    size_t want = align_up(need + need / 4, 1 << 20);
+    if (cudaMalloc(buf, want) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return CGH_ENOMEM;
+    }
+    *cap = want;
+    return CGH_OK;
+}
+
+inline int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return CGH_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? CGH_ENOMEM : CGH_ECUDA;
+}
+
+inline cudaEvent_t take_event(cgh_ctx *ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets the launches made in its scope with events on the context's stream.
+class ProfileScope {
+  public:
+    ProfileScope(cgh_ctx *ctx, const char *name, int launches) : ctx_(ctx), name_(name), launches_(launches)
+    {
+        if (ctx_->profile && (start_ = take_event(ctx_))) cudaEventRecord(start_, ctx_->stream);
+    }
+    ~ProfileScope()
+    {
+        if (!start_) return;
+        cudaEvent_t stop = take_event(ctx_);
+        if (!stop) return;
+        cudaEventRecord(stop, ctx_->stream);
+        ctx_->pending.push_back({name_, launches_, start_, stop});
+    }
+
+  private:
+    cgh_ctx *ctx_;
+    const char *name_;
+    int launches_;
+    cudaEvent_t start_ = nullptr;
+};
+
+inline int64_t padded_points(int64_t n)
+{
+    return (n + kPointTile - 1) / kPointTile * kPointTile;
+}
+
+
+// Pipeline entry points (api.cu).
+int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, double lambda, const float *d_xyz,
+               const float *d_amp, int64_t n, float *d_out);
+int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double lambda, const float *d_xyz,
+             const float *d_amp, int64_t n, float *d_out);
+int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double lambda, const float *d_xyz,
+                     const float *d_amp, int64_t n, float *d_out);
+int factor_mode(int form);
+int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n);
+int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
+
+}  // namespace cgh

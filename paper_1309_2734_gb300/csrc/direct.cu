@@ -72,35 +72,27 @@ __device__ __forceinline__ float cos_term(uint32_t g)
     }
 }
 
+// One unit of work: point tiles [t_begin, t_end) of one cloud into one
+// CTA-sized pixel tile with corner (tile_m0, tile_n0).  kg counts the point
+// tiles this CTA consumed before (stage and mbarrier parity carry across units).
 template <int TL, int TR, int BX, int BY, bool SFU>
-__global__ void __launch_bounds__(BX *BY, 2)
-    direct_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_ptiles, int width,
-                  int height, int tiles_x, int split, float *__restrict__ out, long long slice_stride,
-                  bool vec, int *status, unsigned long long timeout_ns)
+__device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const uint2 *__restrict__ aux,
+                                            int t_begin, int t_end, int tile_m0, int tile_n0, int width,
+                                            int height, float *__restrict__ dst, bool vec, int4 (*s_geo)[kPointTile],
+                                            uint2 (*s_aux)[kPointTile], uint64_t *s_bar, uint32_t &kg, int *status,
+                                            unsigned long long timeout_ns, int drop = -1)
 {
     constexpr int T = kPointTile;
     constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
-    __shared__ alignas(128) int4 s_geo[2][T];
-    __shared__ alignas(128) uint2 s_aux[2][T];
-    __shared__ alignas(8) uint64_t s_bar[2];
-
     const int tid = threadIdx.x;
     const int lx = tid % BX, ly = tid / BX;
-    const int tile = blockIdx.x;
-    const int m0 = (tile % tiles_x) * (BX * TL) + lx * TL;
-    const int n0 = (tile / tiles_x) * (BY * TR) + ly * TR;
-    const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
-    const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
+    const int m0 = tile_m0 + lx * TL;
+    const int n0 = tile_n0 + ly * TR;
     const int nt = t_end - t_begin;
 
-    if (tid == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
     auto issue = [&](int k) {
-        const int st = k & 1;
+        if (k == drop) return;   // test hook: this tile's barrier is never completed
+        const int st = (int)((kg + (uint32_t)k) & 1u);
         const long long first = (long long)(t_begin + k) * T;
         mbar_arrive_expect_tx(&s_bar[st], kTileBytes);
         bulk_copy_g2s(&s_geo[st][0], geo + first, T * sizeof(int4), &s_bar[st]);
@@ -117,11 +109,22 @@ __global__ void __launch_bounds__(BX *BY, 2)
 #pragma unroll
         for (int i = 0; i < TL; ++i) tot[r][i] = 0.0f;
 
+    bool ok = true;
     for (int k = 0; k < nt; ++k) {
-        const int st = k & 1;
-        const bool arrived = mbar_wait(&s_bar[st], (uint32_t)((k >> 1) & 1), timeout_ns);
+        const uint32_t kk = kg + (uint32_t)k;
+        const int st = (int)(kk & 1u);
+        const bool arrived = mbar_wait(&s_bar[st], (kk >> 1) & 1u, timeout_ns);
         if (__syncthreads_or(!arrived)) {
-            if (tid == 0) atomicOr(status, kStatusTimeout);
+            if (tid == 0) {
+                atomicOr(status, kStatusTimeout);
+                // wait (bounded) for the other tile copy this unit may still have in flight
+                if (k + 1 < nt && k + 1 != drop) {
+                    const uint32_t kn = kk + 1u;
+                    mbar_wait(&s_bar[kn & 1u], (kn >> 1) & 1u, timeout_ns);
+                }
+            }
+            __syncthreads();
+            ok = false;
             break;
         }
         float part[TR][TL];
@@ -173,8 +176,9 @@ __global__ void __launch_bounds__(BX *BY, 2)
         __syncthreads();   // every thread is done with stage st
         if (tid == 0 && k + 2 < nt) issue(k + 2);
     }
+    kg += (uint32_t)nt;
+    if (!ok) return false;
 
-    float *dst = out + (long long)blockIdx.y * slice_stride;
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
         const int n = n0 + r;
@@ -190,6 +194,60 @@ __global__ void __launch_bounds__(BX *BY, 2)
                 if (m0 + i < width) row[i] = tot[r][i];
         }
     }
+    return true;
+}
+
+template <int BX, int BY>
+__device__ __forceinline__ void init_point_barriers(uint64_t *s_bar)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+}
+
+// One hologram: blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).
+template <int TL, int TR, int BX, int BY, bool SFU>
+__global__ void __launch_bounds__(BX *BY, 2)
+    direct_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_ptiles, int width,
+                  int height, int tiles_x, int split, float *__restrict__ out, long long slice_stride,
+                  bool vec, int *status, unsigned long long timeout_ns, int drop_tile)
+{
+    __shared__ alignas(128) int4 s_geo[2][kPointTile];
+    __shared__ alignas(128) uint2 s_aux[2][kPointTile];
+    __shared__ alignas(8) uint64_t s_bar[2];
+    init_point_barriers<BX, BY>(s_bar);
+    const int tile = blockIdx.x;
+    const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
+    const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
+    uint32_t kg = 0;
+    direct_unit<TL, TR, BX, BY, SFU>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
+                                     (tile / tiles_x) * (BY * TR), width, height,
+                                     out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg,
+                                     status, timeout_ns, blockIdx.y == 0 ? drop_tile : -1);
+}
+
+// A batch: every CTA walks its list of {job, pixel tile} units over all points of the job.
+template <int TL, int TR, int BX, int BY, bool SFU>
+__global__ void __launch_bounds__(BX *BY, 2)
+    direct_batch_kernel(const DirectJob *__restrict__ jobs, const int *__restrict__ cta_off,
+                        const int2 *__restrict__ units, int *status, unsigned long long timeout_ns)
+{
+    __shared__ alignas(128) int4 s_geo[2][kPointTile];
+    __shared__ alignas(128) uint2 s_aux[2][kPointTile];
+    __shared__ alignas(8) uint64_t s_bar[2];
+    init_point_barriers<BX, BY>(s_bar);
+    uint32_t kg = 0;
+    for (int i = cta_off[blockIdx.x]; i < cta_off[blockIdx.x + 1]; ++i) {
+        const int2 w = units[i];
+        const DirectJob &J = jobs[w.x];
+        if (!direct_unit<TL, TR, BX, BY, SFU>(J.geo, J.aux, 0, J.n_ptiles, (w.y % J.tiles_x) * (BX * TL),
+                                              (w.y / J.tiles_x) * (BY * TR), J.width, J.height, J.out,
+                                              J.vec != 0, s_geo, s_aux, s_bar, kg, status, timeout_ns))
+            break;
+    }
 }
 
 constexpr int kTL = 8, kTR = 4, kBX = 32, kBY = 8;
@@ -203,7 +261,7 @@ DirectShape direct_shape(bool)
 
 cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
                           int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
-                          cudaStream_t s)
+                          cudaStream_t s, int drop_tile)
 {
     const DirectShape sh = direct_shape(sfu);
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
@@ -215,11 +273,33 @@ cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad
     const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
     if (sfu)
         direct_kernel<kTL, kTR, kBX, kBY, true><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns);
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns, drop_tile);
     else
         direct_kernel<kTL, kTR, kBX, kBY, false><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns);
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns, drop_tile);
     return cudaGetLastError();
+}
+
+}  // namespace cgh
+
+namespace cgh {
+
+cudaError_t launch_direct_batch(bool sfu, const DirectJob *d_jobs, const int *d_cta_off, const int2 *d_units,
+                                int ctas, int *status, uint64_t timeout_ns, cudaStream_t s)
+{
+    if (ctas <= 0) return cudaSuccess;
+    if (sfu)
+        direct_batch_kernel<kTL, kTR, kBX, kBY, true><<<ctas, kBX * kBY, 0, s>>>(d_jobs, d_cta_off, d_units, status,
+                                                                                 timeout_ns);
+    else
+        direct_batch_kernel<kTL, kTR, kBX, kBY, false><<<ctas, kBX * kBY, 0, s>>>(d_jobs, d_cta_off, d_units,
+                                                                                  status, timeout_ns);
+    return cudaGetLastError();
+}
+
+int direct_ctas_per_sm()
+{
+    return 2;
 }
 
 }  // namespace cgh

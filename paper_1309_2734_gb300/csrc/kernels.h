@@ -23,9 +23,22 @@ struct DirectShape {
     int threads;          // threads per CTA
 };
 DirectShape direct_shape(bool sfu);
+// drop_tile >= 0 is a test hook: the first point chunk never loads that tile,
+// so its bounded wait runs out and the launch ends with kStatusTimeout.
 cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
                           int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
-                          cudaStream_t s);
+                          cudaStream_t s, int drop_tile = -1);
+
+// a7: one job (hologram) of a batched direct launch; units are {job, pixel tile}.
+struct DirectJob {
+    const int4 *geo;
+    const uint2 *aux;
+    float *out;
+    int n_ptiles, width, height, tiles_x, vec, pad;
+};
+cudaError_t launch_direct_batch(bool sfu, const DirectJob *d_jobs, const int *d_cta_off, const int2 *d_units,
+                                int ctas, int *status, uint64_t timeout_ns, cudaStream_t s);
+int direct_ctas_per_sm();
 
 // a3: separable factors P [height][ld], Q [width][ld] (factors.cu).  For
 // kFactorSplit16 the lo planes follow the hi planes (offset rows * ld).

@@ -1,0 +1,409 @@
+// Autotuner and launch-shape selection (host side).
+//
+// Static rules (no measurement):
+//   choose_point_split  point chunks of the direct kernel, to fill whole waves;
+//   choose_gemm_bn      GEMM tile width with the least padding of the width;
+//   choose_gemm_splits  K splits of the GEMM, to balance tiles over the CTAs.
+//
+// Measured rules (a context, outside any stream capture):
+//   tune_calibrate      times every form on three synthetic clouds on this
+//                       device and fits, per form, t = c0 + c1 W H N + c2 (W + H) N;
+//   tune_choose_form    the fastest form whose stated NRMS bound is within the
+//                       requested tolerance, by that model;
+//   tune_choose_bn      the fastest GEMM tile width for a hologram shape and
+//                       form, timed on that shape with 4096 points, cached.
+// With CGH_TUNE_CACHE=<path> in the environment the measurements are read
+// from and written to a small JSON file keyed by the device name.
+#include "tuner.h"
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "context.h"
+
+namespace cgh {
+
+namespace {
+constexpr int kDirectCtasPerSm = 2;
+constexpr int kForms = 6;
+}  // namespace
+
+int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms)
+{
+    if (pixel_tiles <= 0 || point_tiles <= 1) return 1;
+    const int64_t slots = (int64_t)num_sms * kDirectCtasPerSm;
+    auto efficiency = [&](int64_t s) {
+        const int64_t units = pixel_tiles * s;
+        const int64_t waves = (units + slots - 1) / slots;
+        return (double)units / (double)(waves * slots);
+    };
+    int best = 1;
+    double best_eff = efficiency(1);
+    for (int64_t s = 2; s <= 32 && s * 2 <= point_tiles; ++s) {
+        const double e = efficiency(s);
+        // each extra chunk costs one more plane of partial sums; demand a clear gain
+        if (e > best_eff + 0.03) {
+            best = (int)s;
+            best_eff = e;
+        }
+        if (best_eff > 0.97) break;
+    }
+    return best;
+}
+
+int choose_gemm_bn(int width)
+{
+    static const int cands[] = {256, 240, 192, 128};
+    int best = 256;
+    double best_waste = 1e30;
+    for (int bn : cands) {
+        const int tiles = (width + bn - 1) / bn;
+        const double waste = (double)(tiles * bn - width) / (double)width + 1e-3 * (256 - bn) / 256.0;
+        if (waste < best_waste) {
+            best_waste = waste;
+            best = bn;
+        }
+    }
+    return best;
+}
+
+int choose_gemm_splits(int64_t tiles, int64_t k_blocks, int ctas)
+{
+    if (tiles <= 0 || ctas <= 0) return 1;
+    int best = 1;
+    double best_time = 1e30;
+    for (int64_t s = 1; s <= 32 && s * 4 <= (k_blocks > 4 ? k_blocks : 4); ++s) {
+        const int64_t units = tiles * s;
+        const int64_t rounds = (units + ctas - 1) / ctas;
+        // time in units of one whole-K tile; each extra split costs a partial plane
+        const double t = (double)rounds / (double)s + 0.01 * (double)(s - 1);
+        if (t < best_time - 1e-9) {
+            best_time = t;
+            best = (int)s;
+        }
+    }
+    return best;
+}
+
+// Stated NRMS bound of each form against the FP64 oracle (measured values are
+// below these: direct SFU ~4e-7, direct accurate ~1e-7, split FP16 ~3e-6,
+// FP16 ~3e-4, BF16 ~2e-3 on the display-size clouds).
+double form_nrms_bound(int form)
+{
+    switch (form) {
+    case CGH_DIRECT_SFU: return 1e-5;
+    case CGH_DIRECT_ACCURATE: return 2e-6;
+    case CGH_GEMM_F16: return 2e-3;
+    case CGH_GEMM_BF16: return 1e-2;
+    case CGH_GEMM_SPLIT16: return 1e-5;
+    default: return 1.0;
+    }
+}
+
+struct TuneState {
+    bool calibrated = false;
+    double coef[kForms][3] = {};   // seconds: c0, per W*H*N, per (W+H)*N
+    std::map<std::string, int> bn;
+    std::string device;
+};
+
+void destroy_tune_state(TuneState *t)
+{
+    delete t;
+}
+
+namespace {
+
+std::string device_name(int dev)
+{
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    return std::string(p.name) + ":" + std::to_string(p.multiProcessorCount);
+}
+
+const char *cache_path()
+{
+    const char *p = std::getenv("CGH_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+void save_cache(const TuneState &t)
+{
+    const char *path = cache_path();
+    if (!path) return;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return;
+    std::fprintf(f, "{\n \"abi\": %d,\n \"device\": \"%s\",\n \"coef\": [", CGH_ABI_VERSION, t.device.c_str());
+    for (int i = 0; i < kForms; ++i)
+        std::fprintf(f, "%s[%.9e, %.9e, %.9e]", i ? ", " : "", t.coef[i][0], t.coef[i][1], t.coef[i][2]);
+    std::fprintf(f, "],\n \"bn\": {");
+    bool first = true;
+    for (const auto &kv : t.bn) {
+        std::fprintf(f, "%s\"%s\": %d", first ? "" : ", ", kv.first.c_str(), kv.second);
+        first = false;
+    }
+    std::fprintf(f, "}\n}\n");
+    std::fclose(f);
+}
+
+// Reads a cache written by save_cache for the same device and ABI; anything else is ignored.
+bool load_cache(TuneState &t)
+{
+    const char *path = cache_path();
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+    std::fclose(f);
+    const std::string dev_key = "\"device\": \"" + t.device + "\"";
+    const std::string abi_key = "\"abi\": " + std::to_string(CGH_ABI_VERSION);
+    if (text.find(dev_key) == std::string::npos || text.find(abi_key) == std::string::npos) return false;
+    size_t c = text.find("\"coef\": [");
+    if (c == std::string::npos) return false;
+    const char *p = text.c_str() + c + 9;
+    for (int i = 0; i < kForms; ++i) {
+        double a, b, d;
+        int n = 0;
+        if (std::sscanf(p, " [%lf, %lf, %lf]%n", &a, &b, &d, &n) != 3) return false;
+        t.coef[i][0] = a;
+        t.coef[i][1] = b;
+        t.coef[i][2] = d;
+        p += n;
+        while (*p == ',' || *p == ' ') ++p;
+    }
+    size_t bpos = text.find("\"bn\": {");
+    if (bpos != std::string::npos) {
+        const char *q = text.c_str() + bpos + 7;
+        for (;;) {
+            char key[128];
+            int val, n = 0;
+            if (std::sscanf(q, " \"%127[^\"]\": %d%n", key, &val, &n) != 2) break;
+            if (gemm_bn_supported(val)) t.bn[key] = val;
+            q += n;
+            while (*q == ',' || *q == ' ') ++q;
+        }
+    }
+    t.calibrated = true;
+    return true;
+}
+
+// Deterministic synthetic cloud (integer positions inside the hologram,
+// z in [0.3, 1] m, A in [0.5, 1]) for the measurements.
+void synth_points(int width, int height, int64_t n, std::vector<float> &xyz, std::vector<float> &amp)
+{
+    xyz.resize((size_t)n * 3);
+    amp.resize((size_t)n);
+    uint64_t s = 0x9e3779b97f4a7c15ull;
+    auto next = [&]() {
+        s ^= s << 13;
+        s ^= s >> 7;
+        s ^= s << 17;
+        return s;
+    };
+    for (int64_t j = 0; j < n; ++j) {
+        xyz[3 * j + 0] = (float)(next() % (uint64_t)width);
+        xyz[3 * j + 1] = (float)(next() % (uint64_t)height);
+        xyz[3 * j + 2] = 0.3f + 0.7f * (float)((next() >> 11) * (1.0 / 9007199254740992.0));
+        amp[j] = 0.5f + 0.5f * (float)((next() >> 11) * (1.0 / 9007199254740992.0));
+    }
+}
+
+struct Scratch {
+    float *xyz = nullptr, *amp = nullptr, *out = nullptr;
+    ~Scratch()
+    {
+        if (xyz) cudaFree(xyz);
+        if (amp) cudaFree(amp);
+        if (out) cudaFree(out);
+    }
+};
+
+// Seconds per hologram of `form` (tile width bn, 0 = default) on a synthetic cloud.
+double time_form(cgh_ctx *ctx, int form, int bn, int width, int height, int64_t n, int reps)
+{
+    std::vector<float> hx, ha;
+    synth_points(width, height, n, hx, ha);
+    Scratch s;
+    if (cudaMalloc(&s.xyz, hx.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&s.amp, ha.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&s.out, (size_t)width * height * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    cudaMemcpy(s.xyz, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(s.amp, ha.data(), ha.size() * sizeof(float), cudaMemcpyHostToDevice);
+    const int saved_form = ctx->form, saved_bn = ctx->gemm_bn;
+    const bool saved_profile = ctx->profile;
+    ctx->form = form;
+    ctx->gemm_bn = bn;
+    ctx->profile = false;
+    double sec = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+        compute_hologram(ctx, width, height, ctx->pitch, ctx->lambda, s.xyz, s.amp, n, s.out) == CGH_OK) {
+        cudaEventRecord(e0, ctx->stream);
+        bool ok = true;
+        for (int r = 0; r < reps && ok; ++r)
+            ok = compute_hologram(ctx, width, height, ctx->pitch, ctx->lambda, s.xyz, s.amp, n, s.out) == CGH_OK;
+        cudaEventRecord(e1, ctx->stream);
+        if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) sec = ms * 1e-3 / reps;
+        }
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctx->form = saved_form;
+    ctx->gemm_bn = saved_bn;
+    ctx->profile = saved_profile;
+    return sec;
+}
+
+// Least squares for t = c0 + c1 x1 + c2 x2 over the samples; coefficients kept >= 0.
+void fit3(const std::vector<double> &t, const std::vector<double> &x1, const std::vector<double> &x2, double c[3])
+{
+    const size_t m = t.size();
+    double A[3][3] = {}, b[3] = {};
+    for (size_t i = 0; i < m; ++i) {
+        const double r[3] = {1.0, x1[i], x2[i]};
+        for (int p = 0; p < 3; ++p) {
+            b[p] += r[p] * t[i];
+            for (int q = 0; q < 3; ++q) A[p][q] += r[p] * r[q];
+        }
+    }
+    // Cramer's rule on the normal equations, then clamp
+    auto det3 = [](double M[3][3]) {
+        return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+               M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    };
+    const double d = det3(A);
+    for (int k = 0; k < 3; ++k) {
+        double M[3][3];
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) M[p][q] = (q == k) ? b[p] : A[p][q];
+        c[k] = d != 0.0 ? det3(M) / d : 0.0;
+    }
+    if (c[0] < 0.0 || c[1] < 0.0 || c[2] < 0.0) {
+        // fall back to a proportional model through the largest sample
+        size_t big = 0;
+        for (size_t i = 1; i < m; ++i)
+            if (x1[i] > x1[big]) big = i;
+        c[0] = 0.0;
+        c[1] = x1[big] > 0 ? t[big] / x1[big] : 0.0;
+        c[2] = 0.0;
+    }
+}
+
+std::string bn_key(int width, int height, int form)
+{
+    return std::to_string(width) + "x" + std::to_string(height) + ":" + std::to_string(form);
+}
+
+TuneState *state(cgh_ctx *ctx)
+{
+    if (!ctx->tune) {
+        ctx->tune = new TuneState();
+        ctx->tune->device = device_name(ctx->device);
+        load_cache(*ctx->tune);
+    }
+    return ctx->tune;
+}
+
+}  // namespace
+
+int tune_calibrate(cgh_ctx *ctx, bool force)
+{
+    TuneState *t = state(ctx);
+    if (t->calibrated && !force) return CGH_OK;
+    struct Shape {
+        int w, h;
+        int64_t n;
+    };
+    const Shape shapes[3] = {{256, 256, 2048}, {1024, 512, 8192}, {1024, 1024, 16384}};
+    const int forms[5] = {CGH_DIRECT_SFU, CGH_DIRECT_ACCURATE, CGH_GEMM_F16, CGH_GEMM_BF16, CGH_GEMM_SPLIT16};
+    for (int f : forms) {
+        std::vector<double> ts, x1, x2;
+        for (const Shape &s : shapes) {
+            const double sec = time_form(ctx, f, 0, s.w, s.h, s.n, 3);
+            if (sec <= 0.0) return CGH_ECUDA;
+            ts.push_back(sec);
+            x1.push_back((double)s.w * s.h * (double)s.n);
+            x2.push_back((double)(s.w + s.h) * (double)s.n);
+        }
+        fit3(ts, x1, x2, t->coef[f]);
+    }
+    t->calibrated = true;
+    save_cache(*t);
+    return CGH_OK;
+}
+
+double tune_predict(cgh_ctx *ctx, int form, int width, int height, int64_t n)
+{
+    TuneState *t = state(ctx);
+    const double *c = t->coef[form];
+    return c[0] + c[1] * (double)width * height * (double)n + c[2] * (double)(width + height) * (double)n;
+}
+
+int tune_choose_form(cgh_ctx *ctx, int width, int height, int64_t n, double tol)
+{
+    if (tune_calibrate(ctx, false) != CGH_OK) return CGH_DIRECT_SFU;
+    const int forms[5] = {CGH_DIRECT_SFU, CGH_DIRECT_ACCURATE, CGH_GEMM_F16, CGH_GEMM_BF16, CGH_GEMM_SPLIT16};
+    int best = -1;
+    double best_t = 1e300;
+    for (int f : forms) {
+        if (form_nrms_bound(f) > tol) continue;
+        const double tp = tune_predict(ctx, f, width, height, n);
+        if (tp < best_t) {
+            best_t = tp;
+            best = f;
+        }
+    }
+    // nothing meets a tolerance tighter than every bound: the most accurate form
+    return best >= 0 ? best : CGH_DIRECT_ACCURATE;
+}
+
+int tune_choose_bn(cgh_ctx *ctx, int width, int height, int form)
+{
+    TuneState *t = state(ctx);
+    const std::string key = bn_key(width, height, form);
+    auto it = t->bn.find(key);
+    if (it != t->bn.end()) return it->second;
+    static const int cands[] = {256, 240, 192, 128};
+    int best = choose_gemm_bn(width);
+    double best_t = 1e300;
+    for (int bn : cands) {
+        const double sec = time_form(ctx, form, bn, width, height, 4096, 3);
+        if (sec > 0.0 && sec < best_t) {
+            best_t = sec;
+            best = bn;
+        }
+    }
+    t->bn[key] = best;
+    save_cache(*t);
+    return best;
+}
+
+int choose_form(int width, int height, int64_t n_points, double tol, int num_sms)
+{
+    (void)width;
+    (void)height;
+    (void)n_points;
+    (void)num_sms;
+    // without measurements: the direct SFU form when it is admissible, else the accurate one
+    return form_nrms_bound(CGH_DIRECT_SFU) <= tol ? CGH_DIRECT_SFU
+                                                   : (tol >= form_nrms_bound(CGH_GEMM_F16) ? CGH_GEMM_F16
+                                                                                            : CGH_DIRECT_ACCURATE);
+}
+
+}  // namespace cgh

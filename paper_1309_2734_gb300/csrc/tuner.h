@@ -1,7 +1,9 @@
-// Launch-shape and form selection (host side).
+// Launch-shape selection and the measured autotuner (host side).
 #pragma once
 
 #include <cstdint>
+
+struct cgh_ctx;
 
 namespace cgh {
 
@@ -16,7 +18,19 @@ int choose_gemm_bn(int width);
 // persistent CTAs; each split keeps at least 4 k-blocks of 64.
 int choose_gemm_splits(int64_t tiles, int64_t k_blocks, int ctas);
 
-// Form for CGH_FORM_AUTO: the fastest form whose stated NRMS bound is within tol.
+// Stated NRMS bound of a form against the FP64 oracle.
+double form_nrms_bound(int form);
+
+// Form without measurements (static rule).
 int choose_form(int width, int height, int64_t n_points, double tol, int num_sms);
+
+// Measured: calibrate the per-form time model on this device (once; cached).
+int tune_calibrate(cgh_ctx *ctx, bool force);
+// Predicted seconds per hologram of a form.
+double tune_predict(cgh_ctx *ctx, int form, int width, int height, int64_t n);
+// Fastest admissible form by the calibrated model.
+int tune_choose_form(cgh_ctx *ctx, int width, int height, int64_t n, double tol);
+// Fastest GEMM tile width for a shape and form, timed on that shape.
+int tune_choose_bn(cgh_ctx *ctx, int width, int height, int form);
 
 }  // namespace cgh

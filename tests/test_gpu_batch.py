@@ -1,0 +1,134 @@
+"""Batched holograms (one persistent launch per form kind, captured in a CUDA
+graph) and the autotuner, through the C ABI, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_2734_gb300 import Hologram, batch, workloads
+from paper_1309_2734_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NRMS = {"direct_sfu": 1e-5, "direct_accurate": 1e-5, "gemm_f16": 2e-3, "gemm_bf16": 1e-2, "gemm_split16": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_2734_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+
+
+def _clouds():
+    return [workloads.random_cloud(700, 300, 200, 1500), workloads.random_cloud(701, 128, 130, 300),
+            workloads.random_cloud(702, 257, 65, 0), workloads.random_cloud(703, 500, 120, 2100),
+            workloads.random_cloud(704, 64, 64, 5)]
+
+
+def _dev(clouds):
+    return [(torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda(), c.width, c.height, c.pitch_m,
+             c.lambda_m) for c in clouds]
+
+
+def _check_all(clouds, outs, tol):
+    for c, o in zip(clouds, outs):
+        got = o.cpu().numpy()
+        if c.n_points == 0:
+            assert np.count_nonzero(got) == 0
+            continue
+        ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+        assert oracle.nrms(got, ref) <= tol, (c.name, oracle.nrms(got, ref))
+
+
+@pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
+def test_batch_each_form_vs_oracle(form):
+    clouds = _clouds()
+    dev = _dev(clouds)
+    outs = [torch.full((c.height, c.width), 5.0, device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form=form, timeout_ms=5000) as h:
+        batch(h, dev, outs)
+        h.sync()
+    _check_all(clouds, outs, NRMS[form])
+
+
+def test_batch_replays_graph_on_new_data():
+    clouds = _clouds()
+    dev = _dev(clouds)
+    outs = [torch.zeros((c.height, c.width), device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form="gemm_split16") as h:
+        batch(h, dev, outs)
+        h.sync()
+        first = [o.clone() for o in outs]
+        batch(h, dev, outs)                    # same plan: graph replay
+        h.sync()
+        for a, b in zip(first, outs):
+            assert torch.equal(a, b)
+        # new point data in the same buffers: the replay recomputes
+        fresh = [workloads.random_cloud(800 + i, c.width, c.height, c.n_points) for i, c in enumerate(clouds)]
+        for (xyz, amp, *_), c in zip(dev, fresh):
+            xyz.copy_(torch.from_numpy(c.xyz))
+            amp.copy_(torch.from_numpy(c.amp))
+        batch(h, dev, outs)
+        h.sync()
+    _check_all(fresh, outs, NRMS["gemm_split16"])
+
+
+def test_batch_matches_single_calls():
+    clouds = _clouds()
+    dev = _dev(clouds)
+    outs = [torch.zeros((c.height, c.width), device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form="direct_sfu") as h:
+        batch(h, dev, outs)
+        h.sync()
+    for c, (xyz, amp, *_), o in zip(clouds, dev, outs):
+        with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form="direct_sfu") as h1:
+            one = h1.point_cloud(xyz, amp)
+            h1.sync()
+        assert oracle.nrms(o.cpu().numpy(), one.cpu().numpy()) < 1e-6 or c.n_points == 0
+
+
+@pytest.mark.parametrize("tol_e9,allowed", [(10000, {"direct_sfu", "direct_accurate", "gemm_split16"}),
+                                            (10_000_000, set(NRMS))])
+def test_autotuned_batch_meets_tolerance(tol_e9, allowed):
+    clouds = _clouds()
+    dev = _dev(clouds)
+    outs = [torch.zeros((c.height, c.width), device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form="auto") as h:
+        assert _lib.cgh_autotune(h.ctx, False) == _lib.CGH_OK
+        h.set_option(_lib.CGH_OPT_TOLERANCE_E9, tol_e9)
+        batch(h, dev, outs)
+        h.sync()
+    _check_all(clouds, outs, tol_e9 * 1e-9)
+
+
+def test_auto_single_hologram_meets_tolerance():
+    c = workloads.random_cloud(710, 640, 360, 6000)
+    xyz, amp = torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda()
+    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form="auto") as h:
+        f = h.point_cloud(xyz, amp)
+        h.sync()
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    assert oracle.nrms(f.cpu().numpy(), ref) <= 1e-5
+
+
+def test_video_batch_64_frames_sampled():
+    """64 frames of uneven size (1024^2 / 1920x1080 / 3840x2160, 10^3..2x10^5 points), one
+    batch call at NRMS 1e-5 (autotuned forms), sampled pixels of every frame vs the oracle."""
+    frames = workloads.video_batch()
+    dev = _dev(frames)
+    outs = [torch.empty((c.height, c.width), device="cuda") for c in frames]
+    with Hologram(8, 8, 8e-6, 532e-9, form="auto", timeout_ms=20000) as h:
+        h.set_option(_lib.CGH_OPT_TOLERANCE_E9, 10000)
+        batch(h, dev, outs)
+        h.sync()
+    rng = np.random.default_rng(64)
+    for c, o in zip(frames, outs):
+        cols = rng.integers(0, c.width, 24)
+        rows = rng.integers(0, c.height, 24)
+        ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+        got = o[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
+        assert oracle.nrms(got, ref) <= 1e-5, c.name

@@ -234,3 +234,22 @@ def test_quantize_hologram_vs_oracle_quantisation():
     mism = q != qr
     assert not np.any(mism & ~ties)
     assert ties.mean() < 0.01
+
+
+def test_device_wait_times_out_and_context_recovers():
+    """A point tile that is never loaded (host-side test hook): the kernel's bounded
+    wait runs out, the launch ends with a timeout status, and the context keeps working."""
+    c = workloads.random_cloud(46, 300, 100, 1000)
+    xyz, amp = _dev(c)
+    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form="direct_sfu", timeout_ms=300) as h:
+        h.set_option(_lib.CGH_OPT_POINT_SPLIT, 1)
+        h.set_option(_lib.CGH_OPT_TEST_DROP_TILE, 1)
+        h.point_cloud(xyz, amp)
+        with pytest.raises(CghError) as ei:
+            h.sync()
+        assert ei.value.code == _lib.CGH_ETIMEOUT
+        h.set_option(_lib.CGH_OPT_TEST_DROP_TILE, -1)
+        f = h.point_cloud(xyz, amp)
+        h.sync()
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    _check(f.cpu().numpy(), ref, c.amp)
