@@ -348,14 +348,30 @@ def run_ours(args):
 
     evals_all = cloud.evals * args.steps * world
     value = evals_all / (total_ms * 1e-3) / 1e9
-    dom = "direct_sfu" if args.form == "direct_sfu" else "direct_accurate"
-    dom_launches, dom_ms = prof.get(dom, (0, 0.0))
     props = torch.cuda.get_device_properties(local)
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
-    peak = MUFU_PER_SM_PER_CLK * props.multi_processor_count * sm_max * 1e6 / 1e9
-    achieved = cloud.evals / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e9 if dom_ms > 0 else None
-    kernel_src = os.path.join(ROOT, "paper_1309_2734_gb300", "csrc", "direct.cu")
+    if args.form.startswith("gemm"):
+        # tensor-bound: 4 flop per evaluation per product (3 products for split FP16)
+        dom = "gemm_tcgen05"
+        src = "gemm.cu"
+        dom_launches, dom_ms = prof.get(dom, (0, 0.0))
+        passes = 3 if args.form == "gemm_split16" else 1
+        peak = peaks.get("bf16_tflops") or 1939.7
+        achieved = (4.0 * cloud.evals * passes / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e12) if dom_ms > 0 else None
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
+    else:
+        # MUFU-bound: one hardware sine per evaluation at most
+        dom = args.form
+        src = "direct.cu"
+        dom_launches, dom_ms = prof.get(dom, (0, 0.0))
+        peak = MUFU_PER_SM_PER_CLK * props.multi_processor_count * sm_max * 1e6 / 1e9
+        achieved = cloud.evals / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e9 if dom_ms > 0 else None
+        roof = {"bound": "alu", "unit": "Gcos/s (MUFU)",
+                "peak_basis": f"{MUFU_PER_SM_PER_CLK} MUFU cos/clk/SM x {props.multi_processor_count} SMs x "
+                              f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)"}
+    kernel_src = os.path.join(ROOT, "paper_1309_2734_gb300", "csrc", src)
     traffic = NCU_TRAFFIC.get(dom, {})
     traffic = traffic.get("bytes_per_launch") if traffic.get("sha1") == _sha1(kernel_src) else None
 
@@ -369,9 +385,13 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"gemm_f16": "f16", "gemm_bf16": "bf16", "gemm_split16": "f16x2 (hi+lo)"}.get(args.form, "f32"),
+        "data": "synthetic",
         "config": {"workload": cloud.name, "width": W, "height": H, "n_points": N, "form": args.form,
-                   "step": "prep + direct kernel (+ chunk reduction) + quantize8",
+                   "step": ("prep + factors + tcgen05 GEMM (+ split reduction) + quantize8"
+                            if args.form.startswith("gemm") else
+                            "prep + direct kernel (+ chunk reduction) + quantize8"),
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "holograms_per_s": args.steps * world / (total_ms * 1e-3),
@@ -379,11 +399,9 @@ def run_ours(args):
         "nrms_sample": "the cpu_baseline rows" if nrms is not None else None,
         "gpu_launches": launches,
         "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "Gcos/s (MUFU)", "frac": (achieved / peak) if achieved else None,
-                     "traffic": traffic,
-                     "peak_basis": f"{MUFU_PER_SM_PER_CLK} MUFU cos/clk/SM x {props.multi_processor_count} SMs x "
-                                   f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)"},
+        "roofline": {"kernel": dom, "bound": roof["bound"], "achieved": achieved, "peak": peak,
+                     "unit": roof["unit"], "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic, "peak_basis": roof["peak_basis"]},
         "clocks": clocks,
         "e2e": {"value": cloud.evals * args.steps * world / e2e_total / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": int(cloud.xyz.nbytes + cloud.amp.nbytes),

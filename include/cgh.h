@@ -87,8 +87,9 @@ enum {
     CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */
     CGH_OPT_PROFILE = 6,        /* 1: bracket every kernel launch with CUDA events (cgh_profile_read) */
     CGH_OPT_GEMM_CHUNK = 7,     /* GEMM forms: k-blocks of 64 per tensor-memory accumulation chain; 0 = default */
-    CGH_OPT_TEST_DROP_TILE = 8  /* test hook, direct forms: never load point tile k (>= 0) of the first chunk, so the
+    CGH_OPT_TEST_DROP_TILE = 8, /* test hook, direct forms: never load point tile k (>= 0) of the first chunk, so the
                                    kernel's bounded wait runs out and cgh_sync returns CGH_ETIMEOUT; -1 = off */
+    CGH_OPT_FACTOR_BUDGET_MB = 9 /* GEMM forms: device memory for P and Q of one chunk of points; default 2048 */
 };
 
 typedef struct cgh_ctx cgh_ctx;

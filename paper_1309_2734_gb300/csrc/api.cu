@@ -65,33 +65,45 @@ int factor_mode(int form)
     return form == CGH_GEMM_BF16 ? kFactorBF16 : (form == CGH_GEMM_SPLIT16 ? kFactorSplit16 : kFactorF16);
 }
 
-// GEMM form: prep, factors P and Q (scaled by 1/max|A|), the tcgen05 GEMM over
-// K splits, and the fixed-order split reduction when there is more than one.
+// GEMM form: prep, then per chunk of points the factors P and Q (scaled by
+// 1/max|A|) and the tcgen05 GEMM over K splits, later chunks adding to the
+// planes of the first; then the fixed-order split reduction when there is more
+// than one split.  Chunking bounds the factor workspace (CGH_OPT_FACTOR_BUDGET_MB):
+// 10^6 points of a 4096x4096 split-FP16 hologram would otherwise need 65 GB.
 int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double lambda, const float *d_xyz,
              const float *d_amp, int64_t n, float *d_out)
 {
     const int mode = factor_mode(form);
     const int planes = mode == kFactorSplit16 ? 2 : 1;
     const int64_t n_pad = padded_points(n);
-    const int64_t ld = (2 * n + 63) / 64 * 64;
-    const int64_t nkb = ld / 64;
+    const int64_t bytes_per_point = (int64_t)planes * (width + height) * 2 * 2;
+    const int64_t budget = ctx->factor_budget_mb << 20;
+    int64_t chunk = budget / bytes_per_point / 32 * 32;
+    if (chunk < 32) chunk = 32;
+    if (chunk >= n) chunk = n;
+    const int64_t ld_max = (2 * chunk + 63) / 64 * 64;
+    const int64_t nkb_max = ld_max / 64;
     GemmPlan plan;
     plan.mode = mode;
     plan.bn = ctx->gemm_bn > 0 ? ctx->gemm_bn
                                : (ctx->form == CGH_FORM_AUTO ? tune_choose_bn(ctx, width, height, form)
                                                              : choose_gemm_bn(width));
-    if (plan.bn != 128 && plan.bn != 192 && plan.bn != 240 && plan.bn != 256) return CGH_ENOTSUP;
+    if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
     plan.ctas = gemm_max_ctas(ctx->num_sms);
     plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
+    plan.accumulate = false;
     const int64_t tiles = (int64_t)((height + 127) / 128) * ((width + plan.bn - 1) / plan.bn);
-    plan.splits = ctx->gemm_splitk > 0 ? ctx->gemm_splitk : choose_gemm_splits(tiles, nkb, plan.ctas);
-    if (plan.splits > nkb) plan.splits = (int)nkb;
+    plan.splits = ctx->gemm_splitk > 0 ? ctx->gemm_splitk : choose_gemm_splits(tiles, nkb_max, plan.ctas);
+    // every chunk must write every partial plane: no more splits than the last chunk has k-blocks
+    const int64_t last = n - (n - 1) / chunk * chunk;
+    const int64_t nkb_last = (2 * last + 63) / 64;
+    if (plan.splits > nkb_last) plan.splits = (int)nkb_last;
     const int64_t plane = (int64_t)width * height;
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
     const size_t amax_bytes = 256;
-    const size_t p_bytes = align_up((size_t)planes * height * ld * 2, 256);
-    const size_t q_bytes = align_up((size_t)planes * width * ld * 2, 256);
+    const size_t p_bytes = align_up((size_t)planes * height * ld_max * 2, 256);
+    const size_t q_bytes = align_up((size_t)planes * width * ld_max * 2, 256);
     const size_t part_bytes = plan.splits > 1 ? (size_t)plan.splits * plane * sizeof(float) : 0;
     int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes + part_bytes);
     if (rc) return rc;
@@ -110,18 +122,25 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
                                ctx->stream);
     }
     if (e != cudaSuccess) return cuda_status(e);
-    {
-        ProfileScope ps(ctx, "factors", 1);
-        e = launch_factors(mode, geo, aux, (int)n, height, width, P, Q, ld, amax, ctx->stream);
-    }
-    if (e != cudaSuccess) return cuda_status(e);
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
-    {
-        ProfileScope ps(ctx, "gemm_tcgen05", 1);
-        e = launch_gemm(plan, P, Q, height, width, ld, plan.splits > 1 ? parts : d_out, plane, amax, ctx->d_status,
-                        tmo, ctx->stream);
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t nc = n - c0 < chunk ? n - c0 : chunk;
+        const int64_t ld = (2 * nc + 63) / 64 * 64;
+        {
+            ProfileScope ps(ctx, "factors", 1);
+            e = launch_factors(mode, geo + c0, aux + c0, (int)nc, height, width, P, Q, ld, amax, ctx->stream);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        GemmPlan pc = plan;
+        pc.accumulate = c0 > 0;
+        {
+            ProfileScope ps(ctx, "gemm_tcgen05", 1);
+            e = launch_gemm(pc, P, Q, height, width, ld, plan.splits > 1 ? parts : d_out, plane, amax, ctx->d_status,
+                            tmo, ctx->stream);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
     }
-    if (e != cudaSuccess || plan.splits == 1) return cuda_status(e);
+    if (plan.splits == 1) return CGH_OK;
     ProfileScope ps(ctx, "reduce_slices", 1);
     return cuda_status(launch_reduce_slices(parts, plan.splits, plane, plane, d_out, ctx->stream));
 }
@@ -275,6 +294,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_TEST_DROP_TILE:
         if (value < -1 || value > 0x7fffffff) return CGH_EINVAL;
         ctx->drop_tile = (int)value;
+        return CGH_OK;
+    case CGH_OPT_FACTOR_BUDGET_MB:
+        if (value < 1 || value > (1 << 22)) return CGH_EINVAL;
+        ctx->factor_budget_mb = value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

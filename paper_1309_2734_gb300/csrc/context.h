@@ -35,6 +35,7 @@ struct cgh_ctx {
     int gemm_bn = 0;
     int gemm_chunk = 0;
     int drop_tile = -1;       // CGH_OPT_TEST_DROP_TILE
+    int64_t factor_budget_mb = 2048;   // CGH_OPT_FACTOR_BUDGET_MB
     int64_t tol_e9 = 10000;   // 1e-5
     int *d_status = nullptr;  // [0] status bits, [1..2] quantiser scratch, [3] spare
     void *ws = nullptr;       // grow-only workspace

@@ -29,7 +29,10 @@
 //    FFMA returns exactly RN((f - 1.5) K1): the argument grid is symmetric
 //    about zero and the odd error cancels.  K1 is 1.04e-7 above 2 pi (a
 //    zero-mean phase-scale error below 3.3e-7 rad).  The corner-phase bias
-//    also rounds the 23-bit truncation to nearest.
+//    also rounds the 23-bit truncation to nearest.  (Moving an eighth of the
+//    terms to a sine polynomial on the FMA pipe was measured: the MUFU pipe
+//    went from 90 % to 74 % busy but issue and ALU pressure grew and the kernel
+//    got 6 % slower, so every term uses the MUFU.)
 //  - accurate form: the turn, read as a signed 32-bit integer, converts to
 //    t in [-1/2, 1/2) and cos(2 pi t) is a degree-12 even polynomial
 //    (cospoly.h), all on the FMA pipe.
@@ -52,10 +55,13 @@ constexpr float kK0 = 9.42477893829345703f;   // exactly 1.5 * kK1
 // 2^30: a quarter turn; 2^8 rounds the 23-bit truncation to nearest
 constexpr uint32_t kSfuBias = (1u << 30) + 256u;
 
-template <bool SFU>
+// Evaluation modes of one (point, pixel) term.
+enum { kEvalSfu = 0, kEvalAccurate = 1 };
+
+template <int MODE>
 __device__ __forceinline__ float cos_term(uint32_t g)
 {
-    if constexpr (SFU) {
+    if constexpr (MODE == kEvalSfu) {
         const float f = __uint_as_float(__funnelshift_r(g, 0x7fu, 9));   // 1 + top23(g) 2^-23
         return __sinf(fmaf(f, kK1, -kK0));                              // = -cos(2 pi t)
     } else {
@@ -69,6 +75,41 @@ __device__ __forceinline__ float cos_term(uint32_t g)
         c = fmaf(c, u, CGH_COSPOLY_1);
         c = fmaf(c, u, CGH_COSPOLY_0);
         return c;                                                        // = cos(2 pi t)
+    }
+}
+
+// Adds one point's terms to a thread's TL x TR block (corner m0, n0).
+template <int TL, int TR, int MODE>
+__device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0, int n0, float (&part)[TR][TL])
+{
+    constexpr bool kSfuSign = MODE != kEvalAccurate;
+    const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
+    const uint32_t dx = (uint32_t)(m0 - q.x);
+    const uint32_t dy = (uint32_t)(n0 - q.y);
+    const uint32_t r2 = dx * dx + dy * dy;          // < 2^31, exact
+    const uint32_t r2x = r2 + 2u * dx + 1u;         // (dx+1)^2 + dy^2
+    const uint32_t r2y = r2 + 2u * dy + 1u;         // dx^2 + (dy+1)^2
+    const uint32_t g0 = chi * r2 + __umulhi(clo, r2);
+    uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
+    uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
+    const uint32_t D = w.x;
+    const float a = kSfuSign ? -__uint_as_float(w.y) : __uint_as_float(w.y);
+    uint32_t g[TL];
+    g[0] = g0 + (kSfuSign ? kSfuBias : 0u);
+#pragma unroll
+    for (int i = 1; i < TL; ++i) {
+        g[i] = g[i - 1] + d;
+        d += D;
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+#pragma unroll
+        for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<MODE>(g[i]), part[r][i]);
+        if (r + 1 < TR) {
+#pragma unroll
+            for (int i = 0; i < TL; ++i) g[i] += e;
+            e += D;
+        }
     }
 }
 
@@ -135,38 +176,12 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
 
         const int4 *sg = s_geo[st];
         const uint2 *sa = s_aux[st];
+        if constexpr (SFU) {
 #pragma unroll 1
-        for (int p = 0; p < T; ++p) {
-            const int4 q = sg[p];
-            const uint2 w = sa[p];
-            const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
-            const uint32_t dx = (uint32_t)(m0 - q.x);
-            const uint32_t dy = (uint32_t)(n0 - q.y);
-            const uint32_t r2 = dx * dx + dy * dy;          // < 2^31, exact
-            const uint32_t r2x = r2 + 2u * dx + 1u;         // (dx+1)^2 + dy^2
-            const uint32_t r2y = r2 + 2u * dy + 1u;         // dx^2 + (dy+1)^2
-            const uint32_t g0 = chi * r2 + __umulhi(clo, r2);
-            uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
-            uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
-            const uint32_t D = w.x;
-            const float a = SFU ? -__uint_as_float(w.y) : __uint_as_float(w.y);
-            uint32_t g[TL];
-            g[0] = g0 + (SFU ? kSfuBias : 0u);
-#pragma unroll
-            for (int i = 1; i < TL; ++i) {
-                g[i] = g[i - 1] + d;
-                d += D;
-            }
-#pragma unroll
-            for (int r = 0; r < TR; ++r) {
-#pragma unroll
-                for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<SFU>(g[i]), part[r][i]);
-                if (r + 1 < TR) {
-#pragma unroll
-                    for (int i = 0; i < TL; ++i) g[i] += e;
-                    e += D;
-                }
-            }
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalSfu>(sg[p], sa[p], m0, n0, part);
+        } else {
+#pragma unroll 1
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate>(sg[p], sa[p], m0, n0, part);
         }
 #pragma unroll
         for (int r = 0; r < TR; ++r)

@@ -12,9 +12,12 @@
 // fixed-point constant C_j (prep.cu), the turn is the top 32 bits of
 // C_j d^2 mod 2^64, d the integer distance along one axis (|d| < 2^15, so
 // d^2 < 2^30).  The signed 32-bit turn converts to t in [-1/2, 1/2) (error
-// <= 2^-26 turn) and sincospif(2t) gives the pair to single precision; the
-// pair is rounded to FP16 or BF16, or split into hi = fp16(v) and
-// lo = fp16(v - hi).  No FP64 is needed on the GPU.
+// <= 2^-26 turn), and the hardware sine and cosine (MUFU, |2 pi t| <= pi,
+// absolute error below 4e-7) give the pair, which is rounded to FP16 or BF16,
+// or split into hi = fp16(v) and lo = fp16(v - hi).  That error is far below
+// FP16/BF16 rounding and, in the split form, contributes ~1e-7 to the NRMS
+// (the accumulation dominates).  The kernel is issue-bound; the MUFU leaves
+// the issue slots to the integer phase work.  No FP64 is needed on the GPU.
 //
 // One thread owns 4 consecutive points (8 columns, one 16-byte store per row
 // and plane) and walks a band of rows, so the point constants are read once
@@ -30,6 +33,12 @@ namespace {
 
 constexpr int kRowsPerBlock = 32;
 constexpr int kFactorThreads = 128;
+
+// (cos 2 pi t, sin 2 pi t) for t in [-1/2, 1/2), hardware sine and cosine
+__device__ __forceinline__ void sincos_turn(float t, float &s, float &c)
+{
+    __sincosf(t * 6.28318530717958648f, &s, &c);
+}
 
 __device__ __forceinline__ uint32_t pack(float lo_col, float hi_col, int mode, bool second)
 {
@@ -91,7 +100,7 @@ __global__ void __launch_bounds__(kFactorThreads)
                 const uint32_t d2 = d * d;                                   // < 2^30
                 const uint32_t g = chi[q] * d2 + __umulhi(clo[q], d2);       // turn, 2^-32 units
                 const float t = (float)(int)g * 2.3283064365386963e-10f;     // [-1/2, 1/2)
-                sincospif(2.0f * t, &s, &c);
+                sincos_turn(t, s, c);
                 if (!is_p) {
                     c = a[q] * c;
                     s = -a[q] * s;

@@ -72,6 +72,7 @@ struct UnitInfo {
     int tm, tn, kb0, kb1, bn, passes, kc, height, width;
     uint32_t idesc;
     bool vec;
+    bool accumulate;             // add to the output already there (later point chunks)
 };
 
 // One hologram: everything in the (grid-constant) kernel parameters.
@@ -83,6 +84,7 @@ struct alignas(64) SingleUnits {
     int height, width, nkb, splits, tiles_m, tiles_n, kc, passes, bn;
     uint32_t idesc;
     int vec;
+    int accumulate;
 
     __device__ int begin() const { return blockIdx.x; }
     __device__ int end() const { return tiles_m * tiles_n * splits; }
@@ -109,6 +111,7 @@ struct alignas(64) SingleUnits {
         x.width = width;
         x.idesc = idesc;
         x.vec = vec != 0;
+        x.accumulate = accumulate != 0;
         return x;
     }
 };
@@ -144,6 +147,7 @@ struct BatchUnits {
         x.width = J.width;
         x.idesc = J.idesc;
         x.vec = J.vec != 0;
+        x.accumulate = false;
         return x;
     }
 };
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int c = 0; c < nch; ++c, ++ch) {
                 // the first chunk stores, later chunks add (FP32, fixed order): each TMEM
                 // accumulation chain stays kc k-blocks long
-                const bool first = c == 0;
+                const bool first = c == 0 && !x.accumulate;
                 const int b = (int)(ch & 1u);
                 const uint32_t uph = (ch >> 1) & 1u;
                 if (!mbar_wait(&tfull[b], uph, timeout_ns)) {
@@ -303,33 +307,55 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * C::kAccStride);
 #pragma unroll 1
-                for (int cc = 0; cc < x.bn; cc += 16) {
-                    uint32_t r[16];
-                    tmem_ld16(taddr + (uint32_t)cc, r);
+                for (int cc = 0; cc < x.bn; cc += 64) {
+                    // 64 columns per round (four groups of 16): the previous partial sums
+                    // (if any) are loaded first, all at once, so the global-memory latency is
+                    // paid once per 64 columns and overlaps the tensor-memory reads
+                    const int ncol = min(64, x.bn - cc);   // a multiple of 16
+                    const int col0 = x.tn * x.bn + cc;
+                    const bool in_row = row < x.height;
+                    bool gvec[4];
+#pragma unroll
+                    for (int gq = 0; gq < 4; ++gq)
+                        gvec[gq] = x.vec && in_row && gq * 16 < ncol && col0 + gq * 16 + 16 <= x.width;
+                    float4 old[16];
+#pragma unroll
+                    for (int gq = 0; gq < 4; ++gq)
+                        if (!first && gvec[gq]) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                old[4 * gq + i] = reinterpret_cast<const float4 *>(dst + col0 + 16 * gq)[i];
+                        }
+                    uint32_t r[4][16];
+                    tmem_ld16(taddr + (uint32_t)cc, r[0]);
+                    if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
+                    if (ncol > 32) tmem_ld16(taddr + (uint32_t)(cc + 32), r[2]);
+                    if (ncol > 48) tmem_ld16(taddr + (uint32_t)(cc + 48), r[3]);
                     tmem_ld_wait();
-                    if (row < x.height) {
-                        const int col0 = x.tn * x.bn + cc;
+                    if (!in_row) continue;
+#pragma unroll
+                    for (int gq = 0; gq < 4; ++gq) {
+                        if (gq * 16 >= ncol) continue;
                         float v[16];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = empty_range ? 0.0f : __uint_as_float(r[i]) * unscale;
-                        if (x.vec && col0 + 16 <= x.width) {
+                        for (int i = 0; i < 16; ++i) v[i] = empty_range ? 0.0f : __uint_as_float(r[gq][i]) * unscale;
+                        float *d16 = dst + col0 + 16 * gq;
+                        if (gvec[gq]) {
 #pragma unroll
-                            for (int i = 0; i < 16; i += 4) {
-                                float4 *p4 = reinterpret_cast<float4 *>(dst + col0 + i);
-                                float4 w = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                            for (int i = 0; i < 4; ++i) {
+                                float4 w = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                                 if (!first) {
-                                    const float4 o = *p4;
-                                    w.x += o.x;
-                                    w.y += o.y;
-                                    w.z += o.z;
-                                    w.w += o.w;
+                                    w.x += old[4 * gq + i].x;
+                                    w.y += old[4 * gq + i].y;
+                                    w.z += old[4 * gq + i].z;
+                                    w.w += old[4 * gq + i].w;
                                 }
-                                *p4 = w;
+                                reinterpret_cast<float4 *>(d16)[i] = w;
                             }
                         } else {
 #pragma unroll
                             for (int i = 0; i < 16; ++i)
-                                if (col0 + i < x.width) dst[col0 + i] = first ? v[i] : dst[col0 + i] + v[i];
+                                if (col0 + 16 * gq + i < x.width) d16[i] = first ? v[i] : d16[i] + v[i];
                         }
                     }
                 }
@@ -445,6 +471,7 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
     u.bn = bn;
     u.idesc = umma_idesc_f16(bf16, kBM, bn);
     u.vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    u.accumulate = plan.accumulate ? 1 : 0;
     const int units = u.tiles_m * u.tiles_n * u.splits;
     const int ctas = plan.ctas < units ? plan.ctas : units;
     switch (bn) {

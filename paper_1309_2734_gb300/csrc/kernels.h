@@ -54,6 +54,7 @@ struct GemmPlan {
     int splits;        // K splits; > 1 writes partial planes
     int ctas;          // persistent CTAs
     int chunk_kb;      // k-blocks (of 64) per TMEM accumulation chain; 0 = whole split
+    bool accumulate;   // add to the output (or partial planes) instead of overwriting
 };
 int gemm_max_ctas(int num_sms);
 bool gemm_bn_supported(int bn);
