@@ -39,10 +39,20 @@ MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
 # DRAM bytes per launch of the dominant kernel from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # taken on; a changed source reports null until it is profiled again.
-NCU_TRAFFIC = {
-    # profiles/direct_sfu-1920x1080-n10000.md: 0.265 MB read + 21.99 MB written per launch
-    "direct_sfu": {"sha1": "8c2e19d767a30cb9e62e7a3699111372619139e0", "bytes_per_launch": 22255616},
-}
+NCU_TRAFFIC = [
+    # profiles/gemm_f16-1920x1080-n50000.md: 600.71 MB read + 4.15 MB written per launch
+    {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000", "src": "gemm.cu",
+     "sha1": "2e153cd338946ad225a492ce0f2f5194e2532935", "bytes_per_launch": 604860160},
+]
+
+
+def ncu_traffic(kernel, form, workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged since."""
+    for t in NCU_TRAFFIC:
+        if (t["kernel"], t["form"], t["workload"]) == (kernel, form, workload):
+            src = os.path.join(ROOT, "paper_1309_2734_gb300", "csrc", t["src"])
+            return t["bytes_per_launch"] if _sha1(src) == t["sha1"] else None
+    return None
 
 
 def _sha1(path):
@@ -331,10 +341,43 @@ def run_ours(args):
                 rec["roofline"] = {"kernel": "gemm_tcgen05", "bound": "tensor", "achieved": tflops,
                                    "peak": peak_tc, "unit": "TFLOP/s", "frac": tflops / peak_tc,
                                    "flops_per_eval": 4 * passes,
+                                   "traffic": ncu_traffic("gemm_tcgen05", extra, wc.name),
                                    "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
             key = f"{extra}@{wc.name}"
             forms[key] = rec
             samples[key] = (wc, o.cpu().numpy())
+    # the paper's own timed workload (Tables 3-4): phase-only CGH of 1920x1080 holograms with
+    # 10^3, 10^4 and 10^5 points (complex wave + kinoform quantisation), beside the Tesla K20's
+    # published times for the direct calculation (context only: other hardware, fast math)
+    paper = {}
+    if not args.no_paper_workload:
+        k20 = {1000: 0.016, 10000: 0.168, 100000: 1.68}
+        for n_pts, t_k20 in k20.items():
+            pc = workloads.random_cloud(13092734100 + n_pts, 1920, 1080, n_pts)
+            px, pa = torch.from_numpy(pc.xyz).cuda(), torch.from_numpy(pc.amp).cuda()
+            wbuf = torch.empty((2, 1080, 1920), dtype=torch.float32, device="cuda")
+            kbuf = torch.empty((1080, 1920), dtype=torch.uint8, device="cuda")
+            entry = {"k20_direct_s": t_k20}
+            with Hologram(1920, 1080, pc.pitch_m, pc.lambda_m, stream=stream) as hp:
+                for pform in ("direct_sfu", "gemm_f16", "gemm_split16"):
+                    hp.set_form(pform)
+                    hp.wave(px, pa, wbuf)
+                    hp.kinoform8(wbuf, kbuf)
+                    hp.sync()
+                    reps = 3 if n_pts <= 10000 or pform != "direct_sfu" else 1
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(reps):
+                        hp.wave(px, pa, wbuf)
+                        hp.kinoform8(wbuf, kbuf)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    hp.sync()
+                    sec = e0.elapsed_time(e1) / reps * 1e-3
+                    entry[pform] = {"s_per_hologram": sec, "gevals_per_s": pc.evals / sec / 1e9,
+                                    "speedup_vs_k20": t_k20 / sec}
+            paper[f"n{n_pts}"] = entry
+
     h.set_form(args.form)
     h.point_cloud(xyz, amp, out)
     h.sync()
@@ -371,9 +414,7 @@ def run_ours(args):
         roof = {"bound": "alu", "unit": "Gcos/s (MUFU)",
                 "peak_basis": f"{MUFU_PER_SM_PER_CLK} MUFU cos/clk/SM x {props.multi_processor_count} SMs x "
                               f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)"}
-    kernel_src = os.path.join(ROOT, "paper_1309_2734_gb300", "csrc", src)
-    traffic = NCU_TRAFFIC.get(dom, {})
-    traffic = traffic.get("bytes_per_launch") if traffic.get("sha1") == _sha1(kernel_src) else None
+    traffic = ncu_traffic(dom, args.form, cloud.name)
 
     cpu, nrms = (None, None)
     if not args.no_cpu_baseline:
@@ -408,6 +449,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(W * H * 4),
                 "path": "cgh_point_cloud_host (pinned host buffers, copies and sync inside)"},
         "forms": forms,
+        "paper_kinoform_1920x1080": paper,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -428,6 +470,8 @@ def main():
     ap.add_argument("--compare", nargs="*",
                     default=["direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-paper-workload", action="store_true",
+                    help="skip the phase-only 1920x1080 workload of the paper's Tables 3-4")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

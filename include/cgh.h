@@ -75,7 +75,8 @@ enum {
 
 /* 8-bit quantisation rules (cgh_quantize8). */
 enum {
-    CGH_Q_AMPLITUDE_MINMAX = 0  /* floor((v - min) * s), s = 255 / (max - min) rounded up */
+    CGH_Q_AMPLITUDE_MINMAX = 0, /* floor((v - min) * s), s = 255 / (max - min) rounded up */
+    CGH_Q_PHASE = 1             /* kinoform: floor(255/(2 pi) * arg), arg of (re, im) in [0, 2 pi) */
 };
 
 /* Options (cgh_set_option). */
@@ -148,6 +149,19 @@ int cgh_point_cloud_host(cgh_ctx *ctx, const float *h_xyz, const float *h_amp, i
 int cgh_factors(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points,
                 int dtype_form, void *d_p, void *d_q, int64_t ld);
 
+/*
+ * The complex object wave of one point cloud (Eq. 2 with the same restriction
+ * as above), O(m, n) = sum_j A_j exp(i 2 pi c_j r^2): its real part is the
+ * amplitude hologram of cgh_point_cloud and its argument gives the phase-only
+ * hologram (kinoform) of Eq. 3, the workload the paper times (Section 5).
+ *   d_out : float32 [2][height][width]: the real plane, then the imaginary plane.
+ * Forms: CGH_DIRECT_SFU (both parts in one direct pass, two hardware sines per
+ * term) and the GEMM forms (Re O = P Q^T and Im O = P Q'^T, with
+ * Q'[m][2j] = A_j sin alpha, Q'[m][2j+1] = A_j cos alpha).  CGH_FORM_AUTO
+ * picks among those; CGH_DIRECT_ACCURATE returns CGH_ENOTSUP.
+ */
+int cgh_wave(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, float *d_out);
+
 /* One instance of a batch: a whole hologram problem. */
 typedef struct {
     int width, height;
@@ -183,7 +197,12 @@ int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
 int cgh_autotune(cgh_ctx *ctx, int force);
 
 /*
- * 8-bit quantisation of a float32 field of n values (mode CGH_Q_AMPLITUDE_MINMAX):
+ * 8-bit quantisation.  CGH_Q_PHASE: d_field holds a complex field as two
+ * planes of n floats (real, then imaginary; the layout of cgh_wave); each
+ * output is floor(fl(psi * fl(255/(2 pi)))) clamped to [0, 255], with
+ * psi = atan2f(im, re) plus 2 pi when negative, as the listings of
+ * Section 4.1 quantise their kinoforms.
+ * CGH_Q_AMPLITUDE_MINMAX, a float32 field of n values:
  *   lo = min, hi = max over the field (NaN ignored); if !(hi > lo) all 0;
  *   s  = the smallest float >= 255 / ((double)hi - (double)lo) (at most FLT_MAX);
  *   q  = floor(fl(fl(v - lo) * s)), each operation rounded to nearest, no FMA;

@@ -15,6 +15,7 @@ wraps it with ctypes.  Every function cites the passage it follows:
 * ``factors``: the separable factor matrices P, Q with I = P Q^T.
 * ``quantize8``: the min/max 8-bit quantiser (the listings of Section 4.1
   quantise a phase with 255/(2 pi); this is the amplitude counterpart).
+* ``kinoform8``: that phase rule for the kinoform of Eq. 3.
 * ``recurrence_phases``: Eqs. 6-8 (Section 2.2) iterated in exact rationals.
 """
 from __future__ import annotations
@@ -69,6 +70,7 @@ def _load():
             lib.oracle_factors.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            _F32P, _F32P, ctypes.c_int64, _F64P, _F64P]
             lib.oracle_quantize8.argtypes = [_F32P, ctypes.c_int64, _U8P, _F32P]
+            lib.oracle_kinoform8.argtypes = [_F64P, _F64P, ctypes.c_int64, _U8P]
             _lib = lib
     return _lib
 
@@ -165,6 +167,18 @@ def quantize8(field32) -> tuple:
     if rc != 0:
         raise ValueError("oracle_quantize8 rejected its arguments")
     return out.reshape(f.shape), (float(lohi[0]), float(lohi[1]), float(lohi[2]))
+
+
+def kinoform8(wave_c) -> np.ndarray:
+    """Phase-only 8-bit hologram of a complex field (Eq. 3; floor(255 psi/(2 pi)), psi in [0, 2 pi))."""
+    w = np.asarray(wave_c)
+    re = np.ascontiguousarray(w.real, dtype=np.float64).reshape(-1)
+    im = np.ascontiguousarray(w.imag, dtype=np.float64).reshape(-1)
+    out = np.empty(re.shape[0], dtype=np.uint8)
+    rc = _load().oracle_kinoform8(_ptr(re, _F64P), _ptr(im, _F64P), re.shape[0], _ptr(out, _U8P))
+    if rc != 0:
+        raise ValueError("oracle_kinoform8 rejected its arguments")
+    return out.reshape(w.shape)
 
 
 def nrms(test, ref) -> float:

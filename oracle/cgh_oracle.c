@@ -237,3 +237,21 @@ int oracle_quantize8(const float *field, int64_t n, uint8_t *out, float *lohi)
     if (lohi) { lohi[0] = lo; lohi[1] = hi; lohi[2] = s; }
     return 0;
 }
+
+/*
+ * Kinoform (phase-only hologram) of a complex field, Eq. 3: the argument
+ * psi = atan2(im, re), taken in [0, 2 pi) by adding 2 pi to negative values as
+ * the listings of Section 4.1 do, stored as floor(255 psi / (2 pi)) (at most
+ * 255).  Computed in double from double inputs (the definition); NaN -> 0.
+ */
+int oracle_kinoform8(const double *re, const double *im, int64_t n, uint8_t *out)
+{
+    if (n < 0 || (n > 0 && (!re || !im || !out))) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        double psi = atan2(im[i], re[i]);
+        if (psi < 0.0) psi += TWO_PI;
+        double q = floor(255.0 * psi / TWO_PI);
+        out[i] = (q >= 255.0) ? (uint8_t)255 : ((q >= 0.0) ? (uint8_t)q : (uint8_t)0);
+    }
+    return 0;
+}

@@ -80,6 +80,33 @@ class Hologram:
                                         out.data_ptr()), "cgh_point_cloud")
         return out
 
+    def wave(self, xyz, amp, out=None):
+        """Complex object wave as a float32 [2][height][width] CUDA tensor (real, imaginary)."""
+        import torch
+        _need_cuda_tensor(xyz, "xyz", torch.float32)
+        _need_cuda_tensor(amp, "amp", torch.float32)
+        n = int(amp.numel())
+        if out is None:
+            out = torch.empty((2, self.height, self.width), dtype=torch.float32, device=self.device)
+        _need_cuda_tensor(out, "out", torch.float32)
+        if out.numel() != 2 * self.width * self.height:
+            raise ValueError("out must hold 2 * height * width floats")
+        _lib.check(_lib.cgh_wave(self.ctx, xyz.data_ptr() if n else 0, amp.data_ptr() if n else 0, n,
+                                 out.data_ptr()), "cgh_wave")
+        return out
+
+    def kinoform8(self, wave, out=None):
+        """Phase-only 8-bit hologram of a complex wave [2][...] (Eq. 3, the listings' 255/(2 pi) rule)."""
+        import torch
+        _need_cuda_tensor(wave, "wave", torch.float32)
+        n = wave.numel() // 2
+        if out is None:
+            out = torch.empty(wave.shape[1:], dtype=torch.uint8, device=wave.device)
+        _need_cuda_tensor(out, "out", torch.uint8)
+        _lib.check(_lib.cgh_quantize8(self.ctx, wave.data_ptr(), n, _lib.CGH_Q_PHASE, out.data_ptr()),
+                   "cgh_quantize8")
+        return out
+
     def point_cloud_host(self, xyz_host, amp_host, out_host):
         """Same through host buffers (torch CPU tensors); copies inside, waits at the end."""
         import torch

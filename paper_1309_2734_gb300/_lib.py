@@ -21,6 +21,7 @@ CGH_FORM_AUTO, CGH_DIRECT_SFU, CGH_DIRECT_ACCURATE, CGH_GEMM_F16, CGH_GEMM_BF16,
 FORMS = {"auto": 0, "direct_sfu": 1, "direct_accurate": 2, "gemm_f16": 3, "gemm_bf16": 4, "gemm_split16": 5}
 # quantiser modes
 CGH_Q_AMPLITUDE_MINMAX = 0
+CGH_Q_PHASE = 1
 # options
 CGH_OPT_TIMEOUT_MS, CGH_OPT_POINT_SPLIT, CGH_OPT_GEMM_SPLITK, CGH_OPT_GEMM_BN, CGH_OPT_TOLERANCE_E9 = 1, 2, 3, 4, 5
 CGH_OPT_PROFILE = 6
@@ -31,7 +32,7 @@ CGH_OPT_FACTOR_BUDGET_MB = 9
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
            "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
-           "cgh_autotune")
+           "cgh_autotune", "cgh_wave")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_sync": ([vp], ci),
             "cgh_point_cloud_noalloc": ([ci, ci, cd, cd, vp, vp, i64, vp, vp], ci),
             "cgh_autotune": ([vp, ci], ci),
+            "cgh_wave": ([vp, vp, vp, i64, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -159,6 +161,10 @@ def cgh_profile_read(ctx: int, reset: bool = True) -> dict:
     n = ctypes.c_int(0)
     check(load().cgh_profile_read(ctx, buf, 64, ctypes.byref(n), 1 if reset else 0), "cgh_profile_read")
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def cgh_wave(ctx: int, d_xyz: int, d_amp: int, n_points: int, d_out: int) -> int:
+    return load().cgh_wave(ctx, d_xyz, d_amp, int(n_points), d_out)
 
 
 def cgh_autotune(ctx: int, force: bool = False) -> int:

@@ -145,6 +145,117 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     return cuda_status(launch_reduce_slices(parts, plan.splits, plane, plane, d_out, ctx->stream));
 }
 
+// The complex object wave: real plane at d_out, imaginary plane at d_out + W H.
+// Direct form: one pass accumulating both parts.  GEMM forms: per chunk of
+// points, Re = P Q^T and Im = P Q'^T (the same P), later chunks adding.
+int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int64_t n, float *d_out)
+{
+    const int width = ctx->width, height = ctx->height;
+    const int64_t plane = (int64_t)width * height;
+    const int64_t n_pad = padded_points(n);
+    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
+    const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
+    const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
+    cudaError_t e;
+    if (form == CGH_DIRECT_SFU) {
+        const DirectShape sh = direct_wave_shape();
+        const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
+        const int64_t n_ptiles = n_pad / kPointTile;
+        int split = ctx->point_split > 0 ? ctx->point_split : choose_point_split(tiles, n_ptiles, ctx->num_sms);
+        if (split > n_ptiles) split = (int)n_ptiles;
+        const size_t part_bytes = split > 1 ? (size_t)split * 2 * plane * sizeof(float) : 0;
+        int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + part_bytes);
+        if (rc) return rc;
+        char *base = static_cast<char *>(ctx->ws);
+        int4 *geo = reinterpret_cast<int4 *>(base);
+        uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
+        float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
+        {
+            ProfileScope ps(ctx, "prep_points", 1);
+            e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, ctx->pitch, ctx->lambda, geo, aux, ctx->d_status,
+                                   nullptr, ctx->stream);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        {
+            ProfileScope ps(ctx, "direct_wave", 1);
+            e = launch_direct_wave(geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out,
+                                   2 * plane, plane, ctx->d_status, tmo, ctx->stream);
+        }
+        if (e != cudaSuccess || split == 1) return cuda_status(e);
+        ProfileScope ps(ctx, "reduce_slices", 2);
+        e = launch_reduce_slices(parts, split, plane, 2 * plane, d_out, ctx->stream);
+        if (e == cudaSuccess) e = launch_reduce_slices(parts + plane, split, plane, 2 * plane, d_out + plane, ctx->stream);
+        return cuda_status(e);
+    }
+    if (form < CGH_GEMM_F16 || form > CGH_GEMM_SPLIT16) return CGH_ENOTSUP;
+    const int mode = factor_mode(form);
+    const int planes = mode == kFactorSplit16 ? 2 : 1;
+    const int64_t bytes_per_point = (int64_t)planes * (width + height) * 2 * 2;
+    int64_t chunk = (ctx->factor_budget_mb << 20) / bytes_per_point / 32 * 32;
+    if (chunk < 32) chunk = 32;
+    if (chunk >= n) chunk = n;
+    const int64_t ld_max = (2 * chunk + 63) / 64 * 64;
+    GemmPlan plan;
+    plan.mode = mode;
+    plan.bn = ctx->gemm_bn > 0 ? ctx->gemm_bn : choose_gemm_bn(width);
+    if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
+    plan.ctas = gemm_max_ctas(ctx->num_sms);
+    plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
+    plan.accumulate = false;
+    const int64_t tiles = (int64_t)((height + 127) / 128) * ((width + plan.bn - 1) / plan.bn);
+    plan.splits = ctx->gemm_splitk > 0 ? ctx->gemm_splitk : choose_gemm_splits(tiles, ld_max / 64, plan.ctas);
+    const int64_t last = n - (n - 1) / chunk * chunk;
+    if (plan.splits > (2 * last + 63) / 64) plan.splits = (int)((2 * last + 63) / 64);
+    const size_t amax_bytes = 256;
+    const size_t p_bytes = align_up((size_t)planes * height * ld_max * 2, 256);
+    const size_t q_bytes = align_up((size_t)planes * width * ld_max * 2, 256);
+    const size_t part_bytes = plan.splits > 1 ? (size_t)plan.splits * 2 * plane * sizeof(float) : 0;
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes + part_bytes);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->ws);
+    int4 *geo = reinterpret_cast<int4 *>(base);
+    uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
+    float *amax = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
+    void *P = base + geo_bytes + aux_bytes + amax_bytes;
+    void *Q = base + geo_bytes + aux_bytes + amax_bytes + p_bytes;
+    float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes);
+    e = cudaMemsetAsync(amax, 0, sizeof(float), ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    {
+        ProfileScope ps(ctx, "prep_points", 1);
+        e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, ctx->pitch, ctx->lambda, geo, aux, ctx->d_status,
+                               amax, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    float *re_out = plan.splits > 1 ? parts : d_out;
+    float *im_out = plan.splits > 1 ? parts + (int64_t)plan.splits * plane : d_out + plane;
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t nc = n - c0 < chunk ? n - c0 : chunk;
+        const int64_t ld = (2 * nc + 63) / 64 * 64;
+        GemmPlan pc = plan;
+        pc.accumulate = c0 > 0;
+        for (int part = 0; part < 2; ++part) {
+            {
+                ProfileScope ps(ctx, "factors", 1);
+                e = launch_factors(mode, geo + c0, aux + c0, (int)nc, height, width, P, Q, ld, amax, ctx->stream,
+                                   part == 1);
+            }
+            if (e != cudaSuccess) return cuda_status(e);
+            {
+                ProfileScope ps(ctx, "gemm_tcgen05", 1);
+                e = launch_gemm(pc, P, Q, height, width, ld, part == 0 ? re_out : im_out, plane, amax, ctx->d_status,
+                                tmo, ctx->stream);
+            }
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    if (plan.splits == 1) return CGH_OK;
+    ProfileScope ps(ctx, "reduce_slices", 2);
+    e = launch_reduce_slices(re_out, plan.splits, plane, plane, d_out, ctx->stream);
+    if (e == cudaSuccess) e = launch_reduce_slices(im_out, plan.splits, plane, plane, d_out + plane, ctx->stream);
+    return cuda_status(e);
+}
+
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n)
 {
     if (ctx->form != CGH_FORM_AUTO) return ctx->form;
@@ -395,10 +506,30 @@ int cgh_autotune(cgh_ctx *ctx, int force)
     return tune_calibrate(ctx, force != 0);
 }
 
+int cgh_wave(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, float *d_out)
+{
+    if (!ctx || !d_out || n_points < 0 || n_points > 0x7fffffffll) return CGH_EINVAL;
+    if (n_points > 0 && (!d_xyz || !d_amp)) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    const int64_t plane = (int64_t)ctx->width * ctx->height;
+    if (n_points == 0) return cuda_status(cudaMemsetAsync(d_out, 0, (size_t)2 * plane * sizeof(float), ctx->stream));
+    int form = resolve_form(ctx, ctx->width, ctx->height, n_points);
+    if (form == CGH_DIRECT_ACCURATE) {
+        if (ctx->form == CGH_DIRECT_ACCURATE) return CGH_ENOTSUP;
+        form = CGH_DIRECT_SFU;   // the automatic choice falls back to the other FP32 form
+    }
+    return run_wave(ctx, form, d_xyz, d_amp, n_points, d_out);
+}
+
 int cgh_quantize8(cgh_ctx *ctx, const float *d_field, int64_t n, int mode, uint8_t *d_out)
 {
-    if (!ctx || n < 0 || (n > 0 && (!d_field || !d_out)) || mode != CGH_Q_AMPLITUDE_MINMAX) return CGH_EINVAL;
+    if (!ctx || n < 0 || (n > 0 && (!d_field || !d_out))) return CGH_EINVAL;
+    if (mode != CGH_Q_AMPLITUDE_MINMAX && mode != CGH_Q_PHASE) return CGH_EINVAL;
     DeviceGuard g(ctx->device);
+    if (mode == CGH_Q_PHASE) {
+        ProfileScope ps(ctx, "kinoform8", 1);
+        return cuda_status(launch_kinoform8(d_field, d_field + n, n, d_out, ctx->stream));
+    }
     ProfileScope ps(ctx, "quantize8", 3);
     return cuda_status(
         launch_quantize8(d_field, n, d_out, reinterpret_cast<uint32_t *>(ctx->d_status + 1), ctx->stream));

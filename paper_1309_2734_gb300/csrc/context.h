@@ -174,5 +174,6 @@ int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double l
 int factor_mode(int form);
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n);
 int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
+int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int64_t n, float *d_out);
 
 }  // namespace cgh

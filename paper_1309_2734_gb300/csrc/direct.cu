@@ -78,6 +78,50 @@ __device__ __forceinline__ float cos_term(uint32_t g)
     }
 }
 
+// Adds one point's terms of the complex object wave (Eq. 2, restricted form) to
+// a thread's TL x TR block: Re += A cos(2 pi t) exactly as the SFU amplitude form,
+// Im += A sin(2 pi t) = A sin(v) with v = K1 (f2 - 1.5) from the turn advanced by a
+// half (f2 - 1 = t + 1/2), the same symmetric argument grid, so the MUFU's odd
+// error again averages out.
+template <int TL, int TR>
+__device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, int m0, int n0,
+                                                 float (&pre)[TR][TL], float (&pim)[TR][TL])
+{
+    const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
+    const uint32_t dx = (uint32_t)(m0 - q.x);
+    const uint32_t dy = (uint32_t)(n0 - q.y);
+    const uint32_t r2 = dx * dx + dy * dy;
+    const uint32_t r2x = r2 + 2u * dx + 1u;
+    const uint32_t r2y = r2 + 2u * dy + 1u;
+    const uint32_t g0 = chi * r2 + __umulhi(clo, r2);
+    uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
+    uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
+    const uint32_t D = w.x;
+    const float a = __uint_as_float(w.y);
+    uint32_t g[TL];
+    g[0] = g0 + kSfuBias;
+#pragma unroll
+    for (int i = 1; i < TL; ++i) {
+        g[i] = g[i - 1] + d;
+        d += D;
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+#pragma unroll
+        for (int i = 0; i < TL; ++i) {
+            const float f = __uint_as_float(__funnelshift_r(g[i], 0x7fu, 9));
+            const float f2 = __uint_as_float(__funnelshift_r(g[i] + (1u << 30), 0x7fu, 9));
+            pre[r][i] = fmaf(-a, __sinf(fmaf(f, kK1, -kK0)), pre[r][i]);   // A cos(2 pi t)
+            pim[r][i] = fmaf(a, __sinf(fmaf(f2, kK1, -kK0)), pim[r][i]);   // A sin(2 pi t)
+        }
+        if (r + 1 < TR) {
+#pragma unroll
+            for (int i = 0; i < TL; ++i) g[i] += e;
+            e += D;
+        }
+    }
+}
+
 // Adds one point's terms to a thread's TL x TR block (corner m0, n0).
 template <int TL, int TR, int MODE>
 __device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0, int n0, float (&part)[TR][TL])
@@ -116,12 +160,14 @@ __device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0,
 // One unit of work: point tiles [t_begin, t_end) of one cloud into one
 // CTA-sized pixel tile with corner (tile_m0, tile_n0).  kg counts the point
 // tiles this CTA consumed before (stage and mbarrier parity carry across units).
-template <int TL, int TR, int BX, int BY, bool SFU>
+// PLANES = 1: the amplitude hologram; PLANES = 2: the complex object wave, real
+// part at dst and imaginary part at dst + im_offset (SFU form only).
+template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1>
 __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const uint2 *__restrict__ aux,
                                             int t_begin, int t_end, int tile_m0, int tile_n0, int width,
                                             int height, float *__restrict__ dst, bool vec, int4 (*s_geo)[kPointTile],
                                             uint2 (*s_aux)[kPointTile], uint64_t *s_bar, uint32_t &kg, int *status,
-                                            unsigned long long timeout_ns, int drop = -1)
+                                            unsigned long long timeout_ns, int drop = -1, long long im_offset = 0)
 {
     constexpr int T = kPointTile;
     constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
@@ -144,11 +190,13 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         if (nt > 1) issue(1);
     }
 
-    float tot[TR][TL];
+    float tot[PLANES][TR][TL];
 #pragma unroll
-    for (int r = 0; r < TR; ++r)
+    for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-        for (int i = 0; i < TL; ++i) tot[r][i] = 0.0f;
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int i = 0; i < TL; ++i) tot[c][r][i] = 0.0f;
 
     bool ok = true;
     for (int k = 0; k < nt; ++k) {
@@ -168,25 +216,32 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
             ok = false;
             break;
         }
-        float part[TR][TL];
+        float part[PLANES][TR][TL];
 #pragma unroll
-        for (int r = 0; r < TR; ++r)
+        for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-            for (int i = 0; i < TL; ++i) part[r][i] = 0.0f;
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int i = 0; i < TL; ++i) part[c][r][i] = 0.0f;
 
         const int4 *sg = s_geo[st];
         const uint2 *sa = s_aux[st];
-        if constexpr (SFU) {
+        if constexpr (PLANES == 2) {
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalSfu>(sg[p], sa[p], m0, n0, part);
+            for (int p = 0; p < T; ++p) point_terms_wave<TL, TR>(sg[p], sa[p], m0, n0, part[0], part[PLANES - 1]);
+        } else if constexpr (SFU) {
+#pragma unroll 1
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalSfu>(sg[p], sa[p], m0, n0, part[0]);
         } else {
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate>(sg[p], sa[p], m0, n0, part);
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate>(sg[p], sa[p], m0, n0, part[0]);
         }
 #pragma unroll
-        for (int r = 0; r < TR; ++r)
+        for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-            for (int i = 0; i < TL; ++i) tot[r][i] += part[r][i];
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int i = 0; i < TL; ++i) tot[c][r][i] += part[c][r][i];
 
         __syncthreads();   // every thread is done with stage st
         if (tid == 0 && k + 2 < nt) issue(k + 2);
@@ -195,20 +250,23 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
     if (!ok) return false;
 
 #pragma unroll
-    for (int r = 0; r < TR; ++r) {
-        const int n = n0 + r;
-        if (n >= height || m0 >= width) continue;
-        float *row = dst + (long long)n * width + m0;
-        if (vec && m0 + TL <= width) {
+    for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-            for (int i = 0; i < TL; i += 4)
-                *reinterpret_cast<float4 *>(row + i) = make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
-        } else {
+        for (int r = 0; r < TR; ++r) {
+            const int n = n0 + r;
+            if (n >= height || m0 >= width) continue;
+            float *row = dst + (long long)c * im_offset + (long long)n * width + m0;
+            if (vec && m0 + TL <= width) {
 #pragma unroll
-            for (int i = 0; i < TL; ++i)
-                if (m0 + i < width) row[i] = tot[r][i];
+                for (int i = 0; i < TL; i += 4)
+                    *reinterpret_cast<float4 *>(row + i) =
+                        make_float4(tot[c][r][i], tot[c][r][i + 1], tot[c][r][i + 2], tot[c][r][i + 3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < TL; ++i)
+                    if (m0 + i < width) row[i] = tot[c][r][i];
+            }
         }
-    }
     return true;
 }
 
@@ -242,6 +300,29 @@ __global__ void __launch_bounds__(BX *BY, 2)
                                      (tile / tiles_x) * (BY * TR), width, height,
                                      out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg,
                                      status, timeout_ns, blockIdx.y == 0 ? drop_tile : -1);
+}
+
+// The complex object wave of one hologram: blockIdx.x = pixel tile, blockIdx.y =
+// point chunk; chunk s writes real and imaginary planes at out + s * slice_stride
+// and out + s * slice_stride + im_offset.
+template <int TL, int TR, int BX, int BY>
+__global__ void __launch_bounds__(BX *BY, 2)
+    direct_wave_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_ptiles, int width,
+                       int height, int tiles_x, int split, float *__restrict__ out, long long slice_stride,
+                       long long im_offset, bool vec, int *status, unsigned long long timeout_ns)
+{
+    __shared__ alignas(128) int4 s_geo[2][kPointTile];
+    __shared__ alignas(128) uint2 s_aux[2][kPointTile];
+    __shared__ alignas(8) uint64_t s_bar[2];
+    init_point_barriers<BX, BY>(s_bar);
+    const int tile = blockIdx.x;
+    const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
+    const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
+    uint32_t kg = 0;
+    direct_unit<TL, TR, BX, BY, true, 2>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
+                                         (tile / tiles_x) * (BY * TR), width, height,
+                                         out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg,
+                                         status, timeout_ns, -1, im_offset);
 }
 
 // A batch: every CTA walks its list of {job, pixel tile} units over all points of the job.
@@ -315,6 +396,37 @@ cudaError_t launch_direct_batch(bool sfu, const DirectJob *d_jobs, const int *d_
 int direct_ctas_per_sm()
 {
     return 2;
+}
+
+}  // namespace cgh
+
+namespace cgh {
+
+namespace {
+constexpr int kWaveTL = 8, kWaveTR = 2;   // two planes of accumulators: half the rows per thread
+}
+
+DirectShape direct_wave_shape()
+{
+    return DirectShape{kBX * kWaveTL, kBY * kWaveTR, kBX * kBY};
+}
+
+cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int width, int height, int split,
+                               float *out, int64_t slice_stride, int64_t im_offset, int *status,
+                               uint64_t timeout_ns, cudaStream_t s)
+{
+    const DirectShape sh = direct_wave_shape();
+    const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
+    const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
+    const int n_ptiles = n_pad / kPointTile;
+    if (split < 1) split = 1;
+    dim3 grid(tiles_x * tiles_y, split);
+    const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && (im_offset % 4 == 0) &&
+                     ((uintptr_t)out % 16 == 0);
+    direct_wave_kernel<kWaveTL, kWaveTR, kBX, kBY><<<grid, sh.threads, 0, s>>>(
+        geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, (long long)im_offset, vec,
+        status, timeout_ns);
+    return cudaGetLastError();
 }
 
 }  // namespace cgh

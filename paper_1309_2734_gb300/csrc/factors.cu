@@ -19,6 +19,11 @@
 // (the accumulation dominates).  The kernel is issue-bound; the MUFU leaves
 // the issue slots to the integer phase work.  No FP64 is needed on the GPU.
 //
+// For the imaginary part of the complex wave, sin(alpha + beta) =
+// sin(alpha) cos(beta) + cos(alpha) sin(beta), so Im O = P Q'^T with the same P
+// and Q'[m][2j] = s A_j sin alpha, Q'[m][2j+1] = s A_j cos alpha ("imag" launch,
+// Q' rows only).
+//
 // One thread owns 4 consecutive points (8 columns, one 16-byte store per row
 // and plane) and walks a band of rows, so the point constants are read once
 // per band; rows [0, height) are P's, rows [height, height + width) are Q's.
@@ -56,7 +61,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kFactorThreads)
     factors_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int slots,
                    int height, int width, uint16_t *__restrict__ P, uint16_t *__restrict__ Q, long long ld,
-                   long long plane_p, long long plane_q, const float *__restrict__ amp_max)
+                   long long plane_p, long long plane_q, const float *__restrict__ amp_max, int row_begin,
+                   bool imag)
 {
     const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (j0 >= slots) return;
@@ -87,8 +93,8 @@ __global__ void __launch_bounds__(kFactorThreads)
         }
     }
     const int rows = height + width;
-    const int r_end = min(rows, (int)(blockIdx.y + 1) * kRowsPerBlock);
-    for (int r = blockIdx.y * kRowsPerBlock; r < r_end; ++r) {
+    const int r_end = min(rows, row_begin + (int)(blockIdx.y + 1) * kRowsPerBlock);
+    for (int r = row_begin + blockIdx.y * kRowsPerBlock; r < r_end; ++r) {
         const bool is_p = r < height;
         const int line = is_p ? r : r - height;
         float v[8];
@@ -102,8 +108,9 @@ __global__ void __launch_bounds__(kFactorThreads)
                 const float t = (float)(int)g * 2.3283064365386963e-10f;     // [-1/2, 1/2)
                 sincos_turn(t, s, c);
                 if (!is_p) {
-                    c = a[q] * c;
-                    s = -a[q] * s;
+                    const float cc = c;
+                    c = imag ? a[q] * s : a[q] * c;
+                    s = imag ? a[q] * cc : -a[q] * s;
                 }
             }
             v[2 * q] = c;
@@ -124,11 +131,13 @@ __global__ void __launch_bounds__(kFactorThreads)
 }  // namespace
 
 cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_points, int height, int width,
-                           void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s)
+                           void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s, bool imag_q_only)
 {
     const int slots = (int)(ld / 2);
     const int threads_x = (slots + 3) / 4;
-    dim3 grid((threads_x + kFactorThreads - 1) / kFactorThreads, (height + width + kRowsPerBlock - 1) / kRowsPerBlock);
+    const int row_begin = imag_q_only ? height : 0;
+    const int rows = height + width - row_begin;
+    dim3 grid((threads_x + kFactorThreads - 1) / kFactorThreads, (rows + kRowsPerBlock - 1) / kRowsPerBlock);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     const long long plane_p = (long long)height * ld, plane_q = (long long)width * ld;
     auto *p = static_cast<uint16_t *>(P);
@@ -136,15 +145,17 @@ cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_po
     switch (mode) {
     case kFactorF16:
         factors_kernel<kFactorF16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p, q, ld,
-                                                                   plane_p, plane_q, amp_max);
+                                                                   plane_p, plane_q, amp_max, row_begin, imag_q_only);
         break;
     case kFactorBF16:
         factors_kernel<kFactorBF16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p, q,
-                                                                    ld, plane_p, plane_q, amp_max);
+                                                                    ld, plane_p, plane_q, amp_max, row_begin,
+                                                                    imag_q_only);
         break;
     default:
         factors_kernel<kFactorSplit16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p,
-                                                                       q, ld, plane_p, plane_q, amp_max);
+                                                                       q, ld, plane_p, plane_q, amp_max, row_begin,
+                                                                       imag_q_only);
         break;
     }
     return cudaGetLastError();

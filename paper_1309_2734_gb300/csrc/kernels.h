@@ -29,6 +29,13 @@ cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad
                           int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
                           cudaStream_t s, int drop_tile = -1);
 
+// Complex object wave (Eq. 2, restricted form), SFU form: real part at out,
+// imaginary part at out + im_offset; point chunk s at out + s * slice_stride.
+DirectShape direct_wave_shape();
+cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int width, int height, int split,
+                               float *out, int64_t slice_stride, int64_t im_offset, int *status,
+                               uint64_t timeout_ns, cudaStream_t s);
+
 // a7: one job (hologram) of a batched direct launch; units are {job, pixel tile}.
 struct DirectJob {
     const int4 *geo;
@@ -44,8 +51,10 @@ int direct_ctas_per_sm();
 // kFactorSplit16 the lo planes follow the hi planes (offset rows * ld).
 // amp_max (optional) scales Q by 1 / max|A|.
 enum { kFactorF16 = 0, kFactorBF16 = 1, kFactorSplit16 = 2 };
+// imag_q_only: write only Q' (the factor of the imaginary part) into Q.
 cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_points, int height, int width,
-                           void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s);
+                           void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s,
+                           bool imag_q_only = false);
 
 // a4: tcgen05 GEMM, out[n][m] (+)= sum_k P[n][k] Q[m][k] over K splits (gemm.cu).
 struct GemmPlan {
@@ -83,5 +92,8 @@ cudaError_t launch_reduce_slices(const float *parts, int slices, int64_t n, int6
 
 // a6: 8-bit min/max quantiser (quantize.cu). scratch holds 2 uint32.
 cudaError_t launch_quantize8(const float *field, int64_t n, uint8_t *out, uint32_t *scratch, cudaStream_t s);
+// Kinoform (phase-only hologram, Eq. 3) quantiser: 255/(2 pi) per radian of
+// atan2(im, re) taken in [0, 2 pi).
+cudaError_t launch_kinoform8(const float *re, const float *im, int64_t n, uint8_t *out, cudaStream_t s);
 
 }  // namespace cgh

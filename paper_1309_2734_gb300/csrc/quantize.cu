@@ -136,7 +136,30 @@ int quant_grid(long long work)
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+// Phase of the complex wave in [0, 2 pi) (Eq. 3; the listings add 2 pi to
+// negative phases), scaled by 255 / (2 pi) and floored, as the listings of
+// Section 4.1 store their phase-only holograms (clamped to 255: psi + 2 pi may
+// round up to 2 pi in single precision; NaN -> 0).
+__global__ void kinoform_kernel(const float *__restrict__ re, const float *__restrict__ im, long long n,
+                                uint8_t *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float psi = atan2f(im[i], re[i]);
+        if (psi < 0.0f) psi = __fadd_rn(psi, 6.28318530717958648f);
+        const float x = floorf(__fmul_rn(psi, 40.58451048843331f));   // 255 / (2 pi)
+        out[i] = (x >= 255.0f) ? (uint8_t)255 : ((x >= 0.0f) ? (uint8_t)x : (uint8_t)0);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_kinoform8(const float *re, const float *im, int64_t n, uint8_t *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    kinoform_kernel<<<quant_grid(n), 256, 0, s>>>(re, im, n, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_quantize8(const float *field, int64_t n, uint8_t *out, uint32_t *scratch, cudaStream_t s)
 {

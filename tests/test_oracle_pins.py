@@ -293,3 +293,23 @@ def test_quantize_properties_random():
     fn[5] = np.nan
     qn, _ = oracle.quantize8(fn)
     assert qn[5] == 0
+
+
+def test_kinoform_hand_cases():
+    """Eq. 3 with the listings' rule: floor(255 psi / 2 pi), psi in [0, 2 pi)."""
+    w = np.array([1 + 0j, 1j, -1 + 0j, -1j, 1 - 1e-9j, 1 + 1j, -1 - 1j, 0j, 2.5 + 0j])
+    q = oracle.kinoform8(w)
+    # psi: 0, pi/2, pi, 3pi/2, ~2pi, pi/4, 5pi/4, atan2(0,0)=0, 0
+    assert list(q) == [0, 63, 127, 191, 254, 31, 159, 0, 0]
+    # the phase of a single point's wave is its own Fresnel phase (Eq. 2)
+    xyz = np.array([[3, 2, 0.5]], np.float32)
+    amp = np.array([1.0], np.float32)
+    O = oracle.wave(8e-6, 532e-9, xyz, amp, 16, 8)
+    c = (8e-6) ** 2 / (2 * 532e-9 * float(np.float32(0.5)))
+    m, n = np.meshgrid(np.arange(16), np.arange(8))
+    t = c * ((m - 3.0) ** 2 + (n - 2.0) ** 2)
+    want = np.floor(255.0 * (t - np.floor(t)))
+    got = oracle.kinoform8(O).astype(np.float64)
+    frac = 255.0 * (t - np.floor(t))
+    safe = np.abs(frac - np.round(frac)) > 1e-6
+    assert np.array_equal(got[safe], want[safe])
