@@ -84,13 +84,18 @@ enum {
     CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side wait; host-side waits allow 2x + 1 s; default 5000 */
     CGH_OPT_POINT_SPLIT = 2,    /* direct form: point chunks reduced afterwards; 0 = automatic */
     CGH_OPT_GEMM_SPLITK = 3,    /* GEMM forms: K splits reduced afterwards; 0 = automatic */
-    CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width (16..256, multiple of 16); 0 = automatic */
+    CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width, one of 128, 192, 224, 240, 256; 0 = automatic */
     CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */
     CGH_OPT_PROFILE = 6,        /* 1: bracket every kernel launch with CUDA events (cgh_profile_read) */
     CGH_OPT_GEMM_CHUNK = 7,     /* GEMM forms: k-blocks of 64 per tensor-memory accumulation chain; 0 = default */
     CGH_OPT_TEST_DROP_TILE = 8, /* test hook, direct forms: never load point tile k (>= 0) of the first chunk, so the
                                    kernel's bounded wait runs out and cgh_sync returns CGH_ETIMEOUT; -1 = off */
-    CGH_OPT_FACTOR_BUDGET_MB = 9 /* GEMM forms: device memory for P and Q of one chunk of points; default 2048 */
+    CGH_OPT_FACTOR_BUDGET_MB = 9, /* GEMM forms: device memory for the factors of the points in flight; default 2048 */
+    CGH_OPT_GEMM_PIPELINE = 10, /* GEMM forms: point chunks (>= 8192 points each) whose factor generation overlaps
+                                   the previous chunk's GEMM on a second stream; default 1 = no overlap (on GB300
+                                   the overlap measured no faster at 1920x1080 with 5x10^4 points) */
+    CGH_OPT_GEMM_TRANSPOSE = 11 /* GEMM forms: 0 = automatic, 1 = 128-row tiles of P (hologram rows), 2 = 128-row
+                                   tiles of Q (hologram columns; the result is written back transposed) */
 };
 
 typedef struct cgh_ctx cgh_ctx;

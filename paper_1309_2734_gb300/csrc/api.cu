@@ -59,6 +59,8 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
 
 // k-blocks per TMEM accumulation chain of the split-FP16 form (3 passes each)
 constexpr int kSplit16ChunkKb = 8;
+// smallest point chunk worth a pipeline stage of its own
+constexpr int64_t kPipelineMinPoints = 8192;
 
 int factor_mode(int form)
 {
@@ -68,8 +70,13 @@ int factor_mode(int form)
 // GEMM form: prep, then per chunk of points the factors P and Q (scaled by
 // 1/max|A|) and the tcgen05 GEMM over K splits, later chunks adding to the
 // planes of the first; then the fixed-order split reduction when there is more
-// than one split.  Chunking bounds the factor workspace (CGH_OPT_FACTOR_BUDGET_MB):
-// 10^6 points of a 4096x4096 split-FP16 hologram would otherwise need 65 GB.
+// than one split.  Chunks bound the factor workspace (CGH_OPT_FACTOR_BUDGET_MB:
+// 10^6 points of a 4096x4096 split-FP16 hologram would otherwise need 65 GB)
+// and can pipeline the two halves of the form: with CGH_OPT_GEMM_PIPELINE > 1
+// the factors of chunk c + 1 are generated on a second stream (double-buffered)
+// while the tensor cores run the GEMM of chunk c.  (Measured on GB300 at
+// 1920x1080 with 5x10^4 points: 0.428 ms without, 0.428-0.46 ms with 2-4
+// stages, so it is off by default.)
 int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double lambda, const float *d_xyz,
              const float *d_amp, int64_t n, float *d_out)
 {
@@ -77,43 +84,50 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     const int planes = mode == kFactorSplit16 ? 2 : 1;
     const int64_t n_pad = padded_points(n);
     const int64_t bytes_per_point = (int64_t)planes * (width + height) * 2 * 2;
-    const int64_t budget = ctx->factor_budget_mb << 20;
+    const int depth = ctx->gemm_pipeline;
+    const int64_t budget = (ctx->factor_budget_mb << 20) / (depth > 1 ? 2 : 1);   // per factor buffer
     int64_t chunk = budget / bytes_per_point / 32 * 32;
     if (chunk < 32) chunk = 32;
+    if (depth > 1 && n >= (int64_t)depth * kPipelineMinPoints) {
+        const int64_t even = ((n + depth - 1) / depth + 31) / 32 * 32;
+        if (even < chunk) chunk = even;
+    }
     if (chunk >= n) chunk = n;
+    const int64_t n_chunks = (n + chunk - 1) / chunk;
     const int64_t ld_max = (2 * chunk + 63) / 64 * 64;
     const int64_t nkb_max = ld_max / 64;
     GemmPlan plan;
     plan.mode = mode;
-    plan.bn = ctx->gemm_bn > 0 ? ctx->gemm_bn
-                               : (ctx->form == CGH_FORM_AUTO ? tune_choose_bn(ctx, width, height, form)
-                                                             : choose_gemm_bn(width));
-    if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
     plan.ctas = gemm_max_ctas(ctx->num_sms);
+    const GemmLayout lay = choose_gemm_layout(width, height, nkb_max, plan.ctas, ctx->gemm_bn, ctx->gemm_splitk,
+                                              ctx->gemm_trans);
+    plan.bn = lay.bn;
+    plan.splits = lay.splits;
+    plan.trans = lay.trans;
+    if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
     plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
     plan.accumulate = false;
-    const int64_t tiles = (int64_t)((height + 127) / 128) * ((width + plan.bn - 1) / plan.bn);
-    plan.splits = ctx->gemm_splitk > 0 ? ctx->gemm_splitk : choose_gemm_splits(tiles, nkb_max, plan.ctas);
     // every chunk must write every partial plane: no more splits than the last chunk has k-blocks
-    const int64_t last = n - (n - 1) / chunk * chunk;
+    const int64_t last = n - (n_chunks - 1) * chunk;
     const int64_t nkb_last = (2 * last + 63) / 64;
     if (plan.splits > nkb_last) plan.splits = (int)nkb_last;
     const int64_t plane = (int64_t)width * height;
+    const int nbuf = n_chunks > 1 ? 2 : 1;
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
     const size_t amax_bytes = 256;
     const size_t p_bytes = align_up((size_t)planes * height * ld_max * 2, 256);
     const size_t q_bytes = align_up((size_t)planes * width * ld_max * 2, 256);
     const size_t part_bytes = plan.splits > 1 ? (size_t)plan.splits * plane * sizeof(float) : 0;
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes + part_bytes);
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes,
+                    geo_bytes + aux_bytes + amax_bytes + nbuf * (p_bytes + q_bytes) + part_bytes);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->ws);
     int4 *geo = reinterpret_cast<int4 *>(base);
     uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
     float *amax = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
-    void *P = base + geo_bytes + aux_bytes + amax_bytes;
-    void *Q = base + geo_bytes + aux_bytes + amax_bytes + p_bytes;
-    float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes);
+    char *fac = base + geo_bytes + aux_bytes + amax_bytes;
+    float *parts = reinterpret_cast<float *>(fac + nbuf * (p_bytes + q_bytes));
     cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), ctx->stream);
     if (e != cudaSuccess) return cuda_status(e);
     {
@@ -123,22 +137,49 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     }
     if (e != cudaSuccess) return cuda_status(e);
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
-    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+    // factors on the side stream when pipelining, else on the main stream
+    cudaStream_t fs = ctx->stream;
+    if (nbuf == 2) {
+        rc = ensure_side_stream(ctx);
+        if (rc) return rc;
+        fs = ctx->side_stream;
+        e = cudaEventRecord(ctx->ev_ready, ctx->stream);       // prep (and earlier work) done
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, ctx->ev_ready, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t c0 = c * chunk;
         const int64_t nc = n - c0 < chunk ? n - c0 : chunk;
         const int64_t ld = (2 * nc + 63) / 64 * 64;
+        const int b = (int)(c & 1) % nbuf;
+        void *P = fac + b * (p_bytes + q_bytes);
+        void *Q = fac + b * (p_bytes + q_bytes) + p_bytes;
+        if (nbuf == 2 && c >= 2) {
+            e = cudaStreamWaitEvent(fs, ctx->ev_gemm[b], 0);   // the GEMM of chunk c - 2 has read buffer b
+            if (e != cudaSuccess) return cuda_status(e);
+        }
         {
-            ProfileScope ps(ctx, "factors", 1);
-            e = launch_factors(mode, geo + c0, aux + c0, (int)nc, height, width, P, Q, ld, amax, ctx->stream);
+            ProfileScope ps(ctx, "factors", 1, fs);
+            e = launch_factors(mode, geo + c0, aux + c0, (int)nc, height, width, P, Q, ld, amax, fs);
         }
         if (e != cudaSuccess) return cuda_status(e);
+        if (nbuf == 2) {
+            e = cudaEventRecord(ctx->ev_fact[b], fs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_fact[b], 0);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
         GemmPlan pc = plan;
-        pc.accumulate = c0 > 0;
+        pc.accumulate = c > 0;
         {
             ProfileScope ps(ctx, "gemm_tcgen05", 1);
             e = launch_gemm(pc, P, Q, height, width, ld, plan.splits > 1 ? parts : d_out, plane, amax, ctx->d_status,
                             tmo, ctx->stream);
         }
         if (e != cudaSuccess) return cuda_status(e);
+        if (nbuf == 2) {
+            e = cudaEventRecord(ctx->ev_gemm[b], ctx->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
     }
     if (plan.splits == 1) return CGH_OK;
     ProfileScope ps(ctx, "reduce_slices", 1);
@@ -197,13 +238,15 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
     const int64_t ld_max = (2 * chunk + 63) / 64 * 64;
     GemmPlan plan;
     plan.mode = mode;
-    plan.bn = ctx->gemm_bn > 0 ? ctx->gemm_bn : choose_gemm_bn(width);
-    if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
     plan.ctas = gemm_max_ctas(ctx->num_sms);
+    const GemmLayout lay = choose_gemm_layout(width, height, ld_max / 64, plan.ctas, ctx->gemm_bn, ctx->gemm_splitk,
+                                              ctx->gemm_trans);
+    plan.bn = lay.bn;
+    plan.splits = lay.splits;
+    plan.trans = lay.trans;
+    if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
     plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
     plan.accumulate = false;
-    const int64_t tiles = (int64_t)((height + 127) / 128) * ((width + plan.bn - 1) / plan.bn);
-    plan.splits = ctx->gemm_splitk > 0 ? ctx->gemm_splitk : choose_gemm_splits(tiles, ld_max / 64, plan.ctas);
     const int64_t last = n - (n - 1) / chunk * chunk;
     if (plan.splits > (2 * last + 63) / 64) plan.splits = (int)((2 * last + 63) / 64);
     const size_t amax_bytes = 256;
@@ -354,6 +397,9 @@ int cgh_destroy(cgh_ctx *ctx)
         cudaEventDestroy(p.stop);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+    for (cudaEvent_t ev : {ctx->ev_ready, ctx->ev_fact[0], ctx->ev_fact[1], ctx->ev_gemm[0], ctx->ev_gemm[1]})
+        if (ev) cudaEventDestroy(ev);
     destroy_batch_plan(ctx->batch);
     destroy_tune_state(ctx->tune);
     delete ctx;
@@ -391,7 +437,7 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         ctx->gemm_splitk = (int)value;
         return CGH_OK;
     case CGH_OPT_GEMM_BN:
-        if (value != 0 && (value < 16 || value > 256 || value % 16 != 0)) return CGH_EINVAL;
+        if (value != 0 && !gemm_bn_supported((int)value)) return CGH_EINVAL;
         ctx->gemm_bn = (int)value;
         return CGH_OK;
     case CGH_OPT_TOLERANCE_E9:
@@ -409,6 +455,14 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_FACTOR_BUDGET_MB:
         if (value < 1 || value > (1 << 22)) return CGH_EINVAL;
         ctx->factor_budget_mb = value;
+        return CGH_OK;
+    case CGH_OPT_GEMM_TRANSPOSE:
+        if (value < 0 || value > 2) return CGH_EINVAL;
+        ctx->gemm_trans = (int)value;
+        return CGH_OK;
+    case CGH_OPT_GEMM_PIPELINE:
+        if (value < 1 || value > 64) return CGH_EINVAL;
+        ctx->gemm_pipeline = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

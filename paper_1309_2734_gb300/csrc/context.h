@@ -36,6 +36,10 @@ struct cgh_ctx {
     int gemm_chunk = 0;
     int drop_tile = -1;       // CGH_OPT_TEST_DROP_TILE
     int64_t factor_budget_mb = 2048;   // CGH_OPT_FACTOR_BUDGET_MB
+    int gemm_trans = 0;                // CGH_OPT_GEMM_TRANSPOSE
+    int gemm_pipeline = 1;             // CGH_OPT_GEMM_PIPELINE (measured: no gain on GB300, off)
+    cudaStream_t side_stream = nullptr;   // factor generation of the next point chunk
+    cudaEvent_t ev_ready = nullptr, ev_fact[2] = {nullptr, nullptr}, ev_gemm[2] = {nullptr, nullptr};
     int64_t tol_e9 = 10000;   // 1e-5
     int *d_status = nullptr;  // [0] status bits, [1..2] quantiser scratch, [3] spare
     void *ws = nullptr;       // grow-only workspace
@@ -138,16 +142,17 @@ inline cudaEvent_t take_event(cgh_ctx *ctx)
 // Brackets the launches made in its scope with events on the context's stream.
 class ProfileScope {
   public:
-    ProfileScope(cgh_ctx *ctx, const char *name, int launches) : ctx_(ctx), name_(name), launches_(launches)
+    ProfileScope(cgh_ctx *ctx, const char *name, int launches, cudaStream_t s = nullptr)
+        : ctx_(ctx), name_(name), launches_(launches), stream_(s ? s : ctx->stream)
     {
-        if (ctx_->profile && (start_ = take_event(ctx_))) cudaEventRecord(start_, ctx_->stream);
+        if (ctx_->profile && (start_ = take_event(ctx_))) cudaEventRecord(start_, stream_);
     }
     ~ProfileScope()
     {
         if (!start_) return;
         cudaEvent_t stop = take_event(ctx_);
         if (!stop) return;
-        cudaEventRecord(stop, ctx_->stream);
+        cudaEventRecord(stop, stream_);
         ctx_->pending.push_back({name_, launches_, start_, stop});
     }
 
@@ -155,8 +160,26 @@ class ProfileScope {
     cgh_ctx *ctx_;
     const char *name_;
     int launches_;
+    cudaStream_t stream_;
     cudaEvent_t start_ = nullptr;
 };
+
+// The side stream and events of the factor/GEMM pipeline, created on first use.
+inline int ensure_side_stream(cgh_ctx *ctx)
+{
+    if (ctx->side_stream) return CGH_OK;
+    if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->side_stream = nullptr;
+        return CGH_ECUDA;
+    }
+    for (cudaEvent_t *ev : {&ctx->ev_ready, &ctx->ev_fact[0], &ctx->ev_fact[1], &ctx->ev_gemm[0], &ctx->ev_gemm[1]})
+        if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return CGH_ECUDA;
+        }
+    return CGH_OK;
+}
 
 inline int64_t padded_points(int64_t n)
 {

@@ -73,6 +73,7 @@ struct UnitInfo {
     uint32_t idesc;
     bool vec;
     bool accumulate;             // add to the output already there (later point chunks)
+    bool trans;                  // A = Q, B = P: accumulator rows are hologram columns
 };
 
 // One hologram: everything in the (grid-constant) kernel parameters.
@@ -85,6 +86,7 @@ struct alignas(64) SingleUnits {
     uint32_t idesc;
     int vec;
     int accumulate;
+    int trans;
 
     __device__ int begin() const { return blockIdx.x; }
     __device__ int end() const { return tiles_m * tiles_n * splits; }
@@ -112,6 +114,7 @@ struct alignas(64) SingleUnits {
         x.idesc = idesc;
         x.vec = vec != 0;
         x.accumulate = accumulate != 0;
+        x.trans = trans != 0;
         return x;
     }
 };
@@ -148,6 +151,7 @@ struct BatchUnits {
         x.idesc = J.idesc;
         x.vec = J.vec != 0;
         x.accumulate = false;
+        x.trans = J.trans != 0;
         return x;
     }
 };
@@ -306,6 +310,39 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * C::kAccStride);
+                if (x.trans) {
+                    // accumulator row = hologram column m (the warp's 32 lanes hold 32
+                    // consecutive m), accumulator column = hologram row n: every store
+                    // instruction writes 128 contiguous bytes of out[n][m0 .. m0 + 31]
+                    const int m = row;
+                    const bool in_m = m < x.width;
+#pragma unroll 1
+                    for (int cc = 0; cc < x.bn; cc += 32) {
+                        const int ncol = min(32, x.bn - cc);   // 16 or 32
+                        const int n0 = x.tn * x.bn + cc;
+                        float old[32];
+                        if (!first && in_m) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                old[i] = (i < ncol && n0 + i < x.height) ? x.out[(long long)(n0 + i) * x.width + m] : 0.0f;
+                        }
+                        uint32_t r[2][16];
+                        tmem_ld16(taddr + (uint32_t)cc, r[0]);
+                        if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
+                        tmem_ld_wait();
+                        if (!in_m) continue;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i >= ncol || n0 + i >= x.height) continue;
+                            float v = empty_range ? 0.0f : __uint_as_float(r[i >> 4][i & 15]) * unscale;
+                            if (!first) v += old[i];
+                            x.out[(long long)(n0 + i) * x.width + m] = v;
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&tempty[b]);
+                    continue;
+                }
 #pragma unroll 1
                 for (int cc = 0; cc < x.bn; cc += 64) {
                     // 64 columns per round (four groups of 16): the previous partial sums
@@ -432,7 +469,7 @@ int gemm_max_ctas(int num_sms)
 
 bool gemm_bn_supported(int bn)
 {
-    return bn == 128 || bn == 192 || bn == 240 || bn == 256;
+    return bn == 128 || bn == 192 || bn == 224 || bn == 240 || bn == 256;
 }
 
 cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int height, int width, int64_t ld,
@@ -445,18 +482,23 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
     const bool split3 = plan.mode == kFactorSplit16;
     const int bn = plan.bn;
     SingleUnits u;
-    const uint16_t *p16 = static_cast<const uint16_t *>(P);
-    const uint16_t *q16 = static_cast<const uint16_t *>(Q);
-    if (!make_operand_map(&u.p, P, bf16, ld, height, kBM) || !make_operand_map(&u.q, Q, bf16, ld, width, bn))
+    // A operand: 128-row tiles of P (or of Q when transposed); B operand: bn-row tiles of the other
+    const bool tr = plan.trans;
+    const void *A = tr ? Q : P, *B = tr ? P : Q;
+    const int a_rows = tr ? width : height, b_rows = tr ? height : width;
+    const uint16_t *a16 = static_cast<const uint16_t *>(A);
+    const uint16_t *b16 = static_cast<const uint16_t *>(B);
+    if (!make_operand_map(&u.p, A, bf16, ld, a_rows, kBM) || !make_operand_map(&u.q, B, bf16, ld, b_rows, bn))
         return cudaErrorInvalidValue;
     if (split3) {
-        if (!make_operand_map(&u.pl, p16 + (int64_t)height * ld, false, ld, height, kBM) ||
-            !make_operand_map(&u.ql, q16 + (int64_t)width * ld, false, ld, width, bn))
+        if (!make_operand_map(&u.pl, a16 + (int64_t)a_rows * ld, false, ld, a_rows, kBM) ||
+            !make_operand_map(&u.ql, b16 + (int64_t)b_rows * ld, false, ld, b_rows, bn))
             return cudaErrorInvalidValue;
     } else {
         u.pl = u.p;
         u.ql = u.q;
     }
+    u.trans = tr ? 1 : 0;
     u.nkb = (int)(ld / kBK);
     u.out = out;
     u.amp_max = amp_max;
@@ -464,8 +506,8 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
     u.height = height;
     u.width = width;
     u.splits = plan.splits;
-    u.tiles_m = (height + kBM - 1) / kBM;
-    u.tiles_n = (width + bn - 1) / bn;
+    u.tiles_m = (a_rows + kBM - 1) / kBM;
+    u.tiles_n = (b_rows + bn - 1) / bn;
     u.kc = plan.chunk_kb > 0 ? plan.chunk_kb : u.nkb;
     u.passes = split3 ? 3 : 1;
     u.bn = bn;
@@ -477,6 +519,7 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
     switch (bn) {
     case 128: return launch_single<128>(u, ctas, status, timeout_ns, s);
     case 192: return launch_single<192>(u, ctas, status, timeout_ns, s);
+    case 224: return launch_single<224>(u, ctas, status, timeout_ns, s);
     case 240: return launch_single<240>(u, ctas, status, timeout_ns, s);
     default: return launch_single<256>(u, ctas, status, timeout_ns, s);
     }
@@ -512,6 +555,7 @@ bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q,
     job->bn = bn;
     job->idesc = umma_idesc_f16(bf16, kBM, bn);
     job->vec = (width % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    job->trans = 0;
     return true;
 }
 

@@ -64,6 +64,7 @@ struct GemmPlan {
     int ctas;          // persistent CTAs
     int chunk_kb;      // k-blocks (of 64) per TMEM accumulation chain; 0 = whole split
     bool accumulate;   // add to the output (or partial planes) instead of overwriting
+    bool trans;        // A = Q (128-row tiles of hologram columns), B = P; writes out transposed back
 };
 int gemm_max_ctas(int num_sms);
 bool gemm_bn_supported(int bn);
@@ -80,6 +81,7 @@ struct alignas(64) GemmJob {
     int height, width, nkb, tiles_m, tiles_n, kc, passes, bn;
     uint32_t idesc;
     int vec;
+    int trans;
 };
 bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q, int height, int width, int64_t ld,
                    int chunk_kb, float *out, const float *amp_max);

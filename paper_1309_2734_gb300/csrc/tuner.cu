@@ -71,6 +71,38 @@ int choose_gemm_bn(int width)
     return best;
 }
 
+GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, int force_bn, int force_splits,
+                              int force_trans)
+{
+    static const int cands[] = {256, 240, 224, 192, 128};
+    GemmLayout best{false, 256, 1};
+    double best_t = 1e300;
+    for (int tr = 0; tr < 2; ++tr) {
+        if (force_trans == 1 && tr) continue;    // 1: never transposed
+        if (force_trans == 2 && !tr) continue;   // 2: always transposed
+        const int64_t a_rows = tr ? width : height, b_rows = tr ? height : width;
+        const int64_t tiles_m = (a_rows + 127) / 128;
+        for (int bn : cands) {
+            if (force_bn > 0 && bn != force_bn) continue;
+            const int64_t tiles = tiles_m * ((b_rows + bn - 1) / bn);
+            for (int64_t s = 1; s <= 16; ++s) {
+                if (force_splits > 0 && s != force_splits) continue;
+                if (force_splits <= 0 && s > 1 && s * 4 > k_blocks) break;
+                const int64_t rounds = (tiles * s + ctas - 1) / ctas;
+                // critical path: rounds of units of (k_blocks / s) k-steps on a 128 x bn tile;
+                // each extra split costs a partial plane, narrow tiles cost operand bandwidth
+                double t = (double)rounds * ((double)k_blocks / (double)s) * (double)bn * (1.0 + 0.01 * (double)(s - 1));
+                if (bn < 192) t *= 1.05;
+                if (t < best_t * (1.0 - 1e-9)) {
+                    best_t = t;
+                    best = GemmLayout{tr != 0, bn, (int)s};
+                }
+            }
+        }
+    }
+    return best;
+}
+
 int choose_gemm_splits(int64_t tiles, int64_t k_blocks, int ctas)
 {
     if (tiles <= 0 || ctas <= 0) return 1;
@@ -379,7 +411,7 @@ int tune_choose_bn(cgh_ctx *ctx, int width, int height, int form)
     const std::string key = bn_key(width, height, form);
     auto it = t->bn.find(key);
     if (it != t->bn.end()) return it->second;
-    static const int cands[] = {256, 240, 192, 128};
+    static const int cands[] = {256, 240, 224, 192, 128};
     int best = choose_gemm_bn(width);
     double best_t = 1e300;
     for (int bn : cands) {

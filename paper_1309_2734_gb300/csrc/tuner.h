@@ -11,6 +11,17 @@ namespace cgh {
 // whole waves of resident CTAs; 1 when one wave is already nearly full.
 int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms);
 
+// GEMM orientation, tile width and K splits with the shortest critical path
+// (rounds of units over ctas CTAs, times the work of one unit); force_* > 0
+// pin a choice (force_trans: 1 = never transposed, 2 = always).
+struct GemmLayout {
+    bool trans;
+    int bn;
+    int splits;
+};
+GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, int force_bn, int force_splits,
+                              int force_trans);
+
 // GEMM tile width (columns of the hologram per tile) with the least padding.
 int choose_gemm_bn(int width);
 

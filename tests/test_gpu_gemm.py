@@ -35,9 +35,11 @@ def _dev(c):
     return torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda()
 
 
-def _run(c, form, bn=None, splitk=None, chunk=None, budget_mb=None):
+def _run(c, form, bn=None, splitk=None, chunk=None, budget_mb=None, trans=None):
     xyz, amp = _dev(c)
     with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form=form, timeout_ms=3000) as h:
+        if trans:
+            h.set_option(_lib.CGH_OPT_GEMM_TRANSPOSE, trans)
         if budget_mb:
             h.set_option(_lib.CGH_OPT_FACTOR_BUDGET_MB, budget_mb)
         if bn:
@@ -188,4 +190,41 @@ def test_layered_million_points_split16_sampled():
         f = h.point_cloud(xyz, amp)
         h.sync()
         got = f[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
+    assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]
+
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_split16"])
+def test_factor_gemm_pipeline_matches_unpipelined(form):
+    """Factors of the next point chunk on a second stream while the GEMM of the current one runs:
+    the same result as one chunk at a time."""
+    c = workloads.random_cloud(60, 640, 360, 40000)
+    xyz, amp = _dev(c)
+    outs = []
+    for depth in (1, 4):
+        with Hologram(640, 360, c.pitch_m, c.lambda_m, form=form, timeout_ms=5000) as h:
+            h.set_option(_lib.CGH_OPT_GEMM_PIPELINE, depth)
+            outs.append(h.point_cloud(xyz, amp).cpu().numpy())
+            h.sync()
+    assert oracle.nrms(outs[1], outs[0]) < 1e-5
+    rng = np.random.default_rng(61)
+    cols, rows = rng.integers(0, 640, 200), rng.integers(0, 360, 200)
+    ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    assert oracle.nrms(outs[1][rows, cols], ref) <= NRMS[form]
+
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_split16"])
+@pytest.mark.parametrize("trans", [1, 2])
+@pytest.mark.parametrize("bn,splitk", [(224, 1), (128, 3), (256, 2)])
+def test_both_orientations(form, trans, bn, splitk):
+    """128-row tiles of P or of Q (then written back transposed), ragged in both directions."""
+    c = workloads.random_cloud(62, 500, 270, 1500)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 500, 270)
+    got = _run(c, form, bn=bn, splitk=splitk, trans=trans)
+    assert oracle.nrms(got, ref) <= NRMS[form]
+
+
+def test_transposed_point_chunks_accumulate():
+    c = workloads.random_cloud(63, 333, 250, 3000)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 333, 250)
+    got = _run(c, "gemm_split16", splitk=2, budget_mb=1, trans=2)
     assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]

@@ -113,3 +113,11 @@ def test_kinoform_quantiser_same_field():
     ties = np.abs(scaled - np.round(scaled)) < 1e-4
     assert np.array_equal(q[~ties], want[~ties])
     assert list(q[:4]) == [0, 63, 127, 191]
+
+
+@pytest.mark.parametrize("trans", [1, 2])
+def test_wave_gemm_orientations(trans):
+    c = workloads.random_cloud(313, 300, 140, 1200)
+    ref = oracle.wave(c.pitch_m, c.lambda_m, c.xyz, c.amp, 300, 140)
+    got, _ = _wave(c, "gemm_split16", {_lib.CGH_OPT_GEMM_TRANSPOSE: trans})
+    _check_wave(got, ref, 1e-5)
