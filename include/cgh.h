@@ -94,8 +94,16 @@ enum {
     CGH_OPT_GEMM_PIPELINE = 10, /* GEMM forms: point chunks (>= 8192 points each) whose factor generation overlaps
                                    the previous chunk's GEMM on a second stream; default 1 = no overlap (on GB300
                                    the overlap measured no faster at 1920x1080 with 5x10^4 points) */
-    CGH_OPT_GEMM_TRANSPOSE = 11 /* GEMM forms: 0 = automatic, 1 = 128-row tiles of P (hologram rows), 2 = 128-row
+    CGH_OPT_GEMM_TRANSPOSE = 11, /* GEMM forms: 0 = automatic, 1 = 128-row tiles of P (hologram rows), 2 = 128-row
                                    tiles of Q (hologram columns; the result is written back transposed) */
+    CGH_OPT_GEMM_GROUP = 12     /* GEMM forms, cgh_point_cloud: points on one depth plane (equal z, so equal
+                                   constant of Eq. 5) and one column x share the column factor of the separable
+                                   form, so their row factors are summed first and the GEMM runs over K = 2 x the
+                                   number of such groups.  0 = automatic: tried from 65536 points, used when it at
+                                   least halves K; 1 = never; 2 = whenever it applies.  It applies with at most 64
+                                   distinct depths and at most 1024 points per group, and never while the stream is
+                                   being captured into a graph (it reads two counts back to the host, which waits for
+                                   the stream).  Results agree with the ungrouped form to rounding. */
 };
 
 typedef struct cgh_ctx cgh_ctx;

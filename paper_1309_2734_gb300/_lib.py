@@ -30,6 +30,7 @@ CGH_OPT_TEST_DROP_TILE = 8
 CGH_OPT_FACTOR_BUDGET_MB = 9
 CGH_OPT_GEMM_PIPELINE = 10
 CGH_OPT_GEMM_TRANSPOSE = 11
+CGH_OPT_GEMM_GROUP = 12
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",

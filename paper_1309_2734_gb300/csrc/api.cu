@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <thread>
@@ -61,32 +62,37 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
 constexpr int kSplit16ChunkKb = 8;
 // smallest point chunk worth a pipeline stage of its own
 constexpr int64_t kPipelineMinPoints = 8192;
+// CGH_OPT_GEMM_GROUP = 0 tries the grouped form from this many points
+constexpr int64_t kGroupMinPoints = 65536;
 
 int factor_mode(int form)
 {
     return form == CGH_GEMM_BF16 ? kFactorBF16 : (form == CGH_GEMM_SPLIT16 ? kFactorSplit16 : kFactorF16);
 }
 
-// GEMM form: prep, then per chunk of points the factors P and Q (scaled by
-// 1/max|A|) and the tcgen05 GEMM over K splits, later chunks adding to the
-// planes of the first; then the fixed-order split reduction when there is more
-// than one split.  Chunks bound the factor workspace (CGH_OPT_FACTOR_BUDGET_MB:
-// 10^6 points of a 4096x4096 split-FP16 hologram would otherwise need 65 GB)
-// and can pipeline the two halves of the form: with CGH_OPT_GEMM_PIPELINE > 1
-// the factors of chunk c + 1 are generated on a second stream (double-buffered)
-// while the tensor cores run the GEMM of chunk c.  (Measured on GB300 at
-// 1920x1080 with 5x10^4 points: 0.428 ms without, 0.428-0.46 ms with 2-4
-// stages, so it is off by default.)
-int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double lambda, const float *d_xyz,
-             const float *d_amp, int64_t n, float *d_out)
+// Factor generation for K units [u0, u0 + nu) (points, or groups of points)
+// into P and Q with leading dimension ld, on stream s.
+using FactorLaunch = std::function<cudaError_t(int64_t u0, int64_t nu, void *P, void *Q, int64_t ld, cudaStream_t s)>;
+
+// The GEMM over K units: per chunk of units the factors P and Q and the
+// tcgen05 GEMM over K splits, later chunks adding to the planes of the first;
+// then the fixed-order split reduction when there is more than one split.
+// Chunks bound the factor workspace (CGH_OPT_FACTOR_BUDGET_MB: 10^6 points of
+// a 4096x4096 split-FP16 hologram would otherwise need 65 GB) and can pipeline
+// the two halves of the form: with CGH_OPT_GEMM_PIPELINE > 1 the factors of
+// chunk c + 1 are generated on a second stream (double-buffered) while the
+// tensor cores run the GEMM of chunk c.  (Measured on GB300 at 1920x1080 with
+// 5x10^4 points: 0.428 ms without, 0.428-0.46 ms with 2-4 stages, so it is
+// off by default.)  The epilogue multiplies by *scale, the factor of Q (or
+// P) that keeps the FP16 operands within range.
+int gemm_units(cgh_ctx *ctx, int mode, int width, int height, int64_t n, const char *factor_name,
+               const FactorLaunch &factors, const float *scale, float *d_out)
 {
-    const int mode = factor_mode(form);
     const int planes = mode == kFactorSplit16 ? 2 : 1;
-    const int64_t n_pad = padded_points(n);
-    const int64_t bytes_per_point = (int64_t)planes * (width + height) * 2 * 2;
+    const int64_t bytes_per_unit = (int64_t)planes * (width + height) * 2 * 2;
     const int depth = ctx->gemm_pipeline;
     const int64_t budget = (ctx->factor_budget_mb << 20) / (depth > 1 ? 2 : 1);   // per factor buffer
-    int64_t chunk = budget / bytes_per_point / 32 * 32;
+    int64_t chunk = budget / bytes_per_unit / 32 * 32;
     if (chunk < 32) chunk = 32;
     if (depth > 1 && n >= (int64_t)depth * kPipelineMinPoints) {
         const int64_t even = ((n + depth - 1) / depth + 31) / 32 * 32;
@@ -113,29 +119,14 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     if (plan.splits > nkb_last) plan.splits = (int)nkb_last;
     const int64_t plane = (int64_t)width * height;
     const int nbuf = n_chunks > 1 ? 2 : 1;
-    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
-    const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
-    const size_t amax_bytes = 256;
     const size_t p_bytes = align_up((size_t)planes * height * ld_max * 2, 256);
     const size_t q_bytes = align_up((size_t)planes * width * ld_max * 2, 256);
     const size_t part_bytes = plan.splits > 1 ? (size_t)plan.splits * plane * sizeof(float) : 0;
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes,
-                    geo_bytes + aux_bytes + amax_bytes + nbuf * (p_bytes + q_bytes) + part_bytes);
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, nbuf * (p_bytes + q_bytes) + part_bytes);
     if (rc) return rc;
-    char *base = static_cast<char *>(ctx->ws);
-    int4 *geo = reinterpret_cast<int4 *>(base);
-    uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
-    float *amax = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
-    char *fac = base + geo_bytes + aux_bytes + amax_bytes;
+    char *fac = static_cast<char *>(ctx->ws);
     float *parts = reinterpret_cast<float *>(fac + nbuf * (p_bytes + q_bytes));
-    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), ctx->stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    {
-        ProfileScope ps(ctx, "prep_points", 1);
-        e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status, amax,
-                               ctx->stream);
-    }
-    if (e != cudaSuccess) return cuda_status(e);
+    cudaError_t e;
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
     // factors on the side stream when pipelining, else on the main stream
     cudaStream_t fs = ctx->stream;
@@ -159,8 +150,8 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
             if (e != cudaSuccess) return cuda_status(e);
         }
         {
-            ProfileScope ps(ctx, "factors", 1, fs);
-            e = launch_factors(mode, geo + c0, aux + c0, (int)nc, height, width, P, Q, ld, amax, fs);
+            ProfileScope ps(ctx, factor_name, 1, fs);
+            e = factors(c0, nc, P, Q, ld, fs);
         }
         if (e != cudaSuccess) return cuda_status(e);
         if (nbuf == 2) {
@@ -172,8 +163,8 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
         pc.accumulate = c > 0;
         {
             ProfileScope ps(ctx, "gemm_tcgen05", 1);
-            e = launch_gemm(pc, P, Q, height, width, ld, plan.splits > 1 ? parts : d_out, plane, amax, ctx->d_status,
-                            tmo, ctx->stream);
+            e = launch_gemm(pc, P, Q, height, width, ld, plan.splits > 1 ? parts : d_out, plane, scale,
+                            ctx->d_status, tmo, ctx->stream);
         }
         if (e != cudaSuccess) return cuda_status(e);
         if (nbuf == 2) {
@@ -184,6 +175,118 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     if (plan.splits == 1) return CGH_OK;
     ProfileScope ps(ctx, "reduce_slices", 1);
     return cuda_status(launch_reduce_slices(parts, plan.splits, plane, plane, d_out, ctx->stream));
+}
+
+// Copies n ints of device memory to the context's pinned buffer and waits for
+// them (bounded like cgh_sync); the grouped form's two reads of counts.
+int read_counts(cgh_ctx *ctx, const int *d_src, int n, int *out)
+{
+    if (!ctx->h_meta) {
+        if (cudaMallocHost(&ctx->h_meta, 16 * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_meta = nullptr;
+            return CGH_ENOMEM;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx->h_meta, d_src, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t q = cudaStreamQuery(ctx->stream);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_status(q);
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+        if (ms.count() > 2 * ctx->timeout_ms + 1000) return CGH_ETIMEOUT;
+        std::this_thread::yield();
+    }
+    std::memcpy(out, ctx->h_meta, n * sizeof(int));
+    return CGH_OK;
+}
+
+// GEMM form: prep into the point workspace, then (CGH_OPT_GEMM_GROUP) either
+// the grouped form -- points of one depth plane and one column summed into a
+// single K unit before the GEMM -- or one K unit per point.
+int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double lambda, const float *d_xyz,
+             const float *d_amp, int64_t n, float *d_out)
+{
+    const int mode = factor_mode(form);
+    const int64_t n_pad = padded_points(n);
+    bool try_group = ctx->gemm_group == 2 || (ctx->gemm_group == 0 && n >= kGroupMinPoints);
+    if (try_group) {   // the grouped form reads counts back: not while a graph is being captured
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            try_group = false;
+        } else if (cs != cudaStreamCaptureStatusNone) {
+            try_group = false;
+        }
+    }
+    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
+    const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
+    const size_t meta_bytes = 256;   // amax, wscale, meta[4]
+    const size_t gscratch_bytes = try_group ? align_up(group_workspace_bytes((int)n, kMaxPlanes), 256) : 0;
+    const size_t groups_bytes = try_group ? align_up((size_t)n * sizeof(int4), 256) : 0;
+    const size_t gathered_bytes = try_group ? geo_bytes + aux_bytes : 0;
+    int rc = ensure(&ctx->pws, &ctx->pws_bytes,
+                    geo_bytes + aux_bytes + meta_bytes + gscratch_bytes + groups_bytes + gathered_bytes);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->pws);
+    int4 *geo = reinterpret_cast<int4 *>(base);
+    uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
+    float *amax = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
+    float *wscale = amax + 1;
+    int *meta = reinterpret_cast<int *>(amax + 4);
+    char *gscratch = base + geo_bytes + aux_bytes + meta_bytes;
+    int4 *groups = reinterpret_cast<int4 *>(gscratch + gscratch_bytes);
+    int4 *geo_g = reinterpret_cast<int4 *>(gscratch + gscratch_bytes + groups_bytes);
+    uint2 *aux_g = reinterpret_cast<uint2 *>(gscratch + gscratch_bytes + groups_bytes + geo_bytes);
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    {
+        ProfileScope ps(ctx, "prep_points", 1);
+        e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status, amax,
+                               ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    if (try_group) {
+        int m[4] = {0, 0, 0, 0};
+        {
+            ProfileScope ps(ctx, "group_planes", 2);
+            e = launch_planes(geo, (int)n, gscratch, meta, ctx->stream);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        rc = read_counts(ctx, meta, 1, m);
+        if (rc) return rc;
+        const int n_planes = m[0];
+        if (n_planes >= 1 && n_planes <= kMaxPlanes) {
+            {
+                ProfileScope ps(ctx, "group_count", 4);
+                e = launch_group_count(geo, (int)n, n_planes, gscratch, meta, groups, ctx->stream);
+            }
+            if (e != cudaSuccess) return cuda_status(e);
+            rc = read_counts(ctx, meta, 4, m);
+            if (rc) return rc;
+            const int n_groups = m[2], largest = m[3];
+            const bool pays = ctx->gemm_group == 2 || 2 * (int64_t)n_groups <= n;
+            if (n_groups >= 1 && largest <= kMaxGroupPoints && pays) {
+                {
+                    ProfileScope ps(ctx, "group_build", 4);
+                    e = launch_group_build(geo, aux, (int)n, n_planes, n_groups, gscratch, meta, groups, amax,
+                                           wscale, geo_g, aux_g, ctx->stream);
+                }
+                if (e != cudaSuccess) return cuda_status(e);
+                const FactorLaunch gf = [&](int64_t u0, int64_t nu, void *P, void *Q, int64_t ld, cudaStream_t s) {
+                    return launch_group_factors(mode, groups, (int)u0, (int)nu, geo_g, aux_g, height, width, P, Q, ld,
+                                                wscale, s);
+                };
+                return gemm_units(ctx, mode, width, height, n_groups, "group_factors", gf, wscale, d_out);
+            }
+        }
+    }
+    const FactorLaunch pf = [&](int64_t u0, int64_t nu, void *P, void *Q, int64_t ld, cudaStream_t s) {
+        return launch_factors(mode, geo + u0, aux + u0, (int)nu, height, width, P, Q, ld, amax, s);
+    };
+    return gemm_units(ctx, mode, width, height, n, "factors", pf, amax, d_out);
 }
 
 // The complex object wave: real plane at d_out, imaginary plane at d_out + W H.
@@ -390,6 +493,8 @@ int cgh_destroy(cgh_ctx *ctx)
     DeviceGuard g(ctx->device);
     int rc = cgh_sync(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->pws) cudaFree(ctx->pws);
+    if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->io) cudaFree(ctx->io);
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto &p : ctx->pending) {
@@ -463,6 +568,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_GEMM_PIPELINE:
         if (value < 1 || value > 64) return CGH_EINVAL;
         ctx->gemm_pipeline = (int)value;
+        return CGH_OK;
+    case CGH_OPT_GEMM_GROUP:
+        if (value < 0 || value > 2) return CGH_EINVAL;
+        ctx->gemm_group = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

@@ -44,6 +44,10 @@ struct cgh_ctx {
     int *d_status = nullptr;  // [0] status bits, [1..2] quantiser scratch, [3] spare
     void *ws = nullptr;       // grow-only workspace
     size_t ws_bytes = 0;
+    void *pws = nullptr;      // GEMM forms: prepared points and their groups (grow-only)
+    size_t pws_bytes = 0;
+    int *h_meta = nullptr;    // pinned: counts the grouped GEMM form reads back
+    int gemm_group = 0;       // CGH_OPT_GEMM_GROUP
     void *io = nullptr;       // device staging of cgh_point_cloud_host
     size_t io_bytes = 0;
     // CGH_OPT_PROFILE: events around each launch, folded into per-kernel totals on read

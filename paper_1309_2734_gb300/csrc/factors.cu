@@ -128,7 +128,122 @@ __global__ void __launch_bounds__(kFactorThreads)
     }
 }
 
+// Grouped factors (groups.cu): for group g (plane constant C, column x_g,
+// members in [first, first + count) of the gathered point arrays)
+//   P'[n][2g] + i P'[n][2g+1] = s sum_members A_j exp(i 2 pi C (n - y_j)^2)
+//   Q'[m][2g] + i Q'[m][2g+1] = exp(-i 2 pi C (m - x_g)^2)   (cos alpha, -sin alpha)
+// so that sum_k P'[n][k] Q'[m][k] = s Re sum_g W_g(n) U_g(m) = s I(m, n);
+// s = 1 / wscale keeps |P'| <= 1.
+//
+// A block covers 32 rows (of P', or of Q' for the blocks past the P' rows) and
+// kGroupTile group slots.  Each warp takes whole groups, one lane per row, so
+// the lanes of a warp run the same member loop (no divergence whatever the
+// group sizes) and read each member with one broadcast load.  The block's
+// results meet in shared memory (slot-major, padded against bank conflicts)
+// and leave as full 256-byte row segments.
+constexpr int kGroupTile = 64;
+constexpr int kGroupThreads = 256;
+constexpr int kTileStride = 33;   // words per slot in the shared tile: 32 rows + 1
+
+template <int MODE>
+__global__ void __launch_bounds__(kGroupThreads)
+    group_factors_kernel(const int4 *__restrict__ groups, int g_begin, int n_groups, int slots,
+                         const int4 *__restrict__ geo_g, const uint2 *__restrict__ aux_g, int height, int width,
+                         uint16_t *__restrict__ P, uint16_t *__restrict__ Q, long long ld, long long plane_p,
+                         long long plane_q, const float *__restrict__ wscale)
+{
+    __shared__ uint32_t tile_hi[kGroupTile * kTileStride];
+    __shared__ uint32_t tile_lo[MODE == kFactorSplit16 ? kGroupTile * kTileStride : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p_blocks = (height + 31) / 32;
+    const bool is_p = (int)blockIdx.y < p_blocks;
+    const int r0 = (is_p ? (int)blockIdx.y : (int)blockIdx.y - p_blocks) * 32;
+    const int line = r0 + lane;
+    const int s_base = blockIdx.x * kGroupTile;
+    const float inv = 1.0f / *wscale;
+    for (int k = warp; k < kGroupTile; k += kGroupThreads / 32) {
+        const int s = s_base + k;
+        float re = 0.0f, im = 0.0f;
+        if (s < n_groups) {
+            const int4 d = groups[g_begin + s];   // {first, count, plane, x}
+            if (is_p) {
+                for (int i = 0; i < d.y; ++i) {
+                    const int4 p = geo_g[d.x + i];                       // same address in every lane
+                    const float a = __uint_as_float(aux_g[d.x + i].y);
+                    const uint32_t dy = (uint32_t)(line - p.y);
+                    const uint32_t d2 = dy * dy;
+                    const uint32_t g = (uint32_t)p.z * d2 + __umulhi((uint32_t)p.w, d2);
+                    float sn, cs;
+                    sincos_turn((float)(int)g * 2.3283064365386963e-10f, sn, cs);
+                    re = fmaf(a, cs, re);
+                    im = fmaf(a, sn, im);
+                }
+                re *= inv;
+                im *= inv;
+            } else if (d.y > 0) {
+                const int4 p = geo_g[d.x];
+                const uint32_t dx = (uint32_t)(line - d.w);
+                const uint32_t d2 = dx * dx;
+                const uint32_t g = (uint32_t)p.z * d2 + __umulhi((uint32_t)p.w, d2);
+                float sn, cs;
+                sincos_turn((float)(int)g * 2.3283064365386963e-10f, sn, cs);
+                re = cs;
+                im = -sn;
+            }
+        }
+        tile_hi[k * kTileStride + lane] = pack(re, im, MODE, false);
+        if (MODE == kFactorSplit16) tile_lo[k * kTileStride + lane] = pack(re, im, MODE, true);
+    }
+    __syncthreads();
+    // write-out: a warp stores two rows, 16 lanes x 16 bytes (4 slots) each
+    const int rows = is_p ? height : width;
+    uint16_t *base = is_p ? P : Q;
+    const long long lo_off = is_p ? plane_p : plane_q;
+    for (int item = threadIdx.x; item < 32 * (kGroupTile / 4); item += kGroupThreads) {
+        const int row = item / (kGroupTile / 4), c = item % (kGroupTile / 4);
+        const int s = s_base + 4 * c;
+        if (r0 + row >= rows || s >= slots) continue;
+        uint16_t *dst = base + (long long)(r0 + row) * ld + 2 * s;
+        const int t = 4 * c * kTileStride + row;
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(tile_hi[t], tile_hi[t + kTileStride], tile_hi[t + 2 * kTileStride],
+                                                     tile_hi[t + 3 * kTileStride]);
+        if (MODE == kFactorSplit16)
+            *reinterpret_cast<uint4 *>(dst + lo_off) = make_uint4(
+                tile_lo[t], tile_lo[t + kTileStride], tile_lo[t + 2 * kTileStride], tile_lo[t + 3 * kTileStride]);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int n_groups, const int4 *geo_g,
+                                 const uint2 *aux_g, int height, int width, void *P, void *Q, int64_t ld,
+                                 const float *wscale, cudaStream_t s)
+{
+    const int slots = (int)(ld / 2);
+    dim3 grid((slots + kGroupTile - 1) / kGroupTile, (height + 31) / 32 + (width + 31) / 32);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    const long long plane_p = (long long)height * ld, plane_q = (long long)width * ld;
+    auto *p = static_cast<uint16_t *>(P);
+    auto *q = static_cast<uint16_t *>(Q);
+    switch (mode) {
+    case kFactorF16:
+        group_factors_kernel<kFactorF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, geo_g,
+                                                                        aux_g, height, width, p, q, ld, plane_p,
+                                                                        plane_q, wscale);
+        break;
+    case kFactorBF16:
+        group_factors_kernel<kFactorBF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, geo_g,
+                                                                         aux_g, height, width, p, q, ld, plane_p,
+                                                                         plane_q, wscale);
+        break;
+    default:
+        group_factors_kernel<kFactorSplit16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots,
+                                                                            geo_g, aux_g, height, width, p, q, ld,
+                                                                            plane_p, plane_q, wscale);
+        break;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_points, int height, int width,
                            void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s, bool imag_q_only)

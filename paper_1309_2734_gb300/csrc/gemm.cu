@@ -29,9 +29,13 @@
 // Accumulation chunks.  Long accumulation chains in TMEM lose accuracy much
 // faster than round-to-nearest FP32 would (measured on GB300: NRMS ~1.5e-5
 // after 9000 K elements of split FP16, growing about linearly with the
-// chain), so a unit's K range is cut into chunks of kc k-blocks: each chunk
-// is accumulated in TMEM from zero, and the epilogue adds it to the tile in
-// global memory (L2-resident) in FP32, in a fixed order.
+// chain), so a unit's K range is cut into chunks of kc k-blocks, each
+// accumulated in TMEM from zero.  A unit of several chunks keeps its running
+// total in tensor memory: the first chunk goes to one accumulator (the
+// total), every later chunk to the other, and the epilogue adds it to the
+// total (tcgen05.ld both, FP32 add, tcgen05.st) in a fixed order; the tile
+// reaches global memory once.  The next unit's total takes the accumulator
+// the last chunk used, so its first chunk overlaps the previous write-out.
 //
 // Every wait is bounded; on a timeout the CTA latches kStatusTimeout, drains
 // what it issued (again bounded), frees its TMEM and returns.
@@ -231,15 +235,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            uint32_t it = 0, ch = 0;
+            uint32_t it = 0;
+            uint32_t uses[2] = {0u, 0u};   // chunks each accumulator has received
+            int nb = 0;                    // accumulator of the next unit's first chunk
             bool ok = true;
             for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
                 const UnitInfo x = src.get(u);
                 const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
-                for (int c = 0; c < nch && ok; ++c, ++ch) {
+                const int tb = nb;   // the unit's total
+                for (int c = 0; c < nch && ok; ++c) {
                     const int c0 = x.kb0 + c * x.kc, c1 = min(x.kb1, c0 + x.kc);
-                    const int b = (int)(ch & 1u);
-                    const uint32_t uph = (ch >> 1) & 1u;
+                    const int b = c == 0 ? tb : 1 - tb;
+                    const uint32_t uph = uses[b] & 1u;
+                    ++uses[b];
                     if (!mbar_wait(&tempty[b], uph ^ 1u, timeout_ns)) {
                         atomicOr(status, kStatusTimeout);
                         ok = false;
@@ -275,6 +283,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     // an empty K range issues no MMA; the epilogue then writes zeros itself
                     umma_commit(&tfull[b]);
                 }
+                nb = 1 - tb;   // the other accumulator is released first
             }
             // every MMA issued so far completes before TMEM is freed
             umma_commit(drain);
@@ -284,7 +293,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // ---------------- epilogue ----------------
         const int q = warp & 3;   // TMEM lane quarter this warp may access
         const int row_in_tile = q * 32 + lane;
-        uint32_t ch = 0;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
+        uint32_t uses[2] = {0u, 0u};
+        int nb = 0;
         bool ok = true;
         for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
             const UnitInfo x = src.get(u);
@@ -297,52 +308,73 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
             const int row = x.tm * kBM + row_in_tile;
             float *dst = x.out + (long long)row * x.width;
-            for (int c = 0; c < nch; ++c, ++ch) {
-                // the first chunk stores, later chunks add (FP32, fixed order): each TMEM
-                // accumulation chain stays kc k-blocks long
-                const bool first = c == 0 && !x.accumulate;
-                const int b = (int)(ch & 1u);
-                const uint32_t uph = (ch >> 1) & 1u;
-                if (!mbar_wait(&tfull[b], uph, timeout_ns)) {
+            const int tb = nb;
+            nb = 1 - tb;
+            const uint32_t taddr = lane_base + (uint32_t)(tb * C::kAccStride);          // the unit's total
+            const uint32_t xaddr = lane_base + (uint32_t)((1 - tb) * C::kAccStride);    // its later chunks
+            if (!mbar_wait(&tfull[tb], uses[tb] & 1u, timeout_ns)) {
+                atomicOr(status, kStatusTimeout);
+                ok = false;
+                break;
+            }
+            ++uses[tb];
+            tc_fence_after();
+            for (int c = 1; c < nch; ++c) {
+                // total += chunk c, in FP32 and chunk order
+                if (!mbar_wait(&tfull[1 - tb], uses[1 - tb] & 1u, timeout_ns)) {
                     atomicOr(status, kStatusTimeout);
                     ok = false;
                     break;
                 }
+                ++uses[1 - tb];
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * C::kAccStride);
-                if (x.trans) {
-                    // accumulator row = hologram column m (the warp's 32 lanes hold 32
-                    // consecutive m), accumulator column = hologram row n: every store
-                    // instruction writes 128 contiguous bytes of out[n][m0 .. m0 + 31]
-                    const int m = row;
-                    const bool in_m = m < x.width;
 #pragma unroll 1
-                    for (int cc = 0; cc < x.bn; cc += 32) {
-                        const int ncol = min(32, x.bn - cc);   // 16 or 32
-                        const int n0 = x.tn * x.bn + cc;
-                        float old[32];
-                        if (!first && in_m) {
+                for (int cc = 0; cc < x.bn; cc += 16) {
+                    uint32_t a[16], t[16];
+                    tmem_ld16(xaddr + (uint32_t)cc, a);
+                    tmem_ld16(taddr + (uint32_t)cc, t);
+                    tmem_ld_wait();
 #pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                old[i] = (i < ncol && n0 + i < x.height) ? x.out[(long long)(n0 + i) * x.width + m] : 0.0f;
-                        }
-                        uint32_t r[2][16];
-                        tmem_ld16(taddr + (uint32_t)cc, r[0]);
-                        if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
-                        tmem_ld_wait();
-                        if (!in_m) continue;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            if (i >= ncol || n0 + i >= x.height) continue;
-                            float v = empty_range ? 0.0f : __uint_as_float(r[i >> 4][i & 15]) * unscale;
-                            if (!first) v += old[i];
-                            x.out[(long long)(n0 + i) * x.width + m] = v;
-                        }
-                    }
-                    tc_fence_before();
-                    mbar_arrive(&tempty[b]);
-                    continue;
+                    for (int i = 0; i < 16; ++i) t[i] = __float_as_uint(__uint_as_float(t[i]) + __uint_as_float(a[i]));
+                    tmem_st16(taddr + (uint32_t)cc, t);
                 }
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(&tempty[1 - tb]);
+            }
+            if (!ok) break;
+            // the tile to global memory: stored, or added to what earlier point chunks left there
+            const bool first = !x.accumulate;
+            if (x.trans) {
+                // accumulator row = hologram column m (the warp's 32 lanes hold 32
+                // consecutive m), accumulator column = hologram row n: every store
+                // instruction writes 128 contiguous bytes of out[n][m0 .. m0 + 31]
+                const int m = row;
+                const bool in_m = m < x.width;
+#pragma unroll 1
+                for (int cc = 0; cc < x.bn; cc += 32) {
+                    const int ncol = min(32, x.bn - cc);   // 16 or 32
+                    const int n0 = x.tn * x.bn + cc;
+                    float old[32];
+                    if (!first && in_m) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            old[i] = (i < ncol && n0 + i < x.height) ? x.out[(long long)(n0 + i) * x.width + m] : 0.0f;
+                    }
+                    uint32_t r[2][16];
+                    tmem_ld16(taddr + (uint32_t)cc, r[0]);
+                    if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
+                    tmem_ld_wait();
+                    if (!in_m) continue;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (i >= ncol || n0 + i >= x.height) continue;
+                        float v = empty_range ? 0.0f : __uint_as_float(r[i >> 4][i & 15]) * unscale;
+                        if (!first) v += old[i];
+                        x.out[(long long)(n0 + i) * x.width + m] = v;
+                    }
+                }
+            } else {
 #pragma unroll 1
                 for (int cc = 0; cc < x.bn; cc += 64) {
                     // 64 columns per round (four groups of 16): the previous partial sums
@@ -396,9 +428,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         }
                     }
                 }
-                tc_fence_before();
-                mbar_arrive(&tempty[b]);
             }
+            tc_fence_before();
+            mbar_arrive(&tempty[tb]);
         }
     }
     __syncthreads();

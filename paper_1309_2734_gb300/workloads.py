@@ -119,6 +119,21 @@ def large_layered(n: int = 1_000_000, size: int = 4096, seed: int = 13092734005)
     return Cloud(size, size, PITCH_M, LAMBDA_M, xyz, amp, f"layered-{size}x{size}-n{n}")
 
 
+def layered_cloud(seed: int, width: int, height: int, n: int, n_planes: int,
+                  x_range: Optional[tuple] = None, a_range=(0.1, 1.0)) -> Cloud:
+    """A cloud on n_planes depth planes z_k = 0.2 + 0.8 k / max(n_planes - 1, 1) m.
+
+    x ~ U{x_range[0] .. x_range[1] - 1} (default the hologram's columns), y ~ U{0..H-1},
+    plane ~ U{0..n_planes-1}, A ~ U[a_range]: small stand-ins for the depth-layered case.
+    """
+    rng = np.random.default_rng(seed)
+    planes = 0.2 + 0.8 * np.arange(n_planes) / max(n_planes - 1, 1)
+    xyz, amp = _draw(rng, width, height, n, 0.0, 0.0, a_range[0], a_range[1], z_planes=planes)
+    if x_range is not None:
+        xyz[:, 0] = rng.integers(x_range[0], x_range[1], size=n)
+    return Cloud(width, height, PITCH_M, LAMBDA_M, xyz, amp, f"layered{n_planes}-{width}x{height}-n{n}")
+
+
 def large_crop(size: int = 4096, crop: int = 512) -> tuple:
     """(row0, col0, rows, cols) of the central crop compared for the large case."""
     r0 = (size - crop) // 2
