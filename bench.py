@@ -335,8 +335,8 @@ def run_ours(args):
                    "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kp.items()}}
             if extra.startswith("gemm") and "gemm_tcgen05" in kp:
                 passes = 3 if extra == "gemm_split16" else 1
-                gl, gms = kp["gemm_tcgen05"]
-                tflops = 4.0 * wc.evals * passes / (gms / max(gl, 1) * 1e-3) / 1e12
+                gl, gms = kp["gemm_tcgen05"]   # one launch per chunk of points: time per hologram
+                tflops = 4.0 * wc.evals * passes / (gms / reps * 1e-3) / 1e12
                 peak_tc = _peaks().get("bf16_tflops") or 1939.7
                 rec["roofline"] = {"kernel": "gemm_tcgen05", "bound": "tensor", "achieved": tflops,
                                    "peak": peak_tc, "unit": "TFLOP/s", "frac": tflops / peak_tc,
@@ -377,6 +377,60 @@ def run_ours(args):
                     entry[pform] = {"s_per_hologram": sec, "gevals_per_s": pc.evals / sec / 1e9,
                                     "speedup_vs_k20": t_k20 / sec}
             paper[f"n{n_pts}"] = entry
+
+    # the large depth-layered case: 4096x4096, 10^6 points on 16 planes; the GEMM forms group
+    # the points by plane and column (automatic rule), beside the ungrouped split form and the
+    # direct kernel; NRMS on 256 sampled pixels against the FP64 oracle (CPU leg)
+    large = {}
+    if not args.no_large:
+        from paper_1309_2734_gb300 import _lib
+        lc = workloads.large_layered()
+        lx, la = torch.from_numpy(lc.xyz).cuda(), torch.from_numpy(lc.amp).cuda()
+        lbuf = torch.empty((lc.height, lc.width), dtype=torch.float32, device="cuda")
+        n_groups = int(np.unique(lc.xyz[:, [0, 2]], axis=0).shape[0])
+        rng = np.random.default_rng(4096)
+        lcols, lrows = rng.integers(0, lc.width, 256), rng.integers(0, lc.height, 256)
+        with Hologram(lc.width, lc.height, lc.pitch_m, lc.lambda_m, stream=stream, timeout_ms=60000) as hl:
+            for lform, group, reps in (("gemm_split16", 0, 5), ("gemm_f16", 0, 5), ("gemm_split16", 1, 1),
+                                       ("direct_sfu", 0, 1)):
+                hl.set_form(lform)
+                hl.set_option(_lib.CGH_OPT_GEMM_GROUP, group)
+                hl.point_cloud(lx, la, lbuf)
+                hl.sync()
+                hl.profile(True)
+                hl.profile_read(reset=True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    hl.point_cloud(lx, la, lbuf)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                hl.sync()
+                kp = hl.profile_read(reset=True)
+                hl.profile(False)
+                ms = e0.elapsed_time(e1) / reps
+                grouped = "group_factors" in kp
+                rec = {"ms_per_hologram": ms, "gevals_per_s": lc.evals / ms / 1e6, "grouped": grouped,
+                       "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kp.items()}}
+                if lform.startswith("gemm") and "gemm_tcgen05" in kp:
+                    passes = 3 if lform == "gemm_split16" else 1
+                    k_units = n_groups if grouped else lc.n_points
+                    gl, gms = kp["gemm_tcgen05"]   # one launch per chunk of K units: time per hologram
+                    tflops = 4.0 * lc.width * lc.height * k_units * passes / (gms / reps * 1e-3) / 1e12
+                    peak_tc = _peaks().get("bf16_tflops") or 1939.7
+                    rec["gemm_k"] = 2 * k_units
+                    rec["roofline"] = {"kernel": "gemm_tcgen05", "bound": "tensor", "achieved": tflops,
+                                       "peak": peak_tc, "unit": "TFLOP/s", "frac": tflops / peak_tc}
+                rec["_sample"] = lbuf[torch.from_numpy(lrows).cuda(), torch.from_numpy(lcols).cuda()].cpu().numpy()
+                large[f"{lform}{'' if group == 0 else '/ungrouped'}"] = rec
+        if not args.no_cpu_baseline:
+            import oracle
+            lref = oracle.field_at(lc.pitch_m, lc.lambda_m, lc.xyz, lc.amp, lcols, lrows)
+            for rec in large.values():
+                rec["nrms_vs_oracle"] = oracle.nrms(rec["_sample"], lref)
+        for rec in large.values():
+            rec.pop("_sample", None)
+        del lx, la, lbuf
 
     h.set_form(args.form)
     h.point_cloud(xyz, amp, out)
@@ -450,6 +504,7 @@ def run_ours(args):
                 "path": "cgh_point_cloud_host (pinned host buffers, copies and sync inside)"},
         "forms": forms,
         "paper_kinoform_1920x1080": paper,
+        "layered_4096x4096_n1000000": large,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -470,6 +525,8 @@ def main():
     ap.add_argument("--compare", nargs="*",
                     default=["direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 4096x4096, 10^6-point depth-layered case")
     ap.add_argument("--no-paper-workload", action="store_true",
                     help="skip the phase-only 1920x1080 workload of the paper's Tables 3-4")
     args = ap.parse_args()

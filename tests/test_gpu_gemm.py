@@ -74,7 +74,7 @@ def test_factors_match_fp64_oracle(form):
         Qg = Q.float().cpu().numpy().astype(np.float64)
         pad_p, pad_q = P[:, k:], Q[:, k:]
         rel, floor = (2.0 ** -8, 6e-7) if form == "gemm_bf16" else (2.0 ** -11, 6e-7)
-    # floor: the single-precision sin/cos polynomials (<= 3.8e-7) plus the turn conversion (<= 1e-7)
+    # floor: the hardware sine and cosine on [-pi, pi] (<= 3.8e-7) plus the turn conversion (<= 1e-7)
     for got, ref in ((Pg[:, :k], Pr), (Qg[:, :k], Qr)):
         err = np.abs(got - ref)
         assert np.all(err <= rel * np.abs(ref) + floor), float(np.max(err - rel * np.abs(ref)))
