@@ -226,7 +226,7 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     const size_t meta_bytes = 256;   // amax, wscale, meta[4]
     const size_t gscratch_bytes = try_group ? align_up(group_workspace_bytes((int)n, kMaxPlanes), 256) : 0;
     const size_t groups_bytes = try_group ? align_up((size_t)n * sizeof(int4), 256) : 0;
-    const size_t gathered_bytes = try_group ? geo_bytes + aux_bytes : 0;
+    const size_t gathered_bytes = try_group ? align_up((size_t)n * sizeof(int2), 256) : 0;
     int rc = ensure(&ctx->pws, &ctx->pws_bytes,
                     geo_bytes + aux_bytes + meta_bytes + gscratch_bytes + groups_bytes + gathered_bytes);
     if (rc) return rc;
@@ -238,8 +238,7 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     int *meta = reinterpret_cast<int *>(amax + 4);
     char *gscratch = base + geo_bytes + aux_bytes + meta_bytes;
     int4 *groups = reinterpret_cast<int4 *>(gscratch + gscratch_bytes);
-    int4 *geo_g = reinterpret_cast<int4 *>(gscratch + gscratch_bytes + groups_bytes);
-    uint2 *aux_g = reinterpret_cast<uint2 *>(gscratch + gscratch_bytes + groups_bytes + geo_bytes);
+    int2 *members = reinterpret_cast<int2 *>(gscratch + gscratch_bytes + groups_bytes);
     cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), ctx->stream);
     if (e != cudaSuccess) return cuda_status(e);
     {
@@ -272,12 +271,12 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
                 {
                     ProfileScope ps(ctx, "group_build", 4);
                     e = launch_group_build(geo, aux, (int)n, n_planes, n_groups, gscratch, meta, groups, amax,
-                                           wscale, geo_g, aux_g, ctx->stream);
+                                           wscale, members, ctx->stream);
                 }
                 if (e != cudaSuccess) return cuda_status(e);
                 const FactorLaunch gf = [&](int64_t u0, int64_t nu, void *P, void *Q, int64_t ld, cudaStream_t s) {
-                    return launch_group_factors(mode, groups, (int)u0, (int)nu, geo_g, aux_g, height, width, P, Q, ld,
-                                                wscale, s);
+                    return launch_group_factors(mode, groups, (int)u0, (int)nu, group_plane_table(gscratch), members,
+                                                height, width, P, Q, ld, wscale, s);
                 };
                 return gemm_units(ctx, mode, width, height, n_groups, "group_factors", gf, wscale, d_out);
             }

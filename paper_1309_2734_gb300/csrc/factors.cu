@@ -141,16 +141,34 @@ __global__ void __launch_bounds__(kFactorThreads)
 // group sizes) and read each member with one broadcast load.  The block's
 // results meet in shared memory (slot-major, padded against bank conflicts)
 // and leave as full 256-byte row segments.
+//
+// Per term: the turn C (n - y)^2 mod 1 in 32-bit fixed point (rounded to 23
+// bits by the +256), its top 23 bits as the mantissa of f in [1, 2), and
+// u = (f - 1.5) K1 in [-pi, pi): the angle minus a half turn, so the sine and
+// cosine of u are minus those of the angle -- the members carry -A.  K1 is
+// 2 pi rounded to a float whose 1.5 multiple is exact, so the argument grid is
+// symmetric about zero and the hardware sine's odd error cancels in the sum
+// (as in the direct kernel).
 constexpr int kGroupTile = 64;
 constexpr int kGroupThreads = 256;
 constexpr int kTileStride = 33;   // words per slot in the shared tile: 32 rows + 1
+constexpr float kTurnK1 = 6.28318595886230469f;   // 0x40c90fdc
+constexpr float kTurnK0 = 9.42477893829345703f;   // 1.5 * kTurnK1, exact
+
+__device__ __forceinline__ void half_turn_sincos(uint32_t chi, uint32_t clo, uint32_t d, float &s, float &c)
+{
+    const uint32_t d2 = d * d;                                    // < 2^30
+    const uint32_t g = chi * d2 + 256u + __umulhi(clo, d2);      // turn in 2^-32 units, +1/2 ulp of 23 bits
+    const float f = __uint_as_float((g >> 9) | 0x3f800000u);
+    __sincosf(fmaf(f, kTurnK1, -kTurnK0), &s, &c);
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(kGroupThreads)
     group_factors_kernel(const int4 *__restrict__ groups, int g_begin, int n_groups, int slots,
-                         const int4 *__restrict__ geo_g, const uint2 *__restrict__ aux_g, int height, int width,
-                         uint16_t *__restrict__ P, uint16_t *__restrict__ Q, long long ld, long long plane_p,
-                         long long plane_q, const float *__restrict__ wscale)
+                         const unsigned long long *__restrict__ planes, const int2 *__restrict__ members,
+                         int height, int width, uint16_t *__restrict__ P, uint16_t *__restrict__ Q, long long ld,
+                         long long plane_p, long long plane_q, const float *__restrict__ wscale)
 {
     __shared__ uint32_t tile_hi[kGroupTile * kTileStride];
     __shared__ uint32_t tile_lo[MODE == kFactorSplit16 ? kGroupTile * kTileStride : 1];
@@ -162,33 +180,41 @@ __global__ void __launch_bounds__(kGroupThreads)
     const int s_base = blockIdx.x * kGroupTile;
     const float inv = 1.0f / *wscale;
     for (int k = warp; k < kGroupTile; k += kGroupThreads / 32) {
-        const int s = s_base + k;
+        const int slot = s_base + k;
         float re = 0.0f, im = 0.0f;
-        if (s < n_groups) {
-            const int4 d = groups[g_begin + s];   // {first, count, plane, x}
+        if (slot < n_groups) {
+            const int4 d = groups[g_begin + slot];   // {first, count, plane, x}
+            const unsigned long long C = planes[d.z];
+            const uint32_t chi = (uint32_t)(C >> 32), clo = (uint32_t)C;
             if (is_p) {
-                for (int i = 0; i < d.y; ++i) {
-                    const int4 p = geo_g[d.x + i];                       // same address in every lane
-                    const float a = __uint_as_float(aux_g[d.x + i].y);
-                    const uint32_t dy = (uint32_t)(line - p.y);
-                    const uint32_t d2 = dy * dy;
-                    const uint32_t g = (uint32_t)p.z * d2 + __umulhi((uint32_t)p.w, d2);
+                const int2 *m = members + d.x;       // same address in every lane
+                int i = 0;
+                for (; i + 4 <= d.y; i += 4) {
+                    int2 v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] = m[i + q];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float sn, cs;
+                        half_turn_sincos(chi, clo, (uint32_t)(line - v[q].x), sn, cs);
+                        re = fmaf(__int_as_float(v[q].y), cs, re);
+                        im = fmaf(__int_as_float(v[q].y), sn, im);
+                    }
+                }
+                for (; i < d.y; ++i) {
+                    const int2 v = m[i];
                     float sn, cs;
-                    sincos_turn((float)(int)g * 2.3283064365386963e-10f, sn, cs);
-                    re = fmaf(a, cs, re);
-                    im = fmaf(a, sn, im);
+                    half_turn_sincos(chi, clo, (uint32_t)(line - v.x), sn, cs);
+                    re = fmaf(__int_as_float(v.y), cs, re);
+                    im = fmaf(__int_as_float(v.y), sn, im);
                 }
                 re *= inv;
                 im *= inv;
-            } else if (d.y > 0) {
-                const int4 p = geo_g[d.x];
-                const uint32_t dx = (uint32_t)(line - d.w);
-                const uint32_t d2 = dx * dx;
-                const uint32_t g = (uint32_t)p.z * d2 + __umulhi((uint32_t)p.w, d2);
+            } else {
                 float sn, cs;
-                sincos_turn((float)(int)g * 2.3283064365386963e-10f, sn, cs);
-                re = cs;
-                im = -sn;
+                half_turn_sincos(chi, clo, (uint32_t)(line - d.w), sn, cs);
+                re = -cs;   // cos alpha
+                im = sn;    // -sin alpha
             }
         }
         tile_hi[k * kTileStride + lane] = pack(re, im, MODE, false);
@@ -215,9 +241,9 @@ __global__ void __launch_bounds__(kGroupThreads)
 
 }  // namespace
 
-cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int n_groups, const int4 *geo_g,
-                                 const uint2 *aux_g, int height, int width, void *P, void *Q, int64_t ld,
-                                 const float *wscale, cudaStream_t s)
+cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int n_groups,
+                                 const unsigned long long *planes, const int2 *members, int height, int width,
+                                 void *P, void *Q, int64_t ld, const float *wscale, cudaStream_t s)
 {
     const int slots = (int)(ld / 2);
     dim3 grid((slots + kGroupTile - 1) / kGroupTile, (height + 31) / 32 + (width + 31) / 32);
@@ -227,18 +253,18 @@ cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int 
     auto *q = static_cast<uint16_t *>(Q);
     switch (mode) {
     case kFactorF16:
-        group_factors_kernel<kFactorF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, geo_g,
-                                                                        aux_g, height, width, p, q, ld, plane_p,
+        group_factors_kernel<kFactorF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, planes,
+                                                                        members, height, width, p, q, ld, plane_p,
                                                                         plane_q, wscale);
         break;
     case kFactorBF16:
-        group_factors_kernel<kFactorBF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, geo_g,
-                                                                         aux_g, height, width, p, q, ld, plane_p,
+        group_factors_kernel<kFactorBF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, planes,
+                                                                         members, height, width, p, q, ld, plane_p,
                                                                          plane_q, wscale);
         break;
     default:
         group_factors_kernel<kFactorSplit16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots,
-                                                                            geo_g, aux_g, height, width, p, q, ld,
+                                                                            planes, members, height, width, p, q, ld,
                                                                             plane_p, plane_q, wscale);
         break;
     }

@@ -15,7 +15,7 @@
 //   2. key = plane id * kXSpan + (x + kMaxCoord), a counting sort: histogram,
 //      exclusive scans of the counts and of the non-empty flags, scatter;
 //   3. each group's members sorted by point index (fixed summation order) and
-//      gathered into contiguous copies of the prepared points.
+//      gathered, in group order, as compact {y, -A} records.
 // The host reads the plane count after step 1 and the group count and largest
 // group after step 2, and keeps the ungrouped form when grouping does not pay.
 #include "device_util.cuh"
@@ -189,14 +189,15 @@ __global__ void group_order(const int4 *__restrict__ groups, const int *meta, in
     }
 }
 
+// Members in group order as {y, -A}: the row factor needs only these (the
+// plane constant comes from the sorted plane table, the column from the group).
 __global__ void group_gather(const int *__restrict__ perm, int n, const int4 *__restrict__ geo,
-                             const uint2 *__restrict__ aux, int4 *__restrict__ geo_g, uint2 *__restrict__ aux_g)
+                             const uint2 *__restrict__ aux, int2 *__restrict__ members)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int j = perm[i];
-    geo_g[i] = geo[j];
-    aux_g[i] = aux[j];
+    members[i] = make_int2(geo[j].y, (int)(__float_as_uint(-__uint_as_float(aux[j].y))));
 }
 
 __global__ void group_scale(const float *amp_max, const int *max_count, float *wscale)
@@ -252,6 +253,11 @@ size_t group_workspace_bytes(int n, int n_planes)
            (size_t)n * 2 * sizeof(int) + 256;
 }
 
+const unsigned long long *group_plane_table(const void *scratch)
+{
+    return static_cast<const unsigned long long *>(scratch) + kPlaneSlots;
+}
+
 cudaError_t launch_planes(const int4 *geo, int n, void *scratch, int *meta, cudaStream_t s)
 {
     const GroupScratch w = carve(scratch, n, 0);
@@ -279,13 +285,13 @@ cudaError_t launch_group_count(const int4 *geo, int n, int n_planes, void *scrat
 
 cudaError_t launch_group_build(const int4 *geo, const uint2 *aux, int n, int n_planes, int n_groups, void *scratch,
                                const int *meta, const int4 *groups, const float *amp_max, float *wscale,
-                               int4 *geo_g, uint2 *aux_g, cudaStream_t s)
+                               int2 *members, cudaStream_t s)
 {
     const GroupScratch w = carve(scratch, n, n_planes);
     if (n > 0) {
         group_scatter<<<blocks(n, 256), 256, 0, s>>>(w.key_of, n, w.scan, w.cursor, w.perm);
         if (n_groups > 0) group_order<<<blocks(n_groups, 128), 128, 0, s>>>(groups, meta, w.perm);
-        group_gather<<<blocks(n, 256), 256, 0, s>>>(w.perm, n, geo, aux, geo_g, aux_g);
+        group_gather<<<blocks(n, 256), 256, 0, s>>>(w.perm, n, geo, aux, members);
     }
     group_scale<<<1, 1, 0, s>>>(amp_max, meta + 3, wscale);
     return cudaGetLastError();

@@ -59,20 +59,22 @@ cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_po
 // Grouped GEMM form (groups.cu, factors.cu).  Groups: points with the same
 // plane constant C and the same column x.  meta (device, 4 ints): [0] planes
 // (-1 beyond kMaxPlanes), [1] points, [2] groups, [3] largest group.  groups[g]
-// = {first, count, plane, x} into the gathered geo_g/aux_g (sized n).
+// = {first, count, plane, x} into members[] = {y, -A} (sized n, group order);
+// the plane ids index the sorted table of plane constants in the scratch.
 constexpr int kMaxPlanes = 64;
 constexpr int kXSpan = 2 * 16384 + 1;
 constexpr int kMaxGroupPoints = 1024;   // larger groups: the ungrouped form
 size_t group_workspace_bytes(int n, int n_planes);
+const unsigned long long *group_plane_table(const void *scratch);
 cudaError_t launch_planes(const int4 *geo, int n, void *scratch, int *meta, cudaStream_t s);
 cudaError_t launch_group_count(const int4 *geo, int n, int n_planes, void *scratch, int *meta, int4 *groups,
                                cudaStream_t s);
 cudaError_t launch_group_build(const int4 *geo, const uint2 *aux, int n, int n_planes, int n_groups, void *scratch,
                                const int *meta, const int4 *groups, const float *amp_max, float *wscale,
-                               int4 *geo_g, uint2 *aux_g, cudaStream_t s);
-cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int n_groups, const int4 *geo_g,
-                                 const uint2 *aux_g, int height, int width, void *P, void *Q, int64_t ld,
-                                 const float *wscale, cudaStream_t s);
+                               int2 *members, cudaStream_t s);
+cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int n_groups,
+                                 const unsigned long long *planes, const int2 *members, int height, int width,
+                                 void *P, void *Q, int64_t ld, const float *wscale, cudaStream_t s);
 
 // a4: tcgen05 GEMM, out[n][m] (+)= sum_k P[n][k] Q[m][k] over K splits (gemm.cu).
 struct GemmPlan {
