@@ -17,6 +17,9 @@ wraps it with ctypes.  Every function cites the passage it follows:
   quantise a phase with 255/(2 pi); this is the amplitude counterpart).
 * ``kinoform8``: that phase rule for the kinoform of Eq. 3.
 * ``recurrence_phases``: Eqs. 6-8 (Section 2.2) iterated in exact rationals.
+* ``model_wave``/``model_wave_at``: the phase models of Eq. 1 (exact spherical
+  wave), Eq. 2 with and without the piston, and the plane-wave reference phase
+  of Eqs. 4-5; the amplitude hologram is the real part.
 """
 from __future__ import annotations
 
@@ -71,6 +74,13 @@ def _load():
                                            _F32P, _F32P, ctypes.c_int64, _F64P, _F64P]
             lib.oracle_quantize8.argtypes = [_F32P, ctypes.c_int64, _U8P, _F32P]
             lib.oracle_kinoform8.argtypes = [_F64P, _F64P, ctypes.c_int64, _U8P]
+            lib.oracle_model_window.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, _F32P, _F32P, ctypes.c_int64,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _F64P,
+                                                _F64P]
+            lib.oracle_model_points.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, _F32P, _F32P, ctypes.c_int64,
+                                                _I32P, _I32P, ctypes.c_int64, _F64P, _F64P]
             _lib = lib
     return _lib
 
@@ -140,6 +150,52 @@ def wave(pitch_m: float, lambda_m: float, xyz, amp, width: int, height: int,
                                     amp.shape[0], r0, rows, c0, cols, _ptr(re, _F64P), _ptr(im, _F64P))
     if rc != 0:
         raise ValueError("oracle_wave_window rejected its arguments")
+    return re + 1j * im
+
+
+FRESNEL, FRESNEL_PISTON, SPHERICAL = 0, 1, 2
+
+
+def model_wave(model: int, pitch_m: float, lambda_m: float, xyz, amp, width: int, height: int,
+               reference=(0.0, 0.0, 0.0), window: Optional[Sequence[int]] = None) -> np.ndarray:
+    """O(m, n) = sum_j A_j exp(i (2 pi t_j + phi_r)) in FP64, complex128 [rows][cols].
+
+    model 0: t = r^2/(2 lambda z) (Eq. 2 without the piston), 1: t = (z + r^2/(2 z))/lambda (Eq. 2),
+    2: t = sqrt(r^2 + z^2)/lambda (Eq. 1); r in metres.  reference = (sin_x, sin_y, phase0):
+    phi_r = 2 pi/lambda (m p sin_x + n p sin_y) + phase0, added to every term as in Eq. 5.
+    The amplitude hologram of Eq. 5 is the real part.
+    """
+    xyz = _f32(xyz).reshape(-1, 3)
+    amp = _f32(amp).reshape(-1)
+    if window is None:
+        window = (0, 0, height, width)
+    r0, c0, rows, cols = (int(v) for v in window)
+    re = np.empty((rows, cols), dtype=np.float64)
+    im = np.empty((rows, cols), dtype=np.float64)
+    sx, sy, ph = (float(v) for v in reference)
+    rc = _load().oracle_model_window(int(model), float(pitch_m), float(lambda_m), sx, sy, ph, _ptr(xyz, _F32P),
+                                     _ptr(amp, _F32P), amp.shape[0], r0, rows, c0, cols, _ptr(re, _F64P),
+                                     _ptr(im, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_model_window rejected its arguments")
+    return re + 1j * im
+
+
+def model_wave_at(model: int, pitch_m: float, lambda_m: float, xyz, amp, cols, rows,
+                  reference=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """model_wave at scattered pixels (cols[i], rows[i]), complex128."""
+    xyz = _f32(xyz).reshape(-1, 3)
+    amp = _f32(amp).reshape(-1)
+    pm = np.ascontiguousarray(cols, dtype=np.int32)
+    pn = np.ascontiguousarray(rows, dtype=np.int32)
+    re = np.empty(pm.shape[0], dtype=np.float64)
+    im = np.empty(pm.shape[0], dtype=np.float64)
+    sx, sy, ph = (float(v) for v in reference)
+    rc = _load().oracle_model_points(int(model), float(pitch_m), float(lambda_m), sx, sy, ph, _ptr(xyz, _F32P),
+                                     _ptr(amp, _F32P), amp.shape[0], _ptr(pm, _I32P), _ptr(pn, _I32P),
+                                     pm.shape[0], _ptr(re, _F64P), _ptr(im, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_model_points rejected its arguments")
     return re + 1j * im
 
 

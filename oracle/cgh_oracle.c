@@ -164,6 +164,84 @@ int oracle_wave_window(double pitch, double lambda, const float *xyz, const floa
 }
 
 /*
+ * Phase models beyond the restricted form (Section 2.1), in turns, for the
+ * widened entry points:
+ *
+ *   model 0  Eq. 2 / Eq. 5 without the piston:  t = r^2 / (2 lambda z_j)
+ *   model 1  Eq. 2 / Eq. 5 with the piston:     t = (z_j + r^2 / (2 z_j)) / lambda
+ *   model 2  Eq. 1 (exact spherical wave):      t = sqrt(r^2 + z_j^2) / lambda
+ *
+ * with r^2 = p^2 ((m - x_j)^2 + (n - y_j)^2) in square metres.  The reference
+ * wave R = A_r exp(i phi_r) of Eq. 4 is a plane wave,
+ *   phi_r(x_h, y_h) = 2 pi / lambda (x_h sin_x + y_h sin_y) + phase0,
+ * x_h = m p, y_h = n p, and enters every term as the "+ phi_r" of Eq. 5:
+ *   I(m, n) = sum_j A_j cos(2 pi t_j + phi_r),
+ *   O(m, n) = sum_j A_j exp(i (2 pi t_j + phi_r)).
+ * Each phase is reduced in turns (t - rint(t)) before cos/sin; t is up to
+ * about 2e6 turns, so double precision leaves ~1e-10 turn.
+ */
+static double model_turn(int model, double pitch, double lambda, double m, double n_row, const float *p)
+{
+    const double dx = (m - (double)p[0]) * pitch;
+    const double dy = (n_row - (double)p[1]) * pitch;
+    const double z = (double)p[2];
+    const double r2 = dx * dx + dy * dy;
+    if (model == 2) return sqrt(r2 + z * z) / lambda;
+    const double t = r2 / (2.0 * lambda * z);
+    return model == 1 ? t + z / lambda : t;
+}
+
+static int model_sum(int model, double pitch, double lambda, double sin_x, double sin_y, double phase0,
+                     const float *xyz, const float *amp, int64_t npts, double m, double n_row,
+                     double *re, double *im)
+{
+    const double ref = (m * pitch * sin_x + n_row * pitch * sin_y) / lambda + phase0 / TWO_PI;   /* turns */
+    double sr = 0.0, si = 0.0;
+    for (int64_t j = 0; j < npts; ++j) {
+        double t = model_turn(model, pitch, lambda, m, n_row, xyz + 3 * j);
+        t = (t - rint(t)) + (ref - rint(ref));
+        const double a = reduced_angle(t);
+        sr += (double)amp[j] * cos(a);
+        si += (double)amp[j] * sin(a);
+    }
+    *re = sr;
+    if (im) *im = si;
+    return 0;
+}
+
+/*
+ * Field (re) and, when im is not NULL, the complex wave's imaginary part over
+ * a window, for phase model 0, 1 or 2 and the plane-wave reference above.
+ */
+int oracle_model_window(int model, double pitch, double lambda, double sin_x, double sin_y, double phase0,
+                        const float *xyz, const float *amp, int64_t npts, int row0, int rows, int col0, int cols,
+                        double *re, double *im)
+{
+    if (model < 0 || model > 2 || rows < 0 || cols < 0 || npts < 0 || !re) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < rows; ++r)
+        for (int q = 0; q < cols; ++q) {
+            const int64_t k = (int64_t)r * cols + q;
+            model_sum(model, pitch, lambda, sin_x, sin_y, phase0, xyz, amp, npts, (double)(col0 + q),
+                      (double)(row0 + r), &re[k], im ? &im[k] : NULL);
+        }
+    return 0;
+}
+
+/* The same at npix scattered pixels (pm[i], pn[i]) = (column, row). */
+int oracle_model_points(int model, double pitch, double lambda, double sin_x, double sin_y, double phase0,
+                        const float *xyz, const float *amp, int64_t npts, const int32_t *pm, const int32_t *pn,
+                        int64_t npix, double *re, double *im)
+{
+    if (model < 0 || model > 2 || npix < 0 || npts < 0 || !re) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < npix; ++i)
+        model_sum(model, pitch, lambda, sin_x, sin_y, phase0, xyz, amp, npts, (double)pm[i], (double)pn[i],
+                  &re[i], im ? &im[i] : NULL);
+    return 0;
+}
+
+/*
  * Separable factors: P is [height][2 npts], Q is [width][2 npts] (row-major),
  * with the interleaving described in the header comment.
  */

@@ -313,3 +313,133 @@ def test_kinoform_hand_cases():
     frac = 255.0 * (t - np.floor(t))
     safe = np.abs(frac - np.round(frac)) > 1e-6
     assert np.array_equal(got[safe], want[safe])
+
+
+# ---- phase models of Eq. 1 / Eq. 2 and the plane-wave reference of Eqs. 4-5 ----
+
+def _decimal_model_pixel(model, pitch, lam, ref, xyz, amp, m, n):
+    """Brute force in 60-digit decimal arithmetic: the phase of model 0/1/2 plus phi_r, reduced exactly."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    D = lambda v: Decimal(repr(float(v)))
+    p, L = D(pitch), D(lam)
+    sx, sy, ph = (D(v) for v in ref)
+    two_pi = Decimal("6.283185307179586476925286766559005768394338798750211641949889")
+    reft = (D(m) * p * sx + D(n) * p * sy) / L + ph / two_pi
+    acc = 0.0
+    for (x, y, z), a in zip(xyz.astype(np.float64), amp.astype(np.float64)):
+        dx = (D(m) - D(x)) * p
+        dy = (D(n) - D(y)) * p
+        zz = D(z)
+        r2 = dx * dx + dy * dy
+        if model == 2:
+            t = (r2 + zz * zz).sqrt() / L
+        elif model == 1:
+            t = (zz + r2 / (2 * zz)) / L
+        else:
+            t = r2 / (2 * L * zz)
+        t = t + reft
+        f = t - t.to_integral_value()
+        acc += a * math.cos(2 * math.pi * float(f))
+    return acc
+
+
+def _model_tol(xyz, amp, lam, turns_extra=1e3):
+    """The oracle's own rounding: phases of up to max z/lambda turns carry a few ulps of that size each,
+    so the field is off by at most 2 pi * 8 ulp(t_max) * sum|A| (t_max: the piston plus the quadratic part)."""
+    t_max = float(np.max(xyz[:, 2].astype(np.float64))) / lam + turns_extra
+    return 2 * math.pi * 8 * float(np.spacing(t_max)) * float(np.sum(np.abs(amp.astype(np.float64)))) + 1e-12
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("ref", [(0.0, 0.0, 0.0), (0.0123, -0.0071, 0.7)])
+def test_models_brute_force_tiny(model, ref):
+    rng = np.random.default_rng(40 + model)
+    xyz = np.stack([rng.integers(-20, 40, 5), rng.integers(-20, 40, 5), rng.uniform(0.05, 0.6, 5)], 1)
+    xyz, amp = _cloud(xyz, rng.uniform(0.2, 1.0, 5))
+    w = oracle.model_wave(model, P8, L532, xyz, amp, 7, 6, reference=ref, window=(1, 2, 4, 5))
+    for r in range(4):
+        for q in range(5):
+            want = _decimal_model_pixel(model, P8, L532, ref, xyz, amp, 2 + q, 1 + r)
+            assert abs(w[r, q].real - want) < _model_tol(xyz, amp, L532), (model, r, q, w[r, q].real, want)
+
+
+def test_model0_equals_restricted_field_and_wave():
+    """Model 0 without reference is the restricted form of Eq. 5 that the other pins fix."""
+    c = workloads.random_cloud(91, 24, 17, 40)
+    w = oracle.model_wave(0, c.pitch_m, c.lambda_m, c.xyz, c.amp, 24, 17)
+    assert np.allclose(w, oracle.wave(c.pitch_m, c.lambda_m, c.xyz, c.amp, 24, 17), atol=1e-11, rtol=0)
+
+
+def test_spherical_pythagorean_distance():
+    """Eq. 1 at a pixel whose distance is exact: offset (3k, 4k) px, z = 12 k p gives distance 13 k p."""
+    pitch = 2.0 ** -17          # exact in binary, so z = 12 * 1024 * pitch = 0.09375 is an exact float
+    z = 12 * 1024 * pitch
+    xyz, amp = _cloud([[5.0, 7.0, z]], [0.8])
+    w = oracle.model_wave(2, pitch, L532, xyz, amp, 5 + 3072 + 1, 7 + 4096 + 1,
+                          window=(7 + 4096, 5 + 3072, 1, 1))[0, 0]
+    turns = Fraction(13 * 1024) * Fraction(pitch) / Fraction(L532)
+    f = float(turns - round(turns))
+    a = float(amp[0])                                   # 0.8 as stored in single precision
+    tol = _model_tol(xyz, amp, L532)
+    assert abs(w.real - a * math.cos(2 * math.pi * f)) < tol
+    assert abs(w.imag - a * math.sin(2 * math.pi * f)) < tol
+    # the Fresnel phase of Eq. 2 differs there by (12 + 25/24 - 13) * 1024 p / lambda turns (hundreds)
+    w1 = oracle.model_wave(1, pitch, L532, xyz, amp, 5 + 3072 + 1, 7 + 4096 + 1,
+                           window=(7 + 4096, 5 + 3072, 1, 1))[0, 0]
+    t1 = (Fraction(12) + Fraction(25, 24)) * 1024 * Fraction(pitch) / Fraction(L532)
+    assert abs(w1.real - a * math.cos(2 * math.pi * float(t1 - round(t1)))) < tol
+
+
+def test_piston_is_the_depth_phase():
+    """Eq. 2 with the piston = exp(i 2 pi z/lambda) times Eq. 2 without it, for a single depth plane."""
+    c = workloads.layered_cloud(92, 30, 20, 60, 1)
+    z = float(c.xyz[0, 2])
+    w0 = oracle.model_wave(0, c.pitch_m, c.lambda_m, c.xyz, c.amp, 30, 20)
+    w1 = oracle.model_wave(1, c.pitch_m, c.lambda_m, c.xyz, c.amp, 30, 20)
+    t = Fraction(z) / Fraction(c.lambda_m)
+    rot = np.exp(2j * math.pi * float(t - round(t)))
+    assert np.allclose(w1, w0 * rot, atol=_model_tol(c.xyz, c.amp, c.lambda_m), rtol=0)
+
+
+def test_spherical_tends_to_fresnel():
+    """|t_sph - t_fresnel| <= r^4 / (8 lambda z^3) (Taylor remainder of sqrt(1+u) <= 1 + u/2 - u^2/8 + u^3/16),
+    so the two fields differ by at most sum_j A_j 2 pi r_j^4 / (8 lambda z_j^3) at every pixel."""
+    rng = np.random.default_rng(93)
+    n = 12
+    xyz, amp = _cloud(np.stack([rng.integers(0, 40, n), rng.integers(0, 30, n), rng.uniform(0.3, 1.0, n)], 1),
+                      rng.uniform(0.5, 1.0, n))
+    ws = oracle.model_wave(2, P8, L532, xyz, amp, 40, 30)
+    wf = oracle.model_wave(1, P8, L532, xyz, amp, 40, 30)
+    m, nn = np.meshgrid(np.arange(40), np.arange(30))
+    bound = np.zeros((30, 40))
+    for (x, y, z), a in zip(xyz.astype(np.float64), amp.astype(np.float64)):
+        r2 = ((m - x) ** 2 + (nn - y) ** 2) * P8 * P8
+        bound += a * 2 * math.pi * r2 * r2 / (8 * L532 * z ** 3)
+    diff = np.abs(ws - wf)
+    assert np.all(diff <= bound * 1.001 + 1e-10)
+    assert np.max(diff) > 0.05 * np.max(bound)      # the quartic term is really there
+
+
+def test_reference_phase_rotates_every_pixel():
+    """phi_r is added to every term (Eq. 5): O_ref = exp(i phi_r(m, n)) O, phi_r = 2 pi/lambda (x_h sin_x + y_h sin_y) + phase0;
+    with sin_x = lambda / (4 p) the reference advances a quarter turn per column."""
+    c = workloads.random_cloud(94, 20, 9, 30)
+    sx = c.lambda_m / (4 * c.pitch_m)
+    w0 = oracle.model_wave(0, c.pitch_m, c.lambda_m, c.xyz, c.amp, 20, 9)
+    w = oracle.model_wave(0, c.pitch_m, c.lambda_m, c.xyz, c.amp, 20, 9, reference=(sx, 0.0, 0.25))
+    cols = np.arange(20)[None, :]
+    assert np.allclose(w, w0 * np.exp(1j * (0.5 * math.pi * cols + 0.25)), atol=1e-9, rtol=0)
+    sy = -c.lambda_m / (2 * c.pitch_m)           # half a turn per row, backwards
+    w = oracle.model_wave(0, c.pitch_m, c.lambda_m, c.xyz, c.amp, 20, 9, reference=(0.0, sy, 0.0))
+    rows = np.arange(9)[:, None]
+    assert np.allclose(w, w0 * np.exp(-1j * math.pi * rows), atol=1e-9, rtol=0)
+
+
+def test_model_points_match_window():
+    c = workloads.random_cloud(95, 16, 12, 25)
+    ref = (0.01, 0.02, -1.0)
+    w = oracle.model_wave(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, 16, 12, reference=ref)
+    cols, rows = np.array([0, 15, 7, 3]), np.array([0, 11, 5, 9])
+    at = oracle.model_wave_at(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows, reference=ref)
+    assert np.array_equal(at, w[rows, cols])
