@@ -79,6 +79,14 @@ enum {
     CGH_Q_PHASE = 1             /* kinoform: floor(255/(2 pi) * arg), arg of (re, im) in [0, 2 pi) */
 };
 
+/* Phase models (CGH_OPT_PHASE_MODEL), Section 2.1; r^2 = p^2 ((m - x_j)^2 + (n - y_j)^2). */
+enum {
+    CGH_PHASE_FRESNEL = 0,         /* Eq. 5 without the piston: pi r^2 / (lambda z_j) (the default) */
+    CGH_PHASE_FRESNEL_PISTON = 1,  /* Eq. 2 / Eq. 5 (third line): 2 pi / lambda (z_j + r^2 / (2 z_j)) */
+    CGH_PHASE_SPHERICAL = 2        /* Eq. 1 / Eq. 5 (second line): 2 pi / lambda sqrt(r^2 + z_j^2); CGH_DIRECT_SFU
+                                      (or CGH_FORM_AUTO) only, the exact distance is not separable */
+};
+
 /* Options (cgh_set_option). */
 enum {
     CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side wait; host-side waits allow 2x + 1 s; default 5000 */
@@ -96,14 +104,17 @@ enum {
                                    the overlap measured no faster at 1920x1080 with 5x10^4 points) */
     CGH_OPT_GEMM_TRANSPOSE = 11, /* GEMM forms: 0 = automatic, 1 = 128-row tiles of P (hologram rows), 2 = 128-row
                                    tiles of Q (hologram columns; the result is written back transposed) */
-    CGH_OPT_GEMM_GROUP = 12     /* GEMM forms, cgh_point_cloud: points on one depth plane (equal z, so equal
+    CGH_OPT_GEMM_GROUP = 12,    /* GEMM forms, cgh_point_cloud: points on one depth plane (equal z, so equal
                                    constant of Eq. 5) and one column x share the column factor of the separable
                                    form, so their row factors are summed first and the GEMM runs over K = 2 x the
                                    number of such groups.  0 = automatic: tried from 65536 points, used when it at
                                    least halves K; 1 = never; 2 = whenever it applies.  It applies with at most 64
                                    distinct depths and at most 1024 points per group, and never while the stream is
                                    being captured into a graph (it reads two counts back to the host, which waits for
-                                   the stream).  Results agree with the ungrouped form to rounding. */
+                                   the stream).  Results agree with the ungrouped form to rounding.  Not with the
+                                   piston (CGH_PHASE_FRESNEL_PISTON): points of equal C may differ in depth. */
+    CGH_OPT_PHASE_MODEL = 13    /* CGH_PHASE_* above; default CGH_PHASE_FRESNEL.  cgh_batch supports the default
+                                   only (CGH_ENOTSUP otherwise). */
 };
 
 typedef struct cgh_ctx cgh_ctx;
@@ -122,6 +133,19 @@ int cgh_destroy(cgh_ctx *ctx);
 
 /* Binds a CUDA stream (a cudaStream_t passed as void*; NULL = legacy default stream). */
 int cgh_set_stream(cgh_ctx *ctx, void *cuda_stream);
+
+/*
+ * Sets the reference wave R = A_r exp(i phi_r) of Eq. 4 to a plane wave,
+ *   phi_r(x_h, y_h) = 2 pi / lambda (x_h sin_x + y_h sin_y) + phase0_rad,
+ * x_h = m p, y_h = n p.  Eq. 5 adds phi_r to the phase of every term, so the
+ * amplitude hologram becomes sum_j A_j cos(theta_j + phi_r) and the complex
+ * wave (cgh_wave) sum_j A_j exp(i (theta_j + phi_r)).  (Eq. 4 written out
+ * would give theta_j - phi_r; Eq. 5's sign is the one implemented: negate all
+ * three arguments for the other.)  |sin_x|, |sin_y| <= 1, |phase0_rad| <= 1e6,
+ * all finite; (0, 0, 0), the default, is no reference phase.  All forms except
+ * cgh_batch (CGH_ENOTSUP with a reference set).
+ */
+int cgh_set_reference(cgh_ctx *ctx, double sin_x, double sin_y, double phase0_rad);
 
 /* Selects the form (CGH_FORM_* above). */
 int cgh_set_form(cgh_ctx *ctx, int form);

@@ -62,6 +62,16 @@ class Hologram:
     def set_option(self, key: int, value: int) -> None:
         _lib.cgh_set_option(self.ctx, key, value)
 
+    def set_phase_model(self, model) -> None:
+        """'fresnel' (Eq. 5 without the piston, default), 'fresnel_piston' (Eq. 2) or 'spherical' (Eq. 1)."""
+        models = {"fresnel": _lib.CGH_PHASE_FRESNEL, "fresnel_piston": _lib.CGH_PHASE_FRESNEL_PISTON,
+                  "spherical": _lib.CGH_PHASE_SPHERICAL}
+        _lib.cgh_set_option(self.ctx, _lib.CGH_OPT_PHASE_MODEL, models[model] if isinstance(model, str) else model)
+
+    def set_reference(self, sin_x: float = 0.0, sin_y: float = 0.0, phase0_rad: float = 0.0) -> None:
+        """Plane-wave reference of Eqs. 4-5: phi_r = 2 pi/lambda (x_h sin_x + y_h sin_y) + phase0."""
+        _lib.cgh_set_reference(self.ctx, sin_x, sin_y, phase0_rad)
+
     # -- compute
     def point_cloud(self, xyz, amp, out=None):
         """I(m, n) of Eq. 5 (restricted form) as a float32 [height][width] CUDA tensor."""

@@ -31,11 +31,13 @@ CGH_OPT_FACTOR_BUDGET_MB = 9
 CGH_OPT_GEMM_PIPELINE = 10
 CGH_OPT_GEMM_TRANSPOSE = 11
 CGH_OPT_GEMM_GROUP = 12
+CGH_OPT_PHASE_MODEL = 13
+CGH_PHASE_FRESNEL, CGH_PHASE_FRESNEL_PISTON, CGH_PHASE_SPHERICAL = 0, 1, 2
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
            "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
-           "cgh_autotune", "cgh_wave")
+           "cgh_autotune", "cgh_wave", "cgh_set_reference")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -89,6 +91,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_point_cloud_noalloc": ([ci, ci, cd, cd, vp, vp, i64, vp, vp], ci),
             "cgh_autotune": ([vp, ci], ci),
             "cgh_wave": ([vp, vp, vp, i64, vp], ci),
+            "cgh_set_reference": ([vp, cd, cd, cd], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -134,6 +137,10 @@ def cgh_set_form(ctx: int, form) -> None:
 
 def cgh_set_option(ctx: int, key: int, value: int) -> None:
     check(load().cgh_set_option(ctx, int(key), int(value)), "cgh_set_option")
+
+
+def cgh_set_reference(ctx: int, sin_x: float, sin_y: float, phase0_rad: float) -> None:
+    check(load().cgh_set_reference(ctx, float(sin_x), float(sin_y), float(phase0_rad)), "cgh_set_reference")
 
 
 def cgh_point_cloud(ctx: int, d_xyz: int, d_amp: int, n_points: int, d_out: int) -> int:

@@ -44,14 +44,14 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     {
         ProfileScope ps(ctx, "prep_points", 1);
         e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status,
-                               nullptr, ctx->stream);
+                               nullptr, ctx->stream, aux_mode(ctx));
     }
     if (e != cudaSuccess) return cuda_status(e);
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
     {
         ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);
         e = launch_direct(sfu, geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out, plane,
-                          ctx->d_status, tmo, ctx->stream, ctx->drop_tile);
+                          ctx->d_status, tmo, ctx->stream, ctx->drop_tile, phase_ref(ctx));
     }
     if (e != cudaSuccess || split == 1) return cuda_status(e);
     ProfileScope ps(ctx, "reduce_slices", 1);
@@ -211,7 +211,9 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
 {
     const int mode = factor_mode(form);
     const int64_t n_pad = padded_points(n);
-    bool try_group = ctx->gemm_group == 2 || (ctx->gemm_group == 0 && n >= kGroupMinPoints);
+    // with the piston, points of equal C may still differ in depth: no grouping
+    bool try_group = !piston_on(ctx) && (ctx->gemm_group == 2 || (ctx->gemm_group == 0 && n >= kGroupMinPoints));
+    const PhaseRef ref = phase_ref(ctx);
     if (try_group) {   // the grouped form reads counts back: not while a graph is being captured
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
@@ -244,7 +246,7 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     {
         ProfileScope ps(ctx, "prep_points", 1);
         e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status, amax,
-                               ctx->stream);
+                               ctx->stream, aux_mode(ctx));
     }
     if (e != cudaSuccess) return cuda_status(e);
     if (try_group) {
@@ -276,14 +278,14 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
                 if (e != cudaSuccess) return cuda_status(e);
                 const FactorLaunch gf = [&](int64_t u0, int64_t nu, void *P, void *Q, int64_t ld, cudaStream_t s) {
                     return launch_group_factors(mode, groups, (int)u0, (int)nu, group_plane_table(gscratch), members,
-                                                height, width, P, Q, ld, wscale, s);
+                                                height, width, P, Q, ld, wscale, s, ref);
                 };
                 return gemm_units(ctx, mode, width, height, n_groups, "group_factors", gf, wscale, d_out);
             }
         }
     }
     const FactorLaunch pf = [&](int64_t u0, int64_t nu, void *P, void *Q, int64_t ld, cudaStream_t s) {
-        return launch_factors(mode, geo + u0, aux + u0, (int)nu, height, width, P, Q, ld, amax, s);
+        return launch_factors(mode, geo + u0, aux + u0, (int)nu, height, width, P, Q, ld, amax, s, false, ref);
     };
     return gemm_units(ctx, mode, width, height, n, "factors", pf, amax, d_out);
 }
@@ -316,13 +318,13 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
         {
             ProfileScope ps(ctx, "prep_points", 1);
             e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, ctx->pitch, ctx->lambda, geo, aux, ctx->d_status,
-                                   nullptr, ctx->stream);
+                                   nullptr, ctx->stream, aux_mode(ctx));
         }
         if (e != cudaSuccess) return cuda_status(e);
         {
             ProfileScope ps(ctx, "direct_wave", 1);
             e = launch_direct_wave(geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out,
-                                   2 * plane, plane, ctx->d_status, tmo, ctx->stream);
+                                   2 * plane, plane, ctx->d_status, tmo, ctx->stream, phase_ref(ctx));
         }
         if (e != cudaSuccess || split == 1) return cuda_status(e);
         ProfileScope ps(ctx, "reduce_slices", 2);
@@ -369,9 +371,10 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
     {
         ProfileScope ps(ctx, "prep_points", 1);
         e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, ctx->pitch, ctx->lambda, geo, aux, ctx->d_status,
-                               amax, ctx->stream);
+                               amax, ctx->stream, aux_mode(ctx));
     }
     if (e != cudaSuccess) return cuda_status(e);
+    const PhaseRef ref = phase_ref(ctx);
     float *re_out = plan.splits > 1 ? parts : d_out;
     float *im_out = plan.splits > 1 ? parts + (int64_t)plan.splits * plane : d_out + plane;
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
@@ -383,7 +386,7 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
             {
                 ProfileScope ps(ctx, "factors", 1);
                 e = launch_factors(mode, geo + c0, aux + c0, (int)nc, height, width, P, Q, ld, amax, ctx->stream,
-                                   part == 1);
+                                   part == 1, ref);
             }
             if (e != cudaSuccess) return cuda_status(e);
             {
@@ -401,8 +404,55 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
     return cuda_status(e);
 }
 
+// The exact spherical wave (Eq. 1): prep with the piston and the spherical
+// constants, the spherical kernel over point chunks, then the chunk reduction.
+// planes = 1: the amplitude hologram at d_out; 2: the complex wave (real part
+// at d_out, imaginary part at d_out + W H).
+int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lambda, const float *d_xyz,
+                  const float *d_amp, int64_t n, int planes, float *d_out)
+{
+    const int64_t n_pad = padded_points(n);
+    const int64_t n_ptiles = n_pad / kPointTile;
+    const DirectShape sh = spherical_shape();
+    const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
+    int split = ctx->point_split > 0 ? ctx->point_split : choose_point_split(tiles, n_ptiles, ctx->num_sms);
+    if (split > n_ptiles) split = (int)(n_ptiles > 0 ? n_ptiles : 1);
+    const int64_t plane = (int64_t)width * height;
+    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
+    const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
+    const size_t ext_bytes = align_up((size_t)n_pad * sizeof(float2), 256);
+    const size_t part_bytes = split > 1 ? (size_t)split * planes * plane * sizeof(float) : 0;
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + ext_bytes + part_bytes);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->ws);
+    int4 *geo = reinterpret_cast<int4 *>(base);
+    uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
+    float2 *ext = reinterpret_cast<float2 *>(base + geo_bytes + aux_bytes);
+    float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes + ext_bytes);
+    cudaError_t e;
+    {
+        ProfileScope ps(ctx, "prep_points", 1);
+        e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status, nullptr,
+                               ctx->stream, kAuxPiston, ext);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    {
+        ProfileScope ps(ctx, planes == 2 ? "spherical_wave" : "spherical", 1);
+        e = launch_spherical(geo, aux, ext, (int)n_pad, width, height, split, planes, split > 1 ? parts : d_out,
+                             (int64_t)planes * plane, plane, phase_ref(ctx), ctx->stream);
+    }
+    if (e != cudaSuccess || split == 1) return cuda_status(e);
+    ProfileScope ps(ctx, "reduce_slices", planes);
+    for (int c = 0; c < planes && e == cudaSuccess; ++c)
+        e = launch_reduce_slices(parts + c * plane, split, plane, (int64_t)planes * plane, d_out + c * plane,
+                                 ctx->stream);
+    return cuda_status(e);
+}
+
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n)
 {
+    if (ctx->phase_model == CGH_PHASE_SPHERICAL)   // one form computes Eq. 1
+        return (ctx->form == CGH_FORM_AUTO || ctx->form == CGH_DIRECT_SFU) ? CGH_DIRECT_SFU : -1;
     if (ctx->form != CGH_FORM_AUTO) return ctx->form;
     return tune_choose_form(ctx, width, height, n, (double)ctx->tol_e9 * 1e-9);
 }
@@ -412,6 +462,9 @@ int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double l
 {
     if (n == 0) return cuda_status(cudaMemsetAsync(d_out, 0, (size_t)width * height * sizeof(float), ctx->stream));
     const int form = resolve_form(ctx, width, height, n);
+    if (ctx->phase_model == CGH_PHASE_SPHERICAL)
+        return form == CGH_DIRECT_SFU ? run_spherical(ctx, width, height, pitch, lambda, d_xyz, d_amp, n, 1, d_out)
+                                      : CGH_ENOTSUP;
     switch (form) {
     case CGH_DIRECT_SFU:
         return run_direct(ctx, true, width, height, pitch, lambda, d_xyz, d_amp, n, d_out);
@@ -524,6 +577,16 @@ int cgh_set_form(cgh_ctx *ctx, int form)
     return CGH_OK;
 }
 
+int cgh_set_reference(cgh_ctx *ctx, double sin_x, double sin_y, double phase0_rad)
+{
+    if (!ctx || !std::isfinite(sin_x) || !std::isfinite(sin_y) || !std::isfinite(phase0_rad)) return CGH_EINVAL;
+    if (std::fabs(sin_x) > 1.0 || std::fabs(sin_y) > 1.0 || std::fabs(phase0_rad) > 1e6) return CGH_EINVAL;
+    ctx->ref_sx = sin_x;
+    ctx->ref_sy = sin_y;
+    ctx->ref_phase0 = phase0_rad;
+    return CGH_OK;
+}
+
 int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
 {
     if (!ctx) return CGH_EINVAL;
@@ -571,6 +634,11 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_GEMM_GROUP:
         if (value < 0 || value > 2) return CGH_EINVAL;
         ctx->gemm_group = (int)value;
+        return CGH_OK;
+    case CGH_OPT_PHASE_MODEL:
+        if (value != CGH_PHASE_FRESNEL && value != CGH_PHASE_FRESNEL_PISTON && value != CGH_PHASE_SPHERICAL)
+            return CGH_EINVAL;
+        ctx->phase_model = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;
@@ -639,12 +707,12 @@ int cgh_factors(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_
     {
         ProfileScope ps(ctx, "prep_points", 1);
         e = launch_prep_points(d_xyz, d_amp, (int)n_points, (int)n_pad, ctx->pitch, ctx->lambda, geo, aux,
-                               ctx->d_status, nullptr, ctx->stream);
+                               ctx->d_status, nullptr, ctx->stream, aux_mode(ctx));
     }
     if (e != cudaSuccess) return cuda_status(e);
     ProfileScope ps(ctx, "factors", 1);
     return cuda_status(launch_factors(factor_mode(dtype_form), geo, aux, (int)n_points, ctx->height, ctx->width,
-                                      d_p, d_q, ld, nullptr, ctx->stream));
+                                      d_p, d_q, ld, nullptr, ctx->stream, false, phase_ref(ctx)));
 }
 
 int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst)
@@ -656,6 +724,7 @@ int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst)
             !b.d_out || b.n_points < 0 || b.n_points > 0x3fffffffll || (b.n_points > 0 && (!b.d_xyz || !b.d_amp)))
             return CGH_EINVAL;
     }
+    if (ctx->phase_model != CGH_PHASE_FRESNEL || phase_ref(ctx).any()) return CGH_ENOTSUP;
     if (n_inst == 0) return CGH_OK;
     DeviceGuard g(ctx->device);
     return run_batch(ctx, inst, n_inst);
@@ -676,6 +745,10 @@ int cgh_wave(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_poi
     const int64_t plane = (int64_t)ctx->width * ctx->height;
     if (n_points == 0) return cuda_status(cudaMemsetAsync(d_out, 0, (size_t)2 * plane * sizeof(float), ctx->stream));
     int form = resolve_form(ctx, ctx->width, ctx->height, n_points);
+    if (ctx->phase_model == CGH_PHASE_SPHERICAL)
+        return form == CGH_DIRECT_SFU ? run_spherical(ctx, ctx->width, ctx->height, ctx->pitch, ctx->lambda, d_xyz,
+                                                      d_amp, n_points, 2, d_out)
+                                      : CGH_ENOTSUP;
     if (form == CGH_DIRECT_ACCURATE) {
         if (ctx->form == CGH_DIRECT_ACCURATE) return CGH_ENOTSUP;
         form = CGH_DIRECT_SFU;   // the automatic choice falls back to the other FP32 form

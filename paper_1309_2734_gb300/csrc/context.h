@@ -48,6 +48,8 @@ struct cgh_ctx {
     size_t pws_bytes = 0;
     int *h_meta = nullptr;    // pinned: counts the grouped GEMM form reads back
     int gemm_group = 0;       // CGH_OPT_GEMM_GROUP
+    int phase_model = CGH_PHASE_FRESNEL;                 // CGH_OPT_PHASE_MODEL
+    double ref_sx = 0.0, ref_sy = 0.0, ref_phase0 = 0.0;   // cgh_set_reference
     void *io = nullptr;       // device staging of cgh_point_cloud_host
     size_t io_bytes = 0;
     // CGH_OPT_PROFILE: events around each launch, folded into per-kernel totals on read
@@ -185,6 +187,43 @@ inline int ensure_side_stream(cgh_ctx *ctx)
     return CGH_OK;
 }
 
+// frac(turns) in 2^-64 turn: the double's fraction in two 32-bit halves, so
+// that all of its bits survive.
+inline unsigned long long turns_fixed64(double turns)
+{
+    const double f = turns - std::floor(turns);             // [0, 1)
+    const double hi = std::floor(std::ldexp(f, 32));
+    const double lo = std::ldexp(std::ldexp(f, 32) - hi, 32);   // exact, [0, 2^32)
+    return ((unsigned long long)hi << 32) + (unsigned long long)std::llround(lo);
+}
+
+// The context's plane-wave reference in fixed point: kx = p sin_x / lambda and
+// ky = p sin_y / lambda turns per pixel, phi0 = phase0 / (2 pi) turns.
+inline cgh::PhaseRef phase_ref(const cgh_ctx *ctx)
+{
+    cgh::PhaseRef r;
+    r.kx = turns_fixed64(ctx->pitch * ctx->ref_sx / ctx->lambda);
+    r.ky = turns_fixed64(ctx->pitch * ctx->ref_sy / ctx->lambda);
+    const unsigned long long p0 = turns_fixed64(ctx->ref_phase0 / 6.283185307179586476925286766559);
+    r.phi0 = (uint32_t)((p0 >> 32) + ((p0 >> 31) & 1ull));
+    r.piston = ctx->phase_model != CGH_PHASE_FRESNEL ? 1u : 0u;
+    return r;
+}
+
+inline bool piston_on(const cgh_ctx *ctx)
+{
+    return ctx->phase_model != CGH_PHASE_FRESNEL;   // Eq. 2 with its first term, and Eq. 1
+}
+
+// What the point preparation stores in aux.x for the context's phase terms:
+// the piston, a zero piston slot (reference phase only), or the second
+// difference of the plain recurrence.
+inline int aux_mode(const cgh_ctx *ctx)
+{
+    if (piston_on(ctx)) return cgh::kAuxPiston;
+    return phase_ref(ctx).any() ? cgh::kAuxZero : cgh::kAuxSecondDiff;
+}
+
 inline int64_t padded_points(int64_t n)
 {
     return (n + kPointTile - 1) / kPointTile * kPointTile;
@@ -202,5 +241,7 @@ int factor_mode(int form);
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n);
 int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
 int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int64_t n, float *d_out);
+int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lambda, const float *d_xyz,
+                  const float *d_amp, int64_t n, int planes, float *d_out);
 
 }  // namespace cgh

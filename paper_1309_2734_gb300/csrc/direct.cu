@@ -7,7 +7,8 @@
 // mbarriers, and read back as warp-wide broadcasts.
 //
 // Phase.  For one point, the thread forms its corner phase G = C r^2 mod 2^64
-// (top 32 bits, exact to one unit of 2^-32 turn), the first differences along
+// (top 32 bits, exact to one unit of 2^-32 turn; plus the point's piston and
+// the reference phase when those are on), the first differences along
 // x and y, and then walks its block with the recurrence of Eqs. 6-8
 // (Section 2.2): Gamma_{k+1} = Gamma_k + delta_k, delta_{k+1} = delta_k + Delta,
 // Delta = 2 c_j, in 32-bit fixed-point turns, where wrap-around is the
@@ -78,13 +79,27 @@ __device__ __forceinline__ float cos_term(uint32_t g)
     }
 }
 
+// The reference phase seen by one thread: its value at the thread's corner
+// pixel and its change per column and per row (all 2^-32 turn).  Added to a
+// point's corner phase and first differences, it costs three additions per
+// point, none per term; the kernels without piston and reference (EXTRA =
+// false) skip even those (measured 3 % on the SFU form).
+struct PixelRef {
+    uint32_t g, dx, dy;
+};
+
+__device__ __forceinline__ PixelRef pixel_ref(const PhaseRef &r, int m0, int n0)
+{
+    return PixelRef{ref_turn(r, m0, n0), ref_step(r.kx), ref_step(r.ky)};
+}
+
 // Adds one point's terms of the complex object wave (Eq. 2, restricted form) to
 // a thread's TL x TR block: Re += A cos(2 pi t) exactly as the SFU amplitude form,
 // Im += A sin(2 pi t) = A sin(v) with v = K1 (f2 - 1.5) from the turn advanced by a
 // half (f2 - 1 = t + 1/2), the same symmetric argument grid, so the MUFU's odd
 // error again averages out.
-template <int TL, int TR>
-__device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, int m0, int n0,
+template <int TL, int TR, bool EXTRA>
+__device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
                                                  float (&pre)[TR][TL], float (&pim)[TR][TL])
 {
     const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
@@ -93,10 +108,16 @@ __device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, in
     const uint32_t r2 = dx * dx + dy * dy;
     const uint32_t r2x = r2 + 2u * dx + 1u;
     const uint32_t r2y = r2 + 2u * dy + 1u;
-    const uint32_t g0 = chi * r2 + __umulhi(clo, r2);
-    uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
-    uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
-    const uint32_t D = w.x;
+    const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
+    uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
+    uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
+    uint32_t g0 = c0, D = w.x;
+    if constexpr (EXTRA) {   // piston (aux.x) and reference; 2 C formed from C
+        d += pr.dx;
+        e += pr.dy;
+        g0 += w.x + pr.g;
+        D = __funnelshift_l(clo, chi, 1);
+    }
     const float a = __uint_as_float(w.y);
     uint32_t g[TL];
     g[0] = g0 + kSfuBias;
@@ -123,20 +144,27 @@ __device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, in
 }
 
 // Adds one point's terms to a thread's TL x TR block (corner m0, n0).
-template <int TL, int TR, int MODE>
-__device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0, int n0, float (&part)[TR][TL])
+template <int TL, int TR, int MODE, bool EXTRA>
+__device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
+                                            float (&part)[TR][TL])
 {
     constexpr bool kSfuSign = MODE != kEvalAccurate;
     const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
     const uint32_t dx = (uint32_t)(m0 - q.x);
     const uint32_t dy = (uint32_t)(n0 - q.y);
-    const uint32_t r2 = dx * dx + dy * dy;          // < 2^31, exact
+    const uint32_t r2 = dx * dx + dy * dy;          // < 2^32, exact
     const uint32_t r2x = r2 + 2u * dx + 1u;         // (dx+1)^2 + dy^2
     const uint32_t r2y = r2 + 2u * dy + 1u;         // dx^2 + (dy+1)^2
-    const uint32_t g0 = chi * r2 + __umulhi(clo, r2);
-    uint32_t d = chi * r2x + __umulhi(clo, r2x) - g0;
-    uint32_t e = chi * r2y + __umulhi(clo, r2y) - g0;
-    const uint32_t D = w.x;
+    const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
+    uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
+    uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
+    uint32_t g0 = c0, D = w.x;
+    if constexpr (EXTRA) {   // piston (aux.x) and reference at the corner; 2 C formed from C
+        d += pr.dx;
+        e += pr.dy;
+        g0 += w.x + pr.g;
+        D = __funnelshift_l(clo, chi, 1);
+    }
     const float a = kSfuSign ? -__uint_as_float(w.y) : __uint_as_float(w.y);
     uint32_t g[TL];
     g[0] = g0 + (kSfuSign ? kSfuBias : 0u);
@@ -162,12 +190,13 @@ __device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0,
 // tiles this CTA consumed before (stage and mbarrier parity carry across units).
 // PLANES = 1: the amplitude hologram; PLANES = 2: the complex object wave, real
 // part at dst and imaginary part at dst + im_offset (SFU form only).
-template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1>
+template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1, bool EXTRA = false>
 __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const uint2 *__restrict__ aux,
                                             int t_begin, int t_end, int tile_m0, int tile_n0, int width,
                                             int height, float *__restrict__ dst, bool vec, int4 (*s_geo)[kPointTile],
                                             uint2 (*s_aux)[kPointTile], uint64_t *s_bar, uint32_t &kg, int *status,
-                                            unsigned long long timeout_ns, int drop = -1, long long im_offset = 0)
+                                            unsigned long long timeout_ns, int drop = -1, long long im_offset = 0,
+                                            const PhaseRef &ref = PhaseRef())
 {
     constexpr int T = kPointTile;
     constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
@@ -176,6 +205,7 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
     const int m0 = tile_m0 + lx * TL;
     const int n0 = tile_n0 + ly * TR;
     const int nt = t_end - t_begin;
+    const PixelRef pr = pixel_ref(ref, m0, n0);
 
     auto issue = [&](int k) {
         if (k == drop) return;   // test hook: this tile's barrier is never completed
@@ -228,13 +258,13 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         const uint2 *sa = s_aux[st];
         if constexpr (PLANES == 2) {
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms_wave<TL, TR>(sg[p], sa[p], m0, n0, part[0], part[PLANES - 1]);
+            for (int p = 0; p < T; ++p) point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0], part[PLANES - 1]);
         } else if constexpr (SFU) {
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalSfu>(sg[p], sa[p], m0, n0, part[0]);
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalSfu, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         } else {
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate>(sg[p], sa[p], m0, n0, part[0]);
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
@@ -282,11 +312,11 @@ __device__ __forceinline__ void init_point_barriers(uint64_t *s_bar)
 }
 
 // One hologram: blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).
-template <int TL, int TR, int BX, int BY, bool SFU>
+template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA>
 __global__ void __launch_bounds__(BX *BY, 2)
     direct_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_ptiles, int width,
                   int height, int tiles_x, int split, float *__restrict__ out, long long slice_stride,
-                  bool vec, int *status, unsigned long long timeout_ns, int drop_tile)
+                  bool vec, int *status, unsigned long long timeout_ns, int drop_tile, const PhaseRef ref)
 {
     __shared__ alignas(128) int4 s_geo[2][kPointTile];
     __shared__ alignas(128) uint2 s_aux[2][kPointTile];
@@ -296,20 +326,21 @@ __global__ void __launch_bounds__(BX *BY, 2)
     const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
     const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
     uint32_t kg = 0;
-    direct_unit<TL, TR, BX, BY, SFU>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
+    direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
                                      (tile / tiles_x) * (BY * TR), width, height,
                                      out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg,
-                                     status, timeout_ns, blockIdx.y == 0 ? drop_tile : -1);
+                                     status, timeout_ns, blockIdx.y == 0 ? drop_tile : -1, 0, ref);
 }
 
 // The complex object wave of one hologram: blockIdx.x = pixel tile, blockIdx.y =
 // point chunk; chunk s writes real and imaginary planes at out + s * slice_stride
 // and out + s * slice_stride + im_offset.
-template <int TL, int TR, int BX, int BY>
+template <int TL, int TR, int BX, int BY, bool EXTRA>
 __global__ void __launch_bounds__(BX *BY, 2)
     direct_wave_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_ptiles, int width,
                        int height, int tiles_x, int split, float *__restrict__ out, long long slice_stride,
-                       long long im_offset, bool vec, int *status, unsigned long long timeout_ns)
+                       long long im_offset, bool vec, int *status, unsigned long long timeout_ns,
+                       const PhaseRef ref)
 {
     __shared__ alignas(128) int4 s_geo[2][kPointTile];
     __shared__ alignas(128) uint2 s_aux[2][kPointTile];
@@ -319,10 +350,10 @@ __global__ void __launch_bounds__(BX *BY, 2)
     const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
     const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
     uint32_t kg = 0;
-    direct_unit<TL, TR, BX, BY, true, 2>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
+    direct_unit<TL, TR, BX, BY, true, 2, EXTRA>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
                                          (tile / tiles_x) * (BY * TR), width, height,
                                          out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg,
-                                         status, timeout_ns, -1, im_offset);
+                                         status, timeout_ns, -1, im_offset, ref);
 }
 
 // A batch: every CTA walks its list of {job, pixel tile} units over all points of the job.
@@ -357,7 +388,7 @@ DirectShape direct_shape(bool)
 
 cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
                           int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
-                          cudaStream_t s, int drop_tile)
+                          cudaStream_t s, int drop_tile, const PhaseRef &ref)
 {
     const DirectShape sh = direct_shape(sfu);
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
@@ -367,12 +398,20 @@ cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad
     dim3 grid(tiles_x * tiles_y, split);
     // 16-byte stores only when every row start of every slice is 16-byte aligned
     const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
-    if (sfu)
-        direct_kernel<kTL, kTR, kBX, kBY, true><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns, drop_tile);
+    const long long ss = (long long)slice_stride;
+    const bool extra = ref.any();
+    if (sfu && !extra)
+        direct_kernel<kTL, kTR, kBX, kBY, true, false><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
+    else if (sfu)
+        direct_kernel<kTL, kTR, kBX, kBY, true, true><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
+    else if (!extra)
+        direct_kernel<kTL, kTR, kBX, kBY, false, false><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
     else
-        direct_kernel<kTL, kTR, kBX, kBY, false><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, vec, status, timeout_ns, drop_tile);
+        direct_kernel<kTL, kTR, kBX, kBY, false, true><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
     return cudaGetLastError();
 }
 
@@ -413,7 +452,7 @@ DirectShape direct_wave_shape()
 
 cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int width, int height, int split,
                                float *out, int64_t slice_stride, int64_t im_offset, int *status,
-                               uint64_t timeout_ns, cudaStream_t s)
+                               uint64_t timeout_ns, cudaStream_t s, const PhaseRef &ref)
 {
     const DirectShape sh = direct_wave_shape();
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
@@ -423,9 +462,14 @@ cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int
     dim3 grid(tiles_x * tiles_y, split);
     const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && (im_offset % 4 == 0) &&
                      ((uintptr_t)out % 16 == 0);
-    direct_wave_kernel<kWaveTL, kWaveTR, kBX, kBY><<<grid, sh.threads, 0, s>>>(
-        geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, (long long)im_offset, vec,
-        status, timeout_ns);
+    if (ref.any())
+        direct_wave_kernel<kWaveTL, kWaveTR, kBX, kBY, true><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, (long long)im_offset,
+            vec, status, timeout_ns, ref);
+    else
+        direct_wave_kernel<kWaveTL, kWaveTR, kBX, kBY, false><<<grid, sh.threads, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, (long long)im_offset,
+            vec, status, timeout_ns, ref);
     return cudaGetLastError();
 }
 

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kFactorThreads)
     factors_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int slots,
                    int height, int width, uint16_t *__restrict__ P, uint16_t *__restrict__ Q, long long ld,
                    long long plane_p, long long plane_q, const float *__restrict__ amp_max, int row_begin,
-                   bool imag)
+                   bool imag, const PhaseRef ref)
 {
     const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (j0 >= slots) return;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kFactorThreads)
         if (m > 0.0f) scale = 1.0f / m;
     }
     int px[4], py[4];
-    uint32_t chi[4], clo[4];
+    uint32_t chi[4], clo[4], pist[4];
     float a[4];
     bool live[4];
 #pragma unroll
@@ -85,10 +85,12 @@ __global__ void __launch_bounds__(kFactorThreads)
             py[q] = g.y;
             chi[q] = (uint32_t)g.z;
             clo[q] = (uint32_t)g.w;
-            a[q] = __uint_as_float(aux[j].y) * scale;
+            const uint2 w = aux[j];
+            pist[q] = ref.piston ? w.x : 0u;
+            a[q] = __uint_as_float(w.y) * scale;
         } else {
             px[q] = py[q] = 0;
-            chi[q] = clo[q] = 0u;
+            chi[q] = clo[q] = pist[q] = 0u;
             a[q] = 0.0f;
         }
     }
@@ -97,6 +99,8 @@ __global__ void __launch_bounds__(kFactorThreads)
     for (int r = row_begin + blockIdx.y * kRowsPerBlock; r < r_end; ++r) {
         const bool is_p = r < height;
         const int line = is_p ? r : r - height;
+        // reference phase of this row (P: ky n) or column (Q: kx m + phi0)
+        const uint32_t radd = is_p ? ref_turn(ref, 0, line) - ref.phi0 : ref_turn(ref, line, 0);
         float v[8];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(kFactorThreads)
             if (live[q]) {
                 const uint32_t d = (uint32_t)(line - (is_p ? py[q] : px[q]));
                 const uint32_t d2 = d * d;                                   // < 2^30
-                const uint32_t g = chi[q] * d2 + __umulhi(clo[q], d2);       // turn, 2^-32 units
+                const uint32_t g = chi[q] * d2 + __umulhi(clo[q], d2) + radd + (is_p ? 0u : pist[q]);   // turn
                 const float t = (float)(int)g * 2.3283064365386963e-10f;     // [-1/2, 1/2)
                 sincos_turn(t, s, c);
                 if (!is_p) {
@@ -155,10 +159,11 @@ constexpr int kTileStride = 33;   // words per slot in the shared tile: 32 rows 
 constexpr float kTurnK1 = 6.28318595886230469f;   // 0x40c90fdc
 constexpr float kTurnK0 = 9.42477893829345703f;   // 1.5 * kTurnK1, exact
 
-__device__ __forceinline__ void half_turn_sincos(uint32_t chi, uint32_t clo, uint32_t d, float &s, float &c)
+__device__ __forceinline__ void half_turn_sincos(uint32_t chi, uint32_t clo, uint32_t d, uint32_t add, float &s,
+                                                 float &c)
 {
     const uint32_t d2 = d * d;                                    // < 2^30
-    const uint32_t g = chi * d2 + 256u + __umulhi(clo, d2);      // turn in 2^-32 units, +1/2 ulp of 23 bits
+    const uint32_t g = chi * d2 + add + __umulhi(clo, d2);       // turn in 2^-32 units (add: +1/2 ulp of 23 bits, reference)
     const float f = __uint_as_float((g >> 9) | 0x3f800000u);
     __sincosf(fmaf(f, kTurnK1, -kTurnK0), &s, &c);
 }
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(kGroupThreads)
     group_factors_kernel(const int4 *__restrict__ groups, int g_begin, int n_groups, int slots,
                          const unsigned long long *__restrict__ planes, const int2 *__restrict__ members,
                          int height, int width, uint16_t *__restrict__ P, uint16_t *__restrict__ Q, long long ld,
-                         long long plane_p, long long plane_q, const float *__restrict__ wscale)
+                         long long plane_p, long long plane_q, const float *__restrict__ wscale, const PhaseRef ref)
 {
     __shared__ uint32_t tile_hi[kGroupTile * kTileStride];
     __shared__ uint32_t tile_lo[MODE == kFactorSplit16 ? kGroupTile * kTileStride : 1];
@@ -179,6 +184,9 @@ __global__ void __launch_bounds__(kGroupThreads)
     const int line = r0 + lane;
     const int s_base = blockIdx.x * kGroupTile;
     const float inv = 1.0f / *wscale;
+    // 2^8 rounds the 23-bit mantissa to nearest; plus the reference phase of this row (P': ky n)
+    // or column (Q': kx m + phi0)
+    const uint32_t add = 256u + (is_p ? ref_turn(ref, 0, line) - ref.phi0 : ref_turn(ref, line, 0));
     for (int k = warp; k < kGroupTile; k += kGroupThreads / 32) {
         const int slot = s_base + k;
         float re = 0.0f, im = 0.0f;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(kGroupThreads)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         float sn, cs;
-                        half_turn_sincos(chi, clo, (uint32_t)(line - v[q].x), sn, cs);
+                        half_turn_sincos(chi, clo, (uint32_t)(line - v[q].x), add, sn, cs);
                         re = fmaf(__int_as_float(v[q].y), cs, re);
                         im = fmaf(__int_as_float(v[q].y), sn, im);
                     }
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(kGroupThreads)
                 for (; i < d.y; ++i) {
                     const int2 v = m[i];
                     float sn, cs;
-                    half_turn_sincos(chi, clo, (uint32_t)(line - v.x), sn, cs);
+                    half_turn_sincos(chi, clo, (uint32_t)(line - v.x), add, sn, cs);
                     re = fmaf(__int_as_float(v.y), cs, re);
                     im = fmaf(__int_as_float(v.y), sn, im);
                 }
@@ -212,7 +220,7 @@ __global__ void __launch_bounds__(kGroupThreads)
                 im *= inv;
             } else {
                 float sn, cs;
-                half_turn_sincos(chi, clo, (uint32_t)(line - d.w), sn, cs);
+                half_turn_sincos(chi, clo, (uint32_t)(line - d.w), add, sn, cs);
                 re = -cs;   // cos alpha
                 im = sn;    // -sin alpha
             }
@@ -243,7 +251,8 @@ __global__ void __launch_bounds__(kGroupThreads)
 
 cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int n_groups,
                                  const unsigned long long *planes, const int2 *members, int height, int width,
-                                 void *P, void *Q, int64_t ld, const float *wscale, cudaStream_t s)
+                                 void *P, void *Q, int64_t ld, const float *wscale, cudaStream_t s,
+                                 const PhaseRef &ref)
 {
     const int slots = (int)(ld / 2);
     dim3 grid((slots + kGroupTile - 1) / kGroupTile, (height + 31) / 32 + (width + 31) / 32);
@@ -255,24 +264,25 @@ cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int 
     case kFactorF16:
         group_factors_kernel<kFactorF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, planes,
                                                                         members, height, width, p, q, ld, plane_p,
-                                                                        plane_q, wscale);
+                                                                        plane_q, wscale, ref);
         break;
     case kFactorBF16:
         group_factors_kernel<kFactorBF16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots, planes,
                                                                          members, height, width, p, q, ld, plane_p,
-                                                                         plane_q, wscale);
+                                                                         plane_q, wscale, ref);
         break;
     default:
         group_factors_kernel<kFactorSplit16><<<grid, kGroupThreads, 0, s>>>(groups, g_begin, n_groups, slots,
                                                                             planes, members, height, width, p, q, ld,
-                                                                            plane_p, plane_q, wscale);
+                                                                            plane_p, plane_q, wscale, ref);
         break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_points, int height, int width,
-                           void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s, bool imag_q_only)
+                           void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s, bool imag_q_only,
+                           const PhaseRef &ref)
 {
     const int slots = (int)(ld / 2);
     const int threads_x = (slots + 3) / 4;
@@ -286,17 +296,17 @@ cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_po
     switch (mode) {
     case kFactorF16:
         factors_kernel<kFactorF16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p, q, ld,
-                                                                   plane_p, plane_q, amp_max, row_begin, imag_q_only);
+                                                                   plane_p, plane_q, amp_max, row_begin, imag_q_only, ref);
         break;
     case kFactorBF16:
         factors_kernel<kFactorBF16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p, q,
                                                                     ld, plane_p, plane_q, amp_max, row_begin,
-                                                                    imag_q_only);
+                                                                    imag_q_only, ref);
         break;
     default:
         factors_kernel<kFactorSplit16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p,
                                                                        q, ld, plane_p, plane_q, amp_max, row_begin,
-                                                                       imag_q_only);
+                                                                       imag_q_only, ref);
         break;
     }
     return cudaGetLastError();

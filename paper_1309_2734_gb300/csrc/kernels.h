@@ -12,10 +12,40 @@ namespace cgh {
 constexpr int kPointTile = 256;
 
 // a1: per-point constants and validation (prep.cu).  amp_max (optional, zeroed
-// by the caller) receives max_j |A_j|.
+// by the caller) receives max_j |A_j|.  geo[j] = {x, y, C_hi, C_lo},
+// aux[j] = {w, A} with w per aux_x: kAuxSecondDiff: the second difference
+// 2 C_j (top 32 bits) of the recurrence; kAuxPiston: the piston
+// frac(z_j / lambda) in 2^-32 turn (the phase of Eq. 2 with its first term);
+// kAuxZero: 0 (a piston slot for kernels that add one, none wanted).  ext
+// (optional, the spherical form) receives {(p / z_j)^2, z_j / (2 lambda)}.
+enum { kAuxSecondDiff = 0, kAuxPiston = 1, kAuxZero = 2 };
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
                                double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
-                               cudaStream_t s);
+                               cudaStream_t s, int aux_x = kAuxSecondDiff, float2 *ext = nullptr);
+
+// The plane-wave reference phase of Eq. 5, phi_r(m, n) = kx m + ky n + phi0,
+// common to every point of a launch: kx, ky in 2^-64 turn per pixel, phi0 in
+// 2^-32 turn; piston: the points were prepared with their piston in aux.x.
+// All zero: the restricted phase of Eq. 5.
+struct PhaseRef {
+    unsigned long long kx = 0, ky = 0;
+    uint32_t phi0 = 0;
+    uint32_t piston = 0;
+    bool any() const { return kx != 0 || ky != 0 || phi0 != 0 || piston != 0; }
+};
+
+#ifdef __CUDACC__
+// phi_r at pixel (m, n) >= 0, top 32 bits of the 64-bit fixed point, plus phi0.
+__device__ __forceinline__ uint32_t ref_turn(const PhaseRef &r, int m, int n)
+{
+    return (uint32_t)((r.kx * (unsigned long long)m + r.ky * (unsigned long long)n) >> 32) + r.phi0;
+}
+// Its change per column (per row): kx (ky) rounded to 2^-32 turn.
+__device__ __forceinline__ uint32_t ref_step(unsigned long long k)
+{
+    return (uint32_t)((k >> 32) + ((k >> 31) & 1ull));
+}
+#endif
 
 // a2: direct kernel (direct.cu).
 struct DirectShape {
@@ -27,14 +57,23 @@ DirectShape direct_shape(bool sfu);
 // so its bounded wait runs out and the launch ends with kStatusTimeout.
 cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
                           int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
-                          cudaStream_t s, int drop_tile = -1);
+                          cudaStream_t s, int drop_tile = -1, const PhaseRef &ref = PhaseRef());
 
 // Complex object wave (Eq. 2, restricted form), SFU form: real part at out,
 // imaginary part at out + im_offset; point chunk s at out + s * slice_stride.
 DirectShape direct_wave_shape();
 cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int width, int height, int split,
                                float *out, int64_t slice_stride, int64_t im_offset, int *status,
-                               uint64_t timeout_ns, cudaStream_t s);
+                               uint64_t timeout_ns, cudaStream_t s, const PhaseRef &ref = PhaseRef());
+
+// f2: the exact spherical wave of Eq. 1 (spherical.cu), direct SFU form.
+// Points prepared with the piston and ext.  planes = 1: the amplitude
+// hologram (Eq. 5, middle line) at out; planes = 2: the complex wave, real part
+// at out and imaginary part at out + im_offset.  Point chunk s at out + s * slice_stride.
+DirectShape spherical_shape();
+cudaError_t launch_spherical(const int4 *geo, const uint2 *aux, const float2 *ext, int n_pad, int width, int height,
+                             int split, int planes, float *out, int64_t slice_stride, int64_t im_offset,
+                             const PhaseRef &ref, cudaStream_t s);
 
 // a7: one job (hologram) of a batched direct launch; units are {job, pixel tile}.
 struct DirectJob {
@@ -52,9 +91,11 @@ int direct_ctas_per_sm();
 // amp_max (optional) scales Q by 1 / max|A|.
 enum { kFactorF16 = 0, kFactorBF16 = 1, kFactorSplit16 = 2 };
 // imag_q_only: write only Q' (the factor of the imaginary part) into Q.
+// The reference phase goes to both factors (ky n into P, kx m + phi0 into Q),
+// the piston (aux.x) into Q.
 cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_points, int height, int width,
                            void *P, void *Q, int64_t ld, const float *amp_max, cudaStream_t s,
-                           bool imag_q_only = false);
+                           bool imag_q_only = false, const PhaseRef &ref = PhaseRef());
 
 // Grouped GEMM form (groups.cu, factors.cu).  Groups: points with the same
 // plane constant C and the same column x.  meta (device, 4 ints): [0] planes
@@ -74,7 +115,8 @@ cudaError_t launch_group_build(const int4 *geo, const uint2 *aux, int n, int n_p
                                int2 *members, cudaStream_t s);
 cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int n_groups,
                                  const unsigned long long *planes, const int2 *members, int height, int width,
-                                 void *P, void *Q, int64_t ld, const float *wscale, cudaStream_t s);
+                                 void *P, void *Q, int64_t ld, const float *wscale, cudaStream_t s,
+                                 const PhaseRef &ref = PhaseRef());
 
 // a4: tcgen05 GEMM, out[n][m] (+)= sum_k P[n][k] Q[m][k] over K splits (gemm.cu).
 struct GemmPlan {

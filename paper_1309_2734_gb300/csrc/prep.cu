@@ -7,7 +7,9 @@
 // stored as the 64-bit fixed-point C_j = round(frac(c_j) 2^64).  Every phase
 // the kernels form is then C_j * (integer) mod 2^64, exact up to C_j's own
 // rounding (<= 2^-65 turn per px^2, i.e. < 2^-33 turn for r^2 < 2^32).
-// FP64 is used only here, O(N) work.
+// FP64 is used only here, O(N) work.  With the piston of Eq. 2 the point
+// carries frac(z_j / lambda) (the phase 2 pi z_j / lambda in turns) in place of
+// the second difference, which the kernels then form from C_j itself.
 #include "device_util.cuh"
 #include "kernels.h"
 
@@ -15,10 +17,12 @@ namespace cgh {
 
 __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *__restrict__ amp, int n,
                                    int n_pad, double pitch, double lambda, int4 *__restrict__ geo,
-                                   uint2 *__restrict__ aux, int *status, float *amp_max)
+                                   uint2 *__restrict__ aux, int *status, float *amp_max, int aux_x,
+                                   float2 *__restrict__ ext)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
+    if (ext != nullptr) ext[j] = make_float2(0.0f, 0.0f);
     if (j >= n) {  // padding: zero amplitude, zero phase
         geo[j] = make_int4(0, 0, 0, 0);
         aux[j] = make_uint2(0u, 0u);
@@ -40,20 +44,29 @@ __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *_
     const double scaled = ldexp(fr, 64);                              // exact power-of-two scaling
     unsigned long long C = (scaled >= 18446744073709551616.0) ? 0ull : __double2ull_rn(scaled);
     geo[j] = make_int4((int)fx, (int)fy, (int)(unsigned)(C >> 32), (int)(unsigned)(C & 0xffffffffull));
-    const unsigned delta = (unsigned)((C << 1) >> 32);   // second difference 2 c_j, top 32 bits
-    aux[j] = make_uint2(delta, __float_as_uint(a));
+    unsigned w = aux_x == kAuxSecondDiff ? (unsigned)((C << 1) >> 32) : 0u;   // 2 c_j, top 32 bits
+    if (aux_x == kAuxPiston) {   // frac(z / lambda) in 2^-32 turn (within ~2^-32 turn while z / lambda < 2^21)
+        const double zt = (double)fz / lambda;
+        const double pf = ldexp(zt - floor(zt), 32);
+        w = pf >= 4294967295.5 ? 0u : (unsigned)__double2ull_rn(pf);
+    }
+    aux[j] = make_uint2(w, __float_as_uint(a));
+    if (ext != nullptr) {
+        const double pz = pitch / (double)fz;
+        ext[j] = make_float2((float)(pz * pz), (float)((double)fz / (2.0 * lambda)));
+    }
     if (amp_max != nullptr) atomicMax(reinterpret_cast<unsigned *>(amp_max), __float_as_uint(fabsf(a)));
 }
 
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
                                double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
-                               cudaStream_t s)
+                               cudaStream_t s, int aux_x, float2 *ext)
 {
     if (n_pad <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (n_pad + threads - 1) / threads;
     prep_points_kernel<<<blocks, threads, 0, s>>>(d_xyz, d_amp, n, n_pad, pitch, lambda, geo, aux, status,
-                                                         amp_max);
+                                                         amp_max, aux_x, ext);
     return cudaGetLastError();
 }
 

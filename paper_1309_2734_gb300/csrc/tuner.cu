@@ -274,11 +274,14 @@ double time_form(cgh_ctx *ctx, int form, int bn, int width, int height, int64_t 
     }
     cudaMemcpy(s.xyz, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(s.amp, ha.data(), ha.size() * sizeof(float), cudaMemcpyHostToDevice);
-    const int saved_form = ctx->form, saved_bn = ctx->gemm_bn;
+    const int saved_form = ctx->form, saved_bn = ctx->gemm_bn, saved_model = ctx->phase_model;
+    const int saved_group = ctx->gemm_group;
     const bool saved_profile = ctx->profile;
     ctx->form = form;
     ctx->gemm_bn = bn;
     ctx->profile = false;
+    ctx->phase_model = CGH_PHASE_FRESNEL;   // the forms' own cost; the piston and reference add none per term
+    ctx->gemm_group = 1;                    // synthetic depths are continuous: no grouping
     double sec = -1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
@@ -298,6 +301,8 @@ double time_form(cgh_ctx *ctx, int form, int bn, int width, int height, int64_t 
     if (e1) cudaEventDestroy(e1);
     ctx->form = saved_form;
     ctx->gemm_bn = saved_bn;
+    ctx->phase_model = saved_model;
+    ctx->gemm_group = saved_group;
     ctx->profile = saved_profile;
     return sec;
 }
