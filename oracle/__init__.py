@@ -17,6 +17,9 @@ wraps it with ctypes.  Every function cites the passage it follows:
   quantise a phase with 255/(2 pi); this is the amplitude counterpart).
 * ``kinoform8``: that phase rule for the kinoform of Eq. 3.
 * ``recurrence_phases``: Eqs. 6-8 (Section 2.2) iterated in exact rationals.
+* ``fresnel_at``/``fresnel``: Fresnel diffraction, Eq. 10 (definition; and
+  by numpy FFT); ``wrp_record``/``wrp``: the wavefront-recording method of
+  Section 2.3.
 * ``model_wave``/``model_wave_at``: the phase models of Eq. 1 (exact spherical
   wave), Eq. 2 with and without the piston, and the plane-wave reference phase
   of Eqs. 4-5; the amplitude hologram is the real part.
@@ -78,6 +81,12 @@ def _load():
                                                 ctypes.c_double, ctypes.c_double, _F32P, _F32P, ctypes.c_int64,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _F64P,
                                                 _F64P]
+            lib.oracle_fresnel_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, _F64P, _F64P, _I32P, _I32P, ctypes.c_int64,
+                                                  _F64P, _F64P]
+            lib.oracle_wrp_record.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              _F32P, _F32P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int, _F64P, _F64P]
             lib.oracle_model_points.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_double, _F32P, _F32P, ctypes.c_int64,
                                                 _I32P, _I32P, ctypes.c_int64, _F64P, _F64P]
@@ -197,6 +206,83 @@ def model_wave_at(model: int, pitch_m: float, lambda_m: float, xyz, amp, cols, r
     if rc != 0:
         raise ValueError("oracle_model_points rejected its arguments")
     return re + 1j * im
+
+
+def _fresnel_prefactor(pitch_m: float, lambda_m: float, z_m: float) -> complex:
+    """exp(i 2 pi z / lambda) / (i lambda z) * p^2 of Eq. 10 (the cell area p^2 turns the integral into a sum)."""
+    zt = z_m / lambda_m
+    a0 = 2 * np.pi * (zt - np.rint(zt))
+    return np.exp(1j * a0) * (-1j) * pitch_m * pitch_m / (lambda_m * z_m)
+
+
+def fresnel_at(u, pitch_m: float, lambda_m: float, z_m: float, cols, rows) -> np.ndarray:
+    """Fresnel diffraction (Eq. 10) of the complex plane u [H][W] by z at scattered pixels, by its definition:
+    O(m, n) = pre * sum_{m', n'} u(m', n') exp(i pi p^2 ((m - m')^2 + (n - n')^2) / (lambda z))."""
+    u = np.asarray(u)
+    H, W = u.shape
+    ur = np.ascontiguousarray(u.real, dtype=np.float64)
+    ui = np.ascontiguousarray(u.imag, dtype=np.float64)
+    pm = np.ascontiguousarray(cols, dtype=np.int32)
+    pn = np.ascontiguousarray(rows, dtype=np.int32)
+    re = np.empty(pm.shape[0], dtype=np.float64)
+    im = np.empty(pm.shape[0], dtype=np.float64)
+    rc = _load().oracle_fresnel_points(W, H, float(pitch_m), float(lambda_m), float(z_m), _ptr(ur, _F64P),
+                                       _ptr(ui, _F64P), _ptr(pm, _I32P), _ptr(pn, _I32P), pm.shape[0],
+                                       _ptr(re, _F64P), _ptr(im, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_fresnel_points rejected its arguments")
+    return re + 1j * im
+
+
+def fresnel(u, pitch_m: float, lambda_m: float, z_m: float) -> np.ndarray:
+    """The same sum for every pixel: the linear convolution with the chirp evaluated by zero-padding to
+    2H x 2W and numpy's complex128 FFT (a library step; pinned against fresnel_at), cropped to H x W."""
+    u = np.asarray(u, dtype=np.complex128)
+    H, W = u.shape
+    n = np.arange(2 * H, dtype=np.int64)
+    n = np.where(n < H, n, n - 2 * H)
+    m = np.arange(2 * W, dtype=np.int64)
+    m = np.where(m < W, m, m - 2 * W)
+    c = pitch_m * pitch_m / (2.0 * lambda_m * z_m)
+    t = c * (n[:, None] ** 2 + m[None, :] ** 2).astype(np.float64)
+    h = np.exp(2j * np.pi * (t - np.rint(t)))
+    pad = np.zeros((2 * H, 2 * W), dtype=np.complex128)
+    pad[:H, :W] = u
+    out = np.fft.ifft2(np.fft.fft2(pad) * np.fft.fft2(h))[:H, :W]
+    return out * _fresnel_prefactor(pitch_m, lambda_m, z_m)
+
+
+def wrp_window2(pitch_m: float, lambda_m: float, d_m: float) -> float:
+    """floor(w^2), w = d s / sqrt(1 - s^2) / p, s = lambda / (2 p): the squared window radius in pixels
+    (each operation rounded to double, as in the C oracle)."""
+    s = lambda_m / (2.0 * pitch_m)
+    w = ((d_m * s) / float(np.sqrt(1.0 - s * s))) / pitch_m
+    return float(np.floor(w * w))
+
+
+def wrp_record(model: int, pitch_m: float, lambda_m: float, z_wrp_m: float, xyz, amp, width: int, height: int,
+               window: Optional[Sequence[int]] = None) -> np.ndarray:
+    """WRP step 1 (Section 2.3): the windowed complex sum on the virtual plane at distance z_wrp from the
+    hologram, model 0 or 1 at each point's distance d_j = z_j - z_wrp; complex128 [rows][cols]."""
+    xyz = _f32(xyz).reshape(-1, 3)
+    amp = _f32(amp).reshape(-1)
+    if window is None:
+        window = (0, 0, height, width)
+    r0, c0, rows, cols = (int(v) for v in window)
+    re = np.empty((rows, cols), dtype=np.float64)
+    im = np.empty((rows, cols), dtype=np.float64)
+    rc = _load().oracle_wrp_record(int(model), float(pitch_m), float(lambda_m), float(z_wrp_m), _ptr(xyz, _F32P),
+                                   _ptr(amp, _F32P), amp.shape[0], r0, rows, c0, cols, _ptr(re, _F64P),
+                                   _ptr(im, _F64P))
+    if rc != 0:
+        raise ValueError("oracle_wrp_record rejected its arguments")
+    return re + 1j * im
+
+
+def wrp(model: int, pitch_m: float, lambda_m: float, z_wrp_m: float, xyz, amp, width: int, height: int) -> np.ndarray:
+    """The wavefront-recording method (Section 2.3): wrp_record, then Fresnel diffraction by z_wrp."""
+    u = wrp_record(model, pitch_m, lambda_m, z_wrp_m, xyz, amp, width, height)
+    return fresnel(u, pitch_m, lambda_m, z_wrp_m)
 
 
 def factors(pitch_m: float, lambda_m: float, xyz, amp, width: int, height: int):

@@ -242,6 +242,107 @@ int oracle_model_points(int model, double pitch, double lambda, double sin_x, do
 }
 
 /*
+ * Fresnel diffraction, Eq. 10, by its definition on the pixel grid: the input
+ * plane u (height x width, pitch p) is propagated by z (metres, either sign)
+ * onto a plane of the same grid,
+ *   O(m, n) = exp(i 2 pi z / lambda) / (i lambda z) * p^2
+ *             * sum_{m', n'} u(m', n') exp(i pi p^2 ((m - m')^2 + (n - n')^2) / (lambda z)),
+ * the integral over the input plane as a sum of cells of area p^2 (the output
+ * is the linear convolution, cropped to the input's extent).  The chirp's
+ * phase is c ((m - m')^2 + (n - n')^2) turns with c = p^2 / (2 lambda z),
+ * reduced in turns; out at npix scattered pixels (pm[i], pn[i]).
+ */
+int oracle_fresnel_points(int width, int height, double pitch, double lambda, double z, const double *in_re,
+                          const double *in_im, const int32_t *pm, const int32_t *pn, int64_t npix, double *out_re,
+                          double *out_im)
+{
+    if (width < 1 || height < 1 || npix < 0 || z == 0.0 || !in_re || !in_im || !out_re || !out_im) return -1;
+    const double c = pitch * pitch / (2.0 * lambda * z);
+    const double zt = z / lambda;
+    const double a0 = TWO_PI * (zt - rint(zt));
+    /* exp(i a0) / (i lambda z) * p^2 = exp(i a0) * (-i) * p^2 / (lambda z) */
+    const double s = pitch * pitch / (lambda * z);
+    const double pre_re = s * sin(a0), pre_im = -s * cos(a0);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < npix; ++i) {
+        double sr = 0.0, si = 0.0;
+        for (int n2 = 0; n2 < height; ++n2) {
+            const double dy = (double)pn[i] - (double)n2;
+            for (int m2 = 0; m2 < width; ++m2) {
+                const double dx = (double)pm[i] - (double)m2;
+                const double a = reduced_angle(c * (dx * dx + dy * dy));
+                const double hr = cos(a), hi = sin(a);
+                const double ur = in_re[(int64_t)n2 * width + m2], ui = in_im[(int64_t)n2 * width + m2];
+                sr += ur * hr - ui * hi;
+                si += ur * hi + ui * hr;
+            }
+        }
+        out_re[i] = pre_re * sr - pre_im * si;
+        out_im[i] = pre_re * si + pre_im * sr;
+    }
+    return 0;
+}
+
+/*
+ * The window of the wavefront-recording method (Section 2.3): the light of a
+ * point at distance d = z_j - z_wrp behind the virtual plane that can reach
+ * the hologram within the grid's largest diffraction angle, sin(theta) =
+ * lambda / (2 p), crosses the plane within radius d tan(theta).  In pixels,
+ * w = d s / sqrt(1 - s^2) / p with s = lambda / (2 p), and the window holds the
+ * pixels with (m - x_j)^2 + (n - y_j)^2 <= floor(w^2).  Each operation is
+ * rounded on its own (double), so that any IEEE implementation draws the
+ * same integer boundary.
+ */
+static double wrp_window2(double pitch, double lambda, double d)
+{
+    volatile double s = lambda / (2.0 * pitch);
+    volatile double s2 = s * s;
+    volatile double one_m = 1.0 - s2;
+    volatile double den = sqrt(one_m);
+    volatile double ds = d * s;
+    volatile double t = ds / den;
+    volatile double w = t / pitch;
+    volatile double w2 = w * w;
+    return floor(w2);
+}
+
+/*
+ * WRP step 1 (Section 2.3): the complex amplitude recorded on the virtual
+ * plane at distance z_wrp from the hologram, each point summed over its window
+ * only, with phase model 0 or 1 of model_turn (Eq. 2 without or with the
+ * piston) at the point's distance d_j = z_j - z_wrp > 0 from the plane:
+ *   u(m, n) = sum_{j: r2 <= W2_j} A_j exp(i 2 pi t_j(d_j)).
+ * Returns -1 if a point is not behind the plane (d_j <= 0).
+ */
+int oracle_wrp_record(int model, double pitch, double lambda, double z_wrp, const float *xyz, const float *amp,
+                      int64_t npts, int row0, int rows, int col0, int cols, double *re, double *im)
+{
+    if (model < 0 || model > 1 || rows < 0 || cols < 0 || npts < 0 || !re || !im) return -1;
+    for (int64_t j = 0; j < npts; ++j)
+        if (!((double)xyz[3 * j + 2] - z_wrp > 0.0)) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < rows; ++r)
+        for (int q = 0; q < cols; ++q) {
+            const double m = (double)(col0 + q), n_row = (double)(row0 + r);
+            double sr = 0.0, si = 0.0;
+            for (int64_t j = 0; j < npts; ++j) {
+                const double d = (double)xyz[3 * j + 2] - z_wrp;
+                const double dx = m - (double)xyz[3 * j + 0], dy = n_row - (double)xyz[3 * j + 1];
+                if (dx * dx + dy * dy > wrp_window2(pitch, lambda, d)) continue;
+                const double r2 = (dx * dx + dy * dy) * pitch * pitch;
+                double t = r2 / (2.0 * lambda * d);
+                if (model == 1) t += d / lambda;
+                const double a = reduced_angle(t);
+                sr += (double)amp[j] * cos(a);
+                si += (double)amp[j] * sin(a);
+            }
+            re[(int64_t)r * cols + q] = sr;
+            im[(int64_t)r * cols + q] = si;
+        }
+    return 0;
+}
+
+/*
  * Separable factors: P is [height][2 npts], Q is [width][2 npts] (row-major),
  * with the interleaving described in the header comment.
  */

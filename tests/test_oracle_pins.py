@@ -443,3 +443,78 @@ def test_model_points_match_window():
     cols, rows = np.array([0, 15, 7, 3]), np.array([0, 11, 5, 9])
     at = oracle.model_wave_at(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows, reference=ref)
     assert np.array_equal(at, w[rows, cols])
+
+
+# ---- Fresnel diffraction (Eq. 10) and the wavefront-recording method (Section 2.3) ----
+
+def test_fresnel_fft_equals_definition():
+    """The numpy-FFT convolution (zero-padded to 2H x 2W) equals the direct sum of Eq. 10 on every pixel."""
+    rng = np.random.default_rng(60)
+    for (H, W, z) in ((20, 24, 0.05), (17, 9, -0.2), (1, 13, 0.01)):
+        u = rng.standard_normal((H, W)) + 1j * rng.standard_normal((H, W))
+        full = oracle.fresnel(u, P8, L532, z)
+        m, n = np.meshgrid(np.arange(W), np.arange(H))
+        direct = oracle.fresnel_at(u, P8, L532, z, m.ravel(), n.ravel()).reshape(H, W)
+        assert np.allclose(full, direct, atol=1e-9 * np.abs(direct).max(), rtol=0)
+
+
+def test_fresnel_gaussian_beam_closed_form():
+    """A Gaussian beam exp(-r^2/w0^2) propagated by z has the closed form
+    exp(i 2 pi z/lambda)/(i lambda z) * pi/(a - i b) * exp(i b r^2 - b^2 r^2/(a - i b)), a = 1/w0^2, b = pi/(lambda z)
+    (the Gaussian integral); the grid sum with cells p^2 converges to it (w0 = 20 px, 200 x 200 grid)."""
+    N, w0, z = 200, 20 * P8, 0.1
+    yy, xx = np.meshgrid((np.arange(N) - N // 2) * P8, (np.arange(N) - N // 2) * P8, indexing="ij")
+    u = np.exp(-(xx ** 2 + yy ** 2) / w0 ** 2)
+    got = oracle.fresnel(u, P8, L532, z)
+    a, b = 1.0 / w0 ** 2, math.pi / (L532 * z)
+    zt = Fraction(z) / Fraction(L532)
+    pre = np.exp(2j * math.pi * float(zt - round(zt))) / (1j * L532 * z)
+    r2 = xx ** 2 + yy ** 2
+    want = pre * (math.pi / (a - 1j * b)) * np.exp(1j * b * r2 - b * b * r2 / (a - 1j * b))
+    core = r2 <= (40 * P8) ** 2
+    err = np.abs(got - want)[core].max()
+    assert err <= 1e-8 * np.abs(want).max(), err
+    # a slip of the area element, the prefactor or the sign of the chirp is far larger
+    assert np.abs(np.conj(got) - want)[core].max() > 1e-2 * np.abs(want).max()
+
+
+def test_fresnel_translation_and_linearity():
+    rng = np.random.default_rng(61)
+    u = np.zeros((30, 30), complex)
+    u[5:12, 6:14] = rng.standard_normal((7, 8)) + 1j * rng.standard_normal((7, 8))
+    v = np.roll(np.roll(u, 9, axis=0), 7, axis=1)          # stays inside the plane
+    fu, fv = oracle.fresnel(u, P8, L532, 0.03), oracle.fresnel(v, P8, L532, 0.03)
+    assert np.allclose(fv[9:, 7:], fu[:-9, :-7], atol=1e-10 * np.abs(fu).max())
+    w = oracle.fresnel(2.0 * u - 1j * v, P8, L532, 0.03)
+    assert np.allclose(w, 2.0 * fu - 1j * fv, atol=1e-10 * np.abs(w).max())
+
+
+def test_wrp_window_is_the_lattice_disk():
+    """One point: the recorded plane is nonzero exactly on the integer points of the disk r^2 <= floor(w^2),
+    w = d tan(asin(lambda / 2p)) / p, and equals there the point's wave at depth d (model_wave, pinned above)."""
+    z_wrp, d = 0.4, 0.006
+    xyz, amp = _cloud([[40.0, 37.0, z_wrp + d]], [0.9])
+    u = oracle.wrp_record(1, P8, L532, z_wrp, xyz, amp, 90, 80)
+    w = d * math.tan(math.asin(L532 / (2 * P8))) / P8
+    W2 = oracle.wrp_window2(P8, L532, float(np.float64(xyz[0, 2]) - z_wrp))
+    assert abs(W2 - math.floor(w * w)) <= 1            # same radius, up to the last rounding
+    mm, nn = np.meshgrid(np.arange(90), np.arange(80))
+    disk = (mm - 40) ** 2 + (nn - 37) ** 2 <= W2
+    count = sum(1 for dx in range(-60, 61) for dy in range(-60, 61) if dx * dx + dy * dy <= W2)
+    assert np.count_nonzero(u) == disk.sum() == count
+    # inside: the quadratic phase at distance d (model 0 at a float32 depth of d: relative 1e-8 of a few turns)
+    shifted = xyz.copy()
+    shifted[0, 2] = np.float32(np.float64(xyz[0, 2]) - z_wrp)
+    u0 = oracle.wrp_record(0, P8, L532, z_wrp, xyz, amp, 90, 80)
+    ref0 = oracle.model_wave(0, P8, L532, shifted, amp, 90, 80)
+    assert np.allclose(u0[disk], ref0[disk], atol=1e-6)
+    # and the piston is that of d = z_j - z_wrp, exactly
+    dt = (Fraction(float(xyz[0, 2])) - Fraction(z_wrp)) / Fraction(L532)
+    rot = np.exp(2j * math.pi * float(dt - round(dt)))
+    assert np.allclose(u[disk], u0[disk] * rot, atol=1e-9)
+
+
+def test_wrp_rejects_points_in_front_of_the_plane():
+    xyz, amp = _cloud([[3.0, 3.0, 0.2]])
+    with pytest.raises(ValueError):
+        oracle.wrp_record(0, P8, L532, 0.3, xyz, amp, 8, 8)
