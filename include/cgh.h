@@ -147,6 +147,41 @@ int cgh_set_stream(cgh_ctx *ctx, void *cuda_stream);
  */
 int cgh_set_reference(cgh_ctx *ctx, double sin_x, double sin_y, double phase0_rad);
 
+/*
+ * Fresnel diffraction, Eq. 10 (Section 2.3): propagates the complex plane d_in
+ * by z_m (metres, nonzero, either sign) onto d_out, both [2][H][W] float32
+ * (real plane, then imaginary plane; the context's width W x height H, pitch
+ * p), device memory; d_out may equal d_in.  The integral is the sum over cells
+ * of area p^2 with the prefactor exp(i 2 pi z / lambda) / (i lambda z):
+ *   O(m, n) = exp(i 2 pi z/lambda)/(i lambda z) p^2 sum u(m', n') exp(i pi p^2 ((m-m')^2 + (n-n')^2)/(lambda z)),
+ * evaluated as the paper does by zero-padding to 2H x 2W, FFT (cuFFT, single
+ * precision), product with the chirp's spectrum (cached per z), inverse FFT and
+ * crop.  Allocates 2 x 4 W H complex words and a cuFFT plan on first use.
+ */
+int cgh_fresnel(cgh_ctx *ctx, const float *d_in, double z_m, float *d_out);
+
+/*
+ * The wavefront-recording method (Section 2.3), step 1: records the point
+ * cloud's complex amplitude on a virtual plane at distance z_wrp_m (> 0) from
+ * the hologram, on the hologram's grid, into d_plane ([2][H][W], device).
+ * Each point (z_j > z_wrp_m, else CGH_EINPUT) contributes only inside its
+ * window, the pixels within d tan(asin(lambda/2p)) / p of (x_j, y_j) with
+ * d = z_j - z_wrp_m (the squared radius floored to an integer), with the
+ * phase of Eq. 2 at distance d: without the piston (CGH_PHASE_FRESNEL) or with
+ * it (CGH_PHASE_FRESNEL_PISTON).  CGH_ENOTSUP for CGH_PHASE_SPHERICAL or with
+ * a reference wave set.
+ */
+int cgh_wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, double z_wrp_m,
+                   float *d_plane);
+
+/*
+ * The wavefront-recording method, both steps: cgh_wrp_record, then Fresnel
+ * diffraction (cgh_fresnel) by z_wrp_m onto the hologram: the complex object
+ * wave at d_out ([2][H][W], device); cgh_quantize8 with CGH_Q_PHASE turns it
+ * into the kinoform of Eq. 3.
+ */
+int cgh_wrp(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, double z_wrp_m, float *d_out);
+
 /* Selects the form (CGH_FORM_* above). */
 int cgh_set_form(cgh_ctx *ctx, int form);
 

@@ -320,6 +320,10 @@ int oracle_wrp_record(int model, double pitch, double lambda, double z_wrp, cons
     if (model < 0 || model > 1 || rows < 0 || cols < 0 || npts < 0 || !re || !im) return -1;
     for (int64_t j = 0; j < npts; ++j)
         if (!((double)xyz[3 * j + 2] - z_wrp > 0.0)) return -1;
+    /* the window of each point, once */
+    double *w2 = (double *)malloc(sizeof(double) * (size_t)(npts > 0 ? npts : 1));
+    if (!w2) return -1;
+    for (int64_t j = 0; j < npts; ++j) w2[j] = wrp_window2(pitch, lambda, (double)xyz[3 * j + 2] - z_wrp);
     #pragma omp parallel for schedule(dynamic, 1)
     for (int r = 0; r < rows; ++r)
         for (int q = 0; q < cols; ++q) {
@@ -328,7 +332,7 @@ int oracle_wrp_record(int model, double pitch, double lambda, double z_wrp, cons
             for (int64_t j = 0; j < npts; ++j) {
                 const double d = (double)xyz[3 * j + 2] - z_wrp;
                 const double dx = m - (double)xyz[3 * j + 0], dy = n_row - (double)xyz[3 * j + 1];
-                if (dx * dx + dy * dy > wrp_window2(pitch, lambda, d)) continue;
+                if (dx * dx + dy * dy > w2[j]) continue;
                 const double r2 = (dx * dx + dy * dy) * pitch * pitch;
                 double t = r2 / (2.0 * lambda * d);
                 if (model == 1) t += d / lambda;
@@ -339,6 +343,7 @@ int oracle_wrp_record(int model, double pitch, double lambda, double z_wrp, cons
             re[(int64_t)r * cols + q] = sr;
             im[(int64_t)r * cols + q] = si;
         }
+    free(w2);
     return 0;
 }
 

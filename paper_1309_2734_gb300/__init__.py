@@ -105,6 +105,47 @@ class Hologram:
                                  out.data_ptr()), "cgh_wave")
         return out
 
+    def _planes_out(self, out):
+        import torch
+        if out is None:
+            out = torch.empty((2, self.height, self.width), dtype=torch.float32, device=self.device)
+        _need_cuda_tensor(out, "out", torch.float32)
+        if out.numel() != 2 * self.width * self.height:
+            raise ValueError("out must hold 2 * height * width floats")
+        return out
+
+    def fresnel(self, plane, z_m: float, out=None):
+        """Fresnel diffraction (Eq. 10) of a complex plane [2][height][width] by z_m metres."""
+        import torch
+        _need_cuda_tensor(plane, "plane", torch.float32)
+        if plane.numel() != 2 * self.width * self.height:
+            raise ValueError("plane must hold 2 * height * width floats")
+        out = self._planes_out(out)
+        _lib.check(_lib.cgh_fresnel(self.ctx, plane.data_ptr(), float(z_m), out.data_ptr()), "cgh_fresnel")
+        return out
+
+    def wrp_record(self, xyz, amp, z_wrp_m: float, out=None):
+        """Wavefront-recording method, step 1: the windowed complex sum on the plane at z_wrp_m (Section 2.3)."""
+        import torch
+        _need_cuda_tensor(xyz, "xyz", torch.float32)
+        _need_cuda_tensor(amp, "amp", torch.float32)
+        n = int(amp.numel())
+        out = self._planes_out(out)
+        _lib.check(_lib.cgh_wrp_record(self.ctx, xyz.data_ptr() if n else 0, amp.data_ptr() if n else 0, n,
+                                       float(z_wrp_m), out.data_ptr()), "cgh_wrp_record")
+        return out
+
+    def wrp(self, xyz, amp, z_wrp_m: float, out=None):
+        """Wavefront-recording method: the complex object wave on the hologram, [2][height][width]."""
+        import torch
+        _need_cuda_tensor(xyz, "xyz", torch.float32)
+        _need_cuda_tensor(amp, "amp", torch.float32)
+        n = int(amp.numel())
+        out = self._planes_out(out)
+        _lib.check(_lib.cgh_wrp(self.ctx, xyz.data_ptr() if n else 0, amp.data_ptr() if n else 0, n,
+                                float(z_wrp_m), out.data_ptr()), "cgh_wrp")
+        return out
+
     def kinoform8(self, wave, out=None):
         """Phase-only 8-bit hologram of a complex wave [2][...] (Eq. 3, the listings' 255/(2 pi) rule)."""
         import torch

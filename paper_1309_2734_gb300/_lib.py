@@ -37,7 +37,7 @@ CGH_PHASE_FRESNEL, CGH_PHASE_FRESNEL_PISTON, CGH_PHASE_SPHERICAL = 0, 1, 2
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
            "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
-           "cgh_autotune", "cgh_wave", "cgh_set_reference")
+           "cgh_autotune", "cgh_wave", "cgh_set_reference", "cgh_fresnel", "cgh_wrp_record", "cgh_wrp")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -92,6 +92,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_autotune": ([vp, ci], ci),
             "cgh_wave": ([vp, vp, vp, i64, vp], ci),
             "cgh_set_reference": ([vp, cd, cd, cd], ci),
+            "cgh_fresnel": ([vp, vp, cd, vp], ci),
+            "cgh_wrp_record": ([vp, vp, vp, i64, cd, vp], ci),
+            "cgh_wrp": ([vp, vp, vp, i64, cd, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -175,6 +178,18 @@ def cgh_profile_read(ctx: int, reset: bool = True) -> dict:
 
 def cgh_wave(ctx: int, d_xyz: int, d_amp: int, n_points: int, d_out: int) -> int:
     return load().cgh_wave(ctx, d_xyz, d_amp, int(n_points), d_out)
+
+
+def cgh_fresnel(ctx: int, d_in: int, z_m: float, d_out: int) -> int:
+    return load().cgh_fresnel(ctx, d_in, float(z_m), d_out)
+
+
+def cgh_wrp_record(ctx: int, d_xyz: int, d_amp: int, n_points: int, z_wrp_m: float, d_plane: int) -> int:
+    return load().cgh_wrp_record(ctx, d_xyz, d_amp, int(n_points), float(z_wrp_m), d_plane)
+
+
+def cgh_wrp(ctx: int, d_xyz: int, d_amp: int, n_points: int, z_wrp_m: float, d_out: int) -> int:
+    return load().cgh_wrp(ctx, d_xyz, d_amp, int(n_points), float(z_wrp_m), d_out)
 
 
 def cgh_autotune(ctx: int, force: bool = False) -> int:

@@ -70,7 +70,10 @@ def build(force: bool = False, ptxas_verbose: bool = False, jobs: int = 0) -> st
             sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+    # cuFFT (Fresnel diffraction) from the toolkit next to nvcc, found again at run time through the rpath
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L", cuda_lib, "-lcufft", "-lpthread",
+                                                         "-Xlinker", f"-rpath,{cuda_lib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

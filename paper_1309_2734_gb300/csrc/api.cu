@@ -449,6 +449,93 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
     return cuda_status(e);
 }
 
+// Fresnel diffraction state of the context: the cuFFT plan of the 2H x 2W grid
+// and two padded planes (work plane and the chirp's spectrum), made on first use.
+int ensure_fft(cgh_ctx *ctx)
+{
+    if (ctx->fft_plan) return CGH_OK;
+    const size_t bytes = (size_t)4 * ctx->width * ctx->height * sizeof(float2);
+    if (cudaMalloc(&ctx->fft_pad, bytes) != cudaSuccess || cudaMalloc(&ctx->fft_spec, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->fft_pad) cudaFree(ctx->fft_pad);
+        if (ctx->fft_spec) cudaFree(ctx->fft_spec);
+        ctx->fft_pad = ctx->fft_spec = nullptr;
+        return CGH_ENOMEM;
+    }
+    if (!fft_plan_2d(2 * ctx->height, 2 * ctx->width, &ctx->fft_plan, ctx->stream)) {
+        ctx->fft_plan = nullptr;
+        return CGH_ECUDA;
+    }
+    ctx->fft_spec_z = 0.0;
+    return CGH_OK;
+}
+
+// The padded work plane (holding the expanded input) propagated by z and
+// cropped into d_out ([2][H][W]).  The chirp's spectrum carries the prefactor
+// exp(i 2 pi z / lambda) / (i lambda z) p^2 and the inverse transform's
+// 1 / (4 H W); it is kept for the next call with the same z.
+int fresnel_padded(cgh_ctx *ctx, double z, float *d_out)
+{
+    const int H = ctx->height, W = ctx->width;
+    cudaError_t e = cudaSuccess;
+    if (ctx->fft_spec_z != z) {
+        const double zt = z / ctx->lambda;
+        const double a0 = 6.283185307179586476925286766559 * (zt - std::rint(zt));
+        const double s = ctx->pitch * ctx->pitch / (ctx->lambda * z) / (4.0 * (double)H * (double)W);
+        const unsigned long long C = turns_fixed64(ctx->pitch * ctx->pitch / (2.0 * ctx->lambda * z));
+        {
+            ProfileScope ps(ctx, "fresnel_chirp", 1);
+            e = launch_chirp(ctx->fft_spec, H, W, C, s * std::sin(a0), -s * std::cos(a0), ctx->stream);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        ProfileScope ps(ctx, "cufft_c2c", 1);
+        if (!fft_exec(ctx->fft_plan, ctx->fft_spec, false, ctx->stream)) return CGH_ECUDA;
+        ctx->fft_spec_z = z;
+    }
+    {
+        ProfileScope ps(ctx, "cufft_c2c", 1);
+        if (!fft_exec(ctx->fft_plan, ctx->fft_pad, false, ctx->stream)) return CGH_ECUDA;
+    }
+    {
+        ProfileScope ps(ctx, "fresnel_mul", 1);
+        e = launch_cmul(ctx->fft_pad, ctx->fft_spec, 4ll * H * W, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    {
+        ProfileScope ps(ctx, "cufft_c2c", 1);
+        if (!fft_exec(ctx->fft_plan, ctx->fft_pad, true, ctx->stream)) return CGH_ECUDA;
+    }
+    ProfileScope ps(ctx, "fresnel_crop", 1);
+    return cuda_status(launch_crop(ctx->fft_pad, H, W, d_out, ctx->stream));
+}
+
+// WRP step 1 into the padded work plane (pad, zeroed first) or into planes.
+int wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, double z_wrp, float2 *pad,
+               float *planes)
+{
+    const int64_t n_pad = padded_points(n);
+    const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
+    const size_t win_bytes = align_up((size_t)n_pad * sizeof(uint4), 256);
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + win_bytes);
+    if (rc) return rc;
+    int4 *geo = reinterpret_cast<int4 *>(ctx->ws);
+    uint4 *win = reinterpret_cast<uint4 *>(static_cast<char *>(ctx->ws) + geo_bytes);
+    cudaError_t e;
+    {
+        ProfileScope ps(ctx, "wrp_prep", 1);
+        e = launch_wrp_prep(d_xyz, d_amp, (int)n, (int)n_pad, ctx->pitch, ctx->lambda, z_wrp, piston_on(ctx), geo, win,
+                            ctx->d_status, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    if (pad != nullptr) {
+        e = cudaMemsetAsync(pad, 0, (size_t)4 * ctx->width * ctx->height * sizeof(float2), ctx->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    ProfileScope ps(ctx, "wrp_record", 1);
+    return cuda_status(
+        launch_wrp_record(geo, win, (int)n_pad, ctx->height, ctx->width, pad, 2 * ctx->width, planes, ctx->stream));
+}
+
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n)
 {
     if (ctx->phase_model == CGH_PHASE_SPHERICAL)   // one form computes Eq. 1
@@ -546,6 +633,9 @@ int cgh_destroy(cgh_ctx *ctx)
     int rc = cgh_sync(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pws) cudaFree(ctx->pws);
+    if (ctx->fft_pad) cudaFree(ctx->fft_pad);
+    if (ctx->fft_spec) cudaFree(ctx->fft_spec);
+    fft_plan_destroy(ctx->fft_plan);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->io) cudaFree(ctx->io);
     if (ctx->d_status) cudaFree(ctx->d_status);
@@ -754,6 +844,51 @@ int cgh_wave(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_poi
         form = CGH_DIRECT_SFU;   // the automatic choice falls back to the other FP32 form
     }
     return run_wave(ctx, form, d_xyz, d_amp, n_points, d_out);
+}
+
+int cgh_fresnel(cgh_ctx *ctx, const float *d_in, double z_m, float *d_out)
+{
+    if (!ctx || !d_in || !d_out || !std::isfinite(z_m) || z_m == 0.0) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    int rc = ensure_fft(ctx);
+    if (rc) return rc;
+    cudaError_t e;
+    {
+        ProfileScope ps(ctx, "fresnel_expand", 1);
+        e = launch_expand(d_in, ctx->height, ctx->width, ctx->fft_pad, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    return fresnel_padded(ctx, z_m, d_out);
+}
+
+static int wrp_args(const cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, double z_wrp,
+                    const float *d_out)
+{
+    if (!ctx || !d_out || n < 0 || n > 0x7fffff00ll || !std::isfinite(z_wrp) || !(z_wrp > 0.0)) return CGH_EINVAL;
+    if (n > 0 && (!d_xyz || !d_amp)) return CGH_EINVAL;
+    if (ctx->phase_model == CGH_PHASE_SPHERICAL || phase_ref(ctx).reference()) return CGH_ENOTSUP;
+    return CGH_OK;
+}
+
+int cgh_wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, double z_wrp_m,
+                   float *d_plane)
+{
+    int rc = wrp_args(ctx, d_xyz, d_amp, n_points, z_wrp_m, d_plane);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    return wrp_record(ctx, d_xyz, d_amp, n_points, z_wrp_m, nullptr, d_plane);
+}
+
+int cgh_wrp(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, double z_wrp_m, float *d_out)
+{
+    int rc = wrp_args(ctx, d_xyz, d_amp, n_points, z_wrp_m, d_out);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    rc = ensure_fft(ctx);
+    if (rc) return rc;
+    rc = wrp_record(ctx, d_xyz, d_amp, n_points, z_wrp_m, ctx->fft_pad, nullptr);
+    if (rc) return rc;
+    return fresnel_padded(ctx, z_wrp_m, d_out);
 }
 
 int cgh_quantize8(cgh_ctx *ctx, const float *d_field, int64_t n, int mode, uint8_t *d_out)

@@ -49,6 +49,11 @@ struct cgh_ctx {
     int *h_meta = nullptr;    // pinned: counts the grouped GEMM form reads back
     int gemm_group = 0;       // CGH_OPT_GEMM_GROUP
     int phase_model = CGH_PHASE_FRESNEL;                 // CGH_OPT_PHASE_MODEL
+    // Fresnel diffraction: cuFFT plan for the 2H x 2W grid, padded work plane,
+    // and the chirp's spectrum for the distance fft_spec_z (0: none yet)
+    void *fft_plan = nullptr;
+    float2 *fft_pad = nullptr, *fft_spec = nullptr;
+    double fft_spec_z = 0.0;
     double ref_sx = 0.0, ref_sy = 0.0, ref_phase0 = 0.0;   // cgh_set_reference
     void *io = nullptr;       // device staging of cgh_point_cloud_host
     size_t io_bytes = 0;

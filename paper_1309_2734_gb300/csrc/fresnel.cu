@@ -1,0 +1,138 @@
+// f3: Fresnel diffraction, Eq. 10, on the pixel grid.
+//
+//   O(m, n) = pre * sum_{m', n'} u(m', n') h(m - m', n - n'),
+//   h(k, l) = exp(i pi p^2 (k^2 + l^2) / (lambda z)),  pre = exp(i 2 pi z / lambda) / (i lambda z) * p^2,
+//
+// the linear convolution of the H x W input with the chirp, cropped to H x W.
+// It is evaluated as the paper does, by zero-padding both to 2H x 2W (offsets
+// k in (-H, H) at k mod 2H), FFT, pointwise product, inverse FFT and crop, so
+// that the circular convolution wraps nothing into the kept window.  The FFTs
+// are cuFFT's single-precision C2C transforms; the kernels here expand the
+// input planes into the padded buffer, build the chirp (64-bit fixed-point
+// turns c k^2 + c l^2, accurate sine and cosine; the prefactor and the inverse
+// transform's 1/(4 H W) folded in), multiply by its cached spectrum, and crop
+// back into planes.
+#include <cufft.h>
+
+#include "kernels.h"
+
+namespace cgh {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(long long n)
+{
+    long long b = (n + kThreads - 1) / kThreads;
+    return (int)(b > 1048576 ? 1048576 : (b > 0 ? b : 1));
+}
+
+__global__ void chirp_kernel(float2 *__restrict__ h, int H, int W, unsigned long long C, double pre_re,
+                             double pre_im)
+{
+    const long long total = 4ll * H * W;
+    const int W2 = 2 * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / W2), l = (int)(i % W2);
+        const int kk = k < H ? k : k - 2 * H;
+        const int ll = l < W ? l : l - W2;
+        const unsigned long long r2 = (unsigned long long)((long long)kk * kk + (long long)ll * ll);   // < 2^31
+        const uint32_t t = (uint32_t)((C * r2) >> 32);              // turn, 2^-32 units (exact but the last bit)
+        const double a = (double)(int)t * (1.0 / 2147483648.0);     // [-1, 1): twice the signed turn
+        double s, c;
+        sincospi(a, &s, &c);                                        // exp(i 2 pi t)
+        h[i] = make_float2((float)(pre_re * c - pre_im * s), (float)(pre_re * s + pre_im * c));
+    }
+}
+
+__global__ void expand_kernel(const float *__restrict__ in, int H, int W, float2 *__restrict__ pad)
+{
+    const long long total = 4ll * H * W, plane = (long long)H * W;
+    const int W2 = 2 * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / W2), l = (int)(i % W2);
+        float2 v = make_float2(0.0f, 0.0f);
+        if (k < H && l < W) {
+            const long long j = (long long)k * W + l;
+            v = make_float2(in[j], in[plane + j]);
+        }
+        pad[i] = v;
+    }
+}
+
+__global__ void multiply_kernel(float2 *__restrict__ a, const float2 *__restrict__ b, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 x = a[i], y = b[i];
+        a[i] = make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+    }
+}
+
+__global__ void crop_kernel(const float2 *__restrict__ pad, int H, int W, float *__restrict__ out)
+{
+    const long long plane = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / W), l = (int)(i % W);
+        const float2 v = pad[(long long)k * 2 * W + l];
+        out[i] = v.x;
+        out[plane + i] = v.y;
+    }
+}
+
+}  // namespace
+
+bool fft_plan_2d(int rows, int cols, void **plan, cudaStream_t s)
+{
+    cufftHandle h = 0;
+    if (cufftPlan2d(&h, rows, cols, CUFFT_C2C) != CUFFT_SUCCESS) return false;
+    if (cufftSetStream(h, s) != CUFFT_SUCCESS) {
+        cufftDestroy(h);
+        return false;
+    }
+    *plan = reinterpret_cast<void *>(static_cast<uintptr_t>(h));
+    return true;
+}
+
+void fft_plan_destroy(void *plan)
+{
+    if (plan) cufftDestroy(static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(plan)));
+}
+
+bool fft_exec(void *plan, float2 *data, bool inverse, cudaStream_t s)
+{
+    const cufftHandle h = static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(plan));
+    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return false;
+    return cufftExecC2C(h, reinterpret_cast<cufftComplex *>(data), reinterpret_cast<cufftComplex *>(data),
+                        inverse ? CUFFT_INVERSE : CUFFT_FORWARD) == CUFFT_SUCCESS;
+}
+
+cudaError_t launch_chirp(float2 *h, int H, int W, unsigned long long C, double pre_re, double pre_im, cudaStream_t s)
+{
+    chirp_kernel<<<grid_for(4ll * H * W), kThreads, 0, s>>>(h, H, W, C, pre_re, pre_im);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const float *in, int H, int W, float2 *pad, cudaStream_t s)
+{
+    expand_kernel<<<grid_for(4ll * H * W), kThreads, 0, s>>>(in, H, W, pad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cmul(float2 *a, const float2 *b, int64_t n, cudaStream_t s)
+{
+    multiply_kernel<<<grid_for(n), kThreads, 0, s>>>(a, b, (long long)n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crop(const float2 *pad, int H, int W, float *out, cudaStream_t s)
+{
+    crop_kernel<<<grid_for((long long)H * W), kThreads, 0, s>>>(pad, H, W, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cgh

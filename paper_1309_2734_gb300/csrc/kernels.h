@@ -31,7 +31,8 @@ struct PhaseRef {
     unsigned long long kx = 0, ky = 0;
     uint32_t phi0 = 0;
     uint32_t piston = 0;
-    bool any() const { return kx != 0 || ky != 0 || phi0 != 0 || piston != 0; }
+    bool reference() const { return kx != 0 || ky != 0 || phi0 != 0; }
+    bool any() const { return reference() || piston != 0; }
 };
 
 #ifdef __CUDACC__
@@ -117,6 +118,23 @@ cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int 
                                  const unsigned long long *planes, const int2 *members, int height, int width,
                                  void *P, void *Q, int64_t ld, const float *wscale, cudaStream_t s,
                                  const PhaseRef &ref = PhaseRef());
+
+// f3: Fresnel diffraction (fresnel.cu) and the wavefront-recording method (wrp.cu).
+// Padded planes are [2H][2W] interleaved complex; input/output planes [2][H][W].
+bool fft_plan_2d(int rows, int cols, void **plan, cudaStream_t s);
+void fft_plan_destroy(void *plan);
+bool fft_exec(void *plan, float2 *data, bool inverse, cudaStream_t s);
+// h = pre * exp(i 2 pi C (k^2 + l^2) / 2^64) at the signed offsets of the 2H x 2W grid
+cudaError_t launch_chirp(float2 *h, int H, int W, unsigned long long C, double pre_re, double pre_im, cudaStream_t s);
+cudaError_t launch_expand(const float *in, int H, int W, float2 *pad, cudaStream_t s);
+cudaError_t launch_cmul(float2 *a, const float2 *b, int64_t n, cudaStream_t s);
+cudaError_t launch_crop(const float2 *pad, int H, int W, float *out, cudaStream_t s);
+// win[j] = {piston (or 0), A, floor(w_j^2), floor(w_j)}; geo as in the point preparation, at d_j = z_j - z_wrp
+cudaError_t launch_wrp_prep(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch, double lambda,
+                            double z_wrp, bool piston, int4 *geo, uint4 *win, int *status, cudaStream_t s);
+// into pad (row stride pad_ld) when pad is not null, else into planes [2][H][W]
+cudaError_t launch_wrp_record(const int4 *geo, const uint4 *win, int n_pad, int H, int W, float2 *pad,
+                              int64_t pad_ld, float *planes, cudaStream_t s);
 
 // a4: tcgen05 GEMM, out[n][m] (+)= sum_k P[n][k] Q[m][k] over K splits (gemm.cu).
 struct GemmPlan {

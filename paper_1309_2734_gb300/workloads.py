@@ -134,6 +134,21 @@ def layered_cloud(seed: int, width: int, height: int, n: int, n_planes: int,
     return Cloud(width, height, PITCH_M, LAMBDA_M, xyz, amp, f"layered{n_planes}-{width}x{height}-n{n}")
 
 
+def wrp_cloud(seed: int, width: int, height: int, n: int, z_wrp: float = 0.5,
+              d_range=(0.002, 0.010), a_range=(0.5, 1.0)) -> Cloud:
+    """A cloud for the wavefront-recording method: x ~ U{0..W-1}, y ~ U{0..H-1}, z = z_wrp + U[d_range]
+    (the object just behind the virtual plane), A ~ U[a_range]."""
+    rng = np.random.default_rng(seed)
+    xyz, amp = _draw(rng, width, height, n, z_wrp + d_range[0], z_wrp + d_range[1], a_range[0], a_range[1])
+    return Cloud(width, height, PITCH_M, LAMBDA_M, xyz, amp, f"wrp-{width}x{height}-n{n}")
+
+
+def complex_plane(seed: int, width: int, height: int) -> np.ndarray:
+    """A random complex input plane [2][H][W] float32 (real, imaginary ~ N(0, 1)) for Fresnel diffraction."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((2, height, width)).astype(np.float32)
+
+
 def large_crop(size: int = 4096, crop: int = 512) -> tuple:
     """(row0, col0, rows, cols) of the central crop compared for the large case."""
     r0 = (size - crop) // 2
