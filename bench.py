@@ -432,6 +432,56 @@ def run_ours(args):
             rec.pop("_sample", None)
         del lx, la, lbuf
 
+    # the paper's Fresnel diffraction (Table 5: N x N planes, lambda = 633 nm, z = 1 m as in its listing)
+    # and wavefront-recording method (Table 6: 10^3..10^5 points; here a 2048 x 2048 hologram with the
+    # plane 0.5 m away and the points 2-10 mm behind it), beside the paper's times (other hardware)
+    fresnel_t, wrp_t = {}, {}
+    if not args.no_fresnel:
+        def _ms(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+        table5 = {1024: (0.17, 0.32, 0.011), 2048: (0.60, 0.41, 0.027), 4096: (2.06, 0.87, 0.125),
+                  8192: (9.00, 3.80, None)}
+        for N, (t_cpu, t_phi, t_k20) in table5.items():
+            plane = torch.from_numpy(workloads.complex_plane(5, N, N)).cuda()
+            with Hologram(N, N, 8e-6, 633e-9, stream=stream) as hf:
+                dst = torch.empty_like(plane)
+                ms = _ms(lambda: hf.fresnel(plane, 1.0, dst), 5)
+                hf.profile(True)
+                hf.profile_read(reset=True)
+                hf.fresnel(plane, 1.0, dst)
+                hf.sync()
+                kp = hf.profile_read(reset=True)
+            fresnel_t[f"{N}x{N}"] = {"ms": ms, "paper_s": {"cpu": t_cpu, "xeon_phi": t_phi, "k20": t_k20},
+                                     "speedup_vs_k20": (t_k20 * 1e3 / ms) if t_k20 else None,
+                                     "kernel_ms": {k: v[1] for k, v in kp.items()}}
+            del plane, dst
+        table6 = {1000: (1.02, 0.68, 0.029), 10000: (3.04, 0.70, 0.030), 100000: (9.34, 0.72, 0.035)}
+        for n_pts, (t_cpu, t_phi, t_k20) in table6.items():
+            wc = workloads.wrp_cloud(6, 2048, 2048, n_pts)
+            wx, wa = torch.from_numpy(wc.xyz).cuda(), torch.from_numpy(wc.amp).cuda()
+            obuf = torch.empty((2, 2048, 2048), dtype=torch.float32, device="cuda")
+            kbuf = torch.empty((2048, 2048), dtype=torch.uint8, device="cuda")
+            with Hologram(2048, 2048, wc.pitch_m, wc.lambda_m, stream=stream) as hw:
+                hw.set_phase_model("fresnel_piston")
+                step_w = lambda: (hw.wrp(wx, wa, 0.5, obuf), hw.kinoform8(obuf, kbuf))
+                ms = _ms(step_w, 5)
+                hw.profile(True)
+                hw.profile_read(reset=True)
+                step_w()
+                hw.sync()
+                kp = hw.profile_read(reset=True)
+            wrp_t[f"n{n_pts}"] = {"ms": ms, "paper_s": {"cpu": t_cpu, "xeon_phi": t_phi, "k20": t_k20},
+                                  "speedup_vs_k20": t_k20 * 1e3 / ms, "kernel_ms": {k: v[1] for k, v in kp.items()},
+                                  "step": "WRP record + Fresnel diffraction (2 FFTs, cached chirp spectrum) + kinoform8"}
+
     h.set_form(args.form)
     h.point_cloud(xyz, amp, out)
     h.sync()
@@ -505,6 +555,8 @@ def run_ours(args):
         "forms": forms,
         "paper_kinoform_1920x1080": paper,
         "layered_4096x4096_n1000000": large,
+        "paper_fresnel_diffraction": fresnel_t,
+        "paper_wrp_2048x2048": wrp_t,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -525,6 +577,8 @@ def main():
     ap.add_argument("--compare", nargs="*",
                     default=["direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fresnel", action="store_true",
+                    help="skip the Fresnel diffraction and wavefront-recording workloads of Tables 5-6")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4096x4096, 10^6-point depth-layered case")
     ap.add_argument("--no-paper-workload", action="store_true",

@@ -509,6 +509,9 @@ int fresnel_padded(cgh_ctx *ctx, double z, float *d_out)
     return cuda_status(launch_crop(ctx->fft_pad, H, W, d_out, ctx->stream));
 }
 
+// Largest band-list workspace of the WRP record (points x bands x 4 bytes).
+constexpr size_t kMaxBandListBytes = (size_t)1 << 30;
+
 // WRP step 1 into the padded work plane (pad, zeroed first) or into planes.
 int wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, double z_wrp, float2 *pad,
                float *planes)
@@ -516,10 +519,21 @@ int wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, 
     const int64_t n_pad = padded_points(n);
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t win_bytes = align_up((size_t)n_pad * sizeof(uint4), 256);
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + win_bytes);
+    // band lists hold at most every point in every band; beyond kMaxBandListBytes the tiles walk all points
+    const int bands = (ctx->height + 31) / 32;
+    const int cells = wrp_band_cells(ctx->height, (int)n_pad);
+    const size_t list_bytes = (size_t)n_pad * bands * sizeof(int);
+    const bool binned = list_bytes <= kMaxBandListBytes;
+    const size_t band_bytes = binned ? align_up((size_t)(2 * cells + 1) * sizeof(int), 256) + list_bytes : 0;
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + win_bytes + band_bytes);
     if (rc) return rc;
     int4 *geo = reinterpret_cast<int4 *>(ctx->ws);
     uint4 *win = reinterpret_cast<uint4 *>(static_cast<char *>(ctx->ws) + geo_bytes);
+    int *count = reinterpret_cast<int *>(static_cast<char *>(ctx->ws) + geo_bytes + win_bytes);
+    int *offset = count + cells;
+    int *list = binned ? reinterpret_cast<int *>(reinterpret_cast<char *>(count) +
+                                                 align_up((size_t)(2 * cells + 1) * sizeof(int), 256))
+                       : nullptr;
     cudaError_t e;
     {
         ProfileScope ps(ctx, "wrp_prep", 1);
@@ -531,9 +545,14 @@ int wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, 
         e = cudaMemsetAsync(pad, 0, (size_t)4 * ctx->width * ctx->height * sizeof(float2), ctx->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
+    if (binned) {
+        ProfileScope ps(ctx, "wrp_bands", 3);
+        e = launch_wrp_bands(geo, win, (int)n_pad, ctx->height, count, offset, list, ctx->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     ProfileScope ps(ctx, "wrp_record", 1);
-    return cuda_status(
-        launch_wrp_record(geo, win, (int)n_pad, ctx->height, ctx->width, pad, 2 * ctx->width, planes, ctx->stream));
+    return cuda_status(launch_wrp_record(geo, win, (int)n_pad, ctx->height, ctx->width, offset, list, pad,
+                                         2 * ctx->width, planes, ctx->stream));
 }
 
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n)

@@ -47,41 +47,44 @@ __global__ void chirp_kernel(float2 *__restrict__ h, int H, int W, unsigned long
     }
 }
 
+// One row of the padded plane per blockIdx.y, two complex words per thread.
 __global__ void expand_kernel(const float *__restrict__ in, int H, int W, float2 *__restrict__ pad)
 {
-    const long long total = 4ll * H * W, plane = (long long)H * W;
-    const int W2 = 2 * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / W2), l = (int)(i % W2);
-        float2 v = make_float2(0.0f, 0.0f);
-        if (k < H && l < W) {
-            const long long j = (long long)k * W + l;
-            v = make_float2(in[j], in[plane + j]);
-        }
-        pad[i] = v;
+    const int k = blockIdx.y;
+    const int l = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (l >= 2 * W) return;
+    const long long plane = (long long)H * W;
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (k < H) {
+        const float *re = in + (long long)k * W, *im = re + plane;
+        if (l < W) v.x = re[l], v.y = im[l];
+        if (l + 1 < W) v.z = re[l + 1], v.w = im[l + 1];
     }
+    *reinterpret_cast<float4 *>(pad + (long long)k * 2 * W + l) = v;   // 2W is even: 16-byte aligned
 }
 
+// n is even (4 H W): two complex words per 16-byte access.
 __global__ void multiply_kernel(float2 *__restrict__ a, const float2 *__restrict__ b, long long n)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+    float4 *a4 = reinterpret_cast<float4 *>(a);
+    const float4 *b4 = reinterpret_cast<const float4 *>(b);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n / 2;
          i += (long long)gridDim.x * blockDim.x) {
-        const float2 x = a[i], y = b[i];
-        a[i] = make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+        const float4 x = a4[i], y = b4[i];
+        a4[i] = make_float4(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x, x.z * y.z - x.w * y.w,
+                            x.z * y.w + x.w * y.z);
     }
 }
 
 __global__ void crop_kernel(const float2 *__restrict__ pad, int H, int W, float *__restrict__ out)
 {
-    const long long plane = (long long)H * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / W), l = (int)(i % W);
-        const float2 v = pad[(long long)k * 2 * W + l];
-        out[i] = v.x;
-        out[plane + i] = v.y;
-    }
+    const int k = blockIdx.y;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= W) return;
+    const float2 v = pad[(long long)k * 2 * W + l];
+    const long long j = (long long)k * W + l;
+    out[j] = v.x;
+    out[(long long)H * W + j] = v.y;
 }
 
 }  // namespace
@@ -119,19 +122,21 @@ cudaError_t launch_chirp(float2 *h, int H, int W, unsigned long long C, double p
 
 cudaError_t launch_expand(const float *in, int H, int W, float2 *pad, cudaStream_t s)
 {
-    expand_kernel<<<grid_for(4ll * H * W), kThreads, 0, s>>>(in, H, W, pad);
+    const dim3 grid((W + kThreads - 1) / kThreads, 2 * H);   // 2W columns, two per thread
+    expand_kernel<<<grid, kThreads, 0, s>>>(in, H, W, pad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cmul(float2 *a, const float2 *b, int64_t n, cudaStream_t s)
 {
-    multiply_kernel<<<grid_for(n), kThreads, 0, s>>>(a, b, (long long)n);
+    multiply_kernel<<<grid_for(n / 2), kThreads, 0, s>>>(a, b, (long long)n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_crop(const float2 *pad, int H, int W, float *out, cudaStream_t s)
 {
-    crop_kernel<<<grid_for((long long)H * W), kThreads, 0, s>>>(pad, H, W, out);
+    const dim3 grid((W + kThreads - 1) / kThreads, H);
+    crop_kernel<<<grid, kThreads, 0, s>>>(pad, H, W, out);
     return cudaGetLastError();
 }
 

@@ -132,9 +132,15 @@ cudaError_t launch_crop(const float2 *pad, int H, int W, float *out, cudaStream_
 // win[j] = {piston (or 0), A, floor(w_j^2), floor(w_j)}; geo as in the point preparation, at d_j = z_j - z_wrp
 cudaError_t launch_wrp_prep(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch, double lambda,
                             double z_wrp, bool piston, int4 *geo, uint4 *win, int *status, cudaStream_t s);
-// into pad (row stride pad_ld) when pad is not null, else into planes [2][H][W]
-cudaError_t launch_wrp_record(const int4 *geo, const uint4 *win, int n_pad, int H, int W, float2 *pad,
-                              int64_t pad_ld, float *planes, cudaStream_t s);
+// Band lists (32 rows each, built per segment of 4096 points): count[cells], offset[cells + 1],
+// list[sum of counts] (at most n_pad * bands), cells = bands x segments.
+int wrp_band_cells(int H, int n_pad);
+cudaError_t launch_wrp_bands(const int4 *geo, const uint4 *win, int n_pad, int H, int *count, int *offset, int *list,
+                             cudaStream_t s);
+// into pad (row stride pad_ld) when pad is not null, else into planes [2][H][W]; list == nullptr: every tile
+// walks all points (the same sums)
+cudaError_t launch_wrp_record(const int4 *geo, const uint4 *win, int n_pad, int H, int W, const int *offset,
+                              const int *list, float2 *pad, int64_t pad_ld, float *planes, cudaStream_t s);
 
 // a4: tcgen05 GEMM, out[n][m] (+)= sum_k P[n][k] Q[m][k] over K splits (gemm.cu).
 struct GemmPlan {

@@ -15,11 +15,14 @@
 // with CGH_PHASE_FRESNEL_PISTON; sine and cosine from the hardware on the
 // symmetric argument grid of the direct kernel.
 //
-// Gather, deterministic: one CTA per 32 x 32 pixel tile walks all points in
+// Gather, deterministic: one CTA per 32 x 32 pixel tile walks the points in
 // index order, 256 at a time; the threads test the 256 window bounding boxes
 // against the tile in parallel, compact the hits (warp ballots, order kept)
 // and then every thread adds the hits to its four pixels.  No atomics, so the
-// sums are bit-reproducible.
+// sums are bit-reproducible.  The points a tile walks are those of its band of
+// 32 rows: for every band one CTA lists, in index order, the points whose
+// window reaches the band (count, scan, fill; the same ballot compaction), so
+// a tile skips the points of the other bands and the sums are unchanged.
 #include "device_util.cuh"
 #include "kernels.h"
 
@@ -77,37 +80,105 @@ __global__ void wrp_prep_kernel(const float *__restrict__ xyz, const float *__re
     win[j] = make_uint4(pist, __float_as_uint(a), W2, R);
 }
 
+// Ballot compaction of one chunk: the position of this thread's hit among the
+// chunk's hits (warp order, then lane order: index order kept) and their total.
+__device__ __forceinline__ int compact_hits(bool hit, int *s_wcnt, int &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) s_wcnt[warp] = __popc(mask);
+    __syncthreads();
+    int before = 0;
+    total = 0;
+#pragma unroll
+    for (int k = 0; k < kRecThreads / 32; ++k) {
+        before += k < warp ? s_wcnt[k] : 0;
+        total += s_wcnt[k];
+    }
+    return before + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ bool reaches_rows(const int4 q, const uint4 w, int y0)
+{
+    const int R = (int)w.w;
+    return q.y + R >= y0 && q.y - R <= y0 + kTile - 1;
+}
+
+constexpr int kSegChunks = 16;   // chunks of kRecThreads points per segment of the band lists
+
+// One CTA per (band of kTile rows, segment of kSegChunks x kRecThreads points):
+// count (list == nullptr) or list, in index order, the segment's points whose
+// window reaches the band.  A band's list is its segments' lists in order.
+__global__ void __launch_bounds__(kRecThreads)
+    wrp_band_kernel(const int4 *__restrict__ geo, const uint4 *__restrict__ win, int n_pad, int *count,
+                    const int *__restrict__ offset, int *__restrict__ list)
+{
+    __shared__ int s_wcnt[kRecThreads / 32];
+    const int y0 = blockIdx.x * kTile;
+    const int cell = blockIdx.x * gridDim.y + blockIdx.y;   // band-major, then segment
+    const int begin = blockIdx.y * kSegChunks * kRecThreads;
+    const int end = min(n_pad, begin + kSegChunks * kRecThreads);
+    int written = 0;
+    for (int base = begin; base < end; base += kRecThreads) {
+        const int j = base + threadIdx.x;
+        const bool hit = reaches_rows(geo[j], win[j], y0);
+        __syncthreads();   // s_wcnt of the previous chunk is read
+        int total;
+        const int pos = compact_hits(hit, s_wcnt, total);
+        if (list != nullptr && hit) list[offset[cell] + written + pos] = j;
+        written += total;
+    }
+    if (list == nullptr && threadIdx.x == 0) count[cell] = written;
+}
+
+// Exclusive scan of the (band, segment) counts in that order (one thread).
+__global__ void wrp_band_scan(const int *count, int cells, int *offset)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int run = 0;
+    for (int b = 0; b < cells; ++b) {
+        offset[b] = run;
+        run += count[b];
+    }
+    offset[cells] = run;
+}
+
 __global__ void __launch_bounds__(kRecThreads)
     wrp_record_kernel(const int4 *__restrict__ geo, const uint4 *__restrict__ win, int n_pad, int H, int W,
-                      int tiles_x, float2 *__restrict__ pad, long long pad_ld, float *__restrict__ planes)
+                      int tiles_x, int segs, const int *__restrict__ offset, const int *__restrict__ list,
+                      float2 *__restrict__ pad, long long pad_ld, float *__restrict__ planes)
 {
     __shared__ int4 s_geo[kRecThreads];
     __shared__ uint4 s_win[kRecThreads];
     __shared__ unsigned char s_hit[kRecThreads];
     __shared__ int s_wcnt[kRecThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = (blockIdx.x % tiles_x) * kTile, y0 = (blockIdx.x / tiles_x) * kTile;
+    const int band = blockIdx.x / tiles_x;
+    const int x0 = (blockIdx.x % tiles_x) * kTile, y0 = band * kTile;
     const int m = x0 + lane;
     const int nb = y0 + warp * 4;
+    // the points to walk: the band's list, or all points
+    const int first = list != nullptr ? offset[band * segs] : 0;
+    const int count = list != nullptr ? offset[(band + 1) * segs] - first : n_pad;
     float re[4] = {0.0f, 0.0f, 0.0f, 0.0f}, im[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int base = 0; base < n_pad; base += kRecThreads) {
+    for (int base = 0; base < count; base += kRecThreads) {
         __syncthreads();   // the previous chunk is consumed
-        const int4 q = geo[base + tid];
-        const uint4 w = win[base + tid];
+        const int k = base + tid;
+        int4 q = make_int4(0, 0, 0, 0);
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        bool hit = false;
+        if (k < count) {
+            const int j = list != nullptr ? list[first + k] : k;
+            q = geo[j];
+            w = win[j];
+            const int R = (int)w.w;
+            hit = q.x + R >= x0 && q.x - R <= x0 + kTile - 1 && reaches_rows(q, w, y0);
+        }
         s_geo[tid] = q;
         s_win[tid] = w;
-        const int R = (int)w.w;
-        const bool hit = q.x + R >= x0 && q.x - R <= x0 + kTile - 1 && q.y + R >= y0 && q.y - R <= y0 + kTile - 1;
-        const unsigned mask = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) s_wcnt[warp] = __popc(mask);
-        __syncthreads();
-        int before = 0, total = 0;
-#pragma unroll
-        for (int k = 0; k < kRecThreads / 32; ++k) {
-            before += k < warp ? s_wcnt[k] : 0;
-            total += s_wcnt[k];
-        }
-        if (hit) s_hit[before + __popc(mask & ((1u << lane) - 1u))] = (unsigned char)tid;
+        int total;
+        const int pos = compact_hits(hit, s_wcnt, total);
+        if (hit) s_hit[pos] = (unsigned char)tid;
         __syncthreads();
         for (int h = 0; h < total; ++h) {
             const int p = s_hit[h];
@@ -154,12 +225,34 @@ cudaError_t launch_wrp_prep(const float *d_xyz, const float *d_amp, int n, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_wrp_record(const int4 *geo, const uint4 *win, int n_pad, int H, int W, float2 *pad,
-                              int64_t pad_ld, float *planes, cudaStream_t s)
+int wrp_band_cells(int H, int n_pad)
+{
+    const int segs = (n_pad + kSegChunks * kRecThreads - 1) / (kSegChunks * kRecThreads);
+    return ((H + kTile - 1) / kTile) * (segs > 0 ? segs : 1);
+}
+
+static int wrp_segs(int n_pad)
+{
+    const int segs = (n_pad + kSegChunks * kRecThreads - 1) / (kSegChunks * kRecThreads);
+    return segs > 0 ? segs : 1;
+}
+
+cudaError_t launch_wrp_bands(const int4 *geo, const uint4 *win, int n_pad, int H, int *count, int *offset, int *list,
+                             cudaStream_t s)
+{
+    const dim3 grid((H + kTile - 1) / kTile, wrp_segs(n_pad));
+    wrp_band_kernel<<<grid, kRecThreads, 0, s>>>(geo, win, n_pad, count, nullptr, nullptr);
+    wrp_band_scan<<<1, 32, 0, s>>>(count, (int)(grid.x * grid.y), offset);
+    wrp_band_kernel<<<grid, kRecThreads, 0, s>>>(geo, win, n_pad, count, offset, list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wrp_record(const int4 *geo, const uint4 *win, int n_pad, int H, int W, const int *offset,
+                              const int *list, float2 *pad, int64_t pad_ld, float *planes, cudaStream_t s)
 {
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-    wrp_record_kernel<<<tiles_x * tiles_y, kRecThreads, 0, s>>>(geo, win, n_pad, H, W, tiles_x, pad,
-                                                               (long long)pad_ld, planes);
+    wrp_record_kernel<<<tiles_x * tiles_y, kRecThreads, 0, s>>>(geo, win, n_pad, H, W, tiles_x, wrp_segs(n_pad),
+                                                               offset, list, pad, (long long)pad_ld, planes);
     return cudaGetLastError();
 }
 
