@@ -40,9 +40,12 @@ MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # taken on; a changed source reports null until it is profiled again.
 NCU_TRAFFIC = [
-    # profiles/gemm_f16-1920x1080-n50000.md: 600.71 MB read + 4.15 MB written per launch
+    # profiles/direct_sfu-1920x1080-n10000.md: 0.272 MB read + 22.238 MB written per launch
+    {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000", "src": "direct.cu",
+     "sha1": "615d5dae059e1423a6fcf2b7db038c23fe1cb9f3", "bytes_per_launch": 22510336},
+    # profiles/gemm_f16-1920x1080-n50000.md: 601.197 MB read + 3.845 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000", "src": "gemm.cu",
-     "sha1": "2e153cd338946ad225a492ce0f2f5194e2532935", "bytes_per_launch": 604860160},
+     "sha1": "566d131008ba484d837dd09ad80e462d05bffca1", "bytes_per_launch": 605042432},
 ]
 
 
