@@ -154,9 +154,11 @@ int cgh_set_reference(cgh_ctx *ctx, double sin_x, double sin_y, double phase0_ra
  * p), device memory; d_out may equal d_in.  The integral is the sum over cells
  * of area p^2 with the prefactor exp(i 2 pi z / lambda) / (i lambda z):
  *   O(m, n) = exp(i 2 pi z/lambda)/(i lambda z) p^2 sum u(m', n') exp(i pi p^2 ((m-m')^2 + (n-n')^2)/(lambda z)),
- * evaluated as the paper does by zero-padding to 2H x 2W, FFT (cuFFT, single
- * precision), product with the chirp's spectrum (cached per z), inverse FFT and
- * crop.  Allocates 2 x 4 W H complex words and a cuFFT plan on first use.
+ * evaluated as the paper does by zero-padding (to the powers of two >= 2H - 1,
+ * 2W - 1), FFT, product with the chirp's spectrum (cached per z), inverse FFT
+ * and crop, in single precision, with the library's own FFT (cuFFT for grids
+ * beyond 16384 a side).  Allocates two padded complex planes and the twiddle
+ * tables on first use.
  */
 int cgh_fresnel(cgh_ctx *ctx, const float *d_in, double z_m, float *d_out);
 

@@ -449,48 +449,89 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
     return cuda_status(e);
 }
 
-// Fresnel diffraction state of the context: the cuFFT plan of the 2H x 2W grid
-// and two padded planes (work plane and the chirp's spectrum), made on first use.
+// Fresnel diffraction state of the context, made on first use: the own FFT's
+// grid (Ly x Lx, powers of two), its twiddle tables, the padded work plane and
+// the chirp's spectrum; for grids beyond its lengths, a cuFFT plan of 2H x 2W.
 int ensure_fft(cgh_ctx *ctx)
 {
-    if (ctx->fft_plan) return CGH_OK;
-    const size_t bytes = (size_t)4 * ctx->width * ctx->height * sizeof(float2);
-    if (cudaMalloc(&ctx->fft_pad, bytes) != cudaSuccess || cudaMalloc(&ctx->fft_spec, bytes) != cudaSuccess) {
+    if (ctx->fft_ready) return CGH_OK;
+    const FftGrid g = fft_grid(ctx->height, ctx->width);
+    const size_t words = g.ok ? (size_t)g.Ly * g.Lx : (size_t)4 * ctx->width * ctx->height;
+    auto fail = [&](int rc) {
         cudaGetLastError();
-        if (ctx->fft_pad) cudaFree(ctx->fft_pad);
-        if (ctx->fft_spec) cudaFree(ctx->fft_spec);
-        ctx->fft_pad = ctx->fft_spec = nullptr;
-        return CGH_ENOMEM;
-    }
-    if (!fft_plan_2d(2 * ctx->height, 2 * ctx->width, &ctx->fft_plan, ctx->stream)) {
+        for (float2 **p : {&ctx->fft_pad, &ctx->fft_spec, &ctx->fft_twx, &ctx->fft_twy})
+            if (*p) {
+                cudaFree(*p);
+                *p = nullptr;
+            }
+        return rc;
+    };
+    if (cudaMalloc(&ctx->fft_pad, words * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&ctx->fft_spec, words * sizeof(float2)) != cudaSuccess)
+        return fail(CGH_ENOMEM);
+    if (g.ok) {
+        // e^{-2 pi i k / L} in double, rounded once
+        for (int pass = 0; pass < 2; ++pass) {
+            const int L = pass == 0 ? g.Lx : g.Ly;
+            float2 **dst = pass == 0 ? &ctx->fft_twx : &ctx->fft_twy;
+            std::vector<float2> t((size_t)L);
+            for (int k = 0; k < L; ++k) {
+                const double a = -2.0 * 3.14159265358979323846 * (double)k / (double)L;
+                t[(size_t)k] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+            if (cudaMalloc(dst, (size_t)L * sizeof(float2)) != cudaSuccess) return fail(CGH_ENOMEM);
+            if (cudaMemcpy(*dst, t.data(), (size_t)L * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(CGH_ECUDA);
+        }
+    } else if (!fft_plan_2d(2 * ctx->height, 2 * ctx->width, &ctx->fft_plan, ctx->stream)) {
         ctx->fft_plan = nullptr;
-        return CGH_ECUDA;
+        return fail(CGH_ECUDA);
     }
+    ctx->fft_g = g;
     ctx->fft_spec_z = 0.0;
+    ctx->fft_ready = true;
     return CGH_OK;
 }
 
-// The padded work plane (holding the expanded input) propagated by z and
-// cropped into d_out ([2][H][W]).  The chirp's spectrum carries the prefactor
-// exp(i 2 pi z / lambda) / (i lambda z) p^2 and the inverse transform's
-// 1 / (4 H W); it is kept for the next call with the same z.
-int fresnel_padded(cgh_ctx *ctx, double z, float *d_out)
+// Fresnel diffraction by z into d_out ([2][H][W]) of the input planes in, or
+// (in == nullptr) of the plane already in the work plane (rows < H, columns
+// < W).  The chirp's spectrum carries the prefactor exp(i 2 pi z / lambda) /
+// (i lambda z) p^2 and the inverse transform's 1 / (grid size); it is kept for
+// the next call with the same z.
+int fresnel_run(cgh_ctx *ctx, double z, const float *in, float *d_out)
 {
     const int H = ctx->height, W = ctx->width;
+    const FftGrid &g = ctx->fft_g;
+    const double cells = g.ok ? (double)g.Ly * g.Lx : 4.0 * H * W;
     cudaError_t e = cudaSuccess;
     if (ctx->fft_spec_z != z) {
         const double zt = z / ctx->lambda;
         const double a0 = 6.283185307179586476925286766559 * (zt - std::rint(zt));
-        const double s = ctx->pitch * ctx->pitch / (ctx->lambda * z) / (4.0 * (double)H * (double)W);
+        const double s = ctx->pitch * ctx->pitch / (ctx->lambda * z) / cells;
         const unsigned long long C = turns_fixed64(ctx->pitch * ctx->pitch / (2.0 * ctx->lambda * z));
-        {
-            ProfileScope ps(ctx, "fresnel_chirp", 1);
-            e = launch_chirp(ctx->fft_spec, H, W, C, s * std::sin(a0), -s * std::cos(a0), ctx->stream);
+        if (g.ok) {
+            ProfileScope ps(ctx, "fresnel_spectrum", 5);
+            e = launch_fft_chirp_spectrum(g, ctx->fft_spec, C, s * std::sin(a0), -s * std::cos(a0), ctx->fft_twx,
+                                          ctx->fft_twy, ctx->stream);
+        } else {
+            {
+                ProfileScope ps(ctx, "fresnel_chirp", 1);
+                e = launch_chirp(ctx->fft_spec, H, W, C, s * std::sin(a0), -s * std::cos(a0), ctx->stream);
+            }
+            if (e == cudaSuccess && !fft_exec(ctx->fft_plan, ctx->fft_spec, false, ctx->stream)) return CGH_ECUDA;
         }
         if (e != cudaSuccess) return cuda_status(e);
-        ProfileScope ps(ctx, "cufft_c2c", 1);
-        if (!fft_exec(ctx->fft_plan, ctx->fft_spec, false, ctx->stream)) return CGH_ECUDA;
         ctx->fft_spec_z = z;
+    }
+    if (g.ok) {
+        ProfileScope ps(ctx, "fresnel_fft", 5);
+        return cuda_status(launch_fft_convolve(g, in, H, W, ctx->fft_pad, ctx->fft_spec, ctx->fft_twx, ctx->fft_twy,
+                                               d_out, ctx->stream));
+    }
+    if (in != nullptr) {
+        ProfileScope ps(ctx, "fresnel_expand", 1);
+        e = launch_expand(in, H, W, ctx->fft_pad, ctx->stream);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     {
         ProfileScope ps(ctx, "cufft_c2c", 1);
@@ -541,18 +582,21 @@ int wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, 
                             ctx->d_status, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_status(e);
-    if (pad != nullptr) {
+    // the own FFT reads only the rows < H, columns < W of the work plane; the cuFFT path reads all of it
+    const bool own = ctx->fft_g.ok;
+    if (pad != nullptr && !own) {
         e = cudaMemsetAsync(pad, 0, (size_t)4 * ctx->width * ctx->height * sizeof(float2), ctx->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
+    const int64_t pad_ld = own ? ctx->fft_g.Lx : 2 * ctx->width;
     if (binned) {
         ProfileScope ps(ctx, "wrp_bands", 3);
         e = launch_wrp_bands(geo, win, (int)n_pad, ctx->height, count, offset, list, ctx->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     ProfileScope ps(ctx, "wrp_record", 1);
-    return cuda_status(launch_wrp_record(geo, win, (int)n_pad, ctx->height, ctx->width, offset, list, pad,
-                                         2 * ctx->width, planes, ctx->stream));
+    return cuda_status(launch_wrp_record(geo, win, (int)n_pad, ctx->height, ctx->width, offset, list, pad, pad_ld,
+                                         planes, ctx->stream));
 }
 
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n)
@@ -652,8 +696,8 @@ int cgh_destroy(cgh_ctx *ctx)
     int rc = cgh_sync(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pws) cudaFree(ctx->pws);
-    if (ctx->fft_pad) cudaFree(ctx->fft_pad);
-    if (ctx->fft_spec) cudaFree(ctx->fft_spec);
+    for (float2 *p : {ctx->fft_pad, ctx->fft_spec, ctx->fft_twx, ctx->fft_twy})
+        if (p) cudaFree(p);
     fft_plan_destroy(ctx->fft_plan);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->io) cudaFree(ctx->io);
@@ -871,13 +915,7 @@ int cgh_fresnel(cgh_ctx *ctx, const float *d_in, double z_m, float *d_out)
     DeviceGuard g(ctx->device);
     int rc = ensure_fft(ctx);
     if (rc) return rc;
-    cudaError_t e;
-    {
-        ProfileScope ps(ctx, "fresnel_expand", 1);
-        e = launch_expand(d_in, ctx->height, ctx->width, ctx->fft_pad, ctx->stream);
-    }
-    if (e != cudaSuccess) return cuda_status(e);
-    return fresnel_padded(ctx, z_m, d_out);
+    return fresnel_run(ctx, z_m, d_in, d_out);
 }
 
 static int wrp_args(const cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, double z_wrp,
@@ -907,7 +945,7 @@ int cgh_wrp(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_poin
     if (rc) return rc;
     rc = wrp_record(ctx, d_xyz, d_amp, n_points, z_wrp_m, ctx->fft_pad, nullptr);
     if (rc) return rc;
-    return fresnel_padded(ctx, z_wrp_m, d_out);
+    return fresnel_run(ctx, z_wrp_m, nullptr, d_out);
 }
 
 int cgh_quantize8(cgh_ctx *ctx, const float *d_field, int64_t n, int mode, uint8_t *d_out)

@@ -51,8 +51,11 @@ struct cgh_ctx {
     int phase_model = CGH_PHASE_FRESNEL;                 // CGH_OPT_PHASE_MODEL
     // Fresnel diffraction: cuFFT plan for the 2H x 2W grid, padded work plane,
     // and the chirp's spectrum for the distance fft_spec_z (0: none yet)
-    void *fft_plan = nullptr;
+    void *fft_plan = nullptr;          // cuFFT, only for grids beyond the own FFT's lengths
+    cgh::FftGrid fft_g;                // the own FFT's grid (fft_g.ok)
+    float2 *fft_twx = nullptr, *fft_twy = nullptr;
     float2 *fft_pad = nullptr, *fft_spec = nullptr;
+    bool fft_ready = false;
     double fft_spec_z = 0.0;
     double ref_sx = 0.0, ref_sy = 0.0, ref_phase0 = 0.0;   // cgh_set_reference
     void *io = nullptr;       // device staging of cgh_point_cloud_host

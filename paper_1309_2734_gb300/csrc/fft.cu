@@ -1,0 +1,491 @@
+// f3: the FFTs of Fresnel diffraction (Eq. 10), hand-written for the
+// zero-padded linear convolution.
+//
+// The padded grid is Ly x Lx (powers of two >= 2H - 1, 2W - 1; at most 16384).
+// Forward 2-D transform of the H x W input, product with the chirp's
+// spectrum, inverse transform, crop:
+//   rows     Lx-point FFT of the H nonzero rows only, the input planes read
+//            straight into shared memory (the zero padding is never stored);
+//   columns  Ly = L1 L2 four-step: pass A, L1-point FFTs over the rows
+//            L2 a + b (rows >= H are zero: not loaded); pass B, L2-point FFTs
+//            over the contiguous rows L2 c + b, which leaves the spectrum in
+//            the scrambled order ky = c + L1 d at row L2 c + d.  Any fixed
+//            order serves a convolution, so the chirp's spectrum is kept in
+//            that order, and forward pass B, the product and inverse pass B
+//            are ONE pass (the middle kernel), twiddles e^{-2 pi i c b / Ly}
+//            included; inverse pass A writes only the rows < H;
+//   rows     inverse Lx-point FFT of those H rows, only the first W columns
+//            written, into the output planes.
+// Every transform is a Stockham autosort FFT in shared memory (the
+// formulation of Govindaraju et al., SC 2008: per stage, radix-R butterflies
+// over elements M/R apart, twiddles e^{-2 pi i r (j mod Ns) / (Ns R)}, results
+// at (j / Ns) Ns R + j mod Ns + r Ns), radix 16 (and one stage of 8, 4 or 2):
+// each thread holds 16 values per stage; twiddles come from a table of
+// e^{-2 pi i k / L} built in double on the host.
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace cgh {
+
+namespace {
+
+// Asynchronous global -> shared copies (no register staging: a whole tile in flight at once).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// e^{-2 pi i k / 16}, k = 0..7 (cos(pi/8), sin(pi/8), 1/sqrt(2))
+constexpr float kC1 = 0.923879532511286756f, kS1 = 0.382683432365089772f, kC2 = 0.707106781186547524f;
+__device__ __forceinline__ float2 w16(int k)
+{
+    switch (k & 7) {
+    case 0: return make_float2(1.0f, 0.0f);
+    case 1: return make_float2(kC1, -kS1);
+    case 2: return make_float2(kC2, -kC2);
+    case 3: return make_float2(kS1, -kC1);
+    case 4: return make_float2(0.0f, -1.0f);
+    case 5: return make_float2(-kS1, -kC1);
+    case 6: return make_float2(-kC2, -kC2);
+    default: return make_float2(-kC1, -kS1);
+    }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float2 conj_if(float2 a, bool c)
+{
+    return c ? make_float2(a.x, -a.y) : a;
+}
+
+__host__ __device__ constexpr int rev_bits(int i, int bits)
+{
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// v * e^{-+2 pi i idx / 16} for a compile-time idx: no product for 1, a swap
+// for -i, two for the odd multiples of pi/4 (IEEE rules keep x * 0 + y * 1
+// from folding on its own).
+__device__ __forceinline__ float2 tw16_mul(float2 v, int idx, bool inv)
+{
+    switch (idx & 15) {
+    case 0: return v;
+    case 4: return inv ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+    case 8: return make_float2(-v.x, -v.y);
+    case 12: return inv ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
+    case 2: return inv ? make_float2((v.x - v.y) * kC2, (v.x + v.y) * kC2)
+                       : make_float2((v.x + v.y) * kC2, (v.y - v.x) * kC2);
+    case 6: return inv ? make_float2(-(v.x + v.y) * kC2, (v.x - v.y) * kC2)
+                       : make_float2((v.y - v.x) * kC2, -(v.x + v.y) * kC2);
+    default: return cmul(v, conj_if(w16(idx), inv));
+    }
+}
+
+// y_k = sum_r v_r e^{-+2 pi i r k / R} in registers (radix-2 Cooley-Tukey, natural order out).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_regs(float2 *v)
+{
+    constexpr int bits = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int j = rev_bits(i, bits);
+        if (i < j) {
+            const float2 t = v[i];
+            v[i] = v[j];
+            v[j] = t;
+        }
+    }
+#pragma unroll
+    for (int half = 1; half < R; half *= 2) {
+#pragma unroll
+        for (int k0 = 0; k0 < R; k0 += 2 * half) {
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const float2 a = v[k0 + k], b = tw16_mul(v[k0 + k + half], k * (16 / (2 * half)), INV);
+                v[k0 + k] = make_float2(a.x + b.x, a.y + b.y);
+                v[k0 + k + half] = make_float2(a.x - b.x, a.y - b.y);
+            }
+        }
+    }
+}
+
+enum { kLayoutRows = 0, kLayoutCols = 1 };
+
+__device__ __forceinline__ int ilog2(int v)
+{
+    return 31 - __clz(v);
+}
+
+// Shared-memory address of element e of sequence q.  Rows: sequences of M
+// contiguous values, one float2 of padding per 32 (against bank conflicts of
+// the strided stores); columns: element e of column q at e * stride + q.
+template <int LAYOUT>
+__device__ __forceinline__ int saddr(int e, int q, int M, int stride)
+{
+    if (LAYOUT == kLayoutRows) return q * (M + (M >> 5)) + e + (e >> 5);
+    return e * stride + q;
+}
+
+// e^{-2 pi i r k / (Ns R)} for r = 1..R-1 from three table values (k, 4k and 8k
+// steps) and at most two products each: w_r = w_(r mod 4) w_(r - r mod 4).
+template <int R>
+__device__ __forceinline__ void stage_twiddles(float2 *w, const float2 *tw, int idx1, bool inv)
+{
+    w[0] = make_float2(1.0f, 0.0f);
+    if (R == 1) return;
+    w[1] = conj_if(tw[idx1], inv);
+    if (R == 2) return;
+    w[2] = cmul(w[1], w[1]);
+    w[3] = cmul(w[2], w[1]);
+    if (R == 4) return;
+    w[4] = conj_if(tw[4 * idx1], inv);
+#pragma unroll
+    for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+    if (R == 8) return;
+    w[8] = conj_if(tw[8 * idx1], inv);
+    w[12] = cmul(w[8], w[4]);
+#pragma unroll
+    for (int r = 9; r < 16; ++r)
+        if (r != 12) w[r] = cmul(w[r & 12], w[r & 3]);
+}
+
+// One Stockham stage of radix R over nseq sequences of length M (Ns: size of
+// the sub-transforms done so far); all sizes powers of two (lm = log2 M, lq =
+// log2 nseq, ls = log2 Ns, lt = log2 of the table stride).  Each thread takes
+// 16 / R butterflies.
+template <int R, bool INV, int LAYOUT>
+__device__ __forceinline__ void stockham_stage(float2 *s, int lm, int lq, int stride, int ls, const float2 *tw,
+                                               int lt)
+{
+    constexpr int PER = 16 / R;
+    constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+    const int T = blockDim.x;
+    const int M = 1 << lm, nseq = 1 << lq;
+    const int lspan = lm - LR, span = 1 << lspan;   // butterflies per sequence
+    float2 v[16];
+    int jj[PER], qq[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int w = threadIdx.x + u * T;
+        int q, j;
+        if (LAYOUT == kLayoutCols) {
+            q = w & (nseq - 1);   // neighbouring threads: neighbouring columns
+            j = w >> lq;
+        } else {
+            j = w & (span - 1);
+            q = w >> lspan;
+        }
+        jj[u] = j;
+        qq[u] = q;
+        const bool live = q < nseq && j < span;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            v[u * R + r] = live ? s[saddr<LAYOUT>(j + (r << lspan), q, M, stride)] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = jj[u], q = qq[u];
+        if (q >= nseq || j >= span) continue;
+        const int k = j & ((1 << ls) - 1);
+        if (ls > 0) {
+            float2 w[R];
+            stage_twiddles<R>(w, tw, (k << (lm - ls - LR)) << lt, INV);   // e^{-2 pi i k / (Ns R)}
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[u * R + r] = cmul(v[u * R + r], w[r]);
+        }
+        dft_regs<R, INV>(&v[u * R]);
+        const int base = ((j >> ls) << (ls + LR)) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[saddr<LAYOUT>(base + (r << ls), q, M, stride)] = v[u * R + r];
+    }
+    __syncthreads();
+}
+
+// nseq transforms of length M (power of two) in shared memory; tw[k * tws] = e^{-2 pi i k / M}.
+template <bool INV, int LAYOUT>
+__device__ void smem_fft(float2 *s, int M, int nseq, int stride, const float2 *tw, int tws)
+{
+    const int lm = ilog2(M), lq = ilog2(nseq), lt = ilog2(tws);
+    int ls = 0;
+    while (ls + 4 <= lm) {
+        stockham_stage<16, INV, LAYOUT>(s, lm, lq, stride, ls, tw, lt);
+        ls += 4;
+    }
+    const int rest = lm - ls;
+    if (rest == 3) stockham_stage<8, INV, LAYOUT>(s, lm, lq, stride, ls, tw, lt);
+    else if (rest == 2) stockham_stage<4, INV, LAYOUT>(s, lm, lq, stride, ls, tw, lt);
+    else if (rest == 1) stockham_stage<2, INV, LAYOUT>(s, lm, lq, stride, ls, tw, lt);
+}
+
+enum { kRowExpand = 0, kRowInPlace = 1, kRowCrop = 2, kRowPadRows = 3 };
+
+// Row transforms: nseq rows of length Lx per CTA.
+//   kRowExpand:  rows y < H from the input planes [2][H][W] (zeros beyond W), forward, into pad;
+//   kRowPadRows: rows y < H of pad, columns < W (zeros beyond), forward, in place;
+//   kRowInPlace: rows of pad, forward, in place (the chirp, all Ly rows);
+//   kRowCrop:    rows y < H of pad, inverse, columns < W into the output planes.
+template <int MODE>
+__global__ void fft_rows_kernel(const float *__restrict__ in, float2 *__restrict__ pad, float *__restrict__ out,
+                                int H, int W, int Lx, int rows, int nseq, const float2 *__restrict__ twx)
+{
+    extern __shared__ float2 sm[];
+    const int y0 = blockIdx.x * nseq;
+    const int T = blockDim.x;
+    const long long plane = (long long)H * W;
+    for (int q = 0; q < nseq; ++q) {
+        const int y = y0 + q;
+        for (int x = threadIdx.x; x < Lx; x += T) {
+            float2 *d = &sm[saddr<kLayoutRows>(x, q, Lx, 0)];
+            const bool live = y < rows && (MODE == kRowInPlace || MODE == kRowCrop || x < W);
+            if (!live) {
+                *d = make_float2(0.0f, 0.0f);
+            } else if (MODE == kRowExpand) {
+                cp_async4(&d->x, in + (long long)y * W + x);
+                cp_async4(&d->y, in + plane + (long long)y * W + x);
+            } else {
+                cp_async8(d, pad + (long long)y * Lx + x);
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    smem_fft<MODE == kRowCrop, kLayoutRows>(sm, Lx, nseq, 0, twx, 1);
+    for (int q = 0; q < nseq; ++q) {
+        const int y = y0 + q;
+        if (y >= rows) break;
+        if (MODE == kRowCrop) {
+            for (int x = threadIdx.x; x < W; x += T) {
+                const float2 v = sm[saddr<kLayoutRows>(x, q, Lx, 0)];
+                out[(long long)y * W + x] = v.x;
+                out[plane + (long long)y * W + x] = v.y;
+            }
+        } else {
+            for (int x = threadIdx.x; x < Lx; x += T) pad[(long long)y * Lx + x] = sm[saddr<kLayoutRows>(x, q, Lx, 0)];
+        }
+    }
+}
+
+// Column pass A: for each b < L2 and strip of sw columns, L1-point transforms
+// over the rows L2 a + b.  Forward: rows >= nz_rows are zero (not loaded), all
+// outputs stored at rows L2 c + b.  Inverse: outputs a stored at rows L2 a + b
+// only below keep_rows.  (All sizes powers of two.)
+template <bool INV>
+__global__ void fft_cols_a_kernel(float2 *__restrict__ pad, int Lx, int L1, int L2, int sw, int nz_rows,
+                                  int keep_rows, const float2 *__restrict__ twy)
+{
+    extern __shared__ float2 sm[];
+    const int lsw = ilog2(sw);
+    const int lstrips = ilog2(Lx) - lsw;
+    const int b = blockIdx.x >> lstrips, x0 = (blockIdx.x & ((1 << lstrips) - 1)) << lsw;
+    const int stride = sw + 1;
+    const int n = L1 << lsw;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int a = i >> lsw, c = i & (sw - 1);
+        const int row = L2 * a + b;
+        if (row < nz_rows) cp_async8(&sm[a * stride + c], pad + (long long)row * Lx + x0 + c);
+        else sm[a * stride + c] = make_float2(0.0f, 0.0f);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    smem_fft<INV, kLayoutCols>(sm, L1, sw, stride, twy, L2);   // e^{-2 pi i k / L1} = twy[k L2]
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int a = i >> lsw, c = i & (sw - 1);
+        const int row = L2 * a + b;
+        if (row < keep_rows) pad[(long long)row * Lx + x0 + c] = sm[a * stride + c];
+    }
+}
+
+// Column pass B over the rows L2 c + b (b < L2) of each strip, with the
+// four-step twiddle e^{-2 pi i c b / Ly}.  spec == nullptr: forward only, the
+// result (the spectrum in scrambled order) stored.  Otherwise: forward,
+// product with spec (same order, its tile loaded together with the data),
+// inverse, conjugate twiddle: the middle of the convolution in one pass.
+__global__ void fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__restrict__ spec, int Lx, int L1, int L2,
+                                  int sw, const float2 *__restrict__ twy)
+{
+    extern __shared__ float2 sm[];
+    const int lsw = ilog2(sw);
+    const int lstrips = ilog2(Lx) - lsw;
+    const int c = blockIdx.x >> lstrips, x0 = (blockIdx.x & ((1 << lstrips) - 1)) << lsw;
+    const int stride = sw + 1;
+    const int n = L2 << lsw;
+    float2 *sp = sm + L2 * stride;   // the spectrum's tile
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int b = i >> lsw, q = i & (sw - 1);
+        const long long g = (long long)(L2 * c + b) * Lx + x0 + q;
+        cp_async8(&sm[b * stride + q], pad + g);
+        if (spec != nullptr) cp_async8(&sp[b * stride + q], spec + g);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {   // the four-step twiddle, in shared memory
+        const int b = i >> lsw, q = i & (sw - 1);
+        sm[b * stride + q] = cmul(sm[b * stride + q], twy[c * b]);
+    }
+    __syncthreads();
+    smem_fft<false, kLayoutCols>(sm, L2, sw, stride, twy, L1);   // e^{-2 pi i k / L2} = twy[k L1]
+    if (spec == nullptr) {
+#pragma unroll 4
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int d = i >> lsw, q = i & (sw - 1);
+            pad[(long long)(L2 * c + d) * Lx + x0 + q] = sm[d * stride + q];
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int d = i >> lsw, q = i & (sw - 1);
+        sm[d * stride + q] = cmul(sm[d * stride + q], sp[d * stride + q]);
+    }
+    __syncthreads();
+    smem_fft<true, kLayoutCols>(sm, L2, sw, stride, twy, L1);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int b = i >> lsw, q = i & (sw - 1);
+        const float2 t = twy[c * b];
+        pad[(long long)(L2 * c + b) * Lx + x0 + q] = cmul(sm[b * stride + q], make_float2(t.x, -t.y));
+    }
+}
+
+// The chirp on the Ly x Lx grid: h(k, l) = pre exp(i 2 pi C (k'^2 + l'^2) / 2^64), k' = k or k - Ly (signed offset).
+__global__ void chirp_grid_kernel(float2 *__restrict__ h, int Ly, int Lx, unsigned long long C, double pre_re,
+                                  double pre_im)
+{
+    const int k = blockIdx.y;
+    const int kk = k <= Ly / 2 ? k : k - Ly;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Lx; l += gridDim.x * blockDim.x) {
+        const int ll = l <= Lx / 2 ? l : l - Lx;
+        const unsigned long long r2 = (unsigned long long)((long long)kk * kk + (long long)ll * ll);
+        const uint32_t t = (uint32_t)((C * r2) >> 32);
+        double s, cc;
+        sincospi((double)(int)t * (1.0 / 2147483648.0), &s, &cc);
+        h[(long long)k * Lx + l] = make_float2((float)(pre_re * cc - pre_im * s), (float)(pre_re * s + pre_im * cc));
+    }
+}
+
+int threads_for(int work)
+{
+    int t = work / 16;   // 16 values per thread per stage
+    if (t < 32) t = 32;
+    if (t > 1024) t = 1024;
+    return t;
+}
+
+}  // namespace
+
+FftGrid fft_grid(int H, int W)
+{
+    auto p2 = [](int n) {
+        int l = 1;
+        while (l < n) l *= 2;
+        return l;
+    };
+    FftGrid g;
+    g.Ly = p2(2 * H - 1);
+    g.Lx = p2(2 * W - 1);
+    int lg = 0;
+    while ((1 << lg) < g.Ly) ++lg;
+    g.L1 = 1 << ((lg + 1) / 2);
+    g.L2 = g.Ly / g.L1;
+    g.ok = g.Lx <= kFftMaxLen && g.Ly <= kFftMaxLen;
+    return g;
+}
+
+static int rows_per_cta(int Lx)
+{
+    int n = 4096 / Lx;   // at least 256 threads for short rows
+    return n < 1 ? 1 : n;
+}
+
+static int strip_width(int Lx, int L)
+{
+    int sw = 4096 / (L > 0 ? L : 1);   // L x sw values per tile: 32 KB
+    if (sw < 32) sw = 32;
+    if (sw > Lx) sw = Lx;
+    return sw;
+}
+
+static size_t rows_smem(int Lx, int nseq)
+{
+    return (size_t)nseq * (Lx + (Lx >> 5)) * sizeof(float2);
+}
+
+static cudaError_t configure_rows(size_t bytes)
+{
+    static size_t done = 0;
+    if (bytes <= 48 * 1024 || bytes <= done) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (auto fn : {(const void *)fft_rows_kernel<kRowExpand>, (const void *)fft_rows_kernel<kRowInPlace>,
+                    (const void *)fft_rows_kernel<kRowCrop>, (const void *)fft_rows_kernel<kRowPadRows>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done = bytes;
+    return e;
+}
+
+cudaError_t launch_fft_chirp_spectrum(const FftGrid &g, float2 *spec, unsigned long long C, double pre_re,
+                                      double pre_im, const float2 *twx, const float2 *twy, cudaStream_t s)
+{
+    chirp_grid_kernel<<<dim3((g.Lx + 255) / 256, g.Ly), 256, 0, s>>>(spec, g.Ly, g.Lx, C, pre_re, pre_im);
+    const int nseq = rows_per_cta(g.Lx);
+    const size_t rs = rows_smem(g.Lx, nseq);
+    cudaError_t e = configure_rows(rs);
+    if (e != cudaSuccess) return e;
+    fft_rows_kernel<kRowInPlace><<<(g.Ly + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(
+        nullptr, spec, nullptr, 0, 0, g.Lx, g.Ly, nseq, twx);
+    const int swa = strip_width(g.Lx, g.L1), swb = strip_width(g.Lx, g.L2);
+    fft_cols_a_kernel<false><<<g.L2 * (g.Lx / swa), threads_for(g.L1 * swa), g.L1 * (swa + 1) * sizeof(float2), s>>>(
+        spec, g.Lx, g.L1, g.L2, swa, g.Ly, g.Ly, twy);
+    fft_cols_b_kernel<<<g.L1 * (g.Lx / swb), threads_for(g.L2 * swb), g.L2 * (swb + 1) * sizeof(float2), s>>>(
+        spec, nullptr, g.Lx, g.L1, g.L2, swb, twy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_convolve(const FftGrid &g, const float *in, int H, int W, float2 *pad, const float2 *spec,
+                                const float2 *twx, const float2 *twy, float *out, cudaStream_t s)
+{
+    const int nseq = rows_per_cta(g.Lx);
+    const size_t rs = rows_smem(g.Lx, nseq);
+    cudaError_t e = configure_rows(rs);
+    if (e != cudaSuccess) return e;
+    if (in != nullptr)
+        fft_rows_kernel<kRowExpand><<<(H + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(in, pad, nullptr, H, W,
+                                                                                             g.Lx, H, nseq, twx);
+    else
+        fft_rows_kernel<kRowPadRows><<<(H + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(nullptr, pad, nullptr,
+                                                                                              H, W, g.Lx, H, nseq, twx);
+    const int swa = strip_width(g.Lx, g.L1), swb = strip_width(g.Lx, g.L2);
+    const size_t sa = g.L1 * (swa + 1) * sizeof(float2), sb = g.L2 * (swb + 1) * sizeof(float2);
+    fft_cols_a_kernel<false><<<g.L2 * (g.Lx / swa), threads_for(g.L1 * swa), sa, s>>>(pad, g.Lx, g.L1, g.L2, swa, H,
+                                                                                     g.Ly, twy);
+    static size_t colb_done = 0;   // the product pass holds two tiles: above the default 48 KB
+    if (2 * sb > 48 * 1024 && 2 * sb > colb_done) {
+        e = cudaFuncSetAttribute(fft_cols_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * sb));
+        if (e != cudaSuccess) return e;
+        colb_done = 2 * sb;
+    }
+    fft_cols_b_kernel<<<g.L1 * (g.Lx / swb), threads_for(g.L2 * swb), 2 * sb, s>>>(pad, spec, g.Lx, g.L1, g.L2, swb,
+                                                                                  twy);
+    fft_cols_a_kernel<true><<<g.L2 * (g.Lx / swa), threads_for(g.L1 * swa), sa, s>>>(pad, g.Lx, g.L1, g.L2, swa, g.Ly,
+                                                                                    H, twy);
+    fft_rows_kernel<kRowCrop><<<(H + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(nullptr, pad, out, H, W,
+                                                                                       g.Lx, H, nseq, twx);
+    return cudaGetLastError();
+}
+
+}  // namespace cgh

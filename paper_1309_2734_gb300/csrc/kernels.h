@@ -129,6 +129,24 @@ cudaError_t launch_chirp(float2 *h, int H, int W, unsigned long long C, double p
 cudaError_t launch_expand(const float *in, int H, int W, float2 *pad, cudaStream_t s);
 cudaError_t launch_cmul(float2 *a, const float2 *b, int64_t n, cudaStream_t s);
 cudaError_t launch_crop(const float2 *pad, int H, int W, float *out, cudaStream_t s);
+// The library's own FFT path (fft.cu): padded grid Ly x Lx (powers of two >= 2H - 1, 2W - 1, at most
+// kFftMaxLen), Ly = L1 L2 for the column four-step; pad and spec are [Ly][Lx] complex, twx / twy the
+// tables e^{-2 pi i k / Lx}, e^{-2 pi i k / Ly}.  Larger grids use cuFFT.
+constexpr int kFftMaxLen = 16384;
+struct FftGrid {
+    int Ly = 0, Lx = 0, L1 = 0, L2 = 0;
+    bool ok = false;
+};
+FftGrid fft_grid(int H, int W);
+// The chirp pre * exp(i 2 pi C (k^2 + l^2) / 2^64) on the grid, transformed: its spectrum in the
+// scrambled column order the convolution uses.
+cudaError_t launch_fft_chirp_spectrum(const FftGrid &g, float2 *spec, unsigned long long C, double pre_re,
+                                      double pre_im, const float2 *twx, const float2 *twy, cudaStream_t s);
+// out ([2][H][W]) = crop(IFFT(FFT(input) * spec)); input = the planes in, or (in == nullptr) the rows
+// y < H, columns x < W of pad.
+cudaError_t launch_fft_convolve(const FftGrid &g, const float *in, int H, int W, float2 *pad, const float2 *spec,
+                                const float2 *twx, const float2 *twy, float *out, cudaStream_t s);
+
 // win[j] = {piston (or 0), A, floor(w_j^2), floor(w_j)}; geo as in the point preparation, at d_j = z_j - z_wrp
 cudaError_t launch_wrp_prep(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch, double lambda,
                             double z_wrp, bool piston, int4 *geo, uint4 *win, int *status, cudaStream_t s);

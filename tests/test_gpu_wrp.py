@@ -45,6 +45,36 @@ def test_fresnel_vs_oracle(w, h, z):
     assert _nrms_c(got, ref) <= TOL
 
 
+def test_fresnel_wide_plane_uses_the_library_fft():
+    """A plane wider than the own FFT's longest transform (2W - 1 > 16384): the cuFFT path, same result."""
+    u = workloads.complex_plane(909, 8200, 3)
+    ref = oracle.fresnel(u[0].astype(np.float64) + 1j * u[1], 8e-6, 532e-9, 0.2)
+    with Hologram(8200, 3, 8e-6, 532e-9) as hol:
+        hol.profile(True)
+        got = _cplx(hol.fresnel(torch.from_numpy(u).cuda(), 0.2))
+        hol.sync()
+        names = set(hol.profile_read())
+    assert "cufft_c2c" in names
+    assert _nrms_c(got, ref) <= TOL
+
+
+def test_fresnel_own_fft_on_display_sizes():
+    """1920 x 1080 (padded to 4096 x 4096 by the own FFT): sampled pixels against the direct sum."""
+    u = workloads.complex_plane(908, 1920, 1080)
+    uc = u[0].astype(np.float64) + 1j * u[1]
+    rng = np.random.default_rng(907)
+    cols = np.concatenate([rng.integers(0, 1920, 24), [0, 1919]])
+    rows = np.concatenate([rng.integers(0, 1080, 24), [1079, 0]])
+    ref = oracle.fresnel_at(uc, 8e-6, 532e-9, 0.25, cols, rows)
+    with Hologram(1920, 1080, 8e-6, 532e-9) as hol:
+        hol.profile(True)
+        got = _cplx(hol.fresnel(torch.from_numpy(u).cuda(), 0.25))
+        hol.sync()
+        names = set(hol.profile_read())
+    assert "fresnel_fft" in names and "cufft_c2c" not in names
+    assert _nrms_c(got[rows, cols], ref) <= TOL
+
+
 def test_fresnel_in_place_and_cached_spectra():
     """d_out == d_in, and spectra for alternating distances (the cache must follow z)."""
     u = workloads.complex_plane(910, 96, 80)
