@@ -1,17 +1,18 @@
-// f3: Fresnel diffraction, Eq. 10, on the pixel grid.
+// f3: Fresnel diffraction, Eq. 10, on the pixel grid -- the path for grids
+// beyond the library's own FFT (fft.cu: padded sides up to 16384).
 //
 //   O(m, n) = pre * sum_{m', n'} u(m', n') h(m - m', n - n'),
 //   h(k, l) = exp(i pi p^2 (k^2 + l^2) / (lambda z)),  pre = exp(i 2 pi z / lambda) / (i lambda z) * p^2,
 //
-// the linear convolution of the H x W input with the chirp, cropped to H x W.
-// It is evaluated as the paper does, by zero-padding both to 2H x 2W (offsets
-// k in (-H, H) at k mod 2H), FFT, pointwise product, inverse FFT and crop, so
-// that the circular convolution wraps nothing into the kept window.  The FFTs
-// are cuFFT's single-precision C2C transforms; the kernels here expand the
-// input planes into the padded buffer, build the chirp (64-bit fixed-point
-// turns c k^2 + c l^2, accurate sine and cosine; the prefactor and the inverse
-// transform's 1/(4 H W) folded in), multiply by its cached spectrum, and crop
-// back into planes.
+// the linear convolution of the H x W input with the chirp, cropped to H x W,
+// by zero-padding both to 2H x 2W (offsets k in (-H, H) at k mod 2H), FFT,
+// pointwise product, inverse FFT and crop, so that the circular convolution
+// wraps nothing into the kept window.  Here the FFTs are cuFFT's
+// single-precision C2C transforms; the kernels expand the input planes into
+// the padded buffer, build the chirp (64-bit fixed-point turns c k^2 + c l^2,
+// accurate sine and cosine; the prefactor and the inverse transform's
+// 1/(4 H W) folded in), multiply by its cached spectrum, and crop back into
+// planes.
 #include <cufft.h>
 
 #include "kernels.h"
