@@ -373,8 +373,8 @@ __global__ void chirp_grid_kernel(float2 *__restrict__ h, int Ly, int Lx, unsign
         const int ll = l <= Lx / 2 ? l : l - Lx;
         const unsigned long long r2 = (unsigned long long)((long long)kk * kk + (long long)ll * ll);
         const uint32_t t = (uint32_t)((C * r2) >> 32);
-        double s, cc;
-        sincospi((double)(int)t * (1.0 / 2147483648.0), &s, &cc);
+        float s, cc;   // accurate single-precision sine and cosine of 2 pi t (FP64 is slow on this part)
+        sincospif((float)(int)t * (1.0f / 2147483648.0f), &s, &cc);
         h[(long long)k * Lx + l] = make_float2((float)(pre_re * cc - pre_im * s), (float)(pre_re * s + pre_im * cc));
     }
 }

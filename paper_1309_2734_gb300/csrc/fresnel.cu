@@ -41,9 +41,9 @@ __global__ void chirp_kernel(float2 *__restrict__ h, int H, int W, unsigned long
         const int ll = l < W ? l : l - W2;
         const unsigned long long r2 = (unsigned long long)((long long)kk * kk + (long long)ll * ll);   // < 2^31
         const uint32_t t = (uint32_t)((C * r2) >> 32);              // turn, 2^-32 units (exact but the last bit)
-        const double a = (double)(int)t * (1.0 / 2147483648.0);     // [-1, 1): twice the signed turn
-        double s, c;
-        sincospi(a, &s, &c);                                        // exp(i 2 pi t)
+        const float a = (float)(int)t * (1.0f / 2147483648.0f);     // [-1, 1): twice the signed turn
+        float s, c;
+        sincospif(a, &s, &c);                                       // exp(i 2 pi t), accurate single precision
         h[i] = make_float2((float)(pre_re * c - pre_im * s), (float)(pre_re * s + pre_im * c));
     }
 }

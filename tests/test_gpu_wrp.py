@@ -192,3 +192,22 @@ def test_wrp_empty_cloud_gives_zeros():
         o = hol.wrp(e, e, 0.5)
         hol.sync()
         assert torch.count_nonzero(o).item() == 0
+
+
+def test_numerical_reconstruction_focuses_on_the_point():
+    """Back-propagating the hologram's object wave by the point's distance (Fresnel diffraction with a negative
+    distance, the numerical reconstruction of the paper's Fig. 4) brings the light back to the point: the
+    intensity peaks at (x_j, y_j), with most of the energy of the reconstructed plane there."""
+    z_wrp, d = 0.05, 0.004
+    N = 512
+    xyz = np.array([[200.0, 310.0, z_wrp + d]], dtype=np.float32)
+    amp = np.ones(1, dtype=np.float32)
+    with Hologram(N, N, 8e-6, 532e-9) as hol:
+        hol.set_phase_model("fresnel_piston")
+        o = hol.wrp(torch.from_numpy(xyz).cuda(), torch.from_numpy(amp).cuda(), z_wrp)
+        back = hol.fresnel(o, -(z_wrp + d))
+        hol.sync()
+    inten = np.abs(_cplx(back)) ** 2
+    r, c = np.unravel_index(np.argmax(inten), inten.shape)
+    assert (r, c) == (310, 200)
+    assert inten[305:316, 195:206].sum() > 0.5 * inten.sum()
