@@ -485,6 +485,52 @@ def run_ours(args):
                                   "speedup_vs_k20": t_k20 * 1e3 / ms, "kernel_ms": {k: v[1] for k, v in kp.items()},
                                   "step": "WRP record + Fresnel diffraction (2 FFTs, cached chirp spectrum) + kinoform8"}
 
+    # the batched workload: 64 frames of uneven size and point count in one cgh_batch call (persistent
+    # launches per form kind, captured in a CUDA graph and replayed), forms and tiles per frame from the
+    # autotuner at each accuracy class; NRMS on sampled pixels of every frame (CPU leg)
+    vbatch = {}
+    if not args.no_batch:
+        from paper_1309_2734_gb300 import _lib, batch as run_batch
+        frames = workloads.video_batch()
+        fdev = [(torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda(), c.width, c.height, c.pitch_m,
+                 c.lambda_m) for c in frames]
+        fouts = [torch.empty((c.height, c.width), dtype=torch.float32, device="cuda") for c in frames]
+        evals = sum(c.evals for c in frames)
+        rng = np.random.default_rng(6464)
+        picks = [(rng.integers(0, c.width, 16), rng.integers(0, c.height, 16)) for c in frames]
+        for tol in (1e-5, 2e-3):
+            with Hologram(8, 8, 8e-6, 532e-9, form="auto", stream=stream, timeout_ms=20000) as hb:
+                hb.set_option(_lib.CGH_OPT_TOLERANCE_E9, int(round(tol * 1e9)))
+                _lib.check(_lib.cgh_autotune(hb.ctx, 0), "cgh_autotune")
+                run_batch(hb, fdev, fouts)   # plan and graph, untimed
+                hb.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 3
+                e0.record(stream)
+                for _ in range(reps):
+                    run_batch(hb, fdev, fouts)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                hb.sync()
+                ms = e0.elapsed_time(e1) / reps
+                picked = [o[torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()].cpu().numpy()
+                          for o, (c, r) in zip(fouts, picks)]
+            vbatch[f"nrms_{tol:g}"] = {"ms_per_batch": ms, "holograms_per_s": len(frames) / (ms * 1e-3),
+                                        "gevals_per_s": evals / (ms * 1e-3) / 1e9, "_samples": picked}
+        vbatch["frames"] = len(frames)
+        vbatch["evals_per_batch"] = evals
+        vbatch["sizes"] = sorted({f"{c.width}x{c.height}" for c in frames})
+        vbatch["points"] = [int(min(c.n_points for c in frames)), int(max(c.n_points for c in frames))]
+        if not args.no_cpu_baseline:
+            import oracle
+            refs = [oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cc, rr) for c, (cc, rr) in zip(frames, picks)]
+            for key in [k for k in vbatch if k.startswith("nrms_")]:
+                got = np.concatenate(vbatch[key]["_samples"])
+                vbatch[key]["nrms_vs_oracle"] = oracle.nrms(got, np.concatenate(refs))
+        for key in [k for k in vbatch if k.startswith("nrms_")]:
+            vbatch[key].pop("_samples", None)
+        del fdev, fouts
+
     h.set_form(args.form)
     h.point_cloud(xyz, amp, out)
     h.sync()
@@ -558,6 +604,7 @@ def run_ours(args):
         "forms": forms,
         "paper_kinoform_1920x1080": paper,
         "layered_4096x4096_n1000000": large,
+        "video_batch_64": vbatch,
         "paper_fresnel_diffraction": fresnel_t,
         "paper_wrp_2048x2048": wrp_t,
         "cpu_baseline": cpu,
@@ -580,6 +627,7 @@ def main():
     ap.add_argument("--compare", nargs="*",
                     default=["direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame batched workload")
     ap.add_argument("--no-fresnel", action="store_true",
                     help="skip the Fresnel diffraction and wavefront-recording workloads of Tables 5-6")
     ap.add_argument("--no-large", action="store_true",
