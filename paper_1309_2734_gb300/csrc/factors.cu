@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kGroupThreads)
 {
     __shared__ uint32_t tile_hi[kGroupTile * kTileStride];
     __shared__ uint32_t tile_lo[MODE == kFactorSplit16 ? kGroupTile * kTileStride : 1];
+    __shared__ uint4 stage[kGroupThreads / 32][32];   // per warp: {G, E, -A, 0} of 32 members
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p_blocks = (height + 31) / 32;
     const bool is_p = (int)blockIdx.y < p_blocks;
@@ -184,9 +185,8 @@ __global__ void __launch_bounds__(kGroupThreads)
     const int line = r0 + lane;
     const int s_base = blockIdx.x * kGroupTile;
     const float inv = 1.0f / *wscale;
-    // 2^8 rounds the 23-bit mantissa to nearest; plus the reference phase of this row (P': ky n)
-    // or column (Q': kx m + phi0)
-    const uint32_t add = 256u + (is_p ? ref_turn(ref, 0, line) - ref.phi0 : ref_turn(ref, line, 0));
+    // reference phase of this row (P': ky n) or column (Q': kx m + phi0)
+    const uint32_t radd = is_p ? ref_turn(ref, 0, line) - ref.phi0 : ref_turn(ref, line, 0);
     for (int k = warp; k < kGroupTile; k += kGroupThreads / 32) {
         const int slot = s_base + k;
         float re = 0.0f, im = 0.0f;
@@ -195,32 +195,43 @@ __global__ void __launch_bounds__(kGroupThreads)
             const unsigned long long C = planes[d.z];
             const uint32_t chi = (uint32_t)(C >> 32), clo = (uint32_t)C;
             if (is_p) {
-                const int2 *m = members + d.x;       // same address in every lane
-                int i = 0;
-                for (; i + 4 <= d.y; i += 4) {
-                    int2 v[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) v[q] = m[i + q];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float sn, cs;
-                        half_turn_sincos(chi, clo, (uint32_t)(line - v[q].x), add, sn, cs);
-                        re = fmaf(__int_as_float(v[q].y), cs, re);
-                        im = fmaf(__int_as_float(v[q].y), sn, im);
+                // (r0 + l - y)^2 = D^2 + 2 D l + l^2, D = r0 - y: per member G = C D^2 and E = 2 C D (top 32
+                // bits, one lane each), per lane the phase G + E l; the lane's C l^2 (and the reference) is
+                // one rotation of the sum at the end.  E l in 32 bits is off by at most l < 32 units of 2^-32.
+                const unsigned long long C2 = C << 1;
+                for (int base = 0; base < d.y; base += 32) {
+                    const int j = base + lane;
+                    if (j < d.y) {
+                        const int2 v = members[d.x + j];
+                        const int D = r0 - v.x;
+                        const uint32_t d2 = (uint32_t)(D * D);   // < 2^30
+                        const uint32_t G = chi * d2 + __umulhi(clo, d2);
+                        const uint32_t E = (uint32_t)((C2 * (unsigned long long)(long long)D) >> 32);
+                        stage[warp][lane] = make_uint4(G + 256u, E, (uint32_t)v.y, 0u);   // +2^8: round to 23 bits
                     }
+                    __syncwarp();
+                    const int n = min(32, d.y - base);
+                    for (int i = 0; i < n; ++i) {
+                        const uint4 s = stage[warp][i];                              // same address in every lane
+                        const uint32_t t = s.x + s.y * (uint32_t)lane;
+                        const float f = __uint_as_float((t >> 9) | 0x3f800000u);
+                        float sn, cs;
+                        __sincosf(fmaf(f, kTurnK1, -kTurnK0), &sn, &cs);             // angle - pi
+                        re = fmaf(__uint_as_float(s.z), cs, re);                      // members carry -A
+                        im = fmaf(__uint_as_float(s.z), sn, im);
+                    }
+                    __syncwarp();
                 }
-                for (; i < d.y; ++i) {
-                    const int2 v = m[i];
-                    float sn, cs;
-                    half_turn_sincos(chi, clo, (uint32_t)(line - v.x), add, sn, cs);
-                    re = fmaf(__int_as_float(v.y), cs, re);
-                    im = fmaf(__int_as_float(v.y), sn, im);
-                }
-                re *= inv;
-                im *= inv;
+                // times exp(i 2 pi (C l^2 + reference)): half_turn_sincos gives minus its cosine and sine
+                float sn, cs;
+                half_turn_sincos(chi, clo, (uint32_t)lane, 256u + radd, sn, cs);
+                const float wr = -cs, wi = -sn;
+                const float r2 = re * wr - im * wi, i2 = re * wi + im * wr;
+                re = r2 * inv;
+                im = i2 * inv;
             } else {
                 float sn, cs;
-                half_turn_sincos(chi, clo, (uint32_t)(line - d.w), add, sn, cs);
+                half_turn_sincos(chi, clo, (uint32_t)(line - d.w), 256u + radd, sn, cs);
                 re = -cs;   // cos alpha
                 im = sn;    // -sin alpha
             }
