@@ -1,5 +1,5 @@
 // Internal: the context behind the C ABI's opaque cgh_ctx, its workspace
-// helpers, and the pipeline entry points shared by api.cu, batch.cu and tuner.cpp.
+// helpers, and the pipeline entry points shared by api.cu, batch.cu and tuner.cu.
 #pragma once
 
 #include <chrono>
