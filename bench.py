@@ -161,7 +161,9 @@ def cpu_baseline(cloud, target_s: float = 12.0, gpu_field=None):
            "seconds": dt}
     nrms = None
     if gpu_field is not None:
-        nrms = oracle.nrms(gpu_field[r0:r0 + rows], ref)
+        got = gpu_field[r0:r0 + rows].astype(np.float64)
+        nrms = oracle.nrms(got, ref)
+        out["max_abs_err_over_rms"] = float(np.max(np.abs(got - ref)) / np.sqrt(np.mean(ref * ref)))
     return out, nrms, (r0, rows, ref)
 
 
@@ -567,6 +569,11 @@ def run_ours(args):
         roof = {"bound": "alu", "unit": "Gcos/s (MUFU)",
                 "peak_basis": f"{MUFU_PER_SM_PER_CLK} MUFU cos/clk/SM x {props.multi_processor_count} SMs x "
                               f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)"}
+        # the same pipe measured in this run: independent hardware sines on every SM (cgh_measure_mufu)
+        from paper_1309_2734_gb300 import _lib
+        probe = _lib.cgh_measure_mufu(h.ctx) / 1e9
+        roof["peak_probe"] = probe
+        roof["frac_of_probe"] = (cloud.evals / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e9) / probe if dom_ms > 0 else None
     traffic = ncu_traffic(dom, args.form, cloud.name)
 
     cpu, nrms = (None, None)
@@ -595,7 +602,9 @@ def run_ours(args):
         "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
         "roofline": {"kernel": dom, "bound": roof["bound"], "achieved": achieved, "peak": peak,
                      "unit": roof["unit"], "frac": (achieved / peak) if achieved else None,
-                     "traffic": traffic, "peak_basis": roof["peak_basis"]},
+                     "traffic": traffic, "peak_basis": roof["peak_basis"],
+                     **({"peak_probe": roof["peak_probe"], "frac_of_probe": roof["frac_of_probe"]}
+                        if "peak_probe" in roof else {})},
         "clocks": clocks,
         "e2e": {"value": cloud.evals * args.steps * world / e2e_total / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": int(cloud.xyz.nbytes + cloud.amp.nbytes),

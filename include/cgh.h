@@ -184,6 +184,15 @@ int cgh_wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t
  */
 int cgh_wrp(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_points, double z_wrp_m, float *d_out);
 
+/*
+ * Measures the throughput of the hardware sine (one MUFU operation per
+ * result; eight independent chains per thread, every SM busy), the pipe that
+ * bounds CGH_DIRECT_SFU, and stores it in *results_per_s.  For stating the
+ * direct kernel's roofline against a measured peak; the paper has no
+ * counterpart.  Synchronises the context's stream.  CGH_ECUDA on failure.
+ */
+int cgh_measure_mufu(cgh_ctx *ctx, double *results_per_s);
+
 /* Selects the form (CGH_FORM_* above). */
 int cgh_set_form(cgh_ctx *ctx, int form);
 

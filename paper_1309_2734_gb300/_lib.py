@@ -37,7 +37,8 @@ CGH_PHASE_FRESNEL, CGH_PHASE_FRESNEL_PISTON, CGH_PHASE_SPHERICAL = 0, 1, 2
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
            "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
-           "cgh_autotune", "cgh_wave", "cgh_set_reference", "cgh_fresnel", "cgh_wrp_record", "cgh_wrp")
+           "cgh_autotune", "cgh_wave", "cgh_set_reference", "cgh_fresnel", "cgh_wrp_record", "cgh_wrp",
+           "cgh_measure_mufu")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_fresnel": ([vp, vp, cd, vp], ci),
             "cgh_wrp_record": ([vp, vp, vp, i64, cd, vp], ci),
             "cgh_wrp": ([vp, vp, vp, i64, cd, vp], ci),
+            "cgh_measure_mufu": ([vp, ctypes.POINTER(cd)], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -178,6 +180,13 @@ def cgh_profile_read(ctx: int, reset: bool = True) -> dict:
 
 def cgh_wave(ctx: int, d_xyz: int, d_amp: int, n_points: int, d_out: int) -> int:
     return load().cgh_wave(ctx, d_xyz, d_amp, int(n_points), d_out)
+
+
+def cgh_measure_mufu(ctx: int) -> float:
+    """Measured hardware-sine results per second of the whole GPU."""
+    v = ctypes.c_double(0.0)
+    check(load().cgh_measure_mufu(ctx, ctypes.byref(v)), "cgh_measure_mufu")
+    return float(v.value)
 
 
 def cgh_fresnel(ctx: int, d_in: int, z_m: float, d_out: int) -> int:

@@ -730,6 +730,16 @@ int cgh_set_form(cgh_ctx *ctx, int form)
     return CGH_OK;
 }
 
+int cgh_measure_mufu(cgh_ctx *ctx, double *results_per_s)
+{
+    if (!ctx || !results_per_s) return CGH_EINVAL;
+    DeviceGuard g(ctx->device);
+    const double r = measure_mufu_rate(ctx->num_sms, ctx->stream);
+    if (!(r > 0.0)) return CGH_ECUDA;
+    *results_per_s = r;
+    return CGH_OK;
+}
+
 int cgh_set_reference(cgh_ctx *ctx, double sin_x, double sin_y, double phase0_rad)
 {
     if (!ctx || !std::isfinite(sin_x) || !std::isfinite(sin_y) || !std::isfinite(phase0_rad)) return CGH_EINVAL;

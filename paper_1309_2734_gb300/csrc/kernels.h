@@ -160,6 +160,9 @@ cudaError_t launch_wrp_bands(const int4 *geo, const uint4 *win, int n_pad, int H
 cudaError_t launch_wrp_record(const int4 *geo, const uint4 *win, int n_pad, int H, int W, const int *offset,
                               const int *list, float2 *pad, int64_t pad_ld, float *planes, cudaStream_t s);
 
+// Hardware-sine throughput (results per second) of the whole GPU, measured; -1 on failure (probe.cu).
+double measure_mufu_rate(int num_sms, cudaStream_t s);
+
 // a4: tcgen05 GEMM, out[n][m] (+)= sum_k P[n][k] Q[m][k] over K splits (gemm.cu).
 struct GemmPlan {
     int mode;          // kFactorF16 / kFactorBF16 / kFactorSplit16

@@ -253,3 +253,12 @@ def test_device_wait_times_out_and_context_recovers():
         h.sync()
     ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
     _check(f.cpu().numpy(), ref, c.amp)
+
+
+def test_measured_mufu_rate_is_plausible():
+    """The hardware-sine probe behind the roofline: within (0.5, 1.1) x 16 results/clk/SM x SMs x max clock."""
+    props = torch.cuda.get_device_properties(0)
+    with Hologram(8, 8, 8e-6, 532e-9) as h:
+        r = _lib.cgh_measure_mufu(h.ctx)
+    nominal = 16 * props.multi_processor_count * 2.07e9
+    assert 0.5 * nominal < r < 1.1 * nominal, r
