@@ -67,6 +67,14 @@ def test_null_context_everywhere(lib):
     assert lib.cgh_set_form(None, 1) == _lib.CGH_EINVAL
     assert lib.cgh_set_option(None, 1, 1) == _lib.CGH_EINVAL
     assert lib.cgh_set_stream(None, None) == _lib.CGH_EINVAL
+    assert lib.cgh_set_reference(None, 0.0, 0.0, 0.0) == _lib.CGH_EINVAL
+    assert lib.cgh_wave(None, None, None, 0, None) == _lib.CGH_EINVAL
+    assert lib.cgh_fresnel(None, None, 0.1, None) == _lib.CGH_EINVAL
+    assert lib.cgh_wrp(None, None, None, 0, 0.5, None) == _lib.CGH_EINVAL
+    assert lib.cgh_wrp_record(None, None, None, 0, 0.5, None) == _lib.CGH_EINVAL
+    assert lib.cgh_autotune(None, 0) == _lib.CGH_EINVAL
+    v = ctypes.c_double(0.0)
+    assert lib.cgh_measure_mufu(None, ctypes.byref(v)) == _lib.CGH_EINVAL
     assert lib.cgh_destroy(None) == _lib.CGH_OK
 
 
