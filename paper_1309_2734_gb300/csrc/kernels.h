@@ -19,9 +19,12 @@ constexpr int kPointTile = 256;
 // kAuxZero: 0 (a piston slot for kernels that add one, none wanted).  ext
 // (optional, the spherical form) receives {(p / z_j)^2, z_j / (2 lambda)}.
 enum { kAuxSecondDiff = 0, kAuxPiston = 1, kAuxZero = 2 };
+// ext.x is negated when some pixel of the width x height hologram has u = r^2 / z^2 >= kSeriesU.
+constexpr double kSeriesU = 0.05;
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
                                double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
-                               cudaStream_t s, int aux_x = kAuxSecondDiff, float2 *ext = nullptr);
+                               cudaStream_t s, int aux_x = kAuxSecondDiff, float2 *ext = nullptr, int width = 0,
+                               int height = 0);
 
 // The plane-wave reference phase of Eq. 5, phi_r(m, n) = kx m + ky n + phi0,
 // common to every point of a launch: kx, ky in 2^-64 turn per pixel, phi0 in

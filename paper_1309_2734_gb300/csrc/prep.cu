@@ -18,7 +18,7 @@ namespace cgh {
 __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *__restrict__ amp, int n,
                                    int n_pad, double pitch, double lambda, int4 *__restrict__ geo,
                                    uint2 *__restrict__ aux, int *status, float *amp_max, int aux_x,
-                                   float2 *__restrict__ ext)
+                                   float2 *__restrict__ ext, int width, int height)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
@@ -52,21 +52,27 @@ __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *_
     }
     aux[j] = make_uint2(w, __float_as_uint(a));
     if (ext != nullptr) {
+        // (p / z)^2, positive when u = r^2 / z^2 stays below kSeriesU at every pixel of a width x height
+        // hologram (then the spherical kernel may use the series of sqrt(1 + u)), negated otherwise
         const double pz = pitch / (double)fz;
-        ext[j] = make_float2((float)(pz * pz), (float)((double)fz / (2.0 * lambda)));
+        const double dx = fmax(fabs((double)fx), fabs((double)(width - 1) - (double)fx));
+        const double dy = fmax(fabs((double)fy), fabs((double)(height - 1) - (double)fy));
+        const double umax = (dx * dx + dy * dy) * pz * pz;
+        const float q = (float)(pz * pz);
+        ext[j] = make_float2(umax < kSeriesU ? q : -q, (float)((double)fz / (2.0 * lambda)));
     }
     if (amp_max != nullptr) atomicMax(reinterpret_cast<unsigned *>(amp_max), __float_as_uint(fabsf(a)));
 }
 
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
                                double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
-                               cudaStream_t s, int aux_x, float2 *ext)
+                               cudaStream_t s, int aux_x, float2 *ext, int width, int height)
 {
     if (n_pad <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (n_pad + threads - 1) / threads;
     prep_points_kernel<<<blocks, threads, 0, s>>>(d_xyz, d_amp, n, n_pad, pitch, lambda, geo, aux, status,
-                                                         amp_max, aux_x, ext);
+                                                         amp_max, aux_x, ext, width, height);
     return cudaGetLastError();
 }
 

@@ -14,10 +14,16 @@
 //   delta = Z (u / (1 + s) - u / 2) = -(Z / 2) (u / (1 + s))^2.
 // Per term: one reciprocal square root, one reciprocal (MUFU) and the sine
 // (MUFU); relative error of delta a few 1e-7, i.e. ~1e-7 turn per turn of delta.
+// When u < 0.05 at every pixel for a point (flagged by the point preparation:
+// the sign of (p / z)^2), delta comes from the binomial series instead,
+//   sqrt(1 + u) - 1 - u / 2 = -u^2/8 + u^3/16 - 5 u^4/128 + 7 u^5/256 - 21 u^6/1024 + ...,
+// five FMA-pipe terms whose remainder is below 0.13 u^5 of the first
+// (4e-8 at u = 0.05): the sine is then the only MUFU operation of the term.
 //
 // Point tiles are staged in shared memory with plain cooperative loads (the
-// kernel is bound by the MUFU pipe, three operations per term, so the loads
-// need no asynchronous pipeline and the kernel has no waits to bound).
+// kernel is bound by the MUFU pipe -- three operations per term in the closed
+// form, one with the series -- so the loads need no asynchronous pipeline and
+// the kernel has no waits to bound).
 #include "device_util.cuh"
 #include "kernels.h"
 
@@ -33,7 +39,7 @@ constexpr float kRoundMagic = 12582912.0f;                       // 1.5 2^23: x 
 
 static_assert(kSphBX * kSphBY == kPointTile, "one point per thread in each tile load");
 
-template <int PLANES>
+template <int PLANES, bool SERIES>
 __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, const float2 x, int m0, int n0,
                                                 uint32_t rg, uint32_t rdx, uint32_t rdy,
                                                 float (&acc)[PLANES][kSphTR][kSphTL])
@@ -49,7 +55,7 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
     uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0 + rdy;
     const uint32_t D = __funnelshift_l(clo, chi, 1);
     const float a = __uint_as_float(w.y);
-    const float qz = x.x, zh = x.y;   // (p / z)^2, z / (2 lambda)
+    const float qz = fabsf(x.x), zh = x.y;   // (p / z)^2, z / (2 lambda)
     // squared column and row offsets of the thread's pixels, in pixels^2
     float xs[kSphTL], ys[kSphTR];
 #pragma unroll
@@ -74,10 +80,20 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
 #pragma unroll
         for (int i = 0; i < kSphTL; ++i) {
             const float u = (xs[i] + ys[r]) * qz;
-            const float rs = rsqrtf(1.0f + u);
-            const float s = (1.0f + u) * rs;
-            const float v = __fdividef(u, 1.0f + s);
-            const float delta = -zh * v * v;                                 // turns, <= 0
+            float delta;   // turns, <= 0
+            if constexpr (SERIES) {
+                float c = -0.0205078125f;                      // -21/1024
+                c = fmaf(c, u, 0.02734375f);                   // 7/256
+                c = fmaf(c, u, -0.0390625f);                   // -5/128
+                c = fmaf(c, u, 0.0625f);                       // 1/16
+                c = fmaf(c, u, -0.125f);                       // -1/8
+                delta = (2.0f * zh) * (u * u) * c;             // Z u^2 (...)
+            } else {
+                const float rs = rsqrtf(1.0f + u);
+                const float s = (1.0f + u) * rs;
+                const float v = __fdividef(u, 1.0f + s);
+                delta = -zh * v * v;
+            }
             const float df = delta - ((delta + kRoundMagic) - kRoundMagic);  // its fractional part, [-1/2, 1/2]
             const float f = __uint_as_float(__funnelshift_r(g[i], 0x7fu, 9));
             const float ang = fmaf(df, kSphK1, fmaf(f, kSphK1, -kSphK0));   // 2 pi (t - 1/4), |ang| <= 2 pi
@@ -139,8 +155,12 @@ __global__ void __launch_bounds__(kSphBX *kSphBY, 2)
 #pragma unroll
                 for (int i = 0; i < kSphTL; ++i) part[c][r][i] = 0.0f;
 #pragma unroll 1
-        for (int p = 0; p < kPointTile; ++p)
-            sph_point_terms<PLANES>(s_geo[p], s_aux[p], s_ext[p], m0, n0, rg, rdx, rdy, part);
+        for (int p = 0; p < kPointTile; ++p) {
+            if (s_ext[p].x >= 0.0f)   // the same point, so the same branch, in every thread
+                sph_point_terms<PLANES, true>(s_geo[p], s_aux[p], s_ext[p], m0, n0, rg, rdx, rdy, part);
+            else
+                sph_point_terms<PLANES, false>(s_geo[p], s_aux[p], s_ext[p], m0, n0, rg, rdx, rdy, part);
+        }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
 #pragma unroll

@@ -107,6 +107,17 @@ def test_spherical_vs_oracle(form, w, h, n, z):
     assert oracle.nrms(got, want) < 0.3 * oracle.nrms(got, fres)
 
 
+def test_spherical_closed_form_branch():
+    """Points 4-6 mm from a 160 x 160 hologram: u = r^2/z^2 reaches 0.13, beyond the series' range, so every
+    term takes the closed form -(Z/2)(u/(1+sqrt(1+u)))^2 (delta up to ~20 turns at the corners)."""
+    c = workloads.random_cloud(812, 160, 160, 400, z_range=(0.004, 0.006))
+    umax = ((159 * 8e-6) ** 2 * 2) / (0.004 ** 2)
+    assert umax > 0.05
+    want = oracle.model_wave(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, 160, 160).real
+    got, _, _ = _run(c, "direct_sfu", 2)
+    assert oracle.nrms(got, want) <= 1e-5
+
+
 def test_spherical_wave_kinoform_and_reference():
     c = workloads.random_cloud(807, 330, 210, 1300, z_range=(0.2, 0.6))
     want = oracle.model_wave(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, 330, 210, reference=REF)
