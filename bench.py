@@ -556,8 +556,12 @@ def run_ours(args):
         dom_launches, dom_ms = prof.get(dom, (0, 0.0))
         passes = 3 if args.form == "gemm_split16" else 1
         peak = peaks.get("bf16_tflops") or 1939.7
-        achieved = (4.0 * cloud.evals * passes / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e12) if dom_ms > 0 else None
-        roof = {"bound": "tensor", "unit": "TFLOP/s",
+        # the GEMM's K: 2 per point, or 2 per (plane, column) group when the grouped form ran; the flops of all
+        # timed steps over the kernel's total time = flops per launch over the average launch (chunks included)
+        grouped = "group_factors" in prof
+        k_units = int(np.unique(cloud.xyz[:, [0, 2]], axis=0).shape[0]) if grouped else N
+        achieved = (4.0 * W * H * k_units * passes * args.steps / (dom_ms * 1e-3) / 1e12) if dom_ms > 0 else None
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "gemm_k": 2 * k_units,
                 "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
     else:
         # MUFU-bound: one hardware sine per evaluation at most

@@ -420,14 +420,14 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
     const int64_t plane = (int64_t)width * height;
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
-    const size_t ext_bytes = align_up((size_t)n_pad * sizeof(float2), 256);
+    const size_t ext_bytes = align_up((size_t)n_pad * sizeof(float4), 256);
     const size_t part_bytes = split > 1 ? (size_t)split * planes * plane * sizeof(float) : 0;
     int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + ext_bytes + part_bytes);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->ws);
     int4 *geo = reinterpret_cast<int4 *>(base);
     uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
-    float2 *ext = reinterpret_cast<float2 *>(base + geo_bytes + aux_bytes);
+    float4 *ext = reinterpret_cast<float4 *>(base + geo_bytes + aux_bytes);
     float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes + ext_bytes);
     cudaError_t e;
     {

@@ -18,11 +18,11 @@ namespace cgh {
 __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *__restrict__ amp, int n,
                                    int n_pad, double pitch, double lambda, int4 *__restrict__ geo,
                                    uint2 *__restrict__ aux, int *status, float *amp_max, int aux_x,
-                                   float2 *__restrict__ ext, int width, int height)
+                                   float4 *__restrict__ ext, int width, int height)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
-    if (ext != nullptr) ext[j] = make_float2(0.0f, 0.0f);
+    if (ext != nullptr) ext[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (j >= n) {  // padding: zero amplitude, zero phase
         geo[j] = make_int4(0, 0, 0, 0);
         aux[j] = make_uint2(0u, 0u);
@@ -52,21 +52,28 @@ __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *_
     }
     aux[j] = make_uint2(w, __float_as_uint(a));
     if (ext != nullptr) {
-        // (p / z)^2, positive when u = r^2 / z^2 stays below kSeriesU at every pixel of a width x height
-        // hologram (then the spherical kernel may use the series of sqrt(1 + u)), negated otherwise
-        const double pz = pitch / (double)fz;
-        const double dx = fmax(fabs((double)fx), fabs((double)(width - 1) - (double)fx));
-        const double dy = fmax(fabs((double)fy), fabs((double)(height - 1) - (double)fy));
-        const double umax = (dx * dx + dy * dy) * pz * pz;
-        const float q = (float)(pz * pz);
-        ext[j] = make_float2(umax < kSeriesU ? q : -q, (float)((double)fz / (2.0 * lambda)));
+        // {(p / z)^2, z / (2 lambda)} as float pairs {hi, hi, lo, lo}, the spherical kernel's two flags in the
+        // signs of the high parts.  Tile centres lie up
+        // to half a thread tile (hx, hy) beyond the farthest pixel, so cx, cy bound |centre - point| per axis;
+        // the quadratic in w = u - U0 is used when its truncation error Z max|h'''| wmax^3 / 6 = zh wmax^3 / 8
+        // and its range max|d1 w + d2 w^2| <= zh (umax / 2) wmax + (zh / 4) wmax^2 are within bounds.
+        const double pz = pitch / (double)fz, qz = pz * pz, zh = (double)fz / (2.0 * lambda);
+        const double hx = 0.5 * (kSphTileCols - 1), hy = 0.5 * (kSphTileRows - 1);
+        const double cx = fmax(fabs((double)fx), fabs((double)(width - 1) - (double)fx)) + hx;
+        const double cy = fmax(fabs((double)fy), fabs((double)(height - 1) - (double)fy)) + hy;
+        const double umax = (cx * cx + cy * cy) * qz;
+        const double wmax = (2.0 * hx * cx + hx * hx + 2.0 * hy * cy + hy * hy) * qz;
+        const bool quad = zh * wmax * wmax * wmax / 8.0 <= kSphFitTurns &&
+                          zh * (0.5 * umax) * wmax + 0.25 * zh * wmax * wmax <= kSphRangeTurns;
+        const float q = (float)qz, h = (float)zh;   // and the pair's low parts, for the double-float d0
+        ext[j] = make_float4(quad ? q : -q, umax < kSeriesU ? h : -h, (float)(qz - (double)q), (float)(zh - (double)h));
     }
     if (amp_max != nullptr) atomicMax(reinterpret_cast<unsigned *>(amp_max), __float_as_uint(fabsf(a)));
 }
 
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
                                double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
-                               cudaStream_t s, int aux_x, float2 *ext, int width, int height)
+                               cudaStream_t s, int aux_x, float4 *ext, int width, int height)
 {
     if (n_pad <= 0) return cudaSuccess;
     const int threads = 256;

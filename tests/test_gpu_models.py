@@ -108,14 +108,45 @@ def test_spherical_vs_oracle(form, w, h, n, z):
 
 
 def test_spherical_closed_form_branch():
-    """Points 4-6 mm from a 160 x 160 hologram: u = r^2/z^2 reaches 0.13, beyond the series' range, so every
-    term takes the closed form -(Z/2)(u/(1+sqrt(1+u)))^2 (delta up to ~20 turns at the corners)."""
+    """Points 4-6 mm from a 160 x 160 hologram: u = r^2/z^2 reaches 0.13 and the remainder ~20 turns at the
+    corners, beyond the quadratic's bounds, so every point takes the per-term form."""
     c = workloads.random_cloud(812, 160, 160, 400, z_range=(0.004, 0.006))
-    umax = ((159 * 8e-6) ** 2 * 2) / (0.004 ** 2)
-    assert umax > 0.05
+    mix = _remainder_forms(c)
+    assert mix["term_series"] + mix["term_closed"] == 400, mix
     want = oracle.model_wave(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, 160, 160).real
     got, _, _ = _run(c, "direct_sfu", 2)
     assert oracle.nrms(got, want) <= 1e-5
+
+
+def _remainder_forms(c):
+    """Which remainder form the point preparation selects per point (the same bounds, in FP64): the quadratic
+    about each 4 x 4 thread tile's centre or the per-term form, each with the series (u < 0.05) or the closed form."""
+    x, y, z = (c.xyz[:, k].astype(np.float64) for k in range(3))
+    qz, zh = (c.pitch_m / z) ** 2, z / (2 * c.lambda_m)
+    cx = np.maximum(np.abs(x), np.abs(c.width - 1 - x)) + 1.5
+    cy = np.maximum(np.abs(y), np.abs(c.height - 1 - y)) + 1.5
+    umax, wmax = (cx * cx + cy * cy) * qz, (3 * cx + 3 * cy + 4.5) * qz
+    quad = (zh * wmax ** 3 / 8 <= 2.0 ** -25) & (zh * umax / 2 * wmax + zh / 4 * wmax ** 2 <= 0.45)
+    series = umax < 0.05
+    return {"quad_series": int((quad & series).sum()), "quad_closed": int((quad & ~series).sum()),
+            "term_series": int((~quad & series).sum()), "term_closed": int((~quad & ~series).sum())}
+
+
+@pytest.mark.parametrize("w,h,n,z,forms", [
+    (1920, 1080, 2000, (0.03, 0.06), ("quad_series", "quad_closed", "term_closed")),
+    (1024, 768, 1500, (0.01, 0.08), ("quad_series", "term_series", "term_closed"))])
+def test_spherical_every_remainder_form(w, h, n, z, forms):
+    """Close points on wide holograms: each point's remainder takes the form its bounds allow; sampled pixels
+    (corners included) against the oracle."""
+    c = workloads.random_cloud(813 + n, w, h, n, z_range=z)
+    mix = _remainder_forms(c)
+    assert all(mix[f] >= 50 for f in forms), mix
+    rng = np.random.default_rng(814)
+    cols = np.concatenate([rng.integers(0, w, 400), [0, w - 1, 0, w - 1]])
+    rows = np.concatenate([rng.integers(0, h, 400), [0, 0, h - 1, h - 1]])
+    want = oracle.model_wave_at(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows).real
+    got, _, _ = _run(c, "direct_sfu", 2)
+    assert oracle.nrms(got[rows, cols], want) <= 1e-5
 
 
 def test_spherical_wave_kinoform_and_reference():
