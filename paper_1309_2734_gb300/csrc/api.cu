@@ -413,7 +413,7 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
 {
     const int64_t n_pad = padded_points(n);
     const int64_t n_ptiles = n_pad / kPointTile;
-    const DirectShape sh = spherical_shape();
+    const DirectShape sh = spherical_shape(planes);
     const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
     int split = ctx->point_split > 0 ? ctx->point_split : choose_point_split(tiles, n_ptiles, ctx->num_sms);
     if (split > n_ptiles) split = (int)(n_ptiles > 0 ? n_ptiles : 1);
@@ -433,7 +433,7 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
     {
         ProfileScope ps(ctx, "prep_points", 1);
         e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status, nullptr,
-                               ctx->stream, kAuxPiston, ext, width, height);
+                               ctx->stream, kAuxPiston, ext, width, height, sph_tile_cols(planes));
     }
     if (e != cudaSuccess) return cuda_status(e);
     {

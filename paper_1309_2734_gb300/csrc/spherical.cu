@@ -29,8 +29,8 @@ namespace cgh {
 
 namespace {
 
-constexpr int kSphTL = kSphTileCols, kSphTR = kSphTileRows;       // pixels per thread
-constexpr int kSphBX = 32, kSphBY = 8;                             // 128 x 32 pixels per CTA of 256 threads
+constexpr int kSphTR = kSphTileRows;                             // pixel rows per thread
+constexpr int kSphBX = 32, kSphBY = 8;                             // threads per CTA: 32 x 8
 constexpr float kSphK1 = 6.28318595886230469f;                   // 2 pi rounded so that 1.5 K1 is a float
 constexpr float kSphK0 = 9.42477893829345703f;                   // 1.5 K1
 constexpr uint32_t kSphBias = (1u << 30) + 256u;                 // a quarter turn, and rounding to 23 bits
@@ -102,12 +102,14 @@ __device__ __forceinline__ float sph_d0_frac(float cx, float cy, const float4 x,
 
 // The Fresnel part of the phase (exact, 32-bit fixed-point turns) at the thread's first column of each row:
 // g[i] for its columns, the row step e and second difference D, as in the direct kernel (Eqs. 6-8).
+template <int TL>
 struct SphFresnel {
-    uint32_t g[kSphTL];
+    uint32_t g[TL];
     uint32_t e, D;
 };
 
-__device__ __forceinline__ SphFresnel sph_fresnel(const int4 q, uint32_t piston, int dxi, int dyi, uint32_t rg,
+template <int TL>
+__device__ __forceinline__ SphFresnel<TL> sph_fresnel(const int4 q, uint32_t piston, int dxi, int dyi, uint32_t rg,
                                                   uint32_t rdx, uint32_t rdy)
 {
     const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
@@ -116,13 +118,13 @@ __device__ __forceinline__ SphFresnel sph_fresnel(const int4 q, uint32_t piston,
     const uint32_t r2x = r2 + 2u * dx + 1u;
     const uint32_t r2y = r2 + 2u * dy + 1u;
     const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
-    SphFresnel F;
+    SphFresnel<TL> F;
     uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0 + rdx;
     F.e = chi * r2y + __umulhi(clo, r2y) - c0 + rdy;
     F.D = __funnelshift_l(clo, chi, 1);
     F.g[0] = c0 + piston + rg + kSphBias;
 #pragma unroll
-    for (int i = 1; i < kSphTL; ++i) {
+    for (int i = 1; i < TL; ++i) {
         F.g[i] = F.g[i - 1] + d;
         d += F.D;
     }
@@ -145,7 +147,7 @@ __device__ __forceinline__ void sph_accumulate(uint32_t gi, float a, float &re, 
     }
 }
 
-// One point over the thread's kSphTR x kSphTL pixels, the remainder as a quadratic about the tile's centre.
+// One point over the thread's kSphTR x TL pixels, the remainder as a quadratic about the tile's centre.
 // With cx, cy the centre's offsets from the point (pixels; integer + 1/2 for the 4 x 4 tile), U0 its u and a
 // pixel at offsets (t, s) from the centre,
 //   u = U0 + a + b,  a = t (2 cx + t) (p / z)^2,  b = s (2 cy + s) (p / z)^2,  w = a + b,
@@ -158,16 +160,16 @@ __device__ __forceinline__ void sph_accumulate(uint32_t gi, float a, float &re, 
 // a float in [2^23, 2^24) whose low 22 mantissa bits hold round(2^22 delta) in two's complement: shifted up by
 // ten they add delta to the 32-bit fixed-point phase (resolution 2^-22 turn).  Per term: one add and one FMA
 // for the quadratic, one shift-add into the phase, and the sine as the term's only MUFU operation.
-template <int PLANES, bool SERIES>
+template <int PLANES, int TL, bool SERIES>
 __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, const float4 x, int m0, int n0,
                                                uint32_t rg, uint32_t rdx, uint32_t rdy,
-                                               float (&acc)[PLANES][kSphTR][kSphTL])
+                                               float (&acc)[PLANES][kSphTR][TL])
 {
     const int dxi = m0 - q.x, dyi = n0 - q.y;
-    SphFresnel F = sph_fresnel(q, w.x, dxi, dyi, rg, rdx, rdy);
+    SphFresnel<TL> F = sph_fresnel<TL>(q, w.x, dxi, dyi, rg, rdx, rdy);
     const float a = __uint_as_float(w.y);
     const float qz = x.x, zh = fabsf(x.y);   // (p / z)^2, z / (2 lambda)
-    const float hx = 0.5f * (kSphTL - 1), hy = 0.5f * (kSphTR - 1);
+    const float hx = 0.5f * (TL - 1), hy = 0.5f * (kSphTR - 1);
     const float cx = small_int_to_float(dxi) + hx, cy = small_int_to_float(dyi) + hy;
     float d0f, d1, d2;
     if constexpr (SERIES) {
@@ -205,9 +207,9 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
     }
     const float sd1 = kQuadScale * d1, sd2 = kQuadScale * d2;
     const float X = cx * qz, Y = cy * qz;
-    float av[kSphTL], aq[kSphTL];   // a and 2^22 d2 a per column
+    float av[TL], aq[TL];   // a and 2^22 d2 a per column
 #pragma unroll
-    for (int i = 0; i < kSphTL; ++i) {
+    for (int i = 0; i < TL; ++i) {
         const float t = (float)i - hx;
         av[i] = fmaf(2.0f * t, X, (t * t) * qz);
         aq[i] = sd2 * av[i];
@@ -223,7 +225,7 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
 #pragma unroll
     for (int r = 0; r < kSphTR; ++r) {
 #pragma unroll
-        for (int i = 0; i < kSphTL; ++i) {
+        for (int i = 0; i < TL; ++i) {
             // a (2^22 (d1 + 2 d2 b) + 2^22 d2 a) = 2^22 (d1 a + d2 (2 a b + a^2)), added to M + 2^22 (d0 + ...)
             const float y = fmaf(av[i], qr[r] + aq[i], pm[r]);
             sph_accumulate<PLANES>(F.g[i] + (__float_as_uint(y) << 10), a, acc[0][r][i],
@@ -231,7 +233,7 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
         }
         if (r + 1 < kSphTR) {
 #pragma unroll
-            for (int i = 0; i < kSphTL; ++i) F.g[i] += F.e;
+            for (int i = 0; i < TL; ++i) F.g[i] += F.e;
             F.e += F.D;
         }
     }
@@ -242,24 +244,24 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
 //   Delta = Z ((s - s0) - w / 2) = -(Z / 2) w (v + v0) / (s + s0) = -(Z / 2) w (u + v0 (1 + s)) / ((1 + s)(s + s0)),
 // s = sqrt(1 + u), v = s - 1 = u / (1 + s): no cancellation, so Delta carries ~1e-7 of itself, and d0's
 // fraction ~2^-40 turn.  Per term: a reciprocal square root, a reciprocal and the sine (three MUFU operations).
-template <int PLANES>
+template <int PLANES, int TL>
 __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, const float4 x, int m0, int n0,
                                                 uint32_t rg, uint32_t rdx, uint32_t rdy,
-                                                float (&acc)[PLANES][kSphTR][kSphTL])
+                                                float (&acc)[PLANES][kSphTR][TL])
 {
     const int dxi = m0 - q.x, dyi = n0 - q.y;
-    SphFresnel F = sph_fresnel(q, w.x, dxi, dyi, rg, rdx, rdy);
+    SphFresnel<TL> F = sph_fresnel<TL>(q, w.x, dxi, dyi, rg, rdx, rdy);
     const float a = __uint_as_float(w.y);
     const float qz = fabsf(x.x), zh = fabsf(x.y);
-    const float hx = 0.5f * (kSphTL - 1), hy = 0.5f * (kSphTR - 1);
+    const float hx = 0.5f * (TL - 1), hy = 0.5f * (kSphTR - 1);
     const float cx = small_int_to_float(dxi) + hx, cy = small_int_to_float(dyi) + hy;
     float v0, s0, rs0;
     const float d0f = sph_d0_frac(cx, cy, x, v0, s0, rs0);
     const float U0 = fmaf(cx, cx, cy * cy) * qz;
     const float X = cx * qz, Y = cy * qz;
-    float av[kSphTL], bv[kSphTR];
+    float av[TL], bv[kSphTR];
 #pragma unroll
-    for (int i = 0; i < kSphTL; ++i) {
+    for (int i = 0; i < TL; ++i) {
         const float t = (float)i - hx;
         av[i] = fmaf(2.0f * t, X, (t * t) * qz);
     }
@@ -271,7 +273,7 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
 #pragma unroll
     for (int r = 0; r < kSphTR; ++r) {
 #pragma unroll
-        for (int i = 0; i < kSphTL; ++i) {
+        for (int i = 0; i < TL; ++i) {
             const float wv = av[i] + bv[r];
             const float u = U0 + wv;
             const float ou = 1.0f + u;
@@ -284,37 +286,40 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
         }
         if (r + 1 < kSphTR) {
 #pragma unroll
-            for (int i = 0; i < kSphTL; ++i) F.g[i] += F.e;
+            for (int i = 0; i < TL; ++i) F.g[i] += F.e;
             F.e += F.D;
         }
     }
 }
 
-// blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).
+// blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).  A thread owns kSphTR rows of
+// sph_tile_cols(PLANES) pixels: 8 columns for the amplitude hologram, 4 for the complex wave (its two
+// accumulator planes would not fit the registers of two CTAs per SM at 8).
 template <int PLANES>
 __global__ void __launch_bounds__(kSphBX *kSphBY, 2)
     spherical_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, const float4 *__restrict__ ext,
                      int n_ptiles, int width, int height, int tiles_x, int split, float *__restrict__ out,
                      long long slice_stride, long long im_offset, const PhaseRef ref)
 {
+    constexpr int TL = sph_tile_cols(PLANES);
     __shared__ int4 s_geo[kPointTile];
     __shared__ uint2 s_aux[kPointTile];
     __shared__ float4 s_ext[kPointTile];
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
-    const int m0 = (tile % tiles_x) * (kSphBX * kSphTL) + (tid % kSphBX) * kSphTL;
+    const int m0 = (tile % tiles_x) * (kSphBX * TL) + (tid % kSphBX) * TL;
     const int n0 = (tile / tiles_x) * (kSphBY * kSphTR) + (tid / kSphBX) * kSphTR;
     const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
     const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
     const uint32_t rg = ref_turn(ref, m0, n0), rdx = ref_step(ref.kx), rdy = ref_step(ref.ky);
 
-    float tot[PLANES][kSphTR][kSphTL];
+    float tot[PLANES][kSphTR][TL];
 #pragma unroll
     for (int c = 0; c < PLANES; ++c)
 #pragma unroll
         for (int r = 0; r < kSphTR; ++r)
 #pragma unroll
-            for (int i = 0; i < kSphTL; ++i) tot[c][r][i] = 0.0f;
+            for (int i = 0; i < TL; ++i) tot[c][r][i] = 0.0f;
 
     for (int t = t_begin; t < t_end; ++t) {
         const long long j = (long long)t * kPointTile + tid;
@@ -323,29 +328,29 @@ __global__ void __launch_bounds__(kSphBX *kSphBY, 2)
         s_aux[tid] = aux[j];
         s_ext[tid] = ext[j];
         __syncthreads();
-        float part[PLANES][kSphTR][kSphTL];
+        float part[PLANES][kSphTR][TL];
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
 #pragma unroll
             for (int r = 0; r < kSphTR; ++r)
 #pragma unroll
-                for (int i = 0; i < kSphTL; ++i) part[c][r][i] = 0.0f;
+                for (int i = 0; i < TL; ++i) part[c][r][i] = 0.0f;
 #pragma unroll 1
         for (int p = 0; p < kPointTile; ++p) {
             const float4 x = s_ext[p];   // the same point, so the same branch, in every thread
             if (x.x < 0.0f)
-                sph_point_terms<PLANES>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
+                sph_point_terms<PLANES, TL>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
             else if (x.y >= 0.0f)
-                sph_point_quad<PLANES, true>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
+                sph_point_quad<PLANES, TL, true>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
             else
-                sph_point_quad<PLANES, false>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
+                sph_point_quad<PLANES, TL, false>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
 #pragma unroll
             for (int r = 0; r < kSphTR; ++r)
 #pragma unroll
-                for (int i = 0; i < kSphTL; ++i) tot[c][r][i] += part[c][r][i];
+                for (int i = 0; i < TL; ++i) tot[c][r][i] += part[c][r][i];
     }
 
     float *dst = out + (long long)blockIdx.y * slice_stride;
@@ -356,23 +361,23 @@ __global__ void __launch_bounds__(kSphBX *kSphBY, 2)
             const int n = n0 + r;
             if (n >= height) continue;
 #pragma unroll
-            for (int i = 0; i < kSphTL; ++i)
+            for (int i = 0; i < TL; ++i)
                 if (m0 + i < width) dst[(long long)c * im_offset + (long long)n * width + m0 + i] = tot[c][r][i];
         }
 }
 
 }  // namespace
 
-DirectShape spherical_shape()
+DirectShape spherical_shape(int planes)
 {
-    return DirectShape{kSphBX * kSphTL, kSphBY * kSphTR, kSphBX * kSphBY};
+    return DirectShape{kSphBX * sph_tile_cols(planes), kSphBY * kSphTR, kSphBX * kSphBY};
 }
 
 cudaError_t launch_spherical(const int4 *geo, const uint2 *aux, const float4 *ext, int n_pad, int width, int height,
                              int split, int planes, float *out, int64_t slice_stride, int64_t im_offset,
                              const PhaseRef &ref, cudaStream_t s)
 {
-    const DirectShape sh = spherical_shape();
+    const DirectShape sh = spherical_shape(planes);
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
     const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
     const int n_ptiles = n_pad / kPointTile;

@@ -74,6 +74,11 @@ def test_steep_reference_and_far_columns():
     for form in ("direct_sfu", "gemm_split16"):
         got, _, _ = _run(c, form, 1, ref)
         assert oracle.nrms(got, want) <= NRMS[form], form
+    # the exact distance too: at 72-96 mm from the aperture's edge u reaches 0.1 and the remainder at the tile
+    # centres hundreds of turns, whose fraction the double-float evaluation must keep
+    want = oracle.model_wave(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, 1000, 40, reference=ref).real
+    got, _, _ = _run(c, "direct_sfu", 2, ref)
+    assert oracle.nrms(got, want) <= 1e-5
 
 
 @pytest.mark.parametrize("form", ["gemm_f16", "gemm_split16"])
@@ -118,35 +123,43 @@ def test_spherical_closed_form_branch():
     assert oracle.nrms(got, want) <= 1e-5
 
 
-def _remainder_forms(c):
-    """Which remainder form the point preparation selects per point (the same bounds, in FP64): the quadratic
-    about each 4 x 4 thread tile's centre or the per-term form, each with the series (u < 0.05) or the closed form."""
+def _remainder_forms(c, tile_cols=8):
+    """Which remainder form the point preparation selects per point for the amplitude hologram (thread tiles of
+    4 rows x 8 columns; the same bounds, in FP64): the quadratic about each thread tile's centre or the per-term
+    form, each with the series (u < 0.05) or the closed form."""
     x, y, z = (c.xyz[:, k].astype(np.float64) for k in range(3))
     qz, zh = (c.pitch_m / z) ** 2, z / (2 * c.lambda_m)
-    cx = np.maximum(np.abs(x), np.abs(c.width - 1 - x)) + 1.5
-    cy = np.maximum(np.abs(y), np.abs(c.height - 1 - y)) + 1.5
-    umax, wmax = (cx * cx + cy * cy) * qz, (3 * cx + 3 * cy + 4.5) * qz
+    hx, hy = (tile_cols - 1) / 2, 1.5
+    cx = np.maximum(np.abs(x), np.abs(c.width - 1 - x)) + hx
+    cy = np.maximum(np.abs(y), np.abs(c.height - 1 - y)) + hy
+    umax, wmax = (cx * cx + cy * cy) * qz, (2 * hx * cx + hx * hx + 2 * hy * cy + hy * hy) * qz
     quad = (zh * wmax ** 3 / 8 <= 2.0 ** -25) & (zh * umax / 2 * wmax + zh / 4 * wmax ** 2 <= 0.45)
     series = umax < 0.05
     return {"quad_series": int((quad & series).sum()), "quad_closed": int((quad & ~series).sum()),
             "term_series": int((~quad & series).sum()), "term_closed": int((~quad & ~series).sum())}
 
 
+@pytest.mark.parametrize("wave", [False, True])
 @pytest.mark.parametrize("w,h,n,z,forms", [
-    (1920, 1080, 2000, (0.03, 0.06), ("quad_series", "quad_closed", "term_closed")),
-    (1024, 768, 1500, (0.01, 0.08), ("quad_series", "term_series", "term_closed"))])
-def test_spherical_every_remainder_form(w, h, n, z, forms):
-    """Close points on wide holograms: each point's remainder takes the form its bounds allow; sampled pixels
-    (corners included) against the oracle."""
-    c = workloads.random_cloud(813 + n, w, h, n, z_range=z)
+    (3840, 2160, 2000, (0.08, 0.15), ("quad_series", "quad_closed", "term_closed")),
+    (1920, 1080, 2000, (0.05, 0.1), ("quad_series", "term_series", "term_closed"))])
+def test_spherical_every_remainder_form(w, h, n, z, forms, wave):
+    """Close points on wide holograms: each point's remainder takes the form its bounds allow (the amplitude
+    hologram's 8-column thread tiles; the complex wave's 4-column tiles shift the mix); sampled pixels (corners
+    included) against the oracle."""
+    c = workloads.random_cloud(813 + w, w, h, n, z_range=z)
     mix = _remainder_forms(c)
     assert all(mix[f] >= 50 for f in forms), mix
+    if wave:
+        assert sum(v > 0 for v in _remainder_forms(c, tile_cols=4).values()) >= 3
     rng = np.random.default_rng(814)
     cols = np.concatenate([rng.integers(0, w, 400), [0, w - 1, 0, w - 1]])
     rows = np.concatenate([rng.integers(0, h, 400), [0, 0, h - 1, h - 1]])
-    want = oracle.model_wave_at(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows).real
-    got, _, _ = _run(c, "direct_sfu", 2)
-    assert oracle.nrms(got[rows, cols], want) <= 1e-5
+    want = oracle.model_wave_at(2, c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    got, _, _ = _run(c, "direct_sfu", 2, wave=wave)
+    assert oracle.nrms(got.real[rows, cols], want.real) <= 1e-5
+    if wave:
+        assert oracle.nrms(got.imag[rows, cols], want.imag) <= 1e-5
 
 
 def test_spherical_wave_kinoform_and_reference():
