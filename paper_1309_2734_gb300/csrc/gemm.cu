@@ -53,13 +53,16 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 64;   // 64 16-bit elements = one 128-byte swizzle row
 constexpr int kGemmThreads = 192;
+// Shared memory left for the operand ring: the 227 KB a CTA may use, less the 1024-byte alignment slack and the
+// barriers.
+constexpr int kStageRoom = 232448 - 1024 - 256;
 
 template <int BN>
 struct GemmCfg {
     static constexpr int kStageA = kBM * kBK * 2;
     static constexpr int kStageB = BN * kBK * 2;
     static constexpr int kStageBytes = kStageA + kStageB;
-    static constexpr int kStages = (200 * 1024) / kStageBytes > 8 ? 8 : (200 * 1024) / kStageBytes;
+    static constexpr int kStages = kStageRoom / kStageBytes > 8 ? 8 : kStageRoom / kStageBytes;
     static constexpr int kAccStride = BN <= 128 ? 128 : 256;   // TMEM columns between the two accumulators
     static constexpr int kTmemCols = 2 * kAccStride;
     static constexpr int kBarrierBytes = 256;
