@@ -289,9 +289,13 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
                                reinterpret_cast<const uint2 *>(A + o.aux), (int)b.n_points, b.height, b.width,
                                A + o.p, A + o.q, o.ld, amax, s);
     }
-    if (e == cudaSuccess && gctas)
+    if (e == cudaSuccess && gctas) {
+        int bn_max = 0;
+        for (int i = 0; i < n; ++i)
+            if (inst[i].n_points > 0 && plan->forms[i] >= CGH_GEMM_F16 && bn[i] > bn_max) bn_max = bn[i];
         e = launch_gemm_batch(reinterpret_cast<const GemmJob *>(A + t_gjobs), reinterpret_cast<const int *>(A + t_goff),
-                              reinterpret_cast<const int2 *>(A + t_gunits), gctas, ctx->d_status, tmo, s);
+                              reinterpret_cast<const int2 *>(A + t_gunits), gctas, bn_max, ctx->d_status, tmo, s);
+    }
     for (int w = 0; w < 2 && e == cudaSuccess; ++w)
         if (dctas[w])
             e = launch_direct_batch(w == 0, reinterpret_cast<const DirectJob *>(A + t_djobs[w]),

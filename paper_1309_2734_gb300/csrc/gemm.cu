@@ -594,15 +594,23 @@ bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q,
     return true;
 }
 
-cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas,
-                              int *status, uint64_t timeout_ns, cudaStream_t s)
+template <int BN_MAX>
+cudaError_t launch_batch_as(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas, int *status,
+                            uint64_t timeout_ns, cudaStream_t s)
 {
-    if (ctas <= 0) return cudaSuccess;
-    cudaError_t e = configure<256, BatchUnits>();
+    cudaError_t e = configure<BN_MAX, BatchUnits>();
     if (e != cudaSuccess) return e;
     BatchUnits u{d_jobs, d_cta_off, d_units};
-    gemm_kernel<256, BatchUnits><<<ctas, kGemmThreads, GemmCfg<256>::kSmemBytes, s>>>(u, status, timeout_ns);
+    gemm_kernel<BN_MAX, BatchUnits><<<ctas, kGemmThreads, GemmCfg<BN_MAX>::kSmemBytes, s>>>(u, status, timeout_ns);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas,
+                              int bn_max, int *status, uint64_t timeout_ns, cudaStream_t s)
+{
+    if (ctas <= 0) return cudaSuccess;
+    if (bn_max <= 224) return launch_batch_as<224>(d_jobs, d_cta_off, d_units, ctas, status, timeout_ns, s);
+    return launch_batch_as<256>(d_jobs, d_cta_off, d_units, ctas, status, timeout_ns, s);
 }
 
 }  // namespace cgh

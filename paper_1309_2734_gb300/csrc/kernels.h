@@ -206,8 +206,10 @@ struct alignas(64) GemmJob {
 };
 bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q, int height, int width, int64_t ld,
                    int chunk_kb, float *out, const float *amp_max);
+// bn_max: the widest tile of the jobs; at most 224 selects the kernel whose
+// shared-memory ring has room for 5 stages of 224-wide tiles (4 at 256).
 cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas,
-                              int *status, uint64_t timeout_ns, cudaStream_t s);
+                              int bn_max, int *status, uint64_t timeout_ns, cudaStream_t s);
 
 // a5: fixed-order sum of `slices` planes of n floats (reduce.cu).
 cudaError_t launch_reduce_slices(const float *parts, int slices, int64_t n, int64_t slice_stride, float *out,
