@@ -26,10 +26,9 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
 {
     const int64_t n_pad = padded_points(n);
     const int64_t n_ptiles = n_pad / kPointTile;
-    const DirectShape sh = direct_shape(sfu);
-    const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
-    int split = ctx->point_split > 0 ? ctx->point_split : choose_point_split(tiles, n_ptiles, ctx->num_sms);
-    if (split > n_ptiles) split = (int)(n_ptiles > 0 ? n_ptiles : 1);
+    const DirectLayout lay = choose_direct_layout(false, width, height, n_ptiles, ctx->num_sms, ctx->point_split);
+    const DirectShape sh = lay.shape;
+    const int split = lay.split;
     const int64_t plane = (int64_t)width * height;
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
@@ -50,7 +49,7 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
     {
         ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);
-        e = launch_direct(sfu, geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out, plane,
+        e = launch_direct(sfu, sh, geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out, plane,
                           ctx->d_status, tmo, ctx->stream, ctx->drop_tile, phase_ref(ctx));
     }
     if (e != cudaSuccess || split == 1) return cuda_status(e);
@@ -303,11 +302,10 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
     cudaError_t e;
     if (form == CGH_DIRECT_SFU) {
-        const DirectShape sh = direct_wave_shape();
-        const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         const int64_t n_ptiles = n_pad / kPointTile;
-        int split = ctx->point_split > 0 ? ctx->point_split : choose_point_split(tiles, n_ptiles, ctx->num_sms);
-        if (split > n_ptiles) split = (int)n_ptiles;
+        const DirectLayout lay = choose_direct_layout(true, width, height, n_ptiles, ctx->num_sms, ctx->point_split);
+        const DirectShape sh = lay.shape;
+        const int split = lay.split;
         const size_t part_bytes = split > 1 ? (size_t)split * 2 * plane * sizeof(float) : 0;
         int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + part_bytes);
         if (rc) return rc;
@@ -323,7 +321,7 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
         if (e != cudaSuccess) return cuda_status(e);
         {
             ProfileScope ps(ctx, "direct_wave", 1);
-            e = launch_direct_wave(geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out,
+            e = launch_direct_wave(sh, geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out,
                                    2 * plane, plane, ctx->d_status, tmo, ctx->stream, phase_ref(ctx));
         }
         if (e != cudaSuccess || split == 1) return cuda_status(e);

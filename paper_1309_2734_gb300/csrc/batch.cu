@@ -156,7 +156,7 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
     std::vector<DirectJob> djobs[2];
     std::vector<int2> gunits, dunits[2];
     std::vector<double> gcost, dcost[2];
-    const DirectShape dsh = direct_shape(true);
+    const DirectShape dsh = direct_shape(false);   // the batch kernel takes the wide shape
     for (int i = 0; i < n; ++i) {
         if (inst[i].n_points == 0) continue;
         const int f = plan->forms[i];

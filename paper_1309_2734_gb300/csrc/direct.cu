@@ -377,20 +377,49 @@ __global__ void __launch_bounds__(BX *BY, 2)
     }
 }
 
-constexpr int kTL = 8, kTR = 4, kBX = 32, kBY = 8;
+constexpr int kTL = 8, kTR = 4, kBX = 32, kBY = 8;   // the wide shape (the batch kernel's)
+constexpr int kTallBX = 16, kTallBY = 16;             // the tall shape: 128-pixel-wide tiles
+
+template <int BX, int BY, bool SFU, bool EXTRA>
+void direct_as(dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_ptiles, int width, int height,
+               int tiles_x, int split, float *out, long long ss, bool vec, int *status, uint64_t timeout_ns,
+               int drop_tile, const PhaseRef &ref)
+{
+    direct_kernel<kTL, kTR, BX, BY, SFU, EXTRA><<<grid, BX * BY, 0, s>>>(
+        geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
+}
+
+template <int BX, int BY>
+void direct_shaped(bool sfu, bool extra, dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_ptiles,
+                   int width, int height, int tiles_x, int split, float *out, long long ss, bool vec, int *status,
+                   uint64_t timeout_ns, int drop_tile, const PhaseRef &ref)
+{
+    if (sfu && !extra)
+        direct_as<BX, BY, true, false>(grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec,
+                                       status, timeout_ns, drop_tile, ref);
+    else if (sfu)
+        direct_as<BX, BY, true, true>(grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec,
+                                      status, timeout_ns, drop_tile, ref);
+    else if (!extra)
+        direct_as<BX, BY, false, false>(grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec,
+                                        status, timeout_ns, drop_tile, ref);
+    else
+        direct_as<BX, BY, false, true>(grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec,
+                                       status, timeout_ns, drop_tile, ref);
+}
 
 }  // namespace
 
-DirectShape direct_shape(bool)
+DirectShape direct_shape(bool tall)
 {
-    return DirectShape{kBX * kTL, kBY * kTR, kBX * kBY};
+    return tall ? DirectShape{kTallBX * kTL, kTallBY * kTR, kTallBX * kTallBY, kTallBX}
+                : DirectShape{kBX * kTL, kBY * kTR, kBX * kBY, kBX};
 }
 
-cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
-                          int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
+cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, const uint2 *aux, int n_pad, int width,
+                          int height, int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
                           cudaStream_t s, int drop_tile, const PhaseRef &ref)
 {
-    const DirectShape sh = direct_shape(sfu);
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
     const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
     const int n_ptiles = n_pad / kPointTile;
@@ -400,18 +429,12 @@ cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad
     const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
     const long long ss = (long long)slice_stride;
     const bool extra = ref.any();
-    if (sfu && !extra)
-        direct_kernel<kTL, kTR, kBX, kBY, true, false><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
-    else if (sfu)
-        direct_kernel<kTL, kTR, kBX, kBY, true, true><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
-    else if (!extra)
-        direct_kernel<kTL, kTR, kBX, kBY, false, false><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
+    if (sh.bx == kTallBX)
+        direct_shaped<kTallBX, kTallBY>(sfu, extra, grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out,
+                                        ss, vec, status, timeout_ns, drop_tile, ref);
     else
-        direct_kernel<kTL, kTR, kBX, kBY, false, true><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, vec, status, timeout_ns, drop_tile, ref);
+        direct_shaped<kBX, kBY>(sfu, extra, grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out, ss,
+                                vec, status, timeout_ns, drop_tile, ref);
     return cudaGetLastError();
 }
 
@@ -443,18 +466,31 @@ namespace cgh {
 
 namespace {
 constexpr int kWaveTL = 8, kWaveTR = 2;   // two planes of accumulators: half the rows per thread
+
+template <int BX, int BY>
+void wave_as(bool extra, dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_ptiles, int width,
+             int height, int tiles_x, int split, float *out, long long ss, long long im, bool vec, int *status,
+             uint64_t timeout_ns, const PhaseRef &ref)
+{
+    if (extra)
+        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true><<<grid, BX * BY, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, im, vec, status, timeout_ns, ref);
+    else
+        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false><<<grid, BX * BY, 0, s>>>(
+            geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, im, vec, status, timeout_ns, ref);
+}
+}  // namespace
+
+DirectShape direct_wave_shape(bool tall)
+{
+    return tall ? DirectShape{kTallBX * kWaveTL, kTallBY * kWaveTR, kTallBX * kTallBY, kTallBX}
+                : DirectShape{kBX * kWaveTL, kBY * kWaveTR, kBX * kBY, kBX};
 }
 
-DirectShape direct_wave_shape()
+cudaError_t launch_direct_wave(const DirectShape &sh, const int4 *geo, const uint2 *aux, int n_pad, int width,
+                               int height, int split, float *out, int64_t slice_stride, int64_t im_offset,
+                               int *status, uint64_t timeout_ns, cudaStream_t s, const PhaseRef &ref)
 {
-    return DirectShape{kBX * kWaveTL, kBY * kWaveTR, kBX * kBY};
-}
-
-cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int width, int height, int split,
-                               float *out, int64_t slice_stride, int64_t im_offset, int *status,
-                               uint64_t timeout_ns, cudaStream_t s, const PhaseRef &ref)
-{
-    const DirectShape sh = direct_wave_shape();
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
     const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
     const int n_ptiles = n_pad / kPointTile;
@@ -462,14 +498,12 @@ cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int
     dim3 grid(tiles_x * tiles_y, split);
     const bool vec = (width % 4 == 0) && (slice_stride % 4 == 0) && (im_offset % 4 == 0) &&
                      ((uintptr_t)out % 16 == 0);
-    if (ref.any())
-        direct_wave_kernel<kWaveTL, kWaveTR, kBX, kBY, true><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, (long long)im_offset,
-            vec, status, timeout_ns, ref);
+    if (sh.bx == kTallBX)
+        wave_as<kTallBX, kTallBY>(ref.any(), grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out,
+                                  (long long)slice_stride, (long long)im_offset, vec, status, timeout_ns, ref);
     else
-        direct_wave_kernel<kWaveTL, kWaveTR, kBX, kBY, false><<<grid, sh.threads, 0, s>>>(
-            geo, aux, n_ptiles, width, height, tiles_x, split, out, (long long)slice_stride, (long long)im_offset,
-            vec, status, timeout_ns, ref);
+        wave_as<kBX, kBY>(ref.any(), grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out,
+                          (long long)slice_stride, (long long)im_offset, vec, status, timeout_ns, ref);
     return cudaGetLastError();
 }
 

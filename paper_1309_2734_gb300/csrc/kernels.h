@@ -66,20 +66,24 @@ __device__ __forceinline__ uint32_t ref_step(unsigned long long k)
 struct DirectShape {
     int tile_w, tile_h;   // pixels covered by one CTA
     int threads;          // threads per CTA
+    int bx;               // threads per CTA row: 32 (the wide shape) or 16 (the tall shape)
 };
-DirectShape direct_shape(bool sfu);
+// The CTA shapes of the direct kernels (256 threads, 8 columns of pixels per
+// thread): wide = 32 x 8 threads, tall = 16 x 16 threads.  The batch kernel
+// always takes the wide shape.
+DirectShape direct_shape(bool tall = false);
 // drop_tile >= 0 is a test hook: the first point chunk never loads that tile,
 // so its bounded wait runs out and the launch ends with kStatusTimeout.
-cudaError_t launch_direct(bool sfu, const int4 *geo, const uint2 *aux, int n_pad, int width, int height,
-                          int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
+cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, const uint2 *aux, int n_pad, int width,
+                          int height, int split, float *out, int64_t slice_stride, int *status, uint64_t timeout_ns,
                           cudaStream_t s, int drop_tile = -1, const PhaseRef &ref = PhaseRef());
 
 // Complex object wave (Eq. 2, restricted form), SFU form: real part at out,
 // imaginary part at out + im_offset; point chunk s at out + s * slice_stride.
-DirectShape direct_wave_shape();
-cudaError_t launch_direct_wave(const int4 *geo, const uint2 *aux, int n_pad, int width, int height, int split,
-                               float *out, int64_t slice_stride, int64_t im_offset, int *status,
-                               uint64_t timeout_ns, cudaStream_t s, const PhaseRef &ref = PhaseRef());
+DirectShape direct_wave_shape(bool tall = false);
+cudaError_t launch_direct_wave(const DirectShape &sh, const int4 *geo, const uint2 *aux, int n_pad, int width,
+                               int height, int split, float *out, int64_t slice_stride, int64_t im_offset,
+                               int *status, uint64_t timeout_ns, cudaStream_t s, const PhaseRef &ref = PhaseRef());
 
 // f2: the exact spherical wave of Eq. 1 (spherical.cu), direct SFU form.
 // Points prepared with the piston and ext.  planes = 1: the amplitude

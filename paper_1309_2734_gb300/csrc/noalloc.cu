@@ -58,6 +58,17 @@ int scratch_address(int dev, unsigned char **out)
 
 }  // namespace
 
+// The direct kernel's CTA shape with the fewer padded pixels (one point chunk: no split to balance).
+static cgh::DirectShape noalloc_shape(int width, int height)
+{
+    const cgh::DirectShape wide = cgh::direct_shape(false), tall = cgh::direct_shape(true);
+    auto padded = [&](const cgh::DirectShape &sh) {
+        return (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * sh.tile_w *
+               ((int64_t)((height + sh.tile_h - 1) / sh.tile_h) * sh.tile_h);
+    };
+    return padded(tall) < padded(wide) ? tall : wide;
+}
+
 extern "C" int cgh_point_cloud_noalloc(int width, int height, double pitch_m, double lambda_m, const float *d_xyz,
                                        const float *d_amp, int64_t n_points, float *d_out, void *cuda_stream)
 {
@@ -93,8 +104,8 @@ extern "C" int cgh_point_cloud_noalloc(int width, int height, double pitch_m, do
         cudaError_t e = launch_prep_points(d_xyz, d_amp, (int)n_points, (int)n_pad, pitch_m, lambda_m, geo, aux,
                                            status, nullptr, s);
         if (e == cudaSuccess)
-            e = launch_direct(true, geo, aux, (int)n_pad, width, height, 1, d_out, plane, status,
-                              5000000000ull, s);
+            e = launch_direct(true, noalloc_shape(width, height), geo, aux, (int)n_pad, width, height, 1, d_out,
+                              plane, status, 5000000000ull, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return CGH_ECUDA;

@@ -2,6 +2,7 @@
 //
 // Static rules (no measurement):
 //   choose_point_split  point chunks of the direct kernel, to fill whole waves;
+//   choose_direct_layout  the direct kernels' CTA shape (less padding) with its split;
 //   choose_gemm_bn      GEMM tile width with the least padding of the width;
 //   choose_gemm_splits  K splits of the GEMM, to balance tiles over the CTAs.
 //
@@ -32,25 +33,48 @@ constexpr int kDirectCtasPerSm = 2;
 constexpr int kForms = 6;
 }  // namespace
 
+// Critical path of a direct launch in point-tile steps of one CTA: rounds of pixel tiles x splits over the
+// resident CTA slots, times the longest point chunk (chunks differ by at most one tile); each extra chunk adds a
+// plane of partial sums, written and read back by the reduction: 0.2 % per chunk.
+static double direct_path(int64_t pixel_tiles, int64_t point_tiles, int64_t s, int64_t slots)
+{
+    const int64_t rounds = (pixel_tiles * s + slots - 1) / slots;
+    const int64_t longest = (point_tiles + s - 1) / s;
+    return (double)rounds * (double)longest * (1.0 + 0.002 * (double)(s - 1));
+}
+
 int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms)
 {
     if (pixel_tiles <= 0 || point_tiles <= 1) return 1;
     const int64_t slots = (int64_t)num_sms * kDirectCtasPerSm;
-    auto efficiency = [&](int64_t s) {
-        const int64_t units = pixel_tiles * s;
-        const int64_t waves = (units + slots - 1) / slots;
-        return (double)units / (double)(waves * slots);
-    };
     int best = 1;
-    double best_eff = efficiency(1);
-    for (int64_t s = 2; s <= 32 && s * 2 <= point_tiles; ++s) {
-        const double e = efficiency(s);
-        // each extra chunk costs one more plane of partial sums; demand a clear gain
-        if (e > best_eff + 0.03) {
+    double best_t = direct_path(pixel_tiles, point_tiles, 1, slots);
+    for (int64_t s = 2; s <= 64 && s * 2 <= point_tiles; ++s) {
+        const double t = direct_path(pixel_tiles, point_tiles, s, slots);
+        if (t < best_t * (1.0 - 1e-9)) {
             best = (int)s;
-            best_eff = e;
+            best_t = t;
         }
-        if (best_eff > 0.97) break;
+    }
+    return best;
+}
+
+DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t point_tiles, int num_sms,
+                                  int force_split)
+{
+    DirectLayout best{};
+    double best_t = 1e300;
+    const int64_t slots = (int64_t)num_sms * kDirectCtasPerSm;
+    for (int tall = 0; tall < 2; ++tall) {
+        const DirectShape sh = wave ? direct_wave_shape(tall != 0) : direct_shape(tall != 0);
+        const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
+        int s = force_split > 0 ? force_split : choose_point_split(tiles, point_tiles, num_sms);
+        if (s > point_tiles) s = (int)(point_tiles > 0 ? point_tiles : 1);
+        const double t = direct_path(tiles, point_tiles > 0 ? point_tiles : 1, s, slots);
+        if (t < best_t * (1.0 - 1e-9)) {
+            best_t = t;
+            best = DirectLayout{sh, s};
+        }
     }
     return best;
 }

@@ -3,13 +3,24 @@
 
 #include <cstdint>
 
+#include "kernels.h"
+
 struct cgh_ctx;
 
 namespace cgh {
 
-// Point chunks for the direct kernel so that (pixel tiles x chunks) fills
-// whole waves of resident CTAs; 1 when one wave is already nearly full.
+// Point chunks for the direct kernels: the shortest critical path, rounds of
+// (pixel tiles x chunks) over the resident CTAs times the longest chunk.
 int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms);
+
+// The direct kernels' CTA shape (wide or tall, the one with less padding and the
+// better fill) and its point split; force_split > 0 pins the split.
+struct DirectLayout {
+    DirectShape shape;
+    int split;
+};
+DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t point_tiles, int num_sms,
+                                  int force_split);
 
 // GEMM orientation, tile width and K splits with the shortest critical path
 // (rounds of units over ctas CTAs, times the work of one unit); force_* > 0
