@@ -411,10 +411,10 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
 {
     const int64_t n_pad = padded_points(n);
     const int64_t n_ptiles = n_pad / kPointTile;
-    const DirectShape sh = spherical_shape(planes);
-    const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
-    int split = ctx->point_split > 0 ? ctx->point_split : choose_point_split(tiles, n_ptiles, ctx->num_sms);
-    if (split > n_ptiles) split = (int)(n_ptiles > 0 ? n_ptiles : 1);
+    const DirectShape shapes[2] = {spherical_shape(planes, false), spherical_shape(planes, true)};
+    const DirectLayout lay = choose_layout(shapes, width, height, n_ptiles, ctx->num_sms, ctx->point_split);
+    const DirectShape sh = lay.shape;
+    const int split = lay.split;
     const int64_t plane = (int64_t)width * height;
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
@@ -436,7 +436,7 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
     if (e != cudaSuccess) return cuda_status(e);
     {
         ProfileScope ps(ctx, planes == 2 ? "spherical_wave" : "spherical", 1);
-        e = launch_spherical(geo, aux, ext, (int)n_pad, width, height, split, planes, split > 1 ? parts : d_out,
+        e = launch_spherical(sh, geo, aux, ext, (int)n_pad, width, height, split, planes, split > 1 ? parts : d_out,
                              (int64_t)planes * plane, plane, phase_ref(ctx), ctx->stream);
     }
     if (e != cudaSuccess || split == 1) return cuda_status(e);

@@ -89,10 +89,10 @@ cudaError_t launch_direct_wave(const DirectShape &sh, const int4 *geo, const uin
 // Points prepared with the piston and ext.  planes = 1: the amplitude
 // hologram (Eq. 5, middle line) at out; planes = 2: the complex wave, real part
 // at out and imaginary part at out + im_offset.  Point chunk s at out + s * slice_stride.
-DirectShape spherical_shape(int planes);
-cudaError_t launch_spherical(const int4 *geo, const uint2 *aux, const float4 *ext, int n_pad, int width, int height,
-                             int split, int planes, float *out, int64_t slice_stride, int64_t im_offset,
-                             const PhaseRef &ref, cudaStream_t s);
+DirectShape spherical_shape(int planes, bool tall = false);
+cudaError_t launch_spherical(const DirectShape &sh, const int4 *geo, const uint2 *aux, const float4 *ext, int n_pad,
+                             int width, int height, int split, int planes, float *out, int64_t slice_stride,
+                             int64_t im_offset, const PhaseRef &ref, cudaStream_t s);
 
 // a7: one job (hologram) of a batched direct launch; units are {job, pixel tile}.
 struct DirectJob {

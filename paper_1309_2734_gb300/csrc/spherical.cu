@@ -30,7 +30,8 @@ namespace cgh {
 namespace {
 
 constexpr int kSphTR = kSphTileRows;                             // pixel rows per thread
-constexpr int kSphBX = 32, kSphBY = 8;                             // threads per CTA: 32 x 8
+constexpr int kSphBX = 32, kSphBY = 8;                             // threads per CTA, the wide shape: 32 x 8
+constexpr int kSphTallBX = 16, kSphTallBY = 16;                    // the tall shape: 16 x 16
 constexpr float kSphK1 = 6.28318595886230469f;                   // 2 pi rounded so that 1.5 K1 is a float
 constexpr float kSphK0 = 9.42477893829345703f;                   // 1.5 K1
 constexpr uint32_t kSphBias = (1u << 30) + 256u;                 // a quarter turn, and rounding to 23 bits
@@ -38,7 +39,8 @@ constexpr float kRoundMagic = 12582912.0f;                       // 1.5 2^23: x 
 constexpr float kQuadScale = 4194304.0f;                         // 2^22: turns to the quadratic's units
 constexpr float kSeriesD0Max = 0.5f;                             // |d0| (turns) the float series may carry
 
-static_assert(kSphBX * kSphBY == kPointTile, "one point per thread in each tile load");
+static_assert(kSphBX * kSphBY == kPointTile && kSphTallBX * kSphTallBY == kPointTile,
+              "one point per thread in each tile load");
 
 // Exact small integer to float without a conversion instruction (|v| < 2^22).
 __device__ __forceinline__ float small_int_to_float(int v)
@@ -295,8 +297,8 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
 // blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).  A thread owns kSphTR rows of
 // sph_tile_cols(PLANES) pixels: 8 columns for the amplitude hologram, 4 for the complex wave (its two
 // accumulator planes would not fit the registers of two CTAs per SM at 8).
-template <int PLANES>
-__global__ void __launch_bounds__(kSphBX *kSphBY, 2)
+template <int PLANES, int BX, int BY>
+__global__ void __launch_bounds__(BX *BY, 2)
     spherical_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, const float4 *__restrict__ ext,
                      int n_ptiles, int width, int height, int tiles_x, int split, float *__restrict__ out,
                      long long slice_stride, long long im_offset, const PhaseRef ref)
@@ -307,8 +309,8 @@ __global__ void __launch_bounds__(kSphBX *kSphBY, 2)
     __shared__ float4 s_ext[kPointTile];
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
-    const int m0 = (tile % tiles_x) * (kSphBX * TL) + (tid % kSphBX) * TL;
-    const int n0 = (tile / tiles_x) * (kSphBY * kSphTR) + (tid / kSphBX) * kSphTR;
+    const int m0 = (tile % tiles_x) * (BX * TL) + (tid % BX) * TL;
+    const int n0 = (tile / tiles_x) * (BY * kSphTR) + (tid / BX) * kSphTR;
     const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
     const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
     const uint32_t rg = ref_turn(ref, m0, n0), rdx = ref_step(ref.kx), rdy = ref_step(ref.ky);
@@ -368,27 +370,46 @@ __global__ void __launch_bounds__(kSphBX *kSphBY, 2)
 
 }  // namespace
 
-DirectShape spherical_shape(int planes)
+DirectShape spherical_shape(int planes, bool tall)
 {
-    return DirectShape{kSphBX * sph_tile_cols(planes), kSphBY * kSphTR, kSphBX * kSphBY};
+    return tall ? DirectShape{kSphTallBX * sph_tile_cols(planes), kSphTallBY * kSphTR, kPointTile, kSphTallBX}
+                : DirectShape{kSphBX * sph_tile_cols(planes), kSphBY * kSphTR, kPointTile, kSphBX};
 }
 
-cudaError_t launch_spherical(const int4 *geo, const uint2 *aux, const float4 *ext, int n_pad, int width, int height,
-                             int split, int planes, float *out, int64_t slice_stride, int64_t im_offset,
-                             const PhaseRef &ref, cudaStream_t s)
+namespace {
+template <int PLANES, int BX, int BY>
+void spherical_as(dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, const float4 *ext, int n_ptiles,
+                  int width, int height, int tiles_x, int split, float *out, long long ss, long long im,
+                  const PhaseRef &ref)
 {
-    const DirectShape sh = spherical_shape(planes);
+    spherical_kernel<PLANES, BX, BY><<<grid, BX * BY, 0, s>>>(geo, aux, ext, n_ptiles, width, height, tiles_x, split,
+                                                              out, ss, im, ref);
+}
+}  // namespace
+
+cudaError_t launch_spherical(const DirectShape &sh, const int4 *geo, const uint2 *aux, const float4 *ext, int n_pad,
+                             int width, int height, int split, int planes, float *out, int64_t slice_stride,
+                             int64_t im_offset, const PhaseRef &ref, cudaStream_t s)
+{
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
     const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
     const int n_ptiles = n_pad / kPointTile;
     if (split < 1) split = 1;
     dim3 grid(tiles_x * tiles_y, split);
-    if (planes == 2)
-        spherical_kernel<2><<<grid, sh.threads, 0, s>>>(geo, aux, ext, n_ptiles, width, height, tiles_x, split, out,
-                                                        (long long)slice_stride, (long long)im_offset, ref);
+    const long long ss = (long long)slice_stride;
+    const bool tall = sh.bx == kSphTallBX;
+    if (planes == 2 && tall)
+        spherical_as<2, kSphTallBX, kSphTallBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out,
+                                                ss, (long long)im_offset, ref);
+    else if (planes == 2)
+        spherical_as<2, kSphBX, kSphBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out, ss,
+                                        (long long)im_offset, ref);
+    else if (tall)
+        spherical_as<1, kSphTallBX, kSphTallBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out,
+                                                ss, 0, ref);
     else
-        spherical_kernel<1><<<grid, sh.threads, 0, s>>>(geo, aux, ext, n_ptiles, width, height, tiles_x, split, out,
-                                                        (long long)slice_stride, 0, ref);
+        spherical_as<1, kSphBX, kSphBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out, ss, 0,
+                                        ref);
     return cudaGetLastError();
 }
 

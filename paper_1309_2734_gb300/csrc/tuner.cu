@@ -59,14 +59,13 @@ int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms)
     return best;
 }
 
-DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t point_tiles, int num_sms,
-                                  int force_split)
+DirectLayout choose_layout(const DirectShape (&shapes)[2], int width, int height, int64_t point_tiles, int num_sms,
+                           int force_split)
 {
     DirectLayout best{};
     double best_t = 1e300;
     const int64_t slots = (int64_t)num_sms * kDirectCtasPerSm;
-    for (int tall = 0; tall < 2; ++tall) {
-        const DirectShape sh = wave ? direct_wave_shape(tall != 0) : direct_shape(tall != 0);
+    for (const DirectShape &sh : shapes) {
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         int s = force_split > 0 ? force_split : choose_point_split(tiles, point_tiles, num_sms);
         if (s > point_tiles) s = (int)(point_tiles > 0 ? point_tiles : 1);
@@ -77,6 +76,14 @@ DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t poin
         }
     }
     return best;
+}
+
+DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t point_tiles, int num_sms,
+                                  int force_split)
+{
+    const DirectShape shapes[2] = {wave ? direct_wave_shape(false) : direct_shape(false),
+                                   wave ? direct_wave_shape(true) : direct_shape(true)};
+    return choose_layout(shapes, width, height, point_tiles, num_sms, force_split);
 }
 
 int choose_gemm_bn(int width)
