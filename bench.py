@@ -40,9 +40,9 @@ MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # taken on; a changed source reports null until it is profiled again.
 NCU_TRAFFIC = [
-    # profiles/direct_sfu-1920x1080-n10000.md: 0.272 MB read + 22.238 MB written per launch
+    # profiles/direct_sfu-1920x1080-n10000.md: 0.301 MB read + 104.633 MB written per launch
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000", "src": "direct.cu",
-     "sha1": "615d5dae059e1423a6fcf2b7db038c23fe1cb9f3", "bytes_per_launch": 22510336},
+     "sha1": "e4b5d06e2b824a5edb360c050341c4d54325d6ab", "bytes_per_launch": 104933376},
     # profiles/gemm_f16-1920x1080-n50000.md: 600.727 MB read + 4.504 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000", "src": "gemm.cu",
      "sha1": "89568a5c04f805456a25ad742128f40d28ceb943", "bytes_per_launch": 605230592},
