@@ -156,7 +156,20 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
     std::vector<DirectJob> djobs[2];
     std::vector<int2> gunits, dunits[2];
     std::vector<double> gcost, dcost[2];
-    const DirectShape dsh = direct_shape(false);   // the batch kernel takes the wide shape
+    // the direct batch kernels' CTA shape: the one with fewer padded pixels over the direct instances (weighted by
+    // their points, as the work is)
+    double pad_work[2] = {0.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+        if (inst[i].n_points == 0 || plan->forms[i] >= CGH_GEMM_F16) continue;
+        for (int tall = 0; tall < 2; ++tall) {
+            const DirectShape sh = direct_shape(tall != 0);
+            pad_work[tall] += (double)((inst[i].width + sh.tile_w - 1) / sh.tile_w * sh.tile_w) *
+                              (double)((inst[i].height + sh.tile_h - 1) / sh.tile_h * sh.tile_h) *
+                              (double)off[i].n_pad;
+        }
+    }
+    const bool dtall = pad_work[1] < pad_work[0];
+    const DirectShape dsh = direct_shape(dtall);
     for (int i = 0; i < n; ++i) {
         if (inst[i].n_points == 0) continue;
         const int f = plan->forms[i];
@@ -298,7 +311,7 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
     }
     for (int w = 0; w < 2 && e == cudaSuccess; ++w)
         if (dctas[w])
-            e = launch_direct_batch(w == 0, reinterpret_cast<const DirectJob *>(A + t_djobs[w]),
+            e = launch_direct_batch(w == 0, dtall, reinterpret_cast<const DirectJob *>(A + t_djobs[w]),
                                     reinterpret_cast<const int *>(A + t_doff[w]),
                                     reinterpret_cast<const int2 *>(A + t_dunits[w]), dctas[w], ctx->d_status, tmo, s);
     cudaGraph_t graph = nullptr;

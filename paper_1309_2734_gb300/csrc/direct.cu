@@ -442,13 +442,19 @@ cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, cons
 
 namespace cgh {
 
-cudaError_t launch_direct_batch(bool sfu, const DirectJob *d_jobs, const int *d_cta_off, const int2 *d_units,
-                                int ctas, int *status, uint64_t timeout_ns, cudaStream_t s)
+cudaError_t launch_direct_batch(bool sfu, bool tall, const DirectJob *d_jobs, const int *d_cta_off,
+                                const int2 *d_units, int ctas, int *status, uint64_t timeout_ns, cudaStream_t s)
 {
     if (ctas <= 0) return cudaSuccess;
-    if (sfu)
+    if (sfu && tall)
+        direct_batch_kernel<kTL, kTR, kTallBX, kTallBY, true><<<ctas, kTallBX * kTallBY, 0, s>>>(
+            d_jobs, d_cta_off, d_units, status, timeout_ns);
+    else if (sfu)
         direct_batch_kernel<kTL, kTR, kBX, kBY, true><<<ctas, kBX * kBY, 0, s>>>(d_jobs, d_cta_off, d_units, status,
                                                                                  timeout_ns);
+    else if (tall)
+        direct_batch_kernel<kTL, kTR, kTallBX, kTallBY, false><<<ctas, kTallBX * kTallBY, 0, s>>>(
+            d_jobs, d_cta_off, d_units, status, timeout_ns);
     else
         direct_batch_kernel<kTL, kTR, kBX, kBY, false><<<ctas, kBX * kBY, 0, s>>>(d_jobs, d_cta_off, d_units,
                                                                                   status, timeout_ns);

@@ -69,8 +69,7 @@ struct DirectShape {
     int bx;               // threads per CTA row: 32 (the wide shape) or 16 (the tall shape)
 };
 // The CTA shapes of the direct kernels (256 threads, 8 columns of pixels per
-// thread): wide = 32 x 8 threads, tall = 16 x 16 threads.  The batch kernel
-// always takes the wide shape.
+// thread): wide = 32 x 8 threads, tall = 16 x 16 threads.
 DirectShape direct_shape(bool tall = false);
 // drop_tile >= 0 is a test hook: the first point chunk never loads that tile,
 // so its bounded wait runs out and the launch ends with kStatusTimeout.
@@ -101,8 +100,9 @@ struct DirectJob {
     float *out;
     int n_ptiles, width, height, tiles_x, vec, pad;
 };
-cudaError_t launch_direct_batch(bool sfu, const DirectJob *d_jobs, const int *d_cta_off, const int2 *d_units,
-                                int ctas, int *status, uint64_t timeout_ns, cudaStream_t s);
+// tall: the 16 x 16-thread CTA shape (tiles of direct_shape(true)), else the wide one.
+cudaError_t launch_direct_batch(bool sfu, bool tall, const DirectJob *d_jobs, const int *d_cta_off,
+                                const int2 *d_units, int ctas, int *status, uint64_t timeout_ns, cudaStream_t s);
 int direct_ctas_per_sm();
 
 // a3: separable factors P [height][ld], Q [width][ld] (factors.cu).  For
