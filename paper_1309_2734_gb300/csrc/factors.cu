@@ -139,12 +139,14 @@ __global__ void __launch_bounds__(kFactorThreads)
 // so that sum_k P'[n][k] Q'[m][k] = s Re sum_g W_g(n) U_g(m) = s I(m, n);
 // s = 1 / wscale keeps |P'| <= 1.
 //
-// A block covers 32 rows (of P', or of Q' for the blocks past the P' rows) and
-// kGroupTile group slots.  Each warp takes whole groups, one lane per row, so
-// the lanes of a warp run the same member loop (no divergence whatever the
-// group sizes) and read each member with one broadcast load.  The block's
-// results meet in shared memory (slot-major, padded against bank conflicts)
-// and leave as full 256-byte row segments.
+// A block covers kGroupRows rows (of P', or of Q' for the blocks past the P'
+// rows) and kGroupTile group slots.  Each warp takes whole groups; lane l owns
+// the rows r0 + l + 32 q, q = 0 .. 3, so the lanes of a warp run the same
+// member loop (no divergence whatever the group sizes), read each member's
+// staged constants with one broadcast load for four terms, and step from one of
+// their rows to the next with one integer add.  The block's results meet in
+// shared memory (slot-major, padded against bank conflicts) and leave as full
+// 128-byte row segments.
 //
 // Per term: the turn C (n - y)^2 mod 1 in 32-bit fixed point (rounded to 23
 // bits by the +256), its top 23 bits as the mantissa of f in [1, 2), and
@@ -153,9 +155,11 @@ __global__ void __launch_bounds__(kFactorThreads)
 // 2 pi rounded to a float whose 1.5 multiple is exact, so the argument grid is
 // symmetric about zero and the hardware sine's odd error cancels in the sum
 // (as in the direct kernel).
-constexpr int kGroupTile = 64;
+constexpr int kGroupTile = 32;
 constexpr int kGroupThreads = 256;
-constexpr int kTileStride = 33;   // words per slot in the shared tile: 32 rows + 1
+constexpr int kGroupLaneRows = 4;                      // rows per lane
+constexpr int kGroupRows = 32 * kGroupLaneRows;       // rows per block
+constexpr int kTileStride = kGroupRows + 1;            // words per slot in the shared tile, +1 against conflicts
 constexpr float kTurnK1 = 6.28318595886230469f;   // 0x40c90fdc
 constexpr float kTurnK0 = 9.42477893829345703f;   // 1.5 * kTurnK1, exact
 
@@ -177,27 +181,34 @@ __global__ void __launch_bounds__(kGroupThreads)
 {
     __shared__ uint32_t tile_hi[kGroupTile * kTileStride];
     __shared__ uint32_t tile_lo[MODE == kFactorSplit16 ? kGroupTile * kTileStride : 1];
-    __shared__ uint4 stage[kGroupThreads / 32][32];   // per warp: {G, E, -A, 0} of 32 members
+    __shared__ uint4 stage[kGroupThreads / 32][32];   // per warp: {G, E, -A, 32 E} of 32 members
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p_blocks = (height + 31) / 32;
+    const int p_blocks = (height + kGroupRows - 1) / kGroupRows;
     const bool is_p = (int)blockIdx.y < p_blocks;
-    const int r0 = (is_p ? (int)blockIdx.y : (int)blockIdx.y - p_blocks) * 32;
-    const int line = r0 + lane;
+    const int r0 = (is_p ? (int)blockIdx.y : (int)blockIdx.y - p_blocks) * kGroupRows;
     const int s_base = blockIdx.x * kGroupTile;
     const float inv = 1.0f / *wscale;
-    // reference phase of this row (P': ky n) or column (Q': kx m + phi0)
-    const uint32_t radd = is_p ? ref_turn(ref, 0, line) - ref.phi0 : ref_turn(ref, line, 0);
+    // reference phase of this lane's rows (P': ky n) or columns (Q': kx m + phi0)
+    uint32_t radd[kGroupLaneRows];
+#pragma unroll
+    for (int q = 0; q < kGroupLaneRows; ++q) {
+        const int line = r0 + lane + 32 * q;
+        radd[q] = is_p ? ref_turn(ref, 0, line) - ref.phi0 : ref_turn(ref, line, 0);
+    }
     for (int k = warp; k < kGroupTile; k += kGroupThreads / 32) {
         const int slot = s_base + k;
-        float re = 0.0f, im = 0.0f;
+        float re[kGroupLaneRows], im[kGroupLaneRows];
+#pragma unroll
+        for (int q = 0; q < kGroupLaneRows; ++q) re[q] = im[q] = 0.0f;
         if (slot < n_groups) {
             const int4 d = groups[g_begin + slot];   // {first, count, plane, x}
             const unsigned long long C = planes[d.z];
             const uint32_t chi = (uint32_t)(C >> 32), clo = (uint32_t)C;
             if (is_p) {
-                // (r0 + l - y)^2 = D^2 + 2 D l + l^2, D = r0 - y: per member G = C D^2 and E = 2 C D (top 32
-                // bits, one lane each), per lane the phase G + E l; the lane's C l^2 (and the reference) is
-                // one rotation of the sum at the end.  E l in 32 bits is off by at most l < 32 units of 2^-32.
+                // (r0 + l - y)^2 = D^2 + 2 D l + l^2, D = r0 - y, l = lane + 32 q < 128: per member G = C D^2 and
+                // E = 2 C D (top 32 bits, one lane each), per row the phase G + E l; each row's C l^2 (and the
+                // reference) is one rotation of the sum at the end.  E l in 32 bits is off by at most l < 128
+                // units of 2^-32.
                 const unsigned long long C2 = C << 1;
                 for (int base = 0; base < d.y; base += 32) {
                     const int j = base + lane;
@@ -207,44 +218,58 @@ __global__ void __launch_bounds__(kGroupThreads)
                         const uint32_t d2 = (uint32_t)(D * D);   // < 2^30
                         const uint32_t G = chi * d2 + __umulhi(clo, d2);
                         const uint32_t E = (uint32_t)((C2 * (unsigned long long)(long long)D) >> 32);
-                        stage[warp][lane] = make_uint4(G + 256u, E, (uint32_t)v.y, 0u);   // +2^8: round to 23 bits
+                        stage[warp][lane] = make_uint4(G + 256u, E, (uint32_t)v.y, E << 5);   // +2^8: round to 23 bits
                     }
                     __syncwarp();
                     const int n = min(32, d.y - base);
                     for (int i = 0; i < n; ++i) {
                         const uint4 s = stage[warp][i];                              // same address in every lane
-                        const uint32_t t = s.x + s.y * (uint32_t)lane;
-                        const float f = __uint_as_float((t >> 9) | 0x3f800000u);
-                        float sn, cs;
-                        __sincosf(fmaf(f, kTurnK1, -kTurnK0), &sn, &cs);             // angle - pi
-                        re = fmaf(__uint_as_float(s.z), cs, re);                      // members carry -A
-                        im = fmaf(__uint_as_float(s.z), sn, im);
+                        uint32_t t = s.x + s.y * (uint32_t)lane;
+                        const float a = __uint_as_float(s.z);
+#pragma unroll
+                        for (int q = 0; q < kGroupLaneRows; ++q) {
+                            const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));   // 0x3f800000 | t >> 9
+                            float sn, cs;
+                            __sincosf(fmaf(f, kTurnK1, -kTurnK0), &sn, &cs);             // angle - pi
+                            re[q] = fmaf(a, cs, re[q]);                                   // members carry -A
+                            im[q] = fmaf(a, sn, im[q]);
+                            t += s.w;                                                     // 32 rows on
+                        }
                     }
                     __syncwarp();
                 }
                 // times exp(i 2 pi (C l^2 + reference)): half_turn_sincos gives minus its cosine and sine
-                float sn, cs;
-                half_turn_sincos(chi, clo, (uint32_t)lane, 256u + radd, sn, cs);
-                const float wr = -cs, wi = -sn;
-                const float r2 = re * wr - im * wi, i2 = re * wi + im * wr;
-                re = r2 * inv;
-                im = i2 * inv;
+#pragma unroll
+                for (int q = 0; q < kGroupLaneRows; ++q) {
+                    float sn, cs;
+                    half_turn_sincos(chi, clo, (uint32_t)(lane + 32 * q), 256u + radd[q], sn, cs);
+                    const float wr = -cs, wi = -sn;
+                    const float r2 = re[q] * wr - im[q] * wi, i2 = re[q] * wi + im[q] * wr;
+                    re[q] = r2 * inv;
+                    im[q] = i2 * inv;
+                }
             } else {
-                float sn, cs;
-                half_turn_sincos(chi, clo, (uint32_t)(line - d.w), 256u + radd, sn, cs);
-                re = -cs;   // cos alpha
-                im = sn;    // -sin alpha
+#pragma unroll
+                for (int q = 0; q < kGroupLaneRows; ++q) {
+                    float sn, cs;
+                    half_turn_sincos(chi, clo, (uint32_t)(r0 + lane + 32 * q - d.w), 256u + radd[q], sn, cs);
+                    re[q] = -cs;   // cos alpha
+                    im[q] = sn;    // -sin alpha
+                }
             }
         }
-        tile_hi[k * kTileStride + lane] = pack(re, im, MODE, false);
-        if (MODE == kFactorSplit16) tile_lo[k * kTileStride + lane] = pack(re, im, MODE, true);
+#pragma unroll
+        for (int q = 0; q < kGroupLaneRows; ++q) {
+            tile_hi[k * kTileStride + lane + 32 * q] = pack(re[q], im[q], MODE, false);
+            if (MODE == kFactorSplit16) tile_lo[k * kTileStride + lane + 32 * q] = pack(re[q], im[q], MODE, true);
+        }
     }
     __syncthreads();
-    // write-out: a warp stores two rows, 16 lanes x 16 bytes (4 slots) each
+    // write-out: 8 lanes x 16 bytes (4 slots) per row, four rows per warp
     const int rows = is_p ? height : width;
     uint16_t *base = is_p ? P : Q;
     const long long lo_off = is_p ? plane_p : plane_q;
-    for (int item = threadIdx.x; item < 32 * (kGroupTile / 4); item += kGroupThreads) {
+    for (int item = threadIdx.x; item < kGroupRows * (kGroupTile / 4); item += kGroupThreads) {
         const int row = item / (kGroupTile / 4), c = item % (kGroupTile / 4);
         const int s = s_base + 4 * c;
         if (r0 + row >= rows || s >= slots) continue;
@@ -266,7 +291,7 @@ cudaError_t launch_group_factors(int mode, const int4 *groups, int g_begin, int 
                                  const PhaseRef &ref)
 {
     const int slots = (int)(ld / 2);
-    dim3 grid((slots + kGroupTile - 1) / kGroupTile, (height + 31) / 32 + (width + 31) / 32);
+    dim3 grid((slots + kGroupTile - 1) / kGroupTile, (height + kGroupRows - 1) / kGroupRows + (width + kGroupRows - 1) / kGroupRows);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     const long long plane_p = (long long)height * ld, plane_q = (long long)width * ld;
     auto *p = static_cast<uint16_t *>(P);
