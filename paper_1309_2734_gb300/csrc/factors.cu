@@ -142,19 +142,23 @@ __global__ void __launch_bounds__(kFactorThreads)
 // A block covers kGroupRows rows (of P', or of Q' for the blocks past the P'
 // rows) and kGroupTile group slots.  Each warp takes whole groups; lane l owns
 // the rows r0 + l + 32 q, q = 0 .. 3, so the lanes of a warp run the same
-// member loop (no divergence whatever the group sizes), read each member's
-// staged constants with one broadcast load for four terms, and step from one of
-// their rows to the next with one integer add.  The block's results meet in
-// shared memory (slot-major, padded against bank conflicts) and leave as full
-// 128-byte row segments.
+// member loop (no divergence whatever the group sizes) and read each member's
+// staged constants with one broadcast load for four terms.  The block's results
+// meet in shared memory (slot-major, padded against bank conflicts) and leave as
+// full 128-byte row segments.
 //
-// Per term: the turn C (n - y)^2 mod 1 in 32-bit fixed point (rounded to 23
-// bits by the +256), its top 23 bits as the mantissa of f in [1, 2), and
-// u = (f - 1.5) K1 in [-pi, pi): the angle minus a half turn, so the sine and
-// cosine of u are minus those of the angle -- the members carry -A.  K1 is
-// 2 pi rounded to a float whose 1.5 multiple is exact, so the argument grid is
-// symmetric about zero and the hardware sine's odd error cancels in the sum
-// (as in the direct kernel).
+// Per member and lane, row q = 0: the turn C (n - y)^2 mod 1 in 32-bit fixed
+// point (rounded to 23 bits by the +256), its top 23 bits as the mantissa of f
+// in [1, 2), and u = (f - 1.5) K1 in [-pi, pi): the angle minus a half turn, so
+// the sine and cosine of u are minus those of the angle -- the members carry -A.
+// K1 is 2 pi rounded to a float whose 1.5 multiple is exact, so the argument
+// grid is symmetric about zero and the hardware sine's odd error cancels in the
+// sum (as in the direct kernel).  Rows q = 1 .. 3 are 32 rows apart, where the
+// phase differs by 32 E (up to the common C l^2, applied at the end): their
+// terms are the row-0 phasor rotated by exp(i 2 pi 32 E), which the staging lane
+// computes once per member with the accurate sincospif.  A term then costs a
+// quarter of one hardware sincos and a complex multiply; each rotation adds
+// about 1e-7 of relative error (three at most), against the sincos's 4e-7.
 constexpr int kGroupTile = 32;
 constexpr int kGroupThreads = 256;
 constexpr int kGroupLaneRows = 4;                      // rows per lane
@@ -181,7 +185,8 @@ __global__ void __launch_bounds__(kGroupThreads)
 {
     __shared__ uint32_t tile_hi[kGroupTile * kTileStride];
     __shared__ uint32_t tile_lo[MODE == kFactorSplit16 ? kGroupTile * kTileStride : 1];
-    __shared__ uint4 stage[kGroupThreads / 32][32];   // per warp: {G, E, -A, 32 E} of 32 members
+    __shared__ uint4 stage[kGroupThreads / 32][32];    // per warp: {G, E, -A, 0} of 32 members
+    __shared__ float2 stage_r[kGroupThreads / 32][32];  // and their 32-row rotations exp(i 2 pi 32 E)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p_blocks = (height + kGroupRows - 1) / kGroupRows;
     const bool is_p = (int)blockIdx.y < p_blocks;
@@ -218,22 +223,33 @@ __global__ void __launch_bounds__(kGroupThreads)
                         const uint32_t d2 = (uint32_t)(D * D);   // < 2^30
                         const uint32_t G = chi * d2 + __umulhi(clo, d2);
                         const uint32_t E = (uint32_t)((C2 * (unsigned long long)(long long)D) >> 32);
-                        stage[warp][lane] = make_uint4(G + 256u, E, (uint32_t)v.y, E << 5);   // +2^8: round to 23 bits
+                        stage[warp][lane] = make_uint4(G + 256u, E, (uint32_t)v.y, 0u);   // +2^8: round to 23 bits
+                        // 32 rows on, the phase grows by 32 E: its rotation, accurate (once per member, shared by
+                        // every lane); pi x with x = (32 E as a signed turn) * 2 is the angle in [-pi, pi)
+                        float rs, rc;
+                        sincospif((float)(int)(E << 5) * 4.656612873077393e-10f, &rs, &rc);
+                        stage_r[warp][lane] = make_float2(rc, rs);
                     }
                     __syncwarp();
                     const int n = min(32, d.y - base);
                     for (int i = 0; i < n; ++i) {
                         const uint4 s = stage[warp][i];                              // same address in every lane
-                        uint32_t t = s.x + s.y * (uint32_t)lane;
-                        const float a = __uint_as_float(s.z);
+                        const float2 r = stage_r[warp][i];
+                        const uint32_t t = s.x + s.y * (uint32_t)lane;
+                        const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));   // 0x3f800000 | t >> 9
+                        float sn, cs;
+                        __sincosf(fmaf(f, kTurnK1, -kTurnK0), &sn, &cs);             // angle - pi
+                        const float a = __uint_as_float(s.z);                         // members carry -A
+                        float pc = a * cs, ps = a * sn;                               // A exp(i angle), row q = 0
 #pragma unroll
                         for (int q = 0; q < kGroupLaneRows; ++q) {
-                            const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));   // 0x3f800000 | t >> 9
-                            float sn, cs;
-                            __sincosf(fmaf(f, kTurnK1, -kTurnK0), &sn, &cs);             // angle - pi
-                            re[q] = fmaf(a, cs, re[q]);                                   // members carry -A
-                            im[q] = fmaf(a, sn, im[q]);
-                            t += s.w;                                                     // 32 rows on
+                            re[q] += pc;
+                            im[q] += ps;
+                            if (q + 1 < kGroupLaneRows) {                             // on to row q + 1
+                                const float nc = fmaf(pc, r.x, -ps * r.y);
+                                ps = fmaf(pc, r.y, ps * r.x);
+                                pc = nc;
+                            }
                         }
                     }
                     __syncwarp();
