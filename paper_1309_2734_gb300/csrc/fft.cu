@@ -295,15 +295,17 @@ __global__ void fft_cols_a_kernel(float2 *__restrict__ pad, int Lx, int L1, int 
     const int b = blockIdx.x >> lstrips, x0 = (blockIdx.x & ((1 << lstrips) - 1)) << lsw;
     const int stride = sw + 1;
     const int n = L1 << lsw;
+    float2 *tw = sm + L1 * stride;   // e^{-2 pi i k / L1} = twy[k L2], k < L1, in shared memory
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int a = i >> lsw, c = i & (sw - 1);
         const int row = L2 * a + b;
         if (row < nz_rows) cp_async8(&sm[a * stride + c], pad + (long long)row * Lx + x0 + c);
         else sm[a * stride + c] = make_float2(0.0f, 0.0f);
     }
+    for (int k = threadIdx.x; k < L1; k += blockDim.x) tw[k] = twy[k * L2];
     cp_async_wait_all();
     __syncthreads();
-    smem_fft<INV, kLayoutCols>(sm, L1, sw, stride, twy, L2);   // e^{-2 pi i k / L1} = twy[k L2]
+    smem_fft<INV, kLayoutCols>(sm, L1, sw, stride, tw, 1);
 #pragma unroll 4
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int a = i >> lsw, c = i & (sw - 1);
@@ -327,20 +329,26 @@ __global__ void fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__rest
     const int stride = sw + 1;
     const int n = L2 << lsw;
     float2 *sp = sm + L2 * stride;   // the spectrum's tile
+    // in shared memory: e^{-2 pi i k / L2} = twy[k L1] and the four-step twiddles e^{-2 pi i c b / Ly} = twy[c b]
+    float2 *tw = sm + (spec != nullptr ? 2 : 1) * L2 * stride, *t4 = tw + L2;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int b = i >> lsw, q = i & (sw - 1);
         const long long g = (long long)(L2 * c + b) * Lx + x0 + q;
         cp_async8(&sm[b * stride + q], pad + g);
         if (spec != nullptr) cp_async8(&sp[b * stride + q], spec + g);
     }
+    for (int k = threadIdx.x; k < L2; k += blockDim.x) {
+        tw[k] = twy[k * L1];
+        t4[k] = twy[c * k];
+    }
     cp_async_wait_all();
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {   // the four-step twiddle, in shared memory
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {   // the four-step twiddle
         const int b = i >> lsw, q = i & (sw - 1);
-        sm[b * stride + q] = cmul(sm[b * stride + q], twy[c * b]);
+        sm[b * stride + q] = cmul(sm[b * stride + q], t4[b]);
     }
     __syncthreads();
-    smem_fft<false, kLayoutCols>(sm, L2, sw, stride, twy, L1);   // e^{-2 pi i k / L2} = twy[k L1]
+    smem_fft<false, kLayoutCols>(sm, L2, sw, stride, tw, 1);
     if (spec == nullptr) {
 #pragma unroll 4
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -354,11 +362,11 @@ __global__ void fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__rest
         sm[d * stride + q] = cmul(sm[d * stride + q], sp[d * stride + q]);
     }
     __syncthreads();
-    smem_fft<true, kLayoutCols>(sm, L2, sw, stride, twy, L1);
+    smem_fft<true, kLayoutCols>(sm, L2, sw, stride, tw, 1);
 #pragma unroll 4
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int b = i >> lsw, q = i & (sw - 1);
-        const float2 t = twy[c * b];
+        const float2 t = t4[b];
         pad[(long long)(L2 * c + b) * Lx + x0 + q] = cmul(sm[b * stride + q], make_float2(t.x, -t.y));
     }
 }
@@ -438,6 +446,34 @@ static cudaError_t configure_rows(size_t bytes)
     return e;
 }
 
+// Column passes: the data tile(s) of L x (sw + 1) values and the twiddle tables in shared memory.
+static size_t cols_a_smem(const FftGrid &g, int swa)
+{
+    return ((size_t)g.L1 * (swa + 1) + g.L1) * sizeof(float2);
+}
+
+static size_t cols_b_smem(const FftGrid &g, int swb, bool product)
+{
+    return ((size_t)(product ? 2 : 1) * g.L2 * (swb + 1) + 2 * g.L2) * sizeof(float2);
+}
+
+static cudaError_t configure_cols(const FftGrid &g)
+{
+    static size_t done_a = 0, done_b = 0;
+    const size_t a = cols_a_smem(g, strip_width(g.Lx, g.L1)), b = cols_b_smem(g, strip_width(g.Lx, g.L2), true);
+    cudaError_t e = cudaSuccess;
+    if (a > 48 * 1024 && a > done_a) {
+        for (auto fn : {(const void *)fft_cols_a_kernel<false>, (const void *)fft_cols_a_kernel<true>})
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a);
+        if (e == cudaSuccess) done_a = a;
+    }
+    if (e == cudaSuccess && b > 48 * 1024 && b > done_b) {   // the product pass holds two tiles
+        e = cudaFuncSetAttribute(fft_cols_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        if (e == cudaSuccess) done_b = b;
+    }
+    return e;
+}
+
 cudaError_t launch_fft_chirp_spectrum(const FftGrid &g, float2 *spec, unsigned long long C, double pre_re,
                                       double pre_im, const float2 *twx, const float2 *twy, cudaStream_t s)
 {
@@ -449,9 +485,11 @@ cudaError_t launch_fft_chirp_spectrum(const FftGrid &g, float2 *spec, unsigned l
     fft_rows_kernel<kRowInPlace><<<(g.Ly + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(
         nullptr, spec, nullptr, 0, 0, g.Lx, g.Ly, nseq, twx);
     const int swa = strip_width(g.Lx, g.L1), swb = strip_width(g.Lx, g.L2);
-    fft_cols_a_kernel<false><<<g.L2 * (g.Lx / swa), threads_for(g.L1 * swa), g.L1 * (swa + 1) * sizeof(float2), s>>>(
+    e = configure_cols(g);
+    if (e != cudaSuccess) return e;
+    fft_cols_a_kernel<false><<<g.L2 * (g.Lx / swa), threads_for(g.L1 * swa), cols_a_smem(g, swa), s>>>(
         spec, g.Lx, g.L1, g.L2, swa, g.Ly, g.Ly, twy);
-    fft_cols_b_kernel<<<g.L1 * (g.Lx / swb), threads_for(g.L2 * swb), g.L2 * (swb + 1) * sizeof(float2), s>>>(
+    fft_cols_b_kernel<<<g.L1 * (g.Lx / swb), threads_for(g.L2 * swb), cols_b_smem(g, swb, false), s>>>(
         spec, nullptr, g.Lx, g.L1, g.L2, swb, twy);
     return cudaGetLastError();
 }
@@ -470,17 +508,12 @@ cudaError_t launch_fft_convolve(const FftGrid &g, const float *in, int H, int W,
         fft_rows_kernel<kRowPadRows><<<(H + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(nullptr, pad, nullptr,
                                                                                               H, W, g.Lx, H, nseq, twx);
     const int swa = strip_width(g.Lx, g.L1), swb = strip_width(g.Lx, g.L2);
-    const size_t sa = g.L1 * (swa + 1) * sizeof(float2), sb = g.L2 * (swb + 1) * sizeof(float2);
+    const size_t sa = cols_a_smem(g, swa), sb = cols_b_smem(g, swb, true);
+    e = configure_cols(g);
+    if (e != cudaSuccess) return e;
     fft_cols_a_kernel<false><<<g.L2 * (g.Lx / swa), threads_for(g.L1 * swa), sa, s>>>(pad, g.Lx, g.L1, g.L2, swa, H,
                                                                                      g.Ly, twy);
-    static size_t colb_done = 0;   // the product pass holds two tiles: above the default 48 KB
-    if (2 * sb > 48 * 1024 && 2 * sb > colb_done) {
-        e = cudaFuncSetAttribute(fft_cols_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * sb));
-        if (e != cudaSuccess) return e;
-        colb_done = 2 * sb;
-    }
-    fft_cols_b_kernel<<<g.L1 * (g.Lx / swb), threads_for(g.L2 * swb), 2 * sb, s>>>(pad, spec, g.Lx, g.L1, g.L2, swb,
-                                                                                  twy);
+    fft_cols_b_kernel<<<g.L1 * (g.Lx / swb), threads_for(g.L2 * swb), sb, s>>>(pad, spec, g.Lx, g.L1, g.L2, swb, twy);
     fft_cols_a_kernel<true><<<g.L2 * (g.Lx / swa), threads_for(g.L1 * swa), sa, s>>>(pad, g.Lx, g.L1, g.L2, swa, g.Ly,
                                                                                     H, twy);
     fft_rows_kernel<kRowCrop><<<(H + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(nullptr, pad, out, H, W,
