@@ -241,7 +241,7 @@ enum { kRowExpand = 0, kRowInPlace = 1, kRowCrop = 2, kRowPadRows = 3 };
 //   kRowInPlace: rows of pad, forward, in place (the chirp, all Ly rows);
 //   kRowCrop:    rows y < H of pad, inverse, columns < W into the output planes.
 template <int MODE>
-__global__ void fft_rows_kernel(const float *__restrict__ in, float2 *__restrict__ pad, float *__restrict__ out,
+__global__ void __launch_bounds__(1024) fft_rows_kernel(const float *__restrict__ in, float2 *__restrict__ pad, float *__restrict__ out,
                                 int H, int W, int Lx, int rows, int nseq, const float2 *__restrict__ twx)
 {
     extern __shared__ float2 sm[];
