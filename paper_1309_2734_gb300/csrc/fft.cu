@@ -233,6 +233,114 @@ __device__ void smem_fft(float2 *s, int M, int nseq, int stride, const float2 *t
     else if (rest == 1) stockham_stage<2, INV, LAYOUT>(s, lm, lq, stride, ls, tw, lt);
 }
 
+// The same stages with the geometry known at compile time (LM = log2 M,
+// LQ = log2 nseq, LS = log2 Ns; the CTA has exactly M nseq / 16 threads, so
+// every butterfly slot is live): the index arithmetic folds into shifts and
+// immediate offsets.  Rows layout: for spans of at least 32 values the padding
+// term of an element r spans on is (j >> 5) + r (span / 32).
+template <int LAYOUT, int M, int STRIDE>
+__device__ __forceinline__ int saddr_ct(int e, int q)
+{
+    if (LAYOUT == kLayoutRows) return q * (M + (M >> 5)) + e + (e >> 5);
+    return e * STRIDE + q;
+}
+
+template <int R, bool INV, int LAYOUT, int LM, int LQ, int LS>
+__device__ __forceinline__ void stockham_stage_ct(float2 *s, const float2 *tw)
+{
+    constexpr int PER = 16 / R;
+    constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+    constexpr int M = 1 << LM, NSEQ = 1 << LQ, T = (M << LQ) / 16;
+    constexpr int LSPAN = LM - LR, SPAN = 1 << LSPAN;
+    constexpr int STRIDE = NSEQ + 1;
+    float2 v[16];
+    int jj[PER], qq[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int w = threadIdx.x + u * T;
+        int q, j;
+        if (LAYOUT == kLayoutCols) {
+            q = w & (NSEQ - 1);
+            j = w >> LQ;
+        } else {
+            j = w & (SPAN - 1);
+            q = w >> LSPAN;
+        }
+        jj[u] = j;
+        qq[u] = q;
+        if (LAYOUT == kLayoutRows && LSPAN >= 5) {
+            const int base = q * (M + (M >> 5)) + j + (j >> 5);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u * R + r] = s[base + r * (SPAN + (SPAN >> 5))];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u * R + r] = s[saddr_ct<LAYOUT, M, STRIDE>(j + (r << LSPAN), q)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = jj[u], q = qq[u];
+        const int k = j & ((1 << LS) - 1);
+        if (LS > 0) {
+            float2 w[R];
+            stage_twiddles<R>(w, tw, k << (LM - LS - LR), INV);   // e^{-2 pi i k / (Ns R)}
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[u * R + r] = cmul(v[u * R + r], w[r]);
+        }
+        dft_regs<R, INV>(&v[u * R]);
+        const int base = ((j >> LS) << (LS + LR)) + k;
+        if (LAYOUT == kLayoutRows && LS >= 5) {
+            const int b0 = q * (M + (M >> 5)) + base + (base >> 5);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[b0 + r * ((1 << LS) + (1 << (LS - 5)))] = v[u * R + r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[saddr_ct<LAYOUT, M, STRIDE>(base + (r << LS), q)] = v[u * R + r];
+        }
+    }
+    __syncthreads();
+}
+
+template <bool INV, int LAYOUT, int LM, int LQ, int LS>
+__device__ __forceinline__ void smem_fft_ct(float2 *s, const float2 *tw)
+{
+    if constexpr (LS + 4 <= LM) {
+        stockham_stage_ct<16, INV, LAYOUT, LM, LQ, LS>(s, tw);
+        smem_fft_ct<INV, LAYOUT, LM, LQ, LS + 4>(s, tw);
+    } else if constexpr (LM - LS == 3) {
+        stockham_stage_ct<8, INV, LAYOUT, LM, LQ, LS>(s, tw);
+    } else if constexpr (LM - LS == 2) {
+        stockham_stage_ct<4, INV, LAYOUT, LM, LQ, LS>(s, tw);
+    } else if constexpr (LM - LS == 1) {
+        stockham_stage_ct<2, INV, LAYOUT, LM, LQ, LS>(s, tw);
+    }
+}
+
+// Row transforms of the sizes the display-size planes use, at compile time; the rest at run time
+// (tw[k] = e^{-2 pi i k / M}).
+template <bool INV>
+__device__ __forceinline__ void rows_fft(float2 *s, int M, int nseq, const float2 *tw)
+{
+    const int T = blockDim.x;   // the compile-time forms assume exactly M nseq / 16 threads
+    if (M == 8192 && nseq == 1 && T == 512) smem_fft_ct<INV, kLayoutRows, 13, 0, 0>(s, tw);
+    else if (M == 16384 && nseq == 1 && T == 1024) smem_fft_ct<INV, kLayoutRows, 14, 0, 0>(s, tw);
+    else if (M == 4096 && nseq == 1 && T == 256) smem_fft_ct<INV, kLayoutRows, 12, 0, 0>(s, tw);
+    else if (M == 2048 && nseq == 2 && T == 256) smem_fft_ct<INV, kLayoutRows, 11, 1, 0>(s, tw);
+    else smem_fft<INV, kLayoutRows>(s, M, nseq, 0, tw, 1);
+}
+
+// Column transforms (M points over nseq columns, stride nseq + 1), likewise.
+template <bool INV>
+__device__ __forceinline__ void cols_fft(float2 *s, int M, int nseq, int stride, const float2 *tw)
+{
+    const bool t256 = blockDim.x == 256, s1 = stride == nseq + 1;
+    if (M == 128 && nseq == 32 && t256 && s1) smem_fft_ct<INV, kLayoutCols, 7, 5, 0>(s, tw);
+    else if (M == 64 && nseq == 64 && t256 && s1) smem_fft_ct<INV, kLayoutCols, 6, 6, 0>(s, tw);
+    else if (M == 32 && nseq == 128 && t256 && s1) smem_fft_ct<INV, kLayoutCols, 5, 7, 0>(s, tw);
+    else smem_fft<INV, kLayoutCols>(s, M, nseq, stride, tw, 1);
+}
+
 enum { kRowExpand = 0, kRowInPlace = 1, kRowCrop = 2, kRowPadRows = 3 };
 
 // Row transforms: nseq rows of length Lx per CTA.
@@ -265,7 +373,7 @@ __global__ void __launch_bounds__(1024) fft_rows_kernel(const float *__restrict_
     }
     cp_async_wait_all();
     __syncthreads();
-    smem_fft<MODE == kRowCrop, kLayoutRows>(sm, Lx, nseq, 0, twx, 1);
+    rows_fft<MODE == kRowCrop>(sm, Lx, nseq, twx);
     for (int q = 0; q < nseq; ++q) {
         const int y = y0 + q;
         if (y >= rows) break;
@@ -305,7 +413,7 @@ __global__ void fft_cols_a_kernel(float2 *__restrict__ pad, int Lx, int L1, int 
     for (int k = threadIdx.x; k < L1; k += blockDim.x) tw[k] = twy[k * L2];
     cp_async_wait_all();
     __syncthreads();
-    smem_fft<INV, kLayoutCols>(sm, L1, sw, stride, tw, 1);
+    cols_fft<INV>(sm, L1, sw, stride, tw);
 #pragma unroll 4
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int a = i >> lsw, c = i & (sw - 1);
@@ -348,7 +456,7 @@ __global__ void fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__rest
         sm[b * stride + q] = cmul(sm[b * stride + q], t4[b]);
     }
     __syncthreads();
-    smem_fft<false, kLayoutCols>(sm, L2, sw, stride, tw, 1);
+    cols_fft<false>(sm, L2, sw, stride, tw);
     if (spec == nullptr) {
 #pragma unroll 4
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -362,7 +470,7 @@ __global__ void fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__rest
         sm[d * stride + q] = cmul(sm[d * stride + q], sp[d * stride + q]);
     }
     __syncthreads();
-    smem_fft<true, kLayoutCols>(sm, L2, sw, stride, tw, 1);
+    cols_fft<true>(sm, L2, sw, stride, tw);
 #pragma unroll 4
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int b = i >> lsw, q = i & (sw - 1);
