@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kRecThreads)
             const int p = s_hit[h];
             const int4 g = s_geo[p];
             const uint4 v = s_win[p];
+            if (g.y + (int)v.w < nb || g.y - (int)v.w > nb + 3) continue;   // the window misses this warp's rows
             const float a = -__uint_as_float(v.y);   // the half-turn shift below negates sine and cosine
             const int dx = m - g.x;
 #pragma unroll
