@@ -343,6 +343,130 @@ __device__ __forceinline__ void cols_fft(float2 *s, int M, int nseq, int stride,
 
 enum { kRowExpand = 0, kRowInPlace = 1, kRowCrop = 2, kRowPadRows = 3 };
 
+// Row transforms of compile-time length whose first stage reads its values
+// straight from global memory and whose last stage writes straight to it (the
+// element a thread holds in either is j + r M / R, so a warp's accesses stay
+// contiguous): shared memory carries only the values between stages.  IO
+// supplies load(q, x) and store(q, x, v) for row q of the CTA, element x.
+template <int R, bool INV, int LM, int LQ, int LS, bool FIRST, bool LAST, class IO>
+__device__ __forceinline__ void stockham_stage_io(float2 *s, const float2 *tw, const IO &io)
+{
+    constexpr int PER = 16 / R;
+    constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+    constexpr int M = 1 << LM, T = (M << LQ) / 16;
+    constexpr int LSPAN = LM - LR, SPAN = 1 << LSPAN;
+    static_assert(LSPAN >= 5, "spans of at least 32 values");
+    float2 v[16];
+    int jj[PER], qq[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int w = threadIdx.x + u * T;
+        const int j = w & (SPAN - 1), q = w >> LSPAN;
+        jj[u] = j;
+        qq[u] = q;
+        if (FIRST) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u * R + r] = io.load(q, j + r * SPAN);
+        } else {
+            const int base = q * (M + (M >> 5)) + j + (j >> 5);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u * R + r] = s[base + r * (SPAN + (SPAN >> 5))];
+        }
+    }
+    if (!FIRST) __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = jj[u], q = qq[u];
+        const int k = j & ((1 << LS) - 1);
+        if (LS > 0) {
+            float2 w[R];
+            stage_twiddles<R>(w, tw, k << (LM - LS - LR), INV);
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[u * R + r] = cmul(v[u * R + r], w[r]);
+        }
+        dft_regs<R, INV>(&v[u * R]);
+        if (LAST) {   // LS + LR = LM: the outputs are j + r 2^LS = j + r SPAN
+#pragma unroll
+            for (int r = 0; r < R; ++r) io.store(q, j + r * SPAN, v[u * R + r]);
+        } else {
+            const int base = ((j >> LS) << (LS + LR)) + k;
+            if (LS >= 5) {
+                const int b0 = q * (M + (M >> 5)) + base + (base >> 5);
+#pragma unroll
+                for (int r = 0; r < R; ++r) s[b0 + r * ((1 << LS) + (1 << (LS >= 5 ? LS - 5 : 0)))] = v[u * R + r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int e = base + (r << LS);
+                    s[q * (M + (M >> 5)) + e + (e >> 5)] = v[u * R + r];
+                }
+            }
+        }
+    }
+    if (!LAST) __syncthreads();
+}
+
+template <bool INV, int LM, int LQ, int LS, class IO>
+__device__ __forceinline__ void rows_fft_io(float2 *s, const float2 *tw, const IO &io)
+{
+    if constexpr (LS + 4 < LM) {
+        stockham_stage_io<16, INV, LM, LQ, LS, LS == 0, false>(s, tw, io);
+        rows_fft_io<INV, LM, LQ, LS + 4>(s, tw, io);
+    } else if constexpr (LS + 4 == LM) {
+        stockham_stage_io<16, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
+    } else if constexpr (LM - LS == 3) {
+        stockham_stage_io<8, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
+    } else if constexpr (LM - LS == 2) {
+        stockham_stage_io<4, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
+    } else if constexpr (LM - LS == 1) {
+        stockham_stage_io<2, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
+    }
+}
+
+// Global sources and destinations of the row kernels (row q of the CTA is y0 + q).
+template <int MODE>
+struct RowIO {
+    const float *in;
+    float2 *pad;
+    float *out;
+    long long plane;
+    int y0, rows, W, Lx;
+    __device__ __forceinline__ float2 load(int q, int x) const
+    {
+        const int y = y0 + q;
+        if (y >= rows || ((MODE == kRowExpand || MODE == kRowPadRows) && x >= W)) return make_float2(0.0f, 0.0f);
+        if (MODE == kRowExpand) return make_float2(in[(long long)y * W + x], in[plane + (long long)y * W + x]);
+        return pad[(long long)y * Lx + x];
+    }
+    __device__ __forceinline__ void store(int q, int x, float2 v) const
+    {
+        const int y = y0 + q;
+        if (y >= rows) return;
+        if (MODE == kRowCrop) {
+            if (x < W) {
+                out[(long long)y * W + x] = v.x;
+                out[plane + (long long)y * W + x] = v.y;
+            }
+        } else {
+            pad[(long long)y * Lx + x] = v;
+        }
+    }
+};
+
+// The row kernel's transform when its length has a compile-time form: true if done.
+template <int MODE>
+__device__ __forceinline__ bool rows_fft_direct(float2 *s, int Lx, int nseq, const float2 *tw, const RowIO<MODE> &io)
+{
+    constexpr bool INV = MODE == kRowCrop;
+    const int T = blockDim.x;
+    if (Lx == 8192 && nseq == 1 && T == 512) rows_fft_io<INV, 13, 0, 0>(s, tw, io);
+    else if (Lx == 16384 && nseq == 1 && T == 1024) rows_fft_io<INV, 14, 0, 0>(s, tw, io);
+    else if (Lx == 4096 && nseq == 1 && T == 256) rows_fft_io<INV, 12, 0, 0>(s, tw, io);
+    else if (Lx == 2048 && nseq == 2 && T == 256) rows_fft_io<INV, 11, 1, 0>(s, tw, io);
+    else return false;
+    return true;
+}
+
 // Row transforms: nseq rows of length Lx per CTA.
 //   kRowExpand:  rows y < H from the input planes [2][H][W] (zeros beyond W), forward, into pad;
 //   kRowPadRows: rows y < H of pad, columns < W (zeros beyond), forward, in place;
@@ -356,6 +480,7 @@ __global__ void __launch_bounds__(1024) fft_rows_kernel(const float *__restrict_
     const int y0 = blockIdx.x * nseq;
     const int T = blockDim.x;
     const long long plane = (long long)H * W;
+    if (rows_fft_direct<MODE>(sm, Lx, nseq, twx, RowIO<MODE>{in, pad, out, plane, y0, rows, W, Lx})) return;
     for (int q = 0; q < nseq; ++q) {
         const int y = y0 + q;
         for (int x = threadIdx.x; x < Lx; x += T) {
