@@ -343,30 +343,42 @@ __device__ __forceinline__ void cols_fft(float2 *s, int M, int nseq, int stride,
 
 enum { kRowExpand = 0, kRowInPlace = 1, kRowCrop = 2, kRowPadRows = 3 };
 
-// Row transforms of compile-time length whose first stage reads its values
-// straight from global memory and whose last stage writes straight to it (the
-// element a thread holds in either is j + r M / R, so a warp's accesses stay
-// contiguous): shared memory carries only the values between stages.  IO
-// supplies load(q, x) and store(q, x, v) for row q of the CTA, element x.
-template <int R, bool INV, int LM, int LQ, int LS, bool FIRST, bool LAST, class IO>
+// Transforms of compile-time length whose first stage reads its values from,
+// and whose last stage writes them to, an IO object instead of shared memory
+// (the element a thread holds in either is j + r M / R, so a warp's accesses to
+// global memory stay contiguous: rows j, columns q): shared memory carries only
+// the values between stages.  IO supplies load(q, e) and store(q, e, v) for
+// sequence q, element e.
+template <int R, bool INV, int LAYOUT, int LM, int LQ, int LS, bool FIRST, bool LAST, class IO>
 __device__ __forceinline__ void stockham_stage_io(float2 *s, const float2 *tw, const IO &io)
 {
     constexpr int PER = 16 / R;
     constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
-    constexpr int M = 1 << LM, T = (M << LQ) / 16;
+    constexpr int M = 1 << LM, NSEQ = 1 << LQ, T = (M << LQ) / 16;
     constexpr int LSPAN = LM - LR, SPAN = 1 << LSPAN;
-    static_assert(LSPAN >= 5, "spans of at least 32 values");
+    constexpr int STRIDE = NSEQ + 1;   // columns layout
+    static_assert(LAYOUT == kLayoutCols || LSPAN >= 5, "row spans of at least 32 values");
     float2 v[16];
     int jj[PER], qq[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int w = threadIdx.x + u * T;
-        const int j = w & (SPAN - 1), q = w >> LSPAN;
+        int q, j;
+        if (LAYOUT == kLayoutCols) {
+            q = w & (NSEQ - 1);
+            j = w >> LQ;
+        } else {
+            j = w & (SPAN - 1);
+            q = w >> LSPAN;
+        }
         jj[u] = j;
         qq[u] = q;
         if (FIRST) {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[u * R + r] = io.load(q, j + r * SPAN);
+        } else if (LAYOUT == kLayoutCols) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u * R + r] = s[(j + r * SPAN) * STRIDE + q];
         } else {
             const int base = q * (M + (M >> 5)) + j + (j >> 5);
 #pragma unroll
@@ -385,42 +397,52 @@ __device__ __forceinline__ void stockham_stage_io(float2 *s, const float2 *tw, c
             for (int r = 1; r < R; ++r) v[u * R + r] = cmul(v[u * R + r], w[r]);
         }
         dft_regs<R, INV>(&v[u * R]);
-        if (LAST) {   // LS + LR = LM: the outputs are j + r 2^LS = j + r SPAN
+        const int base = ((j >> LS) << (LS + LR)) + k;
+        if (LAST) {   // LS + LR = LM: base = j, the outputs are j + r 2^LS = j + r SPAN
 #pragma unroll
             for (int r = 0; r < R; ++r) io.store(q, j + r * SPAN, v[u * R + r]);
+        } else if (LAYOUT == kLayoutCols) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[(base + (r << LS)) * STRIDE + q] = v[u * R + r];
+        } else if (LS >= 5) {
+            const int b0 = q * (M + (M >> 5)) + base + (base >> 5);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[b0 + r * ((1 << LS) + (1 << (LS >= 5 ? LS - 5 : 0)))] = v[u * R + r];
         } else {
-            const int base = ((j >> LS) << (LS + LR)) + k;
-            if (LS >= 5) {
-                const int b0 = q * (M + (M >> 5)) + base + (base >> 5);
 #pragma unroll
-                for (int r = 0; r < R; ++r) s[b0 + r * ((1 << LS) + (1 << (LS >= 5 ? LS - 5 : 0)))] = v[u * R + r];
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int e = base + (r << LS);
-                    s[q * (M + (M >> 5)) + e + (e >> 5)] = v[u * R + r];
-                }
+            for (int r = 0; r < R; ++r) {
+                const int e = base + (r << LS);
+                s[q * (M + (M >> 5)) + e + (e >> 5)] = v[u * R + r];
             }
         }
     }
     if (!LAST) __syncthreads();
 }
 
+// IN_IO: the first stage reads io (else shared memory, as left by the caller); OUT_IO: the last stage writes io
+// (else shared memory, natural order).  A last stage writing io does not end with a barrier.
+template <bool INV, int LAYOUT, int LM, int LQ, bool IN_IO, bool OUT_IO, int LS, class IO>
+__device__ __forceinline__ void fft_io(float2 *s, const float2 *tw, const IO &io)
+{
+    constexpr bool F = IN_IO && LS == 0;
+    if constexpr (LS + 4 < LM) {
+        stockham_stage_io<16, INV, LAYOUT, LM, LQ, LS, F, false>(s, tw, io);
+        fft_io<INV, LAYOUT, LM, LQ, IN_IO, OUT_IO, LS + 4>(s, tw, io);
+    } else if constexpr (LS + 4 == LM) {
+        stockham_stage_io<16, INV, LAYOUT, LM, LQ, LS, F, OUT_IO>(s, tw, io);
+    } else if constexpr (LM - LS == 3) {
+        stockham_stage_io<8, INV, LAYOUT, LM, LQ, LS, F, OUT_IO>(s, tw, io);
+    } else if constexpr (LM - LS == 2) {
+        stockham_stage_io<4, INV, LAYOUT, LM, LQ, LS, F, OUT_IO>(s, tw, io);
+    } else if constexpr (LM - LS == 1) {
+        stockham_stage_io<2, INV, LAYOUT, LM, LQ, LS, F, OUT_IO>(s, tw, io);
+    }
+}
+
 template <bool INV, int LM, int LQ, int LS, class IO>
 __device__ __forceinline__ void rows_fft_io(float2 *s, const float2 *tw, const IO &io)
 {
-    if constexpr (LS + 4 < LM) {
-        stockham_stage_io<16, INV, LM, LQ, LS, LS == 0, false>(s, tw, io);
-        rows_fft_io<INV, LM, LQ, LS + 4>(s, tw, io);
-    } else if constexpr (LS + 4 == LM) {
-        stockham_stage_io<16, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
-    } else if constexpr (LM - LS == 3) {
-        stockham_stage_io<8, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
-    } else if constexpr (LM - LS == 2) {
-        stockham_stage_io<4, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
-    } else if constexpr (LM - LS == 1) {
-        stockham_stage_io<2, INV, LM, LQ, LS, LS == 0, true>(s, tw, io);
-    }
+    fft_io<INV, kLayoutRows, LM, LQ, true, true, LS>(s, tw, io);
 }
 
 // Global sources and destinations of the row kernels (row q of the CTA is y0 + q).
@@ -514,6 +536,69 @@ __global__ void __launch_bounds__(1024) fft_rows_kernel(const float *__restrict_
     }
 }
 
+// Column transform lengths with a compile-time form (length L over sw columns, 256 threads).
+__host__ __device__ inline bool cols_ct(int L, int sw)
+{
+    return (L == 128 && sw == 32) || (L == 64 && sw == 64) || (L == 32 && sw == 128);
+}
+
+template <bool INV, bool IN_IO, bool OUT_IO, class IO>
+__device__ __forceinline__ void cols_fft_direct(float2 *s, int L, int sw, const float2 *tw, const IO &io)
+{
+    if (L == 128 && sw == 32) fft_io<INV, kLayoutCols, 7, 5, IN_IO, OUT_IO, 0>(s, tw, io);
+    else if (L == 64 && sw == 64) fft_io<INV, kLayoutCols, 6, 6, IN_IO, OUT_IO, 0>(s, tw, io);
+    else fft_io<INV, kLayoutCols, 5, 7, IN_IO, OUT_IO, 0>(s, tw, io);
+}
+
+// Column pass A's global side: sequence q is column x0 + q, element a is row L2 a + b.
+struct ColsAIO {
+    float2 *pad;
+    int Lx, L2, b, x0, nz_rows, keep_rows;
+    __device__ __forceinline__ float2 load(int q, int a) const
+    {
+        const int row = L2 * a + b;
+        return row < nz_rows ? pad[(long long)row * Lx + x0 + q] : make_float2(0.0f, 0.0f);
+    }
+    __device__ __forceinline__ void store(int q, int a, float2 v) const
+    {
+        const int row = L2 * a + b;
+        if (row < keep_rows) pad[(long long)row * Lx + x0 + q] = v;
+    }
+};
+
+// Column pass B, forward: in, rows L2 c + b times the four-step twiddle; out, the product with the spectrum into
+// shared memory (natural order) -- or, building the spectrum itself (spec == nullptr), straight to pad.
+struct ColsBFwdIO {
+    float2 *pad;
+    const float2 *spec;
+    float2 *s;
+    const float2 *t4;
+    int Lx, L2, c, x0, stride;
+    __device__ __forceinline__ float2 load(int q, int b) const
+    {
+        return cmul(pad[(long long)(L2 * c + b) * Lx + x0 + q], t4[b]);
+    }
+    __device__ __forceinline__ void store(int q, int d, float2 v) const
+    {
+        const long long g = (long long)(L2 * c + d) * Lx + x0 + q;
+        if (spec != nullptr) s[d * stride + q] = cmul(v, spec[g]);
+        else pad[g] = v;
+    }
+};
+
+// Column pass B, inverse: out, rows L2 c + b times the conjugate four-step twiddle.
+struct ColsBInvIO {
+    float2 *pad;
+    const float2 *t4;
+    int Lx, L2, c, x0;
+    __device__ __forceinline__ float2 load(int, int) const { return make_float2(0.0f, 0.0f); }
+    __device__ __forceinline__ void store(int q, int b, float2 v) const
+    {
+        const float2 t = t4[b];
+        pad[(long long)(L2 * c + b) * Lx + x0 + q] = cmul(v, make_float2(t.x, -t.y));
+    }
+};
+
 // Column pass A: for each b < L2 and strip of sw columns, L1-point transforms
 // over the rows L2 a + b.  Forward: rows >= nz_rows are zero (not loaded), all
 // outputs stored at rows L2 c + b.  Inverse: outputs a stored at rows L2 a + b
@@ -529,6 +614,12 @@ __global__ void fft_cols_a_kernel(float2 *__restrict__ pad, int Lx, int L1, int 
     const int stride = sw + 1;
     const int n = L1 << lsw;
     float2 *tw = sm + L1 * stride;   // e^{-2 pi i k / L1} = twy[k L2], k < L1, in shared memory
+    if (cols_ct(L1, sw) && blockDim.x == 256) {   // first and last stages on global memory
+        for (int k = threadIdx.x; k < L1; k += blockDim.x) tw[k] = twy[k * L2];
+        __syncthreads();
+        cols_fft_direct<INV, true, true>(sm, L1, sw, tw, ColsAIO{pad, Lx, L2, b, x0, nz_rows, keep_rows});
+        return;
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int a = i >> lsw, c = i & (sw - 1);
         const int row = L2 * a + b;
@@ -561,6 +652,19 @@ __global__ void fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__rest
     const int c = blockIdx.x >> lstrips, x0 = (blockIdx.x & ((1 << lstrips) - 1)) << lsw;
     const int stride = sw + 1;
     const int n = L2 << lsw;
+    if (cols_ct(L2, sw) && blockDim.x == 256) {   // first and last stages on global memory: one tile, no spectrum tile
+        float2 *tw = sm + L2 * stride, *t4 = tw + L2;
+        for (int k = threadIdx.x; k < L2; k += blockDim.x) {
+            tw[k] = twy[k * L1];
+            t4[k] = twy[c * k];
+        }
+        __syncthreads();
+        cols_fft_direct<false, true, true>(sm, L2, sw, tw, ColsBFwdIO{pad, spec, sm, t4, Lx, L2, c, x0, stride});
+        if (spec == nullptr) return;
+        __syncthreads();   // the products are in shared memory
+        cols_fft_direct<true, false, true>(sm, L2, sw, tw, ColsBInvIO{pad, t4, Lx, L2, c, x0});
+        return;
+    }
     float2 *sp = sm + L2 * stride;   // the spectrum's tile
     // in shared memory: e^{-2 pi i k / L2} = twy[k L1] and the four-step twiddles e^{-2 pi i c b / Ly} = twy[c b]
     float2 *tw = sm + (spec != nullptr ? 2 : 1) * L2 * stride, *t4 = tw + L2;
@@ -687,7 +791,8 @@ static size_t cols_a_smem(const FftGrid &g, int swa)
 
 static size_t cols_b_smem(const FftGrid &g, int swb, bool product)
 {
-    return ((size_t)(product ? 2 : 1) * g.L2 * (swb + 1) + 2 * g.L2) * sizeof(float2);
+    const int tiles = product && !cols_ct(g.L2, swb) ? 2 : 1;   // the compile-time form reads the spectrum directly
+    return ((size_t)tiles * g.L2 * (swb + 1) + 2 * g.L2) * sizeof(float2);
 }
 
 static cudaError_t configure_cols(const FftGrid &g)
