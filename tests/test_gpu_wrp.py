@@ -75,6 +75,25 @@ def test_fresnel_own_fft_on_display_sizes():
     assert _nrms_c(got[rows, cols], ref) <= TOL
 
 
+@pytest.mark.parametrize("w,h", [(4100, 2100), (4200, 64)])
+def test_fresnel_own_fft_long_rows_and_columns(w, h):
+    """Planes padded to 8192 x 8192 (rows of 8192 points, columns split 128 x 64) and 16384 x 128 (rows of 16384
+    points): sampled pixels, edges included, against the direct sum."""
+    u = workloads.complex_plane(920 + h, w, h)
+    uc = u[0].astype(np.float64) + 1j * u[1]
+    rng = np.random.default_rng(921)
+    cols = np.concatenate([rng.integers(0, w, 24), [0, w - 1]])
+    rows = np.concatenate([rng.integers(0, h, 24), [h - 1, 0]])
+    ref = oracle.fresnel_at(uc, 8e-6, 532e-9, 0.4, cols, rows)
+    with Hologram(w, h, 8e-6, 532e-9) as hol:
+        hol.profile(True)
+        got = _cplx(hol.fresnel(torch.from_numpy(u).cuda(), 0.4))
+        hol.sync()
+        names = set(hol.profile_read())
+    assert "fresnel_fft" in names and "cufft_c2c" not in names
+    assert _nrms_c(got[rows, cols], ref) <= TOL
+
+
 def test_fresnel_in_place_and_cached_spectra():
     """d_out == d_in, and spectra for alternating distances (the cache must follow z)."""
     u = workloads.complex_plane(910, 96, 80)
