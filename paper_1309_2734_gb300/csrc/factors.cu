@@ -57,12 +57,75 @@ __device__ __forceinline__ uint32_t pack(float lo_col, float hi_col, int mode, b
     return *reinterpret_cast<const uint32_t *>(&l);
 }
 
-template <int MODE>
+// K1 is 2 pi rounded to a float whose 1.5 multiple K0 is exact, so that the argument grid (f - 1.5) K1 of the
+// fixed-point turn conversions below is symmetric about zero and the hardware sine's odd error cancels in sums.
+constexpr float kTurnK1 = 6.28318595886230469f;   // 0x40c90fdc
+constexpr float kTurnK0 = 9.42477893829345703f;   // 1.5 * kTurnK1, exact
+
+// One point's entry of a row: P (cos b, sin b); Q, the amplitude times (cos a, -sin a), or with IMAG
+// (sin a, cos a) -- the imaginary part's factor.
+template <bool IS_P, bool IMAG>
+__device__ __forceinline__ void factor_entry(float s, float c, float a, float &re, float &im)
+{
+    if (IS_P) {
+        re = c;
+        im = s;
+    } else {
+        re = IMAG ? a * s : a * c;
+        im = IMAG ? a * c : -a * s;
+    }
+}
+
+// FP16 / BF16 factors of rows [line0, line1) of P (IS_P) or Q for the thread's four points: the turn walked down the
+// rows by the second-order recurrence of Eqs. 6-8 in 32-bit fixed point from its exact value and first difference at
+// line0 (drift below 32^2 / 2 units of 2^-32 turn over a block's 32 rows, far below the factors' 2^-11), converted
+// by its top 23 bits as a float mantissa with a half turn added (so (f - 1.5) K1 is the angle itself in [-pi, pi)):
+// no 64-bit product and no conversion instruction per entry.
+template <int MODE, bool IS_P, bool IMAG>
+__device__ __forceinline__ void factor_rows_walk(int line0, int line1, const int (&coord)[4], const uint32_t (&chi)[4],
+                                                 const uint32_t (&clo)[4], const uint32_t (&pist)[4],
+                                                 const float (&a)[4], const bool (&live)[4], uint16_t *base,
+                                                 long long ld, int j0, const PhaseRef &ref)
+{
+    if (line0 >= line1) return;
+    uint32_t g[4], e[4], D[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t d = (uint32_t)(line0 - coord[q]), d1 = d + 1u;
+        const uint32_t G0 = chi[q] * (d * d) + __umulhi(clo[q], d * d);
+        const uint32_t G1 = chi[q] * (d1 * d1) + __umulhi(clo[q], d1 * d1);
+        g[q] = G0 + (IS_P ? 0u : pist[q]) + 0x80000100u;   // a half turn, and rounding to 23 bits
+        e[q] = G1 - G0;
+        D[q] = __funnelshift_l(clo[q], chi[q], 1);          // 2 C, top 32 bits
+    }
+    for (int line = line0; line < line1; ++line) {
+        // reference phase of this row (P: ky n) or column (Q: kx m + phi0)
+        const uint32_t radd = IS_P ? ref_turn(ref, 0, line) - ref.phi0 : ref_turn(ref, line, 0);
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float f = __uint_as_float(__funnelshift_r(g[q] + radd, 0x7fu, 9));
+            float s, c;
+            __sincosf(fmaf(f, kTurnK1, -kTurnK0), &s, &c);
+            float re, im;
+            factor_entry<IS_P, IMAG>(s, c, a[q], re, im);
+            v[2 * q] = live[q] ? re : 0.0f;
+            v[2 * q + 1] = live[q] ? im : 0.0f;
+            g[q] += e[q];
+            e[q] += D[q];
+        }
+        uint16_t *dst = base + (long long)line * ld + 2 * j0;
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(pack(v[0], v[1], MODE, false), pack(v[2], v[3], MODE, false),
+                                                     pack(v[4], v[5], MODE, false), pack(v[6], v[7], MODE, false));
+    }
+}
+
+template <int MODE, bool IMAG>
 __global__ void __launch_bounds__(kFactorThreads)
     factors_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int slots,
                    int height, int width, uint16_t *__restrict__ P, uint16_t *__restrict__ Q, long long ld,
                    long long plane_p, long long plane_q, const float *__restrict__ amp_max, int row_begin,
-                   bool imag, const PhaseRef ref)
+                   const PhaseRef ref)
 {
     const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (j0 >= slots) return;
@@ -95,8 +158,17 @@ __global__ void __launch_bounds__(kFactorThreads)
         }
     }
     const int rows = height + width;
+    const int r_begin = row_begin + blockIdx.y * kRowsPerBlock;
     const int r_end = min(rows, row_begin + (int)(blockIdx.y + 1) * kRowsPerBlock);
-    for (int r = row_begin + blockIdx.y * kRowsPerBlock; r < r_end; ++r) {
+    if constexpr (MODE != kFactorSplit16) {
+        // P rows below height, Q rows (columns) above
+        factor_rows_walk<MODE, true, IMAG>(r_begin, min(r_end, height), py, chi, clo, pist, a, live, P, ld, j0, ref);
+        factor_rows_walk<MODE, false, IMAG>(max(r_begin, height) - height, r_end - height, px, chi, clo, pist, a, live,
+                                            Q, ld, j0, ref);
+        return;
+    }
+    // split FP16: the exact turn of every entry (its hi + lo pair carries 2^-22 of it)
+    for (int r = r_begin; r < r_end; ++r) {
         const bool is_p = r < height;
         const int line = is_p ? r : r - height;
         // reference phase of this row (P: ky n) or column (Q: kx m + phi0)
@@ -113,8 +185,8 @@ __global__ void __launch_bounds__(kFactorThreads)
                 sincos_turn(t, s, c);
                 if (!is_p) {
                     const float cc = c;
-                    c = imag ? a[q] * s : a[q] * c;
-                    s = imag ? a[q] * cc : -a[q] * s;
+                    c = IMAG ? a[q] * s : a[q] * c;
+                    s = IMAG ? a[q] * cc : -a[q] * s;
                 }
             }
             v[2 * q] = c;
@@ -124,11 +196,9 @@ __global__ void __launch_bounds__(kFactorThreads)
         const uint4 hi = make_uint4(pack(v[0], v[1], MODE, false), pack(v[2], v[3], MODE, false),
                                     pack(v[4], v[5], MODE, false), pack(v[6], v[7], MODE, false));
         *reinterpret_cast<uint4 *>(dst) = hi;
-        if (MODE == kFactorSplit16) {
-            const uint4 lo = make_uint4(pack(v[0], v[1], MODE, true), pack(v[2], v[3], MODE, true),
-                                        pack(v[4], v[5], MODE, true), pack(v[6], v[7], MODE, true));
-            *reinterpret_cast<uint4 *>(dst + (is_p ? plane_p : plane_q)) = lo;
-        }
+        const uint4 lo = make_uint4(pack(v[0], v[1], MODE, true), pack(v[2], v[3], MODE, true),
+                                    pack(v[4], v[5], MODE, true), pack(v[6], v[7], MODE, true));
+        *reinterpret_cast<uint4 *>(dst + (is_p ? plane_p : plane_q)) = lo;
     }
 }
 
@@ -164,8 +234,6 @@ constexpr int kGroupThreads = 256;
 constexpr int kGroupLaneRows = 4;                      // rows per lane
 constexpr int kGroupRows = 32 * kGroupLaneRows;       // rows per block
 constexpr int kTileStride = kGroupRows + 1;            // words per slot in the shared tile, +1 against conflicts
-constexpr float kTurnK1 = 6.28318595886230469f;   // 0x40c90fdc
-constexpr float kTurnK0 = 9.42477893829345703f;   // 1.5 * kTurnK1, exact
 
 __device__ __forceinline__ void half_turn_sincos(uint32_t chi, uint32_t clo, uint32_t d, uint32_t add, float &s,
                                                  float &c)
@@ -345,22 +413,25 @@ cudaError_t launch_factors(int mode, const int4 *geo, const uint2 *aux, int n_po
     const long long plane_p = (long long)height * ld, plane_q = (long long)width * ld;
     auto *p = static_cast<uint16_t *>(P);
     auto *q = static_cast<uint16_t *>(Q);
+    const bool im = imag_q_only;
+#define CGH_FACTORS(M, I)                                                                                       \
+    factors_kernel<M, I><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p, q, ld, plane_p, \
+                                                         plane_q, amp_max, row_begin, ref)
     switch (mode) {
     case kFactorF16:
-        factors_kernel<kFactorF16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p, q, ld,
-                                                                   plane_p, plane_q, amp_max, row_begin, imag_q_only, ref);
+        if (im) CGH_FACTORS(kFactorF16, true);
+        else CGH_FACTORS(kFactorF16, false);
         break;
     case kFactorBF16:
-        factors_kernel<kFactorBF16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p, q,
-                                                                    ld, plane_p, plane_q, amp_max, row_begin,
-                                                                    imag_q_only, ref);
+        if (im) CGH_FACTORS(kFactorBF16, true);
+        else CGH_FACTORS(kFactorBF16, false);
         break;
     default:
-        factors_kernel<kFactorSplit16><<<grid, kFactorThreads, 0, s>>>(geo, aux, n_points, slots, height, width, p,
-                                                                       q, ld, plane_p, plane_q, amp_max, row_begin,
-                                                                       imag_q_only, ref);
+        if (im) CGH_FACTORS(kFactorSplit16, true);
+        else CGH_FACTORS(kFactorSplit16, false);
         break;
     }
+#undef CGH_FACTORS
     return cudaGetLastError();
 }
 

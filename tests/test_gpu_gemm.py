@@ -73,8 +73,12 @@ def test_factors_match_fp64_oracle(form):
         Pg = P.float().cpu().numpy().astype(np.float64)
         Qg = Q.float().cpu().numpy().astype(np.float64)
         pad_p, pad_q = P[:, k:], Q[:, k:]
-        rel, floor = (2.0 ** -8, 6e-7) if form == "gemm_bf16" else (2.0 ** -11, 6e-7)
-    # floor: the hardware sine and cosine on [-pi, pi] (<= 3.8e-7) plus the turn conversion (<= 1e-7)
+        # FP16 / BF16 factors walk the turn down a block's rows by the recurrence of Eqs. 6-8 (drift below
+        # 31 * 32 / 2 = 496 units of 2^-32 turn) and convert its top 23 bits (rounding <= 2^-24 turn): the turn
+        # is within 2^-24 + 496 * 2^-32 turn, 2 pi of that is 1.1e-6 rad
+        rel = 2.0 ** -8 if form == "gemm_bf16" else 2.0 ** -11
+        floor = 3.8e-7 + 2 * np.pi * (2.0 ** -24 + 496 * 2.0 ** -32)
+    # floor: the hardware sine and cosine on [-pi, pi] (<= 3.8e-7) plus the turn's own error
     for got, ref in ((Pg[:, :k], Pr), (Qg[:, :k], Qr)):
         err = np.abs(got - ref)
         assert np.all(err <= rel * np.abs(ref) + floor), float(np.max(err - rel * np.abs(ref)))
