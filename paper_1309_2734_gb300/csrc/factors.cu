@@ -8,16 +8,18 @@
 //   Q[m][2j] = s A_j cos alpha_mj, Q[m][2j+1] = -s A_j sin alpha_mj
 // (s = an optional amplitude scale, undone in the GEMM epilogue).
 //
-// Each angle is reduced exactly in integers: with the point's 64-bit
-// fixed-point constant C_j (prep.cu), the turn is the top 32 bits of
-// C_j d^2 mod 2^64, d the integer distance along one axis (|d| < 2^15, so
-// d^2 < 2^30).  The signed 32-bit turn converts to t in [-1/2, 1/2) (error
-// <= 2^-26 turn), and the hardware sine and cosine (MUFU, |2 pi t| <= pi,
-// absolute error below 4e-7) give the pair, which is rounded to FP16 or BF16,
-// or split into hi = fp16(v) and lo = fp16(v - hi).  That error is far below
-// FP16/BF16 rounding and, in the split form, contributes ~1e-7 to the NRMS
-// (the accumulation dominates).  The kernel is issue-bound; the MUFU leaves
-// the issue slots to the integer phase work.  No FP64 is needed on the GPU.
+// Each angle is reduced in integers: with the point's 64-bit fixed-point
+// constant C_j (prep.cu), the turn is the top 32 bits of C_j d^2 mod 2^64, d
+// the integer distance along one axis (|d| < 2^15, so d^2 < 2^30).  Split
+// FP16 (hi = fp16(v), lo = fp16(v - hi), 2^-22 of v): that exact turn for every
+// entry, converted to t in [-1/2, 1/2) (error <= 2^-26 turn), and the hardware
+// sine and cosine (MUFU, |2 pi t| <= pi, absolute error below 4e-7) give the
+// pair -- ~1e-7 of the NRMS, which the accumulation dominates.  FP16 and BF16:
+// the turn is exact at a band's first row and walks down the band by the
+// second-order recurrence of Eqs. 6-8 (drift < 496 units of 2^-32 turn over 32
+// rows), converted through its top 23 bits as a float mantissa -- 1.1e-6 rad at
+// most, far below their rounding, and the kernel becomes HBM-write-bound.  No
+// FP64 is needed on the GPU.
 //
 // For the imaginary part of the complex wave, sin(alpha + beta) =
 // sin(alpha) cos(beta) + cos(alpha) sin(beta), so Im O = P Q'^T with the same P
