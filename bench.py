@@ -42,7 +42,7 @@ MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
 NCU_TRAFFIC = [
     # profiles/direct_sfu-1920x1080-n10000.md: 0.380 MB read + 104.574 MB written per launch
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000", "src": "direct.cu",
-     "sha1": "909d1c730cfe1e0675b3e71114a4b2f5b6ecbd04", "bytes_per_launch": 104954624},
+     "sha1": "6edcd8591c8734ad74f7ec9080191356f51513ac", "bytes_per_launch": 104954624},
     # profiles/gemm_f16-1920x1080-n50000.md: 600.831 MB read + 3.912 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000", "src": "gemm.cu",
      "sha1": "dc9bd0c2611696995acb7c31c0beb99a1dff3738", "bytes_per_launch": 604743680},

@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(BX *BY, 2)
     }
 }
 
-constexpr int kTL = 8, kTR = 4, kBX = 32, kBY = 8;   // the wide shape (the batch kernel's)
-constexpr int kTallBX = 16, kTallBY = 16;             // the tall shape: 128-pixel-wide tiles
+constexpr int kTL = 8, kTR = 4, kBX = 32, kBY = 8;   // the wide shape: 256 x 32 pixels per CTA
+constexpr int kTallBX = 16, kTallBY = 16;             // the tall shape: 128 x 64 pixels per CTA
 
 template <int BX, int BY, bool SFU, bool EXTRA>
 void direct_as(dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_ptiles, int width, int height,

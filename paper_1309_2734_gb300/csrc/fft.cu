@@ -21,7 +21,13 @@
 // over elements M/R apart, twiddles e^{-2 pi i r (j mod Ns) / (Ns R)}, results
 // at (j / Ns) Ns R + j mod Ns + r Ns), radix 16 (and one stage of 8, 4 or 2):
 // each thread holds 16 values per stage; twiddles come from a table of
-// e^{-2 pi i k / L} built in double on the host.
+// e^{-2 pi i k / L} built in double on the host (the column passes copy the
+// entries they use into shared memory).  The transform lengths of display-size
+// planes (rows of 2048 .. 16384 points, columns of 32 .. 128) are compiled with
+// their geometry as constants, and there the first stage reads its values
+// straight from global memory and the last stage writes straight to it, so
+// shared memory carries the values only between stages; other lengths take the
+// run-time form, which stages whole tiles through shared memory.
 #include "device_util.cuh"
 #include "kernels.h"
 
