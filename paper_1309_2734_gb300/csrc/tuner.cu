@@ -64,14 +64,17 @@ DirectLayout choose_layout(const DirectShape (&shapes)[2], int width, int height
 {
     DirectLayout best{};
     double best_t = 1e300;
+    int64_t best_tiles = 0;
     const int64_t slots = (int64_t)num_sms * kDirectCtasPerSm;
     for (const DirectShape &sh : shapes) {
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         int s = force_split > 0 ? force_split : choose_point_split(tiles, point_tiles, num_sms);
         if (s > point_tiles) s = (int)(point_tiles > 0 ? point_tiles : 1);
         const double t = direct_path(tiles, point_tiles > 0 ? point_tiles : 1, s, slots);
-        if (t < best_t * (1.0 - 1e-9)) {
+        // a shorter path wins; on equal paths, fewer (equal-sized) tiles: less padding computed
+        if (t < best_t * (1.0 - 1e-9) || (t <= best_t * (1.0 + 1e-9) && tiles < best_tiles)) {
             best_t = t;
+            best_tiles = tiles;
             best = DirectLayout{sh, s};
         }
     }

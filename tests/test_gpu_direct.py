@@ -102,6 +102,17 @@ def test_point_split_matches_oracle(split):
     assert oracle.nrms(got, one) < 2e-7
 
 
+@pytest.mark.parametrize("split", [1, 3, 0])
+def test_tall_cta_shape_with_point_splits(split):
+    """640 x 64 takes the tall CTA shape (128 x 64-pixel tiles, 5 of them, against 6 wide ones): the whole field
+    against the oracle, at forced and automatic point splits, and the same sums whatever the split."""
+    c = workloads.random_cloud(47, 640, 64, 3000)
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    got = _run(c, "direct_sfu", split=split)
+    _check(got, ref, c.amp)
+    assert oracle.nrms(got, _run(c, "direct_sfu", split=1)) < 2e-7
+
+
 def test_deterministic():
     c = workloads.random_cloud(45, 333, 91, 3000)
     a = _run(c, "direct_sfu")
