@@ -610,7 +610,7 @@ struct ColsBInvIO {
 // outputs stored at rows L2 c + b.  Inverse: outputs a stored at rows L2 a + b
 // only below keep_rows.  (All sizes powers of two.)
 template <bool INV>
-__global__ void fft_cols_a_kernel(float2 *__restrict__ pad, int Lx, int L1, int L2, int sw, int nz_rows,
+__global__ void __launch_bounds__(256, 4) fft_cols_a_kernel(float2 *__restrict__ pad, int Lx, int L1, int L2, int sw, int nz_rows,
                                   int keep_rows, const float2 *__restrict__ twy)
 {
     extern __shared__ float2 sm[];
@@ -649,7 +649,7 @@ __global__ void fft_cols_a_kernel(float2 *__restrict__ pad, int Lx, int L1, int 
 // result (the spectrum in scrambled order) stored.  Otherwise: forward,
 // product with spec (same order, its tile loaded together with the data),
 // inverse, conjugate twiddle: the middle of the convolution in one pass.
-__global__ void fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__restrict__ spec, int Lx, int L1, int L2,
+__global__ void __launch_bounds__(256, 4) fft_cols_b_kernel(float2 *__restrict__ pad, const float2 *__restrict__ spec, int Lx, int L1, int L2,
                                   int sw, const float2 *__restrict__ twy)
 {
     extern __shared__ float2 sm[];
