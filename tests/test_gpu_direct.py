@@ -83,6 +83,24 @@ def test_points_outside_the_hologram_and_negative_coordinates():
         _check(_run(c, form), ref, amp)
 
 
+@pytest.mark.parametrize("w,h", [(16384, 3), (3, 16384)])
+def test_longest_side(w, h):
+    """The longest side accepted (16384 pixels), points at both ends of the coordinate range (|x|, |y| = 16384,
+    so distances reach 32767 pixels): direct and split-FP16 GEMM forms against the oracle; one more pixel is
+    refused."""
+    rng = np.random.default_rng(49)
+    n = 300
+    xyz = np.stack([rng.integers(0, w, n), rng.integers(0, h, n), rng.uniform(0.3, 1.0, n)], 1).astype(np.float32)
+    xyz[:4, :2] = [[-16384, -16384], [16384, 16384], [-16384, 16384], [16384, -16384]]
+    amp = rng.uniform(0.5, 1.0, n).astype(np.float32)
+    c = workloads.Cloud(w, h, 8e-6, 532e-9, xyz, amp, "longest side")
+    ref = oracle.field(c.pitch_m, c.lambda_m, xyz, amp, w, h)
+    _check(_run(c, "direct_sfu"), ref, amp)
+    assert oracle.nrms(_run(c, "gemm_split16"), ref) <= 1e-5
+    with pytest.raises(CghError):
+        Hologram(w + (w > h), h + (h > w), c.pitch_m, c.lambda_m)
+
+
 def test_empty_cloud_writes_zeros():
     c = workloads.random_cloud(1, 70, 50, 0)
     with Hologram(70, 50, c.pitch_m, c.lambda_m, form="direct_sfu") as h:
