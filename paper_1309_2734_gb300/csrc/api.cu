@@ -431,7 +431,8 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
     {
         ProfileScope ps(ctx, "prep_points", 1);
         e = launch_prep_points(d_xyz, d_amp, (int)n, (int)n_pad, pitch, lambda, geo, aux, ctx->d_status, nullptr,
-                               ctx->stream, kAuxPiston, ext, width, height, sph_tile_cols(planes));
+                               ctx->stream, kAuxPiston, ext, width, height, sph_tile_cols(planes),
+                               sph_tile_rows(planes));
     }
     if (e != cudaSuccess) return cuda_status(e);
     {

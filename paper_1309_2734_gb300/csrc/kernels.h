@@ -20,14 +20,14 @@ constexpr int kPointTile = 256;
 // (optional, the spherical form) receives {(p / z_j)^2, z_j / (2 lambda)} as
 // float pairs {hi, hi, lo, lo}.
 enum { kAuxSecondDiff = 0, kAuxPiston = 1, kAuxZero = 2 };
-// The spherical kernel's thread tile (pixels: kSphTileRows rows of
+// The spherical kernel's thread tile (pixels: sph_tile_rows(planes) rows of
 // sph_tile_cols(planes) columns) and the bounds behind the two
 // flags prep writes into ext's signs (both checked at every pixel of the
 // width x height hologram): ext.x >= 0 when the distance remainder may be taken
 // as a quadratic about each thread tile's centre (truncation error at most
 // kSphFitTurns, range within kSphRangeTurns); ext.y >= 0 when u = r^2 / z^2
 // stays below kSeriesU.
-constexpr int kSphTileRows = 4;
+__host__ __device__ constexpr int sph_tile_rows(int planes) { return planes == 1 ? 8 : 4; }
 __host__ __device__ constexpr int sph_tile_cols(int planes) { return planes == 1 ? 8 : 4; }
 constexpr double kSphFitTurns = 2.98023223876953125e-8;   // 2^-25 turn
 constexpr double kSphRangeTurns = 0.45;
@@ -35,7 +35,7 @@ constexpr double kSeriesU = 0.05;
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
                                double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
                                cudaStream_t s, int aux_x = kAuxSecondDiff, float4 *ext = nullptr, int width = 0,
-                               int height = 0, int tile_cols = 4);
+                               int height = 0, int tile_cols = 4, int tile_rows = 4);
 
 // The plane-wave reference phase of Eq. 5, phi_r(m, n) = kx m + ky n + phi0,
 // common to every point of a launch: kx, ky in 2^-64 turn per pixel, phi0 in

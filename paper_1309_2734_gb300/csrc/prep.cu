@@ -18,7 +18,7 @@ namespace cgh {
 __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *__restrict__ amp, int n,
                                    int n_pad, double pitch, double lambda, int4 *__restrict__ geo,
                                    uint2 *__restrict__ aux, int *status, float *amp_max, int aux_x,
-                                   float4 *__restrict__ ext, int width, int height, int tile_cols)
+                                   float4 *__restrict__ ext, int width, int height, int tile_cols, int tile_rows)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
@@ -58,7 +58,7 @@ __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *_
         // the quadratic in w = u - U0 is used when its truncation error Z max|h'''| wmax^3 / 6 = zh wmax^3 / 8
         // and its range max|d1 w + d2 w^2| <= zh (umax / 2) wmax + (zh / 4) wmax^2 are within bounds.
         const double pz = pitch / (double)fz, qz = pz * pz, zh = (double)fz / (2.0 * lambda);
-        const double hx = 0.5 * (tile_cols - 1), hy = 0.5 * (kSphTileRows - 1);
+        const double hx = 0.5 * (tile_cols - 1), hy = 0.5 * (tile_rows - 1);
         const double cx = fmax(fabs((double)fx), fabs((double)(width - 1) - (double)fx)) + hx;
         const double cy = fmax(fabs((double)fy), fabs((double)(height - 1) - (double)fy)) + hy;
         const double umax = (cx * cx + cy * cy) * qz;
@@ -73,13 +73,13 @@ __global__ void prep_points_kernel(const float *__restrict__ xyz, const float *_
 
 cudaError_t launch_prep_points(const float *d_xyz, const float *d_amp, int n, int n_pad, double pitch,
                                double lambda, int4 *geo, uint2 *aux, int *status, float *amp_max,
-                               cudaStream_t s, int aux_x, float4 *ext, int width, int height, int tile_cols)
+                               cudaStream_t s, int aux_x, float4 *ext, int width, int height, int tile_cols, int tile_rows)
 {
     if (n_pad <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (n_pad + threads - 1) / threads;
     prep_points_kernel<<<blocks, threads, 0, s>>>(d_xyz, d_amp, n, n_pad, pitch, lambda, geo, aux, status,
-                                                         amp_max, aux_x, ext, width, height, tile_cols);
+                                                         amp_max, aux_x, ext, width, height, tile_cols, tile_rows);
     return cudaGetLastError();
 }
 

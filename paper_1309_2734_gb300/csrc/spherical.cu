@@ -29,7 +29,6 @@ namespace cgh {
 
 namespace {
 
-constexpr int kSphTR = kSphTileRows;                             // pixel rows per thread
 constexpr int kSphBX = 32, kSphBY = 8;                             // threads per CTA, the wide shape: 32 x 8
 constexpr int kSphTallBX = 16, kSphTallBY = 16;                    // the tall shape: 16 x 16
 constexpr float kSphK1 = 6.28318595886230469f;                   // 2 pi rounded so that 1.5 K1 is a float
@@ -149,7 +148,7 @@ __device__ __forceinline__ void sph_accumulate(uint32_t gi, float a, float &re, 
     }
 }
 
-// One point over the thread's kSphTR x TL pixels, the remainder as a quadratic about the tile's centre.
+// One point over the thread's TR x TL pixels, the remainder as a quadratic about the tile's centre.
 // With cx, cy the centre's offsets from the point (pixels; integer + 1/2 for the 4 x 4 tile), U0 its u and a
 // pixel at offsets (t, s) from the centre,
 //   u = U0 + a + b,  a = t (2 cx + t) (p / z)^2,  b = s (2 cy + s) (p / z)^2,  w = a + b,
@@ -162,16 +161,16 @@ __device__ __forceinline__ void sph_accumulate(uint32_t gi, float a, float &re, 
 // a float in [2^23, 2^24) whose low 22 mantissa bits hold round(2^22 delta) in two's complement: shifted up by
 // ten they add delta to the 32-bit fixed-point phase (resolution 2^-22 turn).  Per term: one add and one FMA
 // for the quadratic, one shift-add into the phase, and the sine as the term's only MUFU operation.
-template <int PLANES, int TL, bool SERIES>
+template <int PLANES, int TL, int TR, bool SERIES>
 __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, const float4 x, int m0, int n0,
                                                uint32_t rg, uint32_t rdx, uint32_t rdy,
-                                               float (&acc)[PLANES][kSphTR][TL])
+                                               float (&acc)[PLANES][TR][TL])
 {
     const int dxi = m0 - q.x, dyi = n0 - q.y;
     SphFresnel<TL> F = sph_fresnel<TL>(q, w.x, dxi, dyi, rg, rdx, rdy);
     const float a = __uint_as_float(w.y);
     const float qz = x.x, zh = fabsf(x.y);   // (p / z)^2, z / (2 lambda)
-    const float hx = 0.5f * (TL - 1), hy = 0.5f * (kSphTR - 1);
+    const float hx = 0.5f * (TL - 1), hy = 0.5f * (TR - 1);
     const float cx = small_int_to_float(dxi) + hx, cy = small_int_to_float(dyi) + hy;
     float d0f, d1, d2;
     if constexpr (SERIES) {
@@ -216,16 +215,16 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
         av[i] = fmaf(2.0f * t, X, (t * t) * qz);
         aq[i] = sd2 * av[i];
     }
-    float pm[kSphTR], qr[kSphTR];   // M + 2^22 (d0 + d1 b + d2 b^2) and 2^22 (d1 + 2 d2 b) per row
+    float pm[TR], qr[TR];   // M + 2^22 (d0 + d1 b + d2 b^2) and 2^22 (d1 + 2 d2 b) per row
 #pragma unroll
-    for (int r = 0; r < kSphTR; ++r) {
+    for (int r = 0; r < TR; ++r) {
         const float s = (float)r - hy;
         const float b = fmaf(2.0f * s, Y, (s * s) * qz);
         pm[r] = fmaf(fmaf(fmaf(d2, b, d1), b, d0f), kQuadScale, kRoundMagic);
         qr[r] = fmaf(2.0f * sd2, b, sd1);
     }
 #pragma unroll
-    for (int r = 0; r < kSphTR; ++r) {
+    for (int r = 0; r < TR; ++r) {
 #pragma unroll
         for (int i = 0; i < TL; ++i) {
             // a (2^22 (d1 + 2 d2 b) + 2^22 d2 a) = 2^22 (d1 a + d2 (2 a b + a^2)), added to M + 2^22 (d0 + ...)
@@ -233,7 +232,7 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
             sph_accumulate<PLANES>(F.g[i] + (__float_as_uint(y) << 10), a, acc[0][r][i],
                                    acc[PLANES - 1][r][i]);
         }
-        if (r + 1 < kSphTR) {
+        if (r + 1 < TR) {
 #pragma unroll
             for (int i = 0; i < TL; ++i) F.g[i] += F.e;
             F.e += F.D;
@@ -246,34 +245,34 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
 //   Delta = Z ((s - s0) - w / 2) = -(Z / 2) w (v + v0) / (s + s0) = -(Z / 2) w (u + v0 (1 + s)) / ((1 + s)(s + s0)),
 // s = sqrt(1 + u), v = s - 1 = u / (1 + s): no cancellation, so Delta carries ~1e-7 of itself, and d0's
 // fraction ~2^-40 turn.  Per term: a reciprocal square root, a reciprocal and the sine (three MUFU operations).
-template <int PLANES, int TL>
+template <int PLANES, int TL, int TR>
 __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, const float4 x, int m0, int n0,
                                                 uint32_t rg, uint32_t rdx, uint32_t rdy,
-                                                float (&acc)[PLANES][kSphTR][TL])
+                                                float (&acc)[PLANES][TR][TL])
 {
     const int dxi = m0 - q.x, dyi = n0 - q.y;
     SphFresnel<TL> F = sph_fresnel<TL>(q, w.x, dxi, dyi, rg, rdx, rdy);
     const float a = __uint_as_float(w.y);
     const float qz = fabsf(x.x), zh = fabsf(x.y);
-    const float hx = 0.5f * (TL - 1), hy = 0.5f * (kSphTR - 1);
+    const float hx = 0.5f * (TL - 1), hy = 0.5f * (TR - 1);
     const float cx = small_int_to_float(dxi) + hx, cy = small_int_to_float(dyi) + hy;
     float v0, s0, rs0;
     const float d0f = sph_d0_frac(cx, cy, x, v0, s0, rs0);
     const float U0 = fmaf(cx, cx, cy * cy) * qz;
     const float X = cx * qz, Y = cy * qz;
-    float av[TL], bv[kSphTR];
+    float av[TL], bv[TR];
 #pragma unroll
     for (int i = 0; i < TL; ++i) {
         const float t = (float)i - hx;
         av[i] = fmaf(2.0f * t, X, (t * t) * qz);
     }
 #pragma unroll
-    for (int r = 0; r < kSphTR; ++r) {
+    for (int r = 0; r < TR; ++r) {
         const float s = (float)r - hy;
         bv[r] = fmaf(2.0f * s, Y, (s * s) * qz);
     }
 #pragma unroll
-    for (int r = 0; r < kSphTR; ++r) {
+    for (int r = 0; r < TR; ++r) {
 #pragma unroll
         for (int i = 0; i < TL; ++i) {
             const float wv = av[i] + bv[r];
@@ -286,7 +285,7 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
             const float y = fmaf(df, kQuadScale, kRoundMagic);                 // into the phase as above
             sph_accumulate<PLANES>(F.g[i] + (__float_as_uint(y) << 10), a, acc[0][r][i], acc[PLANES - 1][r][i]);
         }
-        if (r + 1 < kSphTR) {
+        if (r + 1 < TR) {
 #pragma unroll
             for (int i = 0; i < TL; ++i) F.g[i] += F.e;
             F.e += F.D;
@@ -294,34 +293,32 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
     }
 }
 
-// blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).  A thread owns kSphTR rows of
-// sph_tile_cols(PLANES) pixels: 8 columns for the amplitude hologram, 4 for the complex wave (its two
-// accumulator planes would not fit the registers of two CTAs per SM at 8).
+// blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).  A thread owns
+// sph_tile_rows(PLANES) rows of sph_tile_cols(PLANES) pixels: 8 x 8 for the amplitude hologram, 4 x 4 for the
+// complex wave.  Each point tile's partial sums stay in registers; the running totals live in shared memory
+// (index-major, so a warp's accesses are consecutive words), which leaves the registers of two CTAs per SM to the
+// partial sums.
 template <int PLANES, int BX, int BY>
 __global__ void __launch_bounds__(BX *BY, 2)
     spherical_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, const float4 *__restrict__ ext,
                      int n_ptiles, int width, int height, int tiles_x, int split, float *__restrict__ out,
                      long long slice_stride, long long im_offset, const PhaseRef ref)
 {
-    constexpr int TL = sph_tile_cols(PLANES);
+    constexpr int TL = sph_tile_cols(PLANES), TR = sph_tile_rows(PLANES), T = BX * BY;
     __shared__ int4 s_geo[kPointTile];
     __shared__ uint2 s_aux[kPointTile];
     __shared__ float4 s_ext[kPointTile];
+    extern __shared__ float s_tot[];   // [PLANES * TR * TL][T]
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
     const int m0 = (tile % tiles_x) * (BX * TL) + (tid % BX) * TL;
-    const int n0 = (tile / tiles_x) * (BY * kSphTR) + (tid / BX) * kSphTR;
+    const int n0 = (tile / tiles_x) * (BY * TR) + (tid / BX) * TR;
     const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
     const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
     const uint32_t rg = ref_turn(ref, m0, n0), rdx = ref_step(ref.kx), rdy = ref_step(ref.ky);
 
-    float tot[PLANES][kSphTR][TL];
 #pragma unroll
-    for (int c = 0; c < PLANES; ++c)
-#pragma unroll
-        for (int r = 0; r < kSphTR; ++r)
-#pragma unroll
-            for (int i = 0; i < TL; ++i) tot[c][r][i] = 0.0f;
+    for (int k = 0; k < PLANES * TR * TL; ++k) s_tot[k * T + tid] = 0.0f;
 
     for (int t = t_begin; t < t_end; ++t) {
         const long long j = (long long)t * kPointTile + tid;
@@ -330,41 +327,42 @@ __global__ void __launch_bounds__(BX *BY, 2)
         s_aux[tid] = aux[j];
         s_ext[tid] = ext[j];
         __syncthreads();
-        float part[PLANES][kSphTR][TL];
+        float part[PLANES][TR][TL];
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-            for (int r = 0; r < kSphTR; ++r)
+            for (int r = 0; r < TR; ++r)
 #pragma unroll
                 for (int i = 0; i < TL; ++i) part[c][r][i] = 0.0f;
 #pragma unroll 1
         for (int p = 0; p < kPointTile; ++p) {
             const float4 x = s_ext[p];   // the same point, so the same branch, in every thread
             if (x.x < 0.0f)
-                sph_point_terms<PLANES, TL>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
+                sph_point_terms<PLANES, TL, TR>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
             else if (x.y >= 0.0f)
-                sph_point_quad<PLANES, TL, true>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
+                sph_point_quad<PLANES, TL, TR, true>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
             else
-                sph_point_quad<PLANES, TL, false>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
+                sph_point_quad<PLANES, TL, TR, false>(s_geo[p], s_aux[p], x, m0, n0, rg, rdx, rdy, part);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-            for (int r = 0; r < kSphTR; ++r)
+            for (int r = 0; r < TR; ++r)
 #pragma unroll
-                for (int i = 0; i < TL; ++i) tot[c][r][i] += part[c][r][i];
+                for (int i = 0; i < TL; ++i) s_tot[((c * TR + r) * TL + i) * T + tid] += part[c][r][i];
     }
 
     float *dst = out + (long long)blockIdx.y * slice_stride;
 #pragma unroll
     for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-        for (int r = 0; r < kSphTR; ++r) {
+        for (int r = 0; r < TR; ++r) {
             const int n = n0 + r;
             if (n >= height) continue;
 #pragma unroll
             for (int i = 0; i < TL; ++i)
-                if (m0 + i < width) dst[(long long)c * im_offset + (long long)n * width + m0 + i] = tot[c][r][i];
+                if (m0 + i < width)
+                    dst[(long long)c * im_offset + (long long)n * width + m0 + i] = s_tot[((c * TR + r) * TL + i) * T + tid];
         }
 }
 
@@ -372,8 +370,9 @@ __global__ void __launch_bounds__(BX *BY, 2)
 
 DirectShape spherical_shape(int planes, bool tall)
 {
-    return tall ? DirectShape{kSphTallBX * sph_tile_cols(planes), kSphTallBY * kSphTR, kPointTile, kSphTallBX}
-                : DirectShape{kSphBX * sph_tile_cols(planes), kSphBY * kSphTR, kPointTile, kSphBX};
+    return tall ? DirectShape{kSphTallBX * sph_tile_cols(planes), kSphTallBY * sph_tile_rows(planes), kPointTile,
+                              kSphTallBX}
+                : DirectShape{kSphBX * sph_tile_cols(planes), kSphBY * sph_tile_rows(planes), kPointTile, kSphBX};
 }
 
 namespace {
@@ -382,8 +381,16 @@ void spherical_as(dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, 
                   int width, int height, int tiles_x, int split, float *out, long long ss, long long im,
                   const PhaseRef &ref)
 {
-    spherical_kernel<PLANES, BX, BY><<<grid, BX * BY, 0, s>>>(geo, aux, ext, n_ptiles, width, height, tiles_x, split,
-                                                              out, ss, im, ref);
+    constexpr size_t tot_bytes = (size_t)PLANES * sph_tile_rows(PLANES) * sph_tile_cols(PLANES) * BX * BY * sizeof(float);
+    static bool configured = false;   // the running totals exceed the default 48 KB of dynamic shared memory
+    if (!configured) {
+        if (cudaFuncSetAttribute(spherical_kernel<PLANES, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tot_bytes) != cudaSuccess)
+            return;
+        configured = true;
+    }
+    spherical_kernel<PLANES, BX, BY><<<grid, BX * BY, tot_bytes, s>>>(geo, aux, ext, n_ptiles, width, height, tiles_x,
+                                                                      split, out, ss, im, ref);
 }
 }  // namespace
 

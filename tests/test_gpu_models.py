@@ -123,13 +123,13 @@ def test_spherical_closed_form_branch():
     assert oracle.nrms(got, want) <= 1e-5
 
 
-def _remainder_forms(c, tile_cols=8):
+def _remainder_forms(c, tile_cols=8, tile_rows=8):
     """Which remainder form the point preparation selects per point for the amplitude hologram (thread tiles of
-    4 rows x 8 columns; the same bounds, in FP64): the quadratic about each thread tile's centre or the per-term
+    8 rows x 8 columns; the same bounds, in FP64): the quadratic about each thread tile's centre or the per-term
     form, each with the series (u < 0.05) or the closed form."""
     x, y, z = (c.xyz[:, k].astype(np.float64) for k in range(3))
     qz, zh = (c.pitch_m / z) ** 2, z / (2 * c.lambda_m)
-    hx, hy = (tile_cols - 1) / 2, 1.5
+    hx, hy = (tile_cols - 1) / 2, (tile_rows - 1) / 2
     cx = np.maximum(np.abs(x), np.abs(c.width - 1 - x)) + hx
     cy = np.maximum(np.abs(y), np.abs(c.height - 1 - y)) + hy
     umax, wmax = (cx * cx + cy * cy) * qz, (2 * hx * cx + hx * hx + 2 * hy * cy + hy * hy) * qz
@@ -141,17 +141,17 @@ def _remainder_forms(c, tile_cols=8):
 
 @pytest.mark.parametrize("wave", [False, True])
 @pytest.mark.parametrize("w,h,n,z,forms", [
-    (3840, 2160, 2000, (0.08, 0.15), ("quad_series", "quad_closed", "term_closed")),
+    (8192, 2048, 2000, (0.15, 0.3), ("quad_series", "quad_closed", "term_closed")),
     (1920, 1080, 2000, (0.05, 0.1), ("quad_series", "term_series", "term_closed"))])
 def test_spherical_every_remainder_form(w, h, n, z, forms, wave):
     """Close points on wide holograms: each point's remainder takes the form its bounds allow (the amplitude
-    hologram's 8-column thread tiles; the complex wave's 4-column tiles shift the mix); sampled pixels (corners
+    hologram's 8 x 8 thread tiles; the complex wave's 4 x 4 tiles shift the mix); sampled pixels (corners
     included) against the oracle."""
     c = workloads.random_cloud(813 + w, w, h, n, z_range=z)
     mix = _remainder_forms(c)
     assert all(mix[f] >= 50 for f in forms), mix
     if wave:
-        assert sum(v > 0 for v in _remainder_forms(c, tile_cols=4).values()) >= 3
+        assert sum(v > 0 for v in _remainder_forms(c, tile_cols=4, tile_rows=4).values()) >= 3
     rng = np.random.default_rng(814)
     cols = np.concatenate([rng.integers(0, w, 400), [0, w - 1, 0, w - 1]])
     rows = np.concatenate([rng.integers(0, h, 400), [0, 0, h - 1, h - 1]])
