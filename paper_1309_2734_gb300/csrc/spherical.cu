@@ -8,7 +8,7 @@
 // Eq. 2 with its piston: that part is exact in 64-bit fixed point (C_j and the
 // piston from the point preparation), walked over the thread's pixels with the
 // recurrence of Eqs. 6-8 like the direct kernel.  The remainder delta is split
-// at the centre of each thread's 4 x 4 pixel tile, delta = d0 + (delta - d0):
+// at the centre of each thread's pixel tile, delta = d0 + (delta - d0):
 //  - d0 = Z h(U0) can reach hundreds of turns for close points on wide
 //    holograms; its fraction is taken in double-float arithmetic (float pairs)
 //    once per point and tile, or from the float series while |d0| <= 1/2;
