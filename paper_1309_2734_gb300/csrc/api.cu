@@ -411,8 +411,8 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
 {
     const int64_t n_pad = padded_points(n);
     const int64_t n_ptiles = n_pad / kPointTile;
-    const DirectShape shapes[2] = {spherical_shape(planes, false), spherical_shape(planes, true)};
-    const DirectLayout lay = choose_layout(shapes, width, height, n_ptiles, ctx->num_sms, ctx->point_split);
+    const DirectShape shapes[3] = {spherical_shape(planes, 0), spherical_shape(planes, 1), spherical_shape(planes, 2)};
+    const DirectLayout lay = choose_layout(shapes, 3, width, height, n_ptiles, ctx->num_sms, ctx->point_split);
     const DirectShape sh = lay.shape;
     const int split = lay.split;
     const int64_t plane = (int64_t)width * height;

@@ -66,7 +66,8 @@ __device__ __forceinline__ uint32_t ref_step(unsigned long long k)
 struct DirectShape {
     int tile_w, tile_h;   // pixels covered by one CTA
     int threads;          // threads per CTA
-    int bx;               // threads per CTA row: 32 (the wide shape) or 16 (the tall shape)
+    int bx;               // threads per CTA row: 32 (the wide shape) or 16 (the tall and short shapes)
+    int per_sm = 2;       // CTAs resident per SM
 };
 // The CTA shapes of the direct kernels (256 threads, 8 columns of pixels per
 // thread): wide = 32 x 8 threads, tall = 16 x 16 threads.
@@ -88,7 +89,8 @@ cudaError_t launch_direct_wave(const DirectShape &sh, const int4 *geo, const uin
 // Points prepared with the piston and ext.  planes = 1: the amplitude
 // hologram (Eq. 5, middle line) at out; planes = 2: the complex wave, real part
 // at out and imaginary part at out + im_offset.  Point chunk s at out + s * slice_stride.
-DirectShape spherical_shape(int planes, bool tall = false);
+// variant 0: 32 x 8 threads (wide), 1: 16 x 16 (tall), 2: 16 x 8 (short, four CTAs per SM).
+DirectShape spherical_shape(int planes, int variant = 0);
 cudaError_t launch_spherical(const DirectShape &sh, const int4 *geo, const uint2 *aux, const float4 *ext, int n_pad,
                              int width, int height, int split, int planes, float *out, int64_t slice_stride,
                              int64_t im_offset, const PhaseRef &ref, cudaStream_t s);

@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kSphBX = 32, kSphBY = 8;                             // threads per CTA, the wide shape: 32 x 8
 constexpr int kSphTallBX = 16, kSphTallBY = 16;                    // the tall shape: 16 x 16
+constexpr int kSphShortBX = 16, kSphShortBY = 8;                   // the short shape: 16 x 8, four CTAs per SM
 constexpr float kSphK1 = 6.28318595886230469f;                   // 2 pi rounded so that 1.5 K1 is a float
 constexpr float kSphK0 = 9.42477893829345703f;                   // 1.5 K1
 constexpr uint32_t kSphBias = (1u << 30) + 256u;                 // a quarter turn, and rounding to 23 bits
@@ -38,8 +39,7 @@ constexpr float kRoundMagic = 12582912.0f;                       // 1.5 2^23: x 
 constexpr float kQuadScale = 4194304.0f;                         // 2^22: turns to the quadratic's units
 constexpr float kSeriesD0Max = 0.5f;                             // |d0| (turns) the float series may carry
 
-static_assert(kSphBX * kSphBY == kPointTile && kSphTallBX * kSphTallBY == kPointTile,
-              "one point per thread in each tile load");
+static_assert(kPointTile % (kSphShortBX * kSphShortBY) == 0, "whole points per thread in each tile load");
 
 // Exact small integer to float without a conversion instruction (|v| < 2^22).
 __device__ __forceinline__ float small_int_to_float(int v)
@@ -299,7 +299,7 @@ __device__ __forceinline__ void sph_point_terms(const int4 q, const uint2 w, con
 // (index-major, so a warp's accesses are consecutive words), which leaves the registers of two CTAs per SM to the
 // partial sums.
 template <int PLANES, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY, 2)
+__global__ void __launch_bounds__(BX *BY, 512 / (BX * BY))
     spherical_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, const float4 *__restrict__ ext,
                      int n_ptiles, int width, int height, int tiles_x, int split, float *__restrict__ out,
                      long long slice_stride, long long im_offset, const PhaseRef ref)
@@ -321,11 +321,13 @@ __global__ void __launch_bounds__(BX *BY, 2)
     for (int k = 0; k < PLANES * TR * TL; ++k) s_tot[k * T + tid] = 0.0f;
 
     for (int t = t_begin; t < t_end; ++t) {
-        const long long j = (long long)t * kPointTile + tid;
         __syncthreads();   // the previous tile is consumed
-        s_geo[tid] = geo[j];
-        s_aux[tid] = aux[j];
-        s_ext[tid] = ext[j];
+        for (int k = tid; k < kPointTile; k += T) {
+            const long long j = (long long)t * kPointTile + k;
+            s_geo[k] = geo[j];
+            s_aux[k] = aux[j];
+            s_ext[k] = ext[j];
+        }
         __syncthreads();
         float part[PLANES][TR][TL];
 #pragma unroll
@@ -368,11 +370,12 @@ __global__ void __launch_bounds__(BX *BY, 2)
 
 }  // namespace
 
-DirectShape spherical_shape(int planes, bool tall)
+DirectShape spherical_shape(int planes, int variant)
 {
-    return tall ? DirectShape{kSphTallBX * sph_tile_cols(planes), kSphTallBY * sph_tile_rows(planes), kPointTile,
-                              kSphTallBX}
-                : DirectShape{kSphBX * sph_tile_cols(planes), kSphBY * sph_tile_rows(planes), kPointTile, kSphBX};
+    const int tl = sph_tile_cols(planes), tr = sph_tile_rows(planes);
+    if (variant == 1) return DirectShape{kSphTallBX * tl, kSphTallBY * tr, kSphTallBX * kSphTallBY, kSphTallBX, 2};
+    if (variant == 2) return DirectShape{kSphShortBX * tl, kSphShortBY * tr, kSphShortBX * kSphShortBY, kSphShortBX, 4};
+    return DirectShape{kSphBX * tl, kSphBY * tr, kSphBX * kSphBY, kSphBX, 2};
 }
 
 namespace {
@@ -404,19 +407,20 @@ cudaError_t launch_spherical(const DirectShape &sh, const int4 *geo, const uint2
     if (split < 1) split = 1;
     dim3 grid(tiles_x * tiles_y, split);
     const long long ss = (long long)slice_stride;
-    const bool tall = sh.bx == kSphTallBX;
-    if (planes == 2 && tall)
-        spherical_as<2, kSphTallBX, kSphTallBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out,
-                                                ss, (long long)im_offset, ref);
-    else if (planes == 2)
-        spherical_as<2, kSphBX, kSphBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out, ss,
-                                        (long long)im_offset, ref);
-    else if (tall)
-        spherical_as<1, kSphTallBX, kSphTallBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out,
-                                                ss, 0, ref);
-    else
-        spherical_as<1, kSphBX, kSphBY>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out, ss, 0,
-                                        ref);
+    const long long im = planes == 2 ? (long long)im_offset : 0;
+    const int variant = sh.bx == kSphBX ? 0 : (sh.threads == kSphTallBX * kSphTallBY ? 1 : 2);
+#define CGH_SPH(P, BXV, BYV)                                                                                     \
+    spherical_as<P, BXV, BYV>(grid, s, geo, aux, ext, n_ptiles, width, height, tiles_x, split, out, ss, im, ref)
+    if (planes == 2) {
+        if (variant == 1) CGH_SPH(2, kSphTallBX, kSphTallBY);
+        else if (variant == 2) CGH_SPH(2, kSphShortBX, kSphShortBY);
+        else CGH_SPH(2, kSphBX, kSphBY);
+    } else {
+        if (variant == 1) CGH_SPH(1, kSphTallBX, kSphTallBY);
+        else if (variant == 2) CGH_SPH(1, kSphShortBX, kSphShortBY);
+        else CGH_SPH(1, kSphBX, kSphBY);
+    }
+#undef CGH_SPH
     return cudaGetLastError();
 }
 

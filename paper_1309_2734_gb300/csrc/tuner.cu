@@ -43,10 +43,9 @@ static double direct_path(int64_t pixel_tiles, int64_t point_tiles, int64_t s, i
     return (double)rounds * (double)longest * (1.0 + 0.002 * (double)(s - 1));
 }
 
-int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms)
+static int split_for(int64_t pixel_tiles, int64_t point_tiles, int64_t slots)
 {
     if (pixel_tiles <= 0 || point_tiles <= 1) return 1;
-    const int64_t slots = (int64_t)num_sms * kDirectCtasPerSm;
     int best = 1;
     double best_t = direct_path(pixel_tiles, point_tiles, 1, slots);
     for (int64_t s = 2; s <= 64 && s * 2 <= point_tiles; ++s) {
@@ -59,22 +58,30 @@ int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms)
     return best;
 }
 
-DirectLayout choose_layout(const DirectShape (&shapes)[2], int width, int height, int64_t point_tiles, int num_sms,
-                           int force_split)
+int choose_point_split(int64_t pixel_tiles, int64_t point_tiles, int num_sms)
+{
+    return split_for(pixel_tiles, point_tiles, (int64_t)num_sms * kDirectCtasPerSm);
+}
+
+DirectLayout choose_layout(const DirectShape *shapes, int n_shapes, int width, int height, int64_t point_tiles,
+                           int num_sms, int force_split)
 {
     DirectLayout best{};
-    double best_t = 1e300;
-    int64_t best_tiles = 0;
-    const int64_t slots = (int64_t)num_sms * kDirectCtasPerSm;
-    for (const DirectShape &sh : shapes) {
+    double best_t = 1e300, best_area = 0.0;
+    for (int k = 0; k < n_shapes; ++k) {
+        const DirectShape &sh = shapes[k];
+        const int64_t slots = (int64_t)num_sms * sh.per_sm;
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
-        int s = force_split > 0 ? force_split : choose_point_split(tiles, point_tiles, num_sms);
+        int s = force_split > 0 ? force_split : split_for(tiles, point_tiles, slots);
         if (s > point_tiles) s = (int)(point_tiles > 0 ? point_tiles : 1);
+        // in point-tile steps of one CTA: the shapes keep the same warps per SM (threads x CTAs per SM) and the
+        // same pixels per thread, so a step takes the same time whatever the shape
         const double t = direct_path(tiles, point_tiles > 0 ? point_tiles : 1, s, slots);
-        // a shorter path wins; on equal paths, fewer (equal-sized) tiles: less padding computed
-        if (t < best_t * (1.0 - 1e-9) || (t <= best_t * (1.0 + 1e-9) && tiles < best_tiles)) {
+        const double area = (double)tiles * sh.tile_w * sh.tile_h;
+        // a shorter path wins; on equal paths, fewer padded pixels computed
+        if (t < best_t * (1.0 - 1e-9) || (t <= best_t * (1.0 + 1e-9) && area < best_area)) {
             best_t = t;
-            best_tiles = tiles;
+            best_area = area;
             best = DirectLayout{sh, s};
         }
     }
@@ -86,7 +93,7 @@ DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t poin
 {
     const DirectShape shapes[2] = {wave ? direct_wave_shape(false) : direct_shape(false),
                                    wave ? direct_wave_shape(true) : direct_shape(true)};
-    return choose_layout(shapes, width, height, point_tiles, num_sms, force_split);
+    return choose_layout(shapes, 2, width, height, point_tiles, num_sms, force_split);
 }
 
 int choose_gemm_bn(int width)

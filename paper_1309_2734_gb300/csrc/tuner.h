@@ -21,9 +21,9 @@ struct DirectLayout {
 };
 DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t point_tiles, int num_sms,
                                   int force_split);
-// The same choice between any two CTA shapes of equal work per point tile.
-DirectLayout choose_layout(const DirectShape (&shapes)[2], int width, int height, int64_t point_tiles, int num_sms,
-                           int force_split);
+// The same choice among n_shapes CTA shapes (each with its threads and CTAs per SM).
+DirectLayout choose_layout(const DirectShape *shapes, int n_shapes, int width, int height, int64_t point_tiles,
+                           int num_sms, int force_split);
 
 // GEMM orientation, tile width and K splits with the shortest critical path
 // (rounds of units over ctas CTAs, times the work of one unit); force_* > 0
