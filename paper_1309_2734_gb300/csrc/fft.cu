@@ -714,19 +714,40 @@ __global__ void __launch_bounds__(256, 4) fft_cols_b_kernel(float2 *__restrict__
     }
 }
 
-// The chirp on the Ly x Lx grid: h(k, l) = pre exp(i 2 pi C (k'^2 + l'^2) / 2^64), k' = k or k - Ly (signed offset).
-__global__ void chirp_grid_kernel(float2 *__restrict__ h, int Ly, int Lx, unsigned long long C, double pre_re,
-                                  double pre_im)
+// The chirp on the Ly x Lx grid, h(k, l) = pre exp(i 2 pi C (k'^2 + l'^2) / 2^64) (k' = k or k - Ly, the signed
+// offset; likewise l'), as the product of its separable factors: a(l) = exp(i 2 pi C l'^2 / 2^64) for the thread's
+// kChirpCols columns, computed once, and pre a(k) for each of the block's kChirpRows rows -- a complex product per
+// entry in place of a sine and cosine (the turns of the two factors add to the joint turn within 2^-31; each factor
+// is an accurate single-precision sine and cosine, the product adds about two units of rounding).
+constexpr int kChirpCols = 8, kChirpRows = 64;
+
+__device__ __forceinline__ float2 chirp_factor(unsigned long long C, int k, int L)
 {
-    const int k = blockIdx.y;
-    const int kk = k <= Ly / 2 ? k : k - Ly;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Lx; l += gridDim.x * blockDim.x) {
-        const int ll = l <= Lx / 2 ? l : l - Lx;
-        const unsigned long long r2 = (unsigned long long)((long long)kk * kk + (long long)ll * ll);
-        const uint32_t t = (uint32_t)((C * r2) >> 32);
-        float s, cc;   // accurate single-precision sine and cosine of 2 pi t (FP64 is slow on this part)
-        sincospif((float)(int)t * (1.0f / 2147483648.0f), &s, &cc);
-        h[(long long)k * Lx + l] = make_float2((float)(pre_re * cc - pre_im * s), (float)(pre_re * s + pre_im * cc));
+    const long long kk = k <= L / 2 ? k : k - L;
+    const uint32_t t = (uint32_t)((C * (unsigned long long)(kk * kk)) >> 32);
+    float s, c;
+    sincospif((float)(int)t * (1.0f / 2147483648.0f), &s, &c);
+    return make_float2(c, s);
+}
+
+__global__ void chirp_grid_kernel(float2 *__restrict__ h, int Ly, int Lx, unsigned long long C, float pre_re,
+                                  float pre_im)
+{
+    const int l0 = blockIdx.x * blockDim.x * kChirpCols + threadIdx.x;
+    float2 a[kChirpCols];
+#pragma unroll
+    for (int j = 0; j < kChirpCols; ++j) {
+        const int l = l0 + j * (int)blockDim.x;
+        a[j] = l < Lx ? chirp_factor(C, l, Lx) : make_float2(0.0f, 0.0f);
+    }
+    const int k1 = min(Ly, (int)(blockIdx.y + 1) * kChirpRows);
+    for (int k = blockIdx.y * kChirpRows; k < k1; ++k) {
+        const float2 b = cmul(chirp_factor(C, k, Ly), make_float2(pre_re, pre_im));
+#pragma unroll
+        for (int j = 0; j < kChirpCols; ++j) {
+            const int l = l0 + j * (int)blockDim.x;
+            if (l < Lx) h[(long long)k * Lx + l] = cmul(b, a[j]);
+        }
     }
 }
 
@@ -821,7 +842,8 @@ static cudaError_t configure_cols(const FftGrid &g)
 cudaError_t launch_fft_chirp_spectrum(const FftGrid &g, float2 *spec, unsigned long long C, double pre_re,
                                       double pre_im, const float2 *twx, const float2 *twy, cudaStream_t s)
 {
-    chirp_grid_kernel<<<dim3((g.Lx + 255) / 256, g.Ly), 256, 0, s>>>(spec, g.Ly, g.Lx, C, pre_re, pre_im);
+    chirp_grid_kernel<<<dim3((g.Lx + 256 * kChirpCols - 1) / (256 * kChirpCols), (g.Ly + kChirpRows - 1) / kChirpRows),
+                        256, 0, s>>>(spec, g.Ly, g.Lx, C, (float)pre_re, (float)pre_im);
     const int nseq = rows_per_cta(g.Lx);
     const size_t rs = rows_smem(g.Lx, nseq);
     cudaError_t e = configure_rows(rs);
