@@ -29,22 +29,40 @@ int grid_for(long long n)
     return (int)(b > 1048576 ? 1048576 : (b > 0 ? b : 1));
 }
 
-__global__ void chirp_kernel(float2 *__restrict__ h, int H, int W, unsigned long long C, double pre_re,
-                             double pre_im)
+// The chirp on the 2H x 2W grid, h(k, l) = pre exp(i 2 pi C (k'^2 + l'^2) / 2^64) with the signed offsets k', l',
+// as pre a(k) a(l), a(k) = exp(i 2 pi C k'^2 / 2^64): a thread takes its kChirpCols column factors once and, for each
+// of its block's kChirpRows rows, one row factor and a complex product per entry (each factor an accurate
+// single-precision sine and cosine of its fixed-point turn; the two turns sum to the joint turn within 2^-31).
+constexpr int kChirpCols = 8, kChirpRows = 64;
+
+__device__ __forceinline__ float2 chirp_factor(unsigned long long C, int k, int half)
 {
-    const long long total = 4ll * H * W;
-    const int W2 = 2 * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / W2), l = (int)(i % W2);
-        const int kk = k < H ? k : k - 2 * H;
-        const int ll = l < W ? l : l - W2;
-        const unsigned long long r2 = (unsigned long long)((long long)kk * kk + (long long)ll * ll);   // < 2^31
-        const uint32_t t = (uint32_t)((C * r2) >> 32);              // turn, 2^-32 units (exact but the last bit)
-        const float a = (float)(int)t * (1.0f / 2147483648.0f);     // [-1, 1): twice the signed turn
-        float s, c;
-        sincospif(a, &s, &c);                                       // exp(i 2 pi t), accurate single precision
-        h[i] = make_float2((float)(pre_re * c - pre_im * s), (float)(pre_re * s + pre_im * c));
+    const long long kk = k < half ? k : k - 2 * half;
+    const uint32_t t = (uint32_t)((C * (unsigned long long)(kk * kk)) >> 32);   // turn, 2^-32 units
+    float s, c;
+    sincospif((float)(int)t * (1.0f / 2147483648.0f), &s, &c);   // [-1, 1): twice the signed turn
+    return make_float2(c, s);
+}
+
+__global__ void chirp_kernel(float2 *__restrict__ h, int H, int W, unsigned long long C, float pre_re, float pre_im)
+{
+    const int W2 = 2 * W, l0 = blockIdx.x * kThreads * kChirpCols + threadIdx.x;
+    float2 a[kChirpCols];
+#pragma unroll
+    for (int j = 0; j < kChirpCols; ++j) {
+        const int l = l0 + j * kThreads;
+        a[j] = l < W2 ? chirp_factor(C, l, W) : make_float2(0.0f, 0.0f);
+    }
+    const int k1 = min(2 * H, (int)(blockIdx.y + 1) * kChirpRows);
+    for (int k = blockIdx.y * kChirpRows; k < k1; ++k) {
+        const float2 r = chirp_factor(C, k, H);
+        const float2 b = make_float2(pre_re * r.x - pre_im * r.y, pre_re * r.y + pre_im * r.x);
+#pragma unroll
+        for (int j = 0; j < kChirpCols; ++j) {
+            const int l = l0 + j * kThreads;
+            if (l < W2)
+                h[(long long)k * W2 + l] = make_float2(b.x * a[j].x - b.y * a[j].y, b.x * a[j].y + b.y * a[j].x);
+        }
     }
 }
 
@@ -117,7 +135,8 @@ bool fft_exec(void *plan, float2 *data, bool inverse, cudaStream_t s)
 
 cudaError_t launch_chirp(float2 *h, int H, int W, unsigned long long C, double pre_re, double pre_im, cudaStream_t s)
 {
-    chirp_kernel<<<grid_for(4ll * H * W), kThreads, 0, s>>>(h, H, W, C, pre_re, pre_im);
+    chirp_kernel<<<dim3((2 * W + kThreads * kChirpCols - 1) / (kThreads * kChirpCols), (2 * H + kChirpRows - 1) / kChirpRows),
+                   kThreads, 0, s>>>(h, H, W, C, (float)pre_re, (float)pre_im);
     return cudaGetLastError();
 }
 

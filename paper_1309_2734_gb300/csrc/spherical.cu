@@ -159,8 +159,10 @@ __device__ __forceinline__ void sph_accumulate(uint32_t gi, float a, float &re, 
 // otherwise d0 comes from sph_d0_frac.  With d0 reduced to [-1/2, 1/2] turn and the quadratic's variation over
 // the tile below kSphRangeTurns (the point preparation checks both bounds), M + 2^22 delta with M = 1.5 2^23 is
 // a float in [2^23, 2^24) whose low 22 mantissa bits hold round(2^22 delta) in two's complement: shifted up by
-// ten they add delta to the 32-bit fixed-point phase (resolution 2^-22 turn).  Per term: one add and one FMA
-// for the quadratic, one shift-add into the phase, and the sine as the term's only MUFU operation.
+// ten they add delta to the 32-bit fixed-point phase (resolution 2^-22 turn).  The column constant d2 a^2 is
+// converted so once per point and column and joins the column's phase; the rest, d0 + d1 w + d2 (b^2 + 2 a b),
+// stays below 1 turn in magnitude since |b^2 + 2 a b| <= (|a| + |b|)^2 (each part rounded to 2^-22 turn).  Per
+// term: one FMA for the quadratic, one shift-add into the phase, and the sine as the term's only MUFU operation.
 template <int PLANES, int TL, int TR, bool SERIES>
 __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, const float4 x, int m0, int n0,
                                                uint32_t rg, uint32_t rdx, uint32_t rdy,
@@ -208,12 +210,12 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
     }
     const float sd1 = kQuadScale * d1, sd2 = kQuadScale * d2;
     const float X = cx * qz, Y = cy * qz;
-    float av[TL], aq[TL];   // a and 2^22 d2 a per column
+    float av[TL];   // a per column; d2 a^2, a column constant, joins the column's fixed-point phase
 #pragma unroll
     for (int i = 0; i < TL; ++i) {
         const float t = (float)i - hx;
         av[i] = fmaf(2.0f * t, X, (t * t) * qz);
-        aq[i] = sd2 * av[i];
+        F.g[i] += __float_as_uint(fmaf(sd2 * av[i], av[i], kRoundMagic)) << 10;
     }
     float pm[TR], qr[TR];   // M + 2^22 (d0 + d1 b + d2 b^2) and 2^22 (d1 + 2 d2 b) per row
 #pragma unroll
@@ -227,8 +229,8 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
     for (int r = 0; r < TR; ++r) {
 #pragma unroll
         for (int i = 0; i < TL; ++i) {
-            // a (2^22 (d1 + 2 d2 b) + 2^22 d2 a) = 2^22 (d1 a + d2 (2 a b + a^2)), added to M + 2^22 (d0 + ...)
-            const float y = fmaf(av[i], qr[r] + aq[i], pm[r]);
+            // M + 2^22 (d0 + d1 (a + b) + d2 (b^2 + 2 a b)): the quadratic but its column constant d2 a^2
+            const float y = fmaf(av[i], qr[r], pm[r]);
             sph_accumulate<PLANES>(F.g[i] + (__float_as_uint(y) << 10), a, acc[0][r][i],
                                    acc[PLANES - 1][r][i]);
         }
