@@ -13,7 +13,13 @@
 //            order serves a convolution, so the chirp's spectrum is kept in
 //            that order, and forward pass B, the product and inverse pass B
 //            are ONE pass (the middle kernel), twiddles e^{-2 pi i c b / Ly}
-//            included; inverse pass A writes only the rows < H;
+//            included; inverse pass A writes only the rows < H.  Columns of
+//            256 .. 2048 points instead take ONE pass over strips of 8 to 32
+//            whole columns in shared memory (forward transform of the rows
+//            < H, product with the spectrum in natural order, inverse, rows
+//            < H stored), so the plane crosses HBM once each way; longer
+//            columns do not fit at that strip width (64-byte row segments),
+//            and narrower strips measured slower than the four-step passes;
 //   rows     inverse Lx-point FFT of those H rows, only the first W columns
 //            written, into the output planes.
 // Every transform is a Stockham autosort FFT in shared memory (the
@@ -130,7 +136,16 @@ __device__ __forceinline__ void dft_regs(float2 *v)
     }
 }
 
-enum { kLayoutRows = 0, kLayoutCols = 1 };
+enum { kLayoutRows = 0, kLayoutCols = 1, kLayoutStrip = 2 };
+
+// The strip layout (whole columns of a narrow strip, 2^LQ columns): element e of column q at
+// ((e + e / 16) << LQ) + q -- the columns interleaved, one gap per 16 elements against the bank conflicts of a
+// radix-16 stage's strided stores.
+template <int LQ>
+__device__ __forceinline__ int strip_addr(int e, int q)
+{
+    return ((e + (e >> 4)) << LQ) + q;
+}
 
 __device__ __forceinline__ int ilog2(int v)
 {
@@ -363,14 +378,16 @@ __device__ __forceinline__ void stockham_stage_io(float2 *s, const float2 *tw, c
     constexpr int M = 1 << LM, NSEQ = 1 << LQ, T = (M << LQ) / 16;
     constexpr int LSPAN = LM - LR, SPAN = 1 << LSPAN;
     constexpr int STRIDE = NSEQ + 1;   // columns layout
-    static_assert(LAYOUT == kLayoutCols || LSPAN >= 5, "row spans of at least 32 values");
+    static_assert(LAYOUT != kLayoutRows || LSPAN >= 5, "row spans of at least 32 values");
+    static_assert(LAYOUT != kLayoutStrip || (LSPAN >= 4 && (LS == 0 ? R == 16 : LS >= 4)),
+                  "strip spans of at least 16 values, radix 16 from the start");
     float2 v[16];
     int jj[PER], qq[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int w = threadIdx.x + u * T;
         int q, j;
-        if (LAYOUT == kLayoutCols) {
+        if (LAYOUT != kLayoutRows) {
             q = w & (NSEQ - 1);
             j = w >> LQ;
         } else {
@@ -382,6 +399,10 @@ __device__ __forceinline__ void stockham_stage_io(float2 *s, const float2 *tw, c
         if (FIRST) {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[u * R + r] = io.load(q, j + r * SPAN);
+        } else if (LAYOUT == kLayoutStrip) {   // SPAN is a multiple of 16: the gaps advance by SPAN / 16 per r
+            const int b0 = strip_addr<LQ>(j, q);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u * R + r] = s[b0 + r * ((SPAN + (SPAN >> 4)) << LQ)];
         } else if (LAYOUT == kLayoutCols) {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[u * R + r] = s[(j + r * SPAN) * STRIDE + q];
@@ -407,6 +428,11 @@ __device__ __forceinline__ void stockham_stage_io(float2 *s, const float2 *tw, c
         if (LAST) {   // LS + LR = LM: base = j, the outputs are j + r 2^LS = j + r SPAN
 #pragma unroll
             for (int r = 0; r < R; ++r) io.store(q, j + r * SPAN, v[u * R + r]);
+        } else if (LAYOUT == kLayoutStrip) {   // LS = 0 (base = 16 j, r < 16) or a multiple of 4
+            const int b0 = strip_addr<LQ>(base, q);
+            constexpr int step = LS == 0 ? (1 << LQ) : (((1 << LS) + (1 << (LS >= 4 ? LS - 4 : 0))) << LQ);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[b0 + r * step] = v[u * R + r];
         } else if (LAYOUT == kLayoutCols) {
 #pragma unroll
             for (int r = 0; r < R; ++r) s[(base + (r << LS)) * STRIDE + q] = v[u * R + r];
@@ -714,6 +740,56 @@ __global__ void __launch_bounds__(256, 4) fft_cols_b_kernel(float2 *__restrict__
     }
 }
 
+// The fused column pass's global side: sequence q is column x0 + q, element e is row e (natural order).  Loads
+// read the rows below nz_rows (the rest are zero).  Stores: with spec, the product with the spectrum into shared
+// memory (the input of the inverse transform); without, the rows below keep_rows into pad.
+template <int LQ>
+struct StripIO {
+    float2 *pad;
+    const float2 *spec;
+    float2 *s;
+    int Lx, x0, nz_rows, keep_rows;
+    __device__ __forceinline__ float2 load(int q, int e) const
+    {
+        return e < nz_rows ? pad[e * Lx + x0 + q] : make_float2(0.0f, 0.0f);   // offsets below 2^27
+    }
+    __device__ __forceinline__ void store(int q, int e, float2 v) const
+    {
+        const int g = e * Lx + x0 + q;
+        if (spec != nullptr) s[strip_addr<LQ>(e, q)] = cmul(v, spec[g]);
+        else if (e < keep_rows) pad[g] = v;
+    }
+};
+
+// The columns in one pass, where a whole column fits in shared memory: per strip of 2^LQ columns, the forward
+// Ly-point transform (Ly = 2^LM) of the rows below nz_rows, the product with the spectrum (natural order) as the
+// last forward stage stores, the inverse transform, and the rows below keep_rows stored -- the plane crosses
+// HBM once each way instead of three times.  spec == nullptr: the forward transform alone, every row below
+// keep_rows stored (the chirp's spectrum).  2^(LM + LQ - 4) threads, each holding 16 values per stage.
+template <int LM, int LQ>
+__global__ void __launch_bounds__(1 << (LM + LQ - 4), 1024 >> (LM + LQ - 4))
+    fft_cols_full_kernel(float2 *__restrict__ pad, const float2 *__restrict__ spec, int Lx, int nz_rows,
+                         int keep_rows, const float2 *__restrict__ twy)
+{
+    extern __shared__ float2 sm[];
+    constexpr int T = 1 << (LM + LQ - 4);
+    const int x0 = blockIdx.x << LQ;
+    const StripIO<LQ> io{pad, nullptr, sm, Lx, x0, nz_rows, keep_rows};
+    if (spec == nullptr) {
+        fft_io<false, kLayoutStrip, LM, LQ, true, true, 0>(sm, twy, io);
+        return;
+    }
+    fft_io<false, kLayoutStrip, LM, LQ, true, false, 0>(sm, twy, io);   // natural order in shared memory
+#pragma unroll 4
+    for (int i = threadIdx.x; i < (1 << (LM + LQ)); i += T) {
+        const int q = i & ((1 << LQ) - 1), e = i >> LQ;
+        float2 &v = sm[strip_addr<LQ>(e, q)];
+        v = cmul(v, spec[e * Lx + x0 + q]);
+    }
+    __syncthreads();
+    fft_io<true, kLayoutStrip, LM, LQ, false, true, 0>(sm, twy, io);
+}
+
 // The chirp on the Ly x Lx grid, h(k, l) = pre exp(i 2 pi C (k'^2 + l'^2) / 2^64) (k' = k or k - Ly, the signed
 // offset; likewise l'), as the product of its separable factors: a(l) = exp(i 2 pi C l'^2 / 2^64) for the thread's
 // kChirpCols columns, computed once, and pre a(k) for each of the block's kChirpRows rows -- a complex product per
@@ -839,6 +915,52 @@ static cudaError_t configure_cols(const FftGrid &g)
     return e;
 }
 
+// The fused column pass's strip width (log2) for the grid, or -1 where the four-step passes serve: columns of
+// 256 .. 2048 points, strips of 8 or more columns (64-byte row segments); 512 or 1024 threads per strip.
+static int cols_full_lq(const FftGrid &g)
+{
+    int lq = -1;
+    switch (g.Ly) {
+    case 2048: lq = 3; break;   // 1024 threads
+    case 1024: lq = 3; break;   // 512 threads
+    case 512: lq = 4; break;    // 512 threads
+    case 256: lq = 5; break;    // 512 threads
+    default: break;
+    }
+    return lq >= 0 && g.Lx >= (1 << lq) ? lq : -1;
+}
+
+template <int LM, int LQ>
+static cudaError_t launch_cols_full_as(const FftGrid &g, float2 *pad, const float2 *spec, int nz_rows, int keep_rows,
+                                       const float2 *twy, cudaStream_t s)
+{
+    constexpr int M = 1 << LM;
+    constexpr size_t bytes = (size_t)((M + M / 16) << LQ) * sizeof(float2);
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(fft_cols_full_kernel<LM, LQ>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    fft_cols_full_kernel<LM, LQ><<<g.Lx >> LQ, 1 << (LM + LQ - 4), bytes, s>>>(pad, spec, g.Lx, nz_rows, keep_rows, twy);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_cols_full(const FftGrid &g, float2 *pad, const float2 *spec, int nz_rows, int keep_rows,
+                                    const float2 *twy, cudaStream_t s)
+{
+    const int lq = cols_full_lq(g);
+#define CGH_COLS_FULL(LMV, LQV) \
+    if (g.Ly == (1 << LMV) && lq == LQV) return launch_cols_full_as<LMV, LQV>(g, pad, spec, nz_rows, keep_rows, twy, s);
+    CGH_COLS_FULL(11, 3)
+    CGH_COLS_FULL(10, 3)
+    CGH_COLS_FULL(9, 4)
+    CGH_COLS_FULL(8, 5)
+#undef CGH_COLS_FULL
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_fft_chirp_spectrum(const FftGrid &g, float2 *spec, unsigned long long C, double pre_re,
                                       double pre_im, const float2 *twx, const float2 *twy, cudaStream_t s)
 {
@@ -850,6 +972,7 @@ cudaError_t launch_fft_chirp_spectrum(const FftGrid &g, float2 *spec, unsigned l
     if (e != cudaSuccess) return e;
     fft_rows_kernel<kRowInPlace><<<(g.Ly + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(
         nullptr, spec, nullptr, 0, 0, g.Lx, g.Ly, nseq, twx);
+    if (cols_full_lq(g) >= 0) return launch_cols_full(g, spec, nullptr, g.Ly, g.Ly, twy, s);
     const int swa = strip_width(g.Lx, g.L1), swb = strip_width(g.Lx, g.L2);
     e = configure_cols(g);
     if (e != cudaSuccess) return e;
@@ -873,6 +996,13 @@ cudaError_t launch_fft_convolve(const FftGrid &g, const float *in, int H, int W,
     else
         fft_rows_kernel<kRowPadRows><<<(H + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(nullptr, pad, nullptr,
                                                                                               H, W, g.Lx, H, nseq, twx);
+    if (cols_full_lq(g) >= 0) {
+        e = launch_cols_full(g, pad, spec, H, H, twy, s);
+        if (e != cudaSuccess) return e;
+        fft_rows_kernel<kRowCrop><<<(H + nseq - 1) / nseq, threads_for(nseq * g.Lx), rs, s>>>(nullptr, pad, out, H, W,
+                                                                                           g.Lx, H, nseq, twx);
+        return cudaGetLastError();
+    }
     const int swa = strip_width(g.Lx, g.L1), swb = strip_width(g.Lx, g.L2);
     const size_t sa = cols_a_smem(g, swa), sb = cols_b_smem(g, swb, true);
     e = configure_cols(g);
