@@ -45,6 +45,21 @@ def test_fresnel_vs_oracle(w, h, z):
     assert _nrms_c(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("w,h,z", [(40, 100, 0.03), (3, 100, 0.03), (70, 250, -0.05), (160, 400, 0.08),
+                                   (9, 700, 0.1), (300, 700, 0.12)])
+def test_fresnel_fused_column_forms(w, h, z):
+    """Padded grids of 256, 512, 1024 and 2048 rows, whose columns take the one-pass strip transform (strips of
+    32, 16, 8 and 8 columns), ragged widths, and a plane too narrow for its strip (3 x 100: the four-step passes),
+    against the oracle; the same context then alternates distances (the spectrum, in natural order, rebuilt)."""
+    u = workloads.complex_plane(930 + w + h, w, h)
+    uc = u[0].astype(np.float64) + 1j * u[1]
+    with Hologram(w, h, 8e-6, 532e-9) as hol:
+        for zz in (z, 1.5 * z, z):
+            got = _cplx(hol.fresnel(torch.from_numpy(u).cuda(), zz))
+            hol.sync()
+            assert _nrms_c(got, oracle.fresnel(uc, 8e-6, 532e-9, zz)) <= TOL
+
+
 def test_fresnel_wide_plane_uses_the_library_fft():
     """A plane wider than the own FFT's longest transform (2W - 1 > 16384): the cuFFT path, same result."""
     u = workloads.complex_plane(909, 8200, 3)
