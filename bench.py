@@ -196,6 +196,8 @@ def run_reference(args):
     from paper_1309_2734_gb300 import workloads
     import oracle
     cloud = workloads.WORKLOADS[args.workload]()
+    if world > 1:   # the launcher caps each rank at one OpenMP thread; rank 0 is the only one at work here
+        oracle.set_threads(len(os.sched_getaffinity(0)))
     cores = oracle.threads()
     W, H = cloud.width, cloud.height
     # size one step so that the whole --steps/--warmup run takes about two minutes of host work
