@@ -217,24 +217,37 @@ __device__ __forceinline__ void sph_point_quad(const int4 q, const uint2 w, cons
         av[i] = fmaf(2.0f * t, X, (t * t) * qz);
         F.g[i] += __float_as_uint(fmaf(sd2 * av[i], av[i], kRoundMagic)) << 10;
     }
-    float pm[TR], qr[TR];   // M + 2^22 (d0 + d1 b + d2 b^2) and 2^22 (d1 + 2 d2 b) per row
+    // Per row: M + 2^22 (row part) and 2^22 (d1 + 2 d2 b), the row part being d0 + d1 b + d2 b^2.  On tiles
+    // eight columns wide the row part also takes the row's Fresnel phase relative to the first row (fixed
+    // point, erow; the sum reduced to [-1/2, 1/2) turn), which saves the columns' phases a step per row;
+    // narrower tiles step the columns' phases.
+    constexpr bool kRowFold = TL >= 8;
+    float pm[TR], qr[TR];
+    uint32_t erow = 0u;
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
         const float s = (float)r - hy;
         const float b = fmaf(2.0f * s, Y, (s * s) * qz);
         pm[r] = fmaf(fmaf(fmaf(d2, b, d1), b, d0f), kQuadScale, kRoundMagic);
         qr[r] = fmaf(2.0f * sd2, b, sd1);
+        if constexpr (kRowFold) {
+            const uint32_t row = erow + (__float_as_uint(pm[r]) << 10);   // mod 1 turn, 2^-32 units
+            pm[r] = fmaf((float)(int)row, 1.0f / 1024.0f, kRoundMagic);
+            erow += F.e;
+            F.e += F.D;
+        }
     }
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
 #pragma unroll
         for (int i = 0; i < TL; ++i) {
-            // M + 2^22 (d0 + d1 (a + b) + d2 (b^2 + 2 a b)): the quadratic but its column constant d2 a^2
+            // M + 2^22 (row part + d1 a + 2 d2 a b): the quadratic but its column constant d2 a^2, which the
+            // column's phase holds
             const float y = fmaf(av[i], qr[r], pm[r]);
             sph_accumulate<PLANES>(F.g[i] + (__float_as_uint(y) << 10), a, acc[0][r][i],
                                    acc[PLANES - 1][r][i]);
         }
-        if (r + 1 < TR) {
+        if (!kRowFold && r + 1 < TR) {
 #pragma unroll
             for (int i = 0; i < TL; ++i) F.g[i] += F.e;
             F.e += F.D;
