@@ -93,11 +93,28 @@ __device__ __forceinline__ PixelRef pixel_ref(const PhaseRef &r, int m0, int n0)
     return PixelRef{ref_turn(r, m0, n0), ref_step(r.kx), ref_step(r.ky)};
 }
 
-// Adds one point's terms of the complex object wave (Eq. 2, restricted form) to
-// a thread's TL x TR block: Re += A cos(2 pi t) exactly as the SFU amplitude form,
-// Im += A sin(2 pi t) = A sin(v) with v = K1 (f2 - 1.5) from the turn advanced by a
-// half (f2 - 1 = t + 1/2), the same symmetric argument grid, so the MUFU's odd
-// error again averages out.
+// e^{i 2 pi t} of a fixed-point turn t from the hardware sine on the symmetric argument grid of the SFU
+// amplitude form: cos(2 pi t) as there, sin(2 pi t) = sin(v) with v = K1 (f2 - 1.5) from the turn advanced by a
+// half (f2 - 1 = t + 1/2), so the MUFU's odd error averages out in both parts.
+__device__ __forceinline__ float2 cis_sfu(uint32_t t)
+{
+    const float f = __uint_as_float(__funnelshift_r(t + kSfuBias, 0x7fu, 9));
+    const float f2 = __uint_as_float(__funnelshift_r(t + kSfuBias + (1u << 30), 0x7fu, 9));
+    return make_float2(-__sinf(fmaf(f, kK1, -kK0)), __sinf(fmaf(f2, kK1, -kK0)));
+}
+
+__device__ __forceinline__ float2 cmul_f(float2 x, float2 y)
+{
+    return make_float2(fmaf(x.x, y.x, -x.y * y.y), fmaf(x.x, y.y, x.y * y.x));
+}
+
+// Adds one point's terms of the complex object wave (Eq. 2, restricted form) to a thread's TL x TR block.
+// Along a row the phase is quadratic in the column (Eqs. 6-8): first difference d + i D at column i, the same
+// on every row.  So e^{i 2 pi t} is taken from the hardware only at each row's first column, and for the
+// column steps w_0 = e^{i 2 pi d} and v = e^{i 2 pi D}; then w_i = w_(i-1) v and the row walks by
+// z_i = z_(i-1) w_(i-1): TR + 2 sines and cosines per point instead of TL TR, the rest complex products on
+// the FMA pipe.  The products' rounding (chains of at most 2 TL - 3 of them, restarted at every point and row)
+// stays within a few 10^-7 of the term.
 template <int TL, int TR, bool EXTRA>
 __device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
                                                  float (&pre)[TR][TL], float (&pim)[TR][TL])
@@ -111,33 +128,32 @@ __device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, in
     const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
     uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
     uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
-    uint32_t g0 = c0, D = w.x;
+    uint32_t g = c0, D = w.x;
     if constexpr (EXTRA) {   // piston (aux.x) and reference; 2 C formed from C
         d += pr.dx;
         e += pr.dy;
-        g0 += w.x + pr.g;
+        g += w.x + pr.g;
         D = __funnelshift_l(clo, chi, 1);
     }
     const float a = __uint_as_float(w.y);
-    uint32_t g[TL];
-    g[0] = g0 + kSfuBias;
+    const float2 v = cis_sfu(D);
+    float2 st[TL - 1];   // e^{i 2 pi (d + i D)}: the step from column i to i + 1
+    st[0] = cis_sfu(d);
 #pragma unroll
-    for (int i = 1; i < TL; ++i) {
-        g[i] = g[i - 1] + d;
-        d += D;
-    }
+    for (int i = 1; i < TL - 1; ++i) st[i] = cmul_f(st[i - 1], v);
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
+        float2 z = cis_sfu(g);
+        pre[r][0] = fmaf(a, z.x, pre[r][0]);
+        pim[r][0] = fmaf(a, z.y, pim[r][0]);
 #pragma unroll
-        for (int i = 0; i < TL; ++i) {
-            const float f = __uint_as_float(__funnelshift_r(g[i], 0x7fu, 9));
-            const float f2 = __uint_as_float(__funnelshift_r(g[i] + (1u << 30), 0x7fu, 9));
-            pre[r][i] = fmaf(-a, __sinf(fmaf(f, kK1, -kK0)), pre[r][i]);   // A cos(2 pi t)
-            pim[r][i] = fmaf(a, __sinf(fmaf(f2, kK1, -kK0)), pim[r][i]);   // A sin(2 pi t)
+        for (int i = 1; i < TL; ++i) {
+            z = cmul_f(z, st[i - 1]);
+            pre[r][i] = fmaf(a, z.x, pre[r][i]);
+            pim[r][i] = fmaf(a, z.y, pim[r][i]);
         }
         if (r + 1 < TR) {
-#pragma unroll
-            for (int i = 0; i < TL; ++i) g[i] += e;
+            g += e;
             e += D;
         }
     }
