@@ -108,16 +108,24 @@ __device__ __forceinline__ float2 cmul_f(float2 x, float2 y)
     return make_float2(fmaf(x.x, y.x, -x.y * y.y), fmaf(x.x, y.y, x.y * y.x));
 }
 
+// The point's second difference D (2^-32 turn): v = e^{i 2 pi D}, the same for every pixel, is computed once per
+// point and CTA when its tile arrives.
+template <bool EXTRA>
+__device__ __forceinline__ uint32_t wave_second_difference(const int4 q, const uint2 w)
+{
+    return EXTRA ? __funnelshift_l((uint32_t)q.w, (uint32_t)q.z, 1) : w.x;   // 2 C with the piston, else aux.x
+}
+
 // Adds one point's terms of the complex object wave (Eq. 2, restricted form) to a thread's TL x TR block.
 // Along a row the phase is quadratic in the column (Eqs. 6-8): first difference d + i D at column i, the same
 // on every row.  So e^{i 2 pi t} is taken from the hardware only at each row's first column, and for the
 // column steps w_0 = e^{i 2 pi d} and v = e^{i 2 pi D}; then w_i = w_(i-1) v and the row walks by
-// z_i = z_(i-1) w_(i-1): TR + 2 sines and cosines per point instead of TL TR, the rest complex products on
-// the FMA pipe.  The products' rounding (chains of at most 2 TL - 3 of them, restarted at every point and row)
-// stays within a few 10^-7 of the term.
+// z_i = z_(i-1) w_(i-1): TR + 1 sines and cosines per point and thread (v once per point and CTA) instead of
+// TL TR, the rest complex products on the FMA pipe.  The products' rounding (chains of at most 2 TL - 3 of them,
+// restarted at every point and row) stays within a few 10^-7 of the term.
 template <int TL, int TR, bool EXTRA>
-__device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
-                                                 float (&pre)[TR][TL], float (&pim)[TR][TL])
+__device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, const float2 v, int m0, int n0,
+                                                 const PixelRef &pr, float (&pre)[TR][TL], float (&pim)[TR][TL])
 {
     const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
     const uint32_t dx = (uint32_t)(m0 - q.x);
@@ -128,15 +136,14 @@ __device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, in
     const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
     uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
     uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
-    uint32_t g = c0, D = w.x;
-    if constexpr (EXTRA) {   // piston (aux.x) and reference; 2 C formed from C
+    uint32_t g = c0;
+    const uint32_t D = wave_second_difference<EXTRA>(q, w);
+    if constexpr (EXTRA) {   // piston (aux.x) and reference
         d += pr.dx;
         e += pr.dy;
         g += w.x + pr.g;
-        D = __funnelshift_l(clo, chi, 1);
     }
     const float a = __uint_as_float(w.y);
-    const float2 v = cis_sfu(D);
     float2 st[TL - 1];   // e^{i 2 pi (d + i D)}: the step from column i to i + 1
     st[0] = cis_sfu(d);
 #pragma unroll
@@ -273,8 +280,12 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         const int4 *sg = s_geo[st];
         const uint2 *sa = s_aux[st];
         if constexpr (PLANES == 2) {
+            __shared__ float2 s_rot[T];   // e^{i 2 pi D} of the tile's points, one sine pair each per CTA
+            for (int p = tid; p < T; p += BX * BY) s_rot[p] = cis_sfu(wave_second_difference<EXTRA>(sg[p], sa[p]));
+            __syncthreads();
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0], part[PLANES - 1]);
+            for (int p = 0; p < T; ++p)
+                point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], s_rot[p], m0, n0, pr, part[0], part[PLANES - 1]);
         } else if constexpr (SFU) {
 #pragma unroll 1
             for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalSfu, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
