@@ -108,12 +108,20 @@ __device__ __forceinline__ float2 cmul_f(float2 x, float2 y)
     return make_float2(fmaf(x.x, y.x, -x.y * y.y), fmaf(x.x, y.y, x.y * y.x));
 }
 
-// The point's second difference D (2^-32 turn): v = e^{i 2 pi D}, the same for every pixel, is computed once per
-// point and CTA when its tile arrives.
+// The point's second difference D (2^-32 turn).  v = e^{i 2 pi D}, the same for every pixel, is computed once per
+// point and CTA when its tile arrives, with the accurate single-precision sine and cosine: the term at column i
+// carries v's error i (i - 1) / 2 times over (point_terms_wave).
 template <bool EXTRA>
 __device__ __forceinline__ uint32_t wave_second_difference(const int4 q, const uint2 w)
 {
     return EXTRA ? __funnelshift_l((uint32_t)q.w, (uint32_t)q.z, 1) : w.x;   // 2 C with the piston, else aux.x
+}
+
+__device__ __forceinline__ float2 wave_rotation(uint32_t D)
+{
+    float s, c;
+    sincospif((float)(int)D * (1.0f / 2147483648.0f), &s, &c);   // [-1, 1): twice the signed turn
+    return make_float2(c, s);
 }
 
 // Adds one point's terms of the complex object wave (Eq. 2, restricted form) to a thread's TL x TR block.
@@ -121,8 +129,10 @@ __device__ __forceinline__ uint32_t wave_second_difference(const int4 q, const u
 // on every row.  So e^{i 2 pi t} is taken from the hardware only at each row's first column, and for the
 // column steps w_0 = e^{i 2 pi d} and v = e^{i 2 pi D}; then w_i = w_(i-1) v and the row walks by
 // z_i = z_(i-1) w_(i-1): TR + 1 sines and cosines per point and thread (v once per point and CTA) instead of
-// TL TR, the rest complex products on the FMA pipe.  The products' rounding (chains of at most 2 TL - 3 of them,
-// restarted at every point and row) stays within a few 10^-7 of the term.
+// TL TR, the rest complex products on the FMA pipe.  The term at column i carries the row anchor's error, i times
+// w_0's and i (i - 1) / 2 times v's, and the chains restart at every point and row: about 1.3 10^-6 of the field
+// (NRMS) against 4 10^-7 with two hardware sines per term (2.6 10^-6 with v from the hardware; 7 10^-7, 15 %
+// slower, with the chains restarted at every half row).
 template <int TL, int TR, bool EXTRA>
 __device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, const float2 v, int m0, int n0,
                                                  const PixelRef &pr, float (&pre)[TR][TL], float (&pim)[TR][TL])
@@ -280,8 +290,8 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         const int4 *sg = s_geo[st];
         const uint2 *sa = s_aux[st];
         if constexpr (PLANES == 2) {
-            __shared__ float2 s_rot[T];   // e^{i 2 pi D} of the tile's points, one sine pair each per CTA
-            for (int p = tid; p < T; p += BX * BY) s_rot[p] = cis_sfu(wave_second_difference<EXTRA>(sg[p], sa[p]));
+            __shared__ float2 s_rot[T];   // e^{i 2 pi D} of the tile's points, once each per CTA
+            for (int p = tid; p < T; p += BX * BY) s_rot[p] = wave_rotation(wave_second_difference<EXTRA>(sg[p], sa[p]));
             __syncthreads();
 #pragma unroll 1
             for (int p = 0; p < T; ++p)

@@ -95,6 +95,17 @@ def test_paper_workload_kinoform_display_size_sampled():
             _check_kinoform(q[r:r + 1], got[r:r + 1], ref)
 
 
+def test_wave_many_points_sampled_rows():
+    """10^5 points on a 1920x1080 hologram: the direct wave's row walks by complex rotation (restarted at every
+    point and row) leave no error that grows with the number of points; sampled rows at both edges and the middle."""
+    c = workloads.random_cloud(313, 1920, 1080, 100000)
+    rows = (0, 541, 1079)
+    got, _ = _wave(c, "direct_sfu")
+    for r in rows:
+        ref = oracle.wave(c.pitch_m, c.lambda_m, c.xyz, c.amp, 1920, 1080, window=(r, 0, 1, 1920))
+        _check_wave(got[r:r + 1], ref, 1e-5)
+
+
 def test_kinoform_quantiser_same_field():
     """The GPU phase rule on given float fields against the oracle's on the same values."""
     rng = np.random.default_rng(9)
