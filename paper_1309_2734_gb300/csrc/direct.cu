@@ -223,13 +223,16 @@ __device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0,
 // tiles this CTA consumed before (stage and mbarrier parity carry across units).
 // PLANES = 1: the amplitude hologram; PLANES = 2: the complex object wave, real
 // part at dst and imaginary part at dst + im_offset (SFU form only).
-template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1, bool EXTRA = false>
+// SMEM_TOT: the running totals live in shared memory (s_tot, index-major: entry (c, r, i) of thread tid at
+// ((c TR + r) TL + i) BX BY + tid, so a warp's accesses are consecutive words) instead of registers, which leaves
+// the registers to the point tile's partial sums of a taller thread block.
+template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1, bool EXTRA = false, bool SMEM_TOT = false>
 __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const uint2 *__restrict__ aux,
                                             int t_begin, int t_end, int tile_m0, int tile_n0, int width,
                                             int height, float *__restrict__ dst, bool vec, int4 (*s_geo)[kPointTile],
                                             uint2 (*s_aux)[kPointTile], uint64_t *s_bar, uint32_t &kg, int *status,
                                             unsigned long long timeout_ns, int drop = -1, long long im_offset = 0,
-                                            const PhaseRef &ref = PhaseRef())
+                                            const PhaseRef &ref = PhaseRef(), float *s_tot = nullptr)
 {
     constexpr int T = kPointTile;
     constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
@@ -253,13 +256,18 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         if (nt > 1) issue(1);
     }
 
+    constexpr int NT = BX * BY;
+    auto tidx = [&](int c, int r, int i) { return ((c * TR + r) * TL + i) * NT + tid; };
     float tot[PLANES][TR][TL];
 #pragma unroll
     for (int c = 0; c < PLANES; ++c)
 #pragma unroll
         for (int r = 0; r < TR; ++r)
 #pragma unroll
-            for (int i = 0; i < TL; ++i) tot[c][r][i] = 0.0f;
+            for (int i = 0; i < TL; ++i) {
+                if constexpr (SMEM_TOT) s_tot[tidx(c, r, i)] = 0.0f;
+                else tot[c][r][i] = 0.0f;
+            }
 
     bool ok = true;
     for (int k = 0; k < nt; ++k) {
@@ -308,13 +316,24 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
 #pragma unroll
             for (int r = 0; r < TR; ++r)
 #pragma unroll
-                for (int i = 0; i < TL; ++i) tot[c][r][i] += part[c][r][i];
+                for (int i = 0; i < TL; ++i) {
+                    if constexpr (SMEM_TOT) s_tot[tidx(c, r, i)] += part[c][r][i];
+                    else tot[c][r][i] += part[c][r][i];
+                }
 
         __syncthreads();   // every thread is done with stage st
         if (tid == 0 && k + 2 < nt) issue(k + 2);
     }
     kg += (uint32_t)nt;
     if (!ok) return false;
+    if constexpr (SMEM_TOT) {
+#pragma unroll
+        for (int c = 0; c < PLANES; ++c)
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int i = 0; i < TL; ++i) tot[c][r][i] = s_tot[tidx(c, r, i)];
+    }
 
 #pragma unroll
     for (int c = 0; c < PLANES; ++c)
@@ -382,15 +401,16 @@ __global__ void __launch_bounds__(BX *BY, 2)
     __shared__ alignas(128) int4 s_geo[2][kPointTile];
     __shared__ alignas(128) uint2 s_aux[2][kPointTile];
     __shared__ alignas(8) uint64_t s_bar[2];
+    extern __shared__ float s_tot[];   // the running totals: 2 TR TL floats per thread
     init_point_barriers<BX, BY>(s_bar);
     const int tile = blockIdx.x;
     const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
     const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
     uint32_t kg = 0;
-    direct_unit<TL, TR, BX, BY, true, 2, EXTRA>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
-                                         (tile / tiles_x) * (BY * TR), width, height,
-                                         out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg,
-                                         status, timeout_ns, -1, im_offset, ref);
+    direct_unit<TL, TR, BX, BY, true, 2, EXTRA, true>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
+                                               (tile / tiles_x) * (BY * TR), width, height,
+                                               out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar,
+                                               kg, status, timeout_ns, -1, im_offset, ref, s_tot);
 }
 
 // A batch: every CTA walks its list of {job, pixel tile} units over all points of the job.
@@ -508,18 +528,28 @@ int direct_ctas_per_sm()
 namespace cgh {
 
 namespace {
-constexpr int kWaveTL = 8, kWaveTR = 2;   // two planes of accumulators: half the rows per thread
+constexpr int kWaveTL = 8, kWaveTR = 4;   // two planes of partial sums in registers, the totals in shared memory
 
 template <int BX, int BY>
 void wave_as(bool extra, dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_ptiles, int width,
              int height, int tiles_x, int split, float *out, long long ss, long long im, bool vec, int *status,
              uint64_t timeout_ns, const PhaseRef &ref)
 {
+    constexpr size_t tot_bytes = (size_t)2 * kWaveTR * kWaveTL * BX * BY * sizeof(float);
+    static bool configured = false;   // the running totals exceed the default 48 KB of dynamic shared memory
+    if (!configured) {
+        if (cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes) != cudaSuccess ||
+            cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes) != cudaSuccess)
+            return;
+        configured = true;
+    }
     if (extra)
-        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true><<<grid, BX * BY, 0, s>>>(
+        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true><<<grid, BX * BY, tot_bytes, s>>>(
             geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, im, vec, status, timeout_ns, ref);
     else
-        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false><<<grid, BX * BY, 0, s>>>(
+        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false><<<grid, BX * BY, tot_bytes, s>>>(
             geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, im, vec, status, timeout_ns, ref);
 }
 }  // namespace
