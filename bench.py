@@ -179,6 +179,11 @@ def nrms_of_forms(samples, cloud, rows_ref):
         if wc is cloud:
             out[key] = oracle.nrms(field[r0:r0 + rows], ref)
             continue
+        if wc.evals <= 2e8:   # small clouds: the whole field
+            if wc.name not in cache:
+                cache[wc.name] = oracle.field(wc.pitch_m, wc.lambda_m, wc.xyz, wc.amp, wc.width, wc.height)
+            out[key] = oracle.nrms(field, cache[wc.name])
+            continue
         if wc.name not in cache:
             rng = np.random.default_rng(20260)
             cols = rng.integers(0, wc.width, 256)
@@ -187,6 +192,49 @@ def nrms_of_forms(samples, cloud, rows_ref):
         cols, rws, pix = cache[wc.name]
         out[key] = oracle.nrms(field[rws, cols], pix)
     return out
+
+
+def _r3(v):
+    """v rounded to three significant digits (None stays None)."""
+    if v is None:
+        return None
+    return float(f"{v:.3g}")
+
+
+def compact_summary(forms, large, vbatch, cloud_name):
+    """The figures the comparison rests on, short enough for the end of the printed line: per form and
+    workload the time, throughput, roofline fraction, DRAM traffic and NRMS against the FP64 oracle; the
+    GEMM-versus-direct comparison at 1920x1080; the large case and the batch."""
+    short = {"direct-256x256-n1024": "256x256n1024", "direct-1920x1080-n10000": "1080p-n10k",
+             "gemm-1920x1080-n50000": "1080p-n50k"}
+    fs = {"cols": ["ms", "Gevals/s", "kernel roofline frac", "hologram tensor frac", "nrms vs oracle",
+                   "ncu DRAM bytes/launch"]}
+    for key, rec in forms.items():
+        form, wl = key.split("@")
+        roof = rec.get("roofline") or {}
+        fs[f"{form}@{short.get(wl, wl)}"] = [
+            _r3(rec["ms_per_hologram"]), _r3(rec["gevals_per_s"]), _r3(roof.get("frac")),
+            _r3(rec.get("e2e_tensor_frac")), _r3(rec.get("nrms_vs_oracle")), roof.get("traffic")]
+    # GEMM against direct at 1920x1080: the fastest form within each accuracy class
+    versus = {}
+    for wl in ("direct-1920x1080-n10000", "gemm-1920x1080-n50000"):
+        d = forms.get(f"direct_sfu@{wl}")
+        for g, cls in (("gemm_split16", "1e-5"), ("gemm_f16", "2e-3"), ("gemm_bf16", "1e-2")):
+            r = forms.get(f"{g}@{wl}")
+            if d is not None and r is not None:
+                versus[f"{short[wl]} {g} (NRMS<={cls})"] = [
+                    _r3(r["ms_per_hologram"]), _r3(d["ms_per_hologram"]),
+                    _r3(d["ms_per_hologram"] / r["ms_per_hologram"]),
+                    _r3(r.get("nrms_vs_oracle")), _r3(d.get("nrms_vs_oracle"))]
+    if versus:
+        versus["cols"] = ["gemm ms", "direct_sfu ms", "speedup", "gemm nrms", "direct nrms"]
+    lg = {k: {"ms": _r3(v.get("ms_per_hologram")), "frac": _r3((v.get("roofline") or {}).get("frac")),
+              "nrms": _r3(v.get("nrms_vs_oracle"))} for k, v in large.items()}
+    vb = {k: {"ms": _r3(v.get("ms_per_batch")), "holo_s": _r3(v.get("holograms_per_s")),
+              "tc_frac": _r3(v.get("tensor_frac")), "nrms": _r3(v.get("nrms_vs_oracle")),
+              "kernel_ms": {kk: _r3(vv) for kk, vv in (v.get("kernel_ms") or {}).items()}}
+          for k, v in vbatch.items() if k.startswith("nrms_")}
+    return {"forms": fs, "gemm_vs_direct": versus, "layered_4096": lg, "video_batch_64": vb}
 
 
 def run_reference(args):
@@ -309,50 +357,67 @@ def run_ours(args):
     # GEMM forms also on the 1920x1080, 50,000-point cloud they are meant for
     forms = {}
     samples = {}
-    gemm_cloud = workloads.display_gemm() if any(f.startswith("gemm") for f in args.compare) else None
-    gemm_dev = None
-    for extra in args.compare:
-        for wc in ([cloud] + ([gemm_cloud] if extra.startswith("gemm") else [])):
-            if wc is cloud:
-                cx, ca, hh = xyz, amp, h
-            else:
-                if gemm_dev is None:
-                    gemm_dev = (torch.from_numpy(wc.xyz).cuda(), torch.from_numpy(wc.amp).cuda(),
-                                Hologram(wc.width, wc.height, wc.pitch_m, wc.lambda_m, stream=stream))
-                cx, ca, hh = gemm_dev
-            hh.set_form(extra)
-            o = torch.empty((wc.height, wc.width), dtype=torch.float32, device="cuda")
-            for _ in range(2):
-                hh.point_cloud(cx, ca, o)
-            hh.sync()
-            hh.profile(True)
-            hh.profile_read(reset=True)
-            reps = max(3, args.steps // 4)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                hh.point_cloud(cx, ca, o)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            hh.sync()
-            kp = hh.profile_read(reset=True)
-            hh.profile(False)
-            ms = e0.elapsed_time(e1) / reps
-            rec = {"gevals_per_s": wc.evals / ms / 1e6, "ms_per_hologram": ms,
-                   "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in kp.items()}}
-            if extra.startswith("gemm") and "gemm_tcgen05" in kp:
-                passes = 3 if extra == "gemm_split16" else 1
-                gl, gms = kp["gemm_tcgen05"]   # one launch per chunk of points: time per hologram
-                tflops = 4.0 * wc.evals * passes / (gms / reps * 1e-3) / 1e12
-                peak_tc = _peaks().get("bf16_tflops") or 1939.7
-                rec["roofline"] = {"kernel": "gemm_tcgen05", "bound": "tensor", "achieved": tflops,
-                                   "peak": peak_tc, "unit": "TFLOP/s", "frac": tflops / peak_tc,
-                                   "flops_per_eval": 4 * passes,
-                                   "traffic": ncu_traffic("gemm_tcgen05", extra, wc.name),
-                                   "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
-            key = f"{extra}@{wc.name}"
-            forms[key] = rec
-            samples[key] = (wc, o.cpu().numpy())
+    # every compared form on the headline cloud; the GEMM forms (and the direct kernel, for the comparison the
+    # metric names) on the 1920x1080, 50,000-point cloud they are meant for; every form on the 256x256,
+    # 1,024-point cloud (the small direct case)
+    gemm_forms = [f for f in args.compare if f.startswith("gemm")]
+    extra_clouds = []
+    if gemm_forms:
+        extra_clouds.append((workloads.display_gemm(), gemm_forms + ["direct_sfu"]))
+    if not args.no_small:
+        extra_clouds.append((workloads.small_direct(), ["direct_sfu", "direct_accurate"] + gemm_forms))
+    runs = [(cloud, xyz, amp, h, f) for f in args.compare]
+    for wc, flist in extra_clouds:
+        dev = (torch.from_numpy(wc.xyz).cuda(), torch.from_numpy(wc.amp).cuda(),
+               Hologram(wc.width, wc.height, wc.pitch_m, wc.lambda_m, stream=stream))
+        runs += [(wc, dev[0], dev[1], dev[2], f) for f in flist]
+    for wc, cx, ca, hh, extra in runs:
+        hh.set_form(extra)
+        o = torch.empty((wc.height, wc.width), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            hh.point_cloud(cx, ca, o)
+        hh.sync()
+        hh.profile(True)
+        hh.profile_read(reset=True)
+        reps = max(3, args.steps // 4) if wc.evals > 1e9 else max(20, args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hh.point_cloud(cx, ca, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hh.sync()
+        kp = hh.profile_read(reset=True)
+        hh.profile(False)
+        ms = e0.elapsed_time(e1) / reps
+        rec = {"gevals_per_s": wc.evals / ms / 1e6, "ms_per_hologram": ms,
+               "kernel_ms": {k: v[1] / reps for k, v in kp.items()}}
+        if extra.startswith("gemm") and "gemm_tcgen05" in kp:
+            passes = 3 if extra == "gemm_split16" else 1
+            gl, gms = kp["gemm_tcgen05"]   # one launch per chunk of points: time per hologram
+            tflops = 4.0 * wc.evals * passes / (gms / reps * 1e-3) / 1e12
+            peak_tc = _peaks().get("bf16_tflops") or 1939.7
+            rec["roofline"] = {"kernel": "gemm_tcgen05", "bound": "tensor", "achieved": tflops,
+                               "peak": peak_tc, "unit": "TFLOP/s", "frac": tflops / peak_tc,
+                               "flops_per_eval": 4 * passes,
+                               "traffic": ncu_traffic("gemm_tcgen05", extra, wc.name),
+                               "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
+            # the whole hologram (prep, factors, GEMM, reduction) against the same tensor peak
+            rec["e2e_tensor_frac"] = 4.0 * wc.evals * passes / (ms * 1e-3) / 1e12 / peak_tc
+        elif extra in kp:
+            mufu = MUFU_PER_SM_PER_CLK * torch.cuda.get_device_properties(local).multi_processor_count * \
+                (_peaks().get("sm_max_mhz") or 2070.0) * 1e6
+            dms = kp[extra][1] / max(kp[extra][0], 1)
+            rec["roofline"] = {"kernel": extra, "bound": "alu", "achieved": wc.evals / (dms * 1e-3) / 1e9,
+                               "peak": mufu / 1e9, "unit": "Gcos/s (MUFU)",
+                               "frac": wc.evals / (dms * 1e-3) / mufu,
+                               "traffic": ncu_traffic(extra, extra, wc.name)}
+        key = f"{extra}@{wc.name}"
+        forms[key] = rec
+        samples[key] = (wc, o.cpu().numpy())
+    for wc, cx, ca, hh, extra in runs:
+        if hh is not h:
+            hh.close()
     # the paper's own timed workload (Tables 3-4): phase-only CGH of 1920x1080 holograms with
     # 10^3, 10^4 and 10^5 points (complex wave + kinoform quantisation), beside the Tesla K20's
     # published times for the direct calculation (context only: other hardware, fast math)
@@ -456,9 +521,9 @@ def run_ours(args):
             return e0.elapsed_time(e1) / reps
         table5 = {1024: (0.17, 0.32, 0.011), 2048: (0.60, 0.41, 0.027), 4096: (2.06, 0.87, 0.125),
                   8192: (9.00, 3.80, None)}
-        for N, (t_cpu, t_phi, t_k20) in table5.items():
-            plane = torch.from_numpy(workloads.complex_plane(5, N, N)).cuda()
-            with Hologram(N, N, 8e-6, 633e-9, stream=stream) as hf:
+        for side, (t_cpu, t_phi, t_k20) in table5.items():
+            plane = torch.from_numpy(workloads.complex_plane(5, side, side)).cuda()
+            with Hologram(side, side, 8e-6, 633e-9, stream=stream) as hf:
                 dst = torch.empty_like(plane)
                 ms = _ms(lambda: hf.fresnel(plane, 1.0, dst), 5)
                 hf.profile(True)
@@ -466,7 +531,7 @@ def run_ours(args):
                 hf.fresnel(plane, 1.0, dst)
                 hf.sync()
                 kp = hf.profile_read(reset=True)
-            fresnel_t[f"{N}x{N}"] = {"ms": ms, "paper_s": {"cpu": t_cpu, "xeon_phi": t_phi, "k20": t_k20},
+            fresnel_t[f"{side}x{side}"] = {"ms": ms, "paper_s": {"cpu": t_cpu, "xeon_phi": t_phi, "k20": t_k20},
                                      "speedup_vs_k20": (t_k20 * 1e3 / ms) if t_k20 else None,
                                      "kernel_ms": {k: v[1] for k, v in kp.items()}}
             del plane, dst
@@ -589,6 +654,12 @@ def run_ours(args):
         for k, v in form_nrms.items():
             forms[k]["nrms_vs_oracle"] = v
 
+    # the headline form on its own cloud, beside the compared forms
+    forms = {f"{args.form}@{cloud.name}": {
+        "ms_per_hologram": total_ms / args.steps, "gevals_per_s": value / world,
+        "nrms_vs_oracle": nrms,
+        "roofline": {"frac": (achieved / peak) if achieved else None, "traffic": traffic}}, **forms}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -623,7 +694,9 @@ def run_ours(args):
         "paper_fresnel_diffraction": fresnel_t,
         "paper_wrp_2048x2048": wrp_t,
         "cpu_baseline": cpu,
+        "summary": compact_summary(forms, large, vbatch, cloud.name),
     }
+    assert line["config"]["n_points"] == cloud.n_points and line["config"]["workload"] == cloud.name
     print(json.dumps(line))
     h.close()
     if dist is not None:
@@ -647,6 +720,7 @@ def main():
                     help="skip the Fresnel diffraction and wavefront-recording workloads of Tables 5-6")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4096x4096, 10^6-point depth-layered case")
+    ap.add_argument("--no-small", action="store_true", help="skip the 256x256, 1,024-point cloud")
     ap.add_argument("--no-paper-workload", action="store_true",
                     help="skip the phase-only 1920x1080 workload of the paper's Tables 3-4")
     args = ap.parse_args()

@@ -327,12 +327,16 @@ int cgh_profile_read(cgh_ctx *ctx, cgh_kernel_time *out, int max_entries, int *n
  * until the process exits; n_points > CGH_NOALLOC_MAX_POINTS returns
  * CGH_EINVAL before anything is launched (use cgh_point_cloud instead).
  * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
- * library routine.  It waits for its own work and returns CGH_OK, CGH_EINPUT
- * (bad point data) or CGH_ETIMEOUT.  The first call on a device looks up the
- * scratch address for that device (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call shares the scratch and it keeps the
- * last call's contents; calls that overlap on the GPU (several host threads
- * or streams at once) race on it and must be serialised by the caller.
+ * library routine.  Every call blocks: it synchronises cuda_stream to read
+ * its status word back, and returns CGH_OK, CGH_EINPUT (bad point data) or
+ * CGH_ETIMEOUT.  The first call on a device looks up the scratch address for
+ * that device (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not call
+ * this entry point again after cudaDeviceReset() in the same process (the
+ * kept address would no longer name the scratch).  Every call shares the
+ * scratch and it keeps the last call's contents; calls that overlap on the
+ * GPU (several host threads or streams at once) race on it and must be
+ * serialised by the caller.
  */
 #define CGH_NOALLOC_MAX_POINTS 131072
 int cgh_point_cloud_noalloc(int width, int height, double pitch_m, double lambda_m, const float *d_xyz,

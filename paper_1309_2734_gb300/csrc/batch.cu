@@ -196,13 +196,14 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
         }
     }
     const int gctas = gunits.empty() ? 0 : std::min<int>(gemm_max_ctas(ctx->num_sms), (int)gunits.size());
-    const int dctas_max = ctx->num_sms * direct_ctas_per_sm();
     int dctas[2];
     std::vector<int> goff, doff[2];
     std::vector<int2> gord, dord[2];
     if (gctas) assign(gunits, gcost, gctas, goff, gord);
     for (int w = 0; w < 2; ++w) {
-        dctas[w] = dunits[w].empty() ? 0 : std::min<int>(dctas_max, (int)dunits[w].size());
+        dctas[w] = dunits[w].empty() ? 0
+                                     : std::min<int>(ctx->num_sms * direct_ctas_per_sm(w == 0, dtall),
+                                                     (int)dunits[w].size());
         if (dctas[w]) assign(dunits[w], dcost[w], dctas[w], doff[w], dord[w]);
     }
     const size_t t_gjobs = L.take(gjobs.size() * sizeof(GemmJob), 128);

@@ -43,6 +43,7 @@
 // rounding error at N = 10^6 well below 1e-5 relative.
 #include "cospoly.h"
 #include "device_util.cuh"
+#include "host_util.h"
 #include "kernels.h"
 
 namespace cgh {
@@ -117,11 +118,15 @@ __device__ __forceinline__ uint32_t wave_second_difference(const int4 q, const u
     return EXTRA ? __funnelshift_l((uint32_t)q.w, (uint32_t)q.z, 1) : w.x;   // 2 C with the piston, else aux.x
 }
 
+// D as a signed turn has up to 32 significant bits, more than a float holds: its top 24 bits and its low 8 bits
+// are each exact in single precision, and v = e^{i 2 pi D_hi} e^{i 2 pi D_lo} (the plain conversion dropped up to
+// 2^-25 turn, which column i carries i (i - 1) / 2 times).
 __device__ __forceinline__ float2 wave_rotation(uint32_t D)
 {
-    float s, c;
-    sincospif((float)(int)D * (1.0f / 2147483648.0f), &s, &c);   // [-1, 1): twice the signed turn
-    return make_float2(c, s);
+    float sh, ch, sl, cl;
+    sincospif((float)(int)(D & 0xffffff00u) * (1.0f / 2147483648.0f), &sh, &ch);   // [-1, 1): twice the turn
+    sincospif((float)(D & 0xffu) * (1.0f / 2147483648.0f), &sl, &cl);
+    return cmul_f(make_float2(ch, sh), make_float2(cl, sl));
 }
 
 // Adds one point's terms of the complex object wave (Eq. 2, restricted form) to a thread's TL x TR block.
@@ -518,9 +523,27 @@ cudaError_t launch_direct_batch(bool sfu, bool tall, const DirectJob *d_jobs, co
     return cudaGetLastError();
 }
 
-int direct_ctas_per_sm()
+int direct_ctas_per_sm(bool sfu, bool tall)
 {
-    return 2;
+    int n = 0;
+    cudaError_t e;
+    if (sfu && tall)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_batch_kernel<kTL, kTR, kTallBX, kTallBY, true>,
+                                                          kTallBX * kTallBY, 0);
+    else if (sfu)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_batch_kernel<kTL, kTR, kBX, kBY, true>,
+                                                          kBX * kBY, 0);
+    else if (tall)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_batch_kernel<kTL, kTR, kTallBX, kTallBY, false>,
+                                                          kTallBX * kTallBY, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_batch_kernel<kTL, kTR, kBX, kBY, false>,
+                                                          kBX * kBY, 0);
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
 }
 
 }  // namespace cgh
@@ -536,15 +559,16 @@ void wave_as(bool extra, dim3 grid, cudaStream_t s, const int4 *geo, const uint2
              uint64_t timeout_ns, const PhaseRef &ref)
 {
     constexpr size_t tot_bytes = (size_t)2 * kWaveTR * kWaveTL * BX * BY * sizeof(float);
-    static bool configured = false;   // the running totals exceed the default 48 KB of dynamic shared memory
-    if (!configured) {
-        if (cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes) != cudaSuccess ||
-            cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes) != cudaSuccess)
-            return;
-        configured = true;
-    }
+    static PerDeviceOnce configured;   // the running totals exceed the default 48 KB of dynamic shared memory
+    const cudaError_t e = configured.run([&] {
+        cudaError_t r = cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes);
+        return r;
+    });
+    if (e != cudaSuccess) return;
     if (extra)
         direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true><<<grid, BX * BY, tot_bytes, s>>>(
             geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, im, vec, status, timeout_ns, ref);

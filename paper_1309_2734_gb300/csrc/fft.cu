@@ -35,6 +35,7 @@
 // shared memory carries the values only between stages; other lengths take the
 // run-time form, which stages whole tiles through shared memory.
 #include "device_util.cuh"
+#include "host_util.h"
 #include "kernels.h"
 
 namespace cgh {
@@ -936,13 +937,12 @@ static cudaError_t launch_cols_full_as(const FftGrid &g, float2 *pad, const floa
 {
     constexpr int M = 1 << LM;
     constexpr size_t bytes = (size_t)((M + M / 16) << LQ) * sizeof(float2);
-    static bool configured = false;
-    if (!configured) {
-        const cudaError_t e = cudaFuncSetAttribute(fft_cols_full_kernel<LM, LQ>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static PerDeviceOnce configured;
+    const cudaError_t e = configured.run([&] {
+        return cudaFuncSetAttribute(fft_cols_full_kernel<LM, LQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes);
+    });
+    if (e != cudaSuccess) return e;
     fft_cols_full_kernel<LM, LQ><<<g.Lx >> LQ, 1 << (LM + LQ - 4), bytes, s>>>(pad, spec, g.Lx, nz_rows, keep_rows, twy);
     return cudaGetLastError();
 }

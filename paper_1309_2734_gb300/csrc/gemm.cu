@@ -43,6 +43,7 @@
 #include <cudaTypedefs.h>
 
 #include "device_util.cuh"
+#include "host_util.h"
 #include "kernels.h"
 #include "tcgen05.cuh"
 
@@ -463,12 +464,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 template <int BN_MAX, class Units>
 cudaError_t configure()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN_MAX, Units>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         GemmCfg<BN_MAX>::kSmemBytes);
-    if (e == cudaSuccess) done = true;
-    return e;
+    static PerDeviceOnce done;
+    return done.run([] {
+        return cudaFuncSetAttribute(gemm_kernel<BN_MAX, Units>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    GemmCfg<BN_MAX>::kSmemBytes);
+    });
 }
 
 template <int BN>

@@ -105,7 +105,8 @@ struct DirectJob {
 // tall: the 16 x 16-thread CTA shape (tiles of direct_shape(true)), else the wide one.
 cudaError_t launch_direct_batch(bool sfu, bool tall, const DirectJob *d_jobs, const int *d_cta_off,
                                 const int2 *d_units, int ctas, int *status, uint64_t timeout_ns, cudaStream_t s);
-int direct_ctas_per_sm();
+// CTAs of the batched direct kernel resident per SM (occupancy calculator).
+int direct_ctas_per_sm(bool sfu, bool tall);
 
 // a3: separable factors P [height][ld], Q [width][ld] (factors.cu).  For
 // kFactorSplit16 the lo planes follow the hi planes (offset rows * ld).

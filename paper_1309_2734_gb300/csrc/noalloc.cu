@@ -39,7 +39,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device and kept for the life of the
+// process: after cudaDeviceReset() the module is loaded again and the kept address is stale, so the header tells
+// callers not to use this entry point after a reset.
 int scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return CGH_ECUDA;

@@ -23,6 +23,7 @@
 // kernel is compute-bound, so the loads need no asynchronous pipeline and the
 // kernel has no waits to bound).
 #include "device_util.cuh"
+#include "host_util.h"
 #include "kernels.h"
 
 namespace cgh {
@@ -400,13 +401,12 @@ void spherical_as(dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, 
                   const PhaseRef &ref)
 {
     constexpr size_t tot_bytes = (size_t)PLANES * sph_tile_rows(PLANES) * sph_tile_cols(PLANES) * BX * BY * sizeof(float);
-    static bool configured = false;   // the running totals exceed the default 48 KB of dynamic shared memory
-    if (!configured) {
-        if (cudaFuncSetAttribute(spherical_kernel<PLANES, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tot_bytes) != cudaSuccess)
-            return;
-        configured = true;
-    }
+    static PerDeviceOnce configured;   // the running totals exceed the default 48 KB of dynamic shared memory
+    if (configured.run([&] {
+            return cudaFuncSetAttribute(spherical_kernel<PLANES, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tot_bytes);
+        }) != cudaSuccess)
+        return;
     spherical_kernel<PLANES, BX, BY><<<grid, BX * BY, tot_bytes, s>>>(geo, aux, ext, n_ptiles, width, height, tiles_x,
                                                                       split, out, ss, im, ref);
 }

@@ -115,14 +115,15 @@ def test_auto_single_hologram_meets_tolerance():
     assert oracle.nrms(f.cpu().numpy(), ref) <= 1e-5
 
 
-def test_video_batch_64_frames_sampled():
+@pytest.mark.parametrize("tol_e9", [10000, 2_000_000])
+def test_video_batch_64_frames_sampled(tol_e9):
     """64 frames of uneven size (1024^2 / 1920x1080 / 3840x2160, 10^3..2x10^5 points), one
-    batch call at NRMS 1e-5 (autotuned forms), sampled pixels of every frame vs the oracle."""
+    batch call at NRMS 1e-5 and at 2e-3 (autotuned forms), sampled pixels of every frame vs the oracle."""
     frames = workloads.video_batch()
     dev = _dev(frames)
     outs = [torch.empty((c.height, c.width), device="cuda") for c in frames]
     with Hologram(8, 8, 8e-6, 532e-9, form="auto", timeout_ms=20000) as h:
-        h.set_option(_lib.CGH_OPT_TOLERANCE_E9, 10000)
+        h.set_option(_lib.CGH_OPT_TOLERANCE_E9, tol_e9)
         batch(h, dev, outs)
         h.sync()
     rng = np.random.default_rng(64)
@@ -131,4 +132,4 @@ def test_video_batch_64_frames_sampled():
         rows = rng.integers(0, c.height, 24)
         ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
         got = o[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
-        assert oracle.nrms(got, ref) <= 1e-5, c.name
+        assert oracle.nrms(got, ref) <= tol_e9 * 1e-9, c.name

@@ -1,7 +1,7 @@
 """The large depth-layered case: a 4096x4096 hologram of 10^6 points on 16
 depth planes, split FP16 GEMM form (grouped by plane and column), its 8-bit
-quantised output.  The oracle is checked on a central crop (CGH_LARGE_CROP,
-default 128; 512 takes about five minutes of oracle time on 16 cores)."""
+quantised output.  The oracle is checked on the central 512x512 crop (about
+five minutes of oracle time on 16 cores; CGH_LARGE_CROP sets another size)."""
 import os
 
 import numpy as np
@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-CROP = int(os.environ.get("CGH_LARGE_CROP", "128"))
+CROP = int(os.environ.get("CGH_LARGE_CROP", "512"))
 
 
 @pytest.fixture(scope="module")
