@@ -90,7 +90,9 @@ enum {
 /* Options (cgh_set_option). */
 enum {
     CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side wait; host-side waits allow 2x + 1 s; default 5000 */
-    CGH_OPT_POINT_SPLIT = 2,    /* direct form: point chunks reduced afterwards; 0 = automatic */
+    CGH_OPT_POINT_SPLIT = 2,    /* direct forms: 0 = automatic (the amplitude hologram: every CTA takes an equal
+                                   share of the (pixel tile, point) pairs and the last CTA to finish a tile sums
+                                   its parts); s > 0: s point chunks, each a plane of partial sums, reduced after */
     CGH_OPT_GEMM_SPLITK = 3,    /* GEMM forms: K splits reduced afterwards; 0 = automatic */
     CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width, one of 128, 192, 224, 240, 256; 0 = automatic */
     CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */
@@ -113,8 +115,11 @@ enum {
                                    being captured into a graph (it reads two counts back to the host, which waits for
                                    the stream).  Results agree with the ungrouped form to rounding.  Not with the
                                    piston (CGH_PHASE_FRESNEL_PISTON): points of equal C may differ in depth. */
-    CGH_OPT_PHASE_MODEL = 13    /* CGH_PHASE_* above; default CGH_PHASE_FRESNEL.  cgh_batch supports the default
+    CGH_OPT_PHASE_MODEL = 13,   /* CGH_PHASE_* above; default CGH_PHASE_FRESNEL.  cgh_batch supports the default
                                    only (CGH_ENOTSUP otherwise). */
+    CGH_OPT_DIRECT_TOTALS = 14  /* direct amplitude form with CGH_OPT_POINT_SPLIT = 0: where each thread keeps its
+                                   running totals; 0 = automatic, 1 = registers (two CTAs per SM), 2 = shared
+                                   memory (three CTAs per SM) */
 };
 
 typedef struct cgh_ctx cgh_ctx;

@@ -1,6 +1,7 @@
 // The C ABI (include/cgh.h): argument checks, the context and its workspace,
 // and the order of kernel launches for each entry point.  No arithmetic of
 // the method runs here; every step of the hologram runs in the kernels.
+#include <algorithm>
 #include <cfloat>
 #include <chrono>
 #include <cmath>
@@ -19,26 +20,52 @@ using namespace cgh;
 
 namespace cgh {
 
-// Direct form: prep, then the direct kernel over point chunks, then the
-// fixed-order chunk reduction when there is more than one chunk.
+// Direct form: prep, then the direct kernel.  By default one launch in which the CTAs take equal shares of the
+// (pixel tile, point) pairs and the last CTA to finish a tile sums its parts (no partial planes); with
+// CGH_OPT_POINT_SPLIT > 0, point chunks into partial planes and the fixed-order chunk reduction after.
+constexpr int kStreamMinPoints = 64;   // fewest points of one CTA's share in the balanced layout
+
 int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, double lambda, const float *d_xyz,
                const float *d_amp, int64_t n, float *d_out)
 {
     const int64_t n_pad = padded_points(n);
     const int64_t n_ptiles = n_pad / kPointTile;
-    const DirectLayout lay = choose_direct_layout(false, width, height, n_ptiles, ctx->num_sms, ctx->point_split);
-    const DirectShape sh = lay.shape;
-    const int split = lay.split;
-    const int64_t plane = (int64_t)width * height;
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
-    const size_t part_bytes = split > 1 ? (size_t)split * plane * sizeof(float) : 0;
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + part_bytes);
+    const int64_t plane = (int64_t)width * height;
+    const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
+    const bool stream_k = ctx->point_split == 0;
+    DirectShape sh;
+    int split = 1, ctas = 0;
+    bool smem_tot = false;
+    size_t ws_rest = 0;
+    if (stream_k) {
+        // the shape with the fewer padded pixels; as many CTAs as fit, each with at least kStreamMinPoints points
+        const DirectShape wide = direct_shape(false), tall = direct_shape(true);
+        auto padded = [&](const DirectShape &s) {
+            return (int64_t)((width + s.tile_w - 1) / s.tile_w) * s.tile_w *
+                   (((int64_t)height + s.tile_h - 1) / s.tile_h) * s.tile_h;
+        };
+        sh = padded(tall) <= padded(wide) ? tall : wide;
+        smem_tot = ctx->direct_totals == 2;
+        const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
+        const int64_t units = tiles * n;
+        const int64_t slots = (int64_t)ctx->num_sms * direct_stream_per_sm(sfu, sh, smem_tot);
+        ctas = (int)std::max<int64_t>(1, std::min<int64_t>(slots, units / kStreamMinPoints));
+        ws_rest = align_up((size_t)2 * ctas * sh.tile_w * sh.tile_h * sizeof(float), 256) +
+                  align_up((size_t)tiles * sizeof(int), 256);
+    } else {
+        const DirectLayout lay = choose_direct_layout(false, width, height, n_ptiles, ctx->num_sms, ctx->point_split);
+        sh = lay.shape;
+        split = lay.split;
+        ws_rest = split > 1 ? (size_t)split * plane * sizeof(float) : 0;
+    }
+    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + ws_rest);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->ws);
     int4 *geo = reinterpret_cast<int4 *>(base);
     uint2 *aux = reinterpret_cast<uint2 *>(base + geo_bytes);
-    float *parts = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
+    float *rest = reinterpret_cast<float *>(base + geo_bytes + aux_bytes);
     cudaError_t e;
     {
         ProfileScope ps(ctx, "prep_points", 1);
@@ -46,15 +73,22 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
                                nullptr, ctx->stream, aux_mode(ctx));
     }
     if (e != cudaSuccess) return cuda_status(e);
-    const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
+    if (stream_k) {
+        int *counters = reinterpret_cast<int *>(
+            reinterpret_cast<char *>(rest) + align_up((size_t)2 * ctas * sh.tile_w * sh.tile_h * sizeof(float), 256));
+        ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);   // and the counters' memset
+        return cuda_status(launch_direct_stream(sfu, sh, smem_tot, ctas, geo, aux, (int)n, width, height, d_out, rest,
+                                                counters, ctx->d_status, tmo, ctx->stream, ctx->drop_tile,
+                                                phase_ref(ctx)));
+    }
     {
         ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);
-        e = launch_direct(sfu, sh, geo, aux, (int)n_pad, width, height, split, split > 1 ? parts : d_out, plane,
+        e = launch_direct(sfu, sh, geo, aux, (int)n_pad, width, height, split, split > 1 ? rest : d_out, plane,
                           ctx->d_status, tmo, ctx->stream, ctx->drop_tile, phase_ref(ctx));
     }
     if (e != cudaSuccess || split == 1) return cuda_status(e);
     ProfileScope ps(ctx, "reduce_slices", 1);
-    return cuda_status(launch_reduce_slices(parts, split, plane, plane, d_out, ctx->stream));
+    return cuda_status(launch_reduce_slices(rest, split, plane, plane, d_out, ctx->stream));
 }
 
 // k-blocks per TMEM accumulation chain of the split-FP16 form (3 passes each)
@@ -801,6 +835,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         if (value != CGH_PHASE_FRESNEL && value != CGH_PHASE_FRESNEL_PISTON && value != CGH_PHASE_SPHERICAL)
             return CGH_EINVAL;
         ctx->phase_model = (int)value;
+        return CGH_OK;
+    case CGH_OPT_DIRECT_TOTALS:
+        if (value < 0 || value > 2) return CGH_EINVAL;
+        ctx->direct_totals = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

@@ -41,6 +41,8 @@
 // Accumulation is two-level: each point tile is summed into fresh partials
 // that are then added into the running totals, which keeps single-precision
 // rounding error at N = 10^6 well below 1e-5 relative.
+#include <type_traits>
+
 #include "cospoly.h"
 #include "device_util.cuh"
 #include "host_util.h"
@@ -231,13 +233,20 @@ __device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0,
 // SMEM_TOT: the running totals live in shared memory (s_tot, index-major: entry (c, r, i) of thread tid at
 // ((c TR + r) TL + i) BX BY + tid, so a warp's accesses are consecutive words) instead of registers, which leaves
 // the registers to the point tile's partial sums of a taller thread block.
-template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1, bool EXTRA = false, bool SMEM_TOT = false>
+// The points of the unit are those of tiles [t_begin, t_end), less the first p_first points of the first tile
+// and the points from p_last_end on of the last one.  Sink: PlainStore writes the totals to dst; any other sink
+// is called as sink(tot) with the thread's TR x TL totals of plane 0 (the amplitude hologram only).
+struct PlainStore {};
+
+template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1, bool EXTRA = false, bool SMEM_TOT = false,
+          class Sink = PlainStore>
 __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const uint2 *__restrict__ aux,
                                             int t_begin, int t_end, int tile_m0, int tile_n0, int width,
                                             int height, float *__restrict__ dst, bool vec, int4 (*s_geo)[kPointTile],
                                             uint2 (*s_aux)[kPointTile], uint64_t *s_bar, uint32_t &kg, int *status,
                                             unsigned long long timeout_ns, int drop = -1, long long im_offset = 0,
-                                            const PhaseRef &ref = PhaseRef(), float *s_tot = nullptr)
+                                            const PhaseRef &ref = PhaseRef(), float *s_tot = nullptr,
+                                            int p_first = 0, int p_last_end = kPointTile, Sink sink = Sink())
 {
     constexpr int T = kPointTile;
     constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
@@ -302,19 +311,22 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
 
         const int4 *sg = s_geo[st];
         const uint2 *sa = s_aux[st];
+        const int p_lo = k == 0 ? p_first : 0;
+        const int p_hi = k == nt - 1 ? p_last_end : T;
         if constexpr (PLANES == 2) {
             __shared__ float2 s_rot[T];   // e^{i 2 pi D} of the tile's points, once each per CTA
             for (int p = tid; p < T; p += BX * BY) s_rot[p] = wave_rotation(wave_second_difference<EXTRA>(sg[p], sa[p]));
             __syncthreads();
 #pragma unroll 1
-            for (int p = 0; p < T; ++p)
+            for (int p = p_lo; p < p_hi; ++p)
                 point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], s_rot[p], m0, n0, pr, part[0], part[PLANES - 1]);
         } else if constexpr (SFU) {
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalSfu, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
+            for (int p = p_lo; p < p_hi; ++p) point_terms<TL, TR, kEvalSfu, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         } else {
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
+            for (int p = p_lo; p < p_hi; ++p)
+                point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
@@ -338,6 +350,11 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
             for (int r = 0; r < TR; ++r)
 #pragma unroll
                 for (int i = 0; i < TL; ++i) tot[c][r][i] = s_tot[tidx(c, r, i)];
+    }
+    if constexpr (!std::is_same<Sink, PlainStore>::value) {
+        static_assert(PLANES == 1, "sinks take the amplitude hologram");
+        sink(tot[0]);
+        return true;
     }
 
 #pragma unroll
@@ -391,6 +408,118 @@ __global__ void __launch_bounds__(BX *BY, 2)
                                      (tile / tiles_x) * (BY * TR), width, height,
                                      out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg,
                                      status, timeout_ns, blockIdx.y == 0 ? drop_tile : -1, 0, ref);
+}
+
+// One hologram over a flat work space: unit u = t N + j is (pixel tile t, point j), t < n_tiles, j < N, and
+// CTA c of C takes units [c U / C, (c + 1) U / C) (U = n_tiles N), so every CTA has the same number of terms to
+// within one point, whatever the tile count, and no padded point is evaluated.  A CTA walks its units tile by
+// tile (segments); a segment that covers all N points of its tile stores the tile, any other stores its
+// partial totals in the CTA's slot (0: its first segment, 1: its last) and counts itself on the tile's counter.
+// The CTA that arrives last sums the tile's segments in the order of their CTAs (so the result does not depend
+// on who arrives last) and writes the tile: no partial planes and no separate reduction pass.  counters (one
+// per tile) are zero at launch; slots hold 2 C tiles of totals, thread-major float4s.
+template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
+__global__ void __launch_bounds__(BX *BY, SMEM_TOT ? 3 : 2)
+    direct_stream_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int width,
+                         int height, int tiles_x, long long units, float *__restrict__ out,
+                         float4 *__restrict__ slots, int *__restrict__ counters, bool vec, int *status,
+                         unsigned long long timeout_ns, int drop_tile, const PhaseRef ref)
+{
+    constexpr int T = kPointTile;
+    constexpr int NT = BX * BY;
+    constexpr int Q4 = TL * TR / 4;   // float4s of totals per thread
+    static_assert(TL % 4 == 0, "rows of float4s");
+    __shared__ alignas(128) int4 s_geo[2][kPointTile];
+    __shared__ alignas(128) uint2 s_aux[2][kPointTile];
+    __shared__ alignas(8) uint64_t s_bar[2];
+    __shared__ int s_last;
+    extern __shared__ float s_tot[];   // SMEM_TOT: TR TL floats per thread
+    init_point_barriers<BX, BY>(s_bar);
+    const long long C = gridDim.x, c = blockIdx.x, N = n_points;
+    const long long w0 = c * units / C, w1 = (c + 1) * units / C;
+    const int tid = threadIdx.x;
+    const long long first_tile = w0 / N;
+    // the CTA that owns unit u, and the slot in which CTA cs keeps its segment of tile t
+    auto owner = [&](long long u) { return ((u + 1) * C - 1) / units; };
+    auto slot_of = [&](long long cs, long long t) { return (cs * units / C) / N == t ? 0 : 1; };
+    uint32_t kg = 0;
+    for (long long w = w0; w < w1;) {
+        const long long t = w / N, seg_start = w;
+        const int p0 = (int)(w - t * N);
+        const int p1 = (int)min(N, (long long)p0 + (w1 - w));
+        w += p1 - p0;
+        const int k0 = p0 / T, k1 = (p1 + T - 1) / T;
+        const int tm0 = (int)(t % tiles_x) * (BX * TL), tn0 = (int)(t / tiles_x) * (BY * TR);
+        const bool whole = p0 == 0 && p1 == N;
+        auto sink = [&](float(&tot)[TR][TL]) {
+            const int m0 = tm0 + (tid % BX) * TL, n0 = tn0 + (tid / BX) * TR;
+            float4 *mine = slots + (2 * c + slot_of(c, t)) * (long long)(Q4 * NT) + tid;
+            if (!whole) {
+                // partial totals to the slot, then count this segment on the tile
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int i = 0; i < TL; i += 4)
+                        mine[(r * TL + i) / 4 * NT] = make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) {
+                    const long long lo = owner(t * N), hi = owner(t * N + N - 1);
+                    s_last = atomicAdd(&counters[t], 1) == (int)(hi - lo);
+                }
+                __syncthreads();
+                if (!s_last) return;
+                __threadfence();
+                // the tile's segments in CTA order, one float4 of every thread's block at a time
+                const long long lo = owner(t * N), hi = owner(t * N + N - 1);
+#pragma unroll
+                for (int q = 0; q < Q4; ++q) {
+                    const int r = q * 4 / TL, i = q * 4 % TL;
+                    float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    for (long long cs = lo; cs <= hi; ++cs) {
+                        const float4 v = cs == c ? make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3])
+                                                 : __ldcg(slots + (2 * cs + slot_of(cs, t)) * (long long)(Q4 * NT) +
+                                                          q * NT + tid);
+                        if (cs == lo) {
+                            a = v;
+                        } else {
+                            a.x += v.x;
+                            a.y += v.y;
+                            a.z += v.z;
+                            a.w += v.w;
+                        }
+                    }
+                    tot[r][i] = a.x;
+                    tot[r][i + 1] = a.y;
+                    tot[r][i + 2] = a.z;
+                    tot[r][i + 3] = a.w;
+                }
+                if (tid == 0) counters[t] = 0;
+            }
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const int n = n0 + r;
+                if (n >= height || m0 >= width) continue;
+                float *row = out + (long long)n * width + m0;
+                if (vec && m0 + TL <= width) {
+#pragma unroll
+                    for (int i = 0; i < TL; i += 4)
+                        *reinterpret_cast<float4 *>(row + i) =
+                            make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < TL; ++i)
+                        if (m0 + i < width) row[i] = tot[r][i];
+                }
+            }
+        };
+        if (!direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA, SMEM_TOT>(
+                geo, aux, k0, k1, tm0, tn0, width, height, out, vec, s_geo, s_aux, s_bar, kg, status, timeout_ns,
+                (c == 0 && seg_start == w0) ? drop_tile : -1, 0, ref, s_tot, p0 - k0 * T, p1 - (k1 - 1) * T,
+                sink))
+            break;
+        __syncthreads();   // s_last and the point stages are reused by the next segment
+    }
 }
 
 // The complex object wave of one hologram: blockIdx.x = pixel tile, blockIdx.y =
@@ -498,6 +627,86 @@ cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, cons
         direct_shaped<kBX, kBY>(sfu, extra, grid, s, geo, aux, n_ptiles, width, height, tiles_x, split, out, ss,
                                 vec, status, timeout_ns, drop_tile, ref);
     return cudaGetLastError();
+}
+
+namespace {
+
+template <int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
+cudaError_t direct_stream_as(int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_points, int width,
+                             int height, int tiles_x, long long units, float *out, float4 *slots, int *counters,
+                             bool vec, int *status, uint64_t timeout_ns, int drop_tile, const PhaseRef &ref)
+{
+    const size_t dyn = SMEM_TOT ? (size_t)kTL * kTR * BX * BY * sizeof(float) : 0;
+    direct_stream_kernel<kTL, kTR, BX, BY, SFU, EXTRA, SMEM_TOT><<<ctas, BX * BY, dyn, s>>>(
+        geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, timeout_ns, drop_tile,
+        ref);
+    return cudaGetLastError();
+}
+
+template <int BX, int BY, bool SMEM_TOT>
+cudaError_t direct_stream_shaped(bool sfu, bool extra, int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux,
+                                 int n_points, int width, int height, int tiles_x, long long units, float *out,
+                                 float4 *slots, int *counters, bool vec, int *status, uint64_t timeout_ns,
+                                 int drop_tile, const PhaseRef &ref)
+{
+#define CGH_STREAM_ARGS ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, \
+                        timeout_ns, drop_tile, ref
+    if (sfu && !extra) return direct_stream_as<BX, BY, true, false, SMEM_TOT>(CGH_STREAM_ARGS);
+    if (sfu) return direct_stream_as<BX, BY, true, true, SMEM_TOT>(CGH_STREAM_ARGS);
+    if (!extra) return direct_stream_as<BX, BY, false, false, SMEM_TOT>(CGH_STREAM_ARGS);
+    return direct_stream_as<BX, BY, false, true, SMEM_TOT>(CGH_STREAM_ARGS);
+#undef CGH_STREAM_ARGS
+}
+
+template <int BX, int BY, bool SMEM_TOT>
+int stream_resident(bool sfu)
+{
+    const size_t dyn = SMEM_TOT ? (size_t)kTL * kTR * BX * BY * sizeof(float) : 0;
+    int n = 0;
+    const cudaError_t e =
+        sfu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &n, direct_stream_kernel<kTL, kTR, BX, BY, true, false, SMEM_TOT>, BX * BY, dyn)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &n, direct_stream_kernel<kTL, kTR, BX, BY, false, false, SMEM_TOT>, BX * BY, dyn);
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+int direct_stream_per_sm(bool sfu, const DirectShape &sh, bool smem_tot)
+{
+    if (sh.bx == kTallBX)
+        return smem_tot ? stream_resident<kTallBX, kTallBY, true>(sfu) : stream_resident<kTallBX, kTallBY, false>(sfu);
+    return smem_tot ? stream_resident<kBX, kBY, true>(sfu) : stream_resident<kBX, kBY, false>(sfu);
+}
+
+cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, bool smem_tot, int ctas, const int4 *geo,
+                                 const uint2 *aux, int n_points, int width, int height, float *out, float *slots,
+                                 int *counters, int *status, uint64_t timeout_ns, cudaStream_t s, int drop_tile,
+                                 const PhaseRef &ref)
+{
+    const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
+    const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
+    const long long units = (long long)tiles_x * tiles_y * n_points;
+    if (n_points < 1 || ctas < 1 || (long long)ctas > units || ((uintptr_t)slots % 16) != 0)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(counters, 0, (size_t)tiles_x * tiles_y * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const bool vec = (width % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    float4 *sl = reinterpret_cast<float4 *>(slots);
+    const bool extra = ref.any();
+#define CGH_STREAM_ARGS sfu, extra, ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, sl, counters, vec, \
+                        status, timeout_ns, drop_tile, ref
+    if (sh.bx == kTallBX)
+        return smem_tot ? direct_stream_shaped<kTallBX, kTallBY, true>(CGH_STREAM_ARGS)
+                        : direct_stream_shaped<kTallBX, kTallBY, false>(CGH_STREAM_ARGS);
+    return smem_tot ? direct_stream_shaped<kBX, kBY, true>(CGH_STREAM_ARGS)
+                    : direct_stream_shaped<kBX, kBY, false>(CGH_STREAM_ARGS);
+#undef CGH_STREAM_ARGS
 }
 
 }  // namespace cgh

@@ -265,6 +265,48 @@ def test_quantize_hologram_vs_oracle_quantisation():
     assert ties.mean() < 0.01
 
 
+@pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate"])
+@pytest.mark.parametrize("w,h,n", [(300, 70, 2000), (1920, 1080, 777), (129, 65, 3), (640, 200, 4099)])
+def test_balanced_split_totals_and_determinism(form, w, h, n):
+    """The default layout: equal shares of the (pixel tile, point) pairs per CTA, a tile's parts summed by the
+    last CTA to finish it.  Running totals in registers or in shared memory give the same bits; two runs give
+    the same bits; the result meets the oracle and agrees with the chunked layout to rounding."""
+    c = workloads.random_cloud(4400 + n, w, h, n)
+    xyz, amp = _dev(c)
+    outs = []
+    for totals in (1, 1, 2):
+        with Hologram(w, h, c.pitch_m, c.lambda_m, form=form) as hg:
+            hg.set_option(_lib.CGH_OPT_DIRECT_TOTALS, totals)
+            f = hg.point_cloud(xyz, amp)
+            hg.sync()
+            outs.append(f.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+    if w * h * n <= 2e8:
+        ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
+        _check(outs[0], ref, c.amp)
+    chunked = _run(c, form, split=3)
+    assert oracle.nrms(outs[0], chunked) < 2e-7
+
+
+def test_balanced_split_wait_times_out_and_context_recovers():
+    """The default layout with a point tile that CTA 0 never loads (test hook): the bounded wait runs out, the
+    launch ends with a timeout status, no other CTA waits on the missing part, and the context keeps working."""
+    c = workloads.random_cloud(47, 300, 100, 1000)
+    xyz, amp = _dev(c)
+    with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form="direct_sfu", timeout_ms=300) as h:
+        h.set_option(_lib.CGH_OPT_TEST_DROP_TILE, 0)
+        h.point_cloud(xyz, amp)
+        with pytest.raises(CghError) as ei:
+            h.sync()
+        assert ei.value.code == _lib.CGH_ETIMEOUT
+        h.set_option(_lib.CGH_OPT_TEST_DROP_TILE, -1)
+        f = h.point_cloud(xyz, amp)
+        h.sync()
+    ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, c.width, c.height)
+    _check(f.cpu().numpy(), ref, c.amp)
+
+
 def test_device_wait_times_out_and_context_recovers():
     """A point tile that is never loaded (host-side test hook): the kernel's bounded
     wait runs out, the launch ends with a timeout status, and the context keeps working."""
