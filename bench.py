@@ -7,8 +7,8 @@ Workload (default): a 1920x1080 hologram of 10,000 seeded synthetic points
 (z ~ U[0.3, 1.0] m, A ~ U[0.5, 1.0], lambda = 532 nm, p = 8 um), the
 display-size case of the paper's direct-calculation experiments.  One step is
 one pass of the hot path over that cloud: point preparation, the direct
-kernel (SFU cosine), the chunk reduction when the launch splits the points,
-and the 8-bit quantiser.  Inputs and outputs are far below L2, so a 256 MiB
+kernel (SFU cosine; the CTAs take equal shares of the (pixel tile, point)
+pairs and sum each tile's parts in the kernel), and the 8-bit quantiser.  Inputs and outputs are far below L2, so a 256 MiB
 buffer is written between timed steps to flush L2; the flush is not timed.
 
 Metric: G point-pixel evaluations per second (W*H*N per hologram), with
@@ -669,6 +669,8 @@ def run_ours(args):
         "config": {"workload": cloud.name, "width": W, "height": H, "n_points": N, "form": args.form,
                    "step": ("prep + factors + tcgen05 GEMM (+ split reduction) + quantize8"
                             if args.form.startswith("gemm") else
+                            "prep + direct kernel (equal shares of the (tile, point) pairs, each tile's parts "
+                            "summed in the kernel) + quantize8" if args.form == "direct_sfu" else
                             "prep + direct kernel (+ chunk reduction) + quantize8"),
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -90,9 +90,10 @@ enum {
 /* Options (cgh_set_option). */
 enum {
     CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side wait; host-side waits allow 2x + 1 s; default 5000 */
-    CGH_OPT_POINT_SPLIT = 2,    /* direct forms: 0 = automatic (the amplitude hologram: every CTA takes an equal
-                                   share of the (pixel tile, point) pairs and the last CTA to finish a tile sums
-                                   its parts); s > 0: s point chunks, each a plane of partial sums, reduced after */
+    CGH_OPT_POINT_SPLIT = 2,    /* direct forms: 0 = automatic (the SFU amplitude hologram: every CTA takes an
+                                   equal share of the (pixel tile, point) pairs and the last CTA to finish a tile
+                                   sums its parts; otherwise point chunks as the critical-path model picks them);
+                                   s > 0: s point chunks, each a plane of partial sums, reduced after */
     CGH_OPT_GEMM_SPLITK = 3,    /* GEMM forms: K splits reduced afterwards; 0 = automatic */
     CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width, one of 128, 192, 224, 240, 256; 0 = automatic */
     CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */
@@ -117,9 +118,10 @@ enum {
                                    piston (CGH_PHASE_FRESNEL_PISTON): points of equal C may differ in depth. */
     CGH_OPT_PHASE_MODEL = 13,   /* CGH_PHASE_* above; default CGH_PHASE_FRESNEL.  cgh_batch supports the default
                                    only (CGH_ENOTSUP otherwise). */
-    CGH_OPT_DIRECT_TOTALS = 14  /* direct amplitude form with CGH_OPT_POINT_SPLIT = 0: where each thread keeps its
-                                   running totals; 0 = automatic, 1 = registers (two CTAs per SM), 2 = shared
-                                   memory (three CTAs per SM) */
+    CGH_OPT_DIRECT_CTAS = 14    /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the CTAs that share
+                                   the (pixel tile, point) pairs; 0 = automatic (up to three per resident CTA slot,
+                                   each with at least 1024 points; the hardware schedules those beyond the resident
+                                   ones as others finish) */
 };
 
 typedef struct cgh_ctx cgh_ctx;

@@ -20,10 +20,14 @@ using namespace cgh;
 
 namespace cgh {
 
-// Direct form: prep, then the direct kernel.  By default one launch in which the CTAs take equal shares of the
-// (pixel tile, point) pairs and the last CTA to finish a tile sums its parts (no partial planes); with
-// CGH_OPT_POINT_SPLIT > 0, point chunks into partial planes and the fixed-order chunk reduction after.
-constexpr int kStreamMinPoints = 64;   // fewest points of one CTA's share in the balanced layout
+// Direct form: prep, then the direct kernel.  The SFU form by default: one launch in which the CTAs take equal
+// shares of the (pixel tile, point) pairs and the last CTA to finish a tile sums its parts (no partial planes).
+// The accurate form, or CGH_OPT_POINT_SPLIT > 0: point chunks into partial planes and the fixed-order chunk
+// reduction after (on GB300 the accurate form measured 2 % faster chunked: 6.99 against 7.13 ms at 1920x1080,
+// 10^4 points).
+constexpr int kStreamMinPoints = 64;      // fewest points of one CTA's share in the balanced layout
+constexpr int kStreamSharePoints = 1024;  // points per share from which CTAs beyond the resident ones are added
+constexpr int kStreamWaves = 3;           // at most this many CTAs per resident slot
 
 int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, double lambda, const float *d_xyz,
                const float *d_amp, int64_t n, float *d_out)
@@ -34,24 +38,28 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
     const int64_t plane = (int64_t)width * height;
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
-    const bool stream_k = ctx->point_split == 0;
+    const bool stream_k = sfu && ctx->point_split == 0;
     DirectShape sh;
     int split = 1, ctas = 0;
-    bool smem_tot = false;
     size_t ws_rest = 0;
     if (stream_k) {
-        // the shape with the fewer padded pixels; as many CTAs as fit, each with at least kStreamMinPoints points
+        // the shape with the fewer padded pixels; up to kStreamWaves CTAs per resident slot (measured at
+        // 1920x1080, 10^4 points: 304 CTAs 4.69 ms, 912 4.64, 2128 4.71, 5100 4.86), each share of at least
+        // kStreamSharePoints points beyond the first wave and kStreamMinPoints within it
         const DirectShape wide = direct_shape(false), tall = direct_shape(true);
         auto padded = [&](const DirectShape &s) {
             return (int64_t)((width + s.tile_w - 1) / s.tile_w) * s.tile_w *
                    (((int64_t)height + s.tile_h - 1) / s.tile_h) * s.tile_h;
         };
         sh = padded(tall) <= padded(wide) ? tall : wide;
-        smem_tot = ctx->direct_totals == 2;
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         const int64_t units = tiles * n;
-        const int64_t slots = (int64_t)ctx->num_sms * direct_stream_per_sm(sfu, sh, smem_tot);
-        ctas = (int)std::max<int64_t>(1, std::min<int64_t>(slots, units / kStreamMinPoints));
+        const int64_t slots = (int64_t)ctx->num_sms * direct_stream_per_sm(true, sh);
+        int64_t want = units >= slots * kStreamSharePoints
+                           ? std::min<int64_t>(kStreamWaves * slots, units / kStreamSharePoints)
+                           : std::min<int64_t>(slots, units / kStreamMinPoints);
+        if (ctx->direct_ctas > 0) want = std::min<int64_t>(ctx->direct_ctas, units);
+        ctas = (int)std::max<int64_t>(1, want);
         ws_rest = align_up((size_t)2 * ctas * sh.tile_w * sh.tile_h * sizeof(float), 256) +
                   align_up((size_t)tiles * sizeof(int), 256);
     } else {
@@ -76,8 +84,8 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     if (stream_k) {
         int *counters = reinterpret_cast<int *>(
             reinterpret_cast<char *>(rest) + align_up((size_t)2 * ctas * sh.tile_w * sh.tile_h * sizeof(float), 256));
-        ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);   // and the counters' memset
-        return cuda_status(launch_direct_stream(sfu, sh, smem_tot, ctas, geo, aux, (int)n, width, height, d_out, rest,
+        ProfileScope ps(ctx, "direct_sfu", 1);   // and the counters' memset
+        return cuda_status(launch_direct_stream(sfu, sh, ctas, geo, aux, (int)n, width, height, d_out, rest,
                                                 counters, ctx->d_status, tmo, ctx->stream, ctx->drop_tile,
                                                 phase_ref(ctx)));
     }
@@ -836,9 +844,9 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
             return CGH_EINVAL;
         ctx->phase_model = (int)value;
         return CGH_OK;
-    case CGH_OPT_DIRECT_TOTALS:
-        if (value < 0 || value > 2) return CGH_EINVAL;
-        ctx->direct_totals = (int)value;
+    case CGH_OPT_DIRECT_CTAS:
+        if (value < 0 || value > (1 << 24)) return CGH_EINVAL;
+        ctx->direct_ctas = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

@@ -31,7 +31,7 @@ struct cgh_ctx {
     int form = CGH_FORM_AUTO;
     int64_t timeout_ms = 5000;
     int point_split = 0;
-    int direct_totals = 0;    // CGH_OPT_DIRECT_TOTALS
+    int direct_ctas = 0;      // CGH_OPT_DIRECT_CTAS
     int gemm_splitk = 0;
     int gemm_bn = 0;
     int gemm_chunk = 0;

@@ -320,13 +320,14 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
 #pragma unroll 1
             for (int p = p_lo; p < p_hi; ++p)
                 point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], s_rot[p], m0, n0, pr, part[0], part[PLANES - 1]);
-        } else if constexpr (SFU) {
+        } else if (p_lo == 0 && p_hi == T) {   // a whole tile: the loop with a fixed trip count
+            constexpr int M = SFU ? kEvalSfu : kEvalAccurate;
 #pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p) point_terms<TL, TR, kEvalSfu, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, M, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         } else {
+            constexpr int M = SFU ? kEvalSfu : kEvalAccurate;
 #pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p)
-                point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
+            for (int p = p_lo; p < p_hi; ++p) point_terms<TL, TR, M, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
@@ -418,107 +419,142 @@ __global__ void __launch_bounds__(BX *BY, 2)
 // The CTA that arrives last sums the tile's segments in the order of their CTAs (so the result does not depend
 // on who arrives last) and writes the tile: no partial planes and no separate reduction pass.  counters (one
 // per tile) are zero at launch; slots hold 2 C tiles of totals, thread-major float4s.
-template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
-__global__ void __launch_bounds__(BX *BY, SMEM_TOT ? 3 : 2)
+// What a CTA of the balanced layout knows about its current segment, kept in shared memory so that none of it
+// occupies registers while the point loop runs.
+struct StreamSeg {
+    long long t;      // pixel tile
+    int p0, p1;       // points [p0, p1) of it
+    int last;         // this CTA finished the tile's last part
+};
+
+// The end of a segment: a whole tile is stored; a part goes to the CTA's slot and is counted on the tile, and the
+// CTA that counts last sums the tile's parts in CTA order (so the result does not depend on who is last).
+template <int TL, int TR, int BX, int BY>
+struct StreamSink {
+    StreamSeg *seg;
+    float4 *slots;
+    int *counters;
+    float *out;
+    long long units, C, N;
+    int tiles_x, width, height;
+    bool vec;
+
+    __device__ long long owner(long long u) const { return ((u + 1) * C - 1) / units; }
+    // slot of CTA cs's part of tile t: 0 when it is the CTA's first segment, else 1 (its last)
+    __device__ int slot_of(long long cs, long long t) const { return (cs * units / C) / N == t ? 0 : 1; }
+
+    __device__ void operator()(float (&tot)[TR][TL]) const
+    {
+        constexpr int NT = BX * BY;
+        constexpr int Q4 = TL * TR / 4;   // float4s of totals per thread
+        const int tid = threadIdx.x;
+        const long long c = blockIdx.x;
+        const long long t = seg->t;
+        if (!(seg->p0 == 0 && seg->p1 == N)) {
+            float4 *mine = slots + (2 * c + slot_of(c, t)) * (long long)(Q4 * NT) + tid;
+#pragma unroll
+            for (int q = 0; q < Q4; ++q) {
+                const int r = q * 4 / TL, i = q * 4 % TL;
+                mine[q * NT] = make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
+            }
+            __threadfence();
+            __syncthreads();
+            const long long lo = owner(t * N), hi = owner(t * N + N - 1);
+            if (tid == 0) seg->last = atomicAdd(&counters[t], 1) == (int)(hi - lo);
+            __syncthreads();
+            if (!seg->last) return;
+            __threadfence();
+            // the tile's parts in CTA order, one float4 of every thread's block at a time
+#pragma unroll
+            for (int q = 0; q < Q4; ++q) {
+                const int r = q * 4 / TL, i = q * 4 % TL;
+                float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                for (long long cs = lo; cs <= hi; ++cs) {
+                    const float4 v = cs == c ? make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3])
+                                             : __ldcg(slots + (2 * cs + slot_of(cs, t)) * (long long)(Q4 * NT) +
+                                                      q * NT + tid);
+                    if (cs == lo) {
+                        a = v;
+                    } else {
+                        a.x += v.x;
+                        a.y += v.y;
+                        a.z += v.z;
+                        a.w += v.w;
+                    }
+                }
+                tot[r][i] = a.x;
+                tot[r][i + 1] = a.y;
+                tot[r][i + 2] = a.z;
+                tot[r][i + 3] = a.w;
+            }
+        }
+        const int m0 = (int)(t % tiles_x) * (BX * TL) + (tid % BX) * TL;
+        const int n0 = (int)(t / tiles_x) * (BY * TR) + (tid / BX) * TR;
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            const int n = n0 + r;
+            if (n >= height || m0 >= width) continue;
+            float *row = out + (long long)n * width + m0;
+            if (vec && m0 + TL <= width) {
+#pragma unroll
+                for (int i = 0; i < TL; i += 4)
+                    *reinterpret_cast<float4 *>(row + i) =
+                        make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < TL; ++i)
+                    if (m0 + i < width) row[i] = tot[r][i];
+            }
+        }
+    }
+};
+
+// One hologram over a flat work space: unit u = t N + j is (pixel tile t, point j), t < n_tiles, j < N, and
+// CTA c of C takes units [c U / C, (c + 1) U / C) (U = n_tiles N), so every CTA has the same number of terms to
+// within one point, whatever the tile count, and no padded point is evaluated.  A CTA walks its units tile by
+// tile (segments); a segment that covers all N points of its tile stores the tile, any other stores its
+// partial totals in the CTA's slot (0: its first segment, 1: its last) and counts itself on the tile's counter;
+// the CTA that arrives last sums the tile's parts (StreamSink): no partial planes and no separate reduction
+// pass.  counters (one per tile) are zero at launch; slots hold 2 C tiles of totals, thread-major float4s.
+template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA>
+__global__ void __launch_bounds__(BX *BY, 2)
     direct_stream_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int width,
                          int height, int tiles_x, long long units, float *__restrict__ out,
                          float4 *__restrict__ slots, int *__restrict__ counters, bool vec, int *status,
                          unsigned long long timeout_ns, int drop_tile, const PhaseRef ref)
 {
     constexpr int T = kPointTile;
-    constexpr int NT = BX * BY;
-    constexpr int Q4 = TL * TR / 4;   // float4s of totals per thread
     static_assert(TL % 4 == 0, "rows of float4s");
     __shared__ alignas(128) int4 s_geo[2][kPointTile];
     __shared__ alignas(128) uint2 s_aux[2][kPointTile];
     __shared__ alignas(8) uint64_t s_bar[2];
-    __shared__ int s_last;
-    extern __shared__ float s_tot[];   // SMEM_TOT: TR TL floats per thread
+    __shared__ StreamSeg s_seg;
     init_point_barriers<BX, BY>(s_bar);
-    const long long C = gridDim.x, c = blockIdx.x, N = n_points;
-    const long long w0 = c * units / C, w1 = (c + 1) * units / C;
-    const int tid = threadIdx.x;
-    const long long first_tile = w0 / N;
-    // the CTA that owns unit u, and the slot in which CTA cs keeps its segment of tile t
-    auto owner = [&](long long u) { return ((u + 1) * C - 1) / units; };
-    auto slot_of = [&](long long cs, long long t) { return (cs * units / C) / N == t ? 0 : 1; };
+    const StreamSink<TL, TR, BX, BY> sink{&s_seg, slots, counters, out, units, (long long)gridDim.x,
+                                          (long long)n_points, tiles_x, width, height, vec};
     uint32_t kg = 0;
-    for (long long w = w0; w < w1;) {
-        const long long t = w / N, seg_start = w;
-        const int p0 = (int)(w - t * N);
-        const int p1 = (int)min(N, (long long)p0 + (w1 - w));
-        w += p1 - p0;
+    const long long w0 = (long long)blockIdx.x * units / gridDim.x;
+    for (long long w = w0;;) {
+        const long long w1 = ((long long)blockIdx.x + 1) * units / gridDim.x;
+        if (w >= w1) break;
+        const long long t = w / n_points;
+        const int p0 = (int)(w - t * n_points);
+        const int p1 = (int)min((long long)n_points, (long long)p0 + (w1 - w));
+        if (threadIdx.x == 0) {
+            s_seg.t = t;
+            s_seg.p0 = p0;
+            s_seg.p1 = p1;
+        }
+        __syncthreads();
         const int k0 = p0 / T, k1 = (p1 + T - 1) / T;
-        const int tm0 = (int)(t % tiles_x) * (BX * TL), tn0 = (int)(t / tiles_x) * (BY * TR);
-        const bool whole = p0 == 0 && p1 == N;
-        auto sink = [&](float(&tot)[TR][TL]) {
-            const int m0 = tm0 + (tid % BX) * TL, n0 = tn0 + (tid / BX) * TR;
-            float4 *mine = slots + (2 * c + slot_of(c, t)) * (long long)(Q4 * NT) + tid;
-            if (!whole) {
-                // partial totals to the slot, then count this segment on the tile
-#pragma unroll
-                for (int r = 0; r < TR; ++r)
-#pragma unroll
-                    for (int i = 0; i < TL; i += 4)
-                        mine[(r * TL + i) / 4 * NT] = make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
-                __threadfence();
-                __syncthreads();
-                if (tid == 0) {
-                    const long long lo = owner(t * N), hi = owner(t * N + N - 1);
-                    s_last = atomicAdd(&counters[t], 1) == (int)(hi - lo);
-                }
-                __syncthreads();
-                if (!s_last) return;
-                __threadfence();
-                // the tile's segments in CTA order, one float4 of every thread's block at a time
-                const long long lo = owner(t * N), hi = owner(t * N + N - 1);
-#pragma unroll
-                for (int q = 0; q < Q4; ++q) {
-                    const int r = q * 4 / TL, i = q * 4 % TL;
-                    float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    for (long long cs = lo; cs <= hi; ++cs) {
-                        const float4 v = cs == c ? make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3])
-                                                 : __ldcg(slots + (2 * cs + slot_of(cs, t)) * (long long)(Q4 * NT) +
-                                                          q * NT + tid);
-                        if (cs == lo) {
-                            a = v;
-                        } else {
-                            a.x += v.x;
-                            a.y += v.y;
-                            a.z += v.z;
-                            a.w += v.w;
-                        }
-                    }
-                    tot[r][i] = a.x;
-                    tot[r][i + 1] = a.y;
-                    tot[r][i + 2] = a.z;
-                    tot[r][i + 3] = a.w;
-                }
-                if (tid == 0) counters[t] = 0;
-            }
-#pragma unroll
-            for (int r = 0; r < TR; ++r) {
-                const int n = n0 + r;
-                if (n >= height || m0 >= width) continue;
-                float *row = out + (long long)n * width + m0;
-                if (vec && m0 + TL <= width) {
-#pragma unroll
-                    for (int i = 0; i < TL; i += 4)
-                        *reinterpret_cast<float4 *>(row + i) =
-                            make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < TL; ++i)
-                        if (m0 + i < width) row[i] = tot[r][i];
-                }
-            }
-        };
-        if (!direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA, SMEM_TOT>(
-                geo, aux, k0, k1, tm0, tn0, width, height, out, vec, s_geo, s_aux, s_bar, kg, status, timeout_ns,
-                (c == 0 && seg_start == w0) ? drop_tile : -1, 0, ref, s_tot, p0 - k0 * T, p1 - (k1 - 1) * T,
-                sink))
+        const int drop = (blockIdx.x == 0 && w == w0) ? drop_tile : -1;
+        if (!direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA>(
+                geo, aux, k0, k1, (int)(t % tiles_x) * (BX * TL), (int)(t / tiles_x) * (BY * TR), width, height,
+                out, vec, s_geo, s_aux, s_bar, kg, status, timeout_ns, drop, 0, ref, nullptr, p0 - k0 * T,
+                p1 - (k1 - 1) * T, sink))
             break;
-        __syncthreads();   // s_last and the point stages are reused by the next segment
+        w = s_seg.t * n_points + s_seg.p1;
+        __syncthreads();   // s_seg and the point stages are reused by the next segment
     }
 }
 
@@ -631,19 +667,18 @@ cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, cons
 
 namespace {
 
-template <int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
+template <int BX, int BY, bool SFU, bool EXTRA>
 cudaError_t direct_stream_as(int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_points, int width,
                              int height, int tiles_x, long long units, float *out, float4 *slots, int *counters,
                              bool vec, int *status, uint64_t timeout_ns, int drop_tile, const PhaseRef &ref)
 {
-    const size_t dyn = SMEM_TOT ? (size_t)kTL * kTR * BX * BY * sizeof(float) : 0;
-    direct_stream_kernel<kTL, kTR, BX, BY, SFU, EXTRA, SMEM_TOT><<<ctas, BX * BY, dyn, s>>>(
+    direct_stream_kernel<kTL, kTR, BX, BY, SFU, EXTRA><<<ctas, BX * BY, 0, s>>>(
         geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, timeout_ns, drop_tile,
         ref);
     return cudaGetLastError();
 }
 
-template <int BX, int BY, bool SMEM_TOT>
+template <int BX, int BY>
 cudaError_t direct_stream_shaped(bool sfu, bool extra, int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux,
                                  int n_points, int width, int height, int tiles_x, long long units, float *out,
                                  float4 *slots, int *counters, bool vec, int *status, uint64_t timeout_ns,
@@ -651,23 +686,22 @@ cudaError_t direct_stream_shaped(bool sfu, bool extra, int ctas, cudaStream_t s,
 {
 #define CGH_STREAM_ARGS ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, \
                         timeout_ns, drop_tile, ref
-    if (sfu && !extra) return direct_stream_as<BX, BY, true, false, SMEM_TOT>(CGH_STREAM_ARGS);
-    if (sfu) return direct_stream_as<BX, BY, true, true, SMEM_TOT>(CGH_STREAM_ARGS);
-    if (!extra) return direct_stream_as<BX, BY, false, false, SMEM_TOT>(CGH_STREAM_ARGS);
-    return direct_stream_as<BX, BY, false, true, SMEM_TOT>(CGH_STREAM_ARGS);
+    if (sfu && !extra) return direct_stream_as<BX, BY, true, false>(CGH_STREAM_ARGS);
+    if (sfu) return direct_stream_as<BX, BY, true, true>(CGH_STREAM_ARGS);
+    if (!extra) return direct_stream_as<BX, BY, false, false>(CGH_STREAM_ARGS);
+    return direct_stream_as<BX, BY, false, true>(CGH_STREAM_ARGS);
 #undef CGH_STREAM_ARGS
 }
 
-template <int BX, int BY, bool SMEM_TOT>
+template <int BX, int BY>
 int stream_resident(bool sfu)
 {
-    const size_t dyn = SMEM_TOT ? (size_t)kTL * kTR * BX * BY * sizeof(float) : 0;
     int n = 0;
     const cudaError_t e =
-        sfu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                  &n, direct_stream_kernel<kTL, kTR, BX, BY, true, false, SMEM_TOT>, BX * BY, dyn)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                  &n, direct_stream_kernel<kTL, kTR, BX, BY, false, false, SMEM_TOT>, BX * BY, dyn);
+        sfu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_stream_kernel<kTL, kTR, BX, BY, true, false>,
+                                                            BX * BY, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_stream_kernel<kTL, kTR, BX, BY, false, false>,
+                                                            BX * BY, 0);
     if (e != cudaSuccess || n < 1) {
         cudaGetLastError();
         return 1;
@@ -677,17 +711,14 @@ int stream_resident(bool sfu)
 
 }  // namespace
 
-int direct_stream_per_sm(bool sfu, const DirectShape &sh, bool smem_tot)
+int direct_stream_per_sm(bool sfu, const DirectShape &sh)
 {
-    if (sh.bx == kTallBX)
-        return smem_tot ? stream_resident<kTallBX, kTallBY, true>(sfu) : stream_resident<kTallBX, kTallBY, false>(sfu);
-    return smem_tot ? stream_resident<kBX, kBY, true>(sfu) : stream_resident<kBX, kBY, false>(sfu);
+    return sh.bx == kTallBX ? stream_resident<kTallBX, kTallBY>(sfu) : stream_resident<kBX, kBY>(sfu);
 }
 
-cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, bool smem_tot, int ctas, const int4 *geo,
-                                 const uint2 *aux, int n_points, int width, int height, float *out, float *slots,
-                                 int *counters, int *status, uint64_t timeout_ns, cudaStream_t s, int drop_tile,
-                                 const PhaseRef &ref)
+cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, const int4 *geo, const uint2 *aux,
+                                 int n_points, int width, int height, float *out, float *slots, int *counters,
+                                 int *status, uint64_t timeout_ns, cudaStream_t s, int drop_tile, const PhaseRef &ref)
 {
     const int tiles_x = (width + sh.tile_w - 1) / sh.tile_w;
     const int tiles_y = (height + sh.tile_h - 1) / sh.tile_h;
@@ -701,11 +732,8 @@ cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, bool smem_tot,
     const bool extra = ref.any();
 #define CGH_STREAM_ARGS sfu, extra, ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, sl, counters, vec, \
                         status, timeout_ns, drop_tile, ref
-    if (sh.bx == kTallBX)
-        return smem_tot ? direct_stream_shaped<kTallBX, kTallBY, true>(CGH_STREAM_ARGS)
-                        : direct_stream_shaped<kTallBX, kTallBY, false>(CGH_STREAM_ARGS);
-    return smem_tot ? direct_stream_shaped<kBX, kBY, true>(CGH_STREAM_ARGS)
-                    : direct_stream_shaped<kBX, kBY, false>(CGH_STREAM_ARGS);
+    if (sh.bx == kTallBX) return direct_stream_shaped<kTallBX, kTallBY>(CGH_STREAM_ARGS);
+    return direct_stream_shaped<kBX, kBY>(CGH_STREAM_ARGS);
 #undef CGH_STREAM_ARGS
 }
 

@@ -81,12 +81,12 @@ cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, cons
 // The direct form over a flat (pixel tile, point) work space split evenly over ctas CTAs, with the partial
 // tiles at range boundaries summed in CTA order by the last CTA to finish each tile (direct.cu): out receives
 // the hologram, no padded point is evaluated.  slots: 2 ctas x tile_w x tile_h floats (16-byte aligned);
-// counters: one int per pixel tile (zeroed by the launch).  smem_tot keeps the running totals in shared memory
-// (more CTAs per SM).  drop_tile >= 0: CTA 0 never loads that point tile of its range (test hook).
-int direct_stream_per_sm(bool sfu, const DirectShape &sh, bool smem_tot);
-cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, bool smem_tot, int ctas, const int4 *geo,
-                                 const uint2 *aux, int n_points, int width, int height, float *out, float *slots,
-                                 int *counters, int *status, uint64_t timeout_ns, cudaStream_t s, int drop_tile = -1,
+// counters: one int per pixel tile (zeroed by the launch).  drop_tile >= 0: CTA 0 never loads that point tile
+// of its range (test hook).
+int direct_stream_per_sm(bool sfu, const DirectShape &sh);
+cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, const int4 *geo, const uint2 *aux,
+                                 int n_points, int width, int height, float *out, float *slots, int *counters,
+                                 int *status, uint64_t timeout_ns, cudaStream_t s, int drop_tile = -1,
                                  const PhaseRef &ref = PhaseRef());
 
 // Complex object wave (Eq. 2, restricted form), SFU form: real part at out,

@@ -265,28 +265,29 @@ def test_quantize_hologram_vs_oracle_quantisation():
     assert ties.mean() < 0.01
 
 
-@pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate"])
 @pytest.mark.parametrize("w,h,n", [(300, 70, 2000), (1920, 1080, 777), (129, 65, 3), (640, 200, 4099)])
-def test_balanced_split_totals_and_determinism(form, w, h, n):
-    """The default layout: equal shares of the (pixel tile, point) pairs per CTA, a tile's parts summed by the
-    last CTA to finish it.  Running totals in registers or in shared memory give the same bits; two runs give
-    the same bits; the result meets the oracle and agrees with the chunked layout to rounding."""
+def test_balanced_split_cta_counts_and_determinism(w, h, n):
+    """The SFU form's default layout: equal shares of the (pixel tile, point) pairs per CTA, a tile's parts
+    summed by the last CTA to finish it.  Two runs give the same bits; other CTA counts (other part boundaries,
+    so other single-precision rounding: O(eps sqrt(N)) relative) agree within 1e-6; the result meets the oracle
+    and agrees with the chunked layout within 1e-6."""
     c = workloads.random_cloud(4400 + n, w, h, n)
     xyz, amp = _dev(c)
     outs = []
-    for totals in (1, 1, 2):
-        with Hologram(w, h, c.pitch_m, c.lambda_m, form=form) as hg:
-            hg.set_option(_lib.CGH_OPT_DIRECT_TOTALS, totals)
+    for ctas in (0, 0, 97, 1):
+        with Hologram(w, h, c.pitch_m, c.lambda_m, form="direct_sfu") as hg:
+            hg.set_option(_lib.CGH_OPT_DIRECT_CTAS, ctas)
             f = hg.point_cloud(xyz, amp)
             hg.sync()
             outs.append(f.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
-    assert np.array_equal(outs[0], outs[2])
+    for other in outs[2:]:
+        assert oracle.nrms(outs[0], other) < 1e-6
     if w * h * n <= 2e8:
         ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
         _check(outs[0], ref, c.amp)
-    chunked = _run(c, form, split=3)
-    assert oracle.nrms(outs[0], chunked) < 2e-7
+    chunked = _run(c, "direct_sfu", split=3)
+    assert oracle.nrms(outs[0], chunked) < 1e-6
 
 
 def test_balanced_split_wait_times_out_and_context_recovers():
