@@ -8,8 +8,9 @@ Workload (default): a 1920x1080 hologram of 10,000 seeded synthetic points
 display-size case of the paper's direct-calculation experiments.  One step is
 one pass of the hot path over that cloud: point preparation, the direct
 kernel (SFU cosine; the CTAs take equal shares of the (pixel tile, point)
-pairs and sum each tile's parts in the kernel), and the 8-bit quantiser.  Inputs and outputs are far below L2, so a 256 MiB
-buffer is written between timed steps to flush L2; the flush is not timed.
+pairs and sum each tile's parts in the kernel), and the 8-bit quantiser.
+Inputs and outputs are far below L2, so a 256 MiB buffer is written between
+timed steps to flush L2; the flush is not timed.
 
 Metric: G point-pixel evaluations per second (W*H*N per hologram), with
 holograms/s beside it.  Rank 0 prints one JSON line.  Under torchrun every
