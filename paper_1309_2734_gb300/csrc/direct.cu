@@ -1,50 +1,11 @@
-// a2: the direct kernel.  Every thread owns a TL x TR block of hologram pixels
-// (TL consecutive columns of TR consecutive rows) and sums every point of the
-// cloud into it, I(m, n) = sum_j A_j cos(2 pi c_j r^2) (Eq. 5, restricted form).
-//
-// Point tiles of kPointTile prepared points are staged in shared memory by
-// 1-D bulk copies (TMA engine, no multicast), double buffered behind two
-// mbarriers, and read back as warp-wide broadcasts.
-//
-// Phase.  For one point, the thread forms its corner phase G = C r^2 mod 2^64
-// (top 32 bits, exact to one unit of 2^-32 turn; plus the point's piston and
-// the reference phase when those are on), the first differences along
-// x and y, and then walks its block with the recurrence of Eqs. 6-8
-// (Section 2.2): Gamma_{k+1} = Gamma_k + delta_k, delta_{k+1} = delta_k + Delta,
-// Delta = 2 c_j, in 32-bit fixed-point turns, where wrap-around is the
-// reduction modulo one turn.  Moving down one row adds the row difference
-// (shared by all TL columns) the same way.  The drift of the walk is below
-// 1 + TL + TL^2/2 + TR + TR^2/2 units of 2^-32 turn (about 5e-8 rad for 8 x 4).
-//
-// Cosine.
-//  - SFU form: the turn is advanced by a quarter (t' = t + 1/4, folded into
-//    the corner phase), its top 23 bits become the mantissa of a float f in
-//    [1, 2) (one funnel shift), and u = K1 f - 1.5 K1 = 2 pi (t - 1/4) lies in
-//    [-pi, pi) (one FFMA).  The hardware sine (__sinf, MUFU) of u is
-//    -cos(2 pi t); the point's amplitude is negated to compensate.  The MUFU
-//    sine is exactly odd, but its error is not zero on average over an
-//    arbitrary argument grid: on the grid of the plain fl(2 pi) f - fl(3 pi),
-//    which sits a third of a step off symmetric, it averaged +1.35e-8, a
-//    per-term bias that grows linearly with N (NRMS 1.6e-5 at N = 10^6).  K1
-//    is therefore 2 pi rounded to a float whose 1.5 multiple is exact, so the
-//    FFMA returns exactly RN((f - 1.5) K1): the argument grid is symmetric
-//    about zero and the odd error cancels.  K1 is 1.04e-7 above 2 pi (a
-//    zero-mean phase-scale error below 3.3e-7 rad).  The corner-phase bias
-//    also rounds the 23-bit truncation to nearest.  (Moving an eighth of the
-//    terms to a sine polynomial on the FMA pipe was measured: the MUFU pipe
-//    went from 90 % to 74 % busy but issue and ALU pressure grew and the kernel
-//    got 6 % slower, so every term uses the MUFU.)
-//  - accurate form: the turn, read as a signed 32-bit integer, converts to
-//    t in [-1/2, 1/2) and cos(2 pi t) is a degree-12 even polynomial
-//    (cospoly.h), all on the FMA pipe.
-//
-// Accumulation is two-level: each point tile is summed into fresh partials
-// that are then added into the running totals, which keeps single-precision
-// rounding error at N = 10^6 well below 1e-5 relative.
+// a2: the direct kernels (device code of the term and of a unit of work in
+// direct_dev.cuh): one hologram in the chunked layout (pixel tile x point
+// chunk, partial planes), in the balanced layout (equal shares of the (pixel
+// tile, point) pairs, a tile's parts summed by the last CTA to finish it), the
+// complex object wave, and the per-form batch kernels.
 #include <type_traits>
 
-#include "cospoly.h"
-#include "device_util.cuh"
+#include "direct_dev.cuh"
 #include "host_util.h"
 #include "kernels.h"
 
@@ -52,343 +13,7 @@ namespace cgh {
 
 namespace {
 
-// 2 pi rounded up to the nearest float whose mantissa is a multiple of 4,
-// so that 1.5 K1 is a float too (0x40c90fdc and 0x4116cbe5)
-constexpr float kK1 = 6.28318595886230469f;
-constexpr float kK0 = 9.42477893829345703f;   // exactly 1.5 * kK1
-// 2^30: a quarter turn; 2^8 rounds the 23-bit truncation to nearest
-constexpr uint32_t kSfuBias = (1u << 30) + 256u;
-
-// Evaluation modes of one (point, pixel) term.
-enum { kEvalSfu = 0, kEvalAccurate = 1 };
-
-template <int MODE>
-__device__ __forceinline__ float cos_term(uint32_t g)
-{
-    if constexpr (MODE == kEvalSfu) {
-        const float f = __uint_as_float(__funnelshift_r(g, 0x7fu, 9));   // 1 + top23(g) 2^-23
-        return __sinf(fmaf(f, kK1, -kK0));                              // = -cos(2 pi t)
-    } else {
-        const float t = (float)(int)g * 2.3283064365386963e-10f;        // signed turn, [-1/2, 1/2)
-        const float u = t * t;
-        float c = CGH_COSPOLY_6;
-        c = fmaf(c, u, CGH_COSPOLY_5);
-        c = fmaf(c, u, CGH_COSPOLY_4);
-        c = fmaf(c, u, CGH_COSPOLY_3);
-        c = fmaf(c, u, CGH_COSPOLY_2);
-        c = fmaf(c, u, CGH_COSPOLY_1);
-        c = fmaf(c, u, CGH_COSPOLY_0);
-        return c;                                                        // = cos(2 pi t)
-    }
-}
-
-// The reference phase seen by one thread: its value at the thread's corner
-// pixel and its change per column and per row (all 2^-32 turn).  Added to a
-// point's corner phase and first differences, it costs three additions per
-// point, none per term; the kernels without piston and reference (EXTRA =
-// false) skip even those (measured 3 % on the SFU form).
-struct PixelRef {
-    uint32_t g, dx, dy;
-};
-
-__device__ __forceinline__ PixelRef pixel_ref(const PhaseRef &r, int m0, int n0)
-{
-    return PixelRef{ref_turn(r, m0, n0), ref_step(r.kx), ref_step(r.ky)};
-}
-
-// e^{i 2 pi t} of a fixed-point turn t from the hardware sine on the symmetric argument grid of the SFU
-// amplitude form: cos(2 pi t) as there, sin(2 pi t) = sin(v) with v = K1 (f2 - 1.5) from the turn advanced by a
-// half (f2 - 1 = t + 1/2), so the MUFU's odd error averages out in both parts.
-__device__ __forceinline__ float2 cis_sfu(uint32_t t)
-{
-    const float f = __uint_as_float(__funnelshift_r(t + kSfuBias, 0x7fu, 9));
-    const float f2 = __uint_as_float(__funnelshift_r(t + kSfuBias + (1u << 30), 0x7fu, 9));
-    return make_float2(-__sinf(fmaf(f, kK1, -kK0)), __sinf(fmaf(f2, kK1, -kK0)));
-}
-
-__device__ __forceinline__ float2 cmul_f(float2 x, float2 y)
-{
-    return make_float2(fmaf(x.x, y.x, -x.y * y.y), fmaf(x.x, y.y, x.y * y.x));
-}
-
-// The point's second difference D (2^-32 turn).  v = e^{i 2 pi D}, the same for every pixel, is computed once per
-// point and CTA when its tile arrives, with the accurate single-precision sine and cosine: the term at column i
-// carries v's error i (i - 1) / 2 times over (point_terms_wave).
-template <bool EXTRA>
-__device__ __forceinline__ uint32_t wave_second_difference(const int4 q, const uint2 w)
-{
-    return EXTRA ? __funnelshift_l((uint32_t)q.w, (uint32_t)q.z, 1) : w.x;   // 2 C with the piston, else aux.x
-}
-
-// D as a signed turn has up to 32 significant bits, more than a float holds: its top 24 bits and its low 8 bits
-// are each exact in single precision, and v = e^{i 2 pi D_hi} e^{i 2 pi D_lo} (the plain conversion dropped up to
-// 2^-25 turn, which column i carries i (i - 1) / 2 times).
-__device__ __forceinline__ float2 wave_rotation(uint32_t D)
-{
-    float sh, ch, sl, cl;
-    sincospif((float)(int)(D & 0xffffff00u) * (1.0f / 2147483648.0f), &sh, &ch);   // [-1, 1): twice the turn
-    sincospif((float)(D & 0xffu) * (1.0f / 2147483648.0f), &sl, &cl);
-    return cmul_f(make_float2(ch, sh), make_float2(cl, sl));
-}
-
-// Adds one point's terms of the complex object wave (Eq. 2, restricted form) to a thread's TL x TR block.
-// Along a row the phase is quadratic in the column (Eqs. 6-8): first difference d + i D at column i, the same
-// on every row.  So e^{i 2 pi t} is taken from the hardware only at each row's first column, and for the
-// column steps w_0 = e^{i 2 pi d} and v = e^{i 2 pi D}; then w_i = w_(i-1) v and the row walks by
-// z_i = z_(i-1) w_(i-1): TR + 1 sines and cosines per point and thread (v once per point and CTA) instead of
-// TL TR, the rest complex products on the FMA pipe.  The term at column i carries the row anchor's error, i times
-// w_0's and i (i - 1) / 2 times v's, and the chains restart at every point and row: about 1.3 10^-6 of the field
-// (NRMS) against 4 10^-7 with two hardware sines per term (2.6 10^-6 with v from the hardware; 7 10^-7, 15 %
-// slower, with the chains restarted at every half row).
-template <int TL, int TR, bool EXTRA>
-__device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, const float2 v, int m0, int n0,
-                                                 const PixelRef &pr, float (&pre)[TR][TL], float (&pim)[TR][TL])
-{
-    const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
-    const uint32_t dx = (uint32_t)(m0 - q.x);
-    const uint32_t dy = (uint32_t)(n0 - q.y);
-    const uint32_t r2 = dx * dx + dy * dy;
-    const uint32_t r2x = r2 + 2u * dx + 1u;
-    const uint32_t r2y = r2 + 2u * dy + 1u;
-    const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
-    uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
-    uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
-    uint32_t g = c0;
-    const uint32_t D = wave_second_difference<EXTRA>(q, w);
-    if constexpr (EXTRA) {   // piston (aux.x) and reference
-        d += pr.dx;
-        e += pr.dy;
-        g += w.x + pr.g;
-    }
-    const float a = __uint_as_float(w.y);
-    float2 st[TL - 1];   // e^{i 2 pi (d + i D)}: the step from column i to i + 1
-    st[0] = cis_sfu(d);
-#pragma unroll
-    for (int i = 1; i < TL - 1; ++i) st[i] = cmul_f(st[i - 1], v);
-#pragma unroll
-    for (int r = 0; r < TR; ++r) {
-        float2 z = cis_sfu(g);
-        pre[r][0] = fmaf(a, z.x, pre[r][0]);
-        pim[r][0] = fmaf(a, z.y, pim[r][0]);
-#pragma unroll
-        for (int i = 1; i < TL; ++i) {
-            z = cmul_f(z, st[i - 1]);
-            pre[r][i] = fmaf(a, z.x, pre[r][i]);
-            pim[r][i] = fmaf(a, z.y, pim[r][i]);
-        }
-        if (r + 1 < TR) {
-            g += e;
-            e += D;
-        }
-    }
-}
-
-// Adds one point's terms to a thread's TL x TR block (corner m0, n0).
-template <int TL, int TR, int MODE, bool EXTRA>
-__device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
-                                            float (&part)[TR][TL])
-{
-    constexpr bool kSfuSign = MODE != kEvalAccurate;
-    const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
-    const uint32_t dx = (uint32_t)(m0 - q.x);
-    const uint32_t dy = (uint32_t)(n0 - q.y);
-    const uint32_t r2 = dx * dx + dy * dy;          // < 2^32, exact
-    const uint32_t r2x = r2 + 2u * dx + 1u;         // (dx+1)^2 + dy^2
-    const uint32_t r2y = r2 + 2u * dy + 1u;         // dx^2 + (dy+1)^2
-    const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
-    uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
-    uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
-    uint32_t g0 = c0, D = w.x;
-    if constexpr (EXTRA) {   // piston (aux.x) and reference at the corner; 2 C formed from C
-        d += pr.dx;
-        e += pr.dy;
-        g0 += w.x + pr.g;
-        D = __funnelshift_l(clo, chi, 1);
-    }
-    const float a = kSfuSign ? -__uint_as_float(w.y) : __uint_as_float(w.y);
-    uint32_t g[TL];
-    g[0] = g0 + (kSfuSign ? kSfuBias : 0u);
-#pragma unroll
-    for (int i = 1; i < TL; ++i) {
-        g[i] = g[i - 1] + d;
-        d += D;
-    }
-#pragma unroll
-    for (int r = 0; r < TR; ++r) {
-#pragma unroll
-        for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<MODE>(g[i]), part[r][i]);
-        if (r + 1 < TR) {
-#pragma unroll
-            for (int i = 0; i < TL; ++i) g[i] += e;
-            e += D;
-        }
-    }
-}
-
-// One unit of work: point tiles [t_begin, t_end) of one cloud into one
-// CTA-sized pixel tile with corner (tile_m0, tile_n0).  kg counts the point
-// tiles this CTA consumed before (stage and mbarrier parity carry across units).
-// PLANES = 1: the amplitude hologram; PLANES = 2: the complex object wave, real
-// part at dst and imaginary part at dst + im_offset (SFU form only).
-// SMEM_TOT: the running totals live in shared memory (s_tot, index-major: entry (c, r, i) of thread tid at
-// ((c TR + r) TL + i) BX BY + tid, so a warp's accesses are consecutive words) instead of registers, which leaves
-// the registers to the point tile's partial sums of a taller thread block.
-// The points of the unit are those of tiles [t_begin, t_end), less the first p_first points of the first tile
-// and the points from p_last_end on of the last one.  Sink: PlainStore writes the totals to dst; any other sink
-// is called as sink(tot) with the thread's TR x TL totals of plane 0 (the amplitude hologram only).
-struct PlainStore {};
-
-template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1, bool EXTRA = false, bool SMEM_TOT = false,
-          class Sink = PlainStore>
-__device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const uint2 *__restrict__ aux,
-                                            int t_begin, int t_end, int tile_m0, int tile_n0, int width,
-                                            int height, float *__restrict__ dst, bool vec, int4 (*s_geo)[kPointTile],
-                                            uint2 (*s_aux)[kPointTile], uint64_t *s_bar, uint32_t &kg, int *status,
-                                            unsigned long long timeout_ns, int drop = -1, long long im_offset = 0,
-                                            const PhaseRef &ref = PhaseRef(), float *s_tot = nullptr,
-                                            int p_first = 0, int p_last_end = kPointTile, Sink sink = Sink())
-{
-    constexpr int T = kPointTile;
-    constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
-    const int tid = threadIdx.x;
-    const int lx = tid % BX, ly = tid / BX;
-    const int m0 = tile_m0 + lx * TL;
-    const int n0 = tile_n0 + ly * TR;
-    const int nt = t_end - t_begin;
-    const PixelRef pr = pixel_ref(ref, m0, n0);
-
-    auto issue = [&](int k) {
-        if (k == drop) return;   // test hook: this tile's barrier is never completed
-        const int st = (int)((kg + (uint32_t)k) & 1u);
-        const long long first = (long long)(t_begin + k) * T;
-        mbar_arrive_expect_tx(&s_bar[st], kTileBytes);
-        bulk_copy_g2s(&s_geo[st][0], geo + first, T * sizeof(int4), &s_bar[st]);
-        bulk_copy_g2s(&s_aux[st][0], aux + first, T * sizeof(uint2), &s_bar[st]);
-    };
-    if (tid == 0) {
-        if (nt > 0) issue(0);
-        if (nt > 1) issue(1);
-    }
-
-    constexpr int NT = BX * BY;
-    auto tidx = [&](int c, int r, int i) { return ((c * TR + r) * TL + i) * NT + tid; };
-    float tot[PLANES][TR][TL];
-#pragma unroll
-    for (int c = 0; c < PLANES; ++c)
-#pragma unroll
-        for (int r = 0; r < TR; ++r)
-#pragma unroll
-            for (int i = 0; i < TL; ++i) {
-                if constexpr (SMEM_TOT) s_tot[tidx(c, r, i)] = 0.0f;
-                else tot[c][r][i] = 0.0f;
-            }
-
-    bool ok = true;
-    for (int k = 0; k < nt; ++k) {
-        const uint32_t kk = kg + (uint32_t)k;
-        const int st = (int)(kk & 1u);
-        const bool arrived = mbar_wait(&s_bar[st], (kk >> 1) & 1u, timeout_ns);
-        if (__syncthreads_or(!arrived)) {
-            if (tid == 0) {
-                atomicOr(status, kStatusTimeout);
-                // wait (bounded) for the other tile copy this unit may still have in flight
-                if (k + 1 < nt && k + 1 != drop) {
-                    const uint32_t kn = kk + 1u;
-                    mbar_wait(&s_bar[kn & 1u], (kn >> 1) & 1u, timeout_ns);
-                }
-            }
-            __syncthreads();
-            ok = false;
-            break;
-        }
-        float part[PLANES][TR][TL];
-#pragma unroll
-        for (int c = 0; c < PLANES; ++c)
-#pragma unroll
-            for (int r = 0; r < TR; ++r)
-#pragma unroll
-                for (int i = 0; i < TL; ++i) part[c][r][i] = 0.0f;
-
-        const int4 *sg = s_geo[st];
-        const uint2 *sa = s_aux[st];
-        const int p_lo = k == 0 ? p_first : 0;
-        const int p_hi = k == nt - 1 ? p_last_end : T;
-        if constexpr (PLANES == 2) {
-            __shared__ float2 s_rot[T];   // e^{i 2 pi D} of the tile's points, once each per CTA
-            for (int p = tid; p < T; p += BX * BY) s_rot[p] = wave_rotation(wave_second_difference<EXTRA>(sg[p], sa[p]));
-            __syncthreads();
-#pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p)
-                point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], s_rot[p], m0, n0, pr, part[0], part[PLANES - 1]);
-        } else if (p_lo == 0 && p_hi == T) {   // a whole tile: the loop with a fixed trip count
-            constexpr int M = SFU ? kEvalSfu : kEvalAccurate;
-#pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, M, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
-        } else {
-            constexpr int M = SFU ? kEvalSfu : kEvalAccurate;
-#pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p) point_terms<TL, TR, M, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
-        }
-#pragma unroll
-        for (int c = 0; c < PLANES; ++c)
-#pragma unroll
-            for (int r = 0; r < TR; ++r)
-#pragma unroll
-                for (int i = 0; i < TL; ++i) {
-                    if constexpr (SMEM_TOT) s_tot[tidx(c, r, i)] += part[c][r][i];
-                    else tot[c][r][i] += part[c][r][i];
-                }
-
-        __syncthreads();   // every thread is done with stage st
-        if (tid == 0 && k + 2 < nt) issue(k + 2);
-    }
-    kg += (uint32_t)nt;
-    if (!ok) return false;
-    if constexpr (SMEM_TOT) {
-#pragma unroll
-        for (int c = 0; c < PLANES; ++c)
-#pragma unroll
-            for (int r = 0; r < TR; ++r)
-#pragma unroll
-                for (int i = 0; i < TL; ++i) tot[c][r][i] = s_tot[tidx(c, r, i)];
-    }
-    if constexpr (!std::is_same<Sink, PlainStore>::value) {
-        static_assert(PLANES == 1, "sinks take the amplitude hologram");
-        sink(tot[0]);
-        return true;
-    }
-
-#pragma unroll
-    for (int c = 0; c < PLANES; ++c)
-#pragma unroll
-        for (int r = 0; r < TR; ++r) {
-            const int n = n0 + r;
-            if (n >= height || m0 >= width) continue;
-            float *row = dst + (long long)c * im_offset + (long long)n * width + m0;
-            if (vec && m0 + TL <= width) {
-#pragma unroll
-                for (int i = 0; i < TL; i += 4)
-                    *reinterpret_cast<float4 *>(row + i) =
-                        make_float4(tot[c][r][i], tot[c][r][i + 1], tot[c][r][i + 2], tot[c][r][i + 3]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < TL; ++i)
-                    if (m0 + i < width) row[i] = tot[c][r][i];
-            }
-        }
-    return true;
-}
-
-template <int BX, int BY>
-__device__ __forceinline__ void init_point_barriers(uint64_t *s_bar)
-{
-    if (threadIdx.x == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-}
+using namespace dev;
 
 // One hologram: blockIdx.x = pixel tile, blockIdx.y = point chunk (its own output plane).
 template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA>

@@ -42,47 +42,15 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "device_util.cuh"
+#include "gemm_dev.cuh"
 #include "host_util.h"
 #include "kernels.h"
-#include "tcgen05.cuh"
 
 namespace cgh {
 
 namespace {
 
-constexpr int kBM = 128;
-constexpr int kBK = 64;   // 64 16-bit elements = one 128-byte swizzle row
-constexpr int kGemmThreads = 192;
-// Shared memory left for the operand ring: the 227 KB a CTA may use, less the 1024-byte alignment slack and the
-// barriers.
-constexpr int kStageRoom = 232448 - 1024 - 256;
-
-template <int BN>
-struct GemmCfg {
-    static constexpr int kStageA = kBM * kBK * 2;
-    static constexpr int kStageB = BN * kBK * 2;
-    static constexpr int kStageBytes = kStageA + kStageB;
-    static constexpr int kStages = kStageRoom / kStageBytes > 8 ? 8 : kStageRoom / kStageBytes;
-    static constexpr int kAccStride = BN <= 128 ? 128 : 256;   // TMEM columns between the two accumulators
-    static constexpr int kTmemCols = 2 * kAccStride;
-    static constexpr int kBarrierBytes = 256;
-    static constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarrierBytes;
-    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
-    static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte alignment");
-};
-
-// Everything one unit of work needs.
-struct UnitInfo {
-    const CUtensorMap *mp, *mq, *mpl, *mql;
-    float *out;                  // output (or partial) plane of this unit
-    const float *amp_max;
-    int tm, tn, kb0, kb1, bn, passes, kc, height, width;
-    uint32_t idesc;
-    bool vec;
-    bool accumulate;             // add to the output already there (later point chunks)
-    bool trans;                  // A = Q, B = P: accumulator rows are hologram columns
-};
+using namespace dev;
 
 // One hologram: everything in the (grid-constant) kernel parameters.
 struct alignas(64) SingleUnits {
@@ -96,9 +64,20 @@ struct alignas(64) SingleUnits {
     int accumulate;
     int trans;
 
-    __device__ int begin() const { return blockIdx.x; }
-    __device__ int end() const { return tiles_m * tiles_n * splits; }
-    __device__ int step() const { return gridDim.x; }
+    // every role walks units blockIdx.x, blockIdx.x + gridDim.x, ...
+    struct Cursor {
+        int u;
+    };
+    __device__ Cursor start() const { return Cursor{(int)blockIdx.x}; }
+    __device__ bool next(int, Cursor &c, UnitInfo &x) const
+    {
+        if (c.u >= tiles_m * tiles_n * splits) return false;
+        x = get(c.u);
+        c.u += gridDim.x;
+        return true;
+    }
+    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
+    __device__ void abort(Cursor &, unsigned long long) const {}
     __device__ UnitInfo get(int u) const
     {
         const int n_tiles = tiles_m * tiles_n;
@@ -133,9 +112,20 @@ struct BatchUnits {
     const int *cta_off;     // [ctas + 1]
     const int2 *units;      // {job, tile}
 
-    __device__ int begin() const { return cta_off[blockIdx.x]; }
-    __device__ int end() const { return cta_off[blockIdx.x + 1]; }
-    __device__ int step() const { return 1; }
+    // every role walks the CTA's own list
+    struct Cursor {
+        int i;
+    };
+    __device__ Cursor start() const { return Cursor{cta_off[blockIdx.x]}; }
+    __device__ bool next(int, Cursor &c, UnitInfo &x) const
+    {
+        if (c.i >= cta_off[blockIdx.x + 1]) return false;
+        x = get(c.i);
+        ++c.i;
+        return true;
+    }
+    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
+    __device__ void abort(Cursor &, unsigned long long) const {}
     __device__ UnitInfo get(int i) const
     {
         const int2 w = units[i];
@@ -171,27 +161,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     using C = GemmCfg<BN_MAX>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::kStages * C::kStageBytes);
-    uint64_t *empty = full + C::kStages;
-    uint64_t *tfull = empty + C::kStages;   // [2]
-    uint64_t *tempty = tfull + 2;           // [2]
-    uint64_t *drain = tempty + 2;           // [1]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
-
+    const GemmBars bars = gemm_bars<C>(smem);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars.drain + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C::kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        mbar_init(&tfull[0], 1);
-        mbar_init(&tfull[1], 1);
-        mbar_init(&tempty[0], 128);
-        mbar_init(&tempty[1], 128);
-        mbar_init(drain, 1);
-        fence_barrier_init();
-    }
+    if (threadIdx.x == 0) gemm_init_barriers<C>(bars);
     if (warp == 1) {
         tmem_alloc(tmem_slot, C::kTmemCols);
         tmem_relinquish();
@@ -200,242 +173,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-
     if (warp == 0) {
-        if (lane == 0) {
-            // ---------------- TMA producer ----------------
-            uint32_t it = 0;
-            bool ok = true;
-            for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
-                const UnitInfo x = src.get(u);
-                const uint32_t stage_bytes = (uint32_t)(C::kStageA + x.bn * kBK * 2);
-                for (int c0 = x.kb0; c0 < x.kb1 && ok; c0 += x.kc) {
-                    const int c1 = min(x.kb1, c0 + x.kc);
-                    for (int pass = 0; pass < x.passes && ok; ++pass) {
-                        const CUtensorMap *ma = (pass == 2) ? x.mpl : x.mp;
-                        const CUtensorMap *mb = (pass == 1) ? x.mql : x.mq;
-                        for (int kb = c0; kb < c1; ++kb, ++it) {
-                            const int s = (int)(it % C::kStages);
-                            const uint32_t ph = (it / C::kStages) & 1u;
-                            if (!mbar_wait(&empty[s], ph ^ 1u, timeout_ns)) {
-                                atomicOr(status, kStatusTimeout);
-                                ok = false;
-                                break;
-                            }
-                            uint8_t *sa = smem + s * C::kStageBytes;
-                            mbar_arrive_expect_tx(&full[s], stage_bytes);
-                            tma_load_2d(sa, ma, &full[s], kb * kBK, x.tm * kBM);
-                            tma_load_2d(sa + C::kStageA, mb, &full[s], kb * kBK, x.tn * x.bn);
-                        }
-                    }
-                }
-            }
-            if (!ok) {
-                // drain: wait (bounded) for the loads of the last kStages issues
-                for (uint32_t j = (it > (uint32_t)C::kStages ? it - C::kStages : 0); j < it; ++j)
-                    mbar_wait(&full[j % C::kStages], (j / C::kStages) & 1u, timeout_ns);
-            }
-        }
+        if (lane == 0) gemm_producer<C>(src, smem, bars, status, timeout_ns);
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer ----------------
-            uint32_t it = 0;
-            uint32_t uses[2] = {0u, 0u};   // chunks each accumulator has received
-            int nb = 0;                    // accumulator of the next unit's first chunk
-            bool ok = true;
-            for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
-                const UnitInfo x = src.get(u);
-                const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
-                const int tb = nb;   // the unit's total
-                for (int c = 0; c < nch && ok; ++c) {
-                    const int c0 = x.kb0 + c * x.kc, c1 = min(x.kb1, c0 + x.kc);
-                    const int b = c == 0 ? tb : 1 - tb;
-                    const uint32_t uph = uses[b] & 1u;
-                    ++uses[b];
-                    if (!mbar_wait(&tempty[b], uph ^ 1u, timeout_ns)) {
-                        atomicOr(status, kStatusTimeout);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + (uint32_t)(b * C::kAccStride);
-                    uint32_t acc = 0;
-                    for (int pass = 0; pass < x.passes && ok; ++pass) {
-                        for (int kb = c0; kb < c1; ++kb, ++it) {
-                            const int s = (int)(it % C::kStages);
-                            const uint32_t ph = (it / C::kStages) & 1u;
-                            if (!mbar_wait(&full[s], ph, timeout_ns)) {
-                                atomicOr(status, kStatusTimeout);
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
-                            const uint32_t a_addr = smem_addr(smem + s * C::kStageBytes);
-                            const uint64_t adesc = sw128_kmajor_desc(a_addr);
-                            const uint64_t bdesc = sw128_kmajor_desc(a_addr + C::kStageA);
-#pragma unroll
-                            for (int kk = 0; kk < kBK / 16; ++kk) {
-                                // +32 bytes per K step of 16 elements inside the swizzled row
-                                umma_f16(d_tmem, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), x.idesc,
-                                         acc);
-                                acc = 1;
-                            }
-                            umma_commit(&empty[s]);
-                        }
-                    }
-                    if (!ok) break;
-                    // an empty K range issues no MMA; the epilogue then writes zeros itself
-                    umma_commit(&tfull[b]);
-                }
-                nb = 1 - tb;   // the other accumulator is released first
-            }
-            // every MMA issued so far completes before TMEM is freed
-            umma_commit(drain);
-            mbar_wait(drain, 0, timeout_ns);
-        }
+        if (lane == 0) gemm_mma<C>(src, smem, bars, tmem_base, status, timeout_ns);
     } else {
-        // ---------------- epilogue ----------------
-        const int q = warp & 3;   // TMEM lane quarter this warp may access
-        const int row_in_tile = q * 32 + lane;
-        const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
-        uint32_t uses[2] = {0u, 0u};
-        int nb = 0;
-        bool ok = true;
-        for (int u = src.begin(); u < src.end() && ok; u += src.step()) {
-            const UnitInfo x = src.get(u);
-            float unscale = 1.0f;
-            if (x.amp_max != nullptr) {
-                const float m = *x.amp_max;
-                if (m > 0.0f) unscale = m;
-            }
-            const bool empty_range = x.kb1 <= x.kb0;
-            const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
-            const int row = x.tm * kBM + row_in_tile;
-            float *dst = x.out + (long long)row * x.width;
-            const int tb = nb;
-            nb = 1 - tb;
-            const uint32_t taddr = lane_base + (uint32_t)(tb * C::kAccStride);          // the unit's total
-            const uint32_t xaddr = lane_base + (uint32_t)((1 - tb) * C::kAccStride);    // its later chunks
-            if (!mbar_wait(&tfull[tb], uses[tb] & 1u, timeout_ns)) {
-                atomicOr(status, kStatusTimeout);
-                ok = false;
-                break;
-            }
-            ++uses[tb];
-            tc_fence_after();
-            for (int c = 1; c < nch; ++c) {
-                // total += chunk c, in FP32 and chunk order
-                if (!mbar_wait(&tfull[1 - tb], uses[1 - tb] & 1u, timeout_ns)) {
-                    atomicOr(status, kStatusTimeout);
-                    ok = false;
-                    break;
-                }
-                ++uses[1 - tb];
-                tc_fence_after();
-#pragma unroll 1
-                for (int cc = 0; cc < x.bn; cc += 16) {
-                    uint32_t a[16], t[16];
-                    tmem_ld16(xaddr + (uint32_t)cc, a);
-                    tmem_ld16(taddr + (uint32_t)cc, t);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) t[i] = __float_as_uint(__uint_as_float(t[i]) + __uint_as_float(a[i]));
-                    tmem_st16(taddr + (uint32_t)cc, t);
-                }
-                tmem_st_wait();
-                tc_fence_before();
-                mbar_arrive(&tempty[1 - tb]);
-            }
-            if (!ok) break;
-            // the tile to global memory: stored, or added to what earlier point chunks left there
-            const bool first = !x.accumulate;
-            if (x.trans) {
-                // accumulator row = hologram column m (the warp's 32 lanes hold 32
-                // consecutive m), accumulator column = hologram row n: every store
-                // instruction writes 128 contiguous bytes of out[n][m0 .. m0 + 31]
-                const int m = row;
-                const bool in_m = m < x.width;
-#pragma unroll 1
-                for (int cc = 0; cc < x.bn; cc += 32) {
-                    const int ncol = min(32, x.bn - cc);   // 16 or 32
-                    const int n0 = x.tn * x.bn + cc;
-                    float old[32];
-                    if (!first && in_m) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            old[i] = (i < ncol && n0 + i < x.height) ? x.out[(long long)(n0 + i) * x.width + m] : 0.0f;
-                    }
-                    uint32_t r[2][16];
-                    tmem_ld16(taddr + (uint32_t)cc, r[0]);
-                    if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
-                    tmem_ld_wait();
-                    if (!in_m) continue;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (i >= ncol || n0 + i >= x.height) continue;
-                        float v = empty_range ? 0.0f : __uint_as_float(r[i >> 4][i & 15]) * unscale;
-                        if (!first) v += old[i];
-                        x.out[(long long)(n0 + i) * x.width + m] = v;
-                    }
-                }
-            } else {
-#pragma unroll 1
-                for (int cc = 0; cc < x.bn; cc += 64) {
-                    // 64 columns per round (four groups of 16): the previous partial sums
-                    // (if any) are loaded first, all at once, so the global-memory latency is
-                    // paid once per 64 columns and overlaps the tensor-memory reads
-                    const int ncol = min(64, x.bn - cc);   // a multiple of 16
-                    const int col0 = x.tn * x.bn + cc;
-                    const bool in_row = row < x.height;
-                    bool gvec[4];
-#pragma unroll
-                    for (int gq = 0; gq < 4; ++gq)
-                        gvec[gq] = x.vec && in_row && gq * 16 < ncol && col0 + gq * 16 + 16 <= x.width;
-                    float4 old[16];
-#pragma unroll
-                    for (int gq = 0; gq < 4; ++gq)
-                        if (!first && gvec[gq]) {
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                old[4 * gq + i] = reinterpret_cast<const float4 *>(dst + col0 + 16 * gq)[i];
-                        }
-                    uint32_t r[4][16];
-                    tmem_ld16(taddr + (uint32_t)cc, r[0]);
-                    if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
-                    if (ncol > 32) tmem_ld16(taddr + (uint32_t)(cc + 32), r[2]);
-                    if (ncol > 48) tmem_ld16(taddr + (uint32_t)(cc + 48), r[3]);
-                    tmem_ld_wait();
-                    if (!in_row) continue;
-#pragma unroll
-                    for (int gq = 0; gq < 4; ++gq) {
-                        if (gq * 16 >= ncol) continue;
-                        float v[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = empty_range ? 0.0f : __uint_as_float(r[gq][i]) * unscale;
-                        float *d16 = dst + col0 + 16 * gq;
-                        if (gvec[gq]) {
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                float4 w = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                                if (!first) {
-                                    w.x += old[4 * gq + i].x;
-                                    w.y += old[4 * gq + i].y;
-                                    w.z += old[4 * gq + i].z;
-                                    w.w += old[4 * gq + i].w;
-                                }
-                                reinterpret_cast<float4 *>(d16)[i] = w;
-                            }
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                if (col0 + 16 * gq + i < x.width) d16[i] = first ? v[i] : d16[i] + v[i];
-                        }
-                    }
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&tempty[tb]);
-        }
+        gemm_epilogue<C>(src, bars, tmem_base, warp, lane, status, timeout_ns);
     }
     __syncthreads();
     if (warp == 1) {
