@@ -118,10 +118,14 @@ enum {
                                    piston (CGH_PHASE_FRESNEL_PISTON): points of equal C may differ in depth. */
     CGH_OPT_PHASE_MODEL = 13,   /* CGH_PHASE_* above; default CGH_PHASE_FRESNEL.  cgh_batch supports the default
                                    only (CGH_ENOTSUP otherwise). */
-    CGH_OPT_DIRECT_CTAS = 14    /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the CTAs that share
+    CGH_OPT_DIRECT_CTAS = 14,   /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the CTAs that share
                                    the (pixel tile, point) pairs; 0 = automatic (up to three per resident CTA slot,
                                    each with at least 1024 points; the hardware schedules those beyond the resident
                                    ones as others finish) */
+    CGH_OPT_BATCH_MODE = 15     /* cgh_batch: 0 = one persistent launch for the whole batch (default; GEMM units on
+                                   the tensor cores beside point preparation, factor generation and direct units
+                                   on the same SMs); 1 = per-kind launches (preparation and factors per instance,
+                                   then one GEMM launch and one direct launch per direct form) */
 };
 
 typedef struct cgh_ctx cgh_ctx;
@@ -274,6 +278,16 @@ typedef struct {
  * shapes and buffers replay it.
  */
 int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
+
+/*
+ * The forms (CGH_DIRECT_SFU ... CGH_GEMM_SPLIT16) the last plan of cgh_batch
+ * chose, one per instance in the order given (instances without points report
+ * CGH_DIRECT_SFU and compute nothing).  Writes min(count, max_entries) entries
+ * to the host array forms and the count to *n_entries; 0 entries before the
+ * first cgh_batch call.  Host only: no device work.  Not part of the paper's
+ * method: it reports the autotuner's choices.
+ */
+int cgh_batch_forms(cgh_ctx *ctx, int *forms, int max_entries, int *n_entries);
 
 /*
  * Calibrates the autotuner on this device: times every form on three small

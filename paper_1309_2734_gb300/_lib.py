@@ -33,13 +33,14 @@ CGH_OPT_GEMM_TRANSPOSE = 11
 CGH_OPT_GEMM_GROUP = 12
 CGH_OPT_PHASE_MODEL = 13
 CGH_OPT_DIRECT_CTAS = 14
+CGH_OPT_BATCH_MODE = 15
 CGH_PHASE_FRESNEL, CGH_PHASE_FRESNEL_PISTON, CGH_PHASE_SPHERICAL = 0, 1, 2
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
            "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
            "cgh_autotune", "cgh_wave", "cgh_set_reference", "cgh_fresnel", "cgh_wrp_record", "cgh_wrp",
-           "cgh_measure_mufu")
+           "cgh_measure_mufu", "cgh_batch_forms")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_point_cloud_host": ([vp, vp, vp, i64, vp], ci),
             "cgh_factors": ([vp, vp, vp, i64, ci, vp, vp, i64], ci),
             "cgh_batch": ([vp, ctypes.POINTER(cgh_instance), ci], ci),
+            "cgh_batch_forms": ([vp, ctypes.POINTER(ci), ci, ctypes.POINTER(ci)], ci),
             "cgh_quantize8": ([vp, vp, i64, ci, vp], ci),
             "cgh_profile_read": ([vp, ctypes.POINTER(cgh_kernel_time), ci, ctypes.POINTER(ci), ci], ci),
             "cgh_sync": ([vp], ci),
@@ -165,6 +167,14 @@ def cgh_factors(ctx: int, d_xyz: int, d_amp: int, n_points: int, dtype_form: int
 def cgh_batch(ctx: int, instances) -> int:
     arr = (cgh_instance * len(instances))(*instances)
     return load().cgh_batch(ctx, arr, len(instances))
+
+
+def cgh_batch_forms(ctx: int, max_entries: int = 4096) -> list:
+    """The forms the last cgh_batch plan chose, one per instance."""
+    buf = (ctypes.c_int * max(1, max_entries))()
+    n = ctypes.c_int(0)
+    check(load().cgh_batch_forms(ctx, buf, max_entries, ctypes.byref(n)), "cgh_batch_forms")
+    return [int(buf[i]) for i in range(min(n.value, max_entries))]
 
 
 def cgh_quantize8(ctx: int, d_field: int, n: int, mode: int, d_out: int) -> int:

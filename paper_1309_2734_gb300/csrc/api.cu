@@ -848,6 +848,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         if (value < 0 || value > (1 << 24)) return CGH_EINVAL;
         ctx->direct_ctas = (int)value;
         return CGH_OK;
+    case CGH_OPT_BATCH_MODE:
+        if (value != 0 && value != 1) return CGH_EINVAL;
+        ctx->batch_mode = (int)value;
+        return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->profile = value == 1;
@@ -936,6 +940,13 @@ int cgh_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst)
     if (n_inst == 0) return CGH_OK;
     DeviceGuard g(ctx->device);
     return run_batch(ctx, inst, n_inst);
+}
+
+int cgh_batch_forms(cgh_ctx *ctx, int *forms, int max_entries, int *n_entries)
+{
+    if (!ctx || !n_entries || max_entries < 0 || (max_entries > 0 && !forms)) return CGH_EINVAL;
+    *n_entries = batch_forms(ctx, forms, max_entries);
+    return CGH_OK;
 }
 
 int cgh_autotune(cgh_ctx *ctx, int force)

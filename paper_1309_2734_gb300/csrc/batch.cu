@@ -1,19 +1,19 @@
-// a7: many holograms in one persistent launch, captured in a CUDA graph.
+// a7: many holograms per cgh_batch call, captured in a CUDA graph.
 //
-// The first cgh_batch call with a given set of instances builds a plan:
-//   - a form per instance (the context's form, or the autotuner's choice
-//     under the tolerance) and, for GEMM instances, a tile width;
-//   - one device arena holding every instance's prepared points, factors
-//     and the job tables of the batched kernels;
-//   - the unit lists: GEMM units {job, tile} over the whole K range of their
-//     hologram (accumulation chunks keep TMEM chains short) and direct units
-//     {job, pixel tile} over all points, handed out greedily (largest cost
-//     first within each job order) to the CTA with the least work so far;
-//   - a CUDA graph of the whole batch: per instance the point preparation
-//     (and factor generation), then ONE persistent GEMM launch for all GEMM
-//     instances and ONE persistent direct launch per direct form.
-// Later calls with the same instances (shapes, parameters and buffers) only
-// replay the graph on the context's stream.
+// The first cgh_batch call with a given set of instances builds a plan: a form
+// per instance (the context's form, or the autotuner's choice under the
+// tolerance) and, for GEMM instances, a tile width; one device arena for
+// every instance's prepared points, factors and the unit tables; and a CUDA
+// graph of the batch.  Later calls with the same instances (shapes,
+// parameters and buffers) only replay the graph on the context's stream.
+//
+// Default (CGH_OPT_BATCH_MODE = 0): ONE persistent launch (persist.cu) that
+// dequeues every unit of the batch -- point preparation, factor generation,
+// direct units on the SIMT warps, GEMM units on the tensor cores -- from two
+// global queues, with bounded waits on per-job counters; GEMM jobs are queued
+// longest units first.  Mode 1 (kept for comparison): per instance the point
+// preparation and factor generation, then one persistent GEMM launch over
+// per-CTA unit lists and one persistent direct launch per direct form.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -58,6 +58,8 @@ std::vector<uint64_t> plan_key(const cgh_ctx *ctx, const cgh_instance *inst, int
     k.push_back((uint64_t)ctx->form);
     k.push_back((uint64_t)ctx->tol_e9);
     k.push_back(((uint64_t)ctx->gemm_bn << 32) | (uint64_t)(uint32_t)ctx->gemm_chunk);
+    k.push_back((uint64_t)ctx->batch_mode);
+    k.push_back((uint64_t)(uint32_t)ctx->drop_tile);
     for (int i = 0; i < n; ++i) {
         const cgh_instance &b = inst[i];
         k.push_back(((uint64_t)(uint32_t)b.width << 32) | (uint32_t)b.height);
@@ -106,11 +108,12 @@ struct Layout {
 
 constexpr int kSplit16ChunkKbBatch = 8;
 
-int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
+// Form (and, for the GEMM forms, tile width) of every instance: the context's form, or the autotuner's choice.
+void choose_forms(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan, std::vector<int> &bn)
 {
     const double tol = (double)ctx->tol_e9 * 1e-9;
     plan->forms.assign(n, CGH_DIRECT_SFU);
-    std::vector<int> bn(n, 256);
+    bn.assign(n, 256);
     for (int i = 0; i < n; ++i) {
         if (inst[i].n_points == 0) continue;
         const int f = ctx->form != CGH_FORM_AUTO
@@ -122,6 +125,236 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
                                      : (ctx->form == CGH_FORM_AUTO ? tune_choose_bn(ctx, inst[i].width, inst[i].height, f)
                                                                    : choose_gemm_bn(inst[i].width));
     }
+}
+
+// (Re)allocates the plan's arena for at least `bytes`.
+int ensure_arena(BatchPlan *plan, size_t bytes)
+{
+    if (bytes <= plan->arena_bytes) return CGH_OK;
+    if (plan->arena) {
+        cudaFree(plan->arena);
+        plan->arena = nullptr;
+        plan->arena_bytes = 0;
+    }
+    if (cudaMalloc(&plan->arena, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return CGH_ENOMEM;
+    }
+    plan->arena_bytes = bytes;
+    return CGH_OK;
+}
+
+// Ends the capture on the plan's stream and instantiates the graph.
+int finish_capture(BatchPlan *plan, cudaError_t e)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(plan->capture, &graph);
+    if (e != cudaSuccess || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return CGH_ECUDA;
+    }
+    ec = cudaGraphInstantiate(&plan->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) {
+        plan->exec = nullptr;
+        return cuda_status(ec);
+    }
+    return CGH_OK;
+}
+
+int begin_capture(BatchPlan *plan)
+{
+    if (!plan->capture && cudaStreamCreateWithFlags(&plan->capture, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+    if (plan->exec) {
+        cudaGraphExecDestroy(plan->exec);
+        plan->exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(plan->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+    return CGH_OK;
+}
+
+constexpr int kDirectChunkPoints = 2048;   // points per direct unit of the persistent batch (at most 64 chunks)
+constexpr int kDirectMaxChunks = 64;
+
+// The persistent plan: one job per instance with points, the SIMT and GEMM unit queues, and a graph of
+// (memset of the counters, memsets of the empty instances' outputs, ONE persistent launch).
+int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
+{
+    std::vector<int> bn;
+    choose_forms(ctx, inst, n, plan, bn);
+    const int rows_f = persist_factor_rows(), pts_f = persist_factor_points();
+    const int dtw = persist_direct_tile_w(), dth = persist_direct_tile_h();
+    constexpr int kQ4NT = 8 * 256;   // float4s of one direct tile's totals
+    std::vector<int> job_of(n, -1), inst_of;
+    for (int i = 0; i < n; ++i)
+        if (inst[i].n_points > 0) {
+            job_of[i] = (int)inst_of.size();
+            inst_of.push_back(i);
+        }
+    const int nj = (int)inst_of.size();
+    std::vector<PersistJob> jobs(nj);
+    // arena: the zeroed counters first (one memset), then per-job buffers, then the tables
+    Layout L;
+    const size_t z_heads = L.take(64 * sizeof(int));
+    const size_t z_prep = L.take((size_t)nj * sizeof(int));
+    const size_t z_fact = L.take((size_t)nj * sizeof(int));
+    const size_t z_amax = L.take((size_t)nj * sizeof(float));
+    std::vector<size_t> z_count(nj, 0), o_geo(nj), o_aux(nj), o_p(nj, 0), o_q(nj, 0), o_parts(nj, 0);
+    std::vector<int64_t> work(nj, 0);
+    int bn_max = 0;
+    for (int j = 0; j < nj; ++j) {
+        const cgh_instance &b = inst[inst_of[j]];
+        PersistJob &J = jobs[j];
+        std::memset(&J, 0, sizeof J);
+        J.form = plan->forms[inst_of[j]];
+        J.n = (int)b.n_points;
+        J.n_pad = (int)padded_points(b.n_points);
+        J.width = b.width;
+        J.height = b.height;
+        if (J.form < CGH_GEMM_F16) {
+            J.tiles_x = (b.width + dtw - 1) / dtw;
+            const int tiles = J.tiles_x * ((b.height + dth - 1) / dth);
+            J.chunks = (int)std::min<int64_t>(kDirectMaxChunks,
+                                              std::max<int64_t>(1, (b.n_points + kDirectChunkPoints - 1) / kDirectChunkPoints));
+            if (J.chunks > 1) z_count[j] = L.take((size_t)tiles * sizeof(int));
+        }
+    }
+    const size_t z_end = L.take(0);
+    for (int j = 0; j < nj; ++j) {
+        const cgh_instance &b = inst[inst_of[j]];
+        PersistJob &J = jobs[j];
+        o_geo[j] = L.take((size_t)J.n_pad * sizeof(int4));
+        o_aux[j] = L.take((size_t)J.n_pad * sizeof(uint2));
+        if (J.form >= CGH_GEMM_F16) {
+            const int planes = J.form == CGH_GEMM_SPLIT16 ? 2 : 1;
+            J.ld = (2 * b.n_points + 63) / 64 * 64;
+            o_p[j] = L.take((size_t)planes * b.height * J.ld * 2);
+            o_q[j] = L.take((size_t)planes * b.width * J.ld * 2);
+            bn_max = std::max(bn_max, bn[inst_of[j]]);
+        } else if (J.chunks > 1) {
+            const int tiles = J.tiles_x * ((b.height + dth - 1) / dth);
+            o_parts[j] = L.take((size_t)tiles * J.chunks * kQ4NT * sizeof(float4));
+        }
+    }
+    const size_t t_jobs = L.take((size_t)nj * sizeof(PersistJob), 128);
+    // units
+    std::vector<int4> simt;
+    std::vector<int2> gunits;
+    std::vector<int> gemm_order, direct_order;
+    for (int j = 0; j < nj; ++j) {
+        const cgh_instance &b = inst[inst_of[j]];
+        const int f = jobs[j].form;
+        if (f >= CGH_GEMM_F16) {
+            // per-unit cost: k-blocks x passes x tile width (LPT order: the longest units first)
+            work[j] = (int64_t)((2 * b.n_points + 63) / 64) * (f == CGH_GEMM_SPLIT16 ? 3 : 1) * bn[inst_of[j]];
+            gemm_order.push_back(j);
+        } else {
+            work[j] = (int64_t)((b.n_points + jobs[j].chunks - 1) / jobs[j].chunks);
+            direct_order.push_back(j);
+        }
+    }
+    auto by_work = [&](int a, int c) { return work[a] > work[c] || (work[a] == work[c] && a < c); };
+    std::sort(gemm_order.begin(), gemm_order.end(), by_work);
+    std::sort(direct_order.begin(), direct_order.end(), by_work);
+    for (int j = 0; j < nj; ++j) {
+        jobs[j].prep_units = jobs[j].n_pad / kPointTile;
+        for (int blk = 0; blk < jobs[j].prep_units; ++blk) simt.push_back(make_int4(kPersistPrep, j, blk, 0));
+    }
+    for (int j : gemm_order) {
+        const cgh_instance &b = inst[inst_of[j]];
+        PersistJob &J = jobs[j];
+        J.point_slots = (int)(J.ld / 2);
+        const int bands = (b.height + b.width + rows_f - 1) / rows_f;
+        const int groups = (J.point_slots + pts_f - 1) / pts_f;
+        J.fact_units = bands * groups;
+        for (int band = 0; band < bands; ++band)
+            for (int g = 0; g < groups; ++g) simt.push_back(make_int4(kPersistFactor, j, band, g));
+    }
+    for (int j : direct_order) {
+        const cgh_instance &b = inst[inst_of[j]];
+        const int tiles = jobs[j].tiles_x * ((b.height + dth - 1) / dth);
+        for (int t = 0; t < tiles; ++t)
+            for (int c = 0; c < jobs[j].chunks; ++c) simt.push_back(make_int4(kPersistDirect, j, t, c));
+    }
+    for (int j : gemm_order) {
+        const cgh_instance &b = inst[inst_of[j]];
+        const int tiles = ((b.height + 127) / 128) * ((b.width + bn[inst_of[j]] - 1) / bn[inst_of[j]]);
+        for (int t = 0; t < tiles; ++t) gunits.push_back(make_int2(j, t));
+    }
+    if (ctx->drop_tile >= 0 && nj > 0) {
+        // test hook: job 0 waits for one unit more than exists, so a bounded wait runs out (kStatusTimeout)
+        if (jobs[0].form >= CGH_GEMM_F16) ++jobs[0].fact_units;
+        else ++jobs[0].prep_units;
+    }
+    const size_t t_simt = L.take(simt.size() * sizeof(int4));
+    const size_t t_gemm = L.take(gunits.size() * sizeof(int2));
+    int rc = ensure_arena(plan, L.bytes);
+    if (rc) return rc;
+    char *A = static_cast<char *>(plan->arena);
+    for (int j = 0; j < nj; ++j) {
+        const cgh_instance &b = inst[inst_of[j]];
+        PersistJob &J = jobs[j];
+        J.xyz = b.d_xyz;
+        J.amp = b.d_amp;
+        J.geo = reinterpret_cast<int4 *>(A + o_geo[j]);
+        J.aux = reinterpret_cast<uint2 *>(A + o_aux[j]);
+        J.amax = reinterpret_cast<float *>(A + z_amax) + j;
+        J.out = b.d_out;
+        J.pitch = b.pitch_m;
+        J.lambda = b.lambda_m;
+        J.vec = (b.width % 4 == 0) && ((uintptr_t)b.d_out % 16 == 0);
+        if (J.form >= CGH_GEMM_F16) {
+            J.P = reinterpret_cast<uint16_t *>(A + o_p[j]);
+            J.Q = reinterpret_cast<uint16_t *>(A + o_q[j]);
+            J.plane_p = (long long)b.height * J.ld;
+            J.plane_q = (long long)b.width * J.ld;
+            const int kc = J.form == CGH_GEMM_SPLIT16 ? (ctx->gemm_chunk > 0 ? ctx->gemm_chunk : kSplit16ChunkKbBatch)
+                                                      : ctx->gemm_chunk;
+            if (!fill_gemm_job(&J.g, factor_mode(J.form), bn[inst_of[j]], J.P, J.Q, b.height, b.width, J.ld, kc,
+                               b.d_out, J.amax))
+                return CGH_ECUDA;
+        } else if (J.chunks > 1) {
+            J.parts = reinterpret_cast<float4 *>(A + o_parts[j]);
+            J.tile_count = reinterpret_cast<int *>(A + z_count[j]);
+        }
+    }
+    auto up = [&](size_t at, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpy(A + at, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!up(t_jobs, jobs.data(), jobs.size() * sizeof(PersistJob)) || !up(t_simt, simt.data(), simt.size() * sizeof(int4)) ||
+        !up(t_gemm, gunits.data(), gunits.size() * sizeof(int2)))
+        return cuda_status(cudaGetLastError());
+    PersistParams pp;
+    pp.jobs = reinterpret_cast<const PersistJob *>(A + t_jobs);
+    pp.simt_units = reinterpret_cast<const int4 *>(A + t_simt);
+    pp.simt_total = (int)simt.size();
+    pp.gemm_units = reinterpret_cast<const int2 *>(A + t_gemm);
+    pp.gemm_total = (int)gunits.size();
+    pp.heads = reinterpret_cast<int *>(A + z_heads);
+    pp.prep_done = reinterpret_cast<int *>(A + z_prep);
+    pp.fact_done = reinterpret_cast<int *>(A + z_fact);
+
+    rc = begin_capture(plan);
+    if (rc) return rc;
+    cudaStream_t s = plan->capture;
+    cudaError_t e = cudaMemsetAsync(A, 0, z_end, s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        if (inst[i].n_points == 0) e = cudaMemsetAsync(inst[i].d_out, 0, (size_t)inst[i].width * inst[i].height * sizeof(float), s);
+    if (e == cudaSuccess && nj > 0)
+        e = launch_persist(pp, ctx->num_sms, bn_max, ctx->d_status, (uint64_t)ctx->timeout_ms * 1000000ull, s);
+    rc = finish_capture(plan, e);
+    if (rc) return rc;
+    plan->key = plan_key(ctx, inst, n);
+    return CGH_OK;
+}
+
+int build_plan_kinds(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
+{
+    std::vector<int> bn;
+    choose_forms(ctx, inst, n, plan, bn);
     // arena layout
     Layout L;
     struct Off {
@@ -215,19 +448,8 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
         t_doff[w] = L.take(doff[w].size() * sizeof(int));
         t_dunits[w] = L.take(dord[w].size() * sizeof(int2));
     }
-    // (re)allocate the arena
-    if (L.bytes > plan->arena_bytes) {
-        if (plan->arena) {
-            cudaFree(plan->arena);
-            plan->arena = nullptr;
-            plan->arena_bytes = 0;
-        }
-        if (cudaMalloc(&plan->arena, L.bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return CGH_ENOMEM;
-        }
-        plan->arena_bytes = L.bytes;
-    }
+    const int arc = ensure_arena(plan, L.bytes);
+    if (arc) return arc;
     char *A = static_cast<char *>(plan->arena);
     // fill the job tables with device pointers
     {
@@ -272,16 +494,10 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
             return cuda_status(cudaGetLastError());
 
     // capture the whole batch
-    if (!plan->capture && cudaStreamCreateWithFlags(&plan->capture, cudaStreamNonBlocking) != cudaSuccess)
-        return cuda_status(cudaGetLastError());
-    if (plan->exec) {
-        cudaGraphExecDestroy(plan->exec);
-        plan->exec = nullptr;
-    }
+    const int crc = begin_capture(plan);
+    if (crc) return crc;
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
     cudaStream_t s = plan->capture;
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return cuda_status(cudaGetLastError());
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const cgh_instance &b = inst[i];
@@ -315,24 +531,21 @@ int build_plan(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
             e = launch_direct_batch(w == 0, dtall, reinterpret_cast<const DirectJob *>(A + t_djobs[w]),
                                     reinterpret_cast<const int *>(A + t_doff[w]),
                                     reinterpret_cast<const int2 *>(A + t_dunits[w]), dctas[w], ctx->d_status, tmo, s);
-    cudaGraph_t graph = nullptr;
-    cudaError_t ec = cudaStreamEndCapture(s, &graph);
-    if (e != cudaSuccess || ec != cudaSuccess || !graph) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return CGH_ECUDA;
-    }
-    ec = cudaGraphInstantiate(&plan->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ec != cudaSuccess) {
-        plan->exec = nullptr;
-        return cuda_status(ec);
-    }
+    const int frc = finish_capture(plan, e);
+    if (frc) return frc;
     plan->key = plan_key(ctx, inst, n);
     return CGH_OK;
 }
 
 }  // namespace
+
+int batch_forms(const cgh_ctx *ctx, int *forms, int max_entries)
+{
+    if (!ctx->batch) return 0;
+    const int n = (int)ctx->batch->forms.size();
+    for (int i = 0; i < n && i < max_entries; ++i) forms[i] = ctx->batch->forms[i];
+    return n;
+}
 
 int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n)
 {
@@ -343,10 +556,10 @@ int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n)
         // the previous graph may still be running on the context's stream
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_status(cudaGetLastError());
         plan->key.clear();
-        const int rc = build_plan(ctx, inst, n, plan);
+        const int rc = ctx->batch_mode == 1 ? build_plan_kinds(ctx, inst, n, plan) : build_plan_persist(ctx, inst, n, plan);
         if (rc) return rc;
     }
-    ProfileScope ps(ctx, "batch_graph", 1);
+    ProfileScope ps(ctx, ctx->batch_mode == 1 ? "batch_graph" : "batch_persist", 1);
     return cuda_status(cudaGraphLaunch(plan->exec, ctx->stream));
 }
 

@@ -32,6 +32,7 @@ struct cgh_ctx {
     int64_t timeout_ms = 5000;
     int point_split = 0;
     int direct_ctas = 0;      // CGH_OPT_DIRECT_CTAS
+    int batch_mode = 0;       // CGH_OPT_BATCH_MODE
     int gemm_splitk = 0;
     int gemm_bn = 0;
     int gemm_chunk = 0;
@@ -249,6 +250,7 @@ int compute_hologram(cgh_ctx *ctx, int width, int height, double pitch, double l
 int factor_mode(int form);
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n);
 int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
+int batch_forms(const cgh_ctx *ctx, int *forms, int max_entries);
 int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int64_t n, float *d_out);
 int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lambda, const float *d_xyz,
                   const float *d_amp, int64_t n, int planes, float *d_out);

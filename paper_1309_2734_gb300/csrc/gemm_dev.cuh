@@ -59,6 +59,7 @@ struct UnitInfo {
     bool vec;
     bool accumulate;             // add to the output already there (later point chunks)
     bool trans;                  // A = Q, B = P: accumulator rows are hologram columns
+    int job = 0;                 // a batch's job (the readiness wait of a queue of units)
 };
 
 // The barriers of the ring and of the two accumulators.

@@ -229,6 +229,46 @@ bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q,
 cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas,
                               int bn_max, int *status, uint64_t timeout_ns, cudaStream_t s);
 
+// a7: the persistent batch kernel (persist.cu).  One job per hologram; the SIMT queue holds units
+// {kind, job, a, b}: kPersistPrep (a = block of kPointTile points), kPersistFactor (a = band of
+// persist_factor_rows() stacked rows, b = group of persist_factor_points() point slots), kPersistDirect
+// (a = pixel tile of persist_direct_tile_w() x persist_direct_tile_h(), b = point chunk); the GEMM queue holds
+// {job, tile}.  heads[2], prep_done[jobs], fact_done[jobs], every job's amax and tile_count are zero at launch.
+enum { kPersistPrep = 0, kPersistFactor = 1, kPersistDirect = 2 };
+struct alignas(64) PersistJob {
+    GemmJob g;                  // GEMM forms: tensor maps, shape, output
+    const float *xyz, *amp;     // the caller's points
+    int4 *geo;                  // prepared points (padded to kPointTile)
+    uint2 *aux;
+    float *amax;                // max |A| (GEMM forms)
+    uint16_t *P, *Q;            // factors, [planes][rows][ld]
+    float *out;                 // [height][width]
+    float4 *parts;              // direct units with chunks > 1: [tiles][chunks][totals of a tile]
+    int *tile_count;            // direct units with chunks > 1: one counter per pixel tile
+    double pitch, lambda;
+    long long ld, plane_p, plane_q;
+    int n, n_pad, point_slots, width, height, form;
+    int prep_units, fact_units; // what a factor (direct) unit and a GEMM unit wait for
+    int tiles_x, chunks, vec, pad;
+};
+struct PersistParams {
+    const PersistJob *jobs;
+    const int4 *simt_units;
+    int simt_total;
+    const int2 *gemm_units;
+    int gemm_total;
+    int *heads;                 // [0]: next SIMT unit, [1]: next GEMM unit
+    int *prep_done, *fact_done; // per job
+};
+int persist_factor_rows();
+int persist_factor_points();
+int persist_direct_tile_w();
+int persist_direct_tile_h();
+// ctas persistent CTAs (one per SM); bn_max: the widest GEMM tile of the jobs (224: five ring stages of
+// 224-wide tiles; up to 256: four).
+cudaError_t launch_persist(const PersistParams &p, int ctas, int bn_max, int *status, uint64_t timeout_ns,
+                           cudaStream_t s);
+
 // a5: fixed-order sum of `slices` planes of n floats (reduce.cu).
 cudaError_t launch_reduce_slices(const float *parts, int slices, int64_t n, int64_t slice_stride, float *out,
                                  cudaStream_t s);

@@ -73,6 +73,8 @@ def test_null_context_everywhere(lib):
     assert lib.cgh_wrp(None, None, None, 0, 0.5, None) == _lib.CGH_EINVAL
     assert lib.cgh_wrp_record(None, None, None, 0, 0.5, None) == _lib.CGH_EINVAL
     assert lib.cgh_autotune(None, 0) == _lib.CGH_EINVAL
+    n = ctypes.c_int(0)
+    assert lib.cgh_batch_forms(None, None, 0, ctypes.byref(n)) == _lib.CGH_EINVAL
     v = ctypes.c_double(0.0)
     assert lib.cgh_measure_mufu(None, ctypes.byref(v)) == _lib.CGH_EINVAL
     assert lib.cgh_destroy(None) == _lib.CGH_OK

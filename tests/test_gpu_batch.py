@@ -1,10 +1,11 @@
-"""Batched holograms (one persistent launch per form kind, captured in a CUDA
-graph) and the autotuner, through the C ABI, against the FP64 oracle."""
+"""Batched holograms (one persistent launch for the whole batch, or per-kind
+launches, captured in a CUDA graph) and the autotuner, through the C ABI,
+against the FP64 oracle."""
 import numpy as np
 import pytest
 
 import oracle
-from paper_1309_2734_gb300 import Hologram, batch, workloads
+from paper_1309_2734_gb300 import CghError, Hologram, batch, workloads
 from paper_1309_2734_gb300 import _lib
 
 pytestmark = pytest.mark.gpu
@@ -44,12 +45,66 @@ def _check_all(clouds, outs, tol):
         assert oracle.nrms(got, ref) <= tol, (c.name, oracle.nrms(got, ref))
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
-def test_batch_each_form_vs_oracle(form):
+def test_batch_each_form_vs_oracle(form, mode):
+    """Every form through the persistent launch (mode 0) and the per-kind launches (mode 1)."""
     clouds = _clouds()
     dev = _dev(clouds)
     outs = [torch.full((c.height, c.width), 5.0, device="cuda") for c in clouds]
     with Hologram(8, 8, 8e-6, 532e-9, form=form, timeout_ms=5000) as h:
+        h.set_option(_lib.CGH_OPT_BATCH_MODE, mode)
+        batch(h, dev, outs)
+        h.sync()
+        assert _lib.cgh_batch_forms(h.ctx)[:2] == [getattr(_lib, "CGH_" + form.upper())] * 2
+    _check_all(clouds, outs, NRMS[form])
+
+
+def _mixed_clouds():
+    # direct jobs of several point chunks (their parts are folded), ragged shapes, an empty instance
+    return [workloads.random_cloud(720, 300, 200, 5000), workloads.random_cloud(721, 1000, 70, 700),
+            workloads.random_cloud(722, 130, 257, 9000), workloads.random_cloud(723, 64, 64, 0),
+            workloads.random_cloud(724, 513, 129, 3)]
+
+
+@pytest.mark.parametrize("form", ["direct_sfu", "direct_accurate", "gemm_split16"])
+def test_persistent_batch_is_deterministic_and_matches_kinds(form):
+    """Two replays of the persistent launch give the same bits (the parts of a direct tile are summed in chunk
+    order, whoever finishes last); the per-kind launches agree within single-precision rounding."""
+    clouds = _mixed_clouds()
+    dev = _dev(clouds)
+    outs = [torch.full((c.height, c.width), 3.0, device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form=form) as h:
+        batch(h, dev, outs)
+        h.sync()
+        first = [o.clone() for o in outs]
+        batch(h, dev, outs)
+        h.sync()
+        for a, b in zip(first, outs):
+            assert torch.equal(a, b)
+        h.set_option(_lib.CGH_OPT_BATCH_MODE, 1)
+        batch(h, dev, outs)
+        h.sync()
+    for c, a, b in zip(clouds, first, outs):
+        if c.n_points:
+            assert oracle.nrms(a.cpu().numpy(), b.cpu().numpy()) < 1e-6
+    _check_all(clouds, first, NRMS[form])
+
+
+@pytest.mark.parametrize("form", ["direct_sfu", "gemm_f16"])
+def test_persistent_batch_wait_times_out_and_context_recovers(form):
+    """Test hook: the first job waits for one unit more than exists, so its bounded wait runs out; the launch
+    ends with a timeout status instead of hanging, and the next plan (hook off) computes the batch."""
+    clouds = _clouds()
+    dev = _dev(clouds)
+    outs = [torch.zeros((c.height, c.width), device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form=form, timeout_ms=300) as h:
+        h.set_option(_lib.CGH_OPT_TEST_DROP_TILE, 0)
+        batch(h, dev, outs)
+        with pytest.raises(CghError) as ei:
+            h.sync()
+        assert ei.value.code == _lib.CGH_ETIMEOUT
+        h.set_option(_lib.CGH_OPT_TEST_DROP_TILE, -1)
         batch(h, dev, outs)
         h.sync()
     _check_all(clouds, outs, NRMS[form])
