@@ -176,6 +176,41 @@ int begin_capture(BatchPlan *plan)
     return CGH_OK;
 }
 
+// The persistent batch's GEMM tile: width 192 or 224 (so that the 224-wide kernel with its five-stage operand ring
+// serves every job) and orientation (A = P: 128-row tiles of hologram rows; transposed: of hologram columns), by
+// padded area times the relative cost of the width (128-wide tiles measured about 35 % slower per flop at
+// 1920x1080, 192-wide 3 %).  A forced CGH_OPT_GEMM_BN / CGH_OPT_GEMM_TRANSPOSE wins.
+void choose_persist_tile(const cgh_ctx *ctx, int width, int height, int &bn, bool &trans)
+{
+    static const int cands[] = {224, 192, 128};
+    static const double eff[] = {1.0, 1.03, 1.35};
+    double best = 1e300;
+    bn = 224;
+    trans = false;
+    for (int tr = 0; tr < 2; ++tr) {
+        if ((ctx->gemm_trans == 1 && tr) || (ctx->gemm_trans == 2 && !tr)) continue;
+        const int64_t a_rows = tr ? width : height, b_rows = tr ? height : width;
+        for (int c = 0; c < 3; ++c) {
+            const int w = ctx->gemm_bn > 0 ? ctx->gemm_bn : cands[c];
+            if (ctx->gemm_bn > 0 && c > 0) break;
+            const double cost = (double)((a_rows + 127) / 128 * 128) * (double)((b_rows + w - 1) / w * w) *
+                                (ctx->gemm_bn > 0 ? 1.0 : eff[c]);
+            if (cost < best * (1.0 - 1e-9)) {
+                best = cost;
+                bn = w;
+                trans = tr != 0;
+            }
+        }
+    }
+}
+
+// K chunks of the persistent batch's GEMM units: each unit covers kchunk_kb k-blocks of its tile, and the units
+// of a job are queued chunk by chunk (all tiles of chunk 0, then of chunk 1, ...), so the CTAs in flight stream
+// the same K range of the factors and L2 serves each factor tile to every unit that needs it: a chunk's slice of
+// the job's operands (planes x (A rows + B rows) x 128 bytes per k-block) is kept near kGemmChunkBytes.
+constexpr double kGemmChunkBytes = 64.0 * (1 << 20);
+constexpr int kGemmChunkMinKb = 32;
+
 constexpr int kDirectChunkPoints = 2048;   // points per direct unit of the persistent batch (at most 64 chunks)
 constexpr int kDirectMaxChunks = 64;
 
@@ -196,6 +231,14 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         }
     const int nj = (int)inst_of.size();
     std::vector<PersistJob> jobs(nj);
+    std::vector<char> jtrans(nj, 0);
+    for (int j = 0; j < nj; ++j) {
+        const int i = inst_of[j];
+        if (plan->forms[i] < CGH_GEMM_F16) continue;
+        bool tr = false;
+        choose_persist_tile(ctx, inst[i].width, inst[i].height, bn[i], tr);
+        jtrans[j] = tr ? 1 : 0;
+    }
     // arena: the zeroed counters first (one memset), then per-job buffers, then the tables
     Layout L;
     const size_t z_heads = L.take(64 * sizeof(int));
@@ -214,7 +257,25 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         J.n_pad = (int)padded_points(b.n_points);
         J.width = b.width;
         J.height = b.height;
-        if (J.form < CGH_GEMM_F16) {
+        if (J.form >= CGH_GEMM_F16) {
+            const int i = inst_of[j];
+            const int planes = J.form == CGH_GEMM_SPLIT16 ? 2 : 1;
+            const int64_t nkb = (2 * b.n_points + 63) / 64;
+            const int a_rows = jtrans[j] ? b.width : b.height, b_rows = jtrans[j] ? b.height : b.width;
+            const int64_t a_pad = (a_rows + 127) / 128 * 128, b_pad = (int64_t)(b_rows + bn[i] - 1) / bn[i] * bn[i];
+            const int kc = J.form == CGH_GEMM_SPLIT16 ? (ctx->gemm_chunk > 0 ? ctx->gemm_chunk : kSplit16ChunkKbBatch)
+                                                      : 1;
+            int64_t kcs = (int64_t)(kGemmChunkBytes / ((double)planes * (double)(a_pad + b_pad) * 128.0));
+            kcs = std::max<int64_t>(kGemmChunkMinKb, kcs) / kc * kc;
+            if (kcs <= 0) kcs = kc;
+            J.kchunks = (int)((nkb + kcs - 1) / kcs);
+            if (J.kchunks <= 1) {
+                J.kchunks = 1;
+                kcs = nkb;
+            }
+            J.kchunk_kb = (int)kcs;
+            if (J.kchunks > 1) z_count[j] = L.take((size_t)(a_pad / 128) * ((b_pad) / bn[i]) * 4 * sizeof(int));
+        } else {
             J.tiles_x = (b.width + dtw - 1) / dtw;
             const int tiles = J.tiles_x * ((b.height + dth - 1) / dth);
             J.chunks = (int)std::min<int64_t>(kDirectMaxChunks,
@@ -242,14 +303,14 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     const size_t t_jobs = L.take((size_t)nj * sizeof(PersistJob), 128);
     // units
     std::vector<int4> simt;
-    std::vector<int2> gunits;
+    std::vector<int4> gunits;
     std::vector<int> gemm_order, direct_order;
     for (int j = 0; j < nj; ++j) {
         const cgh_instance &b = inst[inst_of[j]];
         const int f = jobs[j].form;
         if (f >= CGH_GEMM_F16) {
             // per-unit cost: k-blocks x passes x tile width (LPT order: the longest units first)
-            work[j] = (int64_t)((2 * b.n_points + 63) / 64) * (f == CGH_GEMM_SPLIT16 ? 3 : 1) * bn[inst_of[j]];
+            work[j] = (int64_t)jobs[j].kchunk_kb * (f == CGH_GEMM_SPLIT16 ? 3 : 1) * bn[inst_of[j]];
             gemm_order.push_back(j);
         } else {
             work[j] = (int64_t)((b.n_points + jobs[j].chunks - 1) / jobs[j].chunks);
@@ -281,8 +342,10 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     }
     for (int j : gemm_order) {
         const cgh_instance &b = inst[inst_of[j]];
-        const int tiles = ((b.height + 127) / 128) * ((b.width + bn[inst_of[j]] - 1) / bn[inst_of[j]]);
-        for (int t = 0; t < tiles; ++t) gunits.push_back(make_int2(j, t));
+        const int a_rows = jtrans[j] ? b.width : b.height, b_rows = jtrans[j] ? b.height : b.width;
+        const int tiles = ((a_rows + 127) / 128) * ((b_rows + bn[inst_of[j]] - 1) / bn[inst_of[j]]);
+        for (int c = 0; c < jobs[j].kchunks; ++c)
+            for (int t = 0; t < tiles; ++t) gunits.push_back(make_int4(j, t, c, 0));
     }
     if (ctx->drop_tile >= 0 && nj > 0) {
         // test hook: job 0 waits for one unit more than exists, so a bounded wait runs out (kStatusTimeout)
@@ -290,7 +353,7 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         else ++jobs[0].prep_units;
     }
     const size_t t_simt = L.take(simt.size() * sizeof(int4));
-    const size_t t_gemm = L.take(gunits.size() * sizeof(int2));
+    const size_t t_gemm = L.take(gunits.size() * sizeof(int4));
     int rc = ensure_arena(plan, L.bytes);
     if (rc) return rc;
     char *A = static_cast<char *>(plan->arena);
@@ -314,8 +377,9 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
             const int kc = J.form == CGH_GEMM_SPLIT16 ? (ctx->gemm_chunk > 0 ? ctx->gemm_chunk : kSplit16ChunkKbBatch)
                                                       : ctx->gemm_chunk;
             if (!fill_gemm_job(&J.g, factor_mode(J.form), bn[inst_of[j]], J.P, J.Q, b.height, b.width, J.ld, kc,
-                               b.d_out, J.amax))
+                               b.d_out, J.amax, jtrans[j] != 0))
                 return CGH_ECUDA;
+            if (J.kchunks > 1) J.tile_seq = reinterpret_cast<int *>(A + z_count[j]);
         } else if (J.chunks > 1) {
             J.parts = reinterpret_cast<float4 *>(A + o_parts[j]);
             J.tile_count = reinterpret_cast<int *>(A + z_count[j]);
@@ -325,13 +389,13 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         return bytes == 0 || cudaMemcpy(A + at, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
     };
     if (!up(t_jobs, jobs.data(), jobs.size() * sizeof(PersistJob)) || !up(t_simt, simt.data(), simt.size() * sizeof(int4)) ||
-        !up(t_gemm, gunits.data(), gunits.size() * sizeof(int2)))
+        !up(t_gemm, gunits.data(), gunits.size() * sizeof(int4)))
         return cuda_status(cudaGetLastError());
     PersistParams pp;
     pp.jobs = reinterpret_cast<const PersistJob *>(A + t_jobs);
     pp.simt_units = reinterpret_cast<const int4 *>(A + t_simt);
     pp.simt_total = (int)simt.size();
-    pp.gemm_units = reinterpret_cast<const int2 *>(A + t_gemm);
+    pp.gemm_units = reinterpret_cast<const int4 *>(A + t_gemm);
     pp.gemm_total = (int)gunits.size();
     pp.heads = reinterpret_cast<int *>(A + z_heads);
     pp.prep_done = reinterpret_cast<int *>(A + z_prep);

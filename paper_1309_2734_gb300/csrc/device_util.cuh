@@ -89,6 +89,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     }
 }
 
+// Acquire load of a counter another SM updates (never a stale L1 line).
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded spin of one thread until *count >= need; false when timeout_ns of global time ran out.
+__device__ __forceinline__ bool wait_count(const int *count, int need, unsigned long long timeout_ns)
+{
+    if (ld_acquire(count) >= need) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        __nanosleep(200);
+        if (ld_acquire(count) >= need) return true;
+        if (global_timer_ns() - t0 > timeout_ns) return false;
+    }
+}
+
 // 1-D bulk copy (TMA, non-tensor) global -> shared; completes tx bytes on bar.
 // dst, src and bytes must be multiples of 16.
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)

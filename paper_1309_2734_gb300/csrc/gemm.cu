@@ -304,18 +304,21 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
 }
 
 bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q, int height, int width, int64_t ld,
-                   int chunk_kb, float *out, const float *amp_max)
+                   int chunk_kb, float *out, const float *amp_max, bool trans)
 {
     if (ld % kBK != 0 || !gemm_bn_supported(bn)) return false;
     const bool bf16 = mode == kFactorBF16;
     const bool split3 = mode == kFactorSplit16;
-    const uint16_t *p16 = static_cast<const uint16_t *>(P);
-    const uint16_t *q16 = static_cast<const uint16_t *>(Q);
-    if (!make_operand_map(&job->p, P, bf16, ld, height, kBM) || !make_operand_map(&job->q, Q, bf16, ld, width, bn))
+    // A operand: 128-row tiles of P (or of Q when transposed); B operand: bn-row tiles of the other
+    const void *A = trans ? Q : P, *B = trans ? P : Q;
+    const int a_rows = trans ? width : height, b_rows = trans ? height : width;
+    const uint16_t *a16 = static_cast<const uint16_t *>(A);
+    const uint16_t *b16 = static_cast<const uint16_t *>(B);
+    if (!make_operand_map(&job->p, A, bf16, ld, a_rows, kBM) || !make_operand_map(&job->q, B, bf16, ld, b_rows, bn))
         return false;
     if (split3) {
-        if (!make_operand_map(&job->pl, p16 + (int64_t)height * ld, false, ld, height, kBM) ||
-            !make_operand_map(&job->ql, q16 + (int64_t)width * ld, false, ld, width, bn))
+        if (!make_operand_map(&job->pl, a16 + (int64_t)a_rows * ld, false, ld, a_rows, kBM) ||
+            !make_operand_map(&job->ql, b16 + (int64_t)b_rows * ld, false, ld, b_rows, bn))
             return false;
     } else {
         job->pl = job->p;
@@ -326,14 +329,14 @@ bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q,
     job->height = height;
     job->width = width;
     job->nkb = (int)(ld / kBK);
-    job->tiles_m = (height + kBM - 1) / kBM;
-    job->tiles_n = (width + bn - 1) / bn;
+    job->tiles_m = (a_rows + kBM - 1) / kBM;
+    job->tiles_n = (b_rows + bn - 1) / bn;
     job->kc = chunk_kb > 0 ? chunk_kb : job->nkb;
     job->passes = split3 ? 3 : 1;
     job->bn = bn;
     job->idesc = umma_idesc_f16(bf16, kBM, bn);
     job->vec = (width % 4 == 0) && ((uintptr_t)out % 16 == 0);
-    job->trans = 0;
+    job->trans = trans ? 1 : 0;
     return true;
 }
 

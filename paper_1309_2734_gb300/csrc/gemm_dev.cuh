@@ -60,6 +60,10 @@ struct UnitInfo {
     bool accumulate;             // add to the output already there (later point chunks)
     bool trans;                  // A = Q, B = P: accumulator rows are hologram columns
     int job = 0;                 // a batch's job (the readiness wait of a queue of units)
+    // A K chunk of a batch's tile: epilogue warp q stores (adds) its quarter of the tile once seq[q] >= seq_k,
+    // then sets seq[q] = seq_k + 1, so the chunks of a tile reach the output in K order; nullptr: no ordering.
+    int *seq = nullptr;
+    int seq_k = 0;
 };
 
 // The barriers of the ring and of the two accumulators.
@@ -205,7 +209,8 @@ __device__ __forceinline__ void gemm_mma(const Units &src, uint8_t *smem, const 
     mbar_wait(drain, 0, timeout_ns);
 }
 
-template <class C, class Units>
+// ROUND: columns of the accumulator per store round (64 or 32; 32 holds half the registers).
+template <class C, class Units, int ROUND = 64>
 __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &bars, uint32_t tmem_base, int warp,
                                               int lane, int *status, unsigned long long timeout_ns)
 {
@@ -219,11 +224,6 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
     typename Units::Cursor cur = src.start();
     UnitInfo x;
     while (ok && src.next(2, cur, x)) {
-        float unscale = 1.0f;
-        if (x.amp_max != nullptr) {
-            const float m = *x.amp_max;
-            if (m > 0.0f) unscale = m;
-        }
         const bool empty_range = x.kb1 <= x.kb0;
         const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
         const int row = x.tm * kBM + row_in_tile;
@@ -239,6 +239,13 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
         }
         ++uses[tb];
         tc_fence_after();
+        // the factors' scale, read once the unit's MMAs are done (so after every load of its operands), and from
+        // L2: in a persistent batch other SMs wrote it during this launch and this SM's L1 may hold an old line
+        float unscale = 1.0f;
+        if (x.amp_max != nullptr) {
+            const float m = __ldcg(x.amp_max);
+            if (m > 0.0f) unscale = m;
+        }
         for (int c = 1; c < nch; ++c) {
             // total += chunk c, in FP32 and chunk order
             if (!mbar_wait(&tfull[1 - tb], uses[1 - tb] & 1u, timeout_ns)) {
@@ -263,7 +270,19 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
             mbar_arrive(&tempty[1 - tb]);
         }
         if (!ok) break;
-        // the tile to global memory: stored, or added to what earlier point chunks left there
+        if (x.seq != nullptr) {
+            // the tile's previous K chunk has left this warp's quarter first
+            bool got = true;
+            if (lane == 0) got = wait_count(&x.seq[q], x.seq_k, timeout_ns);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                if (lane == 0) atomicOr(status, kStatusTimeout);
+                ok = false;
+                break;
+            }
+        }
+        // the tile to global memory: stored, or added to what earlier point chunks left there (read from L2:
+        // in a batch another SM may have written it during this launch)
         const bool first = !x.accumulate;
         if (x.trans) {
             // accumulator row = hologram column m (the warp's 32 lanes hold 32
@@ -279,7 +298,8 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
                 if (!first && in_m) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        old[i] = (i < ncol && n0 + i < x.height) ? x.out[(long long)(n0 + i) * x.width + m] : 0.0f;
+                        old[i] = (i < ncol && n0 + i < x.height) ? __ldcg(x.out + (long long)(n0 + i) * x.width + m)
+                                                                 : 0.0f;
                 }
                 uint32_t r[2][16];
                 tmem_ld16(taddr + (uint32_t)cc, r[0]);
@@ -296,34 +316,34 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
             }
         } else {
 #pragma unroll 1
-            for (int cc = 0; cc < x.bn; cc += 64) {
-                // 64 columns per round (four groups of 16): the previous partial sums
-                // (if any) are loaded first, all at once, so the global-memory latency is
-                // paid once per 64 columns and overlaps the tensor-memory reads
-                const int ncol = min(64, x.bn - cc);   // a multiple of 16
+            for (int cc = 0; cc < x.bn; cc += ROUND) {
+                // ROUND columns per round (groups of 16): the previous partial sums (if any) are loaded first,
+                // all at once, so the global-memory latency is paid once per round and overlaps the
+                // tensor-memory reads
+                constexpr int G = ROUND / 16;
+                const int ncol = min(ROUND, x.bn - cc);   // a multiple of 16
                 const int col0 = x.tn * x.bn + cc;
                 const bool in_row = row < x.height;
-                bool gvec[4];
+                bool gvec[G];
 #pragma unroll
-                for (int gq = 0; gq < 4; ++gq)
+                for (int gq = 0; gq < G; ++gq)
                     gvec[gq] = x.vec && in_row && gq * 16 < ncol && col0 + gq * 16 + 16 <= x.width;
-                float4 old[16];
+                float4 old[4 * G];
 #pragma unroll
-                for (int gq = 0; gq < 4; ++gq)
+                for (int gq = 0; gq < G; ++gq)
                     if (!first && gvec[gq]) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            old[4 * gq + i] = reinterpret_cast<const float4 *>(dst + col0 + 16 * gq)[i];
+                            old[4 * gq + i] = __ldcg(reinterpret_cast<const float4 *>(dst + col0 + 16 * gq) + i);
                     }
-                uint32_t r[4][16];
-                tmem_ld16(taddr + (uint32_t)cc, r[0]);
-                if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
-                if (ncol > 32) tmem_ld16(taddr + (uint32_t)(cc + 32), r[2]);
-                if (ncol > 48) tmem_ld16(taddr + (uint32_t)(cc + 48), r[3]);
+                uint32_t r[G][16];
+#pragma unroll
+                for (int gq = 0; gq < G; ++gq)
+                    if (gq == 0 || ncol > 16 * gq) tmem_ld16(taddr + (uint32_t)(cc + 16 * gq), r[gq]);
                 tmem_ld_wait();
                 if (!in_row) continue;
 #pragma unroll
-                for (int gq = 0; gq < 4; ++gq) {
+                for (int gq = 0; gq < G; ++gq) {
                     if (gq * 16 >= ncol) continue;
                     float v[16];
 #pragma unroll
@@ -344,10 +364,15 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
                     } else {
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (col0 + 16 * gq + i < x.width) d16[i] = first ? v[i] : d16[i] + v[i];
+                            if (col0 + 16 * gq + i < x.width) d16[i] = first ? v[i] : __ldcg(d16 + i) + v[i];
                     }
                 }
             }
+        }
+        if (x.seq != nullptr) {   // this warp's quarter of the tile is out: the next K chunk may add to it
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release(&x.seq[q], x.seq_k + 1);
         }
         tc_fence_before();
         mbar_arrive(&tempty[tb]);

@@ -222,8 +222,9 @@ struct alignas(64) GemmJob {
     int vec;
     int trans;
 };
+// trans: A = Q (128-row tiles of hologram columns), B = P; the epilogue writes the tile back transposed.
 bool fill_gemm_job(GemmJob *job, int mode, int bn, const void *P, const void *Q, int height, int width, int64_t ld,
-                   int chunk_kb, float *out, const float *amp_max);
+                   int chunk_kb, float *out, const float *amp_max, bool trans = false);
 // bn_max: the widest tile of the jobs; at most 224 selects the kernel whose
 // shared-memory ring has room for 5 stages of 224-wide tiles (4 at 256).
 cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const int2 *d_units, int ctas,
@@ -233,7 +234,8 @@ cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const
 // {kind, job, a, b}: kPersistPrep (a = block of kPointTile points), kPersistFactor (a = band of
 // persist_factor_rows() stacked rows, b = group of persist_factor_points() point slots), kPersistDirect
 // (a = pixel tile of persist_direct_tile_w() x persist_direct_tile_h(), b = point chunk); the GEMM queue holds
-// {job, tile}.  heads[2], prep_done[jobs], fact_done[jobs], every job's amax and tile_count are zero at launch.
+// {job, tile, K chunk} (the chunks of a tile add to the output in K order).  heads[2], prep_done[jobs],
+// fact_done[jobs], every job's amax, tile_count and tile_seq are zero at launch.
 enum { kPersistPrep = 0, kPersistFactor = 1, kPersistDirect = 2 };
 struct alignas(64) PersistJob {
     GemmJob g;                  // GEMM forms: tensor maps, shape, output
@@ -249,13 +251,15 @@ struct alignas(64) PersistJob {
     long long ld, plane_p, plane_q;
     int n, n_pad, point_slots, width, height, form;
     int prep_units, fact_units; // what a factor (direct) unit and a GEMM unit wait for
-    int tiles_x, chunks, vec, pad;
+    int tiles_x, chunks, vec;
+    int kchunk_kb, kchunks;     // GEMM: k-blocks of one K chunk of a unit, and chunks per tile
+    int *tile_seq;              // GEMM with kchunks > 1: [tiles][4], the next K chunk each epilogue quarter takes
 };
 struct PersistParams {
     const PersistJob *jobs;
     const int4 *simt_units;
     int simt_total;
-    const int2 *gemm_units;
+    const int4 *gemm_units;     // {job, tile, K chunk, 0}
     int gemm_total;
     int *heads;                 // [0]: next SIMT unit, [1]: next GEMM unit
     int *prep_done, *fact_done; // per job

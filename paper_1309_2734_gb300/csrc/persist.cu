@@ -62,34 +62,17 @@ constexpr int kPersistRoom = 232448 - 1024 - 256 - 4096;
 
 using SimtSync = GroupSync<1, kSimtThreads, kSimtBase>;
 
-__device__ __forceinline__ int ld_acquire(const int *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void fence_proxy_async_global()
 {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Bounded spin of one thread until *count >= need; false when the limit ran out.
-__device__ __forceinline__ bool wait_count(const int *count, int need, unsigned long long timeout_ns)
-{
-    if (ld_acquire(count) >= need) return true;
-    const uint64_t t0 = global_timer_ns();
-    for (;;) {
-        __nanosleep(200);
-        if (ld_acquire(count) >= need) return true;
-        if (global_timer_ns() - t0 > timeout_ns) return false;
-    }
-}
-
-// GEMM units from the global queue, handed from the producer to the other two roles through the ring.
+// GEMM units {job, tile, K chunk} from the global queue.  The producer takes a unit, waits (bounded) until the
+// job's factors are all written, and only then hands it to the MMA issuer and the epilogue through the ring of
+// unit ids, so no role touches a unit whose inputs are not there.
 struct QueueUnits {
     const PersistJob *jobs;
-    const int2 *units;   // {job, tile}
+    const int4 *units;   // {job, tile, K chunk, 0}
     int total;
     int *head;
     const int *fact_done;
@@ -105,8 +88,9 @@ struct QueueUnits {
 
     __device__ UnitInfo get(int u) const
     {
-        const int2 w = units[u];
-        const GemmJob &J = jobs[w.x].g;
+        const int4 w = units[u];
+        const PersistJob &P = jobs[w.x];
+        const GemmJob &J = P.g;
         UnitInfo x;
         x.mp = &J.p;
         x.mq = &J.q;
@@ -116,8 +100,8 @@ struct QueueUnits {
         x.amp_max = J.amp_max;
         x.tm = w.y % J.tiles_m;
         x.tn = w.y / J.tiles_m;
-        x.kb0 = 0;
-        x.kb1 = J.nkb;
+        x.kb0 = w.z * P.kchunk_kb;
+        x.kb1 = min(J.nkb, x.kb0 + P.kchunk_kb);
         x.bn = J.bn;
         x.passes = J.passes;
         x.kc = J.kc;
@@ -125,9 +109,11 @@ struct QueueUnits {
         x.width = J.width;
         x.idesc = J.idesc;
         x.vec = J.vec != 0;
-        x.accumulate = false;
-        x.trans = false;
+        x.accumulate = w.z > 0;
+        x.trans = J.trans != 0;
         x.job = w.x;
+        x.seq = P.kchunks > 1 ? P.tile_seq + 4 * w.y : nullptr;
+        x.seq_k = w.z;
         return x;
     }
 
@@ -144,8 +130,20 @@ struct QueueUnits {
             }
             u = atomicAdd(head, 1);
             if (u >= total) u = -1;
+            bool fail = false;
+            if (u >= 0) {
+                const int j = units[u].x;
+                if (wait_count(&fact_done[j], jobs[j].fact_units, timeout_ns)) {
+                    fence_proxy_async_global();   // the factors' ordinary stores, for the TMA loads that follow
+                } else {
+                    atomicOr(status, kStatusTimeout);
+                    fail = true;
+                    u = -1;
+                }
+            }
             ring_u[slot] = u;
             mbar_arrive(&ring_full[slot]);
+            if (fail) return false;
         } else {
             // the producer may wait up to the limit for the unit's factors first
             if (!mbar_wait(&ring_full[slot], ph, 2 * timeout_ns)) {
@@ -165,13 +163,8 @@ struct QueueUnits {
         return true;
     }
 
-    // the producer: every factor unit of the job is written (then its TMA loads may read them)
-    __device__ bool ready(const UnitInfo &x, unsigned long long timeout_ns) const
-    {
-        if (!wait_count(&fact_done[x.job], jobs[x.job].fact_units, timeout_ns)) return false;
-        fence_proxy_async_global();
-        return true;
-    }
+    // next() has waited for the unit's factors before handing it out
+    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
 
     // after a failure the producer ends the sequence for the other roles
     __device__ void abort(Cursor &c, unsigned long long timeout_ns) const
@@ -294,7 +287,7 @@ template <int MODE>
 __device__ __forceinline__ void run_factor_unit(const PersistJob &J, int band, int group)
 {
     float scale = 1.0f;
-    const float m = *J.amax;
+    const float m = __ldcg(J.amax);   // written by other SMs in this launch: from L2, never a stale L1 line
     if (m > 0.0f) scale = 1.0f / m;
     const int j0 = group * kFactorPoints + SimtSync::tid() * 4;
     const int r0 = band * kFactorRows;
@@ -348,8 +341,9 @@ __device__ void simt_group(const PersistParams &p, int4 (*s_geo)[kSimtTile], uin
     }
 }
 
+// 448 threads x 144 registers = 64,512 of the SM's 65,536 (one CTA per SM)
 template <int BN_MAX>
-__global__ void __launch_bounds__(kPersistThreads, 1)
+__global__ void __maxnreg__(144)
     persist_kernel(const __grid_constant__ PersistParams p, int *status, unsigned long long timeout_ns)
 {
     using C = GemmCfg<BN_MAX, kPersistRoom>;
@@ -393,7 +387,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             } else if (warp == 1) {
                 if (lane == 0) gemm_mma<C>(src, smem, bars, tmem_base, status, timeout_ns);
             } else {
-                gemm_epilogue<C>(src, bars, tmem_base, warp, lane, status, timeout_ns);
+                gemm_epilogue<C, QueueUnits, 32>(src, bars, tmem_base, warp, lane, status, timeout_ns);
             }
         }
     } else {
