@@ -290,24 +290,27 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
             // instruction writes 128 contiguous bytes of out[n][m0 .. m0 + 31]
             const int m = row;
             const bool in_m = m < x.width;
+            constexpr int TR = ROUND / 2;   // accumulator columns per round: 32 (or 16)
+            constexpr int TG = TR / 16;
 #pragma unroll 1
-            for (int cc = 0; cc < x.bn; cc += 32) {
-                const int ncol = min(32, x.bn - cc);   // 16 or 32
+            for (int cc = 0; cc < x.bn; cc += TR) {
+                const int ncol = min(TR, x.bn - cc);   // a multiple of 16
                 const int n0 = x.tn * x.bn + cc;
-                float old[32];
+                float old[TR];
                 if (!first && in_m) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
+                    for (int i = 0; i < TR; ++i)
                         old[i] = (i < ncol && n0 + i < x.height) ? __ldcg(x.out + (long long)(n0 + i) * x.width + m)
                                                                  : 0.0f;
                 }
-                uint32_t r[2][16];
-                tmem_ld16(taddr + (uint32_t)cc, r[0]);
-                if (ncol > 16) tmem_ld16(taddr + (uint32_t)(cc + 16), r[1]);
+                uint32_t r[TG][16];
+#pragma unroll
+                for (int g = 0; g < TG; ++g)
+                    if (g == 0 || ncol > 16 * g) tmem_ld16(taddr + (uint32_t)(cc + 16 * g), r[g]);
                 tmem_ld_wait();
                 if (!in_m) continue;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < TR; ++i) {
                     if (i >= ncol || n0 + i >= x.height) continue;
                     float v = empty_range ? 0.0f : __uint_as_float(r[i >> 4][i & 15]) * unscale;
                     if (!first) v += old[i];

@@ -341,9 +341,10 @@ __device__ void simt_group(const PersistParams &p, int4 (*s_geo)[kSimtTile], uin
     }
 }
 
-// 448 threads x 144 registers = 64,512 of the SM's 65,536 (one CTA per SM)
+// 14 warps, so one sub-partition holds four of them: at most 128 registers a thread (4 x 32 x 128 = the
+// sub-partition's 16,384)
 template <int BN_MAX>
-__global__ void __maxnreg__(144)
+__global__ void __launch_bounds__(kPersistThreads, 1)
     persist_kernel(const __grid_constant__ PersistParams p, int *status, unsigned long long timeout_ns)
 {
     using C = GemmCfg<BN_MAX, kPersistRoom>;
