@@ -122,10 +122,13 @@ enum {
                                    the (pixel tile, point) pairs; 0 = automatic (up to three per resident CTA slot,
                                    each with at least 1024 points; the hardware schedules those beyond the resident
                                    ones as others finish) */
-    CGH_OPT_BATCH_MODE = 15     /* cgh_batch: 0 = one persistent launch for the whole batch (default; GEMM units on
+    CGH_OPT_BATCH_MODE = 15,    /* cgh_batch: 0 = one persistent launch for the whole batch (default; GEMM units on
                                    the tensor cores beside point preparation, factor generation and direct units
                                    on the same SMs); 1 = per-kind launches (preparation and factors per instance,
                                    then one GEMM launch and one direct launch per direct form) */
+    CGH_OPT_BATCH_OVERLAP = 16  /* cgh_batch, persistent launch: 1 = a GEMM unit starts as soon as its own
+                                   hologram's factors are written (default); 0 = once every hologram's factors
+                                   are written */
 };
 
 typedef struct cgh_ctx cgh_ctx;

@@ -34,6 +34,7 @@ CGH_OPT_GEMM_GROUP = 12
 CGH_OPT_PHASE_MODEL = 13
 CGH_OPT_DIRECT_CTAS = 14
 CGH_OPT_BATCH_MODE = 15
+CGH_OPT_BATCH_OVERLAP = 16
 CGH_PHASE_FRESNEL, CGH_PHASE_FRESNEL_PISTON, CGH_PHASE_SPHERICAL = 0, 1, 2
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",

@@ -852,6 +852,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->batch_mode = (int)value;
         return CGH_OK;
+    case CGH_OPT_BATCH_OVERLAP:
+        if (value != 0 && value != 1) return CGH_EINVAL;
+        ctx->batch_overlap = (int)value;
+        return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->profile = value == 1;

@@ -58,7 +58,7 @@ std::vector<uint64_t> plan_key(const cgh_ctx *ctx, const cgh_instance *inst, int
     k.push_back((uint64_t)ctx->form);
     k.push_back((uint64_t)ctx->tol_e9);
     k.push_back(((uint64_t)ctx->gemm_bn << 32) | (uint64_t)(uint32_t)ctx->gemm_chunk);
-    k.push_back((uint64_t)ctx->batch_mode);
+    k.push_back((uint64_t)ctx->batch_mode | ((uint64_t)ctx->batch_overlap << 8));
     k.push_back((uint64_t)(uint32_t)ctx->drop_tile);
     for (int i = 0; i < n; ++i) {
         const cgh_instance &b = inst[i];
@@ -400,6 +400,9 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     pp.heads = reinterpret_cast<int *>(A + z_heads);
     pp.prep_done = reinterpret_cast<int *>(A + z_prep);
     pp.fact_done = reinterpret_cast<int *>(A + z_fact);
+    pp.fact_all = 0;
+    if (ctx->batch_overlap == 0)
+        for (int j : gemm_order) pp.fact_all += jobs[j].fact_units;
 
     rc = begin_capture(plan);
     if (rc) return rc;

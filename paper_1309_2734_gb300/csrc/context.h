@@ -33,6 +33,7 @@ struct cgh_ctx {
     int point_split = 0;
     int direct_ctas = 0;      // CGH_OPT_DIRECT_CTAS
     int batch_mode = 0;       // CGH_OPT_BATCH_MODE
+    int batch_overlap = 1;    // CGH_OPT_BATCH_OVERLAP
     int gemm_splitk = 0;
     int gemm_bn = 0;
     int gemm_chunk = 0;

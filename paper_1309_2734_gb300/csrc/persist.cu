@@ -80,6 +80,8 @@ struct QueueUnits {
     uint64_t *ring_full, *ring_empty;   // 1 arrival; 5 arrivals (the MMA issuer and the four epilogue warps)
     int *status;
     unsigned long long timeout_ns;
+    const int *fact_all_done;   // factor units done over all jobs
+    int fact_all;               // > 0: wait for that many instead of the job's own
 
     struct Cursor {
         uint32_t i;
@@ -133,7 +135,8 @@ struct QueueUnits {
             bool fail = false;
             if (u >= 0) {
                 const int j = units[u].x;
-                if (wait_count(&fact_done[j], jobs[j].fact_units, timeout_ns)) {
+                if (fact_all > 0 ? wait_count(fact_all_done, fact_all, timeout_ns)
+                                 : wait_count(&fact_done[j], jobs[j].fact_units, timeout_ns)) {
                     fence_proxy_async_global();   // the factors' ordinary stores, for the TMA loads that follow
                 } else {
                     atomicOr(status, kStatusTimeout);
@@ -326,6 +329,7 @@ __device__ void simt_group(const PersistParams &p, int4 (*s_geo)[kSimtTile], uin
                 else if (J.form == CGH_GEMM_BF16) run_factor_unit<kFactorBF16>(J, w.z, w.w);
                 else run_factor_unit<kFactorSplit16>(J, w.z, w.w);
                 publish(&p.fact_done[w.y]);
+                if (t == 0) atomicAdd(&p.heads[2], 1);
             }
         } else {
             ok = group_wait(&p.prep_done[w.y], J.prep_units, timeout_ns);
@@ -381,8 +385,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     if (warp < kGemmWarps) {
         if (gemm) {
             const uint32_t tmem_base = *tmem_slot;
-            const QueueUnits src{p.jobs,    p.gemm_units, p.gemm_total, &p.heads[1], p.fact_done,
-                                 ring_u,    ring_full,    ring_empty,   status,      timeout_ns};
+            const QueueUnits src{p.jobs,  p.gemm_units, p.gemm_total, &p.heads[1], p.fact_done, ring_u,
+                                 ring_full, ring_empty,   status,       timeout_ns,  &p.heads[2], p.fact_all};
             if (warp == 0) {
                 if (lane == 0) gemm_producer<C>(src, smem, bars, status, timeout_ns);
             } else if (warp == 1) {
