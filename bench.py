@@ -574,6 +574,9 @@ def run_ours(args):
                 _lib.check(_lib.cgh_autotune(hb.ctx, 0), "cgh_autotune")
                 run_batch(hb, fdev, fouts)   # plan and graph, untimed
                 hb.sync()
+                forms_b = _lib.cgh_batch_forms(hb.ctx)
+                hb.profile(True)
+                hb.profile_read(reset=True)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 reps = 3
                 e0.record(stream)
@@ -582,11 +585,26 @@ def run_ours(args):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 hb.sync()
+                kp = hb.profile_read(reset=True)
+                hb.profile(False)
                 ms = e0.elapsed_time(e1) / reps
                 picked = [o[torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()].cpu().numpy()
                           for o, (c, r) in zip(fouts, picks)]
-            vbatch[f"nrms_{tol:g}"] = {"ms_per_batch": ms, "holograms_per_s": len(frames) / (ms * 1e-3),
-                                        "gevals_per_s": evals / (ms * 1e-3) / 1e9, "_samples": picked}
+            names = {_lib.CGH_DIRECT_SFU: "direct_sfu", _lib.CGH_DIRECT_ACCURATE: "direct_accurate",
+                     _lib.CGH_GEMM_F16: "gemm_f16", _lib.CGH_GEMM_BF16: "gemm_bf16",
+                     _lib.CGH_GEMM_SPLIT16: "gemm_split16"}
+            flops = sum(4.0 * c.evals * (3 if f == _lib.CGH_GEMM_SPLIT16 else 1)
+                        for c, f in zip(frames, forms_b) if f >= _lib.CGH_GEMM_F16)
+            peak_tc = _peaks().get("bf16_tflops") or 1939.7
+            vbatch[f"nrms_{tol:g}"] = {
+                "ms_per_batch": ms, "holograms_per_s": len(frames) / (ms * 1e-3),
+                "gevals_per_s": evals / (ms * 1e-3) / 1e9, "_samples": picked,
+                "forms": {v: sum(1 for f in forms_b if f == k) for k, v in names.items()
+                          if any(f == k for f in forms_b)},
+                # one persistent launch per batch (and the memset of its counters), timed with CUDA events
+                "kernel_ms": {k: v[1] / reps for k, v in kp.items()},
+                "gemm_tflops": flops / (ms * 1e-3) / 1e12,
+                "tensor_frac": flops / (ms * 1e-3) / 1e12 / peak_tc}
         vbatch["frames"] = len(frames)
         vbatch["evals_per_batch"] = evals
         vbatch["sizes"] = sorted({f"{c.width}x{c.height}" for c in frames})
