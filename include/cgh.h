@@ -60,7 +60,9 @@ enum {
     CGH_ECUDA = 3,     /* CUDA runtime/driver error, or no usable device */
     CGH_ETIMEOUT = 4,  /* a bounded wait (device or host) ran out */
     CGH_EINPUT = 5,    /* bad point data, found on the device */
-    CGH_ENOTSUP = 6    /* form or option not available for this problem */
+    CGH_ENOTSUP = 6,   /* form or option not available for this problem */
+    CGH_EBOUNDS = 7    /* debug build (CGH_DEBUG) only: a device-side bounds check failed, the access was
+                          skipped; the release build never returns it */
 };
 
 /* How the hologram is computed. */
@@ -126,9 +128,12 @@ enum {
                                    the tensor cores beside point preparation, factor generation and direct units
                                    on the same SMs); 1 = per-kind launches (preparation and factors per instance,
                                    then one GEMM launch and one direct launch per direct form) */
-    CGH_OPT_BATCH_OVERLAP = 16  /* cgh_batch, persistent launch: 1 = a GEMM unit starts as soon as its own
+    CGH_OPT_BATCH_OVERLAP = 16, /* cgh_batch, persistent launch: 1 = a GEMM unit starts as soon as its own
                                    hologram's factors are written (default); 0 = once every hologram's factors
                                    are written */
+    CGH_OPT_TEST_ALLOC_FAIL = 17 /* test hook: the next n growths of the context's workspace fail as a failed
+                                   cudaMalloc would (the call returns CGH_ENOMEM, nothing is launched, and the
+                                   context stays usable); 0 = off */
 };
 
 typedef struct cgh_ctx cgh_ctx;
@@ -365,6 +370,17 @@ int cgh_profile_read(cgh_ctx *ctx, cgh_kernel_time *out, int max_entries, int *n
 #define CGH_NOALLOC_MAX_POINTS 131072
 int cgh_point_cloud_noalloc(int width, int height, double pitch_m, double lambda_m, const float *d_xyz,
                             const float *d_amp, int64_t n_points, float *d_out, void *cuda_stream);
+
+/*
+ * Checks an autotuner cache file (the JSON that cgh_autotune writes to
+ * CGH_TUNE_CACHE) without touching a GPU: *accepted = 1 when the file at path
+ * was written for device_name (the cache's "device" string) and this ABI and
+ * holds a complete table of finite, non-negative time coefficients, else 0 --
+ * such a file (truncated, edited, another device or ABI, unreadable) is
+ * ignored by cgh_autotune, which then calibrates and rewrites it.  Not part of
+ * the paper's method: a diagnostic of the autotuner's cache.
+ */
+int cgh_tune_cache_check(const char *path, const char *device_name, int *accepted);
 
 /* Waits for the context's work (bounded by CGH_OPT_TIMEOUT_MS); returns and clears the latched status. */
 int cgh_sync(cgh_ctx *ctx);

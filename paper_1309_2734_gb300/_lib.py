@@ -12,10 +12,12 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcgh.so")
+# CGH_LIB_VARIANT=debug loads the debug build (device-side bounds checks, python -m paper_1309_2734_gb300.build
+# --debug) instead of the release library
+LIB_PATH = os.path.join(HERE, "libcgh_debug.so" if os.environ.get("CGH_LIB_VARIANT") == "debug" else "libcgh.so")
 
 # status codes
-CGH_OK, CGH_EINVAL, CGH_ENOMEM, CGH_ECUDA, CGH_ETIMEOUT, CGH_EINPUT, CGH_ENOTSUP = range(7)
+CGH_OK, CGH_EINVAL, CGH_ENOMEM, CGH_ECUDA, CGH_ETIMEOUT, CGH_EINPUT, CGH_ENOTSUP, CGH_EBOUNDS = range(8)
 # forms
 CGH_FORM_AUTO, CGH_DIRECT_SFU, CGH_DIRECT_ACCURATE, CGH_GEMM_F16, CGH_GEMM_BF16, CGH_GEMM_SPLIT16 = range(6)
 FORMS = {"auto": 0, "direct_sfu": 1, "direct_accurate": 2, "gemm_f16": 3, "gemm_bf16": 4, "gemm_split16": 5}
@@ -35,13 +37,14 @@ CGH_OPT_PHASE_MODEL = 13
 CGH_OPT_DIRECT_CTAS = 14
 CGH_OPT_BATCH_MODE = 15
 CGH_OPT_BATCH_OVERLAP = 16
+CGH_OPT_TEST_ALLOC_FAIL = 17
 CGH_PHASE_FRESNEL, CGH_PHASE_FRESNEL_PISTON, CGH_PHASE_SPHERICAL = 0, 1, 2
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
            "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
            "cgh_autotune", "cgh_wave", "cgh_set_reference", "cgh_fresnel", "cgh_wrp_record", "cgh_wrp",
-           "cgh_measure_mufu", "cgh_batch_forms")
+           "cgh_measure_mufu", "cgh_batch_forms", "cgh_tune_cache_check")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -73,7 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         if _lib is not None:
             return _lib
         if not os.path.exists(path):
-            raise RuntimeError(f"libcgh.so not found at {path}; build it with "
+            raise RuntimeError(f"{os.path.basename(path)} not found at {path}; build it with "
                                "`python -m paper_1309_2734_gb300.build` (no CPU fallback exists)")
         lib = ctypes.CDLL(path)
         vp, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -90,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_factors": ([vp, vp, vp, i64, ci, vp, vp, i64], ci),
             "cgh_batch": ([vp, ctypes.POINTER(cgh_instance), ci], ci),
             "cgh_batch_forms": ([vp, ctypes.POINTER(ci), ci, ctypes.POINTER(ci)], ci),
+            "cgh_tune_cache_check": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(ci)], ci),
             "cgh_quantize8": ([vp, vp, i64, ci, vp], ci),
             "cgh_profile_read": ([vp, ctypes.POINTER(cgh_kernel_time), ci, ctypes.POINTER(ci), ci], ci),
             "cgh_sync": ([vp], ci),
@@ -176,6 +180,14 @@ def cgh_batch_forms(ctx: int, max_entries: int = 4096) -> list:
     n = ctypes.c_int(0)
     check(load().cgh_batch_forms(ctx, buf, max_entries, ctypes.byref(n)), "cgh_batch_forms")
     return [int(buf[i]) for i in range(min(n.value, max_entries))]
+
+
+def cgh_tune_cache_check(path: str, device_name: str) -> bool:
+    """Whether the autotuner would accept the cache file at path for the device (no GPU needed)."""
+    ok = ctypes.c_int(0)
+    check(load().cgh_tune_cache_check(path.encode(), device_name.encode(), ctypes.byref(ok)),
+          "cgh_tune_cache_check")
+    return ok.value == 1
 
 
 def cgh_quantize8(ctx: int, d_field: int, n: int, mode: int, d_out: int) -> int:

@@ -1,9 +1,11 @@
 """Builds libcgh.so in-tree from csrc/ with nvcc for sm_103a only.
 
-    python -m paper_1309_2734_gb300.build [--verbose-ptxas]
+    python -m paper_1309_2734_gb300.build [--verbose-ptxas] [--debug]
 
 Translation units are compiled in parallel and linked with the static CUDA
-runtime, so the library needs only the driver at run time.
+runtime, so the library needs only the driver at run time.  --debug builds
+libcgh_debug.so with -DCGH_DEBUG: device-side bounds checks that latch a
+status bit (CGH_EBOUNDS from cgh_sync) instead of faulting.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcgh.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libcgh_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,25 +41,28 @@ def _deps():
         [os.path.join(os.path.dirname(HERE), "include", "cgh.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, ptxas_verbose: bool = False, jobs: int = 0) -> str:
-    if not force and not ptxas_verbose and up_to_date():
-        return LIB
+def build(force: bool = False, ptxas_verbose: bool = False, jobs: int = 0, debug: bool = False) -> str:
+    lib_path, build_dir = (LIB_DEBUG, BUILD_DEBUG) if debug else (LIB, BUILD)
+    if not force and not ptxas_verbose and up_to_date(lib_path):
+        return lib_path
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", CSRC,
                     "-I", os.path.join(os.path.dirname(HERE), "include")]
+    if debug:
+        flags += ["-DCGH_DEBUG"]
     if ptxas_verbose:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -69,17 +76,17 @@ def build(force: bool = False, ptxas_verbose: bool = False, jobs: int = 0) -> st
         for _, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     # cuFFT (Fresnel diffraction) from the toolkit next to nvcc, found again at run time through the rpath
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L", cuda_lib, "-lcufft", "-lpthread",
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L", cuda_lib, "-lcufft", "-lpthread", "-ldl",
                                                          "-Xlinker", f"-rpath,{cuda_lib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force=True, ptxas_verbose="--verbose-ptxas" in sys.argv))
+    print(build(force=True, ptxas_verbose="--verbose-ptxas" in sys.argv, debug="--debug" in sys.argv))

@@ -68,7 +68,7 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
         split = lay.split;
         ws_rest = split > 1 ? (size_t)split * plane * sizeof(float) : 0;
     }
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + ws_rest);
+    int rc = ensure(ctx, &ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + ws_rest);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->ws);
     int4 *geo = reinterpret_cast<int4 *>(base);
@@ -163,7 +163,7 @@ int gemm_units(cgh_ctx *ctx, int mode, int width, int height, int64_t n, const c
     const size_t p_bytes = align_up((size_t)planes * height * ld_max * 2, 256);
     const size_t q_bytes = align_up((size_t)planes * width * ld_max * 2, 256);
     const size_t part_bytes = plan.splits > 1 ? (size_t)plan.splits * plane * sizeof(float) : 0;
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, nbuf * (p_bytes + q_bytes) + part_bytes);
+    int rc = ensure(ctx, &ctx->ws, &ctx->ws_bytes, nbuf * (p_bytes + q_bytes) + part_bytes);
     if (rc) return rc;
     char *fac = static_cast<char *>(ctx->ws);
     float *parts = reinterpret_cast<float *>(fac + nbuf * (p_bytes + q_bytes));
@@ -270,7 +270,7 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
     const size_t gscratch_bytes = try_group ? align_up(group_workspace_bytes((int)n, kMaxPlanes), 256) : 0;
     const size_t groups_bytes = try_group ? align_up((size_t)n * sizeof(int4), 256) : 0;
     const size_t gathered_bytes = try_group ? align_up((size_t)n * sizeof(int2), 256) : 0;
-    int rc = ensure(&ctx->pws, &ctx->pws_bytes,
+    int rc = ensure(ctx, &ctx->pws, &ctx->pws_bytes,
                     geo_bytes + aux_bytes + meta_bytes + gscratch_bytes + groups_bytes + gathered_bytes);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->pws);
@@ -349,7 +349,7 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
         const DirectShape sh = lay.shape;
         const int split = lay.split;
         const size_t part_bytes = split > 1 ? (size_t)split * 2 * plane * sizeof(float) : 0;
-        int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + part_bytes);
+        int rc = ensure(ctx, &ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + part_bytes);
         if (rc) return rc;
         char *base = static_cast<char *>(ctx->ws);
         int4 *geo = reinterpret_cast<int4 *>(base);
@@ -397,7 +397,7 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
     const size_t p_bytes = align_up((size_t)planes * height * ld_max * 2, 256);
     const size_t q_bytes = align_up((size_t)planes * width * ld_max * 2, 256);
     const size_t part_bytes = plan.splits > 1 ? (size_t)plan.splits * 2 * plane * sizeof(float) : 0;
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes + part_bytes);
+    int rc = ensure(ctx, &ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + amax_bytes + p_bytes + q_bytes + part_bytes);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->ws);
     int4 *geo = reinterpret_cast<int4 *>(base);
@@ -462,7 +462,7 @@ int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lamb
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
     const size_t ext_bytes = align_up((size_t)n_pad * sizeof(float4), 256);
     const size_t part_bytes = split > 1 ? (size_t)split * planes * plane * sizeof(float) : 0;
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + ext_bytes + part_bytes);
+    int rc = ensure(ctx, &ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + ext_bytes + part_bytes);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->ws);
     int4 *geo = reinterpret_cast<int4 *>(base);
@@ -607,7 +607,7 @@ int wrp_record(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n, 
     const size_t list_bytes = (size_t)n_pad * bands * sizeof(int);
     const bool binned = list_bytes <= kMaxBandListBytes;
     const size_t band_bytes = binned ? align_up((size_t)(2 * cells + 1) * sizeof(int), 256) + list_bytes : 0;
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + win_bytes + band_bytes);
+    int rc = ensure(ctx, &ctx->ws, &ctx->ws_bytes, geo_bytes + win_bytes + band_bytes);
     if (rc) return rc;
     int4 *geo = reinterpret_cast<int4 *>(ctx->ws);
     uint4 *win = reinterpret_cast<uint4 *>(static_cast<char *>(ctx->ws) + geo_bytes);
@@ -689,6 +689,7 @@ const char *cgh_status_string(int status)
     case CGH_ETIMEOUT: return "bounded wait ran out";
     case CGH_EINPUT: return "invalid point data (z <= 0, NaN, or non-integer / out-of-range x, y)";
     case CGH_ENOTSUP: return "form or option not supported for this problem";
+    case CGH_EBOUNDS: return "a bounds check of the debug build failed";
     default: return "unknown status";
     }
 }
@@ -856,6 +857,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->batch_overlap = (int)value;
         return CGH_OK;
+    case CGH_OPT_TEST_ALLOC_FAIL:
+        if (value < 0 || value > 1000) return CGH_EINVAL;
+        ctx->test_alloc_fail = (int)value;
+        return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->profile = value == 1;
@@ -881,7 +886,7 @@ int cgh_point_cloud_host(cgh_ctx *ctx, const float *h_xyz, const float *h_amp, i
     const size_t xyz_b = align_up((size_t)n_points * 3 * sizeof(float), 256);
     const size_t amp_b = align_up((size_t)n_points * sizeof(float), 256);
     const size_t out_b = (size_t)ctx->width * ctx->height * sizeof(float);
-    int rc = ensure(&ctx->io, &ctx->io_bytes, xyz_b + amp_b + out_b);
+    int rc = ensure(ctx, &ctx->io, &ctx->io_bytes, xyz_b + amp_b + out_b);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->io);
     float *d_xyz = reinterpret_cast<float *>(base);
@@ -914,7 +919,7 @@ int cgh_factors(cgh_ctx *ctx, const float *d_xyz, const float *d_amp, int64_t n_
     const int64_t n_pad = padded_points(n_points);
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
-    int rc = ensure(&ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + 256);
+    int rc = ensure(ctx, &ctx->ws, &ctx->ws_bytes, geo_bytes + aux_bytes + 256);
     if (rc) return rc;
     char *base = static_cast<char *>(ctx->ws);
     int4 *geo = reinterpret_cast<int4 *>(base);
@@ -1100,6 +1105,7 @@ int cgh_sync(cgh_ctx *ctx)
     if (bits != 0 && cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) return cuda_status(cudaGetLastError());
     if (bits & kStatusTimeout) return CGH_ETIMEOUT;
     if (bits & kStatusInput) return CGH_EINPUT;
+    if (bits & kStatusBounds) return CGH_EBOUNDS;
     return CGH_OK;
 }
 

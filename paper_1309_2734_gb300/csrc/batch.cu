@@ -127,10 +127,14 @@ void choose_forms(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan
     }
 }
 
-// (Re)allocates the plan's arena for at least `bytes`.
-int ensure_arena(BatchPlan *plan, size_t bytes)
+// (Re)allocates the plan's arena for at least `bytes` (a pending CGH_OPT_TEST_ALLOC_FAIL is taken as a failure).
+int ensure_arena(cgh_ctx *ctx, BatchPlan *plan, size_t bytes)
 {
     if (bytes <= plan->arena_bytes) return CGH_OK;
+    if (ctx->test_alloc_fail > 0) {
+        --ctx->test_alloc_fail;
+        return CGH_ENOMEM;
+    }
     if (plan->arena) {
         cudaFree(plan->arena);
         plan->arena = nullptr;
@@ -354,7 +358,7 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     }
     const size_t t_simt = L.take(simt.size() * sizeof(int4));
     const size_t t_gemm = L.take(gunits.size() * sizeof(int4));
-    int rc = ensure_arena(plan, L.bytes);
+    int rc = ensure_arena(ctx, plan, L.bytes);
     if (rc) return rc;
     char *A = static_cast<char *>(plan->arena);
     for (int j = 0; j < nj; ++j) {
@@ -397,6 +401,7 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     pp.simt_total = (int)simt.size();
     pp.gemm_units = reinterpret_cast<const int4 *>(A + t_gemm);
     pp.gemm_total = (int)gunits.size();
+    pp.n_jobs = nj;
     pp.heads = reinterpret_cast<int *>(A + z_heads);
     pp.prep_done = reinterpret_cast<int *>(A + z_prep);
     pp.fact_done = reinterpret_cast<int *>(A + z_fact);
@@ -515,7 +520,7 @@ int build_plan_kinds(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *p
         t_doff[w] = L.take(doff[w].size() * sizeof(int));
         t_dunits[w] = L.take(dord[w].size() * sizeof(int2));
     }
-    const int arc = ensure_arena(plan, L.bytes);
+    const int arc = ensure_arena(ctx, plan, L.bytes);
     if (arc) return arc;
     char *A = static_cast<char *>(plan->arena);
     // fill the job tables with device pointers

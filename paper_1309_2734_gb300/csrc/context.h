@@ -10,6 +10,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/cgh.h"
 #include "device_util.cuh"
@@ -32,6 +33,7 @@ struct cgh_ctx {
     int64_t timeout_ms = 5000;
     int point_split = 0;
     int direct_ctas = 0;      // CGH_OPT_DIRECT_CTAS
+    int test_alloc_fail = 0;  // CGH_OPT_TEST_ALLOC_FAIL: workspace growths still to refuse
     int batch_mode = 0;       // CGH_OPT_BATCH_MODE
     int batch_overlap = 1;    // CGH_OPT_BATCH_OVERLAP
     int gemm_splitk = 0;
@@ -116,9 +118,16 @@ inline size_t align_up(size_t v, size_t a)
     return (v + a - 1) / a * a;
 }
 
-inline int ensure(void **buf, size_t *cap, size_t need)
+// Grows a workspace buffer to at least `need` bytes (contents are not kept).  A pending injected failure
+// (CGH_OPT_TEST_ALLOC_FAIL) is taken instead of a growth: the buffer is left as it was and CGH_ENOMEM returned,
+// as when cudaMalloc fails.
+inline int ensure(cgh_ctx *ctx, void **buf, size_t *cap, size_t need)
 {
     if (need <= *cap) return CGH_OK;
+    if (ctx->test_alloc_fail > 0) {
+        --ctx->test_alloc_fail;
+        return CGH_ENOMEM;
+    }
     if (*buf) {
         cudaFree(*buf);
         *buf = nullptr;
@@ -156,16 +165,19 @@ inline cudaEvent_t take_event(cgh_ctx *ctx)
     return e;
 }
 
-// Brackets the launches made in its scope with events on the context's stream.
+// Brackets the launches made in its scope: an NVTX range named for the kernel (always; it costs nothing
+// without a tool attached), and with CGH_OPT_PROFILE events on the context's stream.
 class ProfileScope {
   public:
     ProfileScope(cgh_ctx *ctx, const char *name, int launches, cudaStream_t s = nullptr)
         : ctx_(ctx), name_(name), launches_(launches), stream_(s ? s : ctx->stream)
     {
+        nvtxRangePushA(name);
         if (ctx_->profile && (start_ = take_event(ctx_))) cudaEventRecord(start_, stream_);
     }
     ~ProfileScope()
     {
+        nvtxRangePop();
         if (!start_) return;
         cudaEvent_t stop = take_event(ctx_);
         if (!stop) return;

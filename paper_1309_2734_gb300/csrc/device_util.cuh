@@ -11,7 +11,16 @@ namespace cgh {
 enum : int {
     kStatusInput = 1,     // bad point data (z <= 0, NaN, non-integer or out-of-range x/y)
     kStatusTimeout = 2,   // a bounded device-side wait ran out
+    kStatusBounds = 4,    // a bounds check of the debug build (CGH_DEBUG) failed; the access was skipped
 };
+
+// Debug build (-DCGH_DEBUG): an index that holds by construction is checked, and a failure latches
+// kStatusBounds (the caller skips the access) instead of faulting.  Release builds compile it to true.
+#ifdef CGH_DEBUG
+#define CGH_DCHECK(cond, status) ((cond) ? true : (atomicOr((status), ::cgh::kStatusBounds), false))
+#else
+#define CGH_DCHECK(cond, status) true
+#endif
 
 // Layout of the prepared points (one entry per point, padded with zero-amplitude
 // points to a multiple of the point tile).

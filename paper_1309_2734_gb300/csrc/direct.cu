@@ -63,6 +63,7 @@ struct StreamSink {
     long long units, C, N;
     int tiles_x, width, height;
     bool vec;
+    int *status;
 
     __device__ long long owner(long long u) const { return ((u + 1) * C - 1) / units; }
     // slot of CTA cs's part of tile t: 0 when it is the CTA's first segment, else 1 (its last)
@@ -75,6 +76,8 @@ struct StreamSink {
         const int tid = threadIdx.x;
         const long long c = blockIdx.x;
         const long long t = seg->t;
+        // the tile and the CTA's slot exist (CTA-uniform, so every thread skips alike)
+        if (!CGH_DCHECK(t >= 0 && t < units / N && c < C, status)) return;
         if (!(seg->p0 == 0 && seg->p1 == N)) {
             float4 *mine = slots + (2 * c + slot_of(c, t)) * (long long)(Q4 * NT) + tid;
 #pragma unroll
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(BX *BY, 2)
     __shared__ StreamSeg s_seg;
     init_point_barriers<BX, BY>(s_bar);
     const StreamSink<TL, TR, BX, BY> sink{&s_seg, slots, counters, out, units, (long long)gridDim.x,
-                                          (long long)n_points, tiles_x, width, height, vec};
+                                          (long long)n_points, tiles_x, width, height, vec, status};
     uint32_t kg = 0;
     const long long w0 = (long long)blockIdx.x * units / gridDim.x;
     for (long long w = w0;;) {

@@ -261,6 +261,7 @@ struct PersistParams {
     int simt_total;
     const int4 *gemm_units;     // {job, tile, K chunk, 0}
     int gemm_total;
+    int n_jobs;
     int *heads;                 // [0]: next SIMT unit, [1]: next GEMM unit, [2]: factor units done (all jobs)
     int *prep_done, *fact_done; // per job
     int fact_all;               // > 0: every GEMM unit waits for heads[2] >= fact_all (all jobs' factors first)

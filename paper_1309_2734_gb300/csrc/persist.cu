@@ -82,6 +82,7 @@ struct QueueUnits {
     unsigned long long timeout_ns;
     const int *fact_all_done;   // factor units done over all jobs
     int fact_all;               // > 0: wait for that many instead of the job's own
+    int n_jobs;
 
     struct Cursor {
         uint32_t i;
@@ -133,6 +134,17 @@ struct QueueUnits {
             u = atomicAdd(head, 1);
             if (u >= total) u = -1;
             bool fail = false;
+            if (u >= 0) {
+                const int4 w = units[u];
+                // the unit names a job, a tile and a K range that exist
+                if (!CGH_DCHECK(w.x >= 0 && w.x < n_jobs && w.y >= 0 &&
+                                    w.y < jobs[w.x].g.tiles_m * jobs[w.x].g.tiles_n && w.z >= 0 &&
+                                    w.z * jobs[w.x].kchunk_kb < jobs[w.x].g.nkb,
+                                status)) {
+                    fail = true;
+                    u = -1;
+                }
+            }
             if (u >= 0) {
                 const int j = units[u].x;
                 if (fact_all > 0 ? wait_count(fact_all_done, fact_all, timeout_ns)
@@ -314,7 +326,17 @@ __device__ void simt_group(const PersistParams &p, int4 (*s_geo)[kSimtTile], uin
         const int4 w = *s_unit;
         SimtSync::sync();
         if (w.x < 0) return;
+        // the unit names a job and a block, band or tile of it that exist (uniform over the group)
+        if (!CGH_DCHECK(w.y >= 0 && w.y < p.n_jobs, status)) return;
         const PersistJob &J = p.jobs[w.y];
+        if (!CGH_DCHECK(w.x == kPersistPrep ? w.z >= 0 && w.z < J.n_pad / kPointTile
+                        : w.x == kPersistFactor
+                            ? w.z >= 0 && w.z * kFactorRows < J.height + J.width && w.w >= 0 &&
+                                  w.w * kFactorPoints < J.point_slots
+                            : w.z >= 0 && w.z < J.tiles_x * ((J.height + kDBY * kDTR - 1) / (kDBY * kDTR)) &&
+                                  w.w >= 0 && w.w < J.chunks,
+                        status))
+            return;
         bool ok = true;
         if (w.x == kPersistPrep) {
             const int j = w.z * kPointTile + t;
@@ -386,7 +408,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         if (gemm) {
             const uint32_t tmem_base = *tmem_slot;
             const QueueUnits src{p.jobs,  p.gemm_units, p.gemm_total, &p.heads[1], p.fact_done, ring_u,
-                                 ring_full, ring_empty,   status,       timeout_ns,  &p.heads[2], p.fact_all};
+                                 ring_full, ring_empty,   status,       timeout_ns,  &p.heads[2], p.fact_all,
+                                 p.n_jobs};
             if (warp == 0) {
                 if (lane == 0) gemm_producer<C>(src, smem, bars, status, timeout_ns);
             } else if (warp == 1) {

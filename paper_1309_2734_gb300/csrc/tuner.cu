@@ -17,6 +17,7 @@
 // from and written to a small JSON file keyed by the device name.
 #include "tuner.h"
 
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -226,48 +227,70 @@ void save_cache(const TuneState &t)
     std::fclose(f);
 }
 
-// Reads a cache written by save_cache for the same device and ABI; anything else is ignored.
-bool load_cache(TuneState &t)
+// Parses a cache written by save_cache: accepted only when it names this device and ABI and every one of the
+// kForms x 3 coefficients is finite and not negative (they are seconds, and seconds per evaluation); anything
+// else -- a truncated or edited file, another device, another ABI -- is refused as a whole and the tuner
+// calibrates instead.  Tile widths that the GEMM does not support are skipped.
+bool parse_cache(const std::string &text, const std::string &device, TuneState &out)
 {
-    const char *path = cache_path();
-    if (!path) return false;
-    FILE *f = std::fopen(path, "r");
-    if (!f) return false;
-    std::string text;
-    char buf[4096];
-    size_t got;
-    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
-    std::fclose(f);
-    const std::string dev_key = "\"device\": \"" + t.device + "\"";
-    const std::string abi_key = "\"abi\": " + std::to_string(CGH_ABI_VERSION);
+    const std::string dev_key = "\"device\": \"" + device + "\"";
+    const std::string abi_key = "\"abi\": " + std::to_string(CGH_ABI_VERSION) + ",";
     if (text.find(dev_key) == std::string::npos || text.find(abi_key) == std::string::npos) return false;
     size_t c = text.find("\"coef\": [");
     if (c == std::string::npos) return false;
+    double coef[kForms][3];
     const char *p = text.c_str() + c + 9;
     for (int i = 0; i < kForms; ++i) {
         double a, b, d;
         int n = 0;
-        if (std::sscanf(p, " [%lf, %lf, %lf]%n", &a, &b, &d, &n) != 3) return false;
-        t.coef[i][0] = a;
-        t.coef[i][1] = b;
-        t.coef[i][2] = d;
+        if (std::sscanf(p, " [%lf, %lf, %lf]%n", &a, &b, &d, &n) != 3 || n <= 0) return false;
+        for (double v : {a, b, d})
+            if (!std::isfinite(v) || v < 0.0) return false;
+        coef[i][0] = a;
+        coef[i][1] = b;
+        coef[i][2] = d;
         p += n;
         while (*p == ',' || *p == ' ') ++p;
     }
+    if (*p != ']') return false;
+    std::map<std::string, int> bn;
     size_t bpos = text.find("\"bn\": {");
-    if (bpos != std::string::npos) {
-        const char *q = text.c_str() + bpos + 7;
-        for (;;) {
-            char key[128];
-            int val, n = 0;
-            if (std::sscanf(q, " \"%127[^\"]\": %d%n", key, &val, &n) != 2) break;
-            if (gemm_bn_supported(val)) t.bn[key] = val;
-            q += n;
-            while (*q == ',' || *q == ' ') ++q;
-        }
+    if (bpos == std::string::npos) return false;
+    const char *q = text.c_str() + bpos + 7;
+    for (;;) {
+        char key[128];
+        int val, n = 0;
+        if (std::sscanf(q, " \"%127[^\"]\": %d%n", key, &val, &n) != 2) break;
+        if (gemm_bn_supported(val)) bn[key] = val;
+        q += n;
+        while (*q == ',' || *q == ' ') ++q;
     }
-    t.calibrated = true;
+    while (*q == ' ' || *q == '\n') ++q;
+    if (*q != '}') return false;   // a truncated tile-width table
+    std::memcpy(out.coef, coef, sizeof coef);
+    out.bn = bn;
+    out.calibrated = true;
     return true;
+}
+
+bool read_file(const char *path, std::string &text)
+{
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+    std::fclose(f);
+    return true;
+}
+
+// Reads the cache of CGH_TUNE_CACHE for this device, if there is an acceptable one.
+bool load_cache(TuneState &t)
+{
+    const char *path = cache_path();
+    std::string text;
+    if (!path || !read_file(path, text)) return false;
+    return parse_cache(text, t.device, t);
 }
 
 // Deterministic synthetic cloud (integer positions inside the hologram,
@@ -485,3 +508,14 @@ int choose_form(int width, int height, int64_t n_points, double tol, int num_sms
 }
 
 }  // namespace cgh
+
+extern "C" int cgh_tune_cache_check(const char *path, const char *device_name, int *accepted)
+{
+    if (!path || !device_name || !accepted) return CGH_EINVAL;
+    *accepted = 0;
+    std::string text;
+    if (!cgh::read_file(path, text)) return CGH_OK;
+    cgh::TuneState t;
+    *accepted = cgh::parse_cache(text, device_name, t) ? 1 : 0;
+    return CGH_OK;
+}
