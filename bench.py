@@ -561,7 +561,12 @@ def run_ours(args):
     vbatch = {}
     if not args.no_batch:
         from paper_1309_2734_gb300 import _lib, batch as run_batch
-        frames = workloads.video_batch()
+        from paper_1309_2734_gb300.shard import shard_instances
+        all_frames = workloads.video_batch()
+        # under torchrun every rank takes its share of the frames (largest W*H*N first to the least-loaded rank;
+        # no collective on the data path) and the batch time is the slowest rank's
+        mine = shard_instances([c.evals for c in all_frames], rank, world) if world > 1 else range(len(all_frames))
+        frames = [all_frames[i] for i in mine]
         fdev = [(torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda(), c.width, c.height, c.pitch_m,
                  c.lambda_m) for c in frames]
         fouts = [torch.empty((c.height, c.width), dtype=torch.float32, device="cuda") for c in frames]
@@ -588,6 +593,10 @@ def run_ours(args):
                 kp = hb.profile_read(reset=True)
                 hb.profile(False)
                 ms = e0.elapsed_time(e1) / reps
+                if dist is not None:
+                    t_ms = torch.tensor([ms], device="cuda")
+                    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+                    ms = float(t_ms.item())
                 picked = [o[torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()].cpu().numpy()
                           for o, (c, r) in zip(fouts, picks)]
             names = {_lib.CGH_DIRECT_SFU: "direct_sfu", _lib.CGH_DIRECT_ACCURATE: "direct_accurate",
@@ -596,19 +605,27 @@ def run_ours(args):
             flops = sum(4.0 * c.evals * (3 if f == _lib.CGH_GEMM_SPLIT16 else 1)
                         for c, f in zip(frames, forms_b) if f >= _lib.CGH_GEMM_F16)
             peak_tc = _peaks().get("bf16_tflops") or 1939.7
+            if dist is not None:   # the whole batch's work and GEMM flops over the slowest rank's time
+                tot = torch.tensor([float(evals), flops], device="cuda", dtype=torch.float64)
+                dist.all_reduce(tot)
+                evals_all, flops = float(tot[0].item()), float(tot[1].item())
+            else:
+                evals_all = evals
             vbatch[f"nrms_{tol:g}"] = {
-                "ms_per_batch": ms, "holograms_per_s": len(frames) / (ms * 1e-3),
-                "gevals_per_s": evals / (ms * 1e-3) / 1e9, "_samples": picked,
+                "ms_per_batch": ms, "holograms_per_s": len(all_frames) / (ms * 1e-3),
+                "gevals_per_s": evals_all / (ms * 1e-3) / 1e9, "_samples": picked,
                 "forms": {v: sum(1 for f in forms_b if f == k) for k, v in names.items()
                           if any(f == k for f in forms_b)},
                 # one persistent launch per batch (and the memset of its counters), timed with CUDA events
                 "kernel_ms": {k: v[1] / reps for k, v in kp.items()},
                 "gemm_tflops": flops / (ms * 1e-3) / 1e12,
                 "tensor_frac": flops / (ms * 1e-3) / 1e12 / peak_tc}
-        vbatch["frames"] = len(frames)
-        vbatch["evals_per_batch"] = evals
-        vbatch["sizes"] = sorted({f"{c.width}x{c.height}" for c in frames})
-        vbatch["points"] = [int(min(c.n_points for c in frames)), int(max(c.n_points for c in frames))]
+        vbatch["frames"] = len(all_frames)
+        vbatch["frames_this_rank"] = len(frames)
+        vbatch["sharding"] = f"frames split over {world} ranks (shard_instances)" if world > 1 else "one GPU"
+        vbatch["evals_per_batch"] = sum(c.evals for c in all_frames)
+        vbatch["sizes"] = sorted({f"{c.width}x{c.height}" for c in all_frames})
+        vbatch["points"] = [int(min(c.n_points for c in all_frames)), int(max(c.n_points for c in all_frames))]
         if not args.no_cpu_baseline:
             import oracle
             refs = [oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cc, rr) for c, (cc, rr) in zip(frames, picks)]
