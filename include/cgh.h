@@ -131,9 +131,13 @@ enum {
     CGH_OPT_BATCH_OVERLAP = 16, /* cgh_batch, persistent launch: 1 = a GEMM unit starts as soon as its own
                                    hologram's factors are written (default); 0 = once every hologram's factors
                                    are written */
-    CGH_OPT_TEST_ALLOC_FAIL = 17 /* test hook: the next n growths of the context's workspace fail as a failed
+    CGH_OPT_TEST_ALLOC_FAIL = 17, /* test hook: the next n growths of the context's workspace fail as a failed
                                    cudaMalloc would (the call returns CGH_ENOMEM, nothing is launched, and the
                                    context stays usable); 0 = off */
+    CGH_OPT_DIRECT_SHAPE = 18   /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the thread block;
+                                   0 = automatic (fewest padded pixels), 1 = 32 x 8 threads of 8 x 4 pixels,
+                                   2 = 16 x 16 threads of 8 x 4, 3 = 16 x 16 threads of 12 x 4 with the running
+                                   totals in shared memory */
 };
 
 typedef struct cgh_ctx cgh_ctx;

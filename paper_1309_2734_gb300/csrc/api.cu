@@ -46,12 +46,19 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
         // the shape with the fewer padded pixels; up to kStreamWaves CTAs per resident slot (measured at
         // 1920x1080, 10^4 points: 304 CTAs 4.69 ms, 912 4.64, 2128 4.71, 5100 4.86), each share of at least
         // kStreamSharePoints points beyond the first wave and kStreamMinPoints within it
-        const DirectShape wide = direct_shape(false), tall = direct_shape(true);
         auto padded = [&](const DirectShape &s) {
             return (int64_t)((width + s.tile_w - 1) / s.tile_w) * s.tile_w *
                    (((int64_t)height + s.tile_h - 1) / s.tile_h) * s.tile_h;
         };
-        sh = padded(tall) <= padded(wide) ? tall : wide;
+        // the thread block with the fewest padded pixels, the 12-column block first among equals (fewer
+        // instructions per term); CGH_OPT_DIRECT_SHAPE pins one
+        if (ctx->direct_shape > 0) {
+            sh = direct_stream_shape(ctx->direct_shape - 1);
+        } else {
+            sh = direct_stream_shape(2);
+            for (int v : {1, 0})
+                if (padded(direct_stream_shape(v)) < padded(sh)) sh = direct_stream_shape(v);
+        }
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         const int64_t units = tiles * n;
         const int64_t slots = (int64_t)ctx->num_sms * direct_stream_per_sm(true, sh);
@@ -860,6 +867,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_TEST_ALLOC_FAIL:
         if (value < 0 || value > 1000) return CGH_EINVAL;
         ctx->test_alloc_fail = (int)value;
+        return CGH_OK;
+    case CGH_OPT_DIRECT_SHAPE:
+        if (value < 0 || value > 3) return CGH_EINVAL;
+        ctx->direct_shape = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

@@ -144,7 +144,9 @@ struct StreamSink {
 // partial totals in the CTA's slot (0: its first segment, 1: its last) and counts itself on the tile's counter;
 // the CTA that arrives last sums the tile's parts (StreamSink): no partial planes and no separate reduction
 // pass.  counters (one per tile) are zero at launch; slots hold 2 C tiles of totals, thread-major float4s.
-template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA>
+// SMEM_TOT: the running totals in shared memory (TR TL floats per thread, dynamic), which leaves the registers to a
+// wider thread block's partial sums.
+template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
 __global__ void __launch_bounds__(BX *BY, 2)
     direct_stream_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int width,
                          int height, int tiles_x, long long units, float *__restrict__ out,
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(BX *BY, 2)
     __shared__ alignas(128) uint2 s_aux[2][kPointTile];
     __shared__ alignas(8) uint64_t s_bar[2];
     __shared__ StreamSeg s_seg;
+    extern __shared__ float s_tot[];
     init_point_barriers<BX, BY>(s_bar);
     const StreamSink<TL, TR, BX, BY> sink{&s_seg, slots, counters, out, units, (long long)gridDim.x,
                                           (long long)n_points, tiles_x, width, height, vec, status};
@@ -176,9 +179,9 @@ __global__ void __launch_bounds__(BX *BY, 2)
         __syncthreads();
         const int k0 = p0 / T, k1 = (p1 + T - 1) / T;
         const int drop = (blockIdx.x == 0 && w == w0) ? drop_tile : -1;
-        if (!direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA>(
+        if (!direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA, SMEM_TOT>(
                 geo, aux, k0, k1, (int)(t % tiles_x) * (BX * TL), (int)(t / tiles_x) * (BY * TR), width, height,
-                out, vec, s_geo, s_aux, s_bar, kg, status, timeout_ns, drop, 0, ref, nullptr, p0 - k0 * T,
+                out, vec, s_geo, s_aux, s_bar, kg, status, timeout_ns, drop, 0, ref, s_tot, p0 - k0 * T,
                 p1 - (k1 - 1) * T, sink))
             break;
         w = s_seg.t * n_points + s_seg.p1;
@@ -295,53 +298,70 @@ cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, cons
 
 namespace {
 
-template <int BX, int BY, bool SFU, bool EXTRA>
-cudaError_t direct_stream_as(int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_points, int width,
-                             int height, int tiles_x, long long units, float *out, float4 *slots, int *counters,
-                             bool vec, int *status, uint64_t timeout_ns, int drop_tile, const PhaseRef &ref)
-{
-    direct_stream_kernel<kTL, kTR, BX, BY, SFU, EXTRA><<<ctas, BX * BY, 0, s>>>(
-        geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, timeout_ns, drop_tile,
-        ref);
-    return cudaGetLastError();
-}
+// The balanced layout's thread blocks: TL x TR pixels per thread, BX x BY threads, totals in registers or shared
+// memory.
+template <int TL, int TR, int BX, int BY, bool SMEM_TOT>
+struct StreamCfg {
+    static constexpr size_t kDyn = SMEM_TOT ? (size_t)TL * TR * BX * BY * sizeof(float) : 0;
 
-template <int BX, int BY>
-cudaError_t direct_stream_shaped(bool sfu, bool extra, int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux,
-                                 int n_points, int width, int height, int tiles_x, long long units, float *out,
-                                 float4 *slots, int *counters, bool vec, int *status, uint64_t timeout_ns,
-                                 int drop_tile, const PhaseRef &ref)
-{
+    template <bool SFU, bool EXTRA>
+    static cudaError_t launch(int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_points, int width,
+                              int height, int tiles_x, long long units, float *out, float4 *slots, int *counters,
+                              bool vec, int *status, uint64_t timeout_ns, int drop_tile, const PhaseRef &ref)
+    {
+        direct_stream_kernel<TL, TR, BX, BY, SFU, EXTRA, SMEM_TOT><<<ctas, BX * BY, kDyn, s>>>(
+            geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, timeout_ns,
+            drop_tile, ref);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t dispatch(bool sfu, bool extra, int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux,
+                                int n_points, int width, int height, int tiles_x, long long units, float *out,
+                                float4 *slots, int *counters, bool vec, int *status, uint64_t timeout_ns,
+                                int drop_tile, const PhaseRef &ref)
+    {
 #define CGH_STREAM_ARGS ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, \
                         timeout_ns, drop_tile, ref
-    if (sfu && !extra) return direct_stream_as<BX, BY, true, false>(CGH_STREAM_ARGS);
-    if (sfu) return direct_stream_as<BX, BY, true, true>(CGH_STREAM_ARGS);
-    if (!extra) return direct_stream_as<BX, BY, false, false>(CGH_STREAM_ARGS);
-    return direct_stream_as<BX, BY, false, true>(CGH_STREAM_ARGS);
+        if (sfu && !extra) return launch<true, false>(CGH_STREAM_ARGS);
+        if (sfu) return launch<true, true>(CGH_STREAM_ARGS);
+        if (!extra) return launch<false, false>(CGH_STREAM_ARGS);
+        return launch<false, true>(CGH_STREAM_ARGS);
 #undef CGH_STREAM_ARGS
-}
-
-template <int BX, int BY>
-int stream_resident(bool sfu)
-{
-    int n = 0;
-    const cudaError_t e =
-        sfu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_stream_kernel<kTL, kTR, BX, BY, true, false>,
-                                                            BX * BY, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, direct_stream_kernel<kTL, kTR, BX, BY, false, false>,
-                                                            BX * BY, 0);
-    if (e != cudaSuccess || n < 1) {
-        cudaGetLastError();
-        return 1;
     }
-    return n;
-}
+
+    static int resident(bool sfu)
+    {
+        int n = 0;
+        const cudaError_t e =
+            sfu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      &n, direct_stream_kernel<TL, TR, BX, BY, true, false, SMEM_TOT>, BX * BY, kDyn)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      &n, direct_stream_kernel<TL, TR, BX, BY, false, false, SMEM_TOT>, BX * BY, kDyn);
+        if (e != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            return 1;
+        }
+        return n;
+    }
+};
+
+constexpr int kWideTL = 12;   // the 12-column thread block: 16 x 16 threads of 12 x 4 pixels, totals in shared memory
+using StreamTall = StreamCfg<kTL, kTR, kTallBX, kTallBY, false>;
+using StreamWide = StreamCfg<kTL, kTR, kBX, kBY, false>;
+using StreamTall12 = StreamCfg<kWideTL, kTR, kTallBX, kTallBY, true>;
 
 }  // namespace
 
+DirectShape direct_stream_shape(int variant)
+{
+    if (variant == 2) return DirectShape{kTallBX * kWideTL, kTallBY * kTR, kTallBX * kTallBY, kTallBX};
+    return direct_shape(variant == 1);
+}
+
 int direct_stream_per_sm(bool sfu, const DirectShape &sh)
 {
-    return sh.bx == kTallBX ? stream_resident<kTallBX, kTallBY>(sfu) : stream_resident<kBX, kBY>(sfu);
+    if (sh.tile_w == kTallBX * kWideTL && sh.bx == kTallBX) return StreamTall12::resident(sfu);
+    return sh.bx == kTallBX ? StreamTall::resident(sfu) : StreamWide::resident(sfu);
 }
 
 cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, const int4 *geo, const uint2 *aux,
@@ -360,8 +380,9 @@ cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, cons
     const bool extra = ref.any();
 #define CGH_STREAM_ARGS sfu, extra, ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, sl, counters, vec, \
                         status, timeout_ns, drop_tile, ref
-    if (sh.bx == kTallBX) return direct_stream_shaped<kTallBX, kTallBY>(CGH_STREAM_ARGS);
-    return direct_stream_shaped<kBX, kBY>(CGH_STREAM_ARGS);
+    if (sh.tile_w == kTallBX * kWideTL && sh.bx == kTallBX) return StreamTall12::dispatch(CGH_STREAM_ARGS);
+    if (sh.bx == kTallBX) return StreamTall::dispatch(CGH_STREAM_ARGS);
+    return StreamWide::dispatch(CGH_STREAM_ARGS);
 #undef CGH_STREAM_ARGS
 }
 
