@@ -309,6 +309,14 @@ struct StreamCfg {
                               int height, int tiles_x, long long units, float *out, float4 *slots, int *counters,
                               bool vec, int *status, uint64_t timeout_ns, int drop_tile, const PhaseRef &ref)
     {
+        if constexpr (SMEM_TOT) {   // with the static tiles the totals exceed the default 48 KB
+            static PerDeviceOnce configured;
+            const cudaError_t e = configured.run([] {
+                return cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, SFU, EXTRA, SMEM_TOT>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDyn);
+            });
+            if (e != cudaSuccess) return e;
+        }
         direct_stream_kernel<TL, TR, BX, BY, SFU, EXTRA, SMEM_TOT><<<ctas, BX * BY, kDyn, s>>>(
             geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, timeout_ns,
             drop_tile, ref);
@@ -331,6 +339,17 @@ struct StreamCfg {
 
     static int resident(bool sfu)
     {
+        if constexpr (SMEM_TOT) {   // the limit the launch will set (occupancy counts it)
+            static PerDeviceOnce configured;
+            configured.run([] {
+                cudaError_t e = cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, true, false, SMEM_TOT>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDyn);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, false, false, SMEM_TOT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDyn);
+                return e;
+            });
+        }
         int n = 0;
         const cudaError_t e =
             sfu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
