@@ -134,11 +134,9 @@ enum {
     CGH_OPT_TEST_ALLOC_FAIL = 17, /* test hook: the next n growths of the context's workspace fail as a failed
                                    cudaMalloc would (the call returns CGH_ENOMEM, nothing is launched, and the
                                    context stays usable); 0 = off */
-    CGH_OPT_DIRECT_SHAPE = 18,  /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the thread block;
+    CGH_OPT_DIRECT_SHAPE = 18   /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the thread block;
                                    0 = automatic (fewer padded pixels), 1 = 32 x 8 threads of 8 x 4 pixels,
                                    2 = 16 x 16 threads of 8 x 4 */
-    CGH_OPT_GEMM_PREFETCH = 19  /* GEMM forms, cgh_point_cloud: k-blocks (of 64) ahead of the tensor-map loads at
-                                   which a warp of each CTA asks L2 for the operand rows; 0 = off */
 };
 
 typedef struct cgh_ctx cgh_ctx;

@@ -158,7 +158,6 @@ int gemm_units(cgh_ctx *ctx, int mode, int width, int height, int64_t n, const c
     plan.trans = lay.trans;
     if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
     plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
-    plan.prefetch_kb = ctx->gemm_prefetch;
     plan.accumulate = false;
     // every chunk must write every partial plane: no more splits than the last chunk has k-blocks
     const int64_t last = n - (n_chunks - 1) * chunk;
@@ -396,7 +395,6 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
     plan.trans = lay.trans;
     if (!gemm_bn_supported(plan.bn)) return CGH_ENOTSUP;
     plan.chunk_kb = ctx->gemm_chunk > 0 ? ctx->gemm_chunk : (mode == kFactorSplit16 ? kSplit16ChunkKb : 0);
-    plan.prefetch_kb = ctx->gemm_prefetch;
     plan.accumulate = false;
     const int64_t last = n - (n - 1) / chunk * chunk;
     if (plan.splits > (2 * last + 63) / 64) plan.splits = (int)((2 * last + 63) / 64);
@@ -871,10 +869,6 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_DIRECT_SHAPE:
         if (value < 0 || value > 2) return CGH_EINVAL;
         ctx->direct_shape = (int)value;
-        return CGH_OK;
-    case CGH_OPT_GEMM_PREFETCH:
-        if (value < 0 || value > 256) return CGH_EINVAL;
-        ctx->gemm_prefetch = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

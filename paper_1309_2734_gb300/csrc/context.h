@@ -34,7 +34,6 @@ struct cgh_ctx {
     int point_split = 0;
     int direct_ctas = 0;      // CGH_OPT_DIRECT_CTAS
     int direct_shape = 0;     // CGH_OPT_DIRECT_SHAPE
-    int gemm_prefetch = 0;    // CGH_OPT_GEMM_PREFETCH
     int test_alloc_fail = 0;  // CGH_OPT_TEST_ALLOC_FAIL: workspace growths still to refuse
     int batch_mode = 0;       // CGH_OPT_BATCH_MODE
     int batch_overlap = 1;    // CGH_OPT_BATCH_OVERLAP

@@ -55,9 +55,6 @@ using namespace dev;
 // One hologram: everything in the (grid-constant) kernel parameters.
 struct alignas(64) SingleUnits {
     CUtensorMap p, q, pl, ql;
-    const uint16_t *pa, *pal, *pb, *pbl;   // the same operands as plain memory (the prefetch warp)
-    long long ld;
-    int a_rows, b_rows, prefetch;          // prefetch: k-blocks ahead of the producer (0 = no prefetch warp work)
     float *out;
     const float *amp_max;
     long long slice_stride;
@@ -105,16 +102,8 @@ struct alignas(64) SingleUnits {
         x.vec = vec != 0;
         x.accumulate = accumulate != 0;
         x.trans = trans != 0;
-        x.a_hi = pa;
-        x.a_lo = pal;
-        x.b_hi = pb;
-        x.b_lo = pbl;
-        x.ld = ld;
-        x.a_rows = a_rows;
-        x.b_rows = b_rows;
         return x;
     }
-    __device__ int prefetch_distance() const { return prefetch; }
 };
 
 // A batch: per-CTA unit lists over a job table in global memory.
@@ -137,7 +126,6 @@ struct BatchUnits {
     }
     __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
     __device__ void abort(Cursor &, unsigned long long) const {}
-    __device__ int prefetch_distance() const { return 0; }
     __device__ UnitInfo get(int i) const
     {
         const int2 w = units[i];
@@ -176,11 +164,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const GemmBars bars = gemm_bars<C>(smem);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars.drain + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ uint32_t s_progress;   // k-blocks the producer has issued (the prefetch warp stays near it)
-    if (threadIdx.x == 0) {
-        gemm_init_barriers<C>(bars);
-        s_progress = 0;
-    }
+    if (threadIdx.x == 0) gemm_init_barriers<C>(bars);
     if (warp == 1) {
         tmem_alloc(tmem_slot, C::kTmemCols);
         tmem_relinquish();
@@ -190,13 +174,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     if (warp == 0) {
-        if (lane == 0) gemm_producer<C>(src, smem, bars, status, timeout_ns, &s_progress);
+        if (lane == 0) gemm_producer<C>(src, smem, bars, status, timeout_ns);
     } else if (warp == 1) {
         if (lane == 0) gemm_mma<C>(src, smem, bars, tmem_base, status, timeout_ns);
-    } else if (warp < 6) {
+    } else {
         gemm_epilogue<C>(src, bars, tmem_base, warp, lane, status, timeout_ns);
-    } else if (src.prefetch_distance() > 0) {
-        gemm_prefetch<C>(src, &s_progress, lane, src.prefetch_distance(), timeout_ns);
     }
     __syncthreads();
     if (warp == 1) {
@@ -295,14 +277,6 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
         u.ql = u.q;
     }
     u.trans = tr ? 1 : 0;
-    u.pa = a16;
-    u.pb = b16;
-    u.pal = split3 ? a16 + (int64_t)a_rows * ld : a16;
-    u.pbl = split3 ? b16 + (int64_t)b_rows * ld : b16;
-    u.ld = (long long)ld;
-    u.a_rows = a_rows;
-    u.b_rows = b_rows;
-    u.prefetch = plan.prefetch_kb;
     u.nkb = (int)(ld / kBK);
     u.out = out;
     u.amp_max = amp_max;

@@ -29,7 +29,7 @@ namespace dev {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;   // 64 16-bit elements = one 128-byte swizzle row
-constexpr int kGemmThreads = 224;   // producer, MMA issuer, four epilogue warps, the L2 prefetch warp
+constexpr int kGemmThreads = 192;
 // Shared memory left for the operand ring: the 227 KB a CTA may use, less the 1024-byte alignment slack and the
 // barriers.
 constexpr int kStageRoom = 232448 - 1024 - 256;
@@ -60,10 +60,6 @@ struct UnitInfo {
     bool accumulate;             // add to the output already there (later point chunks)
     bool trans;                  // A = Q, B = P: accumulator rows are hologram columns
     int job = 0;                 // a batch's job (the readiness wait of a queue of units)
-    // the operands' memory, for the L2 prefetch warp: A (pass 2: a_lo) and B (pass 1: b_lo), [rows][ld] 16-bit
-    const uint16_t *a_hi = nullptr, *a_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
-    long long ld = 0;
-    int a_rows = 0, b_rows = 0;
     // A K chunk of a batch's tile: epilogue warp q stores (adds) its quarter of the tile once seq[q] >= seq_k,
     // then sets seq[q] = seq_k + 1, so the chunks of a tile reach the output in K order; nullptr: no ordering.
     int *seq = nullptr;
@@ -106,10 +102,9 @@ __device__ __forceinline__ void gemm_init_barriers(const GemmBars &b)
     fence_barrier_init();
 }
 
-// progress (optional): the producer's count of k-blocks issued, for the prefetch warp.
 template <class C, class Units>
 __device__ __forceinline__ void gemm_producer(const Units &src, uint8_t *smem, const GemmBars &bars, int *status,
-                                              unsigned long long timeout_ns, volatile uint32_t *progress = nullptr)
+                                              unsigned long long timeout_ns)
 {
     uint64_t *full = bars.full, *empty = bars.empty;
     uint32_t it = 0;
@@ -140,7 +135,6 @@ __device__ __forceinline__ void gemm_producer(const Units &src, uint8_t *smem, c
                     mbar_arrive_expect_tx(&full[s], stage_bytes);
                     tma_load_2d(sa, ma, &full[s], kb * kBK, x.tm * kBM);
                     tma_load_2d(sa + C::kStageA, mb, &full[s], kb * kBK, x.tn * x.bn);
-                    if (progress) *progress = it + 1;
                 }
             }
         }
@@ -150,48 +144,6 @@ __device__ __forceinline__ void gemm_producer(const Units &src, uint8_t *smem, c
         // drain: wait (bounded) for the loads of the last kStages issues
         for (uint32_t j = (it > (uint32_t)C::kStages ? it - C::kStages : 0); j < it; ++j)
             mbar_wait(&full[j % C::kStages], (j / C::kStages) & 1u, timeout_ns);
-    }
-}
-
-// L2 prefetch warp: walks the producer's sequence of k-blocks up to `distance` ahead of it and asks L2 for the
-// rows of both operand tiles (one 128-byte line per row and k-block, a lane per row), so the TMA loads that
-// follow find them in L2 instead of waiting for DRAM.  Stops with the sequence, or when the producer has not
-// moved for timeout_ns.
-template <class C, class Units>
-__device__ __forceinline__ void gemm_prefetch(const Units &src, volatile const uint32_t *progress, int lane,
-                                              int distance, unsigned long long timeout_ns)
-{
-    uint32_t it = 0;
-    typename Units::Cursor cur = src.start();
-    UnitInfo x;
-    while (src.next(3, cur, x)) {
-        for (int c0 = x.kb0; c0 < x.kb1; c0 += x.kc) {
-            const int c1 = min(x.kb1, c0 + x.kc);
-            for (int pass = 0; pass < x.passes; ++pass) {
-                const uint16_t *A = pass == 2 ? x.a_lo : x.a_hi;
-                const uint16_t *B = pass == 1 ? x.b_lo : x.b_hi;
-                for (int kb = c0; kb < c1; ++kb, ++it) {
-                    if (*progress + (uint32_t)distance < it) {
-                        const uint64_t t0 = global_timer_ns();
-                        while (*progress + (uint32_t)distance < it) {
-                            __nanosleep(128);
-                            if (global_timer_ns() - t0 > timeout_ns) return;
-                        }
-                    }
-                    const long long col = (long long)kb * kBK;
-                    for (int r = lane; r < kBM; r += 32) {
-                        const int row = x.tm * kBM + r;
-                        if (row < x.a_rows)
-                            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(A + row * x.ld + col));
-                    }
-                    for (int r = lane; r < x.bn; r += 32) {
-                        const int row = x.tn * x.bn + r;
-                        if (row < x.b_rows)
-                            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(B + row * x.ld + col));
-                    }
-                }
-            }
-        }
     }
 }
 

@@ -206,7 +206,6 @@ struct GemmPlan {
     int chunk_kb;      // k-blocks (of 64) per TMEM accumulation chain; 0 = whole split
     bool accumulate;   // add to the output (or partial planes) instead of overwriting
     bool trans;        // A = Q (128-row tiles of hologram columns), B = P; writes out transposed back
-    int prefetch_kb = 0;   // > 0: a warp asks L2 for the operand rows this many k-blocks ahead of the TMA loads
 };
 int gemm_max_ctas(int num_sms);
 bool gemm_bn_supported(int bn);
