@@ -269,6 +269,21 @@ int run_gemm(cgh_ctx *ctx, int form, int width, int height, double pitch, double
             try_group = false;
         }
     }
+    if (ctx->gemm_persistent && !try_group && !piston_on(ctx) && !ref.any()) {
+        // the persistent kernel: factor generation of later K chunks overlaps the GEMM of earlier ones; all
+        // factors at once, so within the factor budget; not while the stream is captured (a new plan copies
+        // its tables to the device and synchronises)
+        const int planes = mode == kFactorSplit16 ? 2 : 1;
+        const int64_t fbytes = (int64_t)planes * (width + height) * ((2 * n + 63) / 64 * 64) * 2;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const bool capturing = cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess ||
+                               cs != cudaStreamCaptureStatusNone;
+        cudaGetLastError();
+        if (!capturing && fbytes <= (ctx->factor_budget_mb << 20)) {
+            const cgh_instance inst{width, height, pitch, lambda, d_xyz, d_amp, n, d_out};
+            return run_single_persistent(ctx, form, inst);
+        }
+    }
     const size_t geo_bytes = align_up((size_t)n_pad * sizeof(int4), 256);
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
     const size_t meta_bytes = 256;   // amax, wscale, meta[4]
@@ -758,6 +773,7 @@ int cgh_destroy(cgh_ctx *ctx)
     for (cudaEvent_t ev : {ctx->ev_ready, ctx->ev_fact[0], ctx->ev_fact[1], ctx->ev_gemm[0], ctx->ev_gemm[1]})
         if (ev) cudaEventDestroy(ev);
     destroy_batch_plan(ctx->batch);
+    destroy_batch_plan(ctx->single);
     destroy_tune_state(ctx->tune);
     delete ctx;
     return rc == CGH_ETIMEOUT ? rc : CGH_OK;
@@ -869,6 +885,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_DIRECT_SHAPE:
         if (value < 0 || value > 2) return CGH_EINVAL;
         ctx->direct_shape = (int)value;
+        return CGH_OK;
+    case CGH_OPT_GEMM_PERSISTENT:
+        if (value != 0 && value != 1) return CGH_EINVAL;
+        ctx->gemm_persistent = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

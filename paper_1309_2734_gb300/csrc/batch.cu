@@ -109,14 +109,17 @@ struct Layout {
 constexpr int kSplit16ChunkKbBatch = 8;
 
 // Form (and, for the GEMM forms, tile width) of every instance: the context's form, or the autotuner's choice.
-void choose_forms(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan, std::vector<int> &bn)
+// forced > 0: that form for every instance.
+void choose_forms(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan, std::vector<int> &bn,
+                  int forced = 0)
 {
     const double tol = (double)ctx->tol_e9 * 1e-9;
     plan->forms.assign(n, CGH_DIRECT_SFU);
     bn.assign(n, 256);
     for (int i = 0; i < n; ++i) {
         if (inst[i].n_points == 0) continue;
-        const int f = ctx->form != CGH_FORM_AUTO
+        const int f = forced > 0 ? forced
+                      : ctx->form != CGH_FORM_AUTO
                           ? ctx->form
                           : tune_choose_form(ctx, inst[i].width, inst[i].height, inst[i].n_points, tol);
         plan->forms[i] = f;
@@ -220,10 +223,10 @@ constexpr int kDirectMaxChunks = 64;
 
 // The persistent plan: one job per instance with points, the SIMT and GEMM unit queues, and a graph of
 // (memset of the counters, memsets of the empty instances' outputs, ONE persistent launch).
-int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan)
+int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *plan, int forced_form = 0)
 {
     std::vector<int> bn;
-    choose_forms(ctx, inst, n, plan, bn);
+    choose_forms(ctx, inst, n, plan, bn, forced_form);
     const int rows_f = persist_factor_rows(), pts_f = persist_factor_points();
     const int dtw = persist_direct_tile_w(), dth = persist_direct_tile_h();
     constexpr int kQ4NT = 8 * 256;   // float4s of one direct tile's totals
@@ -249,7 +252,8 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     const size_t z_prep = L.take((size_t)nj * sizeof(int));
     const size_t z_fact = L.take((size_t)nj * sizeof(int));
     const size_t z_amax = L.take((size_t)nj * sizeof(float));
-    std::vector<size_t> z_count(nj, 0), o_geo(nj), o_aux(nj), o_p(nj, 0), o_q(nj, 0), o_parts(nj, 0);
+    std::vector<size_t> z_count(nj, 0), z_chunk(nj, 0), o_geo(nj), o_aux(nj), o_p(nj, 0), o_q(nj, 0),
+        o_parts(nj, 0);
     std::vector<int64_t> work(nj, 0);
     int bn_max = 0;
     for (int j = 0; j < nj; ++j) {
@@ -269,16 +273,17 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
             const int64_t a_pad = (a_rows + 127) / 128 * 128, b_pad = (int64_t)(b_rows + bn[i] - 1) / bn[i] * bn[i];
             const int kc = J.form == CGH_GEMM_SPLIT16 ? (ctx->gemm_chunk > 0 ? ctx->gemm_chunk : kSplit16ChunkKbBatch)
                                                       : 1;
+            // a multiple of the factor units' 32 k-blocks (so a unit's readiness is whole factor units) and of the
+            // TMEM chain kc
+            const int gkb = 2 * persist_factor_points() / 64;
+            const int step = kc % gkb == 0 ? kc : (gkb % kc == 0 ? gkb : gkb * kc);
             int64_t kcs = (int64_t)(kGemmChunkBytes / ((double)planes * (double)(a_pad + b_pad) * 128.0));
-            kcs = std::max<int64_t>(kGemmChunkMinKb, kcs) / kc * kc;
-            if (kcs <= 0) kcs = kc;
+            kcs = std::max<int64_t>(kGemmChunkMinKb, kcs) / step * step;
+            if (kcs <= 0) kcs = step;
             J.kchunks = (int)((nkb + kcs - 1) / kcs);
-            if (J.kchunks <= 1) {
-                J.kchunks = 1;
-                kcs = nkb;
-            }
             J.kchunk_kb = (int)kcs;
             if (J.kchunks > 1) z_count[j] = L.take((size_t)(a_pad / 128) * ((b_pad) / bn[i]) * 4 * sizeof(int));
+            z_chunk[j] = L.take((size_t)J.kchunks * sizeof(int));
         } else {
             J.tiles_x = (b.width + dtw - 1) / dtw;
             const int tiles = J.tiles_x * ((b.height + dth - 1) / dth);
@@ -335,8 +340,11 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         const int bands = (b.height + b.width + rows_f - 1) / rows_f;
         const int groups = (J.point_slots + pts_f - 1) / pts_f;
         J.fact_units = bands * groups;
-        for (int band = 0; band < bands; ++band)
-            for (int g = 0; g < groups; ++g) simt.push_back(make_int4(kPersistFactor, j, band, g));
+        J.fact_bands = bands;
+        J.fact_groups = groups;
+        // in K order, so the first K chunks' factors are complete first and their GEMM units can start
+        for (int g = 0; g < groups; ++g)
+            for (int band = 0; band < bands; ++band) simt.push_back(make_int4(kPersistFactor, j, band, g));
     }
     for (int j : direct_order) {
         const cgh_instance &b = inst[inst_of[j]];
@@ -353,8 +361,12 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     }
     if (ctx->drop_tile >= 0 && nj > 0) {
         // test hook: job 0 waits for one unit more than exists, so a bounded wait runs out (kStatusTimeout)
-        if (jobs[0].form >= CGH_GEMM_F16) ++jobs[0].fact_units;
-        else ++jobs[0].prep_units;
+        if (jobs[0].form >= CGH_GEMM_F16) {
+            ++jobs[0].fact_units;
+            jobs[0].chunk_extra = 1;
+        } else {
+            ++jobs[0].prep_units;
+        }
     }
     const size_t t_simt = L.take(simt.size() * sizeof(int4));
     const size_t t_gemm = L.take(gunits.size() * sizeof(int4));
@@ -384,6 +396,7 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
                                b.d_out, J.amax, jtrans[j] != 0))
                 return CGH_ECUDA;
             if (J.kchunks > 1) J.tile_seq = reinterpret_cast<int *>(A + z_count[j]);
+            J.chunk_done = reinterpret_cast<int *>(A + z_chunk[j]);
         } else if (J.chunks > 1) {
             J.parts = reinterpret_cast<float4 *>(A + o_parts[j]);
             J.tile_count = reinterpret_cast<int *>(A + z_count[j]);
@@ -610,6 +623,23 @@ int build_plan_kinds(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan *p
 }
 
 }  // namespace
+
+int run_single_persistent(cgh_ctx *ctx, int form, const cgh_instance &inst)
+{
+    if (!ctx->single) ctx->single = new BatchPlan();
+    BatchPlan *plan = ctx->single;
+    std::vector<uint64_t> key = plan_key(ctx, &inst, 1);
+    key.push_back((uint64_t)form);
+    if (!(plan->exec && plan->key == key)) {
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_status(cudaGetLastError());
+        plan->key.clear();
+        const int rc = build_plan_persist(ctx, &inst, 1, plan, form);
+        if (rc) return rc;
+        plan->key = key;
+    }
+    ProfileScope ps(ctx, "gemm_persist", 1);
+    return cuda_status(cudaGraphLaunch(plan->exec, ctx->stream));
+}
 
 int batch_forms(const cgh_ctx *ctx, int *forms, int max_entries)
 {

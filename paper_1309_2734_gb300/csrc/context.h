@@ -54,6 +54,7 @@ struct cgh_ctx {
     size_t pws_bytes = 0;
     int *h_meta = nullptr;    // pinned: counts the grouped GEMM form reads back
     int gemm_group = 0;       // CGH_OPT_GEMM_GROUP
+    int gemm_persistent = 0;  // CGH_OPT_GEMM_PERSISTENT
     int phase_model = CGH_PHASE_FRESNEL;                 // CGH_OPT_PHASE_MODEL
     // Fresnel diffraction: cuFFT plan for the 2H x 2W grid, padded work plane,
     // and the chirp's spectrum for the distance fft_spec_z (0: none yet)
@@ -82,6 +83,7 @@ struct cgh_ctx {
     std::vector<cudaEvent_t> event_pool;
     std::vector<Total> totals;
     cgh::BatchPlan *batch = nullptr;   // cgh_batch: cached plan and CUDA graph
+    cgh::BatchPlan *single = nullptr;  // CGH_OPT_GEMM_PERSISTENT: one hologram's persistent plan and graph
     cgh::TuneState *tune = nullptr;    // autotuner measurements
 };
 
@@ -265,6 +267,7 @@ int factor_mode(int form);
 int resolve_form(cgh_ctx *ctx, int width, int height, int64_t n);
 int run_batch(cgh_ctx *ctx, const cgh_instance *inst, int n_inst);
 int batch_forms(const cgh_ctx *ctx, int *forms, int max_entries);
+int run_single_persistent(cgh_ctx *ctx, int form, const cgh_instance &inst);
 int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int64_t n, float *d_out);
 int run_spherical(cgh_ctx *ctx, int width, int height, double pitch, double lambda, const float *d_xyz,
                   const float *d_amp, int64_t n, int planes, float *d_out);

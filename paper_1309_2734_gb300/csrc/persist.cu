@@ -54,6 +54,7 @@ constexpr int kSimtTile = 64;                               // points per shared
 constexpr int kRing = 4;                                    // GEMM unit ids in flight between the roles
 constexpr int kFactorRows = 32;                             // rows of a factor unit
 constexpr int kFactorPoints = kSimtThreads * 4;             // point slots of a factor unit
+constexpr int kGroupKb = 2 * kFactorPoints / 64;            // k-blocks (of 64 K elements) of one factor unit: 32
 // the direct units' CTA shape: 16 x 16 threads of 8 x 4 pixels (128 x 64-pixel tiles)
 constexpr int kDTL = 8, kDTR = 4, kDBX = 16, kDBY = 16;
 // shared memory for the GEMM ring: the 227 KB a CTA may use, less the alignment slack, the barriers and the
@@ -146,9 +147,14 @@ struct QueueUnits {
                 }
             }
             if (u >= 0) {
-                const int j = units[u].x;
+                const int4 w = units[u];
+                const PersistJob &J = jobs[w.x];
+                // the factor units of this K chunk: every band, the point groups whose slots fall in the chunk
+                const int g0 = w.z * J.kchunk_kb / kGroupKb;
+                const int g1 = min(J.fact_groups, (w.z + 1) * J.kchunk_kb / kGroupKb);
+                const int need = J.fact_bands * (g1 - g0) + J.chunk_extra;
                 if (fact_all > 0 ? wait_count(fact_all_done, fact_all, timeout_ns)
-                                 : wait_count(&fact_done[j], jobs[j].fact_units, timeout_ns)) {
+                                 : wait_count(&J.chunk_done[w.z], need, timeout_ns)) {
                     fence_proxy_async_global();   // the factors' ordinary stores, for the TMA loads that follow
                 } else {
                     atomicOr(status, kStatusTimeout);
@@ -350,8 +356,11 @@ __device__ void simt_group(const PersistParams &p, int4 (*s_geo)[kSimtTile], uin
                 if (J.form == CGH_GEMM_F16) run_factor_unit<kFactorF16>(J, w.z, w.w);
                 else if (J.form == CGH_GEMM_BF16) run_factor_unit<kFactorBF16>(J, w.z, w.w);
                 else run_factor_unit<kFactorSplit16>(J, w.z, w.w);
-                publish(&p.fact_done[w.y]);
-                if (t == 0) atomicAdd(&p.heads[2], 1);
+                publish(&J.chunk_done[w.w * kGroupKb / J.kchunk_kb]);
+                if (t == 0) {
+                    atomicAdd(&p.fact_done[w.y], 1);
+                    atomicAdd(&p.heads[2], 1);
+                }
             }
         } else {
             ok = group_wait(&p.prep_done[w.y], J.prep_units, timeout_ns);

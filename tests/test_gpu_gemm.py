@@ -232,3 +232,36 @@ def test_transposed_point_chunks_accumulate():
     ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 333, 250)
     got = _run(c, "gemm_split16", splitk=2, budget_mb=1, trans=2)
     assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]
+
+
+# ---- the GEMM form of one hologram through the persistent kernel -----------
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_bf16", "gemm_split16"])
+@pytest.mark.parametrize("w,h,n", [(1920, 1080, 20000), (300, 77, 1000), (130, 257, 5), (1024, 64, 40000)])
+def test_persistent_single_hologram(form, w, h, n):
+    """CGH_OPT_GEMM_PERSISTENT: factors generated K chunk by K chunk beside the GEMM of the chunks already there,
+    the chunks of a tile added in K order; against the oracle (sampled pixels at the large size) and the separate
+    launches (same factors, other summation order: within single-precision rounding); a second call replays the
+    graph and gives the same bits."""
+    c = workloads.random_cloud(5100 + n, w, h, n)
+    xyz, amp = _dev(c)
+    with Hologram(w, h, c.pitch_m, c.lambda_m, form=form) as hg:
+        hg.set_option(_lib.CGH_OPT_GEMM_PERSISTENT, 1)
+        hg.profile(True)
+        a = hg.point_cloud(xyz, amp)
+        b = hg.point_cloud(xyz, amp)
+        hg.sync()
+        names = set(hg.profile_read())
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert "gemm_persist" in names
+    assert np.array_equal(a, b)
+    plain = _run(c, form)
+    assert oracle.nrms(a, plain) < (1e-6 if form == "gemm_split16" else NRMS[form] / 4)
+    if w * h * n <= 2e8:
+        ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
+        assert oracle.nrms(a, ref) <= NRMS[form]
+    else:
+        rng = np.random.default_rng(51)
+        cols, rows = rng.integers(0, w, 256), rng.integers(0, h, 256)
+        ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+        assert oracle.nrms(a[rows, cols], ref) <= NRMS[form]
