@@ -256,7 +256,7 @@ def test_persistent_single_hologram(form, w, h, n):
     assert "gemm_persist" in names
     assert np.array_equal(a, b)
     plain = _run(c, form)
-    assert oracle.nrms(a, plain) < (1e-6 if form == "gemm_split16" else NRMS[form] / 4)
+    assert oracle.nrms(a, plain) < (3e-6 if form == "gemm_split16" else NRMS[form] / 4)
     if w * h * n <= 2e8:
         ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
         assert oracle.nrms(a, ref) <= NRMS[form]
