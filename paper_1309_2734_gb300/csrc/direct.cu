@@ -147,7 +147,7 @@ struct StreamSink {
 // SMEM_TOT: the running totals in shared memory (TR TL floats per thread, dynamic), which leaves the registers to a
 // wider thread block's partial sums.
 template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
-__global__ void __launch_bounds__(BX *BY, 512 / (BX * BY))   // 16 warps per SM
+__global__ void __launch_bounds__(BX *BY, 2)
     direct_stream_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int width,
                          int height, int tiles_x, long long units, float *__restrict__ out,
                          float4 *__restrict__ slots, int *__restrict__ counters, bool vec, int *status,
@@ -368,21 +368,16 @@ struct StreamCfg {
 // per term -- was measured slower: 4.84 against 4.65 ms at 1920x1080, 10^4 points.)
 using StreamTall = StreamCfg<kTL, kTR, kTallBX, kTallBY, false>;
 using StreamWide = StreamCfg<kTL, kTR, kBX, kBY, false>;
-// 16 x 8 threads of 8 x 5 pixels (128 x 40 tiles, four 128-thread CTAs per SM): 40 terms per point and thread
-constexpr int kShortBX = 16, kShortBY = 8, kShortTR = 5;
-using StreamShort = StreamCfg<kTL, kShortTR, kShortBX, kShortBY, false>;
 
 }  // namespace
 
 DirectShape direct_stream_shape(int variant)
 {
-    if (variant == 2) return DirectShape{kShortBX * kTL, kShortBY * kShortTR, kShortBX * kShortBY, kShortBX};
     return direct_shape(variant == 1);
 }
 
 int direct_stream_per_sm(bool sfu, const DirectShape &sh)
 {
-    if (sh.threads == kShortBX * kShortBY) return StreamShort::resident(sfu);
     return sh.bx == kTallBX ? StreamTall::resident(sfu) : StreamWide::resident(sfu);
 }
 
@@ -402,7 +397,6 @@ cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, cons
     const bool extra = ref.any();
 #define CGH_STREAM_ARGS sfu, extra, ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, sl, counters, vec, \
                         status, timeout_ns, drop_tile, ref
-    if (sh.threads == kShortBX * kShortBY) return StreamShort::dispatch(CGH_STREAM_ARGS);
     if (sh.bx == kTallBX) return StreamTall::dispatch(CGH_STREAM_ARGS);
     return StreamWide::dispatch(CGH_STREAM_ARGS);
 #undef CGH_STREAM_ARGS

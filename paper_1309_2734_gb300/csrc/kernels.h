@@ -83,8 +83,7 @@ cudaError_t launch_direct(bool sfu, const DirectShape &sh, const int4 *geo, cons
 // the hologram, no padded point is evaluated.  slots: 2 ctas x tile_w x tile_h floats (16-byte aligned);
 // counters: one int per pixel tile (zeroed by the launch).  drop_tile >= 0: CTA 0 never loads that point tile
 // of its range (test hook).
-// variant 0: 32 x 8 threads of 8 x 4 pixels (256 x 32 tiles); 1: 16 x 16 threads of 8 x 4 (128 x 64);
-// 2: 16 x 8 threads of 8 x 5 (128 x 40, four CTAs per SM).
+// variant 0: 32 x 8 threads of 8 x 4 pixels (256 x 32 tiles); 1: 16 x 16 threads of 8 x 4 (128 x 64).
 DirectShape direct_stream_shape(int variant);
 int direct_stream_per_sm(bool sfu, const DirectShape &sh);
 cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, const int4 *geo, const uint2 *aux,
