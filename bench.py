@@ -563,6 +563,8 @@ def run_ours(args):
         from paper_1309_2734_gb300 import _lib, batch as run_batch
         from paper_1309_2734_gb300.shard import shard_instances
         all_frames = workloads.video_batch()
+        if args.batch_frames:   # a subset of the frames (a small case for profilers)
+            all_frames = [all_frames[int(i)] for i in args.batch_frames.split(",")]
         # under torchrun every rank takes its share of the frames (largest W*H*N first to the least-loaded rank;
         # no collective on the data path) and the batch time is the slowest rank's
         mine = shard_instances([c.evals for c in all_frames], rank, world) if world > 1 else range(len(all_frames))
@@ -573,7 +575,7 @@ def run_ours(args):
         evals = sum(c.evals for c in frames)
         rng = np.random.default_rng(6464)
         picks = [(rng.integers(0, c.width, 16), rng.integers(0, c.height, 16)) for c in frames]
-        for tol in (1e-5, 2e-3):
+        for tol in [float(t) for t in args.batch_tols.split(",")]:
             with Hologram(8, 8, 8e-6, 532e-9, form="auto", stream=stream, timeout_ms=20000) as hb:
                 hb.set_option(_lib.CGH_OPT_TOLERANCE_E9, int(round(tol * 1e9)))
                 _lib.check(_lib.cgh_autotune(hb.ctx, 0), "cgh_autotune")
@@ -754,6 +756,9 @@ def main():
                     default=["direct_accurate", "gemm_f16", "gemm_bf16", "gemm_split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame batched workload")
+    ap.add_argument("--batch-frames", default="",
+                    help="comma-separated indices of the video batch's frames to run instead of all 64")
+    ap.add_argument("--batch-tols", default="1e-5,2e-3", help="NRMS classes at which the batch is timed")
     ap.add_argument("--no-fresnel", action="store_true",
                     help="skip the Fresnel diffraction and wavefront-recording workloads of Tables 5-6")
     ap.add_argument("--no-large", action="store_true",
