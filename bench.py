@@ -41,12 +41,12 @@ MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # taken on; a changed source reports null until it is profiled again.
 NCU_TRAFFIC = [
-    # profiles/direct_sfu-1920x1080-n10000.md: 0.293 MB read + 1.584 MB written per launch
+    # profiles/direct_sfu-1920x1080-n10000.md: 0.293 MB read + 1.543 MB written per launch
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000", "src": "direct.cu",
-     "sha1": "d67d029c0bab287edc5a05ec98f6780950919fdc", "bytes_per_launch": 1876736},
-    # profiles/gemm_f16-1920x1080-n50000.md: 600.831 MB read + 3.912 MB written per launch
+     "sha1": "ea2c334c22f1fbc542b0157a6c2437a8419a37d0", "bytes_per_launch": 1836288},
+    # profiles/gemm_f16-1920x1080-n50000.md: 600.789 MB read + 3.344 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000", "src": "gemm.cu",
-     "sha1": "dc9bd0c2611696995acb7c31c0beb99a1dff3738", "bytes_per_launch": 604743680},
+     "sha1": "37e3978e5c43c21db1a0c42b02482e0ca1b91416", "bytes_per_launch": 604133376},
 ]
 
 
