@@ -137,12 +137,15 @@ enum {
     CGH_OPT_DIRECT_SHAPE = 18,  /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the thread block;
                                    0 = automatic (fewer padded pixels), 1 = 32 x 8 threads of 8 x 4 pixels,
                                    2 = 16 x 16 threads of 8 x 4 */
-    CGH_OPT_GEMM_PERSISTENT = 19 /* GEMM forms, cgh_point_cloud: 1 = the hologram as a one-instance batch in the
+    CGH_OPT_GEMM_PERSISTENT = 19, /* GEMM forms, cgh_point_cloud: 1 = the hologram as a one-instance batch in the
                                    persistent kernel (its factors generated K chunk by K chunk while the tensor
                                    cores run the GEMM of the chunks already there; a CUDA graph replayed while the
                                    buffers stay the same), when all its factors fit CGH_OPT_FACTOR_BUDGET_MB, it is
                                    not grouped, has no piston or reference and the stream is not being captured;
                                    0 = the separate factor and GEMM launches */
+    CGH_OPT_GEMM_PAIR = 20      /* GEMM forms, cgh_point_cloud: 1 = the two-SM tcgen05 form (clusters of two CTAs,
+                                   256-row tiles, each CTA holding half of the B tile, so more operand stages fit);
+                                   0 = one CTA per tile */
 };
 
 typedef struct cgh_ctx cgh_ctx;

@@ -151,8 +151,11 @@ int gemm_units(cgh_ctx *ctx, int mode, int width, int height, int64_t n, const c
     GemmPlan plan;
     plan.mode = mode;
     plan.ctas = gemm_max_ctas(ctx->num_sms);
-    const GemmLayout lay = choose_gemm_layout(width, height, nkb_max, plan.ctas, ctx->gemm_bn, ctx->gemm_splitk,
-                                              ctx->gemm_trans);
+    plan.pair = ctx->gemm_pair != 0 && ctx->gemm_bn != 240;
+    const GemmLayout lay = plan.pair ? choose_gemm_layout(width, height, nkb_max, plan.ctas / 2, ctx->gemm_bn,
+                                                          ctx->gemm_splitk, ctx->gemm_trans, 256)
+                                     : choose_gemm_layout(width, height, nkb_max, plan.ctas, ctx->gemm_bn,
+                                                          ctx->gemm_splitk, ctx->gemm_trans);
     plan.bn = lay.bn;
     plan.splits = lay.splits;
     plan.trans = lay.trans;
@@ -889,6 +892,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
     case CGH_OPT_GEMM_PERSISTENT:
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->gemm_persistent = (int)value;
+        return CGH_OK;
+    case CGH_OPT_GEMM_PAIR:
+        if (value != 0 && value != 1) return CGH_EINVAL;
+        ctx->gemm_pair = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;

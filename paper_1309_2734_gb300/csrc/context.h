@@ -55,6 +55,7 @@ struct cgh_ctx {
     int *h_meta = nullptr;    // pinned: counts the grouped GEMM form reads back
     int gemm_group = 0;       // CGH_OPT_GEMM_GROUP
     int gemm_persistent = 0;  // CGH_OPT_GEMM_PERSISTENT
+    int gemm_pair = 0;        // CGH_OPT_GEMM_PAIR
     int phase_model = CGH_PHASE_FRESNEL;                 // CGH_OPT_PHASE_MODEL
     // Fresnel diffraction: cuFFT plan for the 2H x 2W grid, padded work plane,
     // and the chirp's spectrum for the distance fft_spec_z (0: none yet)

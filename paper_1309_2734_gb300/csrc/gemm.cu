@@ -39,6 +39,8 @@
 //
 // Every wait is bounded; on a timeout the CTA latches kStatusTimeout, drains
 // what it issued (again bounded), frees its TMEM and returns.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -90,6 +92,7 @@ struct alignas(64) SingleUnits {
         x.out = out + (long long)split * slice_stride;
         x.amp_max = amp_max;
         x.tm = t % tiles_m;
+        x.row0 = x.tm * kBM;
         x.tn = t / tiles_m;
         x.kb0 = (int)((long long)split * nkb / splits);
         x.kb1 = (int)((long long)(split + 1) * nkb / splits);
@@ -138,6 +141,7 @@ struct BatchUnits {
         x.out = J.out;
         x.amp_max = J.amp_max;
         x.tm = w.y % J.tiles_m;
+        x.row0 = x.tm * kBM;
         x.tn = w.y / J.tiles_m;
         x.kb0 = 0;
         x.kb1 = J.nkb;
@@ -186,6 +190,153 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tc_fence_after();
         tmem_dealloc(tmem_base, C::kTmemCols);
     }
+}
+
+// ---- the two-SM form: clusters of two CTAs, M = 256 ----------------------------------------------------------
+
+// Stages of a CTA of the pair: its 128 x 64 tile of A and its half (BN/2 rows) of the BN x 64 tile of B, so a
+// stage is 30 KB at BN = 224 and seven fit where five of the single-CTA form's 44 KB stages did.
+template <int BN>
+struct GemmPairCfg {
+    static constexpr int kStageA = kBM * kBK * 2;
+    static constexpr int kStageB = (BN / 2) * kBK * 2;
+    static constexpr int kStageBytes = kStageA + kStageB;
+    static constexpr int kStages = kStageRoom / kStageBytes > 8 ? 8 : kStageRoom / kStageBytes;
+    static constexpr int kAccStride = BN <= 128 ? 128 : 256;
+    static constexpr int kTmemCols = 2 * kAccStride;
+    static constexpr int kBarrierBytes = 256;
+    static constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarrierBytes;
+    static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "UMMA N for M = 256, halves of whole swizzle atoms");
+    static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte alignment");
+};
+
+// One hologram in 256-row tiles: cluster c (CTAs 2c and 2c + 1) walks units c, c + clusters, ...; CTA rank r
+// holds rows [256 tm + 128 r, + 128) of the tile.
+struct alignas(64) PairUnits {
+    CUtensorMap p, q, pl, ql;   // B maps with boxes of bn / 2 rows
+    float *out;
+    const float *amp_max;
+    long long slice_stride;
+    int height, width, nkb, splits, tiles_m, tiles_n, kc, passes, bn;
+    uint32_t idesc;
+    int vec;
+    int accumulate;
+    int trans;
+
+    struct Cursor {
+        int u;
+    };
+    __device__ Cursor start() const { return Cursor{(int)(blockIdx.x >> 1)}; }
+    __device__ bool next(int, Cursor &c, UnitInfo &x) const
+    {
+        if (c.u >= tiles_m * tiles_n * splits) return false;
+        x = get(c.u);
+        c.u += (int)(gridDim.x >> 1);
+        return true;
+    }
+    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
+    __device__ void abort(Cursor &, unsigned long long) const {}
+    __device__ UnitInfo get(int u) const
+    {
+        const int n_tiles = tiles_m * tiles_n;
+        const int split = u / n_tiles, t = u % n_tiles;
+        UnitInfo x;
+        x.mp = &p;
+        x.mq = &q;
+        x.mpl = &pl;
+        x.mql = &ql;
+        x.out = out + (long long)split * slice_stride;
+        x.amp_max = amp_max;
+        x.tm = t % tiles_m;
+        x.tn = t / tiles_m;
+        x.row0 = x.tm * 2 * kBM + (int)cluster_rank() * kBM;
+        x.kb0 = (int)((long long)split * nkb / splits);
+        x.kb1 = (int)((long long)(split + 1) * nkb / splits);
+        x.bn = bn;
+        x.passes = passes;
+        x.kc = kc;
+        x.height = height;
+        x.width = width;
+        x.idesc = idesc;
+        x.vec = vec != 0;
+        x.accumulate = accumulate != 0;
+        x.trans = trans != 0;
+        return x;
+    }
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    gemm_pair_kernel(const __grid_constant__ PairUnits src, int *status, unsigned long long timeout_ns)
+{
+    using C = GemmPairCfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const GemmBars bars = gemm_bars<C>(smem);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars.drain + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            mbar_init(&bars.full[s], 1);
+            mbar_init(&bars.empty[s], 1);
+        }
+        mbar_init(&bars.tfull[0], 1);
+        mbar_init(&bars.tfull[1], 1);
+        mbar_init(&bars.tempty[0], 256);   // both CTAs' epilogue threads (only the even CTA's are used)
+        mbar_init(&bars.tempty[1], 256);
+        mbar_init(bars.drain, 1);
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, C::kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync();   // both CTAs' barriers initialised and tensor memory allocated
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    if (warp == 0) {
+        if (lane == 0) gemm_producer_pair<C>(src, smem, bars, rank, status, timeout_ns);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            if (rank == 0) gemm_mma_pair<C>(src, smem, bars, tmem_base, status, timeout_ns);
+            else mbar_wait(bars.drain, 0, timeout_ns);   // the even CTA's last commit: its MMAs are done
+        }
+    } else {
+        gemm_epilogue<C, PairUnits, 64, true>(src, bars, tmem_base, warp, lane, status, timeout_ns);
+    }
+    tc_fence_before();
+    cluster_sync();   // no CTA leaves while the other may still arrive on its barriers
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc_pair(tmem_base, C::kTmemCols);
+    }
+}
+
+template <int BN>
+cudaError_t launch_pair(const PairUnits &u, int clusters, int *status, uint64_t timeout_ns, cudaStream_t s)
+{
+    using C = GemmPairCfg<BN>;
+    static PerDeviceOnce configured;
+    cudaError_t e = configured.run([] {
+        return cudaFuncSetAttribute(gemm_pair_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    });
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters, 1, 1);
+    cfg.blockDim = dim3(kGemmThreads, 1, 1);
+    cfg.dynamicSmemBytes = C::kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemm_pair_kernel<BN>, u, status, (unsigned long long)timeout_ns);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -292,6 +443,43 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
     u.idesc = umma_idesc_f16(bf16, kBM, bn);
     u.vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
     u.accumulate = plan.accumulate ? 1 : 0;
+    if (plan.pair) {
+        // the two-SM form: 256-row tiles, B maps with boxes of bn / 2 rows
+        PairUnits v;
+        v.p = u.p;
+        v.pl = u.pl;
+        if (!make_operand_map(&v.q, B, bf16, ld, b_rows, bn / 2)) return cudaErrorInvalidValue;
+        if (split3) {
+            if (!make_operand_map(&v.ql, b16 + (int64_t)b_rows * ld, false, ld, b_rows, bn / 2))
+                return cudaErrorInvalidValue;
+        } else {
+            v.ql = v.q;
+        }
+        v.out = u.out;
+        v.amp_max = u.amp_max;
+        v.slice_stride = u.slice_stride;
+        v.height = u.height;
+        v.width = u.width;
+        v.nkb = u.nkb;
+        v.splits = u.splits;
+        v.tiles_m = (a_rows + 2 * kBM - 1) / (2 * kBM);
+        v.tiles_n = u.tiles_n;
+        v.kc = u.kc;
+        v.passes = u.passes;
+        v.bn = bn;
+        v.idesc = umma_idesc_f16(bf16, 2 * kBM, bn);
+        v.vec = u.vec;
+        v.accumulate = u.accumulate;
+        v.trans = u.trans;
+        const int pair_units = v.tiles_m * v.tiles_n * v.splits;
+        const int clusters = std::min(plan.ctas / 2, pair_units);
+        switch (bn) {
+        case 128: return launch_pair<128>(v, clusters, status, timeout_ns, s);
+        case 192: return launch_pair<192>(v, clusters, status, timeout_ns, s);
+        case 224: return launch_pair<224>(v, clusters, status, timeout_ns, s);
+        default: return launch_pair<256>(v, clusters, status, timeout_ns, s);
+        }
+    }
     const int units = u.tiles_m * u.tiles_n * u.splits;
     const int ctas = plan.ctas < units ? plan.ctas : units;
     switch (bn) {

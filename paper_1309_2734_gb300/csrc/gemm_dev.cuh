@@ -60,6 +60,7 @@ struct UnitInfo {
     bool accumulate;             // add to the output already there (later point chunks)
     bool trans;                  // A = Q, B = P: accumulator rows are hologram columns
     int job = 0;                 // a batch's job (the readiness wait of a queue of units)
+    int row0 = 0;                // the hologram row (transposed: column) of this CTA's accumulator lane 0
     // A K chunk of a batch's tile: epilogue warp q stores (adds) its quarter of the tile once seq[q] >= seq_k,
     // then sets seq[q] = seq_k + 1, so the chunks of a tile reach the output in K order; nullptr: no ordering.
     int *seq = nullptr;
@@ -209,12 +210,124 @@ __device__ __forceinline__ void gemm_mma(const Units &src, uint8_t *smem, const 
     mbar_wait(drain, 0, timeout_ns);
 }
 
-// ROUND: columns of the accumulator per store round (64 or 32; 32 holds half the registers).
-template <class C, class Units, int ROUND = 64>
+// The producer of a CTA of a two-SM pair: this CTA's 128 rows of A (at row0) and its half of the bn rows of B
+// into its own stages; the loads of both CTAs are counted on the even CTA's full barrier, on which only the even
+// CTA's producer arrives (with both CTAs' bytes).  Stages are freed by the even CTA's MMA commits, which arrive on
+// both CTAs' empty barriers.
+template <class C, class Units>
+__device__ __forceinline__ void gemm_producer_pair(const Units &src, uint8_t *smem, const GemmBars &bars,
+                                                   uint32_t rank, int *status, unsigned long long timeout_ns)
+{
+    uint64_t *full = bars.full, *empty = bars.empty;
+    uint32_t it = 0;
+    bool ok = true;
+    typename Units::Cursor cur = src.start();
+    UnitInfo x;
+    while (ok && src.next(0, cur, x)) {
+        const int half = x.bn / 2;
+        const uint32_t pair_bytes = 2u * (uint32_t)(C::kStageA + half * kBK * 2);
+        for (int c0 = x.kb0; c0 < x.kb1 && ok; c0 += x.kc) {
+            const int c1 = min(x.kb1, c0 + x.kc);
+            for (int pass = 0; pass < x.passes && ok; ++pass) {
+                const CUtensorMap *ma = (pass == 2) ? x.mpl : x.mp;
+                const CUtensorMap *mb = (pass == 1) ? x.mql : x.mq;
+                for (int kb = c0; kb < c1; ++kb, ++it) {
+                    const int s = (int)(it % C::kStages);
+                    const uint32_t ph = (it / C::kStages) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, timeout_ns)) {
+                        atomicOr(status, kStatusTimeout);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *sa = smem + s * C::kStageBytes;
+                    if (rank == 0) mbar_arrive_expect_tx(&full[s], pair_bytes);
+                    const uint32_t bar = cluster_map(&full[s], 0);
+                    tma_load_2d_pair(sa, ma, bar, kb * kBK, x.row0);
+                    tma_load_2d_pair(sa + C::kStageA, mb, bar, kb * kBK, x.tn * x.bn + (int)rank * half);
+                }
+            }
+        }
+    }
+    if (!ok && rank == 0) {
+        // drain: wait (bounded) for the loads of the last kStages issues
+        for (uint32_t j = (it > (uint32_t)C::kStages ? it - C::kStages : 0); j < it; ++j)
+            mbar_wait(&full[j % C::kStages], (j / C::kStages) & 1u, timeout_ns);
+    }
+}
+
+// The MMA issuer of a two-SM pair (one thread of the even CTA): M = 256 (128 rows of each CTA), N = bn (half of
+// its rows in each CTA), commits to both CTAs' barriers; the epilogues of both CTAs release an accumulator on the
+// even CTA's tempty barrier (256 arrivals).
+template <class C, class Units>
+__device__ __forceinline__ void gemm_mma_pair(const Units &src, uint8_t *smem, const GemmBars &bars,
+                                              uint32_t tmem_base, int *status, unsigned long long timeout_ns)
+{
+    uint64_t *full = bars.full, *empty = bars.empty, *tfull = bars.tfull, *tempty = bars.tempty,
+             *drain = bars.drain;
+    uint32_t it = 0;
+    uint32_t uses[2] = {0u, 0u};
+    int nb = 0;
+    bool ok = true;
+    typename Units::Cursor cur = src.start();
+    UnitInfo x;
+    while (ok && src.next(1, cur, x)) {
+        const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
+        const int tb = nb;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int c0 = x.kb0 + c * x.kc, c1 = min(x.kb1, c0 + x.kc);
+            const int b = c == 0 ? tb : 1 - tb;
+            const uint32_t uph = uses[b] & 1u;
+            ++uses[b];
+            if (!mbar_wait(&tempty[b], uph ^ 1u, timeout_ns)) {
+                atomicOr(status, kStatusTimeout);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(b * C::kAccStride);
+            uint32_t acc = 0;
+            for (int pass = 0; pass < x.passes && ok; ++pass) {
+                for (int kb = c0; kb < c1; ++kb, ++it) {
+                    const int s = (int)(it % C::kStages);
+                    const uint32_t ph = (it / C::kStages) & 1u;
+                    if (!mbar_wait(&full[s], ph, timeout_ns)) {
+                        atomicOr(status, kStatusTimeout);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_addr(smem + s * C::kStageBytes);
+                    const uint64_t adesc = sw128_kmajor_desc(a_addr);
+                    const uint64_t bdesc = sw128_kmajor_desc(a_addr + C::kStageA);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        umma_f16_pair(d_tmem, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), x.idesc, acc);
+                        acc = 1;
+                    }
+                    umma_commit_pair(&empty[s]);
+                }
+            }
+            if (!ok) break;
+            umma_commit_pair(&tfull[b]);
+        }
+        nb = 1 - tb;
+    }
+    umma_commit_pair(drain);   // both CTAs learn when every MMA into their tensor memory is done
+    mbar_wait(drain, 0, timeout_ns);
+}
+
+// ROUND: columns of the accumulator per store round (64 or 32; 32 holds half the registers).  PAIR: a CTA of a
+// two-SM pair; the accumulators are released on the even CTA's barriers (the MMA issuer's), remotely from the
+// odd CTA.
+template <class C, class Units, int ROUND = 64, bool PAIR = false>
 __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &bars, uint32_t tmem_base, int warp,
                                               int lane, int *status, unsigned long long timeout_ns)
 {
     uint64_t *tfull = bars.tfull, *tempty = bars.tempty;
+    auto release = [&](int b) {
+        if constexpr (PAIR) mbar_arrive_cluster(cluster_map(&tempty[b], 0));
+        else mbar_arrive(&tempty[b]);
+    };
     const int q = warp & 3;   // TMEM lane quarter this warp may access
     const int row_in_tile = q * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
@@ -226,7 +339,7 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
     while (ok && src.next(2, cur, x)) {
         const bool empty_range = x.kb1 <= x.kb0;
         const int nch = x.kb1 > x.kb0 ? (x.kb1 - x.kb0 + x.kc - 1) / x.kc : 1;
-        const int row = x.tm * kBM + row_in_tile;
+        const int row = x.row0 + row_in_tile;
         float *dst = x.out + (long long)row * x.width;
         const int tb = nb;
         nb = 1 - tb;
@@ -267,7 +380,7 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
             }
             tmem_st_wait();
             tc_fence_before();
-            mbar_arrive(&tempty[1 - tb]);
+            release(1 - tb);
         }
         if (!ok) break;
         if (x.seq != nullptr) {
@@ -378,7 +491,7 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
             if (lane == 0) st_release(&x.seq[q], x.seq_k + 1);
         }
         tc_fence_before();
-        mbar_arrive(&tempty[tb]);
+        release(tb);
     }
 }
 

@@ -206,6 +206,7 @@ struct GemmPlan {
     int chunk_kb;      // k-blocks (of 64) per TMEM accumulation chain; 0 = whole split
     bool accumulate;   // add to the output (or partial planes) instead of overwriting
     bool trans;        // A = Q (128-row tiles of hologram columns), B = P; writes out transposed back
+    bool pair = false; // the two-SM form (clusters of two CTAs, 256-row tiles, half of B in each CTA); bn != 240
 };
 int gemm_max_ctas(int num_sms);
 bool gemm_bn_supported(int bn);

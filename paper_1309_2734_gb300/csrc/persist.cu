@@ -103,6 +103,7 @@ struct QueueUnits {
         x.out = J.out;
         x.amp_max = J.amp_max;
         x.tm = w.y % J.tiles_m;
+        x.row0 = x.tm * kBM;
         x.tn = w.y / J.tiles_m;
         x.kb0 = w.z * P.kchunk_kb;
         x.kb1 = min(J.nkb, x.kb0 + P.kchunk_kb);

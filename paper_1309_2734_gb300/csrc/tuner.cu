@@ -114,7 +114,7 @@ int choose_gemm_bn(int width)
 }
 
 GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, int force_bn, int force_splits,
-                              int force_trans)
+                              int force_trans, int tile_m)
 {
     static const int cands[] = {256, 240, 224, 192, 128};
     GemmLayout best{false, 256, 1};
@@ -123,9 +123,10 @@ GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas,
         if (force_trans == 1 && tr) continue;    // 1: never transposed
         if (force_trans == 2 && !tr) continue;   // 2: always transposed
         const int64_t a_rows = tr ? width : height, b_rows = tr ? height : width;
-        const int64_t tiles_m = (a_rows + 127) / 128;
+        const int64_t tiles_m = (a_rows + tile_m - 1) / tile_m;
         for (int bn : cands) {
             if (force_bn > 0 && bn != force_bn) continue;
+            if (tile_m == 256 && bn == 240) continue;   // the two-SM form: halves of whole 32-row groups
             const int64_t tiles = tiles_m * ((b_rows + bn - 1) / bn);
             for (int64_t s = 1; s <= 16; ++s) {
                 if (force_splits > 0 && s != force_splits) continue;

@@ -33,8 +33,9 @@ struct GemmLayout {
     int bn;
     int splits;
 };
+// tile_m: rows of an A tile (128; 256 for the two-SM form, whose ctas are clusters of two).
 GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, int force_bn, int force_splits,
-                              int force_trans);
+                              int force_trans, int tile_m = 128);
 
 // GEMM tile width (columns of the hologram per tile) with the least padding.
 int choose_gemm_bn(int width);

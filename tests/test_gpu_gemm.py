@@ -265,3 +265,28 @@ def test_persistent_single_hologram(form, w, h, n):
         cols, rows = rng.integers(0, w, 256), rng.integers(0, h, 256)
         ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
         assert oracle.nrms(a[rows, cols], ref) <= NRMS[form]
+
+
+# ---- the two-SM GEMM (clusters of two CTAs, 256-row tiles) -------------------
+
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_bf16", "gemm_split16"])
+@pytest.mark.parametrize("w,h,n,trans", [(300, 77, 1000, 0), (130, 257, 5, 0), (1920, 1080, 20000, 0),
+                                         (1920, 1080, 20000, 2), (520, 300, 3000, 2)])
+def test_pair_gemm(form, w, h, n, trans):
+    """CGH_OPT_GEMM_PAIR: the tcgen05 MMA of a CTA pair (M = 256, each CTA half of B) against the oracle and the
+    one-CTA form (the same products, so equal within single-precision rounding of the accumulation)."""
+    c = workloads.random_cloud(5300 + n + w, w, h, n)
+    xyz, amp = _dev(c)
+    with Hologram(w, h, c.pitch_m, c.lambda_m, form=form, timeout_ms=3000) as hg:
+        hg.set_option(_lib.CGH_OPT_GEMM_PAIR, 1)
+        hg.set_option(_lib.CGH_OPT_GEMM_GROUP, 1)
+        if trans:
+            hg.set_option(_lib.CGH_OPT_GEMM_TRANSPOSE, trans)
+        a = hg.point_cloud(xyz, amp)
+        hg.sync()
+        a = a.cpu().numpy()
+    plain = _run(c, form, trans=trans or None)
+    assert oracle.nrms(a, plain) < (3e-6 if form == "gemm_split16" else NRMS[form] / 4)
+    if w * h * n <= 2e8:
+        ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
+        assert oracle.nrms(a, ref) <= NRMS[form]
