@@ -143,9 +143,11 @@ enum {
                                    buffers stay the same), when all its factors fit CGH_OPT_FACTOR_BUDGET_MB, it is
                                    not grouped, has no piston or reference and the stream is not being captured;
                                    0 = the separate factor and GEMM launches */
-    CGH_OPT_GEMM_PAIR = 20      /* GEMM forms, cgh_point_cloud: 1 = the two-SM tcgen05 form (clusters of two CTAs,
-                                   256-row tiles, each CTA holding half of the B tile, so more operand stages fit);
-                                   0 = one CTA per tile */
+    CGH_OPT_GEMM_PAIR = 20      /* GEMM forms, cgh_point_cloud: the two-SM tcgen05 form (clusters of two CTAs,
+                                   256-row tiles, each CTA holding half of the B tile, so more operand stages fit)
+                                   or one CTA per 128-row tile.  0 = chosen with the tile width and K splits by the
+                                   measured time model (default), 1 = always the two-SM form (not at width 240),
+                                   2 = never */
 };
 
 typedef struct cgh_ctx cgh_ctx;
@@ -393,6 +395,21 @@ int cgh_point_cloud_noalloc(int width, int height, double pitch_m, double lambda
  * the paper's method: a diagnostic of the autotuner's cache.
  */
 int cgh_tune_cache_check(const char *path, const char *device_name, int *accepted);
+
+/*
+ * The launch shape cgh_point_cloud gives the GEMM of a hologram of
+ * width x height pixels and n_points points in form (CGH_GEMM_F16,
+ * CGH_GEMM_BF16 or CGH_GEMM_SPLIT16; not grouped) on a device of num_sms SMs
+ * with every option at its default, written to layout[0..3]: 1 when the
+ * 128-row A tiles are tiles of hologram columns (the product written back
+ * transposed), else 0; the tile width (columns of the B tile); the K splits;
+ * 1 for the two-SM form (CGH_OPT_GEMM_PAIR), else 0.  Host only: no GPU is
+ * touched.  Returns CGH_EINVAL for sides outside [1, 16384], n_points < 1,
+ * num_sms < 1, another form or a null layout.  Not part of the paper's
+ * method: a diagnostic of the GEMM's launch-shape choice (Section 2.1,
+ * Eq. 5, written as the product of the factors).
+ */
+int cgh_gemm_layout(int width, int height, int64_t n_points, int form, int num_sms, int *layout);
 
 /* Waits for the context's work (bounded by CGH_OPT_TIMEOUT_MS); returns and clears the latched status. */
 int cgh_sync(cgh_ctx *ctx);

@@ -47,7 +47,7 @@ EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", 
            "cgh_set_form", "cgh_set_option", "cgh_point_cloud", "cgh_point_cloud_host", "cgh_factors",
            "cgh_batch", "cgh_quantize8", "cgh_profile_read", "cgh_sync", "cgh_point_cloud_noalloc",
            "cgh_autotune", "cgh_wave", "cgh_set_reference", "cgh_fresnel", "cgh_wrp_record", "cgh_wrp",
-           "cgh_measure_mufu", "cgh_batch_forms", "cgh_tune_cache_check")
+           "cgh_measure_mufu", "cgh_batch_forms", "cgh_tune_cache_check", "cgh_gemm_layout")
 CGH_NOALLOC_MAX_POINTS = 131072
 
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "cgh_batch": ([vp, ctypes.POINTER(cgh_instance), ci], ci),
             "cgh_batch_forms": ([vp, ctypes.POINTER(ci), ci, ctypes.POINTER(ci)], ci),
             "cgh_tune_cache_check": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(ci)], ci),
+            "cgh_gemm_layout": ([ci, ci, i64, ci, ci, ctypes.POINTER(ci)], ci),
             "cgh_quantize8": ([vp, vp, i64, ci, vp], ci),
             "cgh_profile_read": ([vp, ctypes.POINTER(cgh_kernel_time), ci, ctypes.POINTER(ci), ci], ci),
             "cgh_sync": ([vp], ci),
@@ -191,6 +192,14 @@ def cgh_tune_cache_check(path: str, device_name: str) -> bool:
     check(load().cgh_tune_cache_check(path.encode(), device_name.encode(), ctypes.byref(ok)),
           "cgh_tune_cache_check")
     return ok.value == 1
+
+
+def cgh_gemm_layout(width: int, height: int, n_points: int, form: int, num_sms: int) -> dict:
+    """The GEMM launch shape cgh_point_cloud takes at default options (no GPU needed)."""
+    out = (ctypes.c_int * 4)()
+    check(load().cgh_gemm_layout(int(width), int(height), int(n_points), int(form), int(num_sms), out),
+          "cgh_gemm_layout")
+    return {"transposed": bool(out[0]), "bn": int(out[1]), "splits": int(out[2]), "pair": bool(out[3])}
 
 
 def cgh_quantize8(ctx: int, d_field: int, n: int, mode: int, d_out: int) -> int:

@@ -131,15 +131,22 @@ using FactorLaunch = std::function<cudaError_t(int64_t u0, int64_t nu, void *P, 
 // 5x10^4 points: 0.428 ms without, 0.428-0.46 ms with 2-4 stages, so it is
 // off by default.)  The epilogue multiplies by *scale, the factor of Q (or
 // P) that keeps the FP16 operands within range.
+// Points (K units) per factor chunk when one chunk's P and Q may take budget bytes.
+static int64_t gemm_chunk_units(int mode, int width, int height, int64_t budget)
+{
+    const int planes = mode == kFactorSplit16 ? 2 : 1;
+    const int64_t bytes_per_unit = (int64_t)planes * (width + height) * 2 * 2;
+    const int64_t chunk = budget / bytes_per_unit / 32 * 32;
+    return chunk < 32 ? 32 : chunk;
+}
+
 int gemm_units(cgh_ctx *ctx, int mode, int width, int height, int64_t n, const char *factor_name,
                const FactorLaunch &factors, const float *scale, float *d_out)
 {
     const int planes = mode == kFactorSplit16 ? 2 : 1;
-    const int64_t bytes_per_unit = (int64_t)planes * (width + height) * 2 * 2;
     const int depth = ctx->gemm_pipeline;
     const int64_t budget = (ctx->factor_budget_mb << 20) / (depth > 1 ? 2 : 1);   // per factor buffer
-    int64_t chunk = budget / bytes_per_unit / 32 * 32;
-    if (chunk < 32) chunk = 32;
+    int64_t chunk = gemm_chunk_units(mode, width, height, budget);
     if (depth > 1 && n >= (int64_t)depth * kPipelineMinPoints) {
         const int64_t even = ((n + depth - 1) / depth + 31) / 32 * 32;
         if (even < chunk) chunk = even;
@@ -151,11 +158,9 @@ int gemm_units(cgh_ctx *ctx, int mode, int width, int height, int64_t n, const c
     GemmPlan plan;
     plan.mode = mode;
     plan.ctas = gemm_max_ctas(ctx->num_sms);
-    plan.pair = ctx->gemm_pair != 0 && ctx->gemm_bn != 240;
-    const GemmLayout lay = plan.pair ? choose_gemm_layout(width, height, nkb_max, plan.ctas / 2, ctx->gemm_bn,
-                                                          ctx->gemm_splitk, ctx->gemm_trans, 256)
-                                     : choose_gemm_layout(width, height, nkb_max, plan.ctas, ctx->gemm_bn,
-                                                          ctx->gemm_splitk, ctx->gemm_trans);
+    const GemmLayout lay = choose_gemm_layout(width, height, nkb_max, plan.ctas, mode == kFactorSplit16,
+                                              ctx->gemm_bn, ctx->gemm_splitk, ctx->gemm_trans, ctx->gemm_pair);
+    plan.pair = lay.pair;
     plan.bn = lay.bn;
     plan.splits = lay.splits;
     plan.trans = lay.trans;
@@ -225,6 +230,30 @@ int gemm_units(cgh_ctx *ctx, int mode, int width, int height, int64_t n, const c
     ProfileScope ps(ctx, "reduce_slices", 1);
     return cuda_status(launch_reduce_slices(parts, plan.splits, plane, plane, d_out, ctx->stream));
 }
+
+}  // namespace cgh
+
+extern "C" int cgh_gemm_layout(int width, int height, int64_t n_points, int form, int num_sms, int *layout)
+{
+    using namespace cgh;
+    if (width < 1 || height < 1 || width > kMaxSide || height > kMaxSide || n_points < 1 || num_sms < 1 || !layout)
+        return CGH_EINVAL;
+    if (form < CGH_GEMM_F16 || form > CGH_GEMM_SPLIT16) return CGH_EINVAL;
+    const int mode = factor_mode(form);
+    int64_t chunk = gemm_chunk_units(mode, width, height, kDefaultFactorBudgetMb << 20);
+    if (chunk > n_points) chunk = n_points;
+    const GemmLayout lay = choose_gemm_layout(width, height, (2 * chunk + 63) / 64, gemm_max_ctas(num_sms),
+                                              mode == kFactorSplit16, 0, 0, 0, 0);
+    const int64_t last = n_points - (n_points - 1) / chunk * chunk;
+    const int64_t nkb_last = (2 * last + 63) / 64;
+    layout[0] = lay.trans ? 1 : 0;
+    layout[1] = lay.bn;
+    layout[2] = lay.splits > nkb_last ? (int)nkb_last : lay.splits;
+    layout[3] = lay.pair ? 1 : 0;
+    return CGH_OK;
+}
+
+namespace cgh {
 
 // Copies n ints of device memory to the context's pinned buffer and waits for
 // them (bounded like cgh_sync); the grouped form's two reads of counts.
@@ -406,8 +435,9 @@ int run_wave(cgh_ctx *ctx, int form, const float *d_xyz, const float *d_amp, int
     GemmPlan plan;
     plan.mode = mode;
     plan.ctas = gemm_max_ctas(ctx->num_sms);
-    const GemmLayout lay = choose_gemm_layout(width, height, ld_max / 64, plan.ctas, ctx->gemm_bn, ctx->gemm_splitk,
-                                              ctx->gemm_trans);
+    // one CTA per tile: the complex wave's two output planes have no two-SM form
+    const GemmLayout lay = choose_gemm_layout(width, height, ld_max / 64, plan.ctas, mode == kFactorSplit16,
+                                              ctx->gemm_bn, ctx->gemm_splitk, ctx->gemm_trans, 2);
     plan.bn = lay.bn;
     plan.splits = lay.splits;
     plan.trans = lay.trans;
@@ -894,7 +924,7 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         ctx->gemm_persistent = (int)value;
         return CGH_OK;
     case CGH_OPT_GEMM_PAIR:
-        if (value != 0 && value != 1) return CGH_EINVAL;
+        if (value < 0 || value > 2) return CGH_EINVAL;
         ctx->gemm_pair = (int)value;
         return CGH_OK;
     case CGH_OPT_PROFILE:

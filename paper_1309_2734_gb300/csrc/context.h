@@ -17,6 +17,7 @@
 #include "kernels.h"
 
 namespace cgh {
+constexpr int64_t kDefaultFactorBudgetMb = 2048;   // factor workspace of one chunk of points, MiB
 struct BatchPlan;
 struct TuneState;
 void destroy_batch_plan(BatchPlan *plan);
@@ -41,7 +42,7 @@ struct cgh_ctx {
     int gemm_bn = 0;
     int gemm_chunk = 0;
     int drop_tile = -1;       // CGH_OPT_TEST_DROP_TILE
-    int64_t factor_budget_mb = 2048;   // CGH_OPT_FACTOR_BUDGET_MB
+    int64_t factor_budget_mb = cgh::kDefaultFactorBudgetMb;   // CGH_OPT_FACTOR_BUDGET_MB
     int gemm_trans = 0;                // CGH_OPT_GEMM_TRANSPOSE
     int gemm_pipeline = 1;             // CGH_OPT_GEMM_PIPELINE (measured: no gain on GB300, off)
     cudaStream_t side_stream = nullptr;   // factor generation of the next point chunk

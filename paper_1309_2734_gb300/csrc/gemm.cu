@@ -444,7 +444,8 @@ cudaError_t launch_gemm(const GemmPlan &plan, const void *P, const void *Q, int 
     u.vec = (width % 4 == 0) && (slice_stride % 4 == 0) && ((uintptr_t)out % 16 == 0);
     u.accumulate = plan.accumulate ? 1 : 0;
     if (plan.pair) {
-        // the two-SM form: 256-row tiles, B maps with boxes of bn / 2 rows
+        // the two-SM form: 256-row tiles, B maps with boxes of bn / 2 rows (whole 32-row groups: not at 240)
+        if (bn == 240) return cudaErrorInvalidValue;
         PairUnits v;
         v.p = u.p;
         v.pl = u.pl;

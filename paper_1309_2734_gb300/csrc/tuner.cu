@@ -113,36 +113,65 @@ int choose_gemm_bn(int width)
     return best;
 }
 
-GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, int force_bn, int force_splits,
-                              int force_trans, int tile_m)
+// Time of one k-block (64 K elements) of one GEMM unit, in microseconds, by tile width, for the one-CTA and the
+// two-SM form (index 0 and 1) of the FP16/BF16 GEMM and of split FP16 (three products per k-block).  Measured on
+// GB300 (least time per k-block of a unit over 1024x1024, 1920x1080 and 3840x2160 holograms, 4 10^3 to 1.5 10^5
+// points, every width, split and orientation): up to a width of 224 it hardly depends on the width, so a unit is
+// bound by its operand stream, not by its MMAs; the 4-stage ring of the 256-wide one-CTA tile is slower, the
+// two-SM form's 256-wide tile (half of B per CTA) is not.  240 is interpolated (one-CTA form only).
+struct KbCost {
+    int bn;
+    double f16[2], split[2];
+};
+static const KbCost kKbCost[] = {
+    {128, {0.273, 0.269}, {0.908, 0.969}}, {192, {0.271, 0.269}, {0.924, 0.992}},
+    {224, {0.272, 0.275}, {0.939, 1.025}}, {240, {0.295, 0.0}, {0.99, 0.0}},
+    {256, {0.318, 0.274}, {1.048, 1.035}},
+};
+// Effective bandwidth of the split reduction, bytes per microsecond.
+constexpr double kReduceBytesPerUs = 3.0e6;
+
+GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, bool split_form, int force_bn,
+                              int force_splits, int force_trans, int force_pair)
 {
-    static const int cands[] = {256, 240, 224, 192, 128};
-    GemmLayout best{false, 256, 1};
+    GemmLayout best{false, 256, 1, false};
     double best_t = 1e300;
-    for (int tr = 0; tr < 2; ++tr) {
-        if (force_trans == 1 && tr) continue;    // 1: never transposed
-        if (force_trans == 2 && !tr) continue;   // 2: always transposed
-        const int64_t a_rows = tr ? width : height, b_rows = tr ? height : width;
-        const int64_t tiles_m = (a_rows + tile_m - 1) / tile_m;
-        for (int bn : cands) {
-            if (force_bn > 0 && bn != force_bn) continue;
-            if (tile_m == 256 && bn == 240) continue;   // the two-SM form: halves of whole 32-row groups
-            const int64_t tiles = tiles_m * ((b_rows + bn - 1) / bn);
-            for (int64_t s = 1; s <= 16; ++s) {
-                if (force_splits > 0 && s != force_splits) continue;
-                if (force_splits <= 0 && s > 1 && s * 4 > k_blocks) break;
-                const int64_t rounds = (tiles * s + ctas - 1) / ctas;
-                // critical path: rounds of units of (k_blocks / s) k-steps on a 128 x bn tile;
-                // each extra split costs a partial plane, narrow tiles cost operand bandwidth
-                double t = (double)rounds * ((double)k_blocks / (double)s) * (double)bn * (1.0 + 0.01 * (double)(s - 1));
-                if (bn < 192) t *= 1.05;
-                if (t < best_t * (1.0 - 1e-9)) {
-                    best_t = t;
-                    best = GemmLayout{tr != 0, bn, (int)s};
+    for (int pair = 0; pair < 2; ++pair) {
+        if ((force_pair == 1 && !pair) || (force_pair == 2 && pair)) continue;   // 1: always, 2: never
+        if (pair && ctas < 2) continue;
+        const int tile_m = pair ? 256 : 128;
+        const int slots = pair ? ctas / 2 : ctas;   // the two-SM form's units run on clusters of two CTAs
+        for (int tr = 0; tr < 2; ++tr) {
+            if (force_trans == 1 && tr) continue;    // 1: never transposed
+            if (force_trans == 2 && !tr) continue;   // 2: always transposed
+            const int64_t a_rows = tr ? width : height, b_rows = tr ? height : width;
+            const int64_t tiles_m = (a_rows + tile_m - 1) / tile_m;
+            for (const KbCost &kc : kKbCost) {
+                const int bn = kc.bn;
+                if (force_bn > 0 && bn != force_bn) continue;
+                const double c = split_form ? kc.split[pair] : kc.f16[pair];
+                if (c <= 0.0) continue;   // no two-SM form of this width (halves of whole 32-row groups)
+                const int64_t tiles = tiles_m * ((b_rows + bn - 1) / bn);
+                for (int64_t s = 1; s <= 16; ++s) {
+                    if (force_splits > 0 && s != force_splits) continue;
+                    if (force_splits <= 0 && s > 1 && s * 4 > k_blocks) break;
+                    const int64_t rounds = (tiles * s + slots - 1) / slots;
+                    // critical path: rounds of units of ceil(k_blocks / s) k-blocks (each split a little
+                    // slower: the units in flight spread over more K ranges), then the split reduction
+                    double t = (double)rounds * (double)((k_blocks + s - 1) / s) * c * (1.0 + 0.01 * (double)(s - 1));
+                    if (s > 1) t += (double)(s + 1) * (double)width * (double)height * 4.0 / kReduceBytesPerUs;
+                    // the transposed write-out (32 lanes, 32 consecutive columns) breaks ties
+                    if (tr) t *= 0.995;
+                    if (t < best_t * (1.0 - 1e-9)) {
+                        best_t = t;
+                        best = GemmLayout{tr != 0, bn, (int)s, pair != 0};
+                    }
                 }
             }
         }
     }
+    if (best_t == 1e300 && force_pair == 1)   // no two-SM form of the forced width
+        return choose_gemm_layout(width, height, k_blocks, ctas, split_form, force_bn, force_splits, force_trans, 2);
     return best;
 }
 

@@ -25,17 +25,19 @@ DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t poin
 DirectLayout choose_layout(const DirectShape *shapes, int n_shapes, int width, int height, int64_t point_tiles,
                            int num_sms, int force_split);
 
-// GEMM orientation, tile width and K splits with the shortest critical path
-// (rounds of units over ctas CTAs, times the work of one unit); force_* > 0
-// pin a choice (force_trans: 1 = never transposed, 2 = always).
+// GEMM orientation, tile width, K splits and form (one CTA per 128-row tile, or the two-SM form: clusters of two
+// CTAs on 256-row tiles) with the shortest predicted time: rounds of units over the ctas CTAs (ctas / 2 clusters)
+// times a unit's k-blocks times the measured time of one k-block at that width and form, plus the split
+// reduction.  force_* > 0 pin a choice (force_trans: 1 = never transposed, 2 = always; force_pair: 1 = always
+// the two-SM form, 2 = never).
 struct GemmLayout {
     bool trans;
     int bn;
     int splits;
+    bool pair;
 };
-// tile_m: rows of an A tile (128; 256 for the two-SM form, whose ctas are clusters of two).
-GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, int force_bn, int force_splits,
-                              int force_trans, int tile_m = 128);
+GemmLayout choose_gemm_layout(int width, int height, int64_t k_blocks, int ctas, bool split_form, int force_bn,
+                              int force_splits, int force_trans, int force_pair);
 
 // GEMM tile width (columns of the hologram per tile) with the least padding.
 int choose_gemm_bn(int width);

@@ -35,9 +35,11 @@ def _dev(c):
     return torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda()
 
 
-def _run(c, form, bn=None, splitk=None, chunk=None, budget_mb=None, trans=None):
+def _run(c, form, bn=None, splitk=None, chunk=None, budget_mb=None, trans=None, pair=None):
     xyz, amp = _dev(c)
     with Hologram(c.width, c.height, c.pitch_m, c.lambda_m, form=form, timeout_ms=3000) as h:
+        if pair:
+            h.set_option(_lib.CGH_OPT_GEMM_PAIR, pair)
         if trans:
             h.set_option(_lib.CGH_OPT_GEMM_TRANSPOSE, trans)
         if budget_mb:
@@ -122,12 +124,15 @@ def test_gemm_form_vs_oracle(form, w, h, n):
     assert oracle.nrms(got, ref) <= NRMS[form]
 
 
-@pytest.mark.parametrize("bn", [128, 192, 240, 256])
+@pytest.mark.parametrize("pair", [2, 1])
+@pytest.mark.parametrize("bn", [128, 192, 224, 240, 256])
 @pytest.mark.parametrize("splitk", [1, 2, 3, 5])
-def test_tiles_and_splits(bn, splitk):
+def test_tiles_and_splits(bn, splitk, pair):
+    """Every tile width and a few K splits, in the one-CTA form (CGH_OPT_GEMM_PAIR 2) and the two-SM form (1; it
+    has no 240-wide tile, where the one-CTA form runs)."""
     c = workloads.random_cloud(55, 500, 270, 1500)
     ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, 500, 270)
-    got = _run(c, "gemm_split16", bn=bn, splitk=splitk)
+    got = _run(c, "gemm_split16", bn=bn, splitk=splitk, pair=pair)
     assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]
 
 
@@ -285,7 +290,7 @@ def test_pair_gemm(form, w, h, n, trans):
         a = hg.point_cloud(xyz, amp)
         hg.sync()
         a = a.cpu().numpy()
-    plain = _run(c, form, trans=trans or None)
+    plain = _run(c, form, trans=trans or None, pair=2)
     assert oracle.nrms(a, plain) < (3e-6 if form == "gemm_split16" else NRMS[form] / 4)
     if w * h * n <= 2e8:
         ref = oracle.field(c.pitch_m, c.lambda_m, c.xyz, c.amp, w, h)
