@@ -143,11 +143,15 @@ enum {
                                    buffers stay the same), when all its factors fit CGH_OPT_FACTOR_BUDGET_MB, it is
                                    not grouped, has no piston or reference and the stream is not being captured;
                                    0 = the separate factor and GEMM launches */
-    CGH_OPT_GEMM_PAIR = 20      /* GEMM forms, cgh_point_cloud: the two-SM tcgen05 form (clusters of two CTAs,
+    CGH_OPT_GEMM_PAIR = 20,     /* GEMM forms, cgh_point_cloud: the two-SM tcgen05 form (clusters of two CTAs,
                                    256-row tiles, each CTA holding half of the B tile, so more operand stages fit)
                                    or one CTA per 128-row tile.  0 = chosen with the tile width and K splits by the
                                    measured time model (default), 1 = always the two-SM form (not at width 240),
                                    2 = never */
+    CGH_OPT_BATCH_CHUNK_MB = 21 /* cgh_batch persistent launch (and CGH_OPT_GEMM_PERSISTENT): a GEMM unit covers
+                                   one K chunk of its tile whose operands (both factors, all planes) take about
+                                   this many MiB, the chunks of a tile added to the output in K order; 0 = the
+                                   whole K where the batch has tiles enough for the CTAs (default) */
 };
 
 typedef struct cgh_ctx cgh_ctx;

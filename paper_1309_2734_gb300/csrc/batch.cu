@@ -58,7 +58,8 @@ std::vector<uint64_t> plan_key(const cgh_ctx *ctx, const cgh_instance *inst, int
     k.push_back((uint64_t)ctx->form);
     k.push_back((uint64_t)ctx->tol_e9);
     k.push_back(((uint64_t)ctx->gemm_bn << 32) | (uint64_t)(uint32_t)ctx->gemm_chunk);
-    k.push_back((uint64_t)ctx->batch_mode | ((uint64_t)ctx->batch_overlap << 8));
+    k.push_back((uint64_t)ctx->batch_mode | ((uint64_t)ctx->batch_overlap << 8) |
+                ((uint64_t)ctx->batch_chunk_mb << 16));
     k.push_back((uint64_t)(uint32_t)ctx->drop_tile);
     for (int i = 0; i < n; ++i) {
         const cgh_instance &b = inst[i];
@@ -211,12 +212,31 @@ void choose_persist_tile(const cgh_ctx *ctx, int width, int height, int &bn, boo
     }
 }
 
-// K chunks of the persistent batch's GEMM units: each unit covers kchunk_kb k-blocks of its tile, and the units
-// of a job are queued chunk by chunk (all tiles of chunk 0, then of chunk 1, ...), so the CTAs in flight stream
-// the same K range of the factors and L2 serves each factor tile to every unit that needs it: a chunk's slice of
-// the job's operands (planes x (A rows + B rows) x 128 bytes per k-block) is kept near kGemmChunkBytes.
-constexpr double kGemmChunkBytes = 64.0 * (1 << 20);
-constexpr int kGemmChunkMinKb = 32;
+// K chunks of the persistent batch's GEMM units.  A unit is one tile over one K chunk, and its producer streams
+// the k-blocks behind the factor generation (it waits for the factors of each chain), so the chunk is the whole K
+// wherever the batch has tiles enough for the CTAs: one epilogue per tile, nothing added to the output in K order,
+// and the CTAs on one hologram sweep its K range together, so L2 serves each factor tile to every unit that needs
+// it.  Otherwise K is cut into chunks by the rounds model of the one-hologram GEMM (rounds of units over this
+// job's share of the CTAs, times k-blocks per unit, each extra chunk 1 % slower); the chunks of a tile then add
+// to the output in K order.
+static int persist_kchunks(int64_t tiles, int64_t total_tiles, int64_t nkb, int step, int ctas)
+{
+    if (total_tiles >= 2 * (int64_t)ctas) return 1;
+    const double share = (double)ctas * (double)tiles / (double)total_tiles;   // this job's CTAs
+    int best = 1;
+    double best_t = 1e300;
+    for (int s = 1; s <= 16 && (int64_t)s * step <= nkb; ++s) {
+        const int64_t kcs = ((nkb + s - 1) / s + step - 1) / step * step;
+        const int64_t chunks = (nkb + kcs - 1) / kcs;
+        const double rounds = std::ceil((double)(tiles * chunks) / std::max(1.0, share));
+        const double t = rounds * (double)kcs * (1.0 + 0.01 * (double)(chunks - 1));
+        if (t < best_t * (1.0 - 1e-9)) {
+            best_t = t;
+            best = s;
+        }
+    }
+    return best;
+}
 
 constexpr int kDirectChunkPoints = 2048;   // points per direct unit of the persistent batch (at most 64 chunks)
 constexpr int kDirectMaxChunks = 64;
@@ -239,13 +259,19 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     const int nj = (int)inst_of.size();
     std::vector<PersistJob> jobs(nj);
     std::vector<char> jtrans(nj, 0);
+    std::vector<int64_t> jtiles(nj, 0);
+    int64_t total_tiles = 0;
     for (int j = 0; j < nj; ++j) {
         const int i = inst_of[j];
         if (plan->forms[i] < CGH_GEMM_F16) continue;
         bool tr = false;
         choose_persist_tile(ctx, inst[i].width, inst[i].height, bn[i], tr);
         jtrans[j] = tr ? 1 : 0;
+        const int a_rows = tr ? inst[i].width : inst[i].height, b_rows = tr ? inst[i].height : inst[i].width;
+        jtiles[j] = (int64_t)((a_rows + 127) / 128) * ((b_rows + bn[i] - 1) / bn[i]);
+        total_tiles += jtiles[j];
     }
+    const int gctas_max = gemm_max_ctas(ctx->num_sms);
     // arena: the zeroed counters first (one memset), then per-job buffers, then the tables
     Layout L;
     const size_t z_heads = L.take(64 * sizeof(int));
@@ -267,23 +293,29 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         J.height = b.height;
         if (J.form >= CGH_GEMM_F16) {
             const int i = inst_of[j];
-            const int planes = J.form == CGH_GEMM_SPLIT16 ? 2 : 1;
             const int64_t nkb = (2 * b.n_points + 63) / 64;
-            const int a_rows = jtrans[j] ? b.width : b.height, b_rows = jtrans[j] ? b.height : b.width;
-            const int64_t a_pad = (a_rows + 127) / 128 * 128, b_pad = (int64_t)(b_rows + bn[i] - 1) / bn[i] * bn[i];
             const int kc = J.form == CGH_GEMM_SPLIT16 ? (ctx->gemm_chunk > 0 ? ctx->gemm_chunk : kSplit16ChunkKbBatch)
                                                       : 1;
-            // a multiple of the factor units' 32 k-blocks (so a unit's readiness is whole factor units) and of the
-            // TMEM chain kc
+            // a multiple of the factor units' 32 k-blocks (so a chunk's factors are whole factor groups) and of
+            // the TMEM chain kc
             const int gkb = 2 * persist_factor_points() / 64;
             const int step = kc % gkb == 0 ? kc : (gkb % kc == 0 ? gkb : gkb * kc);
-            int64_t kcs = (int64_t)(kGemmChunkBytes / ((double)planes * (double)(a_pad + b_pad) * 128.0));
-            kcs = std::max<int64_t>(kGemmChunkMinKb, kcs) / step * step;
-            if (kcs <= 0) kcs = step;
+            const int s = persist_kchunks(jtiles[j], total_tiles, nkb, step, gctas_max);
+            int64_t kcs = ((nkb + s - 1) / s + step - 1) / step * step;
+            if (ctx->batch_chunk_mb > 0) {   // chunks of a fixed operand size (no longer than the split)
+                const int planes = J.form == CGH_GEMM_SPLIT16 ? 2 : 1;
+                const int a_rows = jtrans[j] ? b.width : b.height, b_rows = jtrans[j] ? b.height : b.width;
+                const double row_bytes = (double)planes *
+                                         (double)((a_rows + 127) / 128 * 128 + (b_rows + bn[i] - 1) / bn[i] * bn[i]) *
+                                         128.0;
+                const int64_t by = (int64_t)((double)ctx->batch_chunk_mb * 1048576.0 / row_bytes) / step * step;
+                kcs = std::min(kcs, std::max<int64_t>(step, by));
+            }
             J.kchunks = (int)((nkb + kcs - 1) / kcs);
             J.kchunk_kb = (int)kcs;
-            if (J.kchunks > 1) z_count[j] = L.take((size_t)(a_pad / 128) * ((b_pad) / bn[i]) * 4 * sizeof(int));
-            z_chunk[j] = L.take((size_t)J.kchunks * sizeof(int));
+            if (J.kchunks > 1) z_count[j] = L.take((size_t)jtiles[j] * 4 * sizeof(int));
+            const int64_t slots = (2 * b.n_points + 63) / 64 * 32;   // point slots: ld / 2
+            z_chunk[j] = L.take((size_t)((slots + pts_f - 1) / pts_f) * sizeof(int));
         } else {
             J.tiles_x = (b.width + dtw - 1) / dtw;
             const int tiles = J.tiles_x * ((b.height + dth - 1) / dth);
@@ -335,6 +367,13 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     }
     for (int j : gemm_order) {
         const cgh_instance &b = inst[inst_of[j]];
+        const int a_rows = jtrans[j] ? b.width : b.height, b_rows = jtrans[j] ? b.height : b.width;
+        const int tiles = ((a_rows + 127) / 128) * ((b_rows + bn[inst_of[j]] - 1) / bn[inst_of[j]]);
+        for (int c = 0; c < jobs[j].kchunks; ++c)
+            for (int t = 0; t < tiles; ++t) gunits.push_back(make_int4(j, t, c, 0));
+    }
+    for (int j : gemm_order) {
+        const cgh_instance &b = inst[inst_of[j]];
         PersistJob &J = jobs[j];
         J.point_slots = (int)(J.ld / 2);
         const int bands = (b.height + b.width + rows_f - 1) / rows_f;
@@ -342,22 +381,21 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         J.fact_units = bands * groups;
         J.fact_bands = bands;
         J.fact_groups = groups;
-        // in K order, so the first K chunks' factors are complete first and their GEMM units can start
-        for (int g = 0; g < groups; ++g)
-            for (int band = 0; band < bands; ++band) simt.push_back(make_int4(kPersistFactor, j, band, g));
+        // in K order within every K chunk, the chunks side by side, so the GEMM units of all chunks find the
+        // factors of their first k-blocks first
+        const int per_chunk = J.kchunk_kb / (2 * pts_f / 64);   // factor groups of one K chunk
+        for (int pos = 0; pos < per_chunk; ++pos)
+            for (int c = 0; c < J.kchunks; ++c) {
+                const int g = c * per_chunk + pos;
+                if (g >= groups) continue;
+                for (int band = 0; band < bands; ++band) simt.push_back(make_int4(kPersistFactor, j, band, g));
+            }
     }
     for (int j : direct_order) {
         const cgh_instance &b = inst[inst_of[j]];
         const int tiles = jobs[j].tiles_x * ((b.height + dth - 1) / dth);
         for (int t = 0; t < tiles; ++t)
             for (int c = 0; c < jobs[j].chunks; ++c) simt.push_back(make_int4(kPersistDirect, j, t, c));
-    }
-    for (int j : gemm_order) {
-        const cgh_instance &b = inst[inst_of[j]];
-        const int a_rows = jtrans[j] ? b.width : b.height, b_rows = jtrans[j] ? b.height : b.width;
-        const int tiles = ((a_rows + 127) / 128) * ((b_rows + bn[inst_of[j]] - 1) / bn[inst_of[j]]);
-        for (int c = 0; c < jobs[j].kchunks; ++c)
-            for (int t = 0; t < tiles; ++t) gunits.push_back(make_int4(j, t, c, 0));
     }
     if (ctx->drop_tile >= 0 && nj > 0) {
         // test hook: job 0 waits for one unit more than exists, so a bounded wait runs out (kStatusTimeout)
@@ -396,7 +434,7 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
                                b.d_out, J.amax, jtrans[j] != 0))
                 return CGH_ECUDA;
             if (J.kchunks > 1) J.tile_seq = reinterpret_cast<int *>(A + z_count[j]);
-            J.chunk_done = reinterpret_cast<int *>(A + z_chunk[j]);
+            J.group_done = reinterpret_cast<int *>(A + z_chunk[j]);
         } else if (J.chunks > 1) {
             J.parts = reinterpret_cast<float4 *>(A + o_parts[j]);
             J.tile_count = reinterpret_cast<int *>(A + z_count[j]);

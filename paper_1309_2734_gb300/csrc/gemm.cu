@@ -78,7 +78,7 @@ struct alignas(64) SingleUnits {
         c.u += gridDim.x;
         return true;
     }
-    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
+    __device__ bool ready(const UnitInfo &, int, int &, unsigned long long) const { return true; }
     __device__ void abort(Cursor &, unsigned long long) const {}
     __device__ UnitInfo get(int u) const
     {
@@ -127,7 +127,7 @@ struct BatchUnits {
         ++c.i;
         return true;
     }
-    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
+    __device__ bool ready(const UnitInfo &, int, int &, unsigned long long) const { return true; }
     __device__ void abort(Cursor &, unsigned long long) const {}
     __device__ UnitInfo get(int i) const
     {
@@ -234,7 +234,7 @@ struct alignas(64) PairUnits {
         c.u += (int)(gridDim.x >> 1);
         return true;
     }
-    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
+    __device__ bool ready(const UnitInfo &, int, int &, unsigned long long) const { return true; }
     __device__ void abort(Cursor &, unsigned long long) const {}
     __device__ UnitInfo get(int u) const
     {

@@ -13,9 +13,10 @@
 // Units (a template parameter) hands every role the same sequence of units of
 // work: Cursor, start(), next(role, cursor, info) with role 0 = producer, 1 =
 // MMA issuer, 2 = epilogue (called by all 128 epilogue threads), ready(info,
-// timeout) -- the producer's bounded wait for the unit's operands -- and
-// abort(cursor, timeout), which the producer calls after a failure so that the
-// consumers stop.
+// kb_end, state, timeout) -- the producer's bounded wait, before it loads a
+// k-block, for the unit's operands of k-blocks below kb_end (state starts at
+// -1 for every unit) -- and abort(cursor, timeout), which the producer calls
+// after a failure so that the consumers stop.
 #pragma once
 
 #include <cuda.h>
@@ -113,12 +114,8 @@ __device__ __forceinline__ void gemm_producer(const Units &src, uint8_t *smem, c
     typename Units::Cursor cur = src.start();
     UnitInfo x;
     while (ok && src.next(0, cur, x)) {
-        if (!src.ready(x, timeout_ns)) {   // the unit's operands (a batch: its factors) are not there
-            atomicOr(status, kStatusTimeout);
-            ok = false;
-            break;
-        }
         const uint32_t stage_bytes = (uint32_t)(C::kStageA + x.bn * kBK * 2);
+        int upto = -1;   // the unit source's record of the operands known to be there
         for (int c0 = x.kb0; c0 < x.kb1 && ok; c0 += x.kc) {
             const int c1 = min(x.kb1, c0 + x.kc);
             for (int pass = 0; pass < x.passes && ok; ++pass) {
@@ -127,6 +124,12 @@ __device__ __forceinline__ void gemm_producer(const Units &src, uint8_t *smem, c
                 for (int kb = c0; kb < c1; ++kb, ++it) {
                     const int s = (int)(it % C::kStages);
                     const uint32_t ph = (it / C::kStages) & 1u;
+                    // the operands of k-block kb (a batch: its factors) are there
+                    if (pass == 0 && !src.ready(x, kb + 1, upto, timeout_ns)) {
+                        atomicOr(status, kStatusTimeout);
+                        ok = false;
+                        break;
+                    }
                     if (!mbar_wait(&empty[s], ph ^ 1u, timeout_ns)) {
                         atomicOr(status, kStatusTimeout);
                         ok = false;
@@ -368,15 +371,27 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
             }
             ++uses[1 - tb];
             tc_fence_after();
+            // FOLD columns per tensor-memory round trip (32 where the registers allow; bn is a multiple of 16)
+            constexpr int FOLD = ROUND >= 64 ? 32 : 16;
 #pragma unroll 1
-            for (int cc = 0; cc < x.bn; cc += 16) {
-                uint32_t a[16], t[16];
-                tmem_ld16(xaddr + (uint32_t)cc, a);
-                tmem_ld16(taddr + (uint32_t)cc, t);
+            for (int cc = 0; cc < x.bn; cc += FOLD) {
+                const bool two = FOLD == 32 && cc + 16 < x.bn;
+                uint32_t a[2][16], t[2][16];
+                tmem_ld16(xaddr + (uint32_t)cc, a[0]);
+                tmem_ld16(taddr + (uint32_t)cc, t[0]);
+                if (two) {
+                    tmem_ld16(xaddr + (uint32_t)(cc + 16), a[1]);
+                    tmem_ld16(taddr + (uint32_t)(cc + 16), t[1]);
+                }
                 tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) t[i] = __float_as_uint(__uint_as_float(t[i]) + __uint_as_float(a[i]));
-                tmem_st16(taddr + (uint32_t)cc, t);
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !two) break;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        t[h][i] = __float_as_uint(__uint_as_float(t[h][i]) + __uint_as_float(a[h][i]));
+                    tmem_st16(taddr + (uint32_t)(cc + 16 * h), t[h]);
+                }
             }
             tmem_st_wait();
             tc_fence_before();

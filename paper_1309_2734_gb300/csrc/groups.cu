@@ -35,24 +35,56 @@ __device__ __forceinline__ unsigned long long c_of(const int4 g)
     return ((unsigned long long)(uint32_t)g.z << 32) | (uint32_t)g.w;
 }
 
+// Distinct C values: each block first collects its points' values in a shared-memory set of the same capacity
+// and inserts only those into the global set, so a layered cloud costs one global probe sequence per (block,
+// plane), and a cloud with more than kMaxPlanes depths stops at its first block (no block walks a full set).
 __global__ void planes_insert(const int4 *__restrict__ geo, int n, unsigned long long *slots, int *overflow)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    if (*(volatile int *)overflow) return;   // already more planes than the set holds
-    const unsigned long long c = c_of(geo[j]);
-    unsigned int h = (unsigned int)((c * 0x9e3779b97f4a7c15ull) >> 40) % kPlaneSlots;
-    for (int probe = 0; probe < kPlaneSlots; ++probe) {
-        // plain read first: a full set costs reads, not contended atomics
-        const unsigned long long seen = *(volatile unsigned long long *)&slots[h];
-        if (seen == c) return;
-        if (seen == kEmptySlot) {
-            const unsigned long long prev = atomicCAS(&slots[h], kEmptySlot, c);
-            if (prev == kEmptySlot || prev == c) return;
-        }
-        h = (h + 1) % kPlaneSlots;
+    __shared__ unsigned long long local[kPlaneSlots];
+    __shared__ int n_local, full;
+    if (threadIdx.x == 0) {
+        n_local = 0;
+        full = *(volatile int *)overflow;   // already more planes than the set holds
     }
-    atomicExch(overflow, 1);
+    for (int i = threadIdx.x; i < kPlaneSlots; i += blockDim.x) local[i] = kEmptySlot;
+    __syncthreads();
+    if (full) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        const unsigned long long c = c_of(geo[j]);
+        unsigned int h = (unsigned int)((c * 0x9e3779b97f4a7c15ull) >> 40) % kPlaneSlots;
+        for (int probe = 0; probe < kPlaneSlots && !*(volatile int *)&full; ++probe) {
+            const unsigned long long prev = atomicCAS(&local[h], kEmptySlot, c);
+            if (prev == c) break;
+            if (prev == kEmptySlot) {
+                if (atomicAdd(&n_local, 1) >= kMaxPlanes) atomicExch(&full, 1);
+                break;
+            }
+            h = (h + 1) % kPlaneSlots;
+        }
+    }
+    __syncthreads();
+    if (full || n_local > kMaxPlanes) {
+        if (threadIdx.x == 0) atomicExch(overflow, 1);
+        return;
+    }
+    for (int i = threadIdx.x; i < kPlaneSlots; i += blockDim.x) {
+        const unsigned long long c = local[i];
+        if (c == kEmptySlot) continue;
+        unsigned int h = (unsigned int)((c * 0x9e3779b97f4a7c15ull) >> 40) % kPlaneSlots;
+        int probe = 0;
+        for (; probe < kPlaneSlots; ++probe) {
+            // plain read first: a present value costs reads, not contended atomics
+            const unsigned long long seen = *(volatile unsigned long long *)&slots[h];
+            if (seen == c) break;
+            if (seen == kEmptySlot) {
+                const unsigned long long prev = atomicCAS(&slots[h], kEmptySlot, c);
+                if (prev == kEmptySlot || prev == c) break;
+            }
+            h = (h + 1) % kPlaneSlots;
+        }
+        if (probe == kPlaneSlots) atomicExch(overflow, 1);
+    }
 }
 
 // One block: the distinct values, sorted; meta[0] = count (or -1 beyond kMaxPlanes).

@@ -237,9 +237,9 @@ cudaError_t launch_gemm_batch(const GemmJob *d_jobs, const int *d_cta_off, const
 // {kind, job, a, b}: kPersistPrep (a = block of kPointTile points), kPersistFactor (a = band of
 // persist_factor_rows() stacked rows, b = group of persist_factor_points() point slots), kPersistDirect
 // (a = pixel tile of persist_direct_tile_w() x persist_direct_tile_h(), b = point chunk); the GEMM queue holds
-// {job, tile, K chunk} (the chunks of a tile add to the output in K order; a unit of chunk c waits only for the
-// factor units of chunk c).  heads[3], prep_done[jobs], fact_done[jobs], every job's amax, tile_count, tile_seq and
-// chunk_done are zero at launch.
+// {job, tile, K chunk} (the chunks of a tile add to the output in K order; before it loads a k-block the producer
+// waits for the factor units of that k-block).  heads[3], prep_done[jobs], fact_done[jobs], every job's
+// amax, tile_count, tile_seq and group_done are zero at launch.
 enum { kPersistPrep = 0, kPersistFactor = 1, kPersistDirect = 2 };
 struct alignas(64) PersistJob {
     GemmJob g;                  // GEMM forms: tensor maps, shape, output
@@ -259,9 +259,9 @@ struct alignas(64) PersistJob {
     int kchunk_kb, kchunks;     // GEMM: k-blocks of one K chunk of a unit (a multiple of the factor units'
                                 // 32), and chunks per tile
     int *tile_seq;              // GEMM with kchunks > 1: [tiles][4], the next K chunk each epilogue quarter takes
-    int *chunk_done;            // GEMM: [kchunks], factor units done whose points fall in the K chunk
+    int *group_done;            // GEMM: [fact_groups], factor units (bands) done of each group of point slots
     int fact_bands, fact_groups;// GEMM: factor units = bands (of stacked rows) x groups (of point slots)
-    int chunk_extra;            // test hook: every K chunk waits for this many factor units more than exist
+    int chunk_extra;            // test hook: every factor group waits for this many bands more than exist
 };
 struct PersistParams {
     const PersistJob *jobs;

@@ -68,9 +68,10 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// GEMM units {job, tile, K chunk} from the global queue.  The producer takes a unit, waits (bounded) until the
-// job's factors are all written, and only then hands it to the MMA issuer and the epilogue through the ring of
-// unit ids, so no role touches a unit whose inputs are not there.
+// GEMM units {job, tile, K chunk} from the global queue.  The producer hands a unit to the MMA issuer and the
+// epilogue through the ring of unit ids at once, and before it loads a k-block it waits (bounded) until the factor
+// units of that k-block are written, so the GEMM of a hologram streams behind its factor generation and no role
+// reads factors that are not there.
 struct QueueUnits {
     const PersistJob *jobs;
     const int4 *units;   // {job, tile, K chunk, 0}
@@ -147,15 +148,8 @@ struct QueueUnits {
                     u = -1;
                 }
             }
-            if (u >= 0) {
-                const int4 w = units[u];
-                const PersistJob &J = jobs[w.x];
-                // the factor units of this K chunk: every band, the point groups whose slots fall in the chunk
-                const int g0 = w.z * J.kchunk_kb / kGroupKb;
-                const int g1 = min(J.fact_groups, (w.z + 1) * J.kchunk_kb / kGroupKb);
-                const int need = J.fact_bands * (g1 - g0) + J.chunk_extra;
-                if (fact_all > 0 ? wait_count(fact_all_done, fact_all, timeout_ns)
-                                 : wait_count(&J.chunk_done[w.z], need, timeout_ns)) {
+            if (u >= 0 && fact_all > 0) {   // every job's factors before any GEMM unit
+                if (wait_count(fact_all_done, fact_all, timeout_ns)) {
                     fence_proxy_async_global();   // the factors' ordinary stores, for the TMA loads that follow
                 } else {
                     atomicOr(status, kStatusTimeout);
@@ -185,8 +179,20 @@ struct QueueUnits {
         return true;
     }
 
-    // next() has waited for the unit's factors before handing it out
-    __device__ bool ready(const UnitInfo &, unsigned long long) const { return true; }
+    // The factor units of k-blocks [x.kb0, kb_end): every band of each group of kGroupKb k-blocks; upto is the
+    // first group not yet seen complete (-1: none checked for this unit).
+    __device__ bool ready(const UnitInfo &x, int kb_end, int &upto, unsigned long long timeout_ns) const
+    {
+        if (fact_all > 0) return true;   // next() waited for all of them
+        const PersistJob &J = jobs[x.job];
+        if (upto < 0) upto = x.kb0 / kGroupKb;
+        const int g_end = min(J.fact_groups, (kb_end + kGroupKb - 1) / kGroupKb);
+        if (upto >= g_end) return true;
+        for (; upto < g_end; ++upto)
+            if (!wait_count(&J.group_done[upto], J.fact_bands + J.chunk_extra, timeout_ns)) return false;
+        fence_proxy_async_global();   // the factors' ordinary stores, for the TMA loads that follow
+        return true;
+    }
 
     // after a failure the producer ends the sequence for the other roles
     __device__ void abort(Cursor &c, unsigned long long timeout_ns) const
@@ -357,7 +363,7 @@ __device__ void simt_group(const PersistParams &p, int4 (*s_geo)[kSimtTile], uin
                 if (J.form == CGH_GEMM_F16) run_factor_unit<kFactorF16>(J, w.z, w.w);
                 else if (J.form == CGH_GEMM_BF16) run_factor_unit<kFactorBF16>(J, w.z, w.w);
                 else run_factor_unit<kFactorSplit16>(J, w.z, w.w);
-                publish(&J.chunk_done[w.w * kGroupKb / J.kchunk_kb]);
+                publish(&J.group_done[w.w]);
                 if (t == 0) {
                     atomicAdd(&p.fact_done[w.y], 1);
                     atomicAdd(&p.heads[2], 1);

@@ -91,6 +91,31 @@ def test_persistent_batch_is_deterministic_and_matches_kinds(form):
     _check_all(clouds, first, NRMS[form])
 
 
+@pytest.mark.parametrize("form", ["gemm_f16", "gemm_split16"])
+def test_persistent_batch_k_chunks(form):
+    """CGH_OPT_BATCH_CHUNK_MB: GEMM units of short K chunks whose results reach each tile in K order (sequence
+    flags), against the default units (here: the K splits of a batch with few tiles) -- other summation order,
+    equal within single-precision rounding -- and bit-equal on a replay."""
+    clouds = _mixed_clouds()
+    dev = _dev(clouds)
+    outs = [torch.full((c.height, c.width), 2.0, device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form=form) as h:
+        batch(h, dev, outs)
+        h.sync()
+        plain = [o.clone() for o in outs]
+        h.set_option(_lib.CGH_OPT_BATCH_CHUNK_MB, 1)
+        batch(h, dev, outs)
+        h.sync()
+        first = [o.clone() for o in outs]
+        batch(h, dev, outs)
+        h.sync()
+    for c, a, b, p in zip(clouds, first, outs, plain):
+        assert torch.equal(a, b)
+        if c.n_points:
+            assert oracle.nrms(a.cpu().numpy(), p.cpu().numpy()) < (3e-6 if form == "gemm_split16" else 2e-4)
+    _check_all(clouds, first, NRMS[form])
+
+
 @pytest.mark.parametrize("form", ["direct_sfu", "gemm_f16"])
 def test_persistent_batch_wait_times_out_and_context_recovers(form):
     """Test hook: the first job waits for one unit more than exists, so its bounded wait runs out; the launch

@@ -107,6 +107,19 @@ def test_too_many_planes_falls_back():
     assert oracle.nrms(got, ref) <= NRMS["gemm_split16"]
 
 
+@pytest.mark.parametrize("planes,grouped", [(64, True), (65, False)])
+def test_plane_count_limit_over_many_blocks(planes, grouped):
+    """The distinct depths are collected per thread block and then across blocks: 64 planes spread over every
+    block of 20,000 points are grouped, 65 fall back to the ungrouped form."""
+    c = workloads.layered_cloud(718 + planes, 180, 140, 20000, planes)
+    got, names = _run(c, "gemm_split16", 2)
+    assert ("group_factors" in names) == grouped
+    rng = np.random.default_rng(5)
+    cols, rows = rng.integers(0, 180, 300), rng.integers(0, 140, 300)
+    ref = oracle.field_at(c.pitch_m, c.lambda_m, c.xyz, c.amp, cols, rows)
+    assert oracle.nrms(got[rows, cols], ref) <= NRMS["gemm_split16"]
+
+
 def test_oversized_group_falls_back():
     """A group above 1024 points (all points in one column of one plane): the ungrouped form runs."""
     c = workloads.layered_cloud(716, 150, 150, 2000, 1)
