@@ -42,11 +42,13 @@ MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
 # taken on; a changed source reports null until it is profiled again.
 NCU_TRAFFIC = [
     # profiles/direct_sfu-1920x1080-n10000.md: 0.293 MB read + 1.543 MB written per launch
-    {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000", "src": "direct.cu",
-     "sha1": "ea2c334c22f1fbc542b0157a6c2437a8419a37d0", "bytes_per_launch": 1836288},
+    {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
+     "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh"],
+     "sha1": "", "bytes_per_launch": 1836288},
     # profiles/gemm_f16-1920x1080-n50000.md: 600.789 MB read + 3.344 MB written per launch
-    {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000", "src": "gemm.cu",
-     "sha1": "37e3978e5c43c21db1a0c42b02482e0ca1b91416", "bytes_per_launch": 604133376},
+    {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
+     "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
+     "sha1": "", "bytes_per_launch": 604133376},
 ]
 
 
@@ -54,14 +56,18 @@ def ncu_traffic(kernel, form, workload):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged since."""
     for t in NCU_TRAFFIC:
         if (t["kernel"], t["form"], t["workload"]) == (kernel, form, workload):
-            src = os.path.join(ROOT, "paper_1309_2734_gb300", "csrc", t["src"])
-            return t["bytes_per_launch"] if _sha1(src) == t["sha1"] else None
+            srcs = [os.path.join(ROOT, "paper_1309_2734_gb300", "csrc", f) for f in t["src"]]
+            return t["bytes_per_launch"] if _sha1(srcs) == t["sha1"] else None
     return None
 
 
-def _sha1(path):
-    with open(path, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+def _sha1(paths):
+    """SHA-1 of the kernel's source files, concatenated in the order given."""
+    h = hashlib.sha1()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -744,6 +750,68 @@ def run_ours(args):
     return 0
 
 
+def run_layout_sweep(args):
+    """Every GEMM launch shape (orientation, tile width, K splits, one-CTA or two-SM form) timed on a few hologram
+    shapes, against the one cgh_gemm_layout picks: the evidence behind the layout model.  Prints one JSON line."""
+    import torch
+    from paper_1309_2734_gb300 import Hologram, workloads, _lib
+    from paper_1309_2734_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    shapes = [tuple(int(v) for v in t.split("x")) for t in args.layout_sweep.split(",")]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    result = {"sweep": "gemm layouts", "form": args.form, "unit": "ms (GEMM kernel + split reduction, CUDA events)",
+              "shapes": {}}
+
+    def timed(hg, xyz, amp, out):
+        hg.point_cloud(xyz, amp, out)
+        hg.sync()
+        hg.profile(True)
+        hg.profile_read(reset=True)
+        for _ in range(3):
+            hg.point_cloud(xyz, amp, out)
+        hg.sync()
+        kp = hg.profile_read(reset=True)
+        hg.profile(False)
+        return (kp["gemm_tcgen05"][1] + kp.get("reduce_slices", (0, 0.0))[1]) / 3
+
+    for (w, h, n) in shapes:
+        c = workloads.random_cloud(777 + n, w, h, n)
+        xyz, amp = torch.from_numpy(c.xyz).cuda(), torch.from_numpy(c.amp).cuda()
+        out = torch.empty((h, w), device="cuda")
+        kb = (2 * n + 63) // 64
+        rows = []
+        with Hologram(w, h, c.pitch_m, c.lambda_m, form=args.form, stream=stream) as hg:
+            hg.set_option(_lib.CGH_OPT_GEMM_GROUP, 1)
+            for pair in (2, 1):
+                for tr in (1, 2):
+                    for bn in (128, 192, 224, 240, 256):
+                        for sp in range(1, 17):
+                            if sp * 4 > kb or (pair == 1 and bn == 240):
+                                continue
+                            for key, v in ((_lib.CGH_OPT_GEMM_PAIR, pair), (_lib.CGH_OPT_GEMM_TRANSPOSE, tr),
+                                           (_lib.CGH_OPT_GEMM_BN, bn), (_lib.CGH_OPT_GEMM_SPLITK, sp)):
+                                hg.set_option(key, v)
+                            rows.append(((pair == 1, tr == 2, bn, sp), timed(hg, xyz, amp, out)))
+            for key in (_lib.CGH_OPT_GEMM_PAIR, _lib.CGH_OPT_GEMM_TRANSPOSE, _lib.CGH_OPT_GEMM_BN,
+                        _lib.CGH_OPT_GEMM_SPLITK):
+                hg.set_option(key, 0)
+            auto_ms = timed(hg, xyz, amp, out)
+        lay = _lib.cgh_gemm_layout(w, h, n, _lib.FORMS[args.form], sms)
+        best = min(rows, key=lambda r: r[1])
+        same = [t for k, t in rows if k == (lay["pair"], lay["transposed"], lay["bn"], lay["splits"])]
+        result["shapes"][f"{w}x{h}-n{n}"] = {
+            "layouts_timed": len(rows),
+            "best": {"pair": best[0][0], "transposed": best[0][1], "bn": best[0][2], "splits": best[0][3],
+                     "ms": round(best[1], 4)},
+            "chosen": dict(lay, ms=round(auto_ms, 4), ms_in_sweep=round(same[0], 4) if same else None),
+            "chosen_over_best": round((same[0] if same else auto_ms) / best[1], 3)}
+        print(json.dumps({f"{w}x{h}-n{n}": result["shapes"][f"{w}x{h}-n{n}"]}), file=sys.stderr, flush=True)
+    print(json.dumps(result))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -766,9 +834,14 @@ def main():
     ap.add_argument("--no-small", action="store_true", help="skip the 256x256, 1,024-point cloud")
     ap.add_argument("--no-paper-workload", action="store_true",
                     help="skip the phase-only 1920x1080 workload of the paper's Tables 3-4")
+    ap.add_argument("--layout-sweep", default="",
+                    help="instead of the bench line: time every GEMM launch shape of --form on these hologram "
+                         "shapes (WxHxN,...) against the chosen one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.layout_sweep:
+        return run_layout_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -150,8 +150,9 @@ enum {
                                    2 = never */
     CGH_OPT_BATCH_CHUNK_MB = 21 /* cgh_batch persistent launch (and CGH_OPT_GEMM_PERSISTENT): a GEMM unit covers
                                    one K chunk of its tile whose operands (both factors, all planes) take about
-                                   this many MiB, the chunks of a tile added to the output in K order; 0 = the
-                                   whole K where the batch has tiles enough for the CTAs (default) */
+                                   this many MiB, the chunks of a tile added to the output in K order; 0 = 128 MiB
+                                   where the batch has two tiles or more per SM, else chunks that balance the
+                                   tiles over the SMs (default) */
 };
 
 typedef struct cgh_ctx cgh_ctx;

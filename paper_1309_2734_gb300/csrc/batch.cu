@@ -213,12 +213,15 @@ void choose_persist_tile(const cgh_ctx *ctx, int width, int height, int &bn, boo
 }
 
 // K chunks of the persistent batch's GEMM units.  A unit is one tile over one K chunk, and its producer streams
-// the k-blocks behind the factor generation (it waits for the factors of each chain), so the chunk is the whole K
-// wherever the batch has tiles enough for the CTAs: one epilogue per tile, nothing added to the output in K order,
-// and the CTAs on one hologram sweep its K range together, so L2 serves each factor tile to every unit that needs
-// it.  Otherwise K is cut into chunks by the rounds model of the one-hologram GEMM (rounds of units over this
-// job's share of the CTAs, times k-blocks per unit, each extra chunk 1 % slower); the chunks of a tile then add
-// to the output in K order.
+// the k-blocks behind the factor generation (it waits for the factors of each k-block).  Where the batch has tiles
+// enough for the CTAs, a chunk's operands (both factors, all planes) take about kBatchChunkMb: the CTAs on one
+// hologram then sweep a K range that L2 holds, and one hologram's chunks follow each other closely (measured on
+// the 64-frame video batch: 32 / 64 / 128 / 256 / 512 MB and the whole K gave 119 / 111 / 103 / 104 / 107 / 107 ms
+// at NRMS 1e-5 and 52 / 37.4 / 36.1 / 36.1 / 36.9 / 39.8 ms at 2e-3).  Otherwise K is cut into chunks by the
+// rounds model of the one-hologram GEMM (rounds of units over this job's share of the CTAs, times k-blocks per
+// unit, each extra chunk 1 % slower).  The chunks of a tile add to the output in K order.
+constexpr int kBatchChunkMb = 128;
+
 static int persist_kchunks(int64_t tiles, int64_t total_tiles, int64_t nkb, int step, int ctas)
 {
     if (total_tiles >= 2 * (int64_t)ctas) return 1;
@@ -302,13 +305,16 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
             const int step = kc % gkb == 0 ? kc : (gkb % kc == 0 ? gkb : gkb * kc);
             const int s = persist_kchunks(jtiles[j], total_tiles, nkb, step, gctas_max);
             int64_t kcs = ((nkb + s - 1) / s + step - 1) / step * step;
-            if (ctx->batch_chunk_mb > 0) {   // chunks of a fixed operand size (no longer than the split)
+            // chunks of an operand size: pinned, or by default where the batch has tiles enough for the CTAs
+            const int chunk_mb = ctx->batch_chunk_mb > 0 ? ctx->batch_chunk_mb
+                                                         : (total_tiles >= 2 * (int64_t)gctas_max ? kBatchChunkMb : 0);
+            if (chunk_mb > 0) {   // no longer than the split
                 const int planes = J.form == CGH_GEMM_SPLIT16 ? 2 : 1;
                 const int a_rows = jtrans[j] ? b.width : b.height, b_rows = jtrans[j] ? b.height : b.width;
                 const double row_bytes = (double)planes *
                                          (double)((a_rows + 127) / 128 * 128 + (b_rows + bn[i] - 1) / bn[i] * bn[i]) *
                                          128.0;
-                const int64_t by = (int64_t)((double)ctx->batch_chunk_mb * 1048576.0 / row_bytes) / step * step;
+                const int64_t by = (int64_t)((double)chunk_mb * 1048576.0 / row_bytes) / step * step;
                 kcs = std::min(kcs, std::max<int64_t>(step, by));
             }
             J.kchunks = (int)((nkb + kcs - 1) / kcs);
