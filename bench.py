@@ -44,11 +44,11 @@ NCU_TRAFFIC = [
     # profiles/direct_sfu-1920x1080-n10000.md: 0.293 MB read + 1.543 MB written per launch
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
      "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh"],
-     "sha1": "", "bytes_per_launch": 1836288},
-    # profiles/gemm_f16-1920x1080-n50000.md: 600.789 MB read + 3.344 MB written per launch
+     "sha1": "36fb7384f442babe84eccbbd5d663223087aec8b", "bytes_per_launch": 1836288},
+    # profiles/gemm_f16-1920x1080-n50000.md: 600.789 MB read + 3.401 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
      "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
-     "sha1": "", "bytes_per_launch": 604133376},
+     "sha1": "99556ba4bfeec90f2f93e6789f16ae25349492a4", "bytes_per_launch": 604190464},
 ]
 
 
