@@ -148,11 +148,15 @@ enum {
                                    or one CTA per 128-row tile.  0 = chosen with the tile width and K splits by the
                                    measured time model (default), 1 = always the two-SM form (not at width 240),
                                    2 = never */
-    CGH_OPT_BATCH_CHUNK_MB = 21 /* cgh_batch persistent launch (and CGH_OPT_GEMM_PERSISTENT): a GEMM unit covers
+    CGH_OPT_BATCH_CHUNK_MB = 21, /* cgh_batch persistent launch (and CGH_OPT_GEMM_PERSISTENT): a GEMM unit covers
                                    one K chunk of its tile whose operands (both factors, all planes) take about
                                    this many MiB, the chunks of a tile added to the output in K order; 0 = 128 MiB
                                    where the batch has two tiles or more per SM, else chunks that balance the
                                    tiles over the SMs (default) */
+    CGH_OPT_BATCH_PREMADE_PCT = 22 /* cgh_batch persistent launch: the first GEMM holograms in queue order, up to
+                                   this percentage of the batch's factor bytes, get their points and factors
+                                   from the plain kernels launched before the persistent one (in the same
+                                   graph); the SIMT groups make the rest */
 };
 
 typedef struct cgh_ctx cgh_ctx;

@@ -42,6 +42,7 @@ CGH_OPT_DIRECT_SHAPE = 18
 CGH_OPT_GEMM_PERSISTENT = 19
 CGH_OPT_GEMM_PAIR = 20
 CGH_OPT_BATCH_CHUNK_MB = 21
+CGH_OPT_BATCH_PREMADE_PCT = 22
 CGH_PHASE_FRESNEL, CGH_PHASE_FRESNEL_PISTON, CGH_PHASE_SPHERICAL = 0, 1, 2
 
 EXPORTS = ("cgh_abi_version", "cgh_status_string", "cgh_create", "cgh_destroy", "cgh_set_stream",

@@ -931,6 +931,10 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         if (value < 0 || value > (1 << 20)) return CGH_EINVAL;
         ctx->batch_chunk_mb = (int)value;
         return CGH_OK;
+    case CGH_OPT_BATCH_PREMADE_PCT:
+        if (value < 0 || value > 100) return CGH_EINVAL;
+        ctx->batch_premade_pct = (int)value;
+        return CGH_OK;
     case CGH_OPT_PROFILE:
         if (value != 0 && value != 1) return CGH_EINVAL;
         ctx->profile = value == 1;

@@ -59,7 +59,7 @@ std::vector<uint64_t> plan_key(const cgh_ctx *ctx, const cgh_instance *inst, int
     k.push_back((uint64_t)ctx->tol_e9);
     k.push_back(((uint64_t)ctx->gemm_bn << 32) | (uint64_t)(uint32_t)ctx->gemm_chunk);
     k.push_back((uint64_t)ctx->batch_mode | ((uint64_t)ctx->batch_overlap << 8) |
-                ((uint64_t)ctx->batch_chunk_mb << 16));
+                ((uint64_t)ctx->batch_chunk_mb << 16) | ((uint64_t)(ctx->batch_premade_pct + 1) << 40));
     k.push_back((uint64_t)(uint32_t)ctx->drop_tile);
     for (int i = 0; i < n; ++i) {
         const cgh_instance &b = inst[i];
@@ -221,6 +221,7 @@ void choose_persist_tile(const cgh_ctx *ctx, int width, int height, int &bn, boo
 // rounds model of the one-hologram GEMM (rounds of units over this job's share of the CTAs, times k-blocks per
 // unit, each extra chunk 1 % slower).  The chunks of a tile add to the output in K order.
 constexpr int kBatchChunkMb = 128;
+constexpr int kBatchPremadePct = 0;   // share of the batch's factor bytes made before the persistent launch
 
 static int persist_kchunks(int64_t tiles, int64_t total_tiles, int64_t nkb, int step, int ctas)
 {
@@ -367,8 +368,21 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     auto by_work = [&](int a, int c) { return work[a] > work[c] || (work[a] == work[c] && a < c); };
     std::sort(gemm_order.begin(), gemm_order.end(), by_work);
     std::sort(direct_order.begin(), direct_order.end(), by_work);
+    // The first GEMM jobs in queue order, up to a share of all factor bytes, get their points and factors from
+    // the plain kernels before the persistent launch (full occupancy, about three times the rate of the SIMT
+    // groups), so the tensor cores start at once and the SIMT groups begin ahead of them on the rest.
+    {
+        double total = 0.0, done = 0.0;
+        for (int j : gemm_order) total += (double)(inst[inst_of[j]].width + inst[inst_of[j]].height) * jobs[j].ld;
+        const double share = (ctx->batch_premade_pct >= 0 ? ctx->batch_premade_pct : kBatchPremadePct) / 100.0;
+        for (int j : gemm_order) {
+            if (done >= share * total) break;
+            jobs[j].premade = 1;
+            done += (double)(inst[inst_of[j]].width + inst[inst_of[j]].height) * jobs[j].ld;
+        }
+    }
     for (int j = 0; j < nj; ++j) {
-        jobs[j].prep_units = jobs[j].n_pad / kPointTile;
+        jobs[j].prep_units = jobs[j].premade ? 0 : jobs[j].n_pad / kPointTile;
         for (int blk = 0; blk < jobs[j].prep_units; ++blk) simt.push_back(make_int4(kPersistPrep, j, blk, 0));
     }
     for (int j : gemm_order) {
@@ -384,9 +398,10 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
         J.point_slots = (int)(J.ld / 2);
         const int bands = (b.height + b.width + rows_f - 1) / rows_f;
         const int groups = (J.point_slots + pts_f - 1) / pts_f;
-        J.fact_units = bands * groups;
+        J.fact_units = J.premade ? 0 : bands * groups;
         J.fact_bands = bands;
         J.fact_groups = groups;
+        if (J.premade) continue;
         // in K order within every K chunk, the chunks side by side, so the GEMM units of all chunks find the
         // factors of their first k-blocks first
         const int per_chunk = J.kchunk_kb / (2 * pts_f / 64);   // factor groups of one K chunk
@@ -472,6 +487,15 @@ int build_plan_persist(cgh_ctx *ctx, const cgh_instance *inst, int n, BatchPlan 
     cudaError_t e = cudaMemsetAsync(A, 0, z_end, s);
     for (int i = 0; i < n && e == cudaSuccess; ++i)
         if (inst[i].n_points == 0) e = cudaMemsetAsync(inst[i].d_out, 0, (size_t)inst[i].width * inst[i].height * sizeof(float), s);
+    for (int j : gemm_order) {
+        if (e != cudaSuccess || !jobs[j].premade) continue;
+        const cgh_instance &b = inst[inst_of[j]];
+        const PersistJob &J = jobs[j];
+        e = launch_prep_points(b.d_xyz, b.d_amp, J.n, J.n_pad, b.pitch_m, b.lambda_m, J.geo, J.aux, ctx->d_status,
+                               J.amax, s);
+        if (e == cudaSuccess)
+            e = launch_factors(factor_mode(J.form), J.geo, J.aux, J.n, b.height, b.width, J.P, J.Q, J.ld, J.amax, s);
+    }
     if (e == cudaSuccess && nj > 0)
         e = launch_persist(pp, ctx->num_sms, bn_max, ctx->d_status, (uint64_t)ctx->timeout_ms * 1000000ull, s);
     rc = finish_capture(plan, e);

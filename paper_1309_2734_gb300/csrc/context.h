@@ -58,6 +58,7 @@ struct cgh_ctx {
     int gemm_persistent = 0;  // CGH_OPT_GEMM_PERSISTENT
     int gemm_pair = 0;        // CGH_OPT_GEMM_PAIR
     int batch_chunk_mb = 0;   // CGH_OPT_BATCH_CHUNK_MB
+    int batch_premade_pct = -1;   // CGH_OPT_BATCH_PREMADE_PCT (-1: the default)
     int phase_model = CGH_PHASE_FRESNEL;                 // CGH_OPT_PHASE_MODEL
     // Fresnel diffraction: cuFFT plan for the 2H x 2W grid, padded work plane,
     // and the chirp's spectrum for the distance fft_spec_z (0: none yet)

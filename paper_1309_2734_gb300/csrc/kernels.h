@@ -262,6 +262,7 @@ struct alignas(64) PersistJob {
     int *group_done;            // GEMM: [fact_groups], factor units (bands) done of each group of point slots
     int fact_bands, fact_groups;// GEMM: factor units = bands (of stacked rows) x groups (of point slots)
     int chunk_extra;            // test hook: every factor group waits for this many bands more than exist
+    int premade;                // GEMM: points and factors written by launches before the persistent one
 };
 struct PersistParams {
     const PersistJob *jobs;

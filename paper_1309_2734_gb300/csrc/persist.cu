@@ -185,6 +185,7 @@ struct QueueUnits {
     {
         if (fact_all > 0) return true;   // next() waited for all of them
         const PersistJob &J = jobs[x.job];
+        if (J.premade) return true;      // written before this launch
         if (upto < 0) upto = x.kb0 / kGroupKb;
         const int g_end = min(J.fact_groups, (kb_end + kGroupKb - 1) / kGroupKb);
         if (upto >= g_end) return true;

@@ -116,6 +116,25 @@ def test_persistent_batch_k_chunks(form):
     _check_all(clouds, first, NRMS[form])
 
 
+@pytest.mark.parametrize("pct", [40, 100])
+def test_persistent_batch_premade_factors(pct):
+    """CGH_OPT_BATCH_PREMADE_PCT: the first GEMM jobs' points and factors come from the plain kernels before the
+    persistent launch (the same device functions as the SIMT units, so the same bits)."""
+    clouds = _mixed_clouds()
+    dev = _dev(clouds)
+    outs = [torch.full((c.height, c.width), 2.0, device="cuda") for c in clouds]
+    with Hologram(8, 8, 8e-6, 532e-9, form="gemm_split16") as h:
+        batch(h, dev, outs)
+        h.sync()
+        plain = [o.clone() for o in outs]
+        h.set_option(_lib.CGH_OPT_BATCH_PREMADE_PCT, pct)
+        batch(h, dev, outs)
+        h.sync()
+    for a, b in zip(plain, outs):
+        assert torch.equal(a, b)
+    _check_all(clouds, outs, NRMS["gemm_split16"])
+
+
 @pytest.mark.parametrize("form", ["direct_sfu", "gemm_f16"])
 def test_persistent_batch_wait_times_out_and_context_recovers(form):
     """Test hook: the first job waits for one unit more than exists, so its bounded wait runs out; the launch
