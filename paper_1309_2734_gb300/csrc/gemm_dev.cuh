@@ -412,6 +412,10 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
         // the tile to global memory: stored, or added to what earlier point chunks left there (read from L2:
         // in a batch another SM may have written it during this launch)
         const bool first = !x.accumulate;
+        // a later K chunk of an ordered tile: the earlier chunks' values are final and visible (sequence flag), so
+        // the additions go to L2 as reductions (the same FP32 sums in the same order, without reading the tile
+        // back into the SM first)
+        const bool reduce = !first && x.seq != nullptr;
         if (x.trans) {
             // accumulator row = hologram column m (the warp's 32 lanes hold 32
             // consecutive m), accumulator column = hologram row n: every store
@@ -425,7 +429,7 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
                 const int ncol = min(TR, x.bn - cc);   // a multiple of 16
                 const int n0 = x.tn * x.bn + cc;
                 float old[TR];
-                if (!first && in_m) {
+                if (!first && !reduce && in_m) {
 #pragma unroll
                     for (int i = 0; i < TR; ++i)
                         old[i] = (i < ncol && n0 + i < x.height) ? __ldcg(x.out + (long long)(n0 + i) * x.width + m)
@@ -441,6 +445,10 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
                 for (int i = 0; i < TR; ++i) {
                     if (i >= ncol || n0 + i >= x.height) continue;
                     float v = empty_range ? 0.0f : __uint_as_float(r[i >> 4][i & 15]) * unscale;
+                    if (reduce) {
+                        atomicAdd(x.out + (long long)(n0 + i) * x.width + m, v);
+                        continue;
+                    }
                     if (!first) v += old[i];
                     x.out[(long long)(n0 + i) * x.width + m] = v;
                 }
@@ -462,7 +470,7 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
                 float4 old[4 * G];
 #pragma unroll
                 for (int gq = 0; gq < G; ++gq)
-                    if (!first && gvec[gq]) {
+                    if (!first && !reduce && gvec[gq]) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
                             old[4 * gq + i] = __ldcg(reinterpret_cast<const float4 *>(dst + col0 + 16 * gq) + i);
@@ -480,6 +488,19 @@ __device__ __forceinline__ void gemm_epilogue(const Units &src, const GemmBars &
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = empty_range ? 0.0f : __uint_as_float(r[gq][i]) * unscale;
                     float *d16 = dst + col0 + 16 * gq;
+                    if (reduce) {
+                        if (gvec[gq]) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                atomicAdd(reinterpret_cast<float4 *>(d16) + i,
+                                          make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if (col0 + 16 * gq + i < x.width) atomicAdd(d16 + i, v[i]);
+                        }
+                        continue;
+                    }
                     if (gvec[gq]) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
