@@ -50,12 +50,13 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
             return (int64_t)((width + s.tile_w - 1) / s.tile_w) * s.tile_w *
                    (((int64_t)height + s.tile_h - 1) / s.tile_h) * s.tile_h;
         };
-        // the thread block with the fewer padded pixels (the tall one among equals); CGH_OPT_DIRECT_SHAPE pins one
+        // the 8 x 8-pixel thread block of the tile with the fewer padded pixels (the tall one among equals);
+        // CGH_OPT_DIRECT_SHAPE pins one
         if (ctx->direct_shape > 0) {
             sh = direct_stream_shape(ctx->direct_shape - 1);
         } else {
-            sh = direct_stream_shape(1);
-            if (padded(direct_stream_shape(0)) < padded(sh)) sh = direct_stream_shape(0);
+            sh = direct_stream_shape(2);
+            if (padded(direct_stream_shape(3)) < padded(sh)) sh = direct_stream_shape(3);
         }
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         const int64_t units = tiles * n;
@@ -916,7 +917,7 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         ctx->test_alloc_fail = (int)value;
         return CGH_OK;
     case CGH_OPT_DIRECT_SHAPE:
-        if (value < 0 || value > 2) return CGH_EINVAL;
+        if (value < 0 || value > 4) return CGH_EINVAL;
         ctx->direct_shape = (int)value;
         return CGH_OK;
     case CGH_OPT_GEMM_PERSISTENT:

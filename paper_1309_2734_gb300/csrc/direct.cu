@@ -147,7 +147,7 @@ struct StreamSink {
 // SMEM_TOT: the running totals in shared memory (TR TL floats per thread, dynamic), which leaves the registers to a
 // wider thread block's partial sums.
 template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
-__global__ void __launch_bounds__(BX *BY, 2)
+__global__ void __launch_bounds__(BX *BY, 512 / (BX * BY))
     direct_stream_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int width,
                          int height, int tiles_x, long long units, float *__restrict__ out,
                          float4 *__restrict__ slots, int *__restrict__ counters, bool vec, int *status,
@@ -368,16 +368,26 @@ struct StreamCfg {
 // per term -- was measured slower: 4.84 against 4.65 ms at 1920x1080, 10^4 points.)
 using StreamTall = StreamCfg<kTL, kTR, kTallBX, kTallBY, false>;
 using StreamWide = StreamCfg<kTL, kTR, kBX, kBY, false>;
+// Blocks of 8 x 8 pixels per thread, 128 threads, totals in shared memory: 16 x 8 threads (the tall shape's
+// 128 x 64 tile) or 32 x 4 (the wide shape's 256 x 32).  With the separable SFU evaluation a point costs a thread
+// 16 hardware sines and cosines for 64 terms.
+constexpr int kSqTL = 8, kSqTR = 8, kSqBX = 16, kSqBY = 8, kSqWideBX = 32, kSqWideBY = 4;
+using StreamSquare = StreamCfg<kSqTL, kSqTR, kSqBX, kSqBY, true>;
+using StreamSquareWide = StreamCfg<kSqTL, kSqTR, kSqWideBX, kSqWideBY, true>;
 
 }  // namespace
 
 DirectShape direct_stream_shape(int variant)
 {
+    if (variant == 2) return DirectShape{kSqBX * kSqTL, kSqBY * kSqTR, kSqBX * kSqBY, kSqBX};
+    if (variant == 3) return DirectShape{kSqWideBX * kSqTL, kSqWideBY * kSqTR, kSqWideBX * kSqWideBY, kSqWideBX};
     return direct_shape(variant == 1);
 }
 
 int direct_stream_per_sm(bool sfu, const DirectShape &sh)
 {
+    if (sh.threads == kSqBX * kSqBY)
+        return sh.bx == kSqBX ? StreamSquare::resident(sfu) : StreamSquareWide::resident(sfu);
     return sh.bx == kTallBX ? StreamTall::resident(sfu) : StreamWide::resident(sfu);
 }
 
@@ -397,6 +407,8 @@ cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, cons
     const bool extra = ref.any();
 #define CGH_STREAM_ARGS sfu, extra, ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, sl, counters, vec, \
                         status, timeout_ns, drop_tile, ref
+    if (sh.threads == kSqBX * kSqBY)
+        return sh.bx == kSqBX ? StreamSquare::dispatch(CGH_STREAM_ARGS) : StreamSquareWide::dispatch(CGH_STREAM_ARGS);
     if (sh.bx == kTallBX) return StreamTall::dispatch(CGH_STREAM_ARGS);
     return StreamWide::dispatch(CGH_STREAM_ARGS);
 #undef CGH_STREAM_ARGS

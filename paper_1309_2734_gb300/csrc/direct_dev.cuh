@@ -237,6 +237,62 @@ __device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0,
 // SMEM_TOT: the running totals live in shared memory (s_tot, index-major: entry (c, r, i) of thread tid at
 // ((c TR + r) TL + i) BX BY + tid, so a warp's accesses are consecutive words) instead of registers, which leaves
 // the registers to the point tile's partial sums of a taller thread block.
+// Adds one point's terms to a thread's TL x TR block by the separability of the squared distance inside the block:
+// with a_i the turn of column m0 + i and b_r that of row n0 + r (each walked by Eqs. 6-8 in exact fixed point, the
+// piston and the reference phase's corner and column steps in a_i, its row step in b_r),
+//     A cos 2 pi (a_i + b_r) = cos 2 pi a_i (A cos 2 pi b_r) - sin 2 pi a_i (A sin 2 pi b_r),
+// so the hardware sine and cosine (one __sincosf, two MUFU operations) of TL + TR turns serve TL x TR terms at two
+// FFMAs each: TL TR / (2 (TL + TR)) times fewer MUFU operations than one cosine per term (2x at 8 x 8).  Each turn
+// is rounded to 2^-23 and taken on the symmetric argument grid of cos_term.  The hardware cosine's error is even in
+// its argument and does not average to zero over the grid, which made the field's error grow with the number of
+// points (NRMS 9.0e-7 at 10^4 points, 3.1e-6 at 2 10^5, 1920x1080); flip = a half turn on every other point
+// shifts both of its turns by pi, which leaves the term as it is (cos((a + pi) + (b + pi)) = cos(a + b)) and
+// turns the sign of that mean, so it cancels over pairs of points (5.8e-7 and 6.9e-7).
+template <int TL, int TR, bool EXTRA>
+__device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
+                                                uint32_t flip, float (&part)[TR][TL])
+{
+    const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
+    const uint32_t dx = (uint32_t)(m0 - q.x);
+    const uint32_t dy = (uint32_t)(n0 - q.y);
+    const uint32_t x2 = dx * dx, x2n = x2 + 2u * dx + 1u;   // dx^2, (dx + 1)^2: below 2^32, exact
+    const uint32_t y2 = dy * dy, y2n = y2 + 2u * dy + 1u;
+    // a half turn (so (f - 1.5) K1 is the angle itself in [-pi, pi)), rounding of the 23-bit truncation, the flip
+    constexpr uint32_t kHalfBias = (1u << 31) + 256u;
+    uint32_t a = chi * x2 + __umulhi(clo, x2) + kHalfBias + flip;
+    uint32_t da = chi * x2n + __umulhi(clo, x2n) - (a - kHalfBias - flip);
+    uint32_t b = chi * y2 + __umulhi(clo, y2) + kHalfBias + flip;
+    uint32_t db = chi * y2n + __umulhi(clo, y2n) - (b - kHalfBias - flip);
+    uint32_t D = w.x;
+    if constexpr (EXTRA) {   // piston (aux.x) and reference; 2 C formed from C
+        da += pr.dx;
+        db += pr.dy;
+        a += w.x + pr.g;
+        D = __funnelshift_l(clo, chi, 1);
+    }
+    const float amp = __uint_as_float(w.y);
+    float ca[TL], sa[TL];
+#pragma unroll
+    for (int i = 0; i < TL; ++i) {
+        const float f = __uint_as_float(__funnelshift_r(a, 0x7fu, 9));
+        __sincosf(fmaf(f, kK1, -kK0), &sa[i], &ca[i]);
+        a += da;
+        da += D;
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const float f = __uint_as_float(__funnelshift_r(b, 0x7fu, 9));
+        float sb, cb;
+        __sincosf(fmaf(f, kK1, -kK0), &sb, &cb);
+        cb *= amp;
+        sb *= amp;
+#pragma unroll
+        for (int i = 0; i < TL; ++i) part[r][i] = fmaf(-sa[i], sb, fmaf(ca[i], cb, part[r][i]));
+        b += db;
+        db += D;
+    }
+}
+
 // The points of the unit are those of tiles [t_begin, t_end), less the first p_first points of the first tile
 // and the points from p_last_end on of the last one.  Sink: PlainStore writes the totals to dst; any other sink
 // is called as sink(tot) with the thread's TR x TL totals of plane 0 (the amplitude hologram only).
@@ -352,14 +408,17 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
 #pragma unroll 1
             for (int p = p_lo; p < p_hi; ++p)
                 point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], s_rot[p], m0, n0, pr, part[0], part[PLANES - 1]);
+        } else if constexpr (SFU) {
+#pragma unroll 1
+            for (int p = p_lo; p < p_hi; ++p)   // p has the parity of the point's index (tiles start even)
+                point_terms_sep<TL, TR, EXTRA>(sg[p], sa[p], m0, n0, pr, (uint32_t)(p & 1) << 31, part[0]);
         } else if (p_lo == 0 && p_hi == T) {   // a whole tile: the loop with a fixed trip count
-            constexpr int M = SFU ? kEvalSfu : kEvalAccurate;
 #pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, M, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
+            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         } else {
-            constexpr int M = SFU ? kEvalSfu : kEvalAccurate;
 #pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p) point_terms<TL, TR, M, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
+            for (int p = p_lo; p < p_hi; ++p)
+                point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
