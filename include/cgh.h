@@ -92,10 +92,11 @@ enum {
 /* Options (cgh_set_option). */
 enum {
     CGH_OPT_TIMEOUT_MS = 1,     /* bound on every device-side wait; host-side waits allow 2x + 1 s; default 5000 */
-    CGH_OPT_POINT_SPLIT = 2,    /* direct forms: 0 = automatic (the SFU amplitude hologram: every CTA takes an
+    CGH_OPT_POINT_SPLIT = 2,    /* direct forms: 0 = automatic (the amplitude hologram: every CTA takes an
                                    equal share of the (pixel tile, point) pairs and the last CTA to finish a tile
-                                   sums its parts; otherwise point chunks as the critical-path model picks them);
-                                   s > 0: s point chunks, each a plane of partial sums, reduced after */
+                                   sums its parts; the complex wave: point chunks as the critical-path model
+                                   picks them); s > 0: s point chunks, each a plane of partial sums, reduced
+                                   after */
     CGH_OPT_GEMM_SPLITK = 3,    /* GEMM forms: K splits reduced afterwards; 0 = automatic */
     CGH_OPT_GEMM_BN = 4,        /* GEMM forms: tile width, one of 128, 192, 224, 240, 256; 0 = automatic */
     CGH_OPT_TOLERANCE_E9 = 5,   /* CGH_FORM_AUTO: largest admissible NRMS, in units of 1e-9 */

@@ -20,11 +20,9 @@ using namespace cgh;
 
 namespace cgh {
 
-// Direct form: prep, then the direct kernel.  The SFU form by default: one launch in which the CTAs take equal
-// shares of the (pixel tile, point) pairs and the last CTA to finish a tile sums its parts (no partial planes).
-// The accurate form, or CGH_OPT_POINT_SPLIT > 0: point chunks into partial planes and the fixed-order chunk
-// reduction after (on GB300 the accurate form measured 2 % faster chunked: 6.99 against 7.13 ms at 1920x1080,
-// 10^4 points).
+// Direct form: prep, then the direct kernel.  By default one launch in which the CTAs take equal shares of the
+// (pixel tile, point) pairs and the last CTA to finish a tile sums its parts (no partial planes).  With
+// CGH_OPT_POINT_SPLIT > 0: point chunks into partial planes and the fixed-order chunk reduction after.
 constexpr int kStreamMinPoints = 64;      // fewest points of one CTA's share in the balanced layout
 constexpr int kStreamSharePoints = 1024;  // points per share from which CTAs beyond the resident ones are added
 constexpr int kStreamWaves = 3;           // at most this many CTAs per resident slot
@@ -38,7 +36,7 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     const size_t aux_bytes = align_up((size_t)n_pad * sizeof(uint2), 256);
     const int64_t plane = (int64_t)width * height;
     const uint64_t tmo = (uint64_t)ctx->timeout_ms * 1000000ull;
-    const bool stream_k = sfu && ctx->point_split == 0;
+    const bool stream_k = ctx->point_split == 0;
     DirectShape sh;
     int split = 1, ctas = 0;
     size_t ws_rest = 0;
@@ -60,7 +58,7 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
         }
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         const int64_t units = tiles * n;
-        const int64_t slots = (int64_t)ctx->num_sms * direct_stream_per_sm(true, sh);
+        const int64_t slots = (int64_t)ctx->num_sms * direct_stream_per_sm(sfu, sh);
         int64_t want = units >= slots * kStreamSharePoints
                            ? std::min<int64_t>(kStreamWaves * slots, units / kStreamSharePoints)
                            : std::min<int64_t>(slots, units / kStreamMinPoints);
@@ -90,7 +88,7 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     if (stream_k) {
         int *counters = reinterpret_cast<int *>(
             reinterpret_cast<char *>(rest) + align_up((size_t)2 * ctas * sh.tile_w * sh.tile_h * sizeof(float), 256));
-        ProfileScope ps(ctx, "direct_sfu", 1);   // and the counters' memset
+        ProfileScope ps(ctx, sfu ? "direct_sfu" : "direct_accurate", 1);   // and the counters' memset
         return cuda_status(launch_direct_stream(sfu, sh, ctas, geo, aux, (int)n, width, height, d_out, rest,
                                                 counters, ctx->d_status, tmo, ctx->stream, ctx->drop_tile,
                                                 phase_ref(ctx)));

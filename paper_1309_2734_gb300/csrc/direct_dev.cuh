@@ -248,7 +248,9 @@ __device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0,
 // points (NRMS 9.0e-7 at 10^4 points, 3.1e-6 at 2 10^5, 1920x1080); flip = a half turn on every other point
 // shifts both of its turns by pi, which leaves the term as it is (cos((a + pi) + (b + pi)) = cos(a + b)) and
 // turns the sign of that mean, so it cancels over pairs of points (5.8e-7 and 6.9e-7).
-template <int TL, int TR, bool EXTRA>
+// ACC: the accurate form -- cos 2 pi t from the polynomial of cos_term and sin 2 pi t = cos 2 pi (t - 1/4) from the
+// same polynomial, on the FMA pipe (no flip needed: the polynomial's mean error over the turns is about zero).
+template <int TL, int TR, bool EXTRA, bool ACC = false>
 __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
                                                 uint32_t flip, float (&part)[TR][TL])
 {
@@ -271,19 +273,28 @@ __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int
         D = __funnelshift_l(clo, chi, 1);
     }
     const float amp = __uint_as_float(w.y);
+    // (cos, sin) of 2 pi times a turn held with the bias above
+    auto cis = [](uint32_t t, float &s, float &c) {
+        if constexpr (ACC) {
+            const uint32_t u = t - kHalfBias;            // the turn itself (the flip is a whole half turn)
+            c = cos_term<kEvalAccurate>(u);
+            s = cos_term<kEvalAccurate>(u - (1u << 30));   // cos 2 pi (t - 1/4)
+        } else {
+            const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));
+            __sincosf(fmaf(f, kK1, -kK0), &s, &c);
+        }
+    };
     float ca[TL], sa[TL];
 #pragma unroll
     for (int i = 0; i < TL; ++i) {
-        const float f = __uint_as_float(__funnelshift_r(a, 0x7fu, 9));
-        __sincosf(fmaf(f, kK1, -kK0), &sa[i], &ca[i]);
+        cis(a, sa[i], ca[i]);
         a += da;
         da += D;
     }
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
-        const float f = __uint_as_float(__funnelshift_r(b, 0x7fu, 9));
         float sb, cb;
-        __sincosf(fmaf(f, kK1, -kK0), &sb, &cb);
+        cis(b, sb, cb);
         cb *= amp;
         sb *= amp;
 #pragma unroll
@@ -408,17 +419,11 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
 #pragma unroll 1
             for (int p = p_lo; p < p_hi; ++p)
                 point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], s_rot[p], m0, n0, pr, part[0], part[PLANES - 1]);
-        } else if constexpr (SFU) {
-#pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p)   // p has the parity of the point's index (tiles start even)
-                point_terms_sep<TL, TR, EXTRA>(sg[p], sa[p], m0, n0, pr, (uint32_t)(p & 1) << 31, part[0]);
-        } else if (p_lo == 0 && p_hi == T) {   // a whole tile: the loop with a fixed trip count
-#pragma unroll 1
-            for (int p = 0; p < T; ++p) point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
         } else {
 #pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p)
-                point_terms<TL, TR, kEvalAccurate, EXTRA>(sg[p], sa[p], m0, n0, pr, part[0]);
+            for (int p = p_lo; p < p_hi; ++p)   // p has the parity of the point's index (tiles start even)
+                point_terms_sep<TL, TR, EXTRA, !SFU>(sg[p], sa[p], m0, n0, pr, SFU ? (uint32_t)(p & 1) << 31 : 0u,
+                                                     part[0]);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
