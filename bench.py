@@ -35,16 +35,35 @@ if ROOT not in sys.path:
 
 METRIC = "G point-pixel evals/s and holograms/s, direct FP32 vs tensor GEMM, at stated NRMS error"
 UNIT = "Gevals/s"
-MUFU_PER_SM_PER_CLK = 16        # __cosf throughput per SM per clock (MUFU pipe)
+MUFU_PER_SM_PER_CLK = 16        # MUFU (hardware sine / cosine) operations per SM per clock
+FMA_PER_SM_PER_CLK = 128        # FP32 FMA-pipe operations per SM per clock
+
+
+def direct_ops(form, width, height, n_points):
+    """The direct kernel's work per launch in the operations of the pipe that bounds it, as the kernel does it:
+    8 x 8 pixels a thread on the 128 x 64 tile (256 x 32 where that pads less), and per point and 8 x 8 block the
+    sine and cosine of 8 column and 8 row turns, then two FFMAs a term.  SFU form: 16 x 2 MUFU operations per
+    point and block (0.5 per evaluation).  Accurate form: FMA-pipe operations -- 16 x 2 polynomials of 8
+    (a multiply by 2^-32, the square, six FFMAs), 16 amplitude products, 128 FFMAs: 400 per point and block.
+    Returns (operations, pipe, peak operations per SM per clock, operations per evaluation)."""
+    def padded(tw, th):
+        return -(-width // tw) * tw * (-(-height // th) * th)
+    px = padded(256, 32) if padded(256, 32) < padded(128, 64) else padded(128, 64)
+    blocks = px // 64
+    if form == "direct_sfu":
+        per = 32
+        return n_points * blocks * per, "MUFU", MUFU_PER_SM_PER_CLK, per * blocks / (width * height)
+    per = 400
+    return n_points * blocks * per, "FMA", FMA_PER_SM_PER_CLK, per * blocks / (width * height)
 
 # DRAM bytes per launch of the dominant kernel from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # taken on; a changed source reports null until it is profiled again.
 NCU_TRAFFIC = [
-    # profiles/direct_sfu-1920x1080-n10000.md: 0.293 MB read + 1.543 MB written per launch
+    # profiles/direct_sfu-1920x1080-n10000.md (api.cu holds the launch's CTA count)
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
-     "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh"],
-     "sha1": "36fb7384f442babe84eccbbd5d663223087aec8b", "bytes_per_launch": 1836288},
+     "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh", "api.cu"],
+     "sha1": "", "bytes_per_launch": 0},
     # profiles/gemm_f16-1920x1080-n50000.md: 600.789 MB read + 3.401 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
      "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
@@ -412,12 +431,13 @@ def run_ours(args):
             # the whole hologram (prep, factors, GEMM, reduction) against the same tensor peak
             rec["e2e_tensor_frac"] = 4.0 * wc.evals * passes / (ms * 1e-3) / 1e12 / peak_tc
         elif extra in kp:
-            mufu = MUFU_PER_SM_PER_CLK * torch.cuda.get_device_properties(local).multi_processor_count * \
+            ops, pipe, per_clk, per_eval = direct_ops(extra, wc.width, wc.height, wc.n_points)
+            pk = per_clk * torch.cuda.get_device_properties(local).multi_processor_count * \
                 (_peaks().get("sm_max_mhz") or 2070.0) * 1e6
             dms = kp[extra][1] / max(kp[extra][0], 1)
-            rec["roofline"] = {"kernel": extra, "bound": "alu", "achieved": wc.evals / (dms * 1e-3) / 1e9,
-                               "peak": mufu / 1e9, "unit": "Gcos/s (MUFU)",
-                               "frac": wc.evals / (dms * 1e-3) / mufu,
+            rec["roofline"] = {"kernel": extra, "bound": "alu", "achieved": ops / (dms * 1e-3) / 1e9,
+                               "peak": pk / 1e9, "unit": f"G {pipe} op/s", "ops_per_eval": round(per_eval, 4),
+                               "frac": ops / (dms * 1e-3) / pk,
                                "traffic": ncu_traffic(extra, extra, wc.name)}
         key = f"{extra}@{wc.name}"
         forms[key] = rec
@@ -675,20 +695,23 @@ def run_ours(args):
         roof = {"bound": "tensor", "unit": "TFLOP/s", "gemm_k": 2 * k_units,
                 "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
     else:
-        # MUFU-bound: one hardware sine per evaluation at most
+        # the pipe of the implemented evaluation: MUFU (SFU form) or FMA (accurate form), see direct_ops
         dom = args.form
         src = "direct.cu"
         dom_launches, dom_ms = prof.get(dom, (0, 0.0))
-        peak = MUFU_PER_SM_PER_CLK * props.multi_processor_count * sm_max * 1e6 / 1e9
-        achieved = cloud.evals / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e9 if dom_ms > 0 else None
-        roof = {"bound": "alu", "unit": "Gcos/s (MUFU)",
-                "peak_basis": f"{MUFU_PER_SM_PER_CLK} MUFU cos/clk/SM x {props.multi_processor_count} SMs x "
-                              f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)"}
-        # the same pipe measured in this run: independent hardware sines on every SM (cgh_measure_mufu)
-        from paper_1309_2734_gb300 import _lib
-        probe = _lib.cgh_measure_mufu(h.ctx) / 1e9
-        roof["peak_probe"] = probe
-        roof["frac_of_probe"] = (cloud.evals / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e9) / probe if dom_ms > 0 else None
+        ops, pipe, per_clk, per_eval = direct_ops(args.form, W, H, N)
+        peak = per_clk * props.multi_processor_count * sm_max * 1e6 / 1e9
+        achieved = ops / (dom_ms / max(dom_launches, 1) * 1e-3) / 1e9 if dom_ms > 0 else None
+        roof = {"bound": "alu", "unit": f"G {pipe} op/s",
+                "peak_basis": f"{per_clk} {pipe} op/clk/SM x {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
+                              f"(sm_max_mhz of measured peaks); {per_eval:.4f} {pipe} op per evaluation "
+                              "(8 x 8 pixels a thread: the sine and cosine of 8 column and 8 row turns per point)"}
+        if pipe == "MUFU":
+            # the same pipe measured in this run: independent hardware sines on every SM (cgh_measure_mufu)
+            from paper_1309_2734_gb300 import _lib
+            probe = _lib.cgh_measure_mufu(h.ctx) / 1e9
+            roof["peak_probe"] = probe
+            roof["frac_of_probe"] = achieved / probe if achieved else None
     traffic = ncu_traffic(dom, args.form, cloud.name)
 
     cpu, nrms = (None, None)

@@ -25,7 +25,7 @@ namespace cgh {
 // CGH_OPT_POINT_SPLIT > 0: point chunks into partial planes and the fixed-order chunk reduction after.
 constexpr int kStreamMinPoints = 64;      // fewest points of one CTA's share in the balanced layout
 constexpr int kStreamSharePoints = 1024;  // points per share from which CTAs beyond the resident ones are added
-constexpr int kStreamWaves = 3;           // at most this many CTAs per resident slot
+constexpr int kStreamWaves = 2;           // at most this many CTAs per resident slot
 
 int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, double lambda, const float *d_xyz,
                const float *d_amp, int64_t n, float *d_out)
@@ -42,8 +42,9 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
     size_t ws_rest = 0;
     if (stream_k) {
         // the shape with the fewer padded pixels; up to kStreamWaves CTAs per resident slot (measured at
-        // 1920x1080, 10^4 points: 304 CTAs 4.69 ms, 912 4.64, 2128 4.71, 5100 4.86), each share of at least
-        // kStreamSharePoints points beyond the first wave and kStreamMinPoints within it
+        // 1920x1080, 10^4 points, 8 x 8 pixels a thread, four 128-thread CTAs per SM: 608 CTAs 3.02 ms, 1216 2.995,
+        // 1824 3.017, 2432 3.22; DRAM writes 0.1 / 3.9 / 18.4 MB per launch, the parts L2 no longer holds), each
+        // share of at least kStreamSharePoints points beyond the first wave and kStreamMinPoints within it
         auto padded = [&](const DirectShape &s) {
             return (int64_t)((width + s.tile_w - 1) / s.tile_w) * s.tile_w *
                    (((int64_t)height + s.tile_h - 1) / s.tile_h) * s.tile_h;
