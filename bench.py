@@ -63,11 +63,11 @@ NCU_TRAFFIC = [
     # profiles/direct_sfu-1920x1080-n10000.md (api.cu holds the launch's CTA count)
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
      "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh", "api.cu"],
-     "sha1": "", "bytes_per_launch": 0},
-    # profiles/gemm_f16-1920x1080-n50000.md: 600.789 MB read + 3.401 MB written per launch
+     "sha1": "8989dc504390e9a6bbad37b1cb76fdabee3cf7b6", "bytes_per_launch": 5392384},
+    # profiles/gemm_f16-1920x1080-n50000.md: 600.731 MB read + 3.053 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
      "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
-     "sha1": "99556ba4bfeec90f2f93e6789f16ae25349492a4", "bytes_per_launch": 604190464},
+     "sha1": "1b3da24ffb355250d6467758d091b4a7b91d7b3a", "bytes_per_launch": 603784192},
 ]
 
 
