@@ -49,13 +49,20 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
             return (int64_t)((width + s.tile_w - 1) / s.tile_w) * s.tile_w *
                    (((int64_t)height + s.tile_h - 1) / s.tile_h) * s.tile_h;
         };
-        // the 8 x 8-pixel thread block of the tile with the fewer padded pixels (the tall one among equals);
-        // CGH_OPT_DIRECT_SHAPE pins one
+        // the 8 x 8-pixel thread block of the tile with the fewer padded pixels (the tall one among equals) when the
+        // hologram fills every resident slot with shares of kStreamSharePoints points; a smaller one takes the
+        // 8 x 4-pixel blocks of twice the threads (256 x 256, 1,024 points: 71 against 83 us at the best CTA
+        // count -- with few points per CTA the fold of a tile's many parts dominates); CGH_OPT_DIRECT_SHAPE pins one
         if (ctx->direct_shape > 0) {
             sh = direct_stream_shape(ctx->direct_shape - 1);
         } else {
             sh = direct_stream_shape(2);
             if (padded(direct_stream_shape(3)) < padded(sh)) sh = direct_stream_shape(3);
+            const int64_t pairs = padded(sh) / ((int64_t)sh.tile_w * sh.tile_h) * n;
+            if (pairs < (int64_t)ctx->num_sms * direct_stream_per_sm(sfu, sh) * kStreamSharePoints) {
+                sh = direct_stream_shape(1);
+                if (padded(direct_stream_shape(0)) < padded(sh)) sh = direct_stream_shape(0);
+            }
         }
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         const int64_t units = tiles * n;

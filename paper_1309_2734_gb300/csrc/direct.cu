@@ -92,28 +92,46 @@ struct StreamSink {
             __syncthreads();
             if (!seg->last) return;
             __threadfence();
-            // the tile's parts in CTA order, one float4 of every thread's block at a time
+            // the tile's parts in CTA order, G float4s of every thread's block at a time: the G loads of one part
+            // are independent, so a part costs one memory round trip per group rather than one per float4
+            constexpr int G = 4;
+            static_assert(Q4 % G == 0, "whole groups of float4s");
 #pragma unroll
-            for (int q = 0; q < Q4; ++q) {
-                const int r = q * 4 / TL, i = q * 4 % TL;
-                float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int q0 = 0; q0 < Q4; q0 += G) {
+                float4 a[G];
                 for (long long cs = lo; cs <= hi; ++cs) {
-                    const float4 v = cs == c ? make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3])
-                                             : __ldcg(slots + (2 * cs + slot_of(cs, t)) * (long long)(Q4 * NT) +
-                                                      q * NT + tid);
-                    if (cs == lo) {
-                        a = v;
+                    float4 v[G];
+                    if (cs == c) {
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            const int r = (q0 + g) * 4 / TL, i = (q0 + g) * 4 % TL;
+                            v[g] = make_float4(tot[r][i], tot[r][i + 1], tot[r][i + 2], tot[r][i + 3]);
+                        }
                     } else {
-                        a.x += v.x;
-                        a.y += v.y;
-                        a.z += v.z;
-                        a.w += v.w;
+                        const float4 *part = slots + (2 * cs + slot_of(cs, t)) * (long long)(Q4 * NT) + tid;
+#pragma unroll
+                        for (int g = 0; g < G; ++g) v[g] = __ldcg(part + (q0 + g) * NT);
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        if (cs == lo) {
+                            a[g] = v[g];
+                        } else {
+                            a[g].x += v[g].x;
+                            a[g].y += v[g].y;
+                            a[g].z += v[g].z;
+                            a[g].w += v[g].w;
+                        }
                     }
                 }
-                tot[r][i] = a.x;
-                tot[r][i + 1] = a.y;
-                tot[r][i + 2] = a.z;
-                tot[r][i + 3] = a.w;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int r = (q0 + g) * 4 / TL, i = (q0 + g) * 4 % TL;
+                    tot[r][i] = a[g].x;
+                    tot[r][i + 1] = a[g].y;
+                    tot[r][i + 2] = a[g].z;
+                    tot[r][i + 3] = a[g].w;
+                }
             }
         }
         const int m0 = (int)(t % tiles_x) * (BX * TL) + (tid % BX) * TL;
