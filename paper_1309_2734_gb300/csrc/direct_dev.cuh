@@ -1,6 +1,6 @@
 // Device-side code of the direct form, shared by its kernels (direct.cu) and by the persistent batch kernel
-// (persist.cu): the per-(point, pixel) term and the unit of work that sums the points of a range into a tile of
-// pixels.
+// (persist.cu): the terms of one point in a thread's block of pixels and the unit of work that sums the points of a
+// range into a tile of pixels.
 //
 // a2, the direct form.  Every thread owns a TL x TR block of hologram pixels
 // (TL consecutive columns of TR consecutive rows) and sums every point of the
@@ -10,37 +10,36 @@
 // 1-D bulk copies (TMA engine, no multicast), double buffered behind two
 // mbarriers, and read back as warp-wide broadcasts.
 //
-// Phase.  For one point, the thread forms its corner phase G = C r^2 mod 2^64
-// (top 32 bits, exact to one unit of 2^-32 turn; plus the point's piston and
-// the reference phase when those are on), the first differences along
-// x and y, and then walks its block with the recurrence of Eqs. 6-8
-// (Section 2.2): Gamma_{k+1} = Gamma_k + delta_k, delta_{k+1} = delta_k + Delta,
-// Delta = 2 c_j, in 32-bit fixed-point turns, where wrap-around is the
-// reduction modulo one turn.  Moving down one row adds the row difference
-// (shared by all TL columns) the same way.  The drift of the walk is below
-// 1 + TL + TL^2/2 + TR + TR^2/2 units of 2^-32 turn (about 5e-8 rad for 8 x 4).
+// Phase.  For one point the squared distance splits into a column part and a
+// row part, r^2 = (m - x)^2 + (n - y)^2.  The thread forms the turns of its
+// first column and first row, C d^2 mod 2^64 (top 32 bits, exact to one unit
+// of 2^-32 turn), their first differences, and walks its TL columns and its TR
+// rows with the recurrence of Eqs. 6-8 (Section 2.2): Gamma_{k+1} = Gamma_k +
+// delta_k, delta_{k+1} = delta_k + Delta, Delta = 2 c_j, in 32-bit fixed-point
+// turns, where wrap-around is the reduction modulo one turn (drift below
+// 1 + TL + TL^2/2 units of 2^-32 turn along the columns, the same with TR down
+// the rows).  The point's piston and the reference phase join the column
+// turns (its row step the row turns).
 //
-// Cosine.
-//  - SFU form: the turn is advanced by a quarter (t' = t + 1/4, folded into
-//    the corner phase), its top 23 bits become the mantissa of a float f in
-//    [1, 2) (one funnel shift), and u = K1 f - 1.5 K1 = 2 pi (t - 1/4) lies in
-//    [-pi, pi) (one FFMA).  The hardware sine (__sinf, MUFU) of u is
-//    -cos(2 pi t); the point's amplitude is negated to compensate.  The MUFU
+// Sine and cosine.  The term is A cos 2 pi (a_i + b_r), taken by the cosine
+// addition formula from the sine and cosine of the TL + TR turns
+// (point_terms_sep).  A turn's top 23 bits become the mantissa of a float f in
+// [1, 2) (one funnel shift, rounded to nearest by a bias) and u = K1 f - K0 is
+// the angle in [-pi, pi) (one FFMA):
+//  - SFU form: the hardware sine and cosine of u (__sincosf, MUFU).  The MUFU
 //    sine is exactly odd, but its error is not zero on average over an
 //    arbitrary argument grid: on the grid of the plain fl(2 pi) f - fl(3 pi),
-//    which sits a third of a step off symmetric, it averaged +1.35e-8, a
-//    per-term bias that grows linearly with N (NRMS 1.6e-5 at N = 10^6).  K1
-//    is therefore 2 pi rounded to a float whose 1.5 multiple is exact, so the
+//    which sits a third of a step off symmetric, it averaged +1.35e-8 (a bias
+//    that grew linearly with N when each term took one hardware sine).  K1 is
+//    therefore 2 pi rounded to a float whose 1.5 multiple K0 is exact, so the
 //    FFMA returns exactly RN((f - 1.5) K1): the argument grid is symmetric
-//    about zero and the odd error cancels.  K1 is 1.04e-7 above 2 pi (a
-//    zero-mean phase-scale error below 3.3e-7 rad).  The corner-phase bias
-//    also rounds the 23-bit truncation to nearest.  (Moving an eighth of the
-//    terms to a sine polynomial on the FMA pipe was measured: the MUFU pipe
-//    went from 90 % to 74 % busy but issue and ALU pressure grew and the kernel
-//    got 6 % slower, so every term uses the MUFU.)
+//    about zero.  K1 is 1.04e-7 above 2 pi (a zero-mean phase-scale error below
+//    3.3e-7 rad).  The hardware cosine's error is even; every other point is
+//    shifted by half a turn so that its mean cancels (point_terms_sep).
 //  - accurate form: the turn, read as a signed 32-bit integer, converts to
 //    t in [-1/2, 1/2) and cos(2 pi t) is a degree-12 even polynomial
-//    (cospoly.h), all on the FMA pipe.
+//    (cospoly.h), all on the FMA pipe; the sine is the cosine a quarter turn
+//    back.
 //
 // Accumulation is two-level: each point tile is summed into fresh partials
 // that are then added into the running totals, which keeps single-precision
@@ -60,30 +59,19 @@ namespace dev {
 // so that 1.5 K1 is a float too (0x40c90fdc and 0x4116cbe5)
 constexpr float kK1 = 6.28318595886230469f;
 constexpr float kK0 = 9.42477893829345703f;   // exactly 1.5 * kK1
-// 2^30: a quarter turn; 2^8 rounds the 23-bit truncation to nearest
-constexpr uint32_t kSfuBias = (1u << 30) + 256u;
-
-// Evaluation modes of one (point, pixel) term.
-enum { kEvalSfu = 0, kEvalAccurate = 1 };
-
-template <int MODE>
-__device__ __forceinline__ float cos_term(uint32_t g)
+// cos(2 pi t) of a signed fixed-point turn t in [-1/2, 1/2) (2^-32 turn) by the polynomial of cospoly.h.
+__device__ __forceinline__ float cos_turn_poly(uint32_t g)
 {
-    if constexpr (MODE == kEvalSfu) {
-        const float f = __uint_as_float(__funnelshift_r(g, 0x7fu, 9));   // 1 + top23(g) 2^-23
-        return __sinf(fmaf(f, kK1, -kK0));                              // = -cos(2 pi t)
-    } else {
-        const float t = (float)(int)g * 2.3283064365386963e-10f;        // signed turn, [-1/2, 1/2)
-        const float u = t * t;
-        float c = CGH_COSPOLY_6;
-        c = fmaf(c, u, CGH_COSPOLY_5);
-        c = fmaf(c, u, CGH_COSPOLY_4);
-        c = fmaf(c, u, CGH_COSPOLY_3);
-        c = fmaf(c, u, CGH_COSPOLY_2);
-        c = fmaf(c, u, CGH_COSPOLY_1);
-        c = fmaf(c, u, CGH_COSPOLY_0);
-        return c;                                                        // = cos(2 pi t)
-    }
+    const float t = (float)(int)g * 2.3283064365386963e-10f;   // signed turn, [-1/2, 1/2)
+    const float u = t * t;
+    float c = CGH_COSPOLY_6;
+    c = fmaf(c, u, CGH_COSPOLY_5);
+    c = fmaf(c, u, CGH_COSPOLY_4);
+    c = fmaf(c, u, CGH_COSPOLY_3);
+    c = fmaf(c, u, CGH_COSPOLY_2);
+    c = fmaf(c, u, CGH_COSPOLY_1);
+    c = fmaf(c, u, CGH_COSPOLY_0);
+    return c;
 }
 
 // The reference phase seen by one thread: its value at the thread's corner
@@ -100,159 +88,24 @@ __device__ __forceinline__ PixelRef pixel_ref(const PhaseRef &r, int m0, int n0)
     return PixelRef{ref_turn(r, m0, n0), ref_step(r.kx), ref_step(r.ky)};
 }
 
-// e^{i 2 pi t} of a fixed-point turn t from the hardware sine on the symmetric argument grid of the SFU
-// amplitude form: cos(2 pi t) as there, sin(2 pi t) = sin(v) with v = K1 (f2 - 1.5) from the turn advanced by a
-// half (f2 - 1 = t + 1/2), so the MUFU's odd error averages out in both parts.
-__device__ __forceinline__ float2 cis_sfu(uint32_t t)
-{
-    const float f = __uint_as_float(__funnelshift_r(t + kSfuBias, 0x7fu, 9));
-    const float f2 = __uint_as_float(__funnelshift_r(t + kSfuBias + (1u << 30), 0x7fu, 9));
-    return make_float2(-__sinf(fmaf(f, kK1, -kK0)), __sinf(fmaf(f2, kK1, -kK0)));
-}
-
-__device__ __forceinline__ float2 cmul_f(float2 x, float2 y)
-{
-    return make_float2(fmaf(x.x, y.x, -x.y * y.y), fmaf(x.x, y.y, x.y * y.x));
-}
-
-// The point's second difference D (2^-32 turn).  v = e^{i 2 pi D}, the same for every pixel, is computed once per
-// point and CTA when its tile arrives, with the accurate single-precision sine and cosine: the term at column i
-// carries v's error i (i - 1) / 2 times over (point_terms_wave).
-template <bool EXTRA>
-__device__ __forceinline__ uint32_t wave_second_difference(const int4 q, const uint2 w)
-{
-    return EXTRA ? __funnelshift_l((uint32_t)q.w, (uint32_t)q.z, 1) : w.x;   // 2 C with the piston, else aux.x
-}
-
-// D as a signed turn has up to 32 significant bits, more than a float holds: its top 24 bits and its low 8 bits
-// are each exact in single precision, and v = e^{i 2 pi D_hi} e^{i 2 pi D_lo} (the plain conversion dropped up to
-// 2^-25 turn, which column i carries i (i - 1) / 2 times).
-__device__ __forceinline__ float2 wave_rotation(uint32_t D)
-{
-    float sh, ch, sl, cl;
-    sincospif((float)(int)(D & 0xffffff00u) * (1.0f / 2147483648.0f), &sh, &ch);   // [-1, 1): twice the turn
-    sincospif((float)(D & 0xffu) * (1.0f / 2147483648.0f), &sl, &cl);
-    return cmul_f(make_float2(ch, sh), make_float2(cl, sl));
-}
-
-// Adds one point's terms of the complex object wave (Eq. 2, restricted form) to a thread's TL x TR block.
-// Along a row the phase is quadratic in the column (Eqs. 6-8): first difference d + i D at column i, the same
-// on every row.  So e^{i 2 pi t} is taken from the hardware only at each row's first column, and for the
-// column steps w_0 = e^{i 2 pi d} and v = e^{i 2 pi D}; then w_i = w_(i-1) v and the row walks by
-// z_i = z_(i-1) w_(i-1): TR + 1 sines and cosines per point and thread (v once per point and CTA) instead of
-// TL TR, the rest complex products on the FMA pipe.  The term at column i carries the row anchor's error, i times
-// w_0's and i (i - 1) / 2 times v's, and the chains restart at every point and row: about 1.3 10^-6 of the field
-// (NRMS) against 4 10^-7 with two hardware sines per term (2.6 10^-6 with v from the hardware; 7 10^-7, 15 %
-// slower, with the chains restarted at every half row).
-template <int TL, int TR, bool EXTRA>
-__device__ __forceinline__ void point_terms_wave(const int4 q, const uint2 w, const float2 v, int m0, int n0,
-                                                 const PixelRef &pr, float (&pre)[TR][TL], float (&pim)[TR][TL])
-{
-    const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
-    const uint32_t dx = (uint32_t)(m0 - q.x);
-    const uint32_t dy = (uint32_t)(n0 - q.y);
-    const uint32_t r2 = dx * dx + dy * dy;
-    const uint32_t r2x = r2 + 2u * dx + 1u;
-    const uint32_t r2y = r2 + 2u * dy + 1u;
-    const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
-    uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
-    uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
-    uint32_t g = c0;
-    const uint32_t D = wave_second_difference<EXTRA>(q, w);
-    if constexpr (EXTRA) {   // piston (aux.x) and reference
-        d += pr.dx;
-        e += pr.dy;
-        g += w.x + pr.g;
-    }
-    const float a = __uint_as_float(w.y);
-    float2 st[TL - 1];   // e^{i 2 pi (d + i D)}: the step from column i to i + 1
-    st[0] = cis_sfu(d);
-#pragma unroll
-    for (int i = 1; i < TL - 1; ++i) st[i] = cmul_f(st[i - 1], v);
-#pragma unroll
-    for (int r = 0; r < TR; ++r) {
-        float2 z = cis_sfu(g);
-        pre[r][0] = fmaf(a, z.x, pre[r][0]);
-        pim[r][0] = fmaf(a, z.y, pim[r][0]);
-#pragma unroll
-        for (int i = 1; i < TL; ++i) {
-            z = cmul_f(z, st[i - 1]);
-            pre[r][i] = fmaf(a, z.x, pre[r][i]);
-            pim[r][i] = fmaf(a, z.y, pim[r][i]);
-        }
-        if (r + 1 < TR) {
-            g += e;
-            e += D;
-        }
-    }
-}
-
-// Adds one point's terms to a thread's TL x TR block (corner m0, n0).
-template <int TL, int TR, int MODE, bool EXTRA>
-__device__ __forceinline__ void point_terms(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
-                                            float (&part)[TR][TL])
-{
-    constexpr bool kSfuSign = MODE != kEvalAccurate;
-    const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
-    const uint32_t dx = (uint32_t)(m0 - q.x);
-    const uint32_t dy = (uint32_t)(n0 - q.y);
-    const uint32_t r2 = dx * dx + dy * dy;          // < 2^32, exact
-    const uint32_t r2x = r2 + 2u * dx + 1u;         // (dx+1)^2 + dy^2
-    const uint32_t r2y = r2 + 2u * dy + 1u;         // dx^2 + (dy+1)^2
-    const uint32_t c0 = chi * r2 + __umulhi(clo, r2);
-    uint32_t d = chi * r2x + __umulhi(clo, r2x) - c0;
-    uint32_t e = chi * r2y + __umulhi(clo, r2y) - c0;
-    uint32_t g0 = c0, D = w.x;
-    if constexpr (EXTRA) {   // piston (aux.x) and reference at the corner; 2 C formed from C
-        d += pr.dx;
-        e += pr.dy;
-        g0 += w.x + pr.g;
-        D = __funnelshift_l(clo, chi, 1);
-    }
-    const float a = kSfuSign ? -__uint_as_float(w.y) : __uint_as_float(w.y);
-    uint32_t g[TL];
-    g[0] = g0 + (kSfuSign ? kSfuBias : 0u);
-#pragma unroll
-    for (int i = 1; i < TL; ++i) {
-        g[i] = g[i - 1] + d;
-        d += D;
-    }
-#pragma unroll
-    for (int r = 0; r < TR; ++r) {
-#pragma unroll
-        for (int i = 0; i < TL; ++i) part[r][i] = fmaf(a, cos_term<MODE>(g[i]), part[r][i]);
-        if (r + 1 < TR) {
-#pragma unroll
-            for (int i = 0; i < TL; ++i) g[i] += e;
-            e += D;
-        }
-    }
-}
-
-// One unit of work: point tiles [t_begin, t_end) of one cloud into one
-// CTA-sized pixel tile with corner (tile_m0, tile_n0).  kg counts the point
-// tiles this CTA consumed before (stage and mbarrier parity carry across units).
-// PLANES = 1: the amplitude hologram; PLANES = 2: the complex object wave, real
-// part at dst and imaginary part at dst + im_offset (SFU form only).
-// SMEM_TOT: the running totals live in shared memory (s_tot, index-major: entry (c, r, i) of thread tid at
-// ((c TR + r) TL + i) BX BY + tid, so a warp's accesses are consecutive words) instead of registers, which leaves
-// the registers to the point tile's partial sums of a taller thread block.
 // Adds one point's terms to a thread's TL x TR block by the separability of the squared distance inside the block:
 // with a_i the turn of column m0 + i and b_r that of row n0 + r (each walked by Eqs. 6-8 in exact fixed point, the
 // piston and the reference phase's corner and column steps in a_i, its row step in b_r),
 //     A cos 2 pi (a_i + b_r) = cos 2 pi a_i (A cos 2 pi b_r) - sin 2 pi a_i (A sin 2 pi b_r),
 // so the hardware sine and cosine (one __sincosf, two MUFU operations) of TL + TR turns serve TL x TR terms at two
 // FFMAs each: TL TR / (2 (TL + TR)) times fewer MUFU operations than one cosine per term (2x at 8 x 8).  Each turn
-// is rounded to 2^-23 and taken on the symmetric argument grid of cos_term.  The hardware cosine's error is even in
+// is rounded to 2^-23 and taken on the symmetric argument grid of kK1 and kK0.  The hardware cosine's error is even in
 // its argument and does not average to zero over the grid, which made the field's error grow with the number of
 // points (NRMS 9.0e-7 at 10^4 points, 3.1e-6 at 2 10^5, 1920x1080); flip = a half turn on every other point
 // shifts both of its turns by pi, which leaves the term as it is (cos((a + pi) + (b + pi)) = cos(a + b)) and
 // turns the sign of that mean, so it cancels over pairs of points (5.8e-7 and 6.9e-7).
-// ACC: the accurate form -- cos 2 pi t from the polynomial of cos_term and sin 2 pi t = cos 2 pi (t - 1/4) from the
+// ACC: the accurate form -- cos 2 pi t from the polynomial of cos_turn_poly and sin 2 pi t = cos 2 pi (t - 1/4) from the
 // same polynomial, on the FMA pipe (no flip needed: the polynomial's mean error over the turns is about zero).
-template <int TL, int TR, bool EXTRA, bool ACC = false>
+// PLANES = 2: the complex object wave (Eq. 2, restricted form), A e^{i 2 pi (a_i + b_r)}: the real part to part,
+// the imaginary part, sin 2 pi a_i (A cos 2 pi b_r) + cos 2 pi a_i (A sin 2 pi b_r), to part_im.
+template <int TL, int TR, bool EXTRA, bool ACC = false, int PLANES = 1>
 __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int m0, int n0, const PixelRef &pr,
-                                                uint32_t flip, float (&part)[TR][TL])
+                                                uint32_t flip, float (&part)[TR][TL], float (&part_im)[TR][TL])
 {
     const uint32_t chi = (uint32_t)q.z, clo = (uint32_t)q.w;
     const uint32_t dx = (uint32_t)(m0 - q.x);
@@ -277,8 +130,8 @@ __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int
     auto cis = [](uint32_t t, float &s, float &c) {
         if constexpr (ACC) {
             const uint32_t u = t - kHalfBias;            // the turn itself (the flip is a whole half turn)
-            c = cos_term<kEvalAccurate>(u);
-            s = cos_term<kEvalAccurate>(u - (1u << 30));   // cos 2 pi (t - 1/4)
+            c = cos_turn_poly(u);
+            s = cos_turn_poly(u - (1u << 30));   // cos 2 pi (t - 1/4)
         } else {
             const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));
             __sincosf(fmaf(f, kK1, -kK0), &s, &c);
@@ -298,7 +151,10 @@ __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int
         cb *= amp;
         sb *= amp;
 #pragma unroll
-        for (int i = 0; i < TL; ++i) part[r][i] = fmaf(-sa[i], sb, fmaf(ca[i], cb, part[r][i]));
+        for (int i = 0; i < TL; ++i) {
+            part[r][i] = fmaf(-sa[i], sb, fmaf(ca[i], cb, part[r][i]));
+            if constexpr (PLANES == 2) part_im[r][i] = fmaf(ca[i], sb, fmaf(sa[i], cb, part_im[r][i]));
+        }
         b += db;
         db += D;
     }
@@ -412,18 +268,13 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         const uint2 *sa = s_aux[st];
         const int p_lo = k == 0 ? p_first : 0;
         const int p_hi = k == nt - 1 ? p_last_end : T;
-        if constexpr (PLANES == 2) {
-            __shared__ float2 s_rot[T];   // e^{i 2 pi D} of the tile's points, once each per CTA
-            for (int p = tid; p < T; p += BX * BY) s_rot[p] = wave_rotation(wave_second_difference<EXTRA>(sg[p], sa[p]));
-            Sync::sync();
-#pragma unroll 1
-            for (int p = p_lo; p < p_hi; ++p)
-                point_terms_wave<TL, TR, EXTRA>(sg[p], sa[p], s_rot[p], m0, n0, pr, part[0], part[PLANES - 1]);
-        } else {
+        {
+            static_assert(PLANES == 1 || SFU, "the complex wave takes the hardware sine and cosine");
 #pragma unroll 1
             for (int p = p_lo; p < p_hi; ++p)   // p has the parity of the point's index (tiles start even)
-                point_terms_sep<TL, TR, EXTRA, !SFU>(sg[p], sa[p], m0, n0, pr, SFU ? (uint32_t)(p & 1) << 31 : 0u,
-                                                     part[0]);
+                point_terms_sep<TL, TR, EXTRA, !SFU, PLANES>(sg[p], sa[p], m0, n0, pr,
+                                                             SFU ? (uint32_t)(p & 1) << 31 : 0u, part[0],
+                                                             part[PLANES - 1]);
         }
 #pragma unroll
         for (int c = 0; c < PLANES; ++c)
