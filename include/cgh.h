@@ -136,9 +136,11 @@ enum {
                                    cudaMalloc would (the call returns CGH_ENOMEM, nothing is launched, and the
                                    context stays usable); 0 = off */
     CGH_OPT_DIRECT_SHAPE = 18,  /* direct SFU amplitude form with CGH_OPT_POINT_SPLIT = 0: the thread block;
-                                   0 = automatic (8 x 8 pixels a thread, the tile with fewer padded pixels),
-                                   1 = 32 x 8 threads of 8 x 4 pixels, 2 = 16 x 16 threads of 8 x 4, 3 = 16 x 8
-                                   threads of 8 x 8, 4 = 32 x 4 threads of 8 x 8 */
+                                   0 = automatic (5 or 6 by the padded pixels), 1 = 32 x 8 threads of 8 x 4
+                                   pixels, 2 = 16 x 16 threads of 8 x 4, 3 = 16 x 8 threads of 8 x 8, 4 = 32 x 4
+                                   threads of 8 x 8 (each thread its own sines and cosines); 5 = 16 x 16 threads of
+                                   8 x 4, 6 = 32 x 8 threads of 8 x 4, with the sines and cosines of a point's
+                                   columns and rows taken once per CTA into shared-memory tables */
     CGH_OPT_GEMM_PERSISTENT = 19, /* GEMM forms, cgh_point_cloud: 1 = the hologram as a one-instance batch in the
                                    persistent kernel (its factors generated K chunk by K chunk while the tensor
                                    cores run the GEMM of the chunks already there; a CUDA graph replayed while the

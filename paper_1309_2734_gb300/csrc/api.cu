@@ -49,20 +49,14 @@ int run_direct(cgh_ctx *ctx, bool sfu, int width, int height, double pitch, doub
             return (int64_t)((width + s.tile_w - 1) / s.tile_w) * s.tile_w *
                    (((int64_t)height + s.tile_h - 1) / s.tile_h) * s.tile_h;
         };
-        // the 8 x 8-pixel thread block of the tile with the fewer padded pixels (the tall one among equals) when the
-        // hologram fills every resident slot with shares of kStreamSharePoints points; a smaller one takes the
-        // 8 x 4-pixel blocks of twice the threads (256 x 256, 1,024 points: 71 against 83 us at the best CTA
-        // count -- with few points per CTA the fold of a tile's many parts dominates); CGH_OPT_DIRECT_SHAPE pins one
+        // blocks of 8 x 4 pixels with the tables of the tile, 16 x 16 threads (a 128 x 64 tile) unless 32 x 8 (256 x
+        // 32) pads a fifth fewer pixels (at equal padding the tall block measured 16 % faster: a point's 192 table
+        // entries over 256 threads instead of 288); CGH_OPT_DIRECT_SHAPE pins any block
         if (ctx->direct_shape > 0) {
             sh = direct_stream_shape(ctx->direct_shape - 1);
         } else {
-            sh = direct_stream_shape(2);
-            if (padded(direct_stream_shape(3)) < padded(sh)) sh = direct_stream_shape(3);
-            const int64_t pairs = padded(sh) / ((int64_t)sh.tile_w * sh.tile_h) * n;
-            if (pairs < (int64_t)ctx->num_sms * direct_stream_per_sm(sfu, sh) * kStreamSharePoints) {
-                sh = direct_stream_shape(1);
-                if (padded(direct_stream_shape(0)) < padded(sh)) sh = direct_stream_shape(0);
-            }
+            sh = direct_stream_shape(4);
+            if (padded(direct_stream_shape(5)) * 6 < padded(sh) * 5) sh = direct_stream_shape(5);
         }
         const int64_t tiles = (int64_t)((width + sh.tile_w - 1) / sh.tile_w) * ((height + sh.tile_h - 1) / sh.tile_h);
         const int64_t units = tiles * n;
@@ -923,7 +917,7 @@ int cgh_set_option(cgh_ctx *ctx, int key, int64_t value)
         ctx->test_alloc_fail = (int)value;
         return CGH_OK;
     case CGH_OPT_DIRECT_SHAPE:
-        if (value < 0 || value > 4) return CGH_EINVAL;
+        if (value < 0 || value > 6) return CGH_EINVAL;
         ctx->direct_shape = (int)value;
         return CGH_OK;
     case CGH_OPT_GEMM_PERSISTENT:

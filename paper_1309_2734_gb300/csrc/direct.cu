@@ -164,7 +164,7 @@ struct StreamSink {
 // pass.  counters (one per tile) are zero at launch; slots hold 2 C tiles of totals, thread-major float4s.
 // SMEM_TOT: the running totals in shared memory (TR TL floats per thread, dynamic), which leaves the registers to a
 // wider thread block's partial sums.
-template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT>
+template <int TL, int TR, int BX, int BY, bool SFU, bool EXTRA, bool SMEM_TOT, bool TABLES>
 __global__ void __launch_bounds__(BX *BY, 512 / (BX * BY))
     direct_stream_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_points, int width,
                          int height, int tiles_x, long long units, float *__restrict__ out,
@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(BX *BY, 512 / (BX * BY))
     __shared__ alignas(128) uint2 s_aux[2][kPointTile];
     __shared__ alignas(8) uint64_t s_bar[2];
     __shared__ StreamSeg s_seg;
-    extern __shared__ float s_tot[];
+    extern __shared__ __align__(16) float s_dyn[];   // the running totals (SMEM_TOT), then the tables (TABLES)
+    float *s_tot = s_dyn;
+    float2 *s_tab = reinterpret_cast<float2 *>(s_dyn + (SMEM_TOT ? TL * TR * BX * BY : 0));
     init_point_barriers<BX, BY>(s_bar);
     const StreamSink<TL, TR, BX, BY> sink{&s_seg, slots, counters, out, units, (long long)gridDim.x,
                                           (long long)n_points, tiles_x, width, height, vec, status};
@@ -197,10 +199,10 @@ __global__ void __launch_bounds__(BX *BY, 512 / (BX * BY))
         __syncthreads();
         const int k0 = p0 / T, k1 = (p1 + T - 1) / T;
         const int drop = (blockIdx.x == 0 && w == w0) ? drop_tile : -1;
-        if (!direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA, SMEM_TOT>(
+        if (!direct_unit<TL, TR, BX, BY, SFU, 1, EXTRA, SMEM_TOT, StreamSink<TL, TR, BX, BY>, CtaSync, T, TABLES>(
                 geo, aux, k0, k1, (int)(t % tiles_x) * (BX * TL), (int)(t / tiles_x) * (BY * TR), width, height,
                 out, vec, s_geo, s_aux, s_bar, kg, status, timeout_ns, drop, 0, ref, s_tot, p0 - k0 * T,
-                p1 - (k1 - 1) * T, sink))
+                p1 - (k1 - 1) * T, sink, s_tab))
             break;
         w = s_seg.t * n_points + s_seg.p1;
         __syncthreads();   // s_seg and the point stages are reused by the next segment
@@ -318,24 +320,26 @@ namespace {
 
 // The balanced layout's thread blocks: TL x TR pixels per thread, BX x BY threads, totals in registers or shared
 // memory.
-template <int TL, int TR, int BX, int BY, bool SMEM_TOT>
+template <int TL, int TR, int BX, int BY, bool SMEM_TOT, bool TABLES = false>
 struct StreamCfg {
-    static constexpr size_t kDyn = SMEM_TOT ? (size_t)TL * TR * BX * BY * sizeof(float) : 0;
+    static constexpr size_t kTotBytes = SMEM_TOT ? (size_t)TL * TR * BX * BY * sizeof(float) : 0;
+    static constexpr size_t kDyn =
+        kTotBytes + (TABLES ? (size_t)2 * kSepGroup * SepTable<BX * TL, BY * TR>::kPerPoint * sizeof(float2) : 0);
 
     template <bool SFU, bool EXTRA>
     static cudaError_t launch(int ctas, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_points, int width,
                               int height, int tiles_x, long long units, float *out, float4 *slots, int *counters,
                               bool vec, int *status, uint64_t timeout_ns, int drop_tile, const PhaseRef &ref)
     {
-        if constexpr (SMEM_TOT) {   // with the static tiles the totals exceed the default 48 KB
+        if constexpr (kDyn > 0) {   // with the static tiles the totals or tables exceed the default 48 KB
             static PerDeviceOnce configured;
             const cudaError_t e = configured.run([] {
-                return cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, SFU, EXTRA, SMEM_TOT>,
+                return cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, SFU, EXTRA, SMEM_TOT, TABLES>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDyn);
             });
             if (e != cudaSuccess) return e;
         }
-        direct_stream_kernel<TL, TR, BX, BY, SFU, EXTRA, SMEM_TOT><<<ctas, BX * BY, kDyn, s>>>(
+        direct_stream_kernel<TL, TR, BX, BY, SFU, EXTRA, SMEM_TOT, TABLES><<<ctas, BX * BY, kDyn, s>>>(
             geo, aux, n_points, width, height, tiles_x, units, out, slots, counters, vec, status, timeout_ns,
             drop_tile, ref);
         return cudaGetLastError();
@@ -357,13 +361,14 @@ struct StreamCfg {
 
     static int resident(bool sfu)
     {
-        if constexpr (SMEM_TOT) {   // the limit the launch will set (occupancy counts it)
+        if constexpr (kDyn > 0) {   // the limit the launch will set (occupancy counts it)
             static PerDeviceOnce configured;
             configured.run([] {
-                cudaError_t e = cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, true, false, SMEM_TOT>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDyn);
+                cudaError_t e =
+                    cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, true, false, SMEM_TOT, TABLES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDyn);
                 if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, false, false, SMEM_TOT>,
+                    e = cudaFuncSetAttribute(direct_stream_kernel<TL, TR, BX, BY, false, false, SMEM_TOT, TABLES>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDyn);
                 return e;
             });
@@ -371,9 +376,9 @@ struct StreamCfg {
         int n = 0;
         const cudaError_t e =
             sfu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                      &n, direct_stream_kernel<TL, TR, BX, BY, true, false, SMEM_TOT>, BX * BY, kDyn)
+                      &n, direct_stream_kernel<TL, TR, BX, BY, true, false, SMEM_TOT, TABLES>, BX * BY, kDyn)
                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                      &n, direct_stream_kernel<TL, TR, BX, BY, false, false, SMEM_TOT>, BX * BY, kDyn);
+                      &n, direct_stream_kernel<TL, TR, BX, BY, false, false, SMEM_TOT, TABLES>, BX * BY, kDyn);
         if (e != cudaSuccess || n < 1) {
             cudaGetLastError();
             return 1;
@@ -392,6 +397,10 @@ using StreamWide = StreamCfg<kTL, kTR, kBX, kBY, false>;
 constexpr int kSqTL = 8, kSqTR = 8, kSqBX = 16, kSqBY = 8, kSqWideBX = 32, kSqWideBY = 4;
 using StreamSquare = StreamCfg<kSqTL, kSqTR, kSqBX, kSqBY, true>;
 using StreamSquareWide = StreamCfg<kSqTL, kSqTR, kSqWideBX, kSqWideBY, true>;
+// The 8 x 4-pixel blocks with the tables of the tile (dev::SepTable): the sines and cosines of a point's columns
+// and rows taken once per CTA.
+using StreamTallTab = StreamCfg<kTL, kTR, kTallBX, kTallBY, false, true>;
+using StreamWideTab = StreamCfg<kTL, kTR, kBX, kBY, false, true>;
 
 }  // namespace
 
@@ -399,11 +408,17 @@ DirectShape direct_stream_shape(int variant)
 {
     if (variant == 2) return DirectShape{kSqBX * kSqTL, kSqBY * kSqTR, kSqBX * kSqBY, kSqBX};
     if (variant == 3) return DirectShape{kSqWideBX * kSqTL, kSqWideBY * kSqTR, kSqWideBX * kSqWideBY, kSqWideBX};
+    if (variant == 4 || variant == 5) {
+        DirectShape sh = direct_shape(variant == 4);
+        sh.tables = 1;
+        return sh;
+    }
     return direct_shape(variant == 1);
 }
 
 int direct_stream_per_sm(bool sfu, const DirectShape &sh)
 {
+    if (sh.tables) return sh.bx == kTallBX ? StreamTallTab::resident(sfu) : StreamWideTab::resident(sfu);
     if (sh.threads == kSqBX * kSqBY)
         return sh.bx == kSqBX ? StreamSquare::resident(sfu) : StreamSquareWide::resident(sfu);
     return sh.bx == kTallBX ? StreamTall::resident(sfu) : StreamWide::resident(sfu);
@@ -425,6 +440,8 @@ cudaError_t launch_direct_stream(bool sfu, const DirectShape &sh, int ctas, cons
     const bool extra = ref.any();
 #define CGH_STREAM_ARGS sfu, extra, ctas, s, geo, aux, n_points, width, height, tiles_x, units, out, sl, counters, vec, \
                         status, timeout_ns, drop_tile, ref
+    if (sh.tables)
+        return sh.bx == kTallBX ? StreamTallTab::dispatch(CGH_STREAM_ARGS) : StreamWideTab::dispatch(CGH_STREAM_ARGS);
     if (sh.threads == kSqBX * kSqBY)
         return sh.bx == kSqBX ? StreamSquare::dispatch(CGH_STREAM_ARGS) : StreamSquareWide::dispatch(CGH_STREAM_ARGS);
     if (sh.bx == kTallBX) return StreamTall::dispatch(CGH_STREAM_ARGS);

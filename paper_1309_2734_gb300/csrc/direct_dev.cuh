@@ -59,6 +59,8 @@ namespace dev {
 // so that 1.5 K1 is a float too (0x40c90fdc and 0x4116cbe5)
 constexpr float kK1 = 6.28318595886230469f;
 constexpr float kK0 = 9.42477893829345703f;   // exactly 1.5 * kK1
+// a half turn (so (f - 1.5) K1 is the angle itself in [-pi, pi)) and rounding of the 23-bit truncation
+constexpr uint32_t kHalfBias = (1u << 31) + 256u;
 // cos(2 pi t) of a signed fixed-point turn t in [-1/2, 1/2) (2^-32 turn) by the polynomial of cospoly.h.
 __device__ __forceinline__ float cos_turn_poly(uint32_t g)
 {
@@ -112,8 +114,6 @@ __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int
     const uint32_t dy = (uint32_t)(n0 - q.y);
     const uint32_t x2 = dx * dx, x2n = x2 + 2u * dx + 1u;   // dx^2, (dx + 1)^2: below 2^32, exact
     const uint32_t y2 = dy * dy, y2n = y2 + 2u * dy + 1u;
-    // a half turn (so (f - 1.5) K1 is the angle itself in [-pi, pi)), rounding of the 23-bit truncation, the flip
-    constexpr uint32_t kHalfBias = (1u << 31) + 256u;
     uint32_t a = chi * x2 + __umulhi(clo, x2) + kHalfBias + flip;
     uint32_t da = chi * x2n + __umulhi(clo, x2n) - (a - kHalfBias - flip);
     uint32_t b = chi * y2 + __umulhi(clo, y2) + kHalfBias + flip;
@@ -160,6 +160,98 @@ __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int
     }
 }
 
+// Tables of the tile (TABLES): the sine and cosine of a column's turn depend on the point and the column only, a
+// row's on the point and the row only, so per group of points the CTA takes them once for its whole pixel tile --
+// TILE_W column pairs and TILE_H row pairs (the amplitude folded into the rows) per point, spread over the threads
+// -- and every thread reads its 8 columns and TR rows from shared memory: 2 FFMAs a term, and per point and
+// thread (TILE_W + TILE_H) / threads sine-cosine pairs instead of TL + TR.  Each group of 8 column pairs is
+// padded to 10 (80 bytes), so the 8 threads of a quarter warp that read their 16-byte column quads fall on
+// distinct banks.
+template <int TILE_W, int TILE_H>
+struct SepTable {
+    static_assert(TILE_W % 8 == 0, "whole groups of 8 columns");
+    static constexpr int kColStride = TILE_W / 8 * 10;   // float2s of one point's column pairs
+    static constexpr int kPerPoint = kColStride + TILE_H;
+    __device__ static int col(int k) { return (k >> 3) * 10 + (k & 7); }
+};
+// points per table fill (double buffered: one CTA barrier per group; 8 measured 2.69 ms, 32 3.04 -- two CTAs no
+// longer fit an SM -- against 2.51 at 16, 1920x1080, 10^4 points)
+constexpr int kSepGroup = 16;
+
+template <int TILE_W, int TILE_H, bool EXTRA, bool ACC>
+__device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa, int p0, int np, int tile_m0,
+                                                int tile_n0, const PhaseRef &ref, float2 *tab, int tid,
+                                                int nthreads)
+{
+    using S = SepTable<TILE_W, TILE_H>;
+    constexpr int E = TILE_W + TILE_H;
+#pragma unroll 1
+    for (int e = tid; e < np * E; e += nthreads) {
+        const int g = e / E, k = e - g * E;
+        const int p = p0 + g;
+        const int4 q = sg[p];
+        const uint2 w = sa[p];
+        const bool is_col = k < TILE_W;
+        const int coord = is_col ? tile_m0 + k : tile_n0 + (k - TILE_W);
+        const uint32_t d = (uint32_t)(coord - (is_col ? q.x : q.y));
+        const uint32_t d2 = d * d;   // below 2^31: exact
+        uint32_t t = (uint32_t)q.z * d2 + __umulhi((uint32_t)q.w, d2);
+        if constexpr (EXTRA)   // piston (aux.x) and the reference phase's column part; its row part
+            t += is_col ? w.x + ref_turn(ref, coord, 0) : ref_turn(ref, 0, coord) - ref.phi0;
+        float sn, cs;
+        if constexpr (ACC) {
+            cs = cos_turn_poly(t);
+            sn = cos_turn_poly(t - (1u << 30));   // cos 2 pi (t - 1/4)
+        } else {
+            t += kHalfBias + ((uint32_t)(p & 1) << 31);   // the flip of every other point (point_terms_sep)
+            const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));
+            __sincosf(fmaf(f, kK1, -kK0), &sn, &cs);
+        }
+        float2 *dst = tab + g * S::kPerPoint;
+        if (is_col) {
+            dst[S::col(k)] = make_float2(cs, sn);
+        } else {
+            const float a = __uint_as_float(w.y);
+            dst[S::kColStride + (k - TILE_W)] = make_float2(a * cs, a * sn);
+        }
+    }
+}
+
+// One point's tables for a thread: its 8 column pairs (from column cx) and TR row pairs (from row ry) as float4s.
+template <int TR, int TILE_W, int TILE_H>
+struct SepQuads {
+    float4 c[4], r[TR / 2];
+    __device__ __forceinline__ void load(const float2 *tab, int cx, int ry)
+    {
+        using S = SepTable<TILE_W, TILE_H>;
+        const float4 *c4 = reinterpret_cast<const float4 *>(tab + (cx >> 3) * 10);
+        const float4 *r4 = reinterpret_cast<const float4 *>(tab + S::kColStride + ry);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j] = c4[j];
+#pragma unroll
+        for (int h = 0; h < TR / 2; ++h) r[h] = r4[h];
+    }
+};
+
+// One point's terms from its quads: part[r][i] += cos a_i (A cos b_r) - sin a_i (A sin b_r).
+template <int TR, int TILE_W, int TILE_H>
+__device__ __forceinline__ void point_terms_table(const SepQuads<TR, TILE_W, TILE_H> &q, float (&part)[TR][8])
+{
+    static_assert(TR % 2 == 0, "row pairs in 16-byte quads");
+#pragma unroll
+    for (int h = 0; h < TR / 2; ++h) {
+        const float4 v = q.r[h];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 cs = q.c[j];   // (cos, sin) of columns 2 j and 2 j + 1
+            part[2 * h][2 * j] = fmaf(-cs.y, v.y, fmaf(cs.x, v.x, part[2 * h][2 * j]));
+            part[2 * h][2 * j + 1] = fmaf(-cs.w, v.y, fmaf(cs.z, v.x, part[2 * h][2 * j + 1]));
+            part[2 * h + 1][2 * j] = fmaf(-cs.y, v.w, fmaf(cs.x, v.z, part[2 * h + 1][2 * j]));
+            part[2 * h + 1][2 * j + 1] = fmaf(-cs.w, v.w, fmaf(cs.z, v.z, part[2 * h + 1][2 * j + 1]));
+        }
+    }
+}
+
 // The points of the unit are those of tiles [t_begin, t_end), less the first p_first points of the first tile
 // and the points from p_last_end on of the last one.  Sink: PlainStore writes the totals to dst; any other sink
 // is called as sink(tot) with the thread's TR x TL totals of plane 0 (the amplitude hologram only).
@@ -194,14 +286,15 @@ struct GroupSync {
 };
 
 template <int TL, int TR, int BX, int BY, bool SFU, int PLANES = 1, bool EXTRA = false, bool SMEM_TOT = false,
-          class Sink = PlainStore, class Sync = CtaSync, int T = kPointTile>
+          class Sink = PlainStore, class Sync = CtaSync, int T = kPointTile, bool TABLES = false>
 __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const uint2 *__restrict__ aux,
                                             int t_begin, int t_end, int tile_m0, int tile_n0, int width,
                                             int height, float *__restrict__ dst, bool vec, int4 (*s_geo)[T],
                                             uint2 (*s_aux)[T], uint64_t *s_bar, uint32_t &kg, int *status,
                                             unsigned long long timeout_ns, int drop = -1, long long im_offset = 0,
                                             const PhaseRef &ref = PhaseRef(), float *s_tot = nullptr,
-                                            int p_first = 0, int p_last_end = T, Sink sink = Sink())
+                                            int p_first = 0, int p_last_end = T, Sink sink = Sink(),
+                                            float2 *s_tab = nullptr)
 {
     static_assert(kPointTile % T == 0 && T % 16 == 0, "point tiles divide the padding");
     constexpr uint32_t kTileBytes = T * (sizeof(int4) + sizeof(uint2));
@@ -268,7 +361,28 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         const uint2 *sa = s_aux[st];
         const int p_lo = k == 0 ? p_first : 0;
         const int p_hi = k == nt - 1 ? p_last_end : T;
-        {
+        if constexpr (TABLES) {
+            static_assert(PLANES == 1 && TL == 8, "tables serve the amplitude hologram's 8-column blocks");
+            constexpr int TW = BX * TL, TH = BY * TR;
+            using ST = SepTable<TW, TH>;
+            int gi = 0;
+#pragma unroll 1
+            for (int p0 = p_lo; p0 < p_hi; p0 += kSepGroup, ++gi) {
+                const int np = min(kSepGroup, p_hi - p0);
+                float2 *buf = s_tab + (gi & 1) * (kSepGroup * ST::kPerPoint);
+                fill_sep_tables<TW, TH, EXTRA, !SFU>(sg, sa, p0, np, tile_m0, tile_n0, ref, buf, tid, BX * BY);
+                Sync::sync();   // the group's tables are written (the other buffer is no longer read)
+                // unrolled by four, so the compiler overlaps the next points' shared-memory loads with these
+                // FFMAs (measured at 1920x1080, 10^4 points: 2.69 ms not unrolled, 2.55 by two, 2.51 by four; a
+                // manual one-point look-ahead ran out of registers, 3.59)
+#pragma unroll 4
+                for (int g = 0; g < np; ++g) {
+                    SepQuads<TR, TW, TH> cur;
+                    cur.load(buf + g * ST::kPerPoint, lx * TL, ly * TR);
+                    point_terms_table<TR, TW, TH>(cur, part[0]);
+                }
+            }
+        } else {
             static_assert(PLANES == 1 || SFU, "the complex wave takes the hardware sine and cosine");
 #pragma unroll 1
             for (int p = p_lo; p < p_hi; ++p)   // p has the parity of the point's index (tiles start even)

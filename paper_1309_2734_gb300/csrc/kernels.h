@@ -68,6 +68,7 @@ struct DirectShape {
     int threads;          // threads per CTA
     int bx;               // threads per CTA row: 32 (the wide shape) or 16 (the tall and short shapes)
     int per_sm = 2;       // CTAs resident per SM
+    int tables = 0;       // 1: the balanced layout's kernel with per-CTA tables of the column and row sines
 };
 // The CTA shapes of the direct kernels (256 threads, 8 columns of pixels per
 // thread): wide = 32 x 8 threads, tall = 16 x 16 threads.

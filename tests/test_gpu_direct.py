@@ -290,12 +290,13 @@ def test_balanced_split_cta_counts_and_determinism(w, h, n):
     assert oracle.nrms(outs[0], chunked) < 1e-6
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("w,h,n", [(300, 70, 2000), (515, 129, 301)])
 def test_balanced_layout_every_thread_block(shape, w, h, n):
     """CGH_OPT_DIRECT_SHAPE: 8 x 4 pixels a thread in 32 x 8 or 16 x 16 threads (totals in registers), 8 x 8 in
-    16 x 8 or 32 x 4 (totals in shared memory); ragged in both directions, against the oracle, and within
-    single-precision rounding of one another (the same terms in the same point order)."""
+    16 x 8 or 32 x 4 (totals in shared memory), 8 x 4 in 16 x 16 or 32 x 8 with the CTA's tables of the column and
+    row sines; ragged in both directions, against the oracle, and within single-precision rounding of one another
+    (the same terms in the same point order)."""
     c = workloads.random_cloud(4600 + n, w, h, n)
     xyz, amp = _dev(c)
     with Hologram(w, h, c.pitch_m, c.lambda_m, form="direct_sfu") as hg:
