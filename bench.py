@@ -40,35 +40,20 @@ FMA_PER_SM_PER_CLK = 128        # FP32 FMA-pipe operations per SM per clock
 
 
 def direct_ops(form, width, height, n_points):
-    """The direct kernel's work per launch in the operations of the pipe that bounds it, as the kernel does it:
-    8 x 8 pixels a thread on the 128 x 64 tile (256 x 32 where that pads less), and per point and 8 x 8 block the
-    sine and cosine of 8 column and 8 row turns, then two FFMAs a term.  SFU form: 16 x 2 MUFU operations per
-    point and block (0.5 per evaluation).  Accurate form: FMA-pipe operations -- 16 x 2 polynomials of 8
-    (a multiply by 2^-32, the square, six FFMAs), 16 amplitude products, 128 FFMAs: 400 per point and block.
-    Returns (operations, pipe, peak operations per SM per clock, operations per evaluation)."""
+    """The direct kernel's work per launch in FMA-pipe operations, as the kernel does it: a CTA covers a 128 x 64
+    tile (256 x 32 where that pads a fifth fewer pixels); per point it takes the sine and cosine of the tile's
+    columns and rows once (the SFU form: one FFMA and the sine's range multiply per entry, and the amplitude's two
+    multiplies per row entry; the accurate form: two polynomials of 8 FMA-pipe operations per entry), then every
+    pixel costs two FFMAs.  Returns (operations, pipe, peak operations per SM per clock, operations per
+    evaluation); the MUFU operations of the SFU form (two per entry, 0.05 per evaluation) bound nothing."""
     def padded(tw, th):
         return -(-width // tw) * tw * (-(-height // th) * th)
-    px = padded(256, 32) if padded(256, 32) < padded(128, 64) else padded(128, 64)
-    blocks = px // 64
-    if form == "direct_sfu":
-        per = 32
-        return n_points * blocks * per, "MUFU", MUFU_PER_SM_PER_CLK, per * blocks / (width * height)
-    per = 400
-    return n_points * blocks * per, "FMA", FMA_PER_SM_PER_CLK, per * blocks / (width * height)
-
-# DRAM bytes per launch of the dominant kernel from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
-# taken on; a changed source reports null until it is profiled again.
-NCU_TRAFFIC = [
-    # profiles/direct_sfu-1920x1080-n10000.md (api.cu holds the launch's CTA count)
-    {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
-     "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh", "api.cu"],
-     "sha1": "8989dc504390e9a6bbad37b1cb76fdabee3cf7b6", "bytes_per_launch": 5392384},
-    # profiles/gemm_f16-1920x1080-n50000.md: 600.731 MB read + 3.053 MB written per launch
-    {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
-     "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
-     "sha1": "1b3da24ffb355250d6467758d091b4a7b91d7b3a", "bytes_per_launch": 603784192},
-]
+    tw, th = (256, 32) if padded(256, 32) * 6 < padded(128, 64) * 5 else (128, 64)
+    tiles = padded(tw, th) // (tw * th)
+    per_col, per_row = (2, 4) if form == "direct_sfu" else (16, 18)
+    per_point_tile = 2 * tw * th + tw * per_col + th * per_row
+    ops = n_points * tiles * per_point_tile
+    return ops, "FMA", FMA_PER_SM_PER_CLK, ops / (n_points * width * height)
 
 
 def ncu_traffic(kernel, form, workload):
@@ -695,7 +680,7 @@ def run_ours(args):
         roof = {"bound": "tensor", "unit": "TFLOP/s", "gemm_k": 2 * k_units,
                 "peak_basis": "measured dense bf16 burst (fp16 nominal rate is the same)"}
     else:
-        # the pipe of the implemented evaluation: MUFU (SFU form) or FMA (accurate form), see direct_ops
+        # the FMA pipe of the implemented evaluation, see direct_ops
         dom = args.form
         src = "direct.cu"
         dom_launches, dom_ms = prof.get(dom, (0, 0.0))
@@ -705,7 +690,8 @@ def run_ours(args):
         roof = {"bound": "alu", "unit": f"G {pipe} op/s",
                 "peak_basis": f"{per_clk} {pipe} op/clk/SM x {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured peaks); {per_eval:.4f} {pipe} op per evaluation "
-                              "(8 x 8 pixels a thread: the sine and cosine of 8 column and 8 row turns per point)"}
+                              "(two FFMAs a pixel and point, and per point the sines and cosines of the CTA's "
+                              "tile columns and rows)"}
         if pipe == "MUFU":
             # the same pipe measured in this run: independent hardware sines on every SM (cgh_measure_mufu)
             from paper_1309_2734_gb300 import _lib
