@@ -56,6 +56,21 @@ def direct_ops(form, width, height, n_points):
     return ops, "FMA", FMA_PER_SM_PER_CLK, ops / (n_points * width * height)
 
 
+# DRAM bytes per launch of the dominant kernel from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the SHA-1 of the kernel's sources they were
+# taken on; a changed source reports null until it is profiled again.
+NCU_TRAFFIC = [
+    # profiles/direct_sfu-1920x1080-n10000.md (api.cu holds the launch's CTA count)
+    {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
+     "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh", "api.cu"],
+     "sha1": "", "bytes_per_launch": 0},
+    # profiles/gemm_f16-1920x1080-n50000.md: 600.731 MB read + 3.053 MB written per launch
+    {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
+     "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
+     "sha1": "1b3da24ffb355250d6467758d091b4a7b91d7b3a", "bytes_per_launch": 603784192},
+]
+
+
 def ncu_traffic(kernel, form, workload):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged since."""
     for t in NCU_TRAFFIC:
