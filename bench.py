@@ -63,7 +63,7 @@ NCU_TRAFFIC = [
     # profiles/direct_sfu-1920x1080-n10000.md (api.cu holds the launch's CTA count)
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
      "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh", "api.cu"],
-     "sha1": "8b10feeadc016b1f147a2cf20434b34057efa9cf", "bytes_per_launch": 329472},
+     "sha1": "b95b8cdc7d7c8b5803ee733822d3eb532d4051c3", "bytes_per_launch": 333568},
     # profiles/gemm_f16-1920x1080-n50000.md: 600.731 MB read + 3.053 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
      "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],

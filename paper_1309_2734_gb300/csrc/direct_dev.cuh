@@ -185,9 +185,7 @@ __device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa,
 {
     using S = SepTable<TILE_W, TILE_H>;
     constexpr int E = TILE_W + TILE_H;
-#pragma unroll 1
-    for (int e = tid; e < np * E; e += nthreads) {
-        const int g = e / E, k = e - g * E;
+    auto entry = [&](int g, int k) {
         const int p = p0 + g;
         const int4 q = sg[p];
         const uint2 w = sa[p];
@@ -213,6 +211,24 @@ __device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa,
         } else {
             const float a = __uint_as_float(w.y);
             dst[S::kColStride + (k - TILE_W)] = make_float2(a * cs, a * sn);
+        }
+    };
+    if constexpr (ACC) {   // the polynomials need the registers the SFU form's loop below keeps its indices in
+#pragma unroll 1
+        for (int e = tid; e < np * E; e += nthreads) entry(e / E, e - (e / E) * E);
+    } else {
+        // entry e = g E + k, e = tid, tid + nthreads, ...: (g, k) advanced without a division
+        int g = tid / E, k = tid - (tid / E) * E;
+        const int step_g = nthreads / E, step_k = nthreads - (nthreads / E) * E;
+#pragma unroll 1
+        for (int e = tid; e < np * E; e += nthreads) {
+            entry(g, k);
+            g += step_g;
+            k += step_k;
+            if (k >= E) {
+                k -= E;
+                ++g;
+            }
         }
     }
 }
