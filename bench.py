@@ -44,7 +44,7 @@ def direct_ops(form, width, height, n_points):
     tile (256 x 32 where that pads a fifth fewer pixels); per point it takes the sine and cosine of the tile's
     columns and rows once (the SFU form: one FFMA and the sine's range multiply per entry, and the amplitude's two
     multiplies per row entry; the accurate form: two polynomials of 8 FMA-pipe operations per entry), then every
-    pixel costs two FFMAs.  Returns (operations, pipe, peak operations per SM per clock, operations per
+    pixel costs two FMAs (one packed two-lane FMA per pair of columns).  Returns (operations, pipe, peak operations per SM per clock, operations per
     evaluation); the MUFU operations of the SFU form (two per entry, 0.05 per evaluation) bound nothing."""
     def padded(tw, th):
         return -(-width // tw) * tw * (-(-height // th) * th)
@@ -63,7 +63,7 @@ NCU_TRAFFIC = [
     # profiles/direct_sfu-1920x1080-n10000.md (api.cu holds the launch's CTA count)
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
      "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh", "api.cu"],
-     "sha1": "b95b8cdc7d7c8b5803ee733822d3eb532d4051c3", "bytes_per_launch": 333568},
+     "sha1": "3beaa167f837dbeda371ebc435ca3558bfdf6bb8", "bytes_per_launch": 495360},
     # profiles/gemm_f16-1920x1080-n50000.md: 600.731 MB read + 3.053 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
      "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
@@ -705,7 +705,7 @@ def run_ours(args):
         roof = {"bound": "alu", "unit": f"G {pipe} op/s",
                 "peak_basis": f"{per_clk} {pipe} op/clk/SM x {props.multi_processor_count} SMs x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured peaks); {per_eval:.4f} {pipe} op per evaluation "
-                              "(two FFMAs a pixel and point, and per point the sines and cosines of the CTA's "
+                              "(two FMAs a pixel and point, and per point the sines and cosines of the CTA's "
                               "tile columns and rows)"}
         if pipe == "MUFU":
             # the same pipe measured in this run: independent hardware sines on every SM (cgh_measure_mufu)

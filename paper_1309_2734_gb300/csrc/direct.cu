@@ -398,8 +398,10 @@ constexpr int kSqTL = 8, kSqTR = 8, kSqBX = 16, kSqBY = 8, kSqWideBX = 32, kSqWi
 using StreamSquare = StreamCfg<kSqTL, kSqTR, kSqBX, kSqBY, true>;
 using StreamSquareWide = StreamCfg<kSqTL, kSqTR, kSqWideBX, kSqWideBY, true>;
 // The 8 x 4-pixel blocks with the tables of the tile (dev::SepTable): the sines and cosines of a point's columns
-// and rows taken once per CTA.
-using StreamTallTab = StreamCfg<kTL, kTR, kTallBX, kTallBY, false, true>;
+// and rows taken once per CTA.  The tall block keeps its totals in shared memory, the registers going to the
+// unrolled point loop (1920x1080, 10^4 points: 2.27 against 2.30 ms); the wide one measured the other way (2.94
+// in registers, 3.71 in shared memory).
+using StreamTallTab = StreamCfg<kTL, kTR, kTallBX, kTallBY, true, true>;
 using StreamWideTab = StreamCfg<kTL, kTR, kBX, kBY, false, true>;
 
 }  // namespace

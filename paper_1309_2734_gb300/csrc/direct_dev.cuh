@@ -163,16 +163,18 @@ __device__ __forceinline__ void point_terms_sep(const int4 q, const uint2 w, int
 // Tables of the tile (TABLES): the sine and cosine of a column's turn depend on the point and the column only, a
 // row's on the point and the row only, so per group of points the CTA takes them once for its whole pixel tile --
 // TILE_W column pairs and TILE_H row pairs (the amplitude folded into the rows) per point, spread over the threads
-// -- and every thread reads its 8 columns and TR rows from shared memory: 2 FFMAs a term, and per point and
-// thread (TILE_W + TILE_H) / threads sine-cosine pairs instead of TL + TR.  Each group of 8 column pairs is
-// padded to 10 (80 bytes), so the 8 threads of a quarter warp that read their 16-byte column quads fall on
-// distinct banks.
+// -- and every thread reads its 8 columns and TR rows from shared memory: 2 FMAs a term, and per point and
+// thread (TILE_W + TILE_H) / threads sine-cosine pairs instead of TL + TR.  A group of 8 columns is stored as
+// four 16-byte quads (cos c, cos c+1, sin c, sin c+1), the operands of packed FMAs over two columns, and padded
+// to five quads (80 bytes), so the 8 threads of a quarter warp that read their quads fall on distinct banks.  A
+// row is stored as (A cos b, -A sin b).
 template <int TILE_W, int TILE_H>
 struct SepTable {
     static_assert(TILE_W % 8 == 0, "whole groups of 8 columns");
-    static constexpr int kColStride = TILE_W / 8 * 10;   // float2s of one point's column pairs
+    static constexpr int kColStride = TILE_W / 8 * 10;   // float2s of one point's columns
     static constexpr int kPerPoint = kColStride + TILE_H;
-    __device__ static int col(int k) { return (k >> 3) * 10 + (k & 7); }
+    // float index of column k's cosine (its sine two floats on)
+    __device__ static int col_cos(int k) { return (k >> 3) * 20 + ((k & 7) >> 1) * 4 + (k & 1); }
 };
 // points per table fill (double buffered: one CTA barrier per group; 8 measured 2.69 ms, 32 3.04 -- two CTAs no
 // longer fit an SM -- against 2.51 at 16, 1920x1080, 10^4 points)
@@ -207,10 +209,12 @@ __device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa,
         }
         float2 *dst = tab + g * S::kPerPoint;
         if (is_col) {
-            dst[S::col(k)] = make_float2(cs, sn);
+            float *c = reinterpret_cast<float *>(dst) + S::col_cos(k);
+            c[0] = cs;
+            c[2] = sn;
         } else {
             const float a = __uint_as_float(w.y);
-            dst[S::kColStride + (k - TILE_W)] = make_float2(a * cs, a * sn);
+            dst[S::kColStride + (k - TILE_W)] = make_float2(a * cs, -(a * sn));
         }
     };
     if constexpr (ACC) {   // the polynomials need the registers the SFU form's loop below keeps its indices in
@@ -249,9 +253,11 @@ struct SepQuads {
     }
 };
 
-// One point's terms from its quads: part[r][i] += cos a_i (A cos b_r) - sin a_i (A sin b_r).
+// One point's terms from its quads, two columns a packed FMA (the two lanes' FMAs in one instruction):
+// acc[r][j] += (cos a_2j, cos a_2j+1) (A cos b_r) + (sin a_2j, sin a_2j+1) (-A sin b_r), the same two roundings per
+// term as two scalar FMAs.
 template <int TR, int TILE_W, int TILE_H>
-__device__ __forceinline__ void point_terms_table(const SepQuads<TR, TILE_W, TILE_H> &q, float (&part)[TR][8])
+__device__ __forceinline__ void point_terms_table(const SepQuads<TR, TILE_W, TILE_H> &q, float2 (&acc)[TR][4])
 {
     static_assert(TR % 2 == 0, "row pairs in 16-byte quads");
 #pragma unroll
@@ -259,11 +265,10 @@ __device__ __forceinline__ void point_terms_table(const SepQuads<TR, TILE_W, TIL
         const float4 v = q.r[h];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float4 cs = q.c[j];   // (cos, sin) of columns 2 j and 2 j + 1
-            part[2 * h][2 * j] = fmaf(-cs.y, v.y, fmaf(cs.x, v.x, part[2 * h][2 * j]));
-            part[2 * h][2 * j + 1] = fmaf(-cs.w, v.y, fmaf(cs.z, v.x, part[2 * h][2 * j + 1]));
-            part[2 * h + 1][2 * j] = fmaf(-cs.y, v.w, fmaf(cs.x, v.z, part[2 * h + 1][2 * j]));
-            part[2 * h + 1][2 * j + 1] = fmaf(-cs.w, v.w, fmaf(cs.z, v.z, part[2 * h + 1][2 * j + 1]));
+            const float2 c = make_float2(q.c[j].x, q.c[j].y), s = make_float2(q.c[j].z, q.c[j].w);
+            acc[2 * h][j] = __ffma2_rn(s, make_float2(v.y, v.y), __ffma2_rn(c, make_float2(v.x, v.x), acc[2 * h][j]));
+            acc[2 * h + 1][j] =
+                __ffma2_rn(s, make_float2(v.w, v.w), __ffma2_rn(c, make_float2(v.z, v.z), acc[2 * h + 1][j]));
         }
     }
 }
@@ -381,6 +386,11 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
             static_assert(PLANES == 1 && TL == 8, "tables serve the amplitude hologram's 8-column blocks");
             constexpr int TW = BX * TL, TH = BY * TR;
             using ST = SepTable<TW, TH>;
+            float2 acc[TR][TL / 2];   // columns 2 j and 2 j + 1
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int j = 0; j < TL / 2; ++j) acc[r][j] = make_float2(0.0f, 0.0f);
             int gi = 0;
 #pragma unroll 1
             for (int p0 = p_lo; p0 < p_hi; p0 += kSepGroup, ++gi) {
@@ -389,15 +399,23 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
                 fill_sep_tables<TW, TH, EXTRA, !SFU>(sg, sa, p0, np, tile_m0, tile_n0, ref, buf, tid, BX * BY);
                 Sync::sync();   // the group's tables are written (the other buffer is no longer read)
                 // unrolled by four, so the compiler overlaps the next points' shared-memory loads with these
-                // FFMAs (measured at 1920x1080, 10^4 points: 2.69 ms not unrolled, 2.55 by two, 2.51 by four; a
-                // manual one-point look-ahead ran out of registers, 3.59)
+                // FMAs (measured at 1920x1080, 10^4 points with scalar FFMAs: 2.69 ms not unrolled, 2.55 by two,
+                // 2.51 by four, a manual one-point look-ahead ran out of registers, 3.59; with the packed FMAs
+                // 2.32 by two, 2.30 by four)
 #pragma unroll 4
                 for (int g = 0; g < np; ++g) {
                     SepQuads<TR, TW, TH> cur;
                     cur.load(buf + g * ST::kPerPoint, lx * TL, ly * TR);
-                    point_terms_table<TR, TW, TH>(cur, part[0]);
+                    point_terms_table<TR, TW, TH>(cur, acc);
                 }
             }
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int j = 0; j < TL / 2; ++j) {
+                    part[0][r][2 * j] = acc[r][j].x;
+                    part[0][r][2 * j + 1] = acc[r][j].y;
+                }
         } else {
             static_assert(PLANES == 1 || SFU, "the complex wave takes the hardware sine and cosine");
 #pragma unroll 1

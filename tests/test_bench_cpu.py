@@ -10,7 +10,7 @@ import bench  # noqa: E402
 
 
 def test_direct_ops_counts():
-    # 1920x1080 on 128 x 64 tiles: 15 x 17 tiles; per point and tile two FFMAs a pixel plus the table entries
+    # 1920x1080 on 128 x 64 tiles: 15 x 17 tiles; per point and tile two FMAs a pixel plus the table entries
     ops, pipe, per_clk, per_eval = bench.direct_ops("direct_sfu", 1920, 1080, 10000)
     assert pipe == "FMA" and per_clk == 128
     assert ops == 10000 * 15 * 17 * (2 * 128 * 64 + 128 * 2 + 64 * 4)
