@@ -180,25 +180,30 @@ struct SepTable {
 // longer fit an SM -- against 2.51 at 16, 1920x1080, 10^4 points)
 constexpr int kSepGroup = 16;
 
-template <int TILE_W, int TILE_H, bool EXTRA, bool ACC>
+// The tables of np <= kSepGroup points p0, p0 + 1, ... for a tile: NTHREADS / kSepGroup threads a point (a half
+// warp), each taking its point's turn constants once and then its share of the columns and rows.  A half warp's
+// column stores cover groups q and q + 4 of 8 columns, whose cosines (and sines) fall on disjoint banks.
+template <int TILE_W, int TILE_H, int NTHREADS, bool EXTRA, bool ACC>
 __device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa, int p0, int np, int tile_m0,
-                                                int tile_n0, const PhaseRef &ref, float2 *tab, int tid,
-                                                int nthreads)
+                                                int tile_n0, const PhaseRef &ref, float2 *tab, int tid)
 {
     using S = SepTable<TILE_W, TILE_H>;
-    constexpr int E = TILE_W + TILE_H;
-    auto entry = [&](int g, int k) {
-        const int p = p0 + g;
-        const int4 q = sg[p];
-        const uint2 w = sa[p];
-        const bool is_col = k < TILE_W;
-        const int coord = is_col ? tile_m0 + k : tile_n0 + (k - TILE_W);
-        const uint32_t d = (uint32_t)(coord - (is_col ? q.x : q.y));
-        const uint32_t d2 = d * d;   // below 2^31: exact
-        uint32_t t = (uint32_t)q.z * d2 + __umulhi((uint32_t)q.w, d2);
-        if constexpr (EXTRA)   // piston (aux.x) and the reference phase's column part; its row part
-            t += is_col ? w.x + ref_turn(ref, coord, 0) : ref_turn(ref, 0, coord) - ref.phi0;
-        float sn, cs;
+    constexpr int TPP = NTHREADS / kSepGroup;   // threads a point
+    static_assert(NTHREADS % kSepGroup == 0 && TPP == 16, "a half warp a point");
+    static_assert(TILE_W % 64 == 0 && TILE_H % TPP == 0, "whole pairs of column groups, whole rows a thread");
+    const int g = tid / TPP, j = tid % TPP;
+    if (g >= np) return;
+    const int p = p0 + g;
+    const int4 q = sg[p];
+    const uint2 w = sa[p];
+    float2 *dst = tab + g * S::kPerPoint;
+    // the point's turn at a column (row) coordinate, exact: C d^2 mod 2^64, top 32 bits (d^2 below 2^31)
+    auto turn = [&](int coord, int center) {
+        const uint32_t d = (uint32_t)(coord - center);
+        const uint32_t d2 = d * d;
+        return (uint32_t)q.z * d2 + __umulhi((uint32_t)q.w, d2);
+    };
+    auto sincos_turn = [&](uint32_t t, float &sn, float &cs) {
         if constexpr (ACC) {
             cs = cos_turn_poly(t);
             sn = cos_turn_poly(t - (1u << 30));   // cos 2 pi (t - 1/4)
@@ -207,33 +212,30 @@ __device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa,
             const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));
             __sincosf(fmaf(f, kK1, -kK0), &sn, &cs);
         }
-        float2 *dst = tab + g * S::kPerPoint;
-        if (is_col) {
-            float *c = reinterpret_cast<float *>(dst) + S::col_cos(k);
-            c[0] = cs;
-            c[2] = sn;
-        } else {
-            const float a = __uint_as_float(w.y);
-            dst[S::kColStride + (k - TILE_W)] = make_float2(a * cs, -(a * sn));
-        }
     };
-    if constexpr (ACC) {   // the polynomials need the registers the SFU form's loop below keeps its indices in
-#pragma unroll 1
-        for (int e = tid; e < np * E; e += nthreads) entry(e / E, e - (e / E) * E);
-    } else {
-        // entry e = g E + k, e = tid, tid + nthreads, ...: (g, k) advanced without a division
-        int g = tid / E, k = tid - (tid / E) * E;
-        const int step_g = nthreads / E, step_k = nthreads - (nthreads / E) * E;
-#pragma unroll 1
-        for (int e = tid; e < np * E; e += nthreads) {
-            entry(g, k);
-            g += step_g;
-            k += step_k;
-            if (k >= E) {
-                k -= E;
-                ++g;
-            }
-        }
+#pragma unroll
+    for (int i = 0; i < TILE_W / TPP; ++i) {
+        const int grp = (i & 3) + 8 * (i >> 2) + (j >= 8 ? 4 : 0);
+        const int k = grp * 8 + (j & 7);
+        const int coord = tile_m0 + k;
+        uint32_t t = turn(coord, q.x);
+        if constexpr (EXTRA) t += w.x + ref_turn(ref, coord, 0);   // piston and the reference phase's column part
+        float sn, cs;
+        sincos_turn(t, sn, cs);
+        float *c = reinterpret_cast<float *>(dst) + S::col_cos(k);
+        c[0] = cs;
+        c[2] = sn;
+    }
+    const float a = __uint_as_float(w.y);
+#pragma unroll
+    for (int i = 0; i < TILE_H / TPP; ++i) {
+        const int k = j + TPP * i;
+        const int coord = tile_n0 + k;
+        uint32_t t = turn(coord, q.y);
+        if constexpr (EXTRA) t += ref_turn(ref, 0, coord) - ref.phi0;   // the reference phase's row part
+        float sn, cs;
+        sincos_turn(t, sn, cs);
+        dst[S::kColStride + k] = make_float2(a * cs, -(a * sn));
     }
 }
 
@@ -396,7 +398,7 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
             for (int p0 = p_lo; p0 < p_hi; p0 += kSepGroup, ++gi) {
                 const int np = min(kSepGroup, p_hi - p0);
                 float2 *buf = s_tab + (gi & 1) * (kSepGroup * ST::kPerPoint);
-                fill_sep_tables<TW, TH, EXTRA, !SFU>(sg, sa, p0, np, tile_m0, tile_n0, ref, buf, tid, BX * BY);
+                fill_sep_tables<TW, TH, BX * BY, EXTRA, !SFU>(sg, sa, p0, np, tile_m0, tile_n0, ref, buf, tid);
                 Sync::sync();   // the group's tables are written (the other buffer is no longer read)
                 // unrolled by four, so the compiler overlaps the next points' shared-memory loads with these
                 // FMAs (measured at 1920x1080, 10^4 points with scalar FFMAs: 2.69 ms not unrolled, 2.55 by two,
