@@ -211,8 +211,9 @@ __global__ void __launch_bounds__(BX *BY, 512 / (BX * BY))
 
 // The complex object wave of one hologram: blockIdx.x = pixel tile, blockIdx.y =
 // point chunk; chunk s writes real and imaginary planes at out + s * slice_stride
-// and out + s * slice_stride + im_offset.
-template <int TL, int TR, int BX, int BY, bool EXTRA>
+// and out + s * slice_stride + im_offset.  TABLES: the sines and cosines of a point's columns and rows taken once
+// per CTA into shared-memory tables (dev::SepTable), after the totals.
+template <int TL, int TR, int BX, int BY, bool EXTRA, bool TABLES>
 __global__ void __launch_bounds__(BX *BY, 2)
     direct_wave_kernel(const int4 *__restrict__ geo, const uint2 *__restrict__ aux, int n_ptiles, int width,
                        int height, int tiles_x, int split, float *__restrict__ out, long long slice_stride,
@@ -222,16 +223,17 @@ __global__ void __launch_bounds__(BX *BY, 2)
     __shared__ alignas(128) int4 s_geo[2][kPointTile];
     __shared__ alignas(128) uint2 s_aux[2][kPointTile];
     __shared__ alignas(8) uint64_t s_bar[2];
-    extern __shared__ float s_tot[];   // the running totals: 2 TR TL floats per thread
+    extern __shared__ __align__(16) float s_tot[];   // the running totals: 2 TR TL floats per thread; the tables
+    float2 *s_tab = reinterpret_cast<float2 *>(s_tot + 2 * TR * TL * BX * BY);
     init_point_barriers<BX, BY>(s_bar);
     const int tile = blockIdx.x;
     const int t_begin = (int)((long long)blockIdx.y * n_ptiles / split);
     const int t_end = (int)((long long)(blockIdx.y + 1) * n_ptiles / split);
     uint32_t kg = 0;
-    direct_unit<TL, TR, BX, BY, true, 2, EXTRA, true>(geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL),
-                                               (tile / tiles_x) * (BY * TR), width, height,
-                                               out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar,
-                                               kg, status, timeout_ns, -1, im_offset, ref, s_tot);
+    direct_unit<TL, TR, BX, BY, true, 2, EXTRA, true, PlainStore, CtaSync, kPointTile, TABLES>(
+        geo, aux, t_begin, t_end, (tile % tiles_x) * (BX * TL), (tile / tiles_x) * (BY * TR), width, height,
+        out + (long long)blockIdx.y * slice_stride, vec, s_geo, s_aux, s_bar, kg, status, timeout_ns, -1, im_offset,
+        ref, s_tot, 0, kPointTile, PlainStore(), s_tab);
 }
 
 // A batch: every CTA walks its list of {job, pixel tile} units over all points of the job.
@@ -504,27 +506,33 @@ namespace cgh {
 namespace {
 constexpr int kWaveTL = 8, kWaveTR = 4;   // two planes of partial sums in registers, the totals in shared memory
 
+// The tall block takes the tables (two CTAs an SM with 8-point groups); the wide one's tables would leave one CTA
+// an SM, so it keeps each thread's own sines and cosines.
 template <int BX, int BY>
 void wave_as(bool extra, dim3 grid, cudaStream_t s, const int4 *geo, const uint2 *aux, int n_ptiles, int width,
              int height, int tiles_x, int split, float *out, long long ss, long long im, bool vec, int *status,
              uint64_t timeout_ns, const PhaseRef &ref)
 {
-    constexpr size_t tot_bytes = (size_t)2 * kWaveTR * kWaveTL * BX * BY * sizeof(float);
+    constexpr bool kTables = BX == kTallBX;
+    constexpr size_t dyn_bytes =
+        (size_t)2 * kWaveTR * kWaveTL * BX * BY * sizeof(float) +
+        (kTables ? (size_t)2 * sep_group<2>() * SepTable<BX * kWaveTL, BY * kWaveTR>::kPerPoint * sizeof(float2)
+                 : 0);
     static PerDeviceOnce configured;   // the running totals exceed the default 48 KB of dynamic shared memory
     const cudaError_t e = configured.run([&] {
-        cudaError_t r = cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes);
+        cudaError_t r = cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true, kTables>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes);
         if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot_bytes);
+            r = cudaFuncSetAttribute(direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false, kTables>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes);
         return r;
     });
     if (e != cudaSuccess) return;
     if (extra)
-        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true><<<grid, BX * BY, tot_bytes, s>>>(
+        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, true, kTables><<<grid, BX * BY, dyn_bytes, s>>>(
             geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, im, vec, status, timeout_ns, ref);
     else
-        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false><<<grid, BX * BY, tot_bytes, s>>>(
+        direct_wave_kernel<kWaveTL, kWaveTR, BX, BY, false, kTables><<<grid, BX * BY, dyn_bytes, s>>>(
             geo, aux, n_ptiles, width, height, tiles_x, split, out, ss, im, vec, status, timeout_ns, ref);
 }
 }  // namespace

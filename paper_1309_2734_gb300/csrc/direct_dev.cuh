@@ -177,20 +177,27 @@ struct SepTable {
     __device__ static int col_cos(int k) { return (k >> 3) * 20 + ((k & 7) >> 1) * 4 + (k & 1); }
 };
 // points per table fill (double buffered: one CTA barrier per group; 8 measured 2.69 ms, 32 3.04 -- two CTAs no
-// longer fit an SM -- against 2.51 at 16, 1920x1080, 10^4 points)
+// longer fit an SM -- against 2.51 at 16, 1920x1080, 10^4 points); the complex wave, whose two planes of totals
+// take twice the shared memory, fills 8
 constexpr int kSepGroup = 16;
+template <int PLANES>
+__host__ __device__ constexpr int sep_group()
+{
+    return PLANES == 2 ? 8 : kSepGroup;
+}
 
-// The tables of np <= kSepGroup points p0, p0 + 1, ... for a tile: NTHREADS / kSepGroup threads a point (a half
+// The tables of np <= GROUP points p0, p0 + 1, ... for a tile: NTHREADS / GROUP threads a point (a half warp or a
 // warp), each taking its point's turn constants once and then its share of the columns and rows.  A half warp's
 // column stores cover groups q and q + 4 of 8 columns, whose cosines (and sines) fall on disjoint banks.
-template <int TILE_W, int TILE_H, int NTHREADS, bool EXTRA, bool ACC>
+template <int TILE_W, int TILE_H, int NTHREADS, int GROUP, bool EXTRA, bool ACC>
 __device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa, int p0, int np, int tile_m0,
                                                 int tile_n0, const PhaseRef &ref, float2 *tab, int tid)
 {
     using S = SepTable<TILE_W, TILE_H>;
-    constexpr int TPP = NTHREADS / kSepGroup;   // threads a point
-    static_assert(NTHREADS % kSepGroup == 0 && TPP == 16, "a half warp a point");
-    static_assert(TILE_W % 64 == 0 && TILE_H % TPP == 0, "whole pairs of column groups, whole rows a thread");
+    constexpr int TPP = NTHREADS / GROUP;   // threads a point
+    static_assert(NTHREADS % GROUP == 0 && (TPP == 16 || TPP == 32), "a half warp or a warp a point");
+    static_assert(TILE_W % TPP == 0 && TILE_W % 64 == 0 && TILE_H % TPP == 0,
+                  "whole pairs of column groups, whole rows a thread");
     const int g = tid / TPP, j = tid % TPP;
     if (g >= np) return;
     const int p = p0 + g;
@@ -215,7 +222,8 @@ __device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa,
     };
 #pragma unroll
     for (int i = 0; i < TILE_W / TPP; ++i) {
-        const int grp = (i & 3) + 8 * (i >> 2) + (j >= 8 ? 4 : 0);
+        const int x = i * (TPP / 8) + (j >> 3);                 // the thread's group of 8 columns, in order ...
+        const int grp = (x & 1) * 4 + ((x >> 1) & 3) + (x & ~7);   // ... taken as 0, 4, 1, 5, 2, 6, 3, 7, 8, 12, ...
         const int k = grp * 8 + (j & 7);
         const int coord = tile_m0 + k;
         uint32_t t = turn(coord, q.x);
@@ -256,10 +264,12 @@ struct SepQuads {
 };
 
 // One point's terms from its quads, two columns a packed FMA (the two lanes' FMAs in one instruction):
-// acc[r][j] += (cos a_2j, cos a_2j+1) (A cos b_r) + (sin a_2j, sin a_2j+1) (-A sin b_r), the same two roundings per
-// term as two scalar FMAs.
-template <int TR, int TILE_W, int TILE_H>
-__device__ __forceinline__ void point_terms_table(const SepQuads<TR, TILE_W, TILE_H> &q, float2 (&acc)[TR][4])
+// acc[0][r][j] += (cos a_2j, cos a_2j+1) (A cos b_r) + (sin a_2j, sin a_2j+1) (-A sin b_r), the same two roundings
+// per term as two scalar FMAs; with PLANES = 2 also the imaginary part, acc[1][r][j] += (sin a) (A cos b_r) +
+// (cos a) (A sin b_r).
+template <int TR, int TILE_W, int TILE_H, int PLANES>
+__device__ __forceinline__ void point_terms_table(const SepQuads<TR, TILE_W, TILE_H> &q,
+                                                  float2 (&acc)[PLANES][TR][4])
 {
     static_assert(TR % 2 == 0, "row pairs in 16-byte quads");
 #pragma unroll
@@ -268,9 +278,16 @@ __device__ __forceinline__ void point_terms_table(const SepQuads<TR, TILE_W, TIL
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float2 c = make_float2(q.c[j].x, q.c[j].y), s = make_float2(q.c[j].z, q.c[j].w);
-            acc[2 * h][j] = __ffma2_rn(s, make_float2(v.y, v.y), __ffma2_rn(c, make_float2(v.x, v.x), acc[2 * h][j]));
-            acc[2 * h + 1][j] =
-                __ffma2_rn(s, make_float2(v.w, v.w), __ffma2_rn(c, make_float2(v.z, v.z), acc[2 * h + 1][j]));
+            acc[0][2 * h][j] =
+                __ffma2_rn(s, make_float2(v.y, v.y), __ffma2_rn(c, make_float2(v.x, v.x), acc[0][2 * h][j]));
+            acc[0][2 * h + 1][j] =
+                __ffma2_rn(s, make_float2(v.w, v.w), __ffma2_rn(c, make_float2(v.z, v.z), acc[0][2 * h + 1][j]));
+            if constexpr (PLANES == 2) {
+                acc[1][2 * h][j] = __ffma2_rn(c, make_float2(-v.y, -v.y),
+                                              __ffma2_rn(s, make_float2(v.x, v.x), acc[1][2 * h][j]));
+                acc[1][2 * h + 1][j] = __ffma2_rn(c, make_float2(-v.w, -v.w),
+                                                  __ffma2_rn(s, make_float2(v.z, v.z), acc[1][2 * h + 1][j]));
+            }
         }
     }
 }
@@ -385,39 +402,45 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
         const int p_lo = k == 0 ? p_first : 0;
         const int p_hi = k == nt - 1 ? p_last_end : T;
         if constexpr (TABLES) {
-            static_assert(PLANES == 1 && TL == 8, "tables serve the amplitude hologram's 8-column blocks");
-            constexpr int TW = BX * TL, TH = BY * TR;
+            static_assert(TL == 8, "tables serve 8-column blocks");
+            static_assert(PLANES == 1 || SFU, "the complex wave takes the hardware sine and cosine");
+            constexpr int TW = BX * TL, TH = BY * TR, GROUP = sep_group<PLANES>();
             using ST = SepTable<TW, TH>;
-            float2 acc[TR][TL / 2];   // columns 2 j and 2 j + 1
+            float2 acc[PLANES][TR][TL / 2];   // columns 2 j and 2 j + 1
 #pragma unroll
-            for (int r = 0; r < TR; ++r)
+            for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-                for (int j = 0; j < TL / 2; ++j) acc[r][j] = make_float2(0.0f, 0.0f);
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int j = 0; j < TL / 2; ++j) acc[c][r][j] = make_float2(0.0f, 0.0f);
             int gi = 0;
 #pragma unroll 1
-            for (int p0 = p_lo; p0 < p_hi; p0 += kSepGroup, ++gi) {
-                const int np = min(kSepGroup, p_hi - p0);
-                float2 *buf = s_tab + (gi & 1) * (kSepGroup * ST::kPerPoint);
-                fill_sep_tables<TW, TH, BX * BY, EXTRA, !SFU>(sg, sa, p0, np, tile_m0, tile_n0, ref, buf, tid);
+            for (int p0 = p_lo; p0 < p_hi; p0 += GROUP, ++gi) {
+                const int np = min(GROUP, p_hi - p0);
+                float2 *buf = s_tab + (gi & 1) * (GROUP * ST::kPerPoint);
+                fill_sep_tables<TW, TH, BX * BY, GROUP, EXTRA, !SFU>(sg, sa, p0, np, tile_m0, tile_n0, ref, buf,
+                                                                     tid);
                 Sync::sync();   // the group's tables are written (the other buffer is no longer read)
-                // unrolled by four, so the compiler overlaps the next points' shared-memory loads with these
-                // FMAs (measured at 1920x1080, 10^4 points with scalar FFMAs: 2.69 ms not unrolled, 2.55 by two,
-                // 2.51 by four, a manual one-point look-ahead ran out of registers, 3.59; with the packed FMAs
-                // 2.32 by two, 2.30 by four)
-#pragma unroll 4
+                // unrolled so that the compiler overlaps the next points' shared-memory loads with these FMAs
+                // (measured at 1920x1080, 10^4 points with scalar FFMAs: 2.69 ms not unrolled, 2.55 by two, 2.51
+                // by four, a manual one-point look-ahead ran out of registers, 3.59; with the packed FMAs 2.32 by
+                // two, 2.30 by four); the complex wave's two planes leave the registers for two
+#pragma unroll(PLANES == 1 ? 4 : 2)
                 for (int g = 0; g < np; ++g) {
                     SepQuads<TR, TW, TH> cur;
                     cur.load(buf + g * ST::kPerPoint, lx * TL, ly * TR);
-                    point_terms_table<TR, TW, TH>(cur, acc);
+                    point_terms_table<TR, TW, TH, PLANES>(cur, acc);
                 }
             }
 #pragma unroll
-            for (int r = 0; r < TR; ++r)
+            for (int c = 0; c < PLANES; ++c)
 #pragma unroll
-                for (int j = 0; j < TL / 2; ++j) {
-                    part[0][r][2 * j] = acc[r][j].x;
-                    part[0][r][2 * j + 1] = acc[r][j].y;
-                }
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int j = 0; j < TL / 2; ++j) {
+                        part[c][r][2 * j] = acc[c][r][j].x;
+                        part[c][r][2 * j + 1] = acc[c][r][j].y;
+                    }
         } else {
             static_assert(PLANES == 1 || SFU, "the complex wave takes the hardware sine and cosine");
 #pragma unroll 1
