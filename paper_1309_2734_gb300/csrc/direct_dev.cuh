@@ -187,65 +187,96 @@ __host__ __device__ constexpr int sep_group()
 }
 
 // The tables of np <= GROUP points p0, p0 + 1, ... for a tile: NTHREADS / GROUP threads a point (a half warp or a
-// warp), each taking its point's turn constants once and then its share of the columns and rows.  A half warp's
-// column stores cover groups q and q + 4 of 8 columns, whose cosines (and sines) fall on disjoint banks.
+// warp), each taking its point's turn constants once and then its share of the columns and rows, one entry at a
+// time (entry(e), e < kEntries: its columns, then its rows), so that a caller can spread them over other work.  A
+// half warp's column stores cover groups q and q + 4 of 8 columns, whose cosines (and sines) fall on disjoint banks.
 template <int TILE_W, int TILE_H, int NTHREADS, int GROUP, bool EXTRA, bool ACC>
-__device__ __forceinline__ void fill_sep_tables(const int4 *sg, const uint2 *sa, int p0, int np, int tile_m0,
-                                                int tile_n0, const PhaseRef &ref, float2 *tab, int tid)
-{
+struct SepFiller {
     using S = SepTable<TILE_W, TILE_H>;
-    constexpr int TPP = NTHREADS / GROUP;   // threads a point
+    static constexpr int TPP = NTHREADS / GROUP;   // threads a point
     static_assert(NTHREADS % GROUP == 0 && (TPP == 16 || TPP == 32), "a half warp or a warp a point");
     static_assert(TILE_W % TPP == 0 && TILE_W % 64 == 0 && TILE_H % TPP == 0,
                   "whole pairs of column groups, whole rows a thread");
-    const int g = tid / TPP, j = tid % TPP;
-    if (g >= np) return;
-    const int p = p0 + g;
-    const int4 q = sg[p];
-    const uint2 w = sa[p];
-    float2 *dst = tab + g * S::kPerPoint;
+    static constexpr int kCols = TILE_W / TPP, kEntries = TILE_W / TPP + TILE_H / TPP;
+
+    int4 q;
+    uint2 w;
+    float2 *dst;
+    int j, tile_m0, tile_n0;
+    uint32_t flip;
+    bool active;
+
+    __device__ __forceinline__ SepFiller(const int4 *sg, const uint2 *sa, int p0, int np, int m0, int n0,
+                                         float2 *tab, int tid)
+    {
+        const int g = tid / TPP;
+        j = tid % TPP;
+        tile_m0 = m0;
+        tile_n0 = n0;
+        active = g < np;
+        const int p = p0 + g;
+        flip = ACC ? 0u : (uint32_t)(p & 1) << 31;   // the flip of every other point (point_terms_sep)
+        dst = tab + g * S::kPerPoint;
+        if (active) {
+            q = sg[p];
+            w = sa[p];
+        }
+    }
+
     // the point's turn at a column (row) coordinate, exact: C d^2 mod 2^64, top 32 bits (d^2 below 2^31)
-    auto turn = [&](int coord, int center) {
+    __device__ __forceinline__ uint32_t turn(int coord, int center) const
+    {
         const uint32_t d = (uint32_t)(coord - center);
         const uint32_t d2 = d * d;
         return (uint32_t)q.z * d2 + __umulhi((uint32_t)q.w, d2);
-    };
-    auto sincos_turn = [&](uint32_t t, float &sn, float &cs) {
+    }
+
+    __device__ __forceinline__ void sincos_turn(uint32_t t, float &sn, float &cs) const
+    {
         if constexpr (ACC) {
             cs = cos_turn_poly(t);
             sn = cos_turn_poly(t - (1u << 30));   // cos 2 pi (t - 1/4)
         } else {
-            t += kHalfBias + ((uint32_t)(p & 1) << 31);   // the flip of every other point (point_terms_sep)
+            t += kHalfBias + flip;
             const float f = __uint_as_float(__funnelshift_r(t, 0x7fu, 9));
             __sincosf(fmaf(f, kK1, -kK0), &sn, &cs);
         }
-    };
-#pragma unroll
-    for (int i = 0; i < TILE_W / TPP; ++i) {
-        const int x = i * (TPP / 8) + (j >> 3);                 // the thread's group of 8 columns, in order ...
-        const int grp = (x & 1) * 4 + ((x >> 1) & 3) + (x & ~7);   // ... taken as 0, 4, 1, 5, 2, 6, 3, 7, 8, 12, ...
-        const int k = grp * 8 + (j & 7);
-        const int coord = tile_m0 + k;
-        uint32_t t = turn(coord, q.x);
-        if constexpr (EXTRA) t += w.x + ref_turn(ref, coord, 0);   // piston and the reference phase's column part
-        float sn, cs;
-        sincos_turn(t, sn, cs);
-        float *c = reinterpret_cast<float *>(dst) + S::col_cos(k);
-        c[0] = cs;
-        c[2] = sn;
     }
-    const float a = __uint_as_float(w.y);
-#pragma unroll
-    for (int i = 0; i < TILE_H / TPP; ++i) {
-        const int k = j + TPP * i;
-        const int coord = tile_n0 + k;
-        uint32_t t = turn(coord, q.y);
-        if constexpr (EXTRA) t += ref_turn(ref, 0, coord) - ref.phi0;   // the reference phase's row part
-        float sn, cs;
-        sincos_turn(t, sn, cs);
-        dst[S::kColStride + k] = make_float2(a * cs, -(a * sn));
+
+    // entry e of the thread (a constant once the caller's loop is unrolled)
+    __device__ __forceinline__ void entry(int e, const PhaseRef &ref) const
+    {
+        if (!active) return;
+        if (e < kCols) {
+            const int x = e * (TPP / 8) + (j >> 3);                 // the thread's group of 8 columns, in order ...
+            const int grp = (x & 1) * 4 + ((x >> 1) & 3) + (x & ~7);   // ... taken as 0, 4, 1, 5, 2, 6, 3, 7, 8, ...
+            const int k = grp * 8 + (j & 7);
+            const int coord = tile_m0 + k;
+            uint32_t t = turn(coord, q.x);
+            if constexpr (EXTRA) t += w.x + ref_turn(ref, coord, 0);   // piston, the reference's column part
+            float sn, cs;
+            sincos_turn(t, sn, cs);
+            float *c = reinterpret_cast<float *>(dst) + S::col_cos(k);
+            c[0] = cs;
+            c[2] = sn;
+        } else {
+            const int k = j + TPP * (e - kCols);
+            const int coord = tile_n0 + k;
+            uint32_t t = turn(coord, q.y);
+            if constexpr (EXTRA) t += ref_turn(ref, 0, coord) - ref.phi0;   // the reference phase's row part
+            float sn, cs;
+            sincos_turn(t, sn, cs);
+            const float a = __uint_as_float(w.y);
+            dst[S::kColStride + k] = make_float2(a * cs, -(a * sn));
+        }
     }
-}
+
+    __device__ __forceinline__ void all(const PhaseRef &ref) const
+    {
+#pragma unroll
+        for (int e = 0; e < kEntries; ++e) entry(e, ref);
+    }
+};
 
 // One point's tables for a thread: its 8 column pairs (from column cx) and TR row pairs (from row ry) as float4s.
 template <int TR, int TILE_W, int TILE_H>
@@ -413,24 +444,55 @@ __device__ __forceinline__ bool direct_unit(const int4 *__restrict__ geo, const 
                 for (int r = 0; r < TR; ++r)
 #pragma unroll
                     for (int j = 0; j < TL / 2; ++j) acc[c][r][j] = make_float2(0.0f, 0.0f);
+            // The next group's tables are filled while this group's are read: for the amplitude hologram the
+            // fill's entries (integer products, hardware or polynomial sines) are spread over the point loop's
+            // packed FMAs (1920x1080, 10^4 points: 1.77 against 1.79 ms filled before the loop; the complex wave,
+            // short of registers, measured 3.26 against 3.21 and fills first); one barrier a group hands the
+            // buffers over.
+            using Filler = SepFiller<TW, TH, BX * BY, GROUP, EXTRA, !SFU>;
+            constexpr int U = PLANES == 1 ? 4 : 2;   // points a step (the loop was measured fastest unrolled by
+                                                     // four, 2.30 ms against 2.32 by two at 1920x1080, 10^4 points;
+                                                     // the complex wave's two planes leave the registers for two)
+            constexpr int kSteps = GROUP / U;
+            constexpr int kPerStep = (Filler::kEntries + kSteps - 1) / kSteps;
+            const int n_grp = (p_hi - p_lo + GROUP - 1) / GROUP;
             int gi = 0;
+            if (n_grp > 0) {
+                Filler(sg, sa, p_lo, min(GROUP, p_hi - p_lo), tile_m0, tile_n0, s_tab, tid).all(ref);
+                Sync::sync();
+            }
 #pragma unroll 1
-            for (int p0 = p_lo; p0 < p_hi; p0 += GROUP, ++gi) {
+            for (int gg = 0; gg < n_grp; ++gg, ++gi) {
+                const int p0 = p_lo + gg * GROUP;
                 const int np = min(GROUP, p_hi - p0);
-                float2 *buf = s_tab + (gi & 1) * (GROUP * ST::kPerPoint);
-                fill_sep_tables<TW, TH, BX * BY, GROUP, EXTRA, !SFU>(sg, sa, p0, np, tile_m0, tile_n0, ref, buf,
-                                                                     tid);
-                Sync::sync();   // the group's tables are written (the other buffer is no longer read)
-                // unrolled so that the compiler overlaps the next points' shared-memory loads with these FMAs
-                // (measured at 1920x1080, 10^4 points with scalar FFMAs: 2.69 ms not unrolled, 2.55 by two, 2.51
-                // by four, a manual one-point look-ahead ran out of registers, 3.59; with the packed FMAs 2.32 by
-                // two, 2.30 by four); the complex wave's two planes leave the registers for two
-#pragma unroll(PLANES == 1 ? 4 : 2)
-                for (int g = 0; g < np; ++g) {
-                    SepQuads<TR, TW, TH> cur;
-                    cur.load(buf + g * ST::kPerPoint, lx * TL, ly * TR);
-                    point_terms_table<TR, TW, TH, PLANES>(cur, acc);
+                const float2 *cur = s_tab + (gi & 1) * (GROUP * ST::kPerPoint);
+                const int pn = p0 + GROUP;
+                const int npn = gg + 1 < n_grp ? min(GROUP, p_hi - pn) : 0;
+                const Filler next(sg, sa, pn, npn, tile_m0, tile_n0, s_tab + ((gi + 1) & 1) * (GROUP * ST::kPerPoint),
+                                  tid);
+                if constexpr (PLANES == 2) next.all(ref);
+                if (PLANES == 1 && np == GROUP) {
+#pragma unroll
+                    for (int st = 0; st < kSteps; ++st) {
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            SepQuads<TR, TW, TH> qd;
+                            qd.load(cur + (st * U + u) * ST::kPerPoint, lx * TL, ly * TR);
+                            point_terms_table<TR, TW, TH, PLANES>(qd, acc);
+                        }
+#pragma unroll
+                        for (int e = st * kPerStep; e < (st + 1) * kPerStep && e < Filler::kEntries; ++e)
+                            next.entry(e, ref);
+                    }
+                } else {   // the complex wave (filled above), or a short last group (nothing to fill after it)
+#pragma unroll U
+                    for (int g = 0; g < np; ++g) {
+                        SepQuads<TR, TW, TH> qd;
+                        qd.load(cur + g * ST::kPerPoint, lx * TL, ly * TR);
+                        point_terms_table<TR, TW, TH, PLANES>(qd, acc);
+                    }
                 }
+                Sync::sync();   // the next group's tables are written, this group's are no longer read
             }
 #pragma unroll
             for (int c = 0; c < PLANES; ++c)
