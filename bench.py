@@ -63,7 +63,7 @@ NCU_TRAFFIC = [
     # profiles/direct_sfu-1920x1080-n10000.md (api.cu holds the launch's CTA count)
     {"kernel": "direct_sfu", "form": "direct_sfu", "workload": "direct-1920x1080-n10000",
      "src": ["direct.cu", "direct_dev.cuh", "device_util.cuh", "api.cu"],
-     "sha1": "09a2a8ad2551e246b73f236952586e1f6c9b1821", "bytes_per_launch": 324096},
+     "sha1": "9b424be116a5758083538cced11cb2c3dd771817", "bytes_per_launch": 365056},
     # profiles/gemm_f16-1920x1080-n50000.md: 600.731 MB read + 3.053 MB written per launch
     {"kernel": "gemm_tcgen05", "form": "gemm_f16", "workload": "gemm-1920x1080-n50000",
      "src": ["gemm.cu", "gemm_dev.cuh", "tcgen05.cuh", "device_util.cuh"],
