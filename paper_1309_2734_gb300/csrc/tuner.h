@@ -21,9 +21,10 @@ struct DirectLayout {
 };
 DirectLayout choose_direct_layout(bool wave, int width, int height, int64_t point_tiles, int num_sms,
                                   int force_split);
-// The same choice among n_shapes CTA shapes (each with its threads and CTAs per SM).
+// The same choice among n_shapes CTA shapes (each with its threads and CTAs per SM); step_cost, if given, scales
+// each shape's predicted path by the relative time of one of its point-tile steps.
 DirectLayout choose_layout(const DirectShape *shapes, int n_shapes, int width, int height, int64_t point_tiles,
-                           int num_sms, int force_split);
+                           int num_sms, int force_split, const double *step_cost = nullptr);
 
 // GEMM orientation, tile width, K splits and form (one CTA per 128-row tile, or the two-SM form: clusters of two
 // CTAs on 256-row tiles) with the shortest predicted time: rounds of units over the ctas CTAs (ctas / 2 clusters)

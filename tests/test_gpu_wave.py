@@ -106,6 +106,16 @@ def test_wave_many_points_sampled_rows():
         _check_wave(got[r:r + 1], ref, 1e-5)
 
 
+def test_wave_wide_block_sampled_rows():
+    """4096 x 32 with 10^5 points: the layout model gives the wave the wide block (16 tiles of 256 x 32 against 32
+    of 128 x 64), whose threads take their own sines and cosines; sampled rows against the oracle."""
+    c = workloads.random_cloud(314, 4096, 32, 100000)
+    got, _ = _wave(c, "direct_sfu")
+    for r in (0, 31):
+        ref = oracle.wave(c.pitch_m, c.lambda_m, c.xyz, c.amp, 4096, 32, window=(r, 0, 1, 4096))
+        _check_wave(got[r:r + 1], ref, 1e-5)
+
+
 def test_kinoform_quantiser_same_field():
     """The GPU phase rule on given float fields against the oracle's on the same values."""
     rng = np.random.default_rng(9)
